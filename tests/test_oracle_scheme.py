@@ -1,0 +1,217 @@
+"""Pins of the oracle march (plain-C FP64 scheme) against what the paper and mathematics fix."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import quadrature as q
+from oracle.couette_exact import (couette_d2qh16_closed_form, couette_semidiscrete,
+                                  free_molecular_pxy)
+from oracle.fixed_point import assemble, solve_steady
+from oracle.march import CAVITY, COUETTE, Problem, make_problem, residual
+from paper_1308_0692_gb300.inputs import random_state
+
+
+def _one_d(kind, n):
+    nodes, weights = q.halfrange_1d(n) if kind == "half" else q.fullrange_1d(n)
+    return [float(v) for v in nodes], [float(v) for v in weights]
+
+
+@pytest.mark.parametrize("kind,n,geom,nx,ny,kn,ub,ut", [
+    ("half", 2, CAVITY, 5, 4, 0.3, 0.0, 0.02),
+    ("half", 4, CAVITY, 3, 3, 0.05, 0.01, -0.02),
+    ("full", 3, CAVITY, 4, 5, 0.1, 0.0, 0.01),
+    ("half", 2, COUETTE, 1, 9, 0.1, 0.01, -0.01),
+    ("half", 2, COUETTE, 3, 4, 1.0, -0.01, 0.01),
+    ("half", 3, COUETTE, 1, 6, math.inf, -0.01, 0.01),
+])
+def test_step_equals_independent_matrix_assembly(kind, n, geom, nx, ny, kn, ub, ut):
+    """One step of the C loops equals A h + b of the separately assembled sparse scheme."""
+    p = make_problem(kind, n, geom, nx, ny, kn, ub, ut)
+    h = random_state(p.n, p.ncells, seed=7)
+    A, b, info = assemble(p.xi_x, p.xi_y, p.w, geom, nx, ny, kn, ub, ut)
+    ref = (A @ h.ravel() + b).reshape(h.shape)
+    got = p.step(h)
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+    assert info["dt"] == p.coeffs["dt"]
+
+
+def test_step_cells_matches_full_step():
+    p = make_problem("half", 4, CAVITY, 7, 6, 0.1, 0.0, 0.01)
+    h = random_state(p.n, p.ncells, seed=3)
+    full = p.step(h)
+    cells = [0, 6, 20, 41, 35, 17]
+    part = p.step_cells(h, cells)
+    np.testing.assert_array_equal(part, full[:, cells].T)
+
+
+@pytest.mark.parametrize("geom,nx,ny", [(CAVITY, 13, 11), (COUETTE, 1, 30), (COUETTE, 4, 9)])
+def test_total_mass_conserved(geom, nx, ny):
+    """Transport with impermeable walls (Eq. 9) and relaxation (Eqs. 5-7) conserve total mass."""
+    p = make_problem("half", 4, geom, nx, ny, 0.05, 0.01, -0.02)
+    h = random_state(p.n, p.ncells, seed=11)
+    m0 = h.sum()
+    h2 = p.step(h, 300)
+    assert abs(h2.sum() - m0) <= 1e-13 * np.abs(h).sum()
+
+
+def test_collision_conserves_density_and_momentum_per_cell():
+    """With collisions only (transport of a uniform field in a periodic column is the identity
+    away from walls), rho and j of every cell are unchanged by the relaxation step."""
+    # periodic channel 8 x 5 at rest, each velocity uniform over all cells: transport is the
+    # identity in the three interior rows, so only the relaxation acts there
+    p = make_problem("half", 4, COUETTE, 8, 5, 0.01, 0.0, 0.0)
+    rng = np.random.default_rng(5)
+    h = np.repeat(rng.standard_normal((p.n, 1)), 40, axis=1)
+    out = p.step(h)
+    interior = [c for c in range(40) if 8 <= c < 32]
+    for c in interior:
+        for mom in (np.ones(p.n), p.xi_x, p.xi_y):
+            assert abs(mom @ out[:, c] - mom @ h[:, c]) <= 1e-14 * np.abs(h[:, c]).sum()
+    # and the relaxation actually acted (h is not an equilibrium)
+    assert np.abs(out - h)[:, interior].max() > 1e-3
+
+
+@pytest.mark.parametrize("n_half", [2, 4])
+def test_couette_antisymmetry(n_half):
+    """Plates at +u and -u: u_x(y) = -u_x(1 - y) (config: plates +0.01 at y=0, -0.01 at y=1)."""
+    p = make_problem("half", n_half, COUETTE, 1, 40, 0.1, 0.01, -0.01)
+    h, steps, r = p.march(p.zeros(), 4000, 100, 1e-9)
+    ux = p.moments(h)["ux"][:, 0]
+    assert np.abs(ux + ux[::-1]).max() <= 1e-15
+    assert ux[0] > 0 > ux[-1]
+
+
+@pytest.mark.parametrize("n_half,ny", [(2, 7), (4, 40), (3, 15)])
+def test_free_molecular_closed_form_shear(n_half, ny):
+    """Kn = inf: the steady shear on every face is the collisionless value (U_b - U_t)/sqrt(2 pi),
+    i.e. -sqrt(2/pi) u_w for plates at -u_w/+u_w (p_fm of the text after Eqs. 10-11)."""
+    u = 0.01
+    p = make_problem("half", n_half, COUETTE, 1, ny, math.inf, -u, u)
+    h, steps, r = p.march(p.zeros(), 200000, 50, 1e-15)
+    flux = p.face_flux_y(h)[:, 0]
+    ref = free_molecular_pxy(-u, u)
+    assert abs(ref + math.sqrt(2 / math.pi) * u) < 1e-17
+    np.testing.assert_allclose(flux, ref, rtol=1e-12, atol=0)
+
+
+def test_kn10_is_not_free_molecular():
+    """Kn = 10 is close to but measurably away from the collisionless limit (about 5.6 %)."""
+    x, w = _one_d("half", 4)
+    sol = couette_semidiscrete(x, w, 10.0, -1.0, 1.0)
+    fm = free_molecular_pxy(-1.0, 1.0)
+    assert 0.04 < (sol["pxy"] - fm) / abs(fm) < 0.07
+
+
+@pytest.mark.parametrize("kn", [0.01, 0.1, 1.0, 10.0])
+def test_semidiscrete_couette_matches_paper_closed_form(kn):
+    """Eqs. (10)-(11) (D2Q^h_16 closed form, 4-digit constants) agree with the semi-discrete
+    eigen-solution for N = 2 to the precision of the printed constants."""
+    x, w = _one_d("half", 2)
+    sol = couette_semidiscrete(x, w, kn, -1.0, 1.0)
+    for yc in (-0.5, -0.25, 0.0, 0.1, 0.5):
+        u_cf, _ = couette_d2qh16_closed_form(kn, yc)
+        assert abs(sol["u"](yc + 0.5) - u_cf) < 3e-4
+    _, p_cf = couette_d2qh16_closed_form(kn, 0.5)
+    assert abs(sol["pxy"] - p_cf) < 3e-4 * abs(p_cf)
+    # decay rate of the Knudsen-layer mode: 1.881 in the closed form's units = sqrt(2)/(xi_1 xi_2)
+    assert abs(sol["decay_rates"][0] * math.sqrt(2) - 1.881) < 1e-3
+    assert abs(sol["decay_rates"][0] - 1.0 / (x[2] * x[3])) < 1e-12
+
+
+def test_semidiscrete_couette_free_molecular_limit():
+    x, w = _one_d("half", 4)
+    sol = couette_semidiscrete(x, w, 1e5, -1.0, 1.0)
+    assert abs(sol["pxy"] - free_molecular_pxy(-1.0, 1.0)) < 1e-4
+
+
+def test_first_order_grid_convergence_to_semidiscrete_solution():
+    """The discrete steady shear converges to the semi-discrete value at first order in dy."""
+    x, w = _one_d("half", 2)
+    exact = couette_semidiscrete(x, w, 0.1, -1.0, 1.0)["pxy"]
+    xi_x, xi_y, ww = q.velocity_set_2d("half", 2)
+    errs = []
+    for ny in (50, 100, 200, 400):
+        h, info, _ = solve_steady(xi_x, xi_y, ww, COUETTE, 1, ny, 0.1, -1.0, 1.0)
+        p = Problem(np.array(xi_x), np.array(xi_y), np.array(ww), COUETTE, 1, ny, 0.1, -1.0, 1.0)
+        flux = p.face_flux_y(h)[:, 0]
+        assert np.ptp(flux) < 1e-10                      # same shear through every face
+        errs.append(abs(flux.mean() - exact))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.8 < r < 2.2 for r in ratios), ratios
+
+
+def test_march_converges_to_direct_steady_solution():
+    """The march's limit is the fully discrete fixed point (Couette, 64 velocities, Kn = 0.1)."""
+    p = make_problem("half", 4, COUETTE, 1, 100, 0.1, 0.01, -0.01)
+    h, steps, r = p.march(p.zeros(), 100000, 100, 1e-13)
+    hd, info, lam = solve_steady(p.xi_x, p.xi_y, p.w, COUETTE, 1, 100, 0.1, 0.01, -0.01)
+    assert r < 1e-13 and abs(lam) < 1e-15
+    assert np.abs(h - hd).max() <= 1e-10 * np.abs(hd).max()
+
+
+def test_near_continuum_linear_profile_with_slip():
+    """Kn = 0.01: the core of the steady profile is linear, with a velocity slip at the plates
+    and a shear stress equal to the (numerical + physical) viscous stress of the core."""
+    u = 0.01
+    xi_x, xi_y, w = q.velocity_set_2d("half", 4)
+    ny = 100
+    h, info, _ = solve_steady(xi_x, xi_y, w, COUETTE, 1, ny, 0.01, u, -u)
+    p = Problem(np.array(xi_x), np.array(xi_y), np.array(w), COUETTE, 1, ny, 0.01, u, -u)
+    ux = p.moments(h)["ux"][:, 0] / u
+    y = (np.arange(ny) + 0.5) / ny
+    core = (y > 0.25) & (y < 0.75)
+    slope = np.polyfit(y[core], ux[core], 1)[0]
+    d2 = np.abs(np.diff(ux[core], 2)).max()
+    assert d2 < 1e-6 * abs(slope) / ny                      # linear core
+    # extrapolate the core line to the plates: the gas does not reach the plate speed (slip)
+    fit = np.polyfit(y[core], ux[core], 1)
+    u_at_wall = np.polyval(fit, 0.0)
+    slip = 1.0 - u_at_wall
+    assert 0.005 < slip < 0.2
+    flux = p.face_flux_y(h)[:, 0] / u
+    assert np.ptp(flux) < 1e-10 * abs(flux).max()           # one shear stress through every face
+    assert flux.mean() * slope < 0                          # p_xy = -mu du/dy: opposite signs
+    # effective viscosity of the core: physical Kn plus first-order upwind diffusion, same order
+    mu_eff = -flux.mean() / slope
+    assert 0.01 < mu_eff < 0.013
+    # the semi-discrete (exact in y) value is approached but first-order error remains at dy = Kn
+    x1, w1 = _one_d("half", 4)
+    exact = couette_semidiscrete(x1, w1, 0.01, 1.0, -1.0)["pxy"]
+    assert 0.05 < (flux.mean() - exact) / exact < 0.2
+
+
+def test_x_axis_rule_does_not_change_couette():
+    """Text after the Couette setup: full-range nodes on the x axis give the same Couette results."""
+    xh, wh = _one_d("half", 2)
+    xf, wf = _one_d("full", 4)
+    set_half = q.mixed_set_2d(xh, wh, xh, wh)
+    set_mixed = q.mixed_set_2d(xf, wf, xh, wh)
+    res = []
+    for xi_x, xi_y, w in (set_half, set_mixed):
+        h, info, _ = solve_steady(xi_x, xi_y, w, COUETTE, 1, 50, 0.1, -0.01, 0.01)
+        p = Problem(np.array(xi_x), np.array(xi_y), np.array(w), COUETTE, 1, 50, 0.1, -0.01, 0.01)
+        res.append((p.moments(h)["ux"][:, 0], p.face_flux_y(h)[:, 0]))
+    np.testing.assert_allclose(res[0][0], res[1][0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(res[0][1], res[1][1], rtol=1e-12, atol=0)
+
+
+def test_cavity_mirror_symmetry_in_the_linear_limit():
+    """Lid-driven cavity at a tiny lid speed: u_x is even and u_y odd about x = 1/2."""
+    u = 1e-8
+    xi_x, xi_y, w = q.velocity_set_2d("half", 2)
+    h, info, _ = solve_steady(xi_x, xi_y, w, CAVITY, 12, 12, 0.2, 0.0, u)
+    p = Problem(np.array(xi_x), np.array(xi_y), np.array(w), CAVITY, 12, 12, 0.2, 0.0, u)
+    m = p.moments(h)
+    ux, uy = m["ux"] / u, m["uy"] / u
+    assert np.abs(ux - ux[:, ::-1]).max() < 1e-6 * np.abs(ux).max()
+    assert np.abs(uy + uy[:, ::-1]).max() < 1e-6 * np.abs(uy).max()
+    assert ux[-1].mean() > 0                  # the gas under the lid follows it
+
+
+def test_residual_definition():
+    a = np.array([[3.0, 4.0]])
+    b = np.zeros_like(a)
+    assert residual(a, b) == 1.0
+    assert residual(b, b) == 0.0
+    assert abs(residual(a, a * 0.5) - 0.5) < 1e-16
