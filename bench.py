@@ -1,0 +1,495 @@
+"""Benchmark of the fused finite-difference LB step on GB300.
+
+Workload (default): lid-driven cavity 2048 x 2048 cells, half-range Gauss-Hermite set
+with N = 6 nodes per half-axis (12 per axis, 144 velocities, 603,979,776 unknowns),
+Kn = 0.05, lid speed 0.01, FP32 perturbation storage, FP64 residual every 10 steps.
+One bench step = one time step of the whole hot path (upwind transport with wall
+ghosts, moments, relaxation; the residual reduction on every 10th step).
+
+Metric: node-velocity updates per second (cells x velocities x steps / s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank marches its own replica of the
+workload (the single-domain march has no data-parallel split without a halo exchange,
+so ranks are independent replicas); value = all ranks' updates / max rank time.
+--impl reference times the CPU oracle (plain FP64 C, all host cores) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "name": "cavity2048_Dh144_fp32",
+    "geom": 1, "nx": 2048, "ny": 2048, "n_half": 6, "kn": 0.05, "u_bottom": 0.0, "u_top": 0.01,
+    "cfl": 0.9, "residual_every": 10,
+}
+METRIC = "node-velocity updates/s"
+UNIT = "updates/s"
+E2E_STEPS = 100            # time steps per end-to-end API call (one residual interval)
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ---------------------------------------------------------------- distributed plumbing
+class Dist:
+    """Rank bookkeeping; N > 1 runs independent replicas, the only collectives are the
+    timing barrier and the max-over-ranks of the elapsed time."""
+
+    def __init__(self, backend: str | None = None):
+        self.world = _env_int("WORLD_SIZE", 1)
+        self.rank = _env_int("RANK", 0)
+        self.local_rank = _env_int("LOCAL_RANK", 0)
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend or ("nccl" if _cuda_ok() else "gloo"))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, value: float) -> float:
+        if not self.pg:
+            return value
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, value: float) -> float:
+        if not self.pg:
+            return value
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def _cuda_ok() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def aggregate(units_per_rank: float, seconds_per_rank: float, dist: Dist):
+    """Whole-job throughput: all ranks' units / the slowest rank's time."""
+    t = dist.max(seconds_per_rank)
+    u = dist.sum(units_per_rank)
+    return u / t, t
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_index}",
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def clocks_bad(clk: dict) -> bool:
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if any(r in bad for r in clk.get("reasons", [])):
+        return True
+    sm, smax = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    if sm and smax and sm < 0.6 * smax and "sw_power_cap" not in clk.get("reasons", []):
+        return True
+    return False
+
+
+# ---------------------------------------------------------------- own arm
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic_record(kernel_key: str):
+    """ncu DRAM bytes per launch for the kernel, if captured for the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel_key)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1308_0692_gb300", "csrc", "step_kernel.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != digest:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_own(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    from paper_1308_0692_gb300 import lbm
+
+    torch.cuda.set_device(dist.local_rank)
+    dev_index = torch.cuda.current_device()
+    w = WORKLOAD
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, w["n_half"])
+    n_vel = (2 * w["n_half"]) ** 2
+    prob = lbm.make_problem(w["geom"], w["nx"], w["ny"], w["kn"], w["u_bottom"], w["u_top"], w["cfl"],
+                            lbm.LBM_FP32_PERTURB, w["residual_every"])
+    stream = torch.cuda.Stream()
+    buf = torch.empty(lbm.lbm_sim_bytes(vs, prob), dtype=torch.uint8, device="cuda")
+    sim = lbm.lbm_init(vs, prob, None, device_buf=buf, stream=stream)
+    ncells = w["nx"] * w["ny"]
+    units_per_step = ncells * n_vel
+
+    def timed_block(K):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(K):
+            starts[i].record(stream)
+            lbm.lbm_step(sim, 1)
+            ends[i].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        total = t0.elapsed_time(t1) / 1e3
+        per = [s.elapsed_time(e) / 1e3 for s, e in zip(starts, ends)]
+        return total, per
+
+    lbm.lbm_step(sim, args.warmup)
+    torch.cuda.synchronize()
+    for attempt in range(2):
+        sampler = ClockSampler(dev_index)
+        sampler.start()
+        time.sleep(0.3)
+        _, step0 = lbm.lbm_state_device(sim)
+        total, per = timed_block(args.steps)
+        clk = sampler.stop()
+        if not clocks_bad(clk):
+            break
+    value, tmax = aggregate(units_per_step * args.steps, total, dist)
+    r, rstep = lbm.lbm_residual(sim)
+
+    # dominant kernel: the plain fused step (steps whose index is not a residual step)
+    plain = [d for i, d in enumerate(per) if (step0 + i + 1) % w["residual_every"] != 0]
+    resid = [d for i, d in enumerate(per) if (step0 + i + 1) % w["residual_every"] == 0]
+    algo_bytes = 8 * units_per_step          # read + write of every FP32 value
+    avg = sum(plain) / len(plain)
+    peak, peak_kind = _peaks()
+    achieved = algo_bytes / avg / 1e9
+    n_resid = len(resid)
+    launches = args.steps + n_resid        # step kernels + residual finalisations
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "lid-driven cavity 2048x2048, D2Q^h_144 (N=6 half-range Gauss-Hermite), "
+                               "Kn=0.05, lid u=0.01, FP32 perturbation storage, FP64 residual every 10 steps",
+                   "nx": w["nx"], "ny": w["ny"], "velocities": n_vel, "unknowns": units_per_step,
+                   "residual_every": w["residual_every"], "cold_start": True,
+                   "l2": "inputs larger than L2 (2.42 GB per state copy), no flush",
+                   "parallelism": f"replicas{dist.world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "step_kernel<float,float,12,G>", "algorithmic_bytes_per_launch": algo_bytes,
+                     "avg_launch_ms": avg * 1e3,
+                     "traffic": _traffic_record("step_f32_m12")},
+        "residual_step_ms": (sum(resid) / len(resid) * 1e3) if resid else None,
+        "last_residual": [r, rstep],
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(sim, prob, n_vel, ncells, stream, dist, args)
+    if not args.no_extras:
+        out["fp64"] = run_fp64_same_workload(vs, dist)
+        out["time_to_residual"] = run_time_to_residual(dist)
+    sim.close()
+    del buf
+    return out
+
+
+def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
+    """Same metric through the public C-ABI with host buffers: upload a host FP64 state
+    (pinned), march E2E_STEPS steps, read back the residual and u_x, u_y."""
+    import ctypes
+
+    import torch
+
+    from paper_1308_0692_gb300 import lbm
+
+    lib = lbm.library()
+    nvals = n_vel * ncells
+    host_h = torch.zeros(nvals, dtype=torch.float64).pin_memory()
+    ux = torch.empty(ncells, dtype=torch.float64).pin_memory()
+    uy = torch.empty(ncells, dtype=torch.float64).pin_memory()
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def one():
+        lbm._check(lib.lbm_set_state(sim.handle, ctypes.cast(host_h.data_ptr(), dp)))
+        lbm.lbm_step(sim, E2E_STEPS)
+        lbm.lbm_residual(sim)
+        lbm._check(lib.lbm_moments(sim.handle, None, ctypes.cast(ux.data_ptr(), dp),
+                                   ctypes.cast(uy.data_ptr(), dp), None, None, None, None))
+
+    one()
+    reps = 3
+    dist.barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    value, _ = aggregate(float(nvals) * E2E_STEPS * reps, el, dist)
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nvals * 8,
+            "d2h_bytes_per_step": 2 * ncells * 8 + 32,
+            "definition": f"one API call = lbm_set_state(host FP64, pinned) + lbm_step({E2E_STEPS}) + "
+                          "lbm_residual + lbm_moments(ux, uy); value counts the marched updates"}
+
+
+def run_fp64_same_workload(vs, dist):
+    """The plain FP64 march of the same workload (FP64 storage and arithmetic), few steps."""
+    import torch
+
+    from paper_1308_0692_gb300 import lbm
+    w = WORKLOAD
+    prob = lbm.make_problem(w["geom"], w["nx"], w["ny"], w["kn"], w["u_bottom"], w["u_top"], w["cfl"],
+                            lbm.LBM_FP64, w["residual_every"])
+    stream = torch.cuda.Stream()
+    sim = lbm.lbm_init(vs, prob, None, stream=stream)
+    lbm.lbm_step(sim, 3)
+    K = 20
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    lbm.lbm_step(sim, K)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    sec = t0.elapsed_time(t1) / 1e3
+    units = w["nx"] * w["ny"] * (2 * w["n_half"]) ** 2 * K
+    sim.close()
+    return {"value": units / sec, "unit": UNIT, "steps": K, "ms_per_step": sec / K * 1e3,
+            "achieved_hbm_gbs": 16 * units / sec / 1e9,
+            "note": "FP64 storage+arithmetic; bounded by the FP64 pipe of GB300, not HBM"}
+
+
+def run_time_to_residual(dist):
+    """Cavity 128x128, 64 half-range velocities, Kn = 0.1, lid 0.01: plain FP64 march from
+    the cold start to residual < 1e-8 (checked every 100 steps)."""
+    import torch
+
+    from paper_1308_0692_gb300 import lbm
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    prob = lbm.make_problem(1, 128, 128, 0.1, 0.0, 0.01, 0.9, lbm.LBM_FP64, 100)
+    stream = torch.cuda.Stream()
+    sim = lbm.lbm_init(vs, prob, None, stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    steps = 0
+    r = math.inf
+    while steps < 400000:
+        lbm.lbm_step(sim, 100)
+        steps += 100
+        r, _ = lbm.lbm_residual(sim)
+        if r < 1e-8:
+            break
+    el = time.perf_counter() - t
+    sim.close()
+    return {"workload": "cavity 128x128, D2Q^h_64, Kn=0.1, lid 0.01, cold start",
+            "fp64": {"seconds": el, "steps": steps, "residual": r,
+                     "updates_per_s": 128 * 128 * 64 * steps / el}}
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+def _oracle_setup(rows: int):
+    import numpy as np
+
+    from oracle.march import CAVITY, make_problem
+    w = WORKLOAD
+    p = make_problem("half", w["n_half"], CAVITY, w["nx"], w["ny"], w["kn"], w["u_bottom"], w["u_top"], w["cfl"])
+    nx = w["nx"]
+    # a band of rows in the middle of the grid; the state is zero elsewhere (never read)
+    rows = max(1, min(rows, w["ny"] - 2))
+    r0 = max(1, w["ny"] // 2 - rows // 2)
+    h = np.zeros((p.n, p.ncells))
+    rng = np.random.default_rng(4)
+    lo, hi = (r0 - 1) * nx, (r0 + rows + 1) * nx
+    h[:, lo:hi] = rng.standard_normal((p.n, hi - lo))
+    cells = np.arange(r0 * nx, (r0 + rows) * nx, dtype=np.int64)
+    return p, h, cells
+
+
+def oracle_sample(seconds_target: float, threads: int):
+    """Time the oracle's step on bands of cells of the workload grid with `threads` host
+    threads (each calling the oracle on its own chunk).  Returns (updates/s, sample)."""
+    p, h, cells = _oracle_setup(rows=8)
+    chunks = [c for c in __import__("numpy").array_split(cells, threads) if len(c)]
+
+    def one_pass():
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda c: p.step_cells(h, c), chunks))
+
+    one_pass()
+    t = time.perf_counter()
+    passes = 0
+    while True:
+        one_pass()
+        passes += 1
+        el = time.perf_counter() - t
+        if el >= seconds_target:
+            break
+    ups = len(cells) * p.n * passes / el
+    return ups, {"cells_per_pass": int(len(cells)), "passes": passes, "seconds": el}
+
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return None
+    from oracle import march
+    march.build()
+    threads = os.cpu_count() or 1
+    ups_probe, _ = oracle_sample(1.0, threads)
+    # size each bench step so that warmup + steps end in about a minute
+    budget = 60.0
+    per_step_updates = max(144 * 2048, ups_probe * budget / max(1, args.steps + args.warmup))
+    rows = max(1, min(int(per_step_updates / (2048 * 144)), WORKLOAD["ny"] - 2))
+    p, h, cells = _oracle_setup(rows=rows)
+    import numpy as np
+    chunks = [c for c in np.array_split(cells, threads) if len(c)]
+
+    def step():
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda c: p.step_cells(h, c), chunks))
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t
+    units = len(cells) * p.n * args.steps
+    value = units / el
+    sample = (f"{rows} grid rows ({len(cells)} cells x {p.n} velocities) of the 2048x2048 cavity per step, "
+              f"oracle step evaluated cell by cell on {threads} host threads")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "lid-driven cavity 2048x2048, D2Q^h_144 (N=6 half-range Gauss-Hermite), "
+                                   "Kn=0.05, lid u=0.01 (CPU oracle, FP64)", "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- main
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        dist = Dist(backend="gloo") if _env_int("WORLD_SIZE", 1) > 1 else Dist()
+        out = run_reference(args, dist)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        dist.close()
+        return 0
+    dist = Dist()
+    out = run_own(args, dist)
+    if dist.rank == 0:
+        if dist.world == 1 and not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            ups, sample = oracle_sample(12.0, threads)
+            out["cpu_baseline"] = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                   "sample": f"oracle FP64 step on {sample['cells_per_pass']} cells "
+                                             f"(8 middle rows) of the 2048x2048 x 144 workload, "
+                                             f"{sample['passes']} passes in {sample['seconds']:.1f} s"}
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * lbm.h -- C-ABI of the GB300 (sm_103a) half-range finite-difference lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * Method: Ghiroldi & Gibelli, "A finite-difference lattice Boltzmann approach for
+ * gas microflows" (arXiv:1308.0692).  The library marches the discrete,
+ * linearised BGKW equation (Eq. 1) on a half-range (or full-range) Gauss-Hermite
+ * velocity set (Table 1, tensor product in 2-D) with Maxwell diffuse walls
+ * (Eqs. 8-9), using the paper's fully discrete scheme: first-order time
+ * splitting, first-order upwind transport, explicit Euler relaxation.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an lbm_status; nothing is thrown or aborted across
+ *     the ABI.  On failure lbm_last_error() (thread-local) describes the cause.
+ *   - Opaque objects (lbm_vset, lbm_sim) are owned by the library: free them with
+ *     lbm_vset_destroy / lbm_destroy.  Host arrays are owned by the caller.
+ *   - Host field arrays are FP64, row-major [ny][nx] (cell index c = y*nx + x).
+ *     Distribution arrays are structure-of-arrays [n][ny][nx] (index a*ncells + c)
+ *     of the perturbation h_a = (f_a - w_a) / u_ref, u_ref = max(|u_bottom|,|u_top|)
+ *     (1 when both are zero).
+ *   - Device work is enqueued on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  lbm_step is asynchronous;
+ *     lbm_residual, lbm_moments, lbm_face_flux and lbm_get_state synchronise that
+ *     stream.
+ *   - Units are those of Eq. (1): lengths in units of l (plate gap / cavity side),
+ *     velocities in units of sqrt(R T0), densities in units of the reference.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,       /* invalid argument (sizes, Kn <= 0, CFL, NULL pointers, ...) */
+    LBM_ENOMEM = 2,       /* device or host allocation failed, or caller buffer too small */
+    LBM_ECUDA = 3,        /* a CUDA runtime call failed */
+    LBM_ENONFINITE = 4,   /* a reduction met a NaN or Inf */
+    LBM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    LBM_EUNSUPPORTED = 6  /* valid request with no kernel (e.g. a velocity-set size) */
+} lbm_status;
+
+typedef enum { LBM_HALF_RANGE_GH = 0, LBM_FULL_RANGE_GH = 1 } lbm_vset_kind;
+typedef enum { LBM_COUETTE = 0, LBM_CAVITY = 1 } lbm_geometry;
+typedef enum { LBM_FP64 = 0, LBM_FP32_PERTURB = 1 } lbm_precision;
+
+typedef struct lbm_vset lbm_vset;
+typedef struct lbm_sim lbm_sim;
+
+/* One boundary-value problem (the two flows of the paper's examples).
+ *   geom      LBM_COUETTE: nx columns periodic in x, ny cells between plates at
+ *             y = 0 (speed u_bottom along x) and y = 1 (speed u_top); square cells
+ *             of side 1/ny.  LBM_CAVITY: unit square, nx x ny cells, diffuse walls
+ *             on all faces, bottom moving at u_bottom, top (the lid) at u_top,
+ *             side walls at rest.
+ *   kn        Knudsen number of Eq. (1), > 0; +inf switches collisions off.
+ *   cfl       dt = cfl / (max|xi_x|/dx + max|xi_y|/dy), the x term dropped for a single
+ *             periodic Couette column, then dt <= kn.  0 < cfl <= 1.
+ *   prec      LBM_FP64: FP64 storage and arithmetic.  LBM_FP32_PERTURB: FP32 storage
+ *             and arithmetic of h; FP64 wall sums and reductions.
+ *   residual_every  the relative residual ||h^{n+1}-h^n|| / ||h^{n+1}|| is evaluated
+ *             on every step whose index is a multiple of it and on the last step of
+ *             every lbm_step call (>= 1). */
+typedef struct {
+    int geom;
+    int nx, ny;
+    double kn;
+    double u_bottom, u_top;
+    double cfl;
+    int prec;
+    int residual_every;
+} lbm_problem;
+
+/* Build the 2-D tensor-product velocity set (Table 1 and the paragraph after it).
+ *   kind LBM_HALF_RANGE_GH: n = N Gauss nodes per half-axis of the weight
+ *        exp(-xi^2/2)/sqrt(2 pi) on [0, inf), mirrored; M = 2N nodes per axis, M^2
+ *        velocities (N = 2: D2Q^h_16, N = 4: D2Q^h_64, N = 6: D2Q^h_144).  1 <= N <= 8.
+ *   kind LBM_FULL_RANGE_GH: n = M Gauss-Hermite nodes per axis on the whole line
+ *        (M = 3: the standard D2Q9).  2 <= M <= 16.
+ * Computed on the host in double-double arithmetic and rounded to FP64.
+ * Velocity a = iy*M + ix has xi = (node[ix], node[iy]), weight wt[ix]*wt[iy];
+ * nodes ascending.  *out receives a new object (free with lbm_vset_destroy). */
+lbm_status lbm_make_velocity_set(int kind, int n, lbm_vset **out);
+
+/* Query a velocity set.  *n_vel = M^2, *m = M.  Arrays, when non-NULL, receive
+ * xi_x[n_vel], xi_y[n_vel], w[n_vel] (caller-sized). */
+lbm_status lbm_vset_query(const lbm_vset *vs, int *n_vel, int *m, double *xi_x, double *xi_y,
+                          double *w);
+void lbm_vset_destroy(lbm_vset *vs);
+
+/* Device bytes a simulation of this problem needs when the caller provides the memory. */
+lbm_status lbm_sim_bytes(const lbm_vset *vs, const lbm_problem *prob, size_t *bytes);
+
+/* Create a simulation (Eqs. 1, 5-9 on the grid of `prob`).
+ *   init_h      host FP64 [n][ny][nx] initial perturbation, or NULL for the cold start
+ *               h = 0 (f_a = w_a: rho = 1, u = 0).
+ *   device_buf  caller-owned device memory of at least lbm_sim_bytes() bytes, 256-byte
+ *               aligned, which must outlive the simulation; NULL = the library allocates
+ *               (and frees in lbm_destroy).
+ *   stream      cudaStream_t on which all device work of this simulation is ordered.
+ * Returns LBM_EUNSUPPORTED for a velocity-set size without a compiled kernel
+ * (supported: M in {3, 4, 6, 8, 12}). */
+lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *init_h,
+                    void *device_buf, size_t buf_bytes, void *stream, lbm_sim **out);
+void lbm_destroy(lbm_sim *sim);
+
+/* Coefficients the simulation uses: time step dt, relaxation factor omega = dt/Kn,
+ * reference speed u_ref (any pointer may be NULL). */
+lbm_status lbm_coeffs(const lbm_sim *sim, double *dt, double *omega, double *u_ref);
+
+/* Advance nsteps >= 0 time steps (asynchronous, stream-ordered).  Each step is one
+ * fused pass: upwind transport with wall ghosts (Eqs. 8-9), moments (Eqs. 6-7),
+ * relaxation towards w_a (rho + xi_a . j) (Eqs. 1, 5). */
+lbm_status lbm_step(lbm_sim *sim, long nsteps);
+
+/* Latest relative residual r and the step count at which it was evaluated
+ * (synchronises).  LBM_ENONFINITE if the state contains NaN/Inf. */
+lbm_status lbm_residual(lbm_sim *sim, double *r, long *step);
+
+/* Macroscopic fields of the current state, Eq. (1) units, linearised about rho = 1:
+ *   rho = 1 + u_ref sum h, u = u_ref sum xi h / rho, P_ij = delta_ij + u_ref sum xi_i xi_j h.
+ * Each output is host FP64 [ny][nx] or NULL.  wall_shear (NULL or double[4]) receives
+ * the mean tangential momentum flux through the bottom, top, left and right walls
+ * (the drag the gas exerts; left/right are 0 for Couette).  Synchronises. */
+lbm_status lbm_moments(lbm_sim *sim, double *rho, double *ux, double *uy, double *pxx,
+                       double *pxy, double *pyy, double *wall_shear);
+
+/* Momentum flux through the cell faces, u_ref sum xi_x xi_y h_upwind, with the wall
+ * ghost as upwind value on a wall face.  flux_y (NULL or host [ny+1][nx]): horizontal
+ * faces, row j between cells j-1 and j (j = 0 bottom wall, j = ny top wall).  flux_x
+ * (NULL or host [ny][nx+1], cavity only): vertical faces.  Synchronises. */
+lbm_status lbm_face_flux(lbm_sim *sim, double *flux_y, double *flux_x);
+
+/* Copy the current state to / from host FP64 [n][ny][nx].  get synchronises. */
+lbm_status lbm_get_state(lbm_sim *sim, double *h);
+lbm_status lbm_set_state(lbm_sim *sim, const double *h);
+
+/* Device pointer of the current state (FP64 or FP32 elements per the precision) and
+ * the step counter.  The pointer changes after every step (double buffering). */
+lbm_status lbm_state_device(lbm_sim *sim, void **ptr, long *step);
+
+/* Squared norms of device vectors, FP64 accumulation (the residual reduction):
+ *   out[0] = sum (a_i - b_i)^2, out[1] = sum a_i^2, i < count; b may be NULL (then
+ *   out[0] = out[1]).
+ *   prec      element type of a and b (LBM_FP64 or LBM_FP32_PERTURB: float).
+ *   scratch   device memory of at least lbm_norms_scratch_bytes(count) bytes for the
+ *             per-block partial sums (caller-owned).
+ *   out       device pointer to 2 doubles (written stream-ordered).
+ * Deterministic (fixed summation order).  Not part of the paper: the residual
+ * definition the march uses, exported for callers that keep their own buffers. */
+lbm_status lbm_norms_scratch_bytes(long count, size_t *bytes);
+lbm_status lbm_norms(const void *a, const void *b, long count, int prec, void *scratch,
+                     size_t scratch_bytes, double *out, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

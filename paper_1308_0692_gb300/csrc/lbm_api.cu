@@ -1,0 +1,582 @@
+// C-ABI of liblbm.so (declarations and contracts in include/lbm.h).
+//
+// Host side of the march: velocity-set construction, coefficients of the fully
+// discrete scheme (time step from the CFL number, upwind Courant numbers, relaxation
+// factor, wall-ghost coefficients of Eqs. 8-9), device memory layout, and the
+// stream-ordered launch sequence of the fused step kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+cudaError_t launch_step_f64(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
+                               cudaStream_t s);
+
+struct lbm_vset {
+    int kind;
+    int n_arg;
+    int m;
+    std::vector<double> nodes, weights;   // 1-D rule, ascending
+    std::vector<double> xi_x, xi_y, w;    // 2-D tensor product, a = iy*M + ix
+};
+
+struct lbm_sim {
+    lbm_vset vs;
+    lbm_problem prob;
+    int nv;
+    long ncells;
+    double dt, dx, dy, omega, u_ref;
+    cudaStream_t stream;
+    int lanes;            // lanes per cell of the step kernel
+    int grid;             // blocks of one step launch
+    // device memory
+    void *base;
+    bool owns;
+    size_t bytes;
+    void *buf[4];         // state ping-pong (0,1); refinement: defect (2), correction (3)
+    int cur;              // index of the current state buffer
+    double *tab64;
+    float *tab32;
+    TableHeader *hdr;
+    double *partials;
+    int npartials;
+    double *result;       // [0] sum d^2, [1] sum h^2, [2] r, [3] non-finite flag
+    double *moments;      // 6 * ncells
+    double *flux_y;       // (ny+1) * nx
+    double *flux_x;       // ny * (nx+1)
+    double *host_res;     // pinned host copy of result
+    long step;
+    long resid_step;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+lbm_status fail(lbm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t elem_size(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(float); }
+
+bool kernel_m_supported(int m) { return m == 3 || m == 4 || m == 6 || m == 8 || m == 12; }
+
+struct Layout {
+    size_t off_buf[4];
+    size_t off_tab64, off_tab32, off_hdr, off_partials, off_result, off_moments, off_fy, off_fx;
+    size_t total;
+    int nbuf;
+    int npartials;
+};
+
+Layout make_layout(const lbm_vset *vs, const lbm_problem *p)
+{
+    Layout L{};
+    const long ncells = (long)p->nx * p->ny;
+    const size_t nvals = (size_t)vs->m * vs->m * ncells;
+    const size_t es = elem_size(p->prec);
+    L.nbuf = (p->prec == LBM_FP64) ? 2 : 4;
+    size_t off = 0;
+    for (int i = 0; i < L.nbuf; ++i) {
+        L.off_buf[i] = off;
+        off = align256(off + nvals * es);
+    }
+    // FP32: buf[2] and buf[3] are adjacent, so from buf[2] on there are at least
+    // 8 bytes per value: the FP64 staging area of state upload/download
+    L.off_tab64 = off;
+    off = align256(off + sizeof(double) * TAB_ROWS * LBM_MAX_V);
+    L.off_tab32 = off;
+    off = align256(off + sizeof(float) * TAB_ROWS * LBM_MAX_V);
+    L.off_hdr = off;
+    off = align256(off + sizeof(TableHeader));
+    // the finest launch has LBM_BLOCK/4 cells per block; norms use at most 152*8 blocks
+    long nb = (ncells + LBM_BLOCK / 4 - 1) / (LBM_BLOCK / 4);
+    if (nb < 152 * 8) nb = 152 * 8;
+    L.npartials = (int)nb;
+    L.off_partials = off;
+    off = align256(off + sizeof(double) * 2 * nb);
+    L.off_result = off;
+    off = align256(off + sizeof(double) * 8);
+    L.off_moments = off;
+    off = align256(off + sizeof(double) * 6 * ncells);
+    L.off_fy = off;
+    off = align256(off + sizeof(double) * (size_t)(p->ny + 1) * p->nx);
+    L.off_fx = off;
+    off = align256(off + sizeof(double) * (size_t)p->ny * (p->nx + 1));
+    L.total = off;
+    return L;
+}
+
+lbm_status validate(const lbm_vset *vs, const lbm_problem *p)
+{
+    if (!vs || !p) return fail(LBM_EINVAL, "NULL velocity set or problem");
+    if (p->geom != LBM_COUETTE && p->geom != LBM_CAVITY)
+        return fail(LBM_EINVAL, "geom must be LBM_COUETTE or LBM_CAVITY");
+    if (p->nx < 1 || p->ny < 2) return fail(LBM_EINVAL, "grid %d x %d too small", p->nx, p->ny);
+    if (p->geom == LBM_CAVITY && p->nx < 2) return fail(LBM_EINVAL, "cavity needs nx >= 2");
+    if ((long)p->nx * p->ny > (1L << 31)) return fail(LBM_EINVAL, "grid too large");
+    if (!(p->kn > 0)) return fail(LBM_EINVAL, "Kn must be > 0 (got %g)", p->kn);
+    if (!(p->cfl > 0 && p->cfl <= 1)) return fail(LBM_EINVAL, "cfl must be in (0, 1] (got %g)", p->cfl);
+    if (!std::isfinite(p->u_bottom) || !std::isfinite(p->u_top))
+        return fail(LBM_EINVAL, "wall speeds must be finite");
+    if (p->prec != LBM_FP64 && p->prec != LBM_FP32_PERTURB)
+        return fail(LBM_EINVAL, "unknown precision %d", p->prec);
+    if (p->residual_every < 1) return fail(LBM_EINVAL, "residual_every must be >= 1");
+    if (!kernel_m_supported(vs->m))
+        return fail(LBM_EUNSUPPORTED, "no step kernel for %d nodes per axis (have 3, 4, 6, 8, 12)", vs->m);
+    return LBM_OK;
+}
+
+// dt, Courant numbers, relaxation and ghost coefficients (host, FP64)
+void fill_tables(lbm_sim *s, std::vector<double> &t64, std::vector<float> &t32, TableHeader &hdr)
+{
+    const lbm_problem &p = s->prob;
+    const lbm_vset &v = s->vs;
+    const int m = v.m, nv = m * m;
+    double mx = 0, dxw = 0, dyw = 0;
+    for (int i = 0; i < m; ++i) mx = std::fmax(mx, std::fabs(v.nodes[i]));
+    for (int a = 0; a < nv; ++a) {
+        if (v.xi_x[a] > 0) dxw += v.xi_x[a] * v.w[a];
+        if (v.xi_y[a] > 0) dyw += v.xi_y[a] * v.w[a];
+    }
+    if (p.geom == LBM_COUETTE) {
+        s->dy = 1.0 / p.ny;
+        s->dx = s->dy;
+    } else {
+        s->dx = 1.0 / p.nx;
+        s->dy = 1.0 / p.ny;
+    }
+    double rate = mx / s->dy;
+    if (!(p.geom == LBM_COUETTE && p.nx == 1)) rate += mx / s->dx;
+    s->dt = p.cfl / rate;
+    if (std::isfinite(p.kn) && s->dt > p.kn) s->dt = p.kn;
+    s->omega = std::isfinite(p.kn) ? s->dt / p.kn : 0.0;
+    s->u_ref = std::fmax(std::fabs(p.u_bottom), std::fabs(p.u_top));
+    if (s->u_ref == 0) s->u_ref = 1.0;
+
+    t64.assign((size_t)TAB_ROWS * LBM_MAX_V, 0.0);
+    for (int a = 0; a < nv; ++a) {
+        const double nux = std::fabs(v.xi_x[a]) * s->dt / s->dx;
+        const double nuy = std::fabs(v.xi_y[a]) * s->dt / s->dy;
+        // a Couette column of width one cell has no x transport
+        const double nux_eff = (p.geom == LBM_COUETTE && p.nx == 1) ? 0.0 : nux;
+        t64[TAB_A0 * LBM_MAX_V + a] = 1.0 - nux_eff - nuy;
+        t64[TAB_NUX * LBM_MAX_V + a] = nux_eff;
+        t64[TAB_NUY * LBM_MAX_V + a] = nuy;
+        t64[TAB_CW * LBM_MAX_V + a] = s->omega * v.w[a];
+        t64[TAB_GB_LIN * LBM_MAX_V + a] = v.w[a] * (1.0 + v.xi_x[a] * p.u_bottom);
+        t64[TAB_GB_C * LBM_MAX_V + a] = v.w[a] * v.xi_x[a] * p.u_bottom / s->u_ref;
+        t64[TAB_GT_LIN * LBM_MAX_V + a] = v.w[a] * (1.0 + v.xi_x[a] * p.u_top);
+        t64[TAB_GT_C * LBM_MAX_V + a] = v.w[a] * v.xi_x[a] * p.u_top / s->u_ref;
+        t64[TAB_W * LBM_MAX_V + a] = v.w[a];
+    }
+    t32.resize(t64.size());
+    for (size_t i = 0; i < t64.size(); ++i) t32[i] = (float)t64[i];
+    std::memset(&hdr, 0, sizeof hdr);
+    for (int i = 0; i < m; ++i) hdr.xi1[i] = v.nodes[i];
+    hdr.b = 1.0 - s->omega;
+    hdr.inv_dx_wall = 1.0 / dxw;
+    hdr.inv_dy_wall = 1.0 / dyw;
+}
+
+lbm_status upload_state(lbm_sim *s, const double *h, void *dst)
+{
+    const size_t nvals = (size_t)s->nv * s->ncells;
+    cudaError_t e;
+    if (s->prob.prec == LBM_FP64) {
+        e = cudaMemcpyAsync(dst, h, nvals * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    } else {
+        // FP64 host values staged in the two spare float arrays (adjacent, 8 bytes per
+        // value in total), rounded to float on the device
+        double *stage = (double *)s->buf[2];
+        e = cudaMemcpyAsync(stage, h, nvals * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = launch_convert(stage, (float *)dst, (long)nvals, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "uploading the state");
+}
+
+StepArgs base_args(const lbm_sim *s)
+{
+    StepArgs a{};
+    a.tab64 = s->tab64;
+    a.tab32 = s->tab32;
+    a.hdr = s->hdr;
+    a.partials = s->partials;
+    a.nx = s->prob.nx;
+    a.ny = s->prob.ny;
+    a.ncells = s->ncells;
+    a.cavity = s->prob.geom == LBM_CAVITY;
+    a.homogeneous = 0;
+    return a;
+}
+
+int grid_for(long ncells, int lanes)
+{
+    const long cpb = LBM_BLOCK / lanes;
+    return (int)((ncells + cpb - 1) / cpb);
+}
+
+}  // namespace
+
+int default_lanes_per_cell(int prec, int m)
+{
+    if (prec == LBM_FP64) return m <= 6 ? 1 : (m == 8 ? 2 : 4);
+    return m <= 8 ? 1 : 2;
+}
+
+bool step_supported(int prec, int m, int g)
+{
+    static const int f64[][2] = {{3, 1}, {4, 1}, {6, 1}, {6, 2}, {8, 2}, {8, 4}, {12, 2}, {12, 4}};
+    static const int f32[][2] = {{3, 1}, {4, 1}, {6, 1}, {6, 2}, {8, 1}, {8, 2}, {12, 1}, {12, 2}, {12, 4}};
+    if (prec == LBM_FP64) {
+        for (auto &v : f64) if (v[0] == m && v[1] == g) return true;
+    } else {
+        for (auto &v : f32) if (v[0] == m && v[1] == g) return true;
+    }
+    return false;
+}
+
+cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
+                        cudaStream_t s)
+{
+    return prec == LBM_FP64 ? launch_step_f64(m, g, resid, a, grid, s)
+                            : launch_step_f32(m, g, resid, a, grid, s);
+}
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_make_velocity_set(int kind, int n, lbm_vset **out)
+{
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (kind != LBM_HALF_RANGE_GH && kind != LBM_FULL_RANGE_GH)
+        return fail(LBM_EINVAL, "unknown velocity-set kind %d", kind);
+    if (kind == LBM_HALF_RANGE_GH && (n < 1 || n > 8))
+        return fail(LBM_EINVAL, "half-range sets need 1 <= N <= 8 nodes per half-axis (got %d)", n);
+    if (kind == LBM_FULL_RANGE_GH && (n < 2 || n > 16))
+        return fail(LBM_EINVAL, "full-range sets need 2 <= M <= 16 nodes per axis (got %d)", n);
+    lbm_vset *v = new (std::nothrow) lbm_vset;
+    if (!v) return fail(LBM_ENOMEM, "host allocation failed");
+    v->kind = kind;
+    v->n_arg = n;
+    if (!lbm_rule_1d(kind, n, v->nodes, v->weights)) {
+        delete v;
+        return fail(LBM_EINVAL, "quadrature construction failed");
+    }
+    v->m = (int)v->nodes.size();
+    for (int iy = 0; iy < v->m; ++iy)
+        for (int ix = 0; ix < v->m; ++ix) {
+            v->xi_x.push_back(v->nodes[ix]);
+            v->xi_y.push_back(v->nodes[iy]);
+            v->w.push_back(v->weights[ix] * v->weights[iy]);
+        }
+    *out = v;
+    return LBM_OK;
+}
+
+lbm_status lbm_vset_query(const lbm_vset *vs, int *n_vel, int *m, double *xi_x, double *xi_y,
+                          double *w)
+{
+    if (!vs) return fail(LBM_EINVAL, "velocity set is NULL");
+    const int nv = vs->m * vs->m;
+    if (n_vel) *n_vel = nv;
+    if (m) *m = vs->m;
+    if (xi_x) std::memcpy(xi_x, vs->xi_x.data(), sizeof(double) * nv);
+    if (xi_y) std::memcpy(xi_y, vs->xi_y.data(), sizeof(double) * nv);
+    if (w) std::memcpy(w, vs->w.data(), sizeof(double) * nv);
+    return LBM_OK;
+}
+
+void lbm_vset_destroy(lbm_vset *vs) { delete vs; }
+
+lbm_status lbm_sim_bytes(const lbm_vset *vs, const lbm_problem *prob, size_t *bytes)
+{
+    if (!bytes) return fail(LBM_EINVAL, "bytes is NULL");
+    lbm_status st = validate(vs, prob);
+    if (st != LBM_OK) return st;
+    *bytes = make_layout(vs, prob).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *init_h,
+                    void *device_buf, size_t buf_bytes, void *stream, lbm_sim **out)
+{
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_status st = validate(vs, prob);
+    if (st != LBM_OK) return st;
+    Layout L = make_layout(vs, prob);
+    if (device_buf) {
+        if (buf_bytes < L.total)
+            return fail(LBM_ENOMEM, "device buffer of %zu bytes < %zu needed", buf_bytes, L.total);
+        if (((uintptr_t)device_buf) & 255) return fail(LBM_EINVAL, "device buffer must be 256-byte aligned");
+    }
+    lbm_sim *s = new (std::nothrow) lbm_sim;
+    if (!s) return fail(LBM_ENOMEM, "host allocation failed");
+    s->vs = *vs;
+    s->prob = *prob;
+    s->nv = vs->m * vs->m;
+    s->ncells = (long)prob->nx * prob->ny;
+    s->stream = (cudaStream_t)stream;
+    s->lanes = default_lanes_per_cell(prob->prec, vs->m);
+    s->grid = grid_for(s->ncells, s->lanes);
+    s->step = 0;
+    s->resid_step = -1;
+    s->cur = 0;
+    s->host_res = nullptr;
+    s->owns = device_buf == nullptr;
+    s->bytes = L.total;
+    if (s->owns) {
+        cudaError_t e = cudaMalloc(&s->base, L.total);
+        if (e != cudaSuccess) {
+            delete s;
+            return fail(LBM_ENOMEM, "cudaMalloc of %zu bytes: %s", L.total, cudaGetErrorString(e));
+        }
+    } else {
+        s->base = device_buf;
+    }
+    char *b = (char *)s->base;
+    for (int i = 0; i < 4; ++i) s->buf[i] = (i < L.nbuf) ? b + L.off_buf[i] : nullptr;
+    s->tab64 = (double *)(b + L.off_tab64);
+    s->tab32 = (float *)(b + L.off_tab32);
+    s->hdr = (TableHeader *)(b + L.off_hdr);
+    s->partials = (double *)(b + L.off_partials);
+    s->npartials = L.npartials;
+    s->result = (double *)(b + L.off_result);
+    s->moments = (double *)(b + L.off_moments);
+    s->flux_y = (double *)(b + L.off_fy);
+    s->flux_x = (double *)(b + L.off_fx);
+
+    std::vector<double> t64;
+    std::vector<float> t32;
+    TableHeader hdr;
+    fill_tables(s, t64, t32, hdr);
+    cudaError_t e = cudaMallocHost(&s->host_res, sizeof(double) * 8);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->tab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->tab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->hdr, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, sizeof(double) * 8, s->stream);
+    const size_t state_bytes = (size_t)s->nv * s->ncells * elem_size(prob->prec);
+    if (e == cudaSuccess && !init_h) e = cudaMemsetAsync(s->buf[0], 0, state_bytes, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        lbm_status r = cuda_fail(e, "initialising the simulation");
+        lbm_destroy(s);
+        return r;
+    }
+    if (init_h) {
+        st = upload_state(s, init_h, s->buf[0]);
+        if (st != LBM_OK) {
+            lbm_destroy(s);
+            return st;
+        }
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_sim *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    if (s->owns && s->base) cudaFree(s->base);
+    if (s->host_res) cudaFreeHost(s->host_res);
+    delete s;
+}
+
+lbm_status lbm_coeffs(const lbm_sim *s, double *dt, double *omega, double *u_ref)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (dt) *dt = s->dt;
+    if (omega) *omega = s->omega;
+    if (u_ref) *u_ref = s->u_ref;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_sim *s, long nsteps)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
+    StepArgs a = base_args(s);
+    const int m = s->vs.m;
+    for (long i = 0; i < nsteps; ++i) {
+        const long idx = s->step + 1;
+        const bool resid = idx % s->prob.residual_every == 0;
+        a.h = s->buf[s->cur];
+        a.hn = s->buf[s->cur ^ 1];
+        cudaError_t e = launch_step(s->prob.prec, m, s->lanes, resid, a, s->grid, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
+        if (resid) {
+            e = launch_finalize_residual(s->partials, s->grid, s->result, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "launching the residual reduction");
+            s->resid_step = idx;
+        }
+        s->cur ^= 1;
+        s->step = idx;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_sim *s, double *r, long *step)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    cudaError_t e = cudaMemcpyAsync(s->host_res, s->result, sizeof(double) * 4,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the residual");
+    if (r) *r = s->resid_step < 0 ? INFINITY : s->host_res[2];
+    if (step) *step = s->resid_step;
+    if (s->resid_step >= 0 && s->host_res[3] != 0.0)
+        return fail(LBM_ENONFINITE, "non-finite values in the state at step %ld", s->resid_step);
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *pxx,
+                       double *pxy, double *pyy, double *wall_shear)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    const int m = s->vs.m;
+    cudaError_t e = launch_moments(s->prob.prec, s->buf[s->cur], s->tab64, s->hdr, m, s->prob.nx,
+                                   s->prob.ny, s->u_ref, s->moments, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the moments kernel");
+    double *outs[6] = {rho, ux, uy, pxx, pxy, pyy};
+    for (int k = 0; k < 6; ++k) {
+        if (!outs[k]) continue;
+        e = cudaMemcpyAsync(outs[k], s->moments + (size_t)k * s->ncells, sizeof(double) * s->ncells,
+                            cudaMemcpyDeviceToHost, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copying moments");
+    }
+    if (wall_shear) {
+        const int nx = s->prob.nx, ny = s->prob.ny;
+        const bool cav = s->prob.geom == LBM_CAVITY;
+        e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->tab64, s->hdr, m, nx, ny, cav,
+                             s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
+        std::vector<double> fy((size_t)(ny + 1) * nx), fx(cav ? (size_t)ny * (nx + 1) : 0);
+        e = cudaMemcpyAsync(fy.data(), s->flux_y, sizeof(double) * fy.size(), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess && cav)
+            e = cudaMemcpyAsync(fx.data(), s->flux_x, sizeof(double) * fx.size(), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copying face fluxes");
+        double sb = 0, st = 0, sl = 0, sr = 0;
+        for (int x = 0; x < nx; ++x) {
+            sb += fy[x];
+            st += fy[(size_t)ny * nx + x];
+        }
+        if (cav)
+            for (int y = 0; y < ny; ++y) {
+                sl += fx[(size_t)y * (nx + 1)];
+                sr += fx[(size_t)y * (nx + 1) + nx];
+            }
+        wall_shear[0] = sb / nx;
+        wall_shear[1] = st / nx;
+        wall_shear[2] = cav ? sl / ny : 0.0;
+        wall_shear[3] = cav ? sr / ny : 0.0;
+    }
+    e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "moments");
+}
+
+lbm_status lbm_face_flux(lbm_sim *s, double *flux_y, double *flux_x)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    const int nx = s->prob.nx, ny = s->prob.ny;
+    const bool cav = s->prob.geom == LBM_CAVITY;
+    if (flux_x && !cav) return fail(LBM_EINVAL, "flux_x is defined for the cavity only");
+    cudaError_t e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->tab64, s->hdr, s->vs.m, nx,
+                                     ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
+    if (flux_y)
+        e = cudaMemcpyAsync(flux_y, s->flux_y, sizeof(double) * (size_t)(ny + 1) * nx,
+                            cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && flux_x)
+        e = cudaMemcpyAsync(flux_x, s->flux_x, sizeof(double) * (size_t)ny * (nx + 1),
+                            cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "face fluxes");
+}
+
+lbm_status lbm_get_state(lbm_sim *s, double *h)
+{
+    if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
+    const size_t nvals = (size_t)s->nv * s->ncells;
+    cudaError_t e;
+    if (s->prob.prec == LBM_FP64) {
+        e = cudaMemcpyAsync(h, s->buf[s->cur], nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    } else {
+        double *stage = (double *)s->buf[2];
+        e = launch_widen((const float *)s->buf[s->cur], stage, (long)nvals, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h, stage, nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "reading the state");
+}
+
+lbm_status lbm_set_state(lbm_sim *s, const double *h)
+{
+    if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
+    return upload_state(s, h, s->buf[s->cur]);
+}
+
+lbm_status lbm_state_device(lbm_sim *s, void **ptr, long *step)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (ptr) *ptr = s->buf[s->cur];
+    if (step) *step = s->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_norms_scratch_bytes(long count, size_t *bytes)
+{
+    if (!bytes || count < 0) return fail(LBM_EINVAL, "invalid argument");
+    *bytes = sizeof(double) * 2 * (size_t)norms_blocks(count);
+    return LBM_OK;
+}
+
+lbm_status lbm_norms(const void *a, const void *b, long count, int prec, void *scratch,
+                     size_t scratch_bytes, double *out, void *stream)
+{
+    if (!a || !scratch || !out) return fail(LBM_EINVAL, "NULL argument");
+    if (count < 0) return fail(LBM_EINVAL, "count must be >= 0");
+    if (prec != LBM_FP64 && prec != LBM_FP32_PERTURB) return fail(LBM_EINVAL, "unknown precision %d", prec);
+    const int nb = norms_blocks(count);
+    if (scratch_bytes < sizeof(double) * 2 * (size_t)nb)
+        return fail(LBM_ENOMEM, "scratch of %zu bytes < %zu needed", scratch_bytes, sizeof(double) * 2 * (size_t)nb);
+    cudaError_t e = launch_norms(a, b, count, prec, (double *)scratch, nb, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "launching the norms kernels");
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <vector>
+
+#define LBM_MAX_M 12
+#define LBM_MAX_V (LBM_MAX_M * LBM_MAX_M)
+#define LBM_BLOCK 256
+
+// Per-velocity coefficient table of one simulation, structure of arrays, in device memory.
+// Rows (each LBM_MAX_V long), velocity a = iy*M + ix:
+enum {
+    TAB_A0 = 0,    // 1 - nu_x - nu_y           (upwind transport, own cell)
+    TAB_NUX,       // |xi_x| dt / dx            (upwind neighbour in x)
+    TAB_NUY,       // |xi_y| dt / dy            (upwind neighbour in y)
+    TAB_CW,        // omega * w_a               (relaxation towards w_a (rho + xi.j))
+    TAB_GB_LIN,    // w_a (1 + xi_x U_bottom)   (bottom-wall ghost, coefficient of rho'_w)
+    TAB_GB_C,      // w_a xi_x U_bottom / u_ref (bottom-wall ghost, driving term)
+    TAB_GT_LIN,    // same, top wall
+    TAB_GT_C,
+    TAB_W,         // w_a                       (side-wall ghost, walls at rest)
+    TAB_ROWS
+};
+
+struct TableHeader {
+    double xi1[LBM_MAX_M];   // 1-D nodes (ascending)
+    double b;                // 1 - omega
+    double inv_dx_wall;      // 1 / sum_{xi_x>0} xi_x w  (side walls)
+    double inv_dy_wall;      // 1 / sum_{xi_y>0} xi_y w  (bottom / top walls)
+};
+
+// Arguments of one fused step launch.
+struct StepArgs {
+    const void *h;        // state at time n   [n][ncells]
+    void *hn;             // state at time n+1 [n][ncells]
+    const void *src;      // optional source added after relaxation (correction sweeps)
+    const double *tab64;  // TAB_ROWS x LBM_MAX_V doubles
+    const float *tab32;   // same, rounded to float
+    const TableHeader *hdr;
+    double *partials;     // per-block residual partial sums [2 * gridDim.x]
+    int nx, ny;
+    long ncells;
+    int cavity;
+    int homogeneous;      // drop the wall driving terms (correction sweeps)
+};
+
+// Launchers (step_*.cu).  `variant` selects lanes-per-cell G; returns cudaError_t.
+cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
+                        cudaStream_t s);
+cudaError_t launch_defect(int m, const StepArgs &a, int grid, cudaStream_t s);
+int default_lanes_per_cell(int prec, int m);
+bool step_supported(int prec, int m, int g);
+
+// Reductions and diagnostics (reduce.cu)
+cudaError_t launch_finalize_residual(const double *partials, int nparts, double *result,
+                                     cudaStream_t s);
+cudaError_t launch_norms(const void *a, const void *b, long count, int prec, double *partials,
+                         int nparts, double *out, cudaStream_t s);
+int norms_blocks(long count);
+cudaError_t launch_moments(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+                           int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s);
+cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+                             int m, int nx, int ny, int cavity, double u_ref, double *flux_y,
+                             double *flux_x, double *wall_sums, cudaStream_t s);
+
+cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s);
+cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s);
+
+// Host quadrature (quadrature.cpp)
+bool lbm_rule_1d(int kind, int n, std::vector<double> &nodes, std::vector<double> &weights);

@@ -1,0 +1,283 @@
+// Reductions and diagnostics of the march (sm_103a): residual finalisation, squared
+// norms, macroscopic moments (Eqs. 6-7 and the second moments behind p_xy) and the
+// momentum flux through cell faces (the shear stress the scheme transmits; on a wall
+// face the upwind value is the Maxwell ghost of Eqs. 8-9).  All accumulation in FP64.
+#include <cmath>
+
+#include "lbm_internal.h"
+
+namespace {
+
+constexpr int RED_BLOCK = 1024;
+
+// Sum per-block partial pairs in a fixed order; result[0..1] = sums, and when
+// nres >= 4: result[2] = sqrt(sd/sn) (0 if both are 0), result[3] = 1 if non-finite.
+__global__ void __launch_bounds__(RED_BLOCK) finalize_kernel(const double *partials, int nparts,
+                                                             double *result, int nres)
+{
+    __shared__ double s_d[RED_BLOCK / 32], s_n[RED_BLOCK / 32];
+    double sd = 0.0, sn = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += RED_BLOCK) {
+        sd += partials[2 * i];
+        sn += partials[2 * i + 1];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, off);
+        sn += __shfl_xor_sync(0xffffffffu, sn, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_d[warp] = sd;
+        s_n[warp] = sn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double td = 0.0, tn = 0.0;
+        for (int w = 0; w < RED_BLOCK / 32; ++w) {
+            td += s_d[w];
+            tn += s_n[w];
+        }
+        result[0] = td;
+        result[1] = tn;
+        if (nres >= 4) {
+            const bool bad = !isfinite(td) || !isfinite(tn);
+            result[2] = (tn > 0.0) ? sqrt(td / tn) : (td == 0.0 ? 0.0 : INFINITY);
+            result[3] = bad ? 1.0 : 0.0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) norms_kernel(const T *a, const T *b, long count,
+                                                   double *partials)
+{
+    __shared__ double s_d[8], s_n[8];
+    double sd = 0.0, sn = 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const double va = (double)a[i];
+        const double d = b ? va - (double)b[i] : va;
+        sd += d * d;
+        sn += va * va;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, off);
+        sn += __shfl_xor_sync(0xffffffffu, sn, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_d[warp] = sd;
+        s_n[warp] = sn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double td = 0.0, tn = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            td += s_d[w];
+            tn += s_n[w];
+        }
+        partials[2 * blockIdx.x] = td;
+        partials[2 * blockIdx.x + 1] = tn;
+    }
+}
+
+// Per cell: rho, ux, uy, pxx, pxy, pyy (linearised, Eq. (1) units).
+template <typename T>
+__global__ void moments_kernel(const T *h, const TableHeader *hdr, int m, long ncells,
+                               double u_ref, double *out)
+{
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    double s0 = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
+    for (int iy = 0; iy < m; ++iy) {
+        const double ey = hdr->xi1[iy];
+        for (int ix = 0; ix < m; ++ix) {
+            const double ex = hdr->xi1[ix];
+            const double v = (double)h[(long)(iy * m + ix) * ncells + c];
+            s0 += v;
+            sx += ex * v;
+            sy += ey * v;
+            sxx += ex * ex * v;
+            sxy += ex * ey * v;
+            syy += ey * ey * v;
+        }
+    }
+    const double rho = 1.0 + u_ref * s0;
+    out[c] = rho;
+    out[ncells + c] = u_ref * sx / rho;
+    out[2 * ncells + c] = u_ref * sy / rho;
+    out[3 * ncells + c] = 1.0 + u_ref * sxx;
+    out[4 * ncells + c] = u_ref * sxy;
+    out[5 * ncells + c] = 1.0 + u_ref * syy;
+}
+
+// rho'_w of a wall face of cell c; dir: 0 bottom, 1 top, 2 left, 3 right
+template <typename T>
+__device__ double wall_rho(const T *h, const TableHeader *hdr, int m, long ncells, long c, int dir)
+{
+    double s = 0.0;
+    for (int iy = 0; iy < m; ++iy) {
+        for (int ix = 0; ix < m; ++ix) {
+            const double xn = (dir == 0) ? hdr->xi1[iy] : (dir == 1) ? -hdr->xi1[iy]
+                            : (dir == 2) ? hdr->xi1[ix] : -hdr->xi1[ix];
+            if (xn < 0.0) s -= xn * (double)h[(long)(iy * m + ix) * ncells + c];
+        }
+    }
+    return s * ((dir < 2) ? hdr->inv_dy_wall : hdr->inv_dx_wall);
+}
+
+template <typename T>
+__global__ void face_flux_y_kernel(const T *h, const double *tab, const TableHeader *hdr, int m,
+                                   int nx, int ny, double u_ref, double *out)
+{
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nfaces = (long)(ny + 1) * nx;
+    if (f >= nfaces) return;
+    const long ncells = (long)nx * ny;
+    const int j = (int)(f / nx), x = (int)(f - (long)j * nx);
+    const long below = (long)(j - 1) * nx + x, above = (long)j * nx + x;
+    const double rb = (j == 0) ? wall_rho(h, hdr, m, ncells, above, 0) : 0.0;
+    const double rt = (j == ny) ? wall_rho(h, hdr, m, ncells, below, 1) : 0.0;
+    double s = 0.0;
+    for (int iy = 0; iy < m; ++iy) {
+        const double ey = hdr->xi1[iy];
+        if (ey == 0.0) continue;
+        for (int ix = 0; ix < m; ++ix) {
+            const int al = iy * m + ix;
+            double v;
+            if (ey > 0.0)
+                v = (j == 0) ? rb * tab[TAB_GB_LIN * LBM_MAX_V + al] + tab[TAB_GB_C * LBM_MAX_V + al]
+                             : (double)h[(long)al * ncells + below];
+            else
+                v = (j == ny) ? rt * tab[TAB_GT_LIN * LBM_MAX_V + al] + tab[TAB_GT_C * LBM_MAX_V + al]
+                              : (double)h[(long)al * ncells + above];
+            s += hdr->xi1[ix] * ey * v;
+        }
+    }
+    out[f] = u_ref * s;
+}
+
+template <typename T>
+__global__ void face_flux_x_kernel(const T *h, const double *tab, const TableHeader *hdr, int m,
+                                   int nx, int ny, double u_ref, double *out)
+{
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nfaces = (long)ny * (nx + 1);
+    if (f >= nfaces) return;
+    const long ncells = (long)nx * ny;
+    const int y = (int)(f / (nx + 1)), i = (int)(f - (long)y * (nx + 1));
+    const long left = (long)y * nx + i - 1, right = (long)y * nx + i;
+    const double rl = (i == 0) ? wall_rho(h, hdr, m, ncells, right, 2) : 0.0;
+    const double rr = (i == nx) ? wall_rho(h, hdr, m, ncells, left, 3) : 0.0;
+    double s = 0.0;
+    for (int iy = 0; iy < m; ++iy) {
+        const double ey = hdr->xi1[iy];
+        for (int ix = 0; ix < m; ++ix) {
+            const double ex = hdr->xi1[ix];
+            if (ex == 0.0) continue;
+            const int al = iy * m + ix;
+            double v;
+            if (ex > 0.0)
+                v = (i == 0) ? rl * tab[TAB_W * LBM_MAX_V + al] : (double)h[(long)al * ncells + left];
+            else
+                v = (i == nx) ? rr * tab[TAB_W * LBM_MAX_V + al] : (double)h[(long)al * ncells + right];
+            s += ex * ey * v;
+        }
+    }
+    out[f] = u_ref * s;
+}
+
+__global__ void convert_kernel(const double *src, float *dst, long count)
+{
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        dst[i] = (float)src[i];
+}
+
+__global__ void widen_kernel(const float *src, double *dst, long count)
+{
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        dst[i] = (double)src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s)
+{
+    convert_kernel<<<152 * 8, 256, 0, s>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s)
+{
+    widen_kernel<<<152 * 8, 256, 0, s>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_residual(const double *partials, int nparts, double *result,
+                                     cudaStream_t s)
+{
+    finalize_kernel<<<1, RED_BLOCK, 0, s>>>(partials, nparts, result, 4);
+    return cudaGetLastError();
+}
+
+int norms_blocks(long count)
+{
+    long b = (count + 256L * 8 - 1) / (256L * 8);
+    if (b < 1) b = 1;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)b;
+}
+
+cudaError_t launch_norms(const void *a, const void *b, long count, int prec, double *partials,
+                         int nparts, double *out, cudaStream_t s)
+{
+    if (prec == 0)
+        norms_kernel<double><<<nparts, 256, 0, s>>>((const double *)a, (const double *)b, count,
+                                                    partials);
+    else
+        norms_kernel<float><<<nparts, 256, 0, s>>>((const float *)a, (const float *)b, count,
+                                                   partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    finalize_kernel<<<1, RED_BLOCK, 0, s>>>(partials, nparts, out, 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+                           int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s)
+{
+    (void)tab64;
+    const long ncells = (long)nx * ny;
+    const int grid = (int)((ncells + 255) / 256);
+    if (prec == 0)
+        moments_kernel<double><<<grid, 256, 0, s>>>((const double *)h, hdr, m, ncells, u_ref, out6);
+    else
+        moments_kernel<float><<<grid, 256, 0, s>>>((const float *)h, hdr, m, ncells, u_ref, out6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+                             int m, int nx, int ny, int cavity, double u_ref, double *flux_y,
+                             double *flux_x, double *wall_sums, cudaStream_t s)
+{
+    (void)wall_sums;
+    const long ny_faces = (long)(ny + 1) * nx;
+    const long nx_faces = (long)ny * (nx + 1);
+    if (prec == 0)
+        face_flux_y_kernel<double><<<(int)((ny_faces + 255) / 256), 256, 0, s>>>(
+            (const double *)h, tab64, hdr, m, nx, ny, u_ref, flux_y);
+    else
+        face_flux_y_kernel<float><<<(int)((ny_faces + 255) / 256), 256, 0, s>>>(
+            (const float *)h, tab64, hdr, m, nx, ny, u_ref, flux_y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !cavity || !flux_x) return e;
+    if (prec == 0)
+        face_flux_x_kernel<double><<<(int)((nx_faces + 255) / 256), 256, 0, s>>>(
+            (const double *)h, tab64, hdr, m, nx, ny, u_ref, flux_x);
+    else
+        face_flux_x_kernel<float><<<(int)((nx_faces + 255) / 256), 256, 0, s>>>(
+            (const float *)h, tab64, hdr, m, nx, ny, u_ref, flux_x);
+    return cudaGetLastError();
+}

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of liblbm.so (argument marshalling only).
+
+Every function has the name of the C entry point it calls (declared in
+``include/lbm.h``); all computation happens in the library's CUDA kernels.
+Device memory and streams may come from PyTorch: pass ``device_buf`` as a
+``torch.uint8`` CUDA tensor of ``lbm_sim_bytes(...)`` bytes and ``stream`` as a
+``torch.cuda.Stream`` (or a raw ``cudaStream_t`` integer).
+
+The library is loaded on first use; if it has not been built a RuntimeError
+says how to build it -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(7)
+LBM_HALF_RANGE_GH, LBM_FULL_RANGE_GH = 0, 1
+LBM_COUETTE, LBM_CAVITY = 0, 1
+LBM_FP64, LBM_FP32_PERTURB = 0, 1
+
+_STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
+                 4: "LBM_ENONFINITE", 5: "LBM_ETIMEOUT", 6: "LBM_EUNSUPPORTED"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lbm_problem(ctypes.Structure):
+    _fields_ = [("geom", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("kn", ctypes.c_double), ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("prec", ctypes.c_int), ("residual_every", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_1308_0692_gb300.build` "
+                           "(the CUDA library is the only implementation)")
+    lib = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    sig = {
+        "lbm_make_velocity_set": (st, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+        "lbm_vset_query": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]),
+        "lbm_vset_destroy": (None, [_vp]),
+        "lbm_sim_bytes": (st, [_vp, ctypes.POINTER(lbm_problem), ctypes.POINTER(ctypes.c_size_t)]),
+        "lbm_init": (st, [_vp, ctypes.POINTER(lbm_problem), _dp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+        "lbm_destroy": (None, [_vp]),
+        "lbm_coeffs": (st, [_vp, _dp, _dp, _dp]),
+        "lbm_step": (st, [_vp, ctypes.c_long]),
+        "lbm_residual": (st, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
+        "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
+        "lbm_face_flux": (st, [_vp, _dp, _dp]),
+        "lbm_get_state": (st, [_vp, _dp]),
+        "lbm_set_state": (st, [_vp, _dp]),
+        "lbm_state_device": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_long)]),
+        "lbm_norms_scratch_bytes": (st, [ctypes.c_long, ctypes.POINTER(ctypes.c_size_t)]),
+        "lbm_norms": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp]),
+        "lbm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def library():
+    """The loaded ctypes library (for callers that bind extra entry points)."""
+    return _load()
+
+
+def _check(status: int):
+    if status != LBM_OK:
+        raise LBMError(status, _load().lbm_last_error().decode())
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class VelocitySet:
+    """Owner of an lbm_vset* (freed on garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.lbm_vset_destroy(self.handle)
+            self.handle = None
+
+
+class Sim:
+    """Owner of an lbm_sim* and of the device buffer it lives in (if any)."""
+
+    def __init__(self, handle: int, prob: lbm_problem, n_vel: int, keepalive=None):
+        self.handle = handle
+        self.prob = prob
+        self.n_vel = n_vel
+        self._keepalive = keepalive
+
+    @property
+    def ncells(self) -> int:
+        return self.prob.nx * self.prob.ny
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.lbm_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def make_problem(geom: int, nx: int, ny: int, kn: float, u_bottom: float, u_top: float,
+                 cfl: float = 0.9, prec: int = LBM_FP64, residual_every: int = 100) -> lbm_problem:
+    return lbm_problem(geom, nx, ny, kn, u_bottom, u_top, cfl, prec, residual_every)
+
+
+def lbm_make_velocity_set(kind: int, n: int) -> VelocitySet:
+    h = _vp()
+    _check(_load().lbm_make_velocity_set(kind, n, ctypes.byref(h)))
+    return VelocitySet(h.value)
+
+
+def lbm_vset_query(vs: VelocitySet):
+    """Returns (xi_x, xi_y, w, M) as float64 arrays."""
+    lib = _load()
+    nv, m = ctypes.c_int(), ctypes.c_int()
+    _check(lib.lbm_vset_query(vs.handle, ctypes.byref(nv), ctypes.byref(m), None, None, None))
+    xi_x, xi_y, w = (np.empty(nv.value) for _ in range(3))
+    _check(lib.lbm_vset_query(vs.handle, None, None, _ptr(xi_x), _ptr(xi_y), _ptr(w)))
+    return xi_x, xi_y, w, m.value
+
+
+def lbm_sim_bytes(vs: VelocitySet, prob: lbm_problem) -> int:
+    b = ctypes.c_size_t()
+    _check(_load().lbm_sim_bytes(vs.handle, ctypes.byref(prob), ctypes.byref(b)))
+    return b.value
+
+
+def lbm_init(vs: VelocitySet, prob: lbm_problem, init_h: np.ndarray | None = None,
+             device_buf=None, stream=None) -> Sim:
+    """device_buf: None (library allocates) or a CUDA torch tensor (kept alive by the Sim)."""
+    lib = _load()
+    out = _vp()
+    buf_ptr, buf_bytes = None, 0
+    if device_buf is not None:
+        buf_ptr = device_buf.data_ptr()
+        buf_bytes = device_buf.numel() * device_buf.element_size()
+    h = None if init_h is None else np.ascontiguousarray(init_h, dtype=np.float64)
+    _check(lib.lbm_init(vs.handle, ctypes.byref(prob), _ptr(h), buf_ptr, buf_bytes,
+                        _stream_handle(stream), ctypes.byref(out)))
+    nv = ctypes.c_int()
+    _check(lib.lbm_vset_query(vs.handle, ctypes.byref(nv), None, None, None, None))
+    return Sim(out.value, prob, nv.value, keepalive=(device_buf, stream, vs))
+
+
+def lbm_destroy(sim: Sim):
+    sim.close()
+
+
+def lbm_coeffs(sim: Sim):
+    dt, om, ur = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_load().lbm_coeffs(sim.handle, ctypes.byref(dt), ctypes.byref(om), ctypes.byref(ur)))
+    return {"dt": dt.value, "omega": om.value, "u_ref": ur.value}
+
+
+def lbm_step(sim: Sim, nsteps: int):
+    _check(_load().lbm_step(sim.handle, int(nsteps)))
+
+
+def lbm_residual(sim: Sim):
+    r, s = ctypes.c_double(), ctypes.c_long()
+    _check(_load().lbm_residual(sim.handle, ctypes.byref(r), ctypes.byref(s)))
+    return r.value, s.value
+
+
+def lbm_moments(sim: Sim, wall_shear: bool = True):
+    n = sim.ncells
+    outs = {k: np.empty(n) for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy")}
+    ws = np.empty(4) if wall_shear else None
+    _check(_load().lbm_moments(sim.handle, *[_ptr(outs[k]) for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy")],
+                               _ptr(ws)))
+    res = {k: v.reshape(sim.prob.ny, sim.prob.nx) for k, v in outs.items()}
+    if ws is not None:
+        res["wall_shear"] = ws
+    return res
+
+
+def lbm_face_flux(sim: Sim):
+    nx, ny = sim.prob.nx, sim.prob.ny
+    fy = np.empty((ny + 1) * nx)
+    fx = np.empty(ny * (nx + 1)) if sim.prob.geom == LBM_CAVITY else None
+    _check(_load().lbm_face_flux(sim.handle, _ptr(fy), _ptr(fx)))
+    return fy.reshape(ny + 1, nx), (None if fx is None else fx.reshape(ny, nx + 1))
+
+
+def lbm_get_state(sim: Sim) -> np.ndarray:
+    h = np.empty((sim.n_vel, sim.ncells))
+    _check(_load().lbm_get_state(sim.handle, _ptr(h)))
+    return h
+
+
+def lbm_set_state(sim: Sim, h: np.ndarray):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    assert h.size == sim.n_vel * sim.ncells
+    _check(_load().lbm_set_state(sim.handle, _ptr(h)))
+
+
+def lbm_state_device(sim: Sim):
+    p, s = _vp(), ctypes.c_long()
+    _check(_load().lbm_state_device(sim.handle, ctypes.byref(p), ctypes.byref(s)))
+    return p.value, s.value
+
+
+def lbm_norms_scratch_bytes(count: int) -> int:
+    b = ctypes.c_size_t()
+    _check(_load().lbm_norms_scratch_bytes(int(count), ctypes.byref(b)))
+    return b.value
+
+
+def lbm_norms(a_ptr: int, b_ptr: int | None, count: int, prec: int, scratch_ptr: int,
+              scratch_bytes: int, out_ptr: int, stream=None):
+    _check(_load().lbm_norms(a_ptr, b_ptr, int(count), prec, scratch_ptr, scratch_bytes, out_ptr,
+                             _stream_handle(stream)))

@@ -1,0 +1,231 @@
+"""GPU parity of the fused step kernels against the FP64 CPU oracle, through the C-ABI.
+
+Tolerances: FP64 path 1e-12 relative (max |delta h| / max |h|) at equal step counts;
+FP32 path per step: 2e-6 of max |h| per step marched (single-precision rounding of
+the O(10) operations and the velocity sums per value, which are far below any
+indexing, sign or coefficient mistake, those being O(1)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.march import CAVITY, COUETTE, make_problem as oracle_problem, residual as oracle_residual
+from paper_1308_0692_gb300 import lbm
+from paper_1308_0692_gb300.inputs import random_cells, random_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL_PER_STEP = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1308_0692_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _kind(kind):
+    return lbm.LBM_HALF_RANGE_GH if kind == "half" else lbm.LBM_FULL_RANGE_GH
+
+
+def gpu_run(kind, n, geom, nx, ny, kn, ub, ut, prec, h0, steps, stream=None, device_buf=False,
+            residual_every=1):
+    vs = lbm.lbm_make_velocity_set(_kind(kind), n)
+    prob = lbm.make_problem(geom, nx, ny, kn, ub, ut, prec=prec, residual_every=residual_every)
+    buf = None
+    if device_buf:
+        buf = torch.empty(lbm.lbm_sim_bytes(vs, prob), dtype=torch.uint8, device="cuda")
+    sim = lbm.lbm_init(vs, prob, h0, device_buf=buf, stream=stream)
+    lbm.lbm_step(sim, steps)
+    return lbm.lbm_get_state(sim), sim
+
+
+CASES = [
+    # kind, n, geom, nx, ny, kn, u_bottom, u_top
+    ("half", 4, COUETTE, 1, 100, 0.1, 0.01, -0.01),        # configuration of the Couette runs
+    ("half", 4, COUETTE, 1, 100, 0.01, 0.01, -0.01),
+    ("half", 4, COUETTE, 1, 100, 10.0, 0.01, -0.01),
+    ("half", 4, COUETTE, 1, 37, math.inf, -0.01, 0.01),    # collisionless
+    ("half", 2, COUETTE, 3, 41, 0.3, -0.02, 0.01),         # several periodic columns
+    ("half", 4, CAVITY, 37, 29, 0.1, 0.0, 0.01),           # ragged: 1073 cells
+    ("half", 4, CAVITY, 130, 67, 0.05, 0.003, 0.01),       # several tiles, moving bottom
+    ("full", 3, CAVITY, 23, 19, 0.1, 0.0, 0.01),           # D2Q9
+    ("full", 4, CAVITY, 23, 19, 0.2, 0.0, 0.01),           # D2Q16
+    ("half", 2, CAVITY, 31, 33, 1.0, 0.0, 0.01),           # D2Q^h_16
+    ("half", 3, CAVITY, 21, 17, 0.1, 0.0, 0.01),           # D2Q^h_36
+    ("half", 6, CAVITY, 45, 38, 0.05, 0.0, 0.01),          # D2Q^h_144
+    ("half", 4, CAVITY, 2, 2, 0.1, 0.0, 0.01),             # smallest cavity
+    ("half", 4, COUETTE, 1, 2, 0.1, 0.01, -0.01),          # smallest channel
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}{c[1]}-{'cav' if c[2] else 'cou'}-{c[3]}x{c[4]}-kn{c[5]}" for c in CASES])
+def test_fp64_step_parity_random_state(case):
+    kind, n, geom, nx, ny, kn, ub, ut = case
+    p = oracle_problem(kind, n, geom, nx, ny, kn, ub, ut)
+    h0 = random_state(p.n, p.ncells, seed=1000 + nx * ny)
+    steps = 7
+    got, sim = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP64, h0, steps)
+    ref = p.step(h0, steps)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err <= FP64_TOL, err
+    # residual of the last step against the oracle's definition
+    r, st = lbm.lbm_residual(sim)
+    assert st == steps
+    r_ref = oracle_residual(ref, p.step(h0, steps - 1))
+    assert abs(r - r_ref) <= 1e-10 * r_ref
+
+
+@pytest.mark.parametrize("case", CASES[:2] + CASES[5:9] + CASES[11:12])
+def test_fp32_step_parity_random_state(case):
+    kind, n, geom, nx, ny, kn, ub, ut = case
+    p = oracle_problem(kind, n, geom, nx, ny, kn, ub, ut)
+    h0 = random_state(p.n, p.ncells, seed=2000 + nx * ny).astype(np.float32).astype(np.float64)
+    steps = 5
+    got, _ = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP32_PERTURB, h0, steps)
+    ref = p.step(h0, steps)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err <= FP32_TOL_PER_STEP * steps, err
+
+
+def test_fp64_cold_start_march_cavity_128():
+    """Lid-driven cavity 128 x 128, 64 velocities, Kn 0.1, from f = w: 300 steps agree to 1e-12."""
+    kind, n, geom, nx, ny, kn, ub, ut = "half", 4, CAVITY, 128, 128, 0.1, 0.0, 0.01
+    p = oracle_problem(kind, n, geom, nx, ny, kn, ub, ut)
+    got, sim = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP64, None, 300)
+    ref = p.step(p.zeros(), 300)
+    assert np.abs(got - ref).max() <= FP64_TOL * np.abs(ref).max()
+    m = lbm.lbm_moments(sim)
+    mr = p.moments(ref)
+    for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy"):
+        scale = np.abs(mr[k] - (1.0 if k in ("rho", "pxx", "pyy") else 0.0)).max()
+        assert np.abs(m[k] - mr[k]).max() <= 1e-12 * scale, k
+    fy, fx = lbm.lbm_face_flux(sim)
+    fyr, fxr = p.face_flux_y(ref), p.face_flux_x(ref)
+    assert np.abs(fy - fyr).max() <= 1e-12 * np.abs(fyr).max()
+    assert np.abs(fx - fxr).max() <= 1e-12 * np.abs(fxr).max()
+    ws = m["wall_shear"]
+    assert abs(ws[1] - fyr[-1].mean()) <= 1e-12 * abs(fyr[-1].mean())
+    assert abs(ws[0] - fyr[0].mean()) <= 1e-12 * np.abs(fyr).max()
+    assert abs(ws[2] - fxr[:, 0].mean()) <= 1e-12 * np.abs(fxr).max()
+
+
+def test_couette_converged_to_steady_state_fp64():
+    """Couette ny=100, 64 velocities, Kn = 0.1, marched to r < 1e-10 on the GPU, matches the
+    oracle marched the same number of steps to 1e-12; face shear equals the oracle's."""
+    kind, n, geom, nx, ny, kn, ub, ut = "half", 4, COUETTE, 1, 100, 0.1, 0.01, -0.01
+    vs = lbm.lbm_make_velocity_set(_kind(kind), n)
+    prob = lbm.make_problem(geom, nx, ny, kn, ub, ut, residual_every=100)
+    sim = lbm.lbm_init(vs, prob)
+    steps = 0
+    while True:
+        lbm.lbm_step(sim, 100)
+        steps += 100
+        r, _ = lbm.lbm_residual(sim)
+        if r < 1e-10 or steps > 50000:
+            break
+    assert r < 1e-10
+    p = oracle_problem(kind, n, geom, nx, ny, kn, ub, ut)
+    ref = p.step(p.zeros(), steps)
+    got = lbm.lbm_get_state(sim)
+    assert np.abs(got - ref).max() <= FP64_TOL * np.abs(ref).max()
+    fy, _ = lbm.lbm_face_flux(sim)
+    assert np.ptp(fy) < 1e-8 * np.abs(fy).max()
+
+
+def test_caller_buffer_and_stream_give_identical_bits():
+    kind, n, geom, nx, ny, kn, ub, ut = "half", 4, CAVITY, 50, 40, 0.1, 0.0, 0.01
+    h0 = random_state(64, nx * ny, seed=5)
+    a, _ = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP64, h0, 11)
+    s = torch.cuda.Stream()
+    b, _ = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP64, h0, 11, stream=s, device_buf=True)
+    np.testing.assert_array_equal(a, b)       # deterministic: no atomics, fixed order
+
+
+def test_zero_steps_and_set_get_roundtrip():
+    kind, n, geom, nx, ny, kn, ub, ut = "half", 4, CAVITY, 9, 7, 0.1, 0.0, 0.01
+    h0 = random_state(64, 63, seed=9)
+    got, sim = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP64, h0, 0)
+    np.testing.assert_array_equal(got, h0)
+    h1 = random_state(64, 63, seed=10)
+    lbm.lbm_set_state(sim, h1)
+    np.testing.assert_array_equal(lbm.lbm_get_state(sim), h1)
+
+
+def test_nonfinite_state_is_reported():
+    kind, n, geom, nx, ny, kn, ub, ut = "half", 2, CAVITY, 8, 8, 0.1, 0.0, 0.01
+    h0 = random_state(16, 64, seed=3)
+    h0[5, 17] = np.nan           # planted on the host before upload
+    _, sim = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, lbm.LBM_FP64, h0, 3)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_residual(sim)
+    assert e.value.status == lbm.LBM_ENONFINITE
+
+
+def test_small_device_buffer_rejected():
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    prob = lbm.make_problem(CAVITY, 16, 16, 0.1, 0.0, 0.01)
+    need = lbm.lbm_sim_bytes(vs, prob)
+    buf = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_init(vs, prob, device_buf=buf)
+    assert e.value.status == lbm.LBM_ENOMEM
+
+
+@pytest.mark.parametrize("prec,dtype", [(lbm.LBM_FP64, torch.float64), (lbm.LBM_FP32_PERTURB, torch.float32)])
+@pytest.mark.parametrize("count", [1, 1000, 3 * 10 ** 6 + 17])
+def test_norms_against_host(prec, dtype, count):
+    g = torch.Generator(device="cpu").manual_seed(count)
+    a = torch.randn(count, generator=g, dtype=torch.float64).to(dtype)
+    b = torch.randn(count, generator=g, dtype=torch.float64).to(dtype)
+    ad, bd = a.cuda(), b.cuda()
+    nbytes = lbm.lbm_norms_scratch_bytes(count)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    lbm.lbm_norms(ad.data_ptr(), bd.data_ptr(), count, prec, scratch.data_ptr(), nbytes, out.data_ptr(), s)
+    torch.cuda.synchronize()
+    a64, b64 = a.double().numpy(), b.double().numpy()
+    ref = np.array([np.sum((a64 - b64) ** 2), np.sum(a64 ** 2)])
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12)
+
+
+# ---- full-size configurations: sampled outputs the oracle computes one by one ----
+
+FULL = [
+    # (kind, n, geom, nx, ny, kn, ub, ut, prec) at the sizes the benchmark and the examples use
+    ("half", 6, CAVITY, 2048, 2048, 0.05, 0.0, 0.01, lbm.LBM_FP32_PERTURB),
+    ("half", 6, CAVITY, 2048, 2048, 0.05, 0.0, 0.01, lbm.LBM_FP64),
+    ("half", 4, CAVITY, 256, 256, 0.1, 0.0, 0.01, lbm.LBM_FP32_PERTURB),
+    ("half", 4, COUETTE, 1, 512, 0.02, 0.01, -0.01, lbm.LBM_FP32_PERTURB),
+]
+
+
+@pytest.mark.parametrize("case", FULL, ids=["cavity2048-144-fp32", "cavity2048-144-fp64",
+                                            "cavity256-64-fp32", "couette512-64-fp32"])
+def test_full_size_sampled_step(case):
+    kind, n, geom, nx, ny, kn, ub, ut, prec = case
+    p = oracle_problem(kind, n, geom, nx, ny, kn, ub, ut)
+    h0 = random_state(p.n, p.ncells, seed=77)
+    if prec == lbm.LBM_FP32_PERTURB:
+        h0 = h0.astype(np.float32).astype(np.float64)
+    corners = [0, nx - 1, (ny - 1) * nx, ny * nx - 1, nx // 2, (ny // 2) * nx, (ny // 2) * nx + nx - 1,
+               (ny - 1) * nx + nx // 2, (ny // 2) * nx + nx // 2]
+    cells = random_cells(p.ncells, 400, seed=78, include=corners)
+    got, sim = gpu_run(kind, n, geom, nx, ny, kn, ub, ut, prec, h0, 1)
+    del h0
+    ref = p.step_cells(_host_state_for(p, seed=77, prec=prec), cells)
+    g = got[:, cells].T
+    tol = FP64_TOL if prec == lbm.LBM_FP64 else FP32_TOL_PER_STEP
+    assert np.abs(g - ref).max() <= tol * np.abs(ref).max()
+
+
+def _host_state_for(p, seed, prec):
+    h = random_state(p.n, p.ncells, seed=seed)
+    if prec == lbm.LBM_FP32_PERTURB:
+        h = h.astype(np.float32).astype(np.float64)
+    return h
