@@ -63,8 +63,8 @@ typedef struct lbm_sim lbm_sim;
  *   prec      LBM_FP64: FP64 storage and arithmetic.  LBM_FP32_PERTURB: FP32 storage
  *             and arithmetic of h; FP64 wall sums and reductions.
  *   residual_every  the relative residual ||h^{n+1}-h^n|| / ||h^{n+1}|| is evaluated
- *             on every step whose index is a multiple of it and on the last step of
- *             every lbm_step call (>= 1). */
+ *             on every step whose index (counted from 1 since lbm_init) is a multiple
+ *             of it (>= 1); lbm_residual returns the latest one. */
 typedef struct {
     int geom;
     int nx, ny;
@@ -116,6 +116,13 @@ lbm_status lbm_coeffs(const lbm_sim *sim, double *dt, double *omega, double *u_r
  * fused pass: upwind transport with wall ghosts (Eqs. 8-9), moments (Eqs. 6-7),
  * relaxation towards w_a (rho + xi_a . j) (Eqs. 1, 5). */
 lbm_status lbm_step(lbm_sim *sim, long nsteps);
+
+/* Kernel variant: the number of warp lanes that share one cell (1, 2 or 4; each lane
+ * owns M/lanes velocity rows).  It changes speed, not results beyond rounding order.
+ * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
+ * without a compiled kernel.  Used by the autotuner.  Call between steps only. */
+lbm_status lbm_set_variant(lbm_sim *sim, int lanes_per_cell);
+lbm_status lbm_get_variant(const lbm_sim *sim, int *lanes_per_cell);
 
 /* Latest relative residual r and the step count at which it was evaluated
  * (synchronises).  LBM_ENONFINITE if the state contains NaN/Inf. */

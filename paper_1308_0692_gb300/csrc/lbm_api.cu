@@ -38,7 +38,10 @@ struct lbm_sim {
     double dt, dx, dy, omega, u_ref;
     cudaStream_t stream;
     int lanes;            // lanes per cell of the step kernel
-    int grid;             // blocks of one step launch
+    int grid;             // blocks of the bulk step kernel
+    int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
+    int *wall_segs;       // device list of wall segments for the current lanes
+    int wall_cap;
     // device memory
     void *base;
     bool owns;
@@ -55,6 +58,7 @@ struct lbm_sim {
     double *flux_y;       // (ny+1) * nx
     double *flux_x;       // ny * (nx+1)
     double *host_res;     // pinned host copy of result
+    StepArgs args;        // launch arguments except the buffer pointers
     long step;
     long resid_step;
 };
@@ -88,7 +92,8 @@ bool kernel_m_supported(int m) { return m == 3 || m == 4 || m == 6 || m == 8 || 
 
 struct Layout {
     size_t off_buf[4];
-    size_t off_tab64, off_tab32, off_hdr, off_partials, off_result, off_moments, off_fy, off_fx;
+    size_t off_tab64, off_tab32, off_hdr, off_partials, off_result, off_moments, off_fy, off_fx, off_wsegs;
+    int wall_cap;
     size_t total;
     int nbuf;
     int npartials;
@@ -114,8 +119,13 @@ Layout make_layout(const lbm_vset *vs, const lbm_problem *p)
     off = align256(off + sizeof(float) * TAB_ROWS * LBM_MAX_V);
     L.off_hdr = off;
     off = align256(off + sizeof(TableHeader));
-    // the finest launch has LBM_BLOCK/4 cells per block; norms use at most 152*8 blocks
-    long nb = (ncells + LBM_BLOCK / 4 - 1) / (LBM_BLOCK / 4);
+    // segments with a wall cell: at most one per wall cell
+    L.wall_cap = 2 * (p->nx + p->ny) + 4;
+    L.off_wsegs = off;
+    off = align256(off + sizeof(int) * L.wall_cap);
+    // the finest bulk launch has LBM_BLOCK/4 cells per block, plus the wall kernel's
+    // blocks; norms use at most 152*8 blocks
+    long nb = (ncells + LBM_BLOCK / 4 - 1) / (LBM_BLOCK / 4) + wall_grid(L.wall_cap);
     if (nb < 152 * 8) nb = 152 * 8;
     L.npartials = (int)nb;
     L.off_partials = off;
@@ -221,19 +231,40 @@ lbm_status upload_state(lbm_sim *s, const double *h, void *dst)
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "uploading the state");
 }
 
-StepArgs base_args(const lbm_sim *s)
+StepArgs base_args(const lbm_sim *s) { return s->args; }
+
+void fill_args(lbm_sim *s, const TableHeader &hdr)
 {
-    StepArgs a{};
-    a.tab64 = s->tab64;
-    a.tab32 = s->tab32;
-    a.hdr = s->hdr;
+    StepArgs &a = s->args;
+    std::memset(&a, 0, sizeof a);
+    const lbm_problem &p = s->prob;
+    const lbm_vset &v = s->vs;
     a.partials = s->partials;
-    a.nx = s->prob.nx;
-    a.ny = s->prob.ny;
+    a.nx = p.nx;
+    a.ny = p.ny;
     a.ncells = s->ncells;
-    a.cavity = s->prob.geom == LBM_CAVITY;
+    a.cavity = p.geom == LBM_CAVITY;
     a.homogeneous = 0;
-    return a;
+    const bool column = p.geom == LBM_COUETTE && p.nx == 1;
+    for (int i = 0; i < v.m; ++i) {
+        a.xi[i] = v.nodes[i];
+        a.nux[i] = column ? 0.0 : std::fabs(v.nodes[i]) * s->dt / s->dx;
+        a.nuy[i] = std::fabs(v.nodes[i]) * s->dt / s->dy;
+        a.w1[i] = v.weights[i];
+        a.xi_f[i] = (float)a.xi[i];
+        a.nux_f[i] = (float)a.nux[i];
+        a.nuy_f[i] = (float)a.nuy[i];
+        a.w1_f[i] = (float)a.w1[i];
+    }
+    a.omega = s->omega;
+    a.b = 1.0 - s->omega;
+    a.omega_f = (float)a.omega;
+    a.b_f = (float)a.b;
+    a.inv_dx_wall = hdr.inv_dx_wall;
+    a.inv_dy_wall = hdr.inv_dy_wall;
+    a.u_bottom = p.u_bottom;
+    a.u_top = p.u_top;
+    a.inv_u_ref = 1.0 / s->u_ref;
 }
 
 int grid_for(long ncells, int lanes)
@@ -242,12 +273,45 @@ int grid_for(long ncells, int lanes)
     return (int)((ncells + cpb - 1) / cpb);
 }
 
+// Select the lanes-per-cell variant: grid of the bulk kernel and the device list of
+// segments (runs of 32/lanes consecutive cells, one warp each) that contain a wall cell.
+lbm_status set_lanes(lbm_sim *s, int lanes)
+{
+    const int cpw = 32 / lanes;
+    const int nx = s->prob.nx, ny = s->prob.ny;
+    const bool cav = s->prob.geom == LBM_CAVITY;
+    std::vector<int> segs;
+    auto add = [&](long c) {
+        const int sg = (int)(c / cpw);
+        if (segs.empty() || segs.back() != sg) segs.push_back(sg);
+    };
+    // wall cells in ascending order: bottom row, the side cells of each inner row (cavity),
+    // top row
+    for (int x = 0; x < nx; ++x) add(x);
+    for (int y = 1; y < ny - 1 && cav; ++y) {
+        add((long)y * nx);
+        add((long)y * nx + nx - 1);
+    }
+    for (int x = 0; x < nx; ++x) add((long)(ny - 1) * nx + x);
+    if ((int)segs.size() > s->wall_cap) return fail(LBM_EINVAL, "internal: wall segment list overflow");
+    cudaError_t e = cudaMemcpyAsync(s->wall_segs, segs.data(), sizeof(int) * segs.size(),
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the wall segment list");
+    s->lanes = lanes;
+    s->grid = grid_for(s->ncells, lanes);
+    s->args.wall_segs = s->wall_segs;
+    s->args.n_wall_segs = (int)segs.size();
+    s->nparts_step = s->grid + wall_grid((int)segs.size());
+    return LBM_OK;
+}
+
 }  // namespace
 
 int default_lanes_per_cell(int prec, int m)
 {
-    if (prec == LBM_FP64) return m <= 6 ? 1 : (m == 8 ? 2 : 4);
-    return m <= 8 ? 1 : 2;
+    if (prec == LBM_FP64) return m <= 4 ? 1 : (m == 6 ? 2 : 4);
+    return m <= 6 ? 1 : (m == 8 ? 2 : 4);
 }
 
 bool step_supported(int prec, int m, int g)
@@ -347,7 +411,6 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->ncells = (long)prob->nx * prob->ny;
     s->stream = (cudaStream_t)stream;
     s->lanes = default_lanes_per_cell(prob->prec, vs->m);
-    s->grid = grid_for(s->ncells, s->lanes);
     s->step = 0;
     s->resid_step = -1;
     s->cur = 0;
@@ -374,11 +437,14 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->moments = (double *)(b + L.off_moments);
     s->flux_y = (double *)(b + L.off_fy);
     s->flux_x = (double *)(b + L.off_fx);
+    s->wall_segs = (int *)(b + L.off_wsegs);
+    s->wall_cap = L.wall_cap;
 
     std::vector<double> t64;
     std::vector<float> t32;
     TableHeader hdr;
     fill_tables(s, t64, t32, hdr);
+    fill_args(s, hdr);
     cudaError_t e = cudaMallocHost(&s->host_res, sizeof(double) * 8);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->tab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, s->stream);
@@ -394,6 +460,11 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
         lbm_status r = cuda_fail(e, "initialising the simulation");
         lbm_destroy(s);
         return r;
+    }
+    st = set_lanes(s, s->lanes);
+    if (st != LBM_OK) {
+        lbm_destroy(s);
+        return st;
     }
     if (init_h) {
         st = upload_state(s, init_h, s->buf[0]);
@@ -439,13 +510,28 @@ lbm_status lbm_step(lbm_sim *s, long nsteps)
         cudaError_t e = launch_step(s->prob.prec, m, s->lanes, resid, a, s->grid, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
         if (resid) {
-            e = launch_finalize_residual(s->partials, s->grid, s->result, s->stream);
+            e = launch_finalize_residual(s->partials, s->nparts_step, s->result, s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "launching the residual reduction");
             s->resid_step = idx;
         }
         s->cur ^= 1;
         s->step = idx;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_variant(lbm_sim *s, int lanes_per_cell)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (!step_supported(s->prob.prec, s->vs.m, lanes_per_cell))
+        return fail(LBM_EUNSUPPORTED, "no step kernel with %d lanes per cell for M = %d", lanes_per_cell, s->vs.m);
+    return set_lanes(s, lanes_per_cell);
+}
+
+lbm_status lbm_get_variant(const lbm_sim *s, int *lanes_per_cell)
+{
+    if (!s || !lanes_per_cell) return fail(LBM_EINVAL, "NULL argument");
+    *lanes_per_cell = s->lanes;
     return LBM_OK;
 }
 

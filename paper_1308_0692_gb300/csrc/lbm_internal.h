@@ -32,26 +32,42 @@ struct TableHeader {
     double inv_dy_wall;      // 1 / sum_{xi_y>0} xi_y w  (bottom / top walls)
 };
 
-// Arguments of one fused step launch.
+// Arguments of one fused step launch (passed by value: the 1-D coefficient tables
+// live in the kernel-parameter constant bank).
 struct StepArgs {
     const void *h;        // state at time n   [n][ncells]
     void *hn;             // state at time n+1 [n][ncells]
     const void *src;      // optional source added after relaxation (correction sweeps)
-    const double *tab64;  // TAB_ROWS x LBM_MAX_V doubles
-    const float *tab32;   // same, rounded to float
-    const TableHeader *hdr;
     double *partials;     // per-block residual partial sums [2 * gridDim.x]
     int nx, ny;
     long ncells;
     int cavity;
     int homogeneous;      // drop the wall driving terms (correction sweeps)
+    const int *wall_segs; // segments (CPW consecutive cells) that contain a wall cell
+    int n_wall_segs;
+    long partials_offset; // first partials slot of the wall kernel
+    // 1-D tables over the M nodes of one axis (velocity a = iy*M + ix)
+    double xi[LBM_MAX_M];   // nodes
+    double nux[LBM_MAX_M];  // |xi| dt / dx (0 for a single periodic Couette column)
+    double nuy[LBM_MAX_M];  // |xi| dt / dy
+    double w1[LBM_MAX_M];   // 1-D weights (w_a = w1[ix] w1[iy])
+    float xi_f[LBM_MAX_M], nux_f[LBM_MAX_M], nuy_f[LBM_MAX_M], w1_f[LBM_MAX_M];
+    double omega, b;        // dt / Kn, 1 - omega
+    float omega_f, b_f;
+    double inv_dx_wall;     // 1 / sum_{xi_x>0} xi_x w  (side walls)
+    double inv_dy_wall;     // 1 / sum_{xi_y>0} xi_y w  (bottom / top walls)
+    double u_bottom, u_top; // wall speeds
+    double inv_u_ref;       // 1 / u_ref
 };
 
-// Launchers (step_*.cu).  `variant` selects lanes-per-cell G; returns cudaError_t.
+// Launchers (step_*.cu).  `g` selects lanes per cell; a launch is the bulk kernel over
+// `grid` blocks followed by the wall kernel over the wall segments; the residual partials
+// of one step occupy grid + wall_grid(n_wall_segs) slots.
 cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s);
 cudaError_t launch_defect(int m, const StepArgs &a, int grid, cudaStream_t s);
 int default_lanes_per_cell(int prec, int m);
+inline int wall_grid(int n_wall_segs) { return (n_wall_segs + LBM_BLOCK / 32 - 1) / (LBM_BLOCK / 32); }
 bool step_supported(int prec, int m, int g);
 
 // Reductions and diagnostics (reduce.cu)

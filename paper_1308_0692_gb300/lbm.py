@@ -64,6 +64,8 @@ def _load():
         "lbm_coeffs": (st, [_vp, _dp, _dp, _dp]),
         "lbm_step": (st, [_vp, ctypes.c_long]),
         "lbm_residual": (st, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
+        "lbm_set_variant": (st, [_vp, ctypes.c_int]),
+        "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int)]),
         "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
         "lbm_get_state": (st, [_vp, _dp]),
@@ -196,6 +198,16 @@ def lbm_coeffs(sim: Sim):
 
 def lbm_step(sim: Sim, nsteps: int):
     _check(_load().lbm_step(sim.handle, int(nsteps)))
+
+
+def lbm_set_variant(sim: Sim, lanes_per_cell: int):
+    _check(_load().lbm_set_variant(sim.handle, int(lanes_per_cell)))
+
+
+def lbm_get_variant(sim: Sim) -> int:
+    v = ctypes.c_int()
+    _check(_load().lbm_get_variant(sim.handle, ctypes.byref(v)))
+    return v.value
 
 
 def lbm_residual(sim: Sim):
