@@ -16,9 +16,11 @@
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
 
-cudaError_t launch_step_f64(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_step_f32(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f64_small(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f64_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_small(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, int *g_used, cudaStream_t s);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
                                cudaStream_t s);
 
@@ -123,9 +125,9 @@ Layout make_layout(const lbm_vset *vs, const lbm_problem *p)
     L.wall_cap = 2 * (p->nx + p->ny) + 4;
     L.off_wsegs = off;
     off = align256(off + sizeof(int) * L.wall_cap);
-    // the finest bulk launch has LBM_BLOCK/4 cells per block, plus the wall kernel's
+    // the finest bulk launch has one 32-cell segment per block, plus the wall kernel's
     // blocks; norms use at most 152*8 blocks
-    long nb = (ncells + LBM_BLOCK / 4 - 1) / (LBM_BLOCK / 4) + wall_grid(L.wall_cap);
+    long nb = (ncells + 31) / 32 + L.wall_cap;
     if (nb < 152 * 8) nb = 152 * 8;
     L.npartials = (int)nb;
     L.off_partials = off;
@@ -269,7 +271,7 @@ void fill_args(lbm_sim *s, const TableHeader &hdr)
 
 int grid_for(long ncells, int lanes)
 {
-    const long cpb = LBM_BLOCK / lanes;
+    const long cpb = 32L * segs_per_block(lanes);
     return (int)((ncells + cpb - 1) / cpb);
 }
 
@@ -277,7 +279,7 @@ int grid_for(long ncells, int lanes)
 // segments (runs of 32/lanes consecutive cells, one warp each) that contain a wall cell.
 lbm_status set_lanes(lbm_sim *s, int lanes)
 {
-    const int cpw = 32 / lanes;
+    const int cpw = 32;
     const int nx = s->prob.nx, ny = s->prob.ny;
     const bool cav = s->prob.geom == LBM_CAVITY;
     std::vector<int> segs;
@@ -302,7 +304,7 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     s->grid = grid_for(s->ncells, lanes);
     s->args.wall_segs = s->wall_segs;
     s->args.n_wall_segs = (int)segs.size();
-    s->nparts_step = s->grid + wall_grid((int)segs.size());
+    s->nparts_step = s->grid + wall_grid(lanes, (int)segs.size());
     return LBM_OK;
 }
 
@@ -316,8 +318,8 @@ int default_lanes_per_cell(int prec, int m)
 
 bool step_supported(int prec, int m, int g)
 {
-    static const int f64[][2] = {{3, 1}, {4, 1}, {6, 1}, {6, 2}, {8, 2}, {8, 4}, {12, 2}, {12, 4}};
-    static const int f32[][2] = {{3, 1}, {4, 1}, {6, 1}, {6, 2}, {8, 1}, {8, 2}, {12, 1}, {12, 2}, {12, 4}};
+    static const int f64[][2] = {{3, 1}, {4, 1}, {4, 2}, {6, 1}, {6, 2}, {8, 2}, {8, 4}, {12, 3}, {12, 4}, {12, 6}};
+    static const int f32[][2] = {{3, 1}, {4, 1}, {6, 1}, {6, 2}, {8, 1}, {8, 2}, {8, 4}, {12, 2}, {12, 3}, {12, 4}, {12, 6}};
     if (prec == LBM_FP64) {
         for (auto &v : f64) if (v[0] == m && v[1] == g) return true;
     } else {
@@ -329,8 +331,11 @@ bool step_supported(int prec, int m, int g)
 cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s)
 {
-    return prec == LBM_FP64 ? launch_step_f64(m, g, resid, a, grid, s)
-                            : launch_step_f32(m, g, resid, a, grid, s);
+    if (prec == LBM_FP64)
+        return m >= 8 ? launch_step_f64_large(m, g, resid, a, grid, s)
+                      : launch_step_f64_small(m, g, resid, a, grid, s);
+    return m >= 12 ? launch_step_f32_large(m, g, resid, a, grid, s)
+                   : launch_step_f32_small(m, g, resid, a, grid, s);
 }
 
 extern "C" {

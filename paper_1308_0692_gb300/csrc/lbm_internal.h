@@ -43,7 +43,7 @@ struct StepArgs {
     long ncells;
     int cavity;
     int homogeneous;      // drop the wall driving terms (correction sweeps)
-    const int *wall_segs; // segments (CPW consecutive cells) that contain a wall cell
+    const int *wall_segs; // segments (32 consecutive cells) that contain a wall cell
     int n_wall_segs;
     long partials_offset; // first partials slot of the wall kernel
     // 1-D tables over the M nodes of one axis (velocity a = iy*M + ix)
@@ -60,14 +60,15 @@ struct StepArgs {
     double inv_u_ref;       // 1 / u_ref
 };
 
-// Launchers (step_*.cu).  `g` selects lanes per cell; a launch is the bulk kernel over
-// `grid` blocks followed by the wall kernel over the wall segments; the residual partials
-// of one step occupy grid + wall_grid(n_wall_segs) slots.
+// Launchers (step_*.cu).  `g` selects the warps per 32-cell segment; a launch is the
+// bulk kernel over `grid` blocks followed by the wall kernel over the wall segments; the
+// residual partials of one step occupy grid + wall_grid(g, n_wall_segs) slots.
 cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s);
 cudaError_t launch_defect(int m, const StepArgs &a, int grid, cudaStream_t s);
 int default_lanes_per_cell(int prec, int m);
-inline int wall_grid(int n_wall_segs) { return (n_wall_segs + LBM_BLOCK / 32 - 1) / (LBM_BLOCK / 32); }
+inline int segs_per_block(int g) { return g >= 8 ? 1 : 8 / g; }
+inline int wall_grid(int g, int n_wall_segs) { return (n_wall_segs + segs_per_block(g) - 1) / segs_per_block(g); }
 bool step_supported(int prec, int m, int g);
 
 // Reductions and diagnostics (reduce.cu)

@@ -3,35 +3,52 @@
 //             change M(h) - h (the defect) as float, with its norms;
 //   correct : the FP32 step of the homogeneous problem (wall driving removed) plus a
 //             source array -- the correction equation delta = L(delta) + defect.
+// (generated instantiation list; the kernel is in step_kernel.cuh)
 #include "step_kernel.cuh"
 
 using namespace lbmk;
 
-#define LBM_CASE_DEF(M_, G_)                                                                 \
-    if (m == M_) return launch_one<float, double, M_, G_, false, false, true>(a, grid, s);
-
-cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, int *g_used, cudaStream_t s)
 {
-    LBM_CASE_DEF(3, 1)
-    LBM_CASE_DEF(4, 1)
-    LBM_CASE_DEF(6, 1)
-    LBM_CASE_DEF(8, 2)
-    LBM_CASE_DEF(12, 4)
+    if (m == 3) {
+        *g_used = 1;
+        return launch_one<float, double, 3, 1, false, false, true>(a, grid, s);
+    }
+    if (m == 4) {
+        *g_used = 1;
+        return launch_one<float, double, 4, 1, false, false, true>(a, grid, s);
+    }
+    if (m == 6) {
+        *g_used = 2;
+        return launch_one<float, double, 6, 2, false, false, true>(a, grid, s);
+    }
+    if (m == 8) {
+        *g_used = 4;
+        return launch_one<float, double, 8, 4, false, false, true>(a, grid, s);
+    }
+    if (m == 12) {
+        *g_used = 6;
+        return launch_one<float, double, 12, 6, false, false, true>(a, grid, s);
+    }
     return cudaErrorInvalidValue;
 }
 
-#define LBM_CASE_COR(M_, G_)                                                                  \
-    if (m == M_ && g == G_)                                                                   \
-        return resid ? launch_one<float, float, M_, G_, true, true, false>(a, grid, s)        \
-                     : launch_one<float, float, M_, G_, false, true, false>(a, grid, s);
-
-cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
-                               cudaStream_t s)
+cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s)
 {
-    LBM_CASE_COR(3, 1)
-    LBM_CASE_COR(4, 1)
-    LBM_CASE_COR(6, 1)
-    LBM_CASE_COR(8, 1)
-    LBM_CASE_COR(12, 2)
+    if (m == 3 && g == 1)
+        return resid ? launch_one<float, float, 3, 1, true, true, false>(a, grid, s)
+                     : launch_one<float, float, 3, 1, false, true, false>(a, grid, s);
+    if (m == 4 && g == 1)
+        return resid ? launch_one<float, float, 4, 1, true, true, false>(a, grid, s)
+                     : launch_one<float, float, 4, 1, false, true, false>(a, grid, s);
+    if (m == 6 && g == 1)
+        return resid ? launch_one<float, float, 6, 1, true, true, false>(a, grid, s)
+                     : launch_one<float, float, 6, 1, false, true, false>(a, grid, s);
+    if (m == 8 && g == 2)
+        return resid ? launch_one<float, float, 8, 2, true, true, false>(a, grid, s)
+                     : launch_one<float, float, 8, 2, false, true, false>(a, grid, s);
+    if (m == 12 && g == 4)
+        return resid ? launch_one<float, float, 12, 4, true, true, false>(a, grid, s)
+                     : launch_one<float, float, 12, 4, false, true, false>(a, grid, s);
     return cudaErrorInvalidValue;
 }
