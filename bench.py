@@ -257,11 +257,11 @@ def run_own(args, dist: Dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "lid-driven cavity 2048x2048, D2Q^h_144 (N=6 half-range Gauss-Hermite), "
+        "config": {"workload": f"lid-driven cavity {w['nx']}x{w['ny']}, D2Q^h_144 (N=6 half-range Gauss-Hermite), "
                                "Kn=0.05, lid u=0.01, FP32 perturbation storage, FP64 residual every 10 steps",
                    "nx": w["nx"], "ny": w["ny"], "velocities": n_vel, "unknowns": units_per_step,
                    "residual_every": w["residual_every"], "cold_start": True,
-                   "l2": "inputs larger than L2 (2.42 GB per state copy), no flush",
+                   "l2": f"inputs larger than L2 ({units_per_step * 4 / 1e9:.2f} GB per state copy), no flush",
                    "parallelism": f"replicas{dist.world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
@@ -466,7 +466,11 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=None,
+                    help="side of the cavity (default 2048); smaller sides are for profiling only")
     args = ap.parse_args(argv)
+    if args.nx:
+        WORKLOAD["nx"] = WORKLOAD["ny"] = args.nx
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

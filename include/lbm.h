@@ -117,12 +117,35 @@ lbm_status lbm_coeffs(const lbm_sim *sim, double *dt, double *omega, double *u_r
  * relaxation towards w_a (rho + xi_a . j) (Eqs. 1, 5). */
 lbm_status lbm_step(lbm_sim *sim, long nsteps);
 
-/* Kernel variant: the number of warp lanes that share one cell (1, 2 or 4; each lane
- * owns M/lanes velocity rows).  It changes speed, not results beyond rounding order.
+/* Result of lbm_solve. */
+typedef struct {
+    long steps;             /* time steps of the march (FP32: of the FP32 march) */
+    long correction_steps;  /* FP32 refinement: steps of all correction marches */
+    int sweeps;             /* FP32 refinement: defect-correction sweeps applied */
+    double residual;        /* last per-step residual of the march */
+    double defect;          /* FP32 with refinement: ||M(h) - h|| / ||M(h)|| of the final
+                               state, one step M evaluated in FP64; otherwise = residual */
+} lbm_solve_info;
+
+/* March to the steady state: whole residual intervals (residual_every steps) until the
+ * residual drops below tol or max_steps steps were taken (synchronises once per interval).
+ * FP32 simulations may then apply refine_sweeps mixed-precision refinement sweeps: the
+ * defect D = M(h) - h of the stored FP32 state under one FP64 step, a correction march
+ * delta <- L(delta) + D of the homogeneous problem (walls without driving) in FP32 until
+ * its per-step change is below tol * ||h||, and h += delta; sweeps stop early once the
+ * defect stops halving (FP32 rounding floor).  This removes the bias of the FP32 fixed
+ * point (the FP32 operator's rounding amplified by the conditioning of the slow modes),
+ * which plain FP32 storage cannot.  refine_sweeps must be 0 for FP64 simulations. */
+lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps,
+                     lbm_solve_info *info);
+
+/* Kernel variant: the number of warps that share one 32-cell segment (1, 2, 3, 4 or 6
+ * dividing M; each warp owns M/warps velocity rows).  It changes speed, not results
+ * beyond rounding order.
  * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
  * without a compiled kernel.  Used by the autotuner.  Call between steps only. */
-lbm_status lbm_set_variant(lbm_sim *sim, int lanes_per_cell);
-lbm_status lbm_get_variant(const lbm_sim *sim, int *lanes_per_cell);
+lbm_status lbm_set_variant(lbm_sim *sim, int warps_per_segment);
+lbm_status lbm_get_variant(const lbm_sim *sim, int *warps_per_segment);
 
 /* Latest relative residual r and the step count at which it was evaluated
  * (synchronises).  LBM_ENONFINITE if the state contains NaN/Inf. */
@@ -162,6 +185,39 @@ lbm_status lbm_state_device(lbm_sim *sim, void **ptr, long *step);
 lbm_status lbm_norms_scratch_bytes(long count, size_t *bytes);
 lbm_status lbm_norms(const void *a, const void *b, long count, int prec, void *scratch,
                      size_t scratch_bytes, double *out, void *stream);
+
+/* ---- Batched sweeps: many independent instances in one persistent launch ----
+ * A batch holds independent problems (Couette channels and cavities of any size, Kn and
+ * wall speeds; one shared velocity set, precision and residual_every) packed in one
+ * device allocation.  lbm_batch_advance enqueues one cooperative, persistent kernel
+ * launch (captured into a CUDA graph on a non-default stream) that advances every
+ * unconverged instance by nsteps time steps: work items are (instance, 32-cell segment)
+ * pairs taken round-robin by the resident blocks, a grid-wide barrier with a bounded wait
+ * separates steps, and every residual_every steps instances whose residual is below tol
+ * are frozen (their items are skipped from then on).  Supported: FP32 perturbation
+ * storage with 4 or 8 nodes per axis (D2Q^h_16 / D2Q16, D2Q^h_64); wall densities are
+ * summed in FP64, the ghosts evaluated in FP32.  A barrier that gives up makes the next
+ * lbm_batch_poll return LBM_ETIMEOUT. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_bytes(const lbm_vset *vs, const lbm_problem *insts, int count, size_t *bytes);
+lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int count, void *device_buf,
+                          size_t buf_bytes, void *stream, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+/* Schedule: warps per segment (1, 2 or 4), resident blocks per SM (<= 0: the occupancy
+ * maximum), item order (0 given order, 1 largest instance first, 2 segments interleaved
+ * across instances).  Chosen by the autotuner; any choice gives the same results. */
+lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int blocks_per_sm, int order);
+lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, int *blocks_per_sm,
+                                  int *order, int *grid);
+lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol);     /* asynchronous */
+/* Limit of every bounded wait in the grid barrier, in SM clock cycles (default 4e9, about
+ * 2 s).  Exposed so that tests can make a wait give up and check the error path. */
+lbm_status lbm_batch_set_timeout(lbm_batch *b, long long cycles);
+lbm_status lbm_batch_poll(lbm_batch *b, int *n_active, long *step);     /* synchronises */
+/* Instance i: steps taken (the step at which it converged, or all steps so far), last
+ * residual, converged flag; its state as host FP64 [n][ny][nx]. */
+lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, int *converged);
+lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *lbm_last_error(void);

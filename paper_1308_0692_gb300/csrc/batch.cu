@@ -1,0 +1,798 @@
+// Batched march of many independent boundary-value problems (Couette channels and
+// lid-driven cavities of different sizes, Knudsen numbers and wall speeds) in one
+// persistent, cooperative kernel launch that advances every unconverged instance by a
+// block of time steps, captured once into a CUDA graph and replayed.
+//
+// Each time step is the paper's fully discrete scheme (Eqs. 1, 5-9; the same arithmetic
+// as step_kernel.cuh) applied to every active instance.  Work items are (instance,
+// 32-cell segment) pairs in a schedule order chosen by the autotuner; the blocks of the
+// persistent grid take items round-robin, a grid-wide barrier separates time steps, and
+// every `resid_every` steps the per-instance residuals are reduced (FP64 atomics) and
+// instances below the tolerance are frozen: from then on their items are skipped and
+// their state stays in the buffer of the step at which they converged.
+//
+// Every wait in the grid barrier is bounded (clock64 against a limit); a barrier that
+// gives up sets an error word that all blocks check after each barrier, so the kernel
+// returns and the host reports LBM_ETIMEOUT.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+#include "step_kernel.cuh"
+
+lbm_status lbm_norms_fail(lbm_status s, const char *msg);
+
+namespace {
+
+struct BatchInst {
+    long off;           // element offset of the instance's state [n][ncells] in each array
+    long ncells;
+    int nx, ny, cavity;
+    int pad;
+    double cx, cy;      // dt/dx (0 for a single periodic Couette column), dt/dy
+    double omega, b;
+    double u_bottom, u_top, inv_u_ref;
+};
+
+struct BatchArgs {
+    void *buf[2];
+    const BatchInst *inst;
+    int ninst;
+    const int2 *items;     // (instance, segment)
+    int nitems;
+    double *acc;           // [ninst][2] residual sums of the current interval
+    double *last_r;        // [ninst]
+    long *frozen;          // [ninst] step count at convergence (LONG_MAX while active)
+    unsigned *bar_count;
+    unsigned *bar_gen;
+    int *err;
+    long step0;
+    int nsteps;
+    int resid_every;
+    double tol;
+    long long timeout_cycles;
+    double xi[LBM_MAX_M], w1[LBM_MAX_M];
+    float xi_f[LBM_MAX_M], w1_f[LBM_MAX_M];
+    double inv_dx_wall, inv_dy_wall;
+};
+
+// Grid-wide barrier with a bounded wait; returns false once any block has given up.
+__device__ bool grid_barrier(const BatchArgs &a)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = a.bar_gen;
+        const unsigned my_gen = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(a.bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(a.bar_count, 0u);
+            __threadfence();
+            atomicAdd(a.bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == my_gen) {
+                if (*(volatile int *)a.err != 0) break;
+                if (clock64() - t0 > a.timeout_cycles) {
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)a.err == 0;
+}
+
+template <typename TC>
+__device__ __forceinline__ TC pk(const double *d, const float *f, int i) { return lbmk::pick<TC>(d, f, i); }
+
+template <typename TS, typename TC, int M, int G>
+__global__ void __launch_bounds__(lbmk::Shape<G>::THREADS) batch_kernel(const BatchArgs a)
+{
+    constexpr int SPB = lbmk::Shape<G>::SPB;
+    constexpr int WARPS = lbmk::Shape<G>::WARPS;
+    constexpr int RPL = M / G;
+    constexpr int HALF = M / 2;
+    __shared__ TC s_mom[3][G][SPB][32];
+    __shared__ double s_wall[4][G][SPB][32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl = warp / G, g = warp - sl * G;
+    (void)WARPS;
+
+    for (int si = 0; si < a.nsteps; ++si) {
+        const long s = a.step0 + si;
+        const TS *__restrict__ h = reinterpret_cast<const TS *>(a.buf[s & 1]);
+        TS *__restrict__ hn = reinterpret_cast<TS *>(a.buf[(s + 1) & 1]);
+        const bool resid = ((s + 1) % a.resid_every) == 0;
+        const long ngroups = ((long)a.nitems + SPB - 1) / SPB;
+        for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+            const long item = grp * SPB + sl;
+            bool active = item < a.nitems;
+            int2 it = make_int2(0, 0);
+            if (active) it = a.items[item];
+            const BatchInst &I = a.inst[it.x];
+            if (active && a.frozen[it.x] <= s) active = false;
+            const long ncells = I.ncells;
+            const int nx = I.nx, ny = I.ny;
+            const bool cav = I.cavity != 0;
+            const long cell0 = (long)it.y * 32 + lane;
+            const bool in_grid = cell0 < ncells;
+            const long c = in_grid ? cell0 : ncells - 1;
+            const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+            const bool is_wall = in_grid && (y == 0 || y == ny - 1 || (cav && (x == 0 || x == nx - 1)));
+            const bool wall_seg = active && __any_sync(FULL, is_wall);
+            const bool valid = active && in_grid;
+            const TS *hi = h + I.off;
+            TS *hno = hn + I.off;
+            const bool wl = cav && x == 0, wr = cav && x == nx - 1, wb = y == 0, wt = y == ny - 1;
+            const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);
+            const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
+            const long c_below = (y > 0) ? c - nx : c;
+            const long c_above = (y < ny - 1) ? c + nx : c;
+
+            // wall densities (FP64, Eq. 9), summed across the G warps of the segment
+            double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
+            if (wall_seg) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int iy = g * RPL + r;
+                    const double xiy = a.xi[iy];
+                    double rowsum = 0.0, left = 0.0, right = 0.0;
+#pragma unroll
+                    for (int ix = 0; ix < M; ++ix) {
+                        const double v = (double)__ldg(hi + (long)(iy * M + ix) * ncells + c);
+                        rowsum += v;
+                        if (ix < HALF) left -= a.xi[ix] * v;
+                        if (ix >= M - HALF) right += a.xi[ix] * v;
+                    }
+                    if (xiy < 0.0) sb -= xiy * rowsum;
+                    if (xiy > 0.0) st += xiy * rowsum;
+                    sls += left;
+                    srs += right;
+                }
+            }
+            s_wall[0][g][sl][lane] = sb;
+            s_wall[1][g][sl][lane] = st;
+            s_wall[2][g][sl][lane] = sls;
+            s_wall[3][g][sl][lane] = srs;
+            __syncthreads();
+            sb = st = sls = srs = 0.0;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                sb += s_wall[0][q][sl][lane];
+                st += s_wall[1][q][sl][lane];
+                sls += s_wall[2][q][sl][lane];
+                srs += s_wall[3][q][sl][lane];
+            }
+            const double rb = sb * a.inv_dy_wall, rt = st * a.inv_dy_wall;
+            const double rl = sls * a.inv_dx_wall, rr = srs * a.inv_dx_wall;
+
+            // transport + moment row sums.  Upwind values across a wall are the ghosts
+            // w_a [rho'_w (1 + xi_t U) + xi_t U / u_ref] (Eq. 8), evaluated in the
+            // arithmetic type from the FP64 wall densities and selected per lane, so wall
+            // and interior segments share one code path.
+            TC hs[RPL * M];
+            TC rho = 0, jx = 0, jy = 0;
+            if (active) {
+                const TC cx = (TC)I.cx, cy = (TC)I.cy;
+                const TC rl_t = (TC)rl, rr_t = (TC)rr;
+                const bool xw_l = wall_seg && wl, xw_r = wall_seg && wr;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int iy = g * RPL + r;
+                    const TC xiy = pk<TC>(a.xi, a.xi_f, iy);
+                    const TC nuy = (xiy < TC(0) ? -xiy : xiy) * cy;
+                    const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
+                    const long cy_idx = ypos ? c_below : (yneg ? c_above : c);
+                    const bool ywall = wall_seg && ((ypos && wb) || (yneg && wt));
+                    const TC rho_y = (TC)(ypos ? rb : rt);
+                    const TC u_y = (TC)(ypos ? I.u_bottom : I.u_top);
+                    const TC drive_y = (TC)((ypos ? I.u_bottom : I.u_top) * I.inv_u_ref);
+                    const TC wy = pk<TC>(a.w1, a.w1_f, iy);
+                    TC R = 0, X = 0;
+#pragma unroll
+                    for (int ix = 0; ix < M; ++ix) {
+                        const TS *hp = hi + (long)(iy * M + ix) * ncells;
+                        const TC hc = (TC)__ldg(hp + c);
+                        const TC xix = pk<TC>(a.xi, a.xi_f, ix);
+                        const TC wxy = pk<TC>(a.w1, a.w1_f, ix) * wy;
+                        TC v = hc;
+                        if (ix >= M - HALF || ix < HALF) {
+                            const bool right_side = ix < HALF;          // xi_x < 0: upwind is the right cell
+                            const TC hl = (TC)__ldg(hp + (right_side ? c_right : c_left));
+                            const bool xw = right_side ? xw_r : xw_l;
+                            const TC hx = xw ? wxy * (right_side ? rr_t : rl_t) : hl;
+                            v += (xix < TC(0) ? -xix : xix) * cx * (hx - hc);
+                        }
+                        const TC hl = (TC)__ldg(hp + cy_idx);
+                        const TC hy = ywall ? wxy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y) : hl;
+                        v += nuy * (hy - hc);
+                        hs[r * M + ix] = v;
+                        R += v;
+                        X += xix * v;
+                    }
+                    rho += R;
+                    jx += X;
+                    jy += xiy * R;
+                }
+            }
+            s_mom[0][g][sl][lane] = rho;
+            s_mom[1][g][sl][lane] = jx;
+            s_mom[2][g][sl][lane] = jy;
+            __syncthreads();
+            rho = jx = jy = 0;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                rho += s_mom[0][q][sl][lane];
+                jx += s_mom[1][q][sl][lane];
+                jy += s_mom[2][q][sl][lane];
+            }
+
+            // relaxation, store, residual sums
+            TC psd = 0, psn = 0;
+            if (active) {
+                const TC om = (TC)I.omega, b = (TC)I.b;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int iy = g * RPL + r;
+                    const TC wom = om * pk<TC>(a.w1, a.w1_f, iy);
+                    const TC q = wom * (rho + pk<TC>(a.xi, a.xi_f, iy) * jy);
+                    const TC jj = wom * jx;
+#pragma unroll
+                    for (int ix = 0; ix < M; ++ix) {
+                        const long off = (long)(iy * M + ix) * ncells + c;
+                        const TC t = q + pk<TC>(a.xi, a.xi_f, ix) * jj;
+                        const TC v = b * hs[r * M + ix] + pk<TC>(a.w1, a.w1_f, ix) * t;
+                        if (resid) {
+                            const TC d = v - (TC)__ldg(hi + off);
+                            psd += d * d;
+                            psn += v * v;
+                        }
+                        if (valid) hno[off] = (TS)v;
+                    }
+                }
+            }
+            if (resid && active) {
+                double dsd = valid ? (double)psd : 0.0, dsn = valid ? (double)psn : 0.0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    dsd += __shfl_xor_sync(FULL, dsd, off);
+                    dsn += __shfl_xor_sync(FULL, dsn, off);
+                }
+                if (lane == 0) {
+                    atomicAdd(a.acc + 2 * it.x, dsd);
+                    atomicAdd(a.acc + 2 * it.x + 1, dsn);
+                }
+            }
+            __syncthreads();   // shared arrays are reused by the next group
+        }
+        if (!grid_barrier(a)) return;
+        if (resid) {
+            if (blockIdx.x == 0) {
+                for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
+                    if (a.frozen[i] <= s) continue;
+                    const double sd = a.acc[2 * i], sn = a.acc[2 * i + 1];
+                    const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
+                    a.last_r[i] = r;
+                    if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
+                    if (r < a.tol) a.frozen[i] = s + 1;
+                    a.acc[2 * i] = 0.0;
+                    a.acc[2 * i + 1] = 0.0;
+                }
+            }
+            if (!grid_barrier(a)) return;
+        }
+    }
+}
+
+template <typename TS, typename TC, int M, int G>
+void *kernel_ptr() { return (void *)batch_kernel<TS, TC, M, G>; }
+
+struct Variant {
+    int prec, m, g;
+    void *fn;
+    int threads;
+};
+
+const std::vector<Variant> &variants()
+{
+    static const std::vector<Variant> v = {
+        {LBM_FP32_PERTURB, 8, 1, kernel_ptr<float, float, 8, 1>(), lbmk::Shape<1>::THREADS},
+        {LBM_FP32_PERTURB, 8, 2, kernel_ptr<float, float, 8, 2>(), lbmk::Shape<2>::THREADS},
+        {LBM_FP32_PERTURB, 8, 4, kernel_ptr<float, float, 8, 4>(), lbmk::Shape<4>::THREADS},
+        {LBM_FP32_PERTURB, 4, 1, kernel_ptr<float, float, 4, 1>(), lbmk::Shape<1>::THREADS},
+        {LBM_FP32_PERTURB, 4, 2, kernel_ptr<float, float, 4, 2>(), lbmk::Shape<2>::THREADS},
+    };
+    return v;
+}
+
+const Variant *find_variant(int prec, int m, int g)
+{
+    for (const auto &v : variants())
+        if (v.prec == prec && v.m == m && v.g == g) return &v;
+    return nullptr;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct lbm_batch {
+    std::vector<lbm_problem> probs;
+    std::vector<BatchInst> inst;
+    int m, nv, prec;
+    std::vector<double> nodes, weights;
+    cudaStream_t stream;
+    void *base;
+    bool owns;
+    size_t bytes;
+    long total_vals;
+    // device pointers
+    void *buf[2];
+    BatchInst *d_inst;
+    int2 *d_items;
+    double *d_acc, *d_last_r;
+    long *d_frozen;
+    unsigned *d_bar;
+    int *d_err;
+    // schedule
+    int g, blocks_per_sm, order, nitems;
+    int grid;
+    const Variant *var;
+    long step;
+    int resid_every;
+    cudaGraphExec_t graph;
+    bool graph_ok;
+    long long timeout_cycles;
+};
+
+namespace {
+
+lbm_status bfail(lbm_status s, const std::string &m) { return lbm_norms_fail(s, m.c_str()); }
+
+void inst_coeffs(const lbm_problem &p, const std::vector<double> &nodes, BatchInst &I)
+{
+    double mx = 0;
+    for (double v : nodes) mx = std::max(mx, std::fabs(v));
+    double dx, dy;
+    if (p.geom == LBM_COUETTE) {
+        dy = 1.0 / p.ny;
+        dx = dy;
+    } else {
+        dx = 1.0 / p.nx;
+        dy = 1.0 / p.ny;
+    }
+    double rate = mx / dy;
+    const bool column = p.geom == LBM_COUETTE && p.nx == 1;
+    if (!column) rate += mx / dx;
+    double dt = p.cfl / rate;
+    if (std::isfinite(p.kn) && dt > p.kn) dt = p.kn;
+    I.cx = column ? 0.0 : dt / dx;
+    I.cy = dt / dy;
+    I.omega = std::isfinite(p.kn) ? dt / p.kn : 0.0;
+    I.b = 1.0 - I.omega;
+    I.u_bottom = p.u_bottom;
+    I.u_top = p.u_top;
+    double ur = std::max(std::fabs(p.u_bottom), std::fabs(p.u_top));
+    if (ur == 0) ur = 1.0;
+    I.inv_u_ref = 1.0 / ur;
+    I.nx = p.nx;
+    I.ny = p.ny;
+    I.cavity = p.geom == LBM_CAVITY;
+    I.ncells = (long)p.nx * p.ny;
+}
+
+// Build the (instance, segment) list in one of three orders:
+//   0: instance by instance, in the given order;
+//   1: instances by decreasing size;
+//   2: segments interleaved round-robin across instances (largest first).
+std::vector<int2> build_items(const lbm_batch *b, int order)
+{
+    const int ni = (int)b->inst.size();
+    std::vector<int> idx(ni);
+    for (int i = 0; i < ni; ++i) idx[i] = i;
+    if (order >= 1)
+        std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return b->inst[p].ncells > b->inst[q].ncells; });
+    std::vector<int2> items;
+    if (order <= 1) {
+        for (int i : idx) {
+            const int nseg = (int)((b->inst[i].ncells + 31) / 32);
+            for (int sgm = 0; sgm < nseg; ++sgm) items.push_back(make_int2(i, sgm));
+        }
+    } else {
+        int maxseg = 0;
+        for (int i : idx) maxseg = std::max(maxseg, (int)((b->inst[i].ncells + 31) / 32));
+        for (int sgm = 0; sgm < maxseg; ++sgm)
+            for (int i : idx)
+                if (sgm < (int)((b->inst[i].ncells + 31) / 32)) items.push_back(make_int2(i, sgm));
+    }
+    return items;
+}
+
+lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
+{
+    const Variant *v = find_variant(b->prec, b->m, g);
+    if (!v) return bfail(LBM_EUNSUPPORTED, "no batched kernel for this precision / velocity set / warps per segment");
+    int dev = 0, nsm = 0, maxb = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, v->fn, v->threads, 0);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    if (maxb < 1) return bfail(LBM_EUNSUPPORTED, "batched kernel does not fit on an SM");
+    if (bpsm < 1 || bpsm > maxb) bpsm = maxb;
+    std::vector<int2> items = build_items(b, order);
+    e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("uploading the schedule: ") + cudaGetErrorString(e));
+    if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+    b->graph_ok = false;
+    b->var = v;
+    b->g = g;
+    b->blocks_per_sm = bpsm;
+    b->order = order;
+    b->nitems = (int)items.size();
+    const int spb = segs_per_block(g);
+    const long groups = ((long)b->nitems + spb - 1) / spb;
+    b->grid = (int)std::min<long>((long)nsm * bpsm, std::max<long>(1, groups));
+    return LBM_OK;
+}
+
+BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
+{
+    BatchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.buf[0] = b->buf[0];
+    a.buf[1] = b->buf[1];
+    a.inst = b->d_inst;
+    a.ninst = (int)b->inst.size();
+    a.items = b->d_items;
+    a.nitems = b->nitems;
+    a.acc = b->d_acc;
+    a.last_r = b->d_last_r;
+    a.frozen = b->d_frozen;
+    a.bar_count = b->d_bar;
+    a.bar_gen = b->d_bar + 1;
+    a.err = b->d_err;
+    a.step0 = b->step;
+    a.nsteps = nsteps;
+    a.resid_every = b->resid_every;
+    a.tol = tol;
+    a.timeout_cycles = b->timeout_cycles;
+    double sx = 0, sy = 0;
+    const int m = b->m;
+    for (int i = 0; i < m; ++i) {
+        a.xi[i] = b->nodes[i];
+        a.w1[i] = b->weights[i];
+        a.xi_f[i] = (float)b->nodes[i];
+        a.w1_f[i] = (float)b->weights[i];
+    }
+    for (int iy = 0; iy < m; ++iy)
+        for (int ix = 0; ix < m; ++ix) {
+            const double w = b->weights[ix] * b->weights[iy];
+            if (b->nodes[ix] > 0) sx += b->nodes[ix] * w;
+            if (b->nodes[iy] > 0) sy += b->nodes[iy] * w;
+        }
+    a.inv_dx_wall = 1.0 / sx;
+    a.inv_dy_wall = 1.0 / sy;
+    return a;
+}
+
+cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a)
+{
+    void *args[] = {(void *)&a};
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(b->var->threads);
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, b->var->fn, args);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_bytes(const lbm_vset *vs, const lbm_problem *insts, int count, size_t *bytes);
+lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int count, void *device_buf,
+                          size_t buf_bytes, void *stream, lbm_batch **out);
+
+static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int count, int *prec,
+                               long *total_vals, long *total_segs, size_t *bytes)
+{
+    int nv = 0, m = 0;
+    lbm_status st = lbm_vset_query(vs, &nv, &m, nullptr, nullptr, nullptr);
+    if (st != LBM_OK) return st;
+    if (!insts || count < 1) return bfail(LBM_EINVAL, "batch needs at least one instance");
+    const int p0 = insts[0].prec;
+    long vals = 0, segs = 0;
+    for (int i = 0; i < count; ++i) {
+        size_t one;
+        st = lbm_sim_bytes(vs, &insts[i], &one);   // validates the instance
+        if (st != LBM_OK) return st;
+        if (insts[i].prec != p0) return bfail(LBM_EINVAL, "all batch instances must share the precision");
+        if (insts[i].residual_every != insts[0].residual_every)
+            return bfail(LBM_EINVAL, "all batch instances must share residual_every");
+        const long nc = (long)insts[i].nx * insts[i].ny;
+        vals += (long)nv * nc;
+        segs += (nc + 31) / 32;
+    }
+    if (p0 != LBM_FP32_PERTURB || !find_variant(p0, m, 1))
+        return bfail(LBM_EUNSUPPORTED, "batched kernels exist for FP32 with 4 or 8 nodes per axis");
+    const size_t es = p0 == LBM_FP64 ? 8 : 4;
+    size_t off = 0;
+    off = align256(off + vals * es);          // buffer 0
+    off = align256(off + vals * es);          // buffer 1
+    off = align256(off + sizeof(BatchInst) * count);
+    off = align256(off + sizeof(int2) * segs);
+    off = align256(off + sizeof(double) * 2 * count);
+    off = align256(off + sizeof(double) * count);
+    off = align256(off + sizeof(long) * count);
+    off = align256(off + 64);
+    *prec = p0;
+    *total_vals = vals;
+    *total_segs = segs;
+    *bytes = off;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_bytes(const lbm_vset *vs, const lbm_problem *insts, int count, size_t *bytes)
+{
+    if (!bytes) return bfail(LBM_EINVAL, "bytes is NULL");
+    int prec;
+    long vals, segs;
+    return batch_layout(vs, insts, count, &prec, &vals, &segs, bytes);
+}
+
+lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int count, void *device_buf,
+                          size_t buf_bytes, void *stream, lbm_batch **out)
+{
+    if (!out) return bfail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int prec;
+    long vals, segs;
+    size_t bytes;
+    lbm_status st = batch_layout(vs, insts, count, &prec, &vals, &segs, &bytes);
+    if (st != LBM_OK) return st;
+    if (device_buf && buf_bytes < bytes) return bfail(LBM_ENOMEM, "device buffer too small for the batch");
+    if (device_buf && ((uintptr_t)device_buf & 255)) return bfail(LBM_EINVAL, "device buffer must be 256-byte aligned");
+    lbm_batch *b = new (std::nothrow) lbm_batch;
+    if (!b) return bfail(LBM_ENOMEM, "host allocation failed");
+    int nv = 0, m = 0;
+    lbm_vset_query(vs, &nv, &m, nullptr, nullptr, nullptr);
+    std::vector<double> xx(nv), yy(nv), ww(nv);
+    lbm_vset_query(vs, nullptr, nullptr, xx.data(), yy.data(), ww.data());
+    b->m = m;
+    b->nv = nv;
+    b->prec = prec;
+    b->nodes.assign(xx.begin(), xx.begin() + m);
+    b->weights.resize(m);
+    // 1-D weights from the tensor product: w[ix] = w(ix, iy0) / w1[iy0], w1 from the row sums
+    for (int ix = 0; ix < m; ++ix) {
+        double col = 0;
+        for (int iy = 0; iy < m; ++iy) col += ww[iy * m + ix];
+        b->weights[ix] = col;
+    }
+    b->probs.assign(insts, insts + count);
+    b->inst.resize(count);
+    long off = 0;
+    for (int i = 0; i < count; ++i) {
+        inst_coeffs(insts[i], b->nodes, b->inst[i]);
+        b->inst[i].off = off;
+        off += (long)nv * b->inst[i].ncells;
+    }
+    b->stream = (cudaStream_t)stream;
+    b->owns = device_buf == nullptr;
+    b->bytes = bytes;
+    b->total_vals = vals;
+    b->step = 0;
+    b->resid_every = insts[0].residual_every;
+    b->graph_ok = false;
+    b->timeout_cycles = 4000000000LL;   // about 2 s at the GB300 SM clock
+    if (b->owns) {
+        cudaError_t e = cudaMalloc(&b->base, bytes);
+        if (e != cudaSuccess) {
+            delete b;
+            return bfail(LBM_ENOMEM, std::string("cudaMalloc for the batch: ") + cudaGetErrorString(e));
+        }
+    } else {
+        b->base = device_buf;
+    }
+    const size_t es = prec == LBM_FP64 ? 8 : 4;
+    char *p = (char *)b->base;
+    size_t o = 0;
+    b->buf[0] = p + o;
+    o = align256(o + vals * es);
+    b->buf[1] = p + o;
+    o = align256(o + vals * es);
+    b->d_inst = (BatchInst *)(p + o);
+    o = align256(o + sizeof(BatchInst) * count);
+    b->d_items = (int2 *)(p + o);
+    o = align256(o + sizeof(int2) * segs);
+    b->d_acc = (double *)(p + o);
+    o = align256(o + sizeof(double) * 2 * count);
+    b->d_last_r = (double *)(p + o);
+    o = align256(o + sizeof(double) * count);
+    b->d_frozen = (long *)(p + o);
+    o = align256(o + sizeof(long) * count);
+    b->d_bar = (unsigned *)(p + o);
+    b->d_err = (int *)(p + o + 16);
+    std::vector<long> frozen(count, LONG_MAX);
+    std::vector<double> last(count, INFINITY);
+    cudaError_t e = cudaMemsetAsync(b->buf[0], 0, vals * es, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[1], 0, vals * es, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_acc, 0, sizeof(double) * 2 * count, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_last_r, last.data(), sizeof(double) * count, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_frozen, frozen.data(), sizeof(long) * count, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 64, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return bfail(LBM_ECUDA, std::string("initialising the batch: ") + cudaGetErrorString(e));
+    }
+    st = apply_schedule(b, b->m == 8 ? 4 : 2, 0, 2);
+    if (st != LBM_OK) {
+        lbm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+    if (b->owns && b->base) cudaFree(b->base);
+    delete b;
+}
+
+lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int blocks_per_sm, int order)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (order < 0 || order > 2) return bfail(LBM_EINVAL, "order must be 0, 1 or 2");
+    return apply_schedule(b, warps_per_segment, blocks_per_sm, order);
+}
+
+lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, int *blocks_per_sm, int *order,
+                                  int *grid)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (warps_per_segment) *warps_per_segment = b->g;
+    if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+    if (order) *order = b->order;
+    if (grid) *grid = b->grid;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_timeout(lbm_batch *b, long long cycles)
+{
+    if (!b || cycles < 1) return bfail(LBM_EINVAL, "invalid timeout");
+    b->timeout_cycles = cycles;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (nsteps < 1 || !(tol >= 0)) return bfail(LBM_EINVAL, "nsteps must be >= 1 and tol >= 0");
+    BatchArgs a = make_args(b, nsteps, tol);
+    cudaError_t e;
+    // the graph holds the launch arguments by value: re-capture whenever they change
+    // (the start step does; so the captured graph covers whole blocks of nsteps steps from
+    // an even start, replayed with the start step patched through a kernel-node update)
+    if (b->stream) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = launch_batch(b, a);
+            e = cudaStreamEndCapture(b->stream, &g);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) {
+            if (b->graph_ok) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(b->graph, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(b->graph);
+                    b->graph_ok = false;
+                }
+            }
+            if (!b->graph_ok) {
+                e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (e == cudaSuccess) b->graph_ok = true;
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) {        // fall back to a direct cooperative launch
+            cudaGetLastError();
+            e = launch_batch(b, a);
+        }
+    } else {
+        e = launch_batch(b, a);
+    }
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("launching the batched kernel: ") + cudaGetErrorString(e));
+    b->step += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_poll(lbm_batch *b, int *n_active, long *step)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    const int n = (int)b->inst.size();
+    std::vector<long> frozen(n);
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(frozen.data(), b->d_frozen, sizeof(long) * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("polling the batch: ") + cudaGetErrorString(e));
+    if (err == 1) return bfail(LBM_ETIMEOUT, "a grid barrier of the batched kernel timed out");
+    if (err == 2) return bfail(LBM_ENONFINITE, "non-finite residual in the batch");
+    int act = 0;
+    for (long f : frozen) act += f == LONG_MAX;
+    if (n_active) *n_active = act;
+    if (step) *step = b->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, int *converged)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
+    long f;
+    double r;
+    cudaError_t e = cudaMemcpyAsync(&f, b->d_frozen + i, sizeof(long), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, b->d_last_r + i, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("reading instance status: ") + cudaGetErrorString(e));
+    if (steps) *steps = f == LONG_MAX ? b->step : f;
+    if (residual) *residual = r;
+    if (converged) *converged = f != LONG_MAX;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h)
+{
+    if (!b || !h) return bfail(LBM_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
+    long steps;
+    lbm_status st = lbm_batch_status(b, i, &steps, nullptr, nullptr);
+    if (st != LBM_OK) return st;
+    const long n = (long)b->nv * b->inst[i].ncells;
+    const int par = (int)(steps & 1);
+    cudaError_t e;
+    if (b->prec == LBM_FP64) {
+        e = cudaMemcpyAsync(h, (double *)b->buf[par] + b->inst[i].off, sizeof(double) * n,
+                            cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else {
+        std::vector<float> tmp(n);
+        e = cudaMemcpyAsync(tmp.data(), (float *)b->buf[par] + b->inst[i].off, sizeof(float) * n,
+                            cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess)
+            for (long k = 0; k < n; ++k) h[k] = tmp[k];
+    }
+    return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("reading instance state: ") + cudaGetErrorString(e));
+}
+
+}  // extern "C"

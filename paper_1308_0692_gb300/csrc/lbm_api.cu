@@ -20,7 +20,9 @@ cudaError_t launch_step_f64_small(int m, int g, bool resid, const StepArgs &a, i
 cudaError_t launch_step_f64_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_step_f32_small(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_step_f32_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, int *g_used, cudaStream_t s);
+cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s);
+int defect_lanes(int m);
+int correct_lanes(int m);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
                                cudaStream_t s);
 
@@ -61,6 +63,8 @@ struct lbm_sim {
     double *flux_x;       // ny * (nx+1)
     double *host_res;     // pinned host copy of result
     StepArgs args;        // launch arguments except the buffer pointers
+    cudaGraphExec_t graph[2];  // residual_every steps starting from buffer 0 / 1
+    bool graph_ok[2];
     long step;
     long resid_step;
 };
@@ -80,6 +84,13 @@ lbm_status fail(lbm_status s, const char *fmt, ...)
     g_err = buf;
     return s;
 }
+
+}  // namespace
+
+// error reporting for the other translation units of the library
+lbm_status lbm_norms_fail(lbm_status s, const char *msg) { return fail(s, "%s", msg); }
+
+namespace {
 
 lbm_status cuda_fail(cudaError_t e, const char *what)
 {
@@ -275,6 +286,53 @@ int grid_for(long ncells, int lanes)
     return (int)((ncells + cpb - 1) / cpb);
 }
 
+void drop_graphs(lbm_sim *s)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (s->graph_ok[p]) cudaGraphExecDestroy(s->graph[p]);
+        s->graph_ok[p] = false;
+    }
+}
+
+// Enqueue steps [first, first + count) starting from buffer `cur` (no bookkeeping).
+cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur)
+{
+    StepArgs a = s->args;
+    for (long i = 0; i < count; ++i) {
+        const long idx = first + i;
+        const bool resid = idx % s->prob.residual_every == 0;
+        a.h = s->buf[cur];
+        a.hn = s->buf[cur ^ 1];
+        cudaError_t e = launch_step(s->prob.prec, s->vs.m, s->lanes, resid, a, s->grid, s->stream);
+        if (e != cudaSuccess) return e;
+        if (resid) {
+            e = launch_finalize_residual(s->partials, s->nparts_step, s->result, s->stream);
+            if (e != cudaSuccess) return e;
+        }
+        cur ^= 1;
+    }
+    return cudaSuccess;
+}
+
+// CUDA graph of residual_every steps from buffer `cur`, captured on the sim's stream.
+cudaError_t make_graph(lbm_sim *s, int cur)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const long K = s->prob.residual_every;
+    cudaError_t e2 = enqueue_steps(s, 1, K, cur);   // indices 1..K: residual on the last
+    e = cudaStreamEndCapture(s->stream, &g);
+    if (e2 != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e2 != cudaSuccess ? e2 : e;
+    }
+    e = cudaGraphInstantiate(&s->graph[cur], g, 0);
+    cudaGraphDestroy(g);
+    if (e == cudaSuccess) s->graph_ok[cur] = true;
+    return e;
+}
+
 // Select the lanes-per-cell variant: grid of the bulk kernel and the device list of
 // segments (runs of 32/lanes consecutive cells, one warp each) that contain a wall cell.
 lbm_status set_lanes(lbm_sim *s, int lanes)
@@ -300,6 +358,7 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
                                     cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the wall segment list");
+    drop_graphs(s);
     s->lanes = lanes;
     s->grid = grid_for(s->ncells, lanes);
     s->args.wall_segs = s->wall_segs;
@@ -420,6 +479,7 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->resid_step = -1;
     s->cur = 0;
     s->host_res = nullptr;
+    s->graph_ok[0] = s->graph_ok[1] = false;
     s->owns = device_buf == nullptr;
     s->bytes = L.total;
     if (s->owns) {
@@ -487,6 +547,7 @@ void lbm_destroy(lbm_sim *s)
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
+    drop_graphs(s);
     if (s->owns && s->base) cudaFree(s->base);
     if (s->host_res) cudaFreeHost(s->host_res);
     delete s;
@@ -505,23 +566,156 @@ lbm_status lbm_step(lbm_sim *s, long nsteps)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps must be >= 0");
-    StepArgs a = base_args(s);
-    const int m = s->vs.m;
-    for (long i = 0; i < nsteps; ++i) {
-        const long idx = s->step + 1;
-        const bool resid = idx % s->prob.residual_every == 0;
-        a.h = s->buf[s->cur];
-        a.hn = s->buf[s->cur ^ 1];
-        cudaError_t e = launch_step(s->prob.prec, m, s->lanes, resid, a, s->grid, s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
-        if (resid) {
-            e = launch_finalize_residual(s->partials, s->nparts_step, s->result, s->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "launching the residual reduction");
-            s->resid_step = idx;
+    const long K = s->prob.residual_every;
+    // whole residual intervals replay a captured graph (not on the legacy stream, and not
+    // while the caller is capturing this stream: then the launches go into their graph)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    bool graphs = s->stream != nullptr && K >= 2;
+    if (graphs && cudaStreamIsCapturing(s->stream, &cap) != cudaSuccess) graphs = false;
+    if (cap != cudaStreamCaptureStatusNone) graphs = false;
+    long i = 0;
+    while (i < nsteps) {
+        if (graphs && s->step % K == 0 && nsteps - i >= K) {
+            const int p = s->cur;
+            if (!s->graph_ok[p]) {
+                cudaError_t e = make_graph(s, p);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    graphs = false;
+                    continue;
+                }
+            }
+            cudaError_t e = cudaGraphLaunch(s->graph[p], s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "launching the step graph");
+            s->cur = p ^ (int)(K & 1);
+            s->step += K;
+            s->resid_step = s->step;
+            i += K;
+            continue;
         }
+        const long idx = s->step + 1;
+        cudaError_t e = enqueue_steps(s, idx, 1, s->cur);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the step kernels");
+        if (idx % K == 0) s->resid_step = idx;
         s->cur ^= 1;
         s->step = idx;
+        ++i;
     }
+    return LBM_OK;
+}
+
+namespace {
+
+lbm_status read_result(lbm_sim *s, double out[4])
+{
+    cudaError_t e = cudaMemcpyAsync(s->host_res, s->result, sizeof(double) * 4,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading a reduction result");
+    for (int k = 0; k < 4; ++k) out[k] = s->host_res[k];
+    if (out[3] != 0.0) return fail(LBM_ENONFINITE, "non-finite values met in a reduction");
+    return LBM_OK;
+}
+
+int nparts_for(const lbm_sim *s, int lanes)
+{
+    return grid_for(s->ncells, lanes) + wall_grid(lanes, s->args.n_wall_segs);
+}
+
+// FP64 defect of the FP32 state H: D = M64(H) - H (float); returns ||D||^2, ||M64(H)||^2.
+lbm_status defect_pass(lbm_sim *s, void *H, void *D, double *dsum, double *nsum)
+{
+    StepArgs a = s->args;
+    a.h = H;
+    a.hn = D;
+    const int g = defect_lanes(s->vs.m);
+    cudaError_t e = launch_defect_f32(s->vs.m, a, grid_for(s->ncells, g), s->stream);
+    if (e == cudaSuccess) e = launch_finalize_residual(s->partials, nparts_for(s, g), s->result, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the defect pass");
+    double r[4];
+    lbm_status st = read_result(s, r);
+    if (st != LBM_OK) return st;
+    *dsum = r[0];
+    *nsum = r[1];
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, lbm_solve_info *info)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (!(tol > 0) || max_steps < 0 || refine_sweeps < 0) return fail(LBM_EINVAL, "invalid solve arguments");
+    if (refine_sweeps > 0 && s->prob.prec != LBM_FP32_PERTURB)
+        return fail(LBM_EINVAL, "refinement sweeps apply to the FP32 precision only");
+    lbm_solve_info out{};
+    const long K = s->prob.residual_every;
+    // --- the march: whole residual intervals until r < tol ---
+    double r = INFINITY;
+    long taken = 0;
+    while (taken < max_steps) {
+        const long todo = K - (s->step % K);
+        lbm_status st = lbm_step(s, todo);
+        if (st != LBM_OK) return st;
+        taken += todo;
+        long rs;
+        st = lbm_residual(s, &r, &rs);
+        if (st != LBM_OK) return st;
+        if (r < tol) break;
+    }
+    out.steps = taken;
+    out.residual = r;
+    out.defect = r;
+    // --- FP32: mixed-precision refinement (defect in FP64, correction march in FP32) ---
+    if (refine_sweeps > 0) {
+        void *H = s->buf[s->cur];
+        void *D = s->buf[2];
+        double dsum, nsum;
+        lbm_status st = defect_pass(s, H, D, &dsum, &nsum);
+        if (st != LBM_OK) return st;
+        double r64 = nsum > 0 ? std::sqrt(dsum / nsum) : 0.0;
+        const double hnorm = std::sqrt(nsum);
+        const int g = correct_lanes(s->vs.m);
+        const int grid = grid_for(s->ncells, g), nparts = nparts_for(s, g);
+        const size_t state_bytes = (size_t)s->nv * s->ncells * sizeof(float);
+        for (int sw = 0; sw < refine_sweeps && r64 >= tol * 1e-2 && hnorm > 0; ++sw) {
+            // correction march delta <- L(delta) + D from delta = 0 (homogeneous walls)
+            void *C[2] = {s->buf[s->cur ^ 1], s->buf[3]};
+            int cc = 0;
+            cudaError_t e = cudaMemsetAsync(C[0], 0, state_bytes, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "clearing the correction");
+            StepArgs a = s->args;
+            a.src = D;
+            a.homogeneous = 1;
+            long k = 0;
+            while (k < max_steps) {
+                for (long j = 1; j <= K; ++j) {
+                    a.h = C[cc];
+                    a.hn = C[cc ^ 1];
+                    e = launch_correct_f32(s->vs.m, g, j == K, a, grid, s->stream);
+                    if (e == cudaSuccess && j == K) e = launch_finalize_residual(s->partials, nparts, s->result, s->stream);
+                    if (e != cudaSuccess) return cuda_fail(e, "launching the correction march");
+                    cc ^= 1;
+                }
+                k += K;
+                double rr[4];
+                st = read_result(s, rr);
+                if (st != LBM_OK) return st;
+                if (std::sqrt(rr[0]) < tol * hnorm) break;     // change per step relative to ||h||
+            }
+            out.correction_steps += k;
+            e = launch_add_f32((float *)H, (const float *)C[cc], (long)s->nv * s->ncells, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "applying the correction");
+            out.sweeps = sw + 1;
+            const double prev = r64;
+            st = defect_pass(s, H, D, &dsum, &nsum);
+            if (st != LBM_OK) return st;
+            r64 = nsum > 0 ? std::sqrt(dsum / nsum) : 0.0;
+            if (r64 > 0.5 * prev) break;      // at the FP32 rounding floor
+        }
+        out.defect = r64;
+    }
+    if (info) *info = out;
     return LBM_OK;
 }
 

@@ -74,6 +74,9 @@ bool step_supported(int prec, int m, int g);
 // Reductions and diagnostics (reduce.cu)
 cudaError_t launch_finalize_residual(const double *partials, int nparts, double *result,
                                      cudaStream_t s);
+// Sum `nparts` (d, n) pairs in a fixed order into out[0..1] (and r, flag when nres >= 4).
+cudaError_t launch_finalize_pairs(const double *partials, int nparts, double *out, int nres,
+                                  cudaStream_t s);
 cudaError_t launch_norms(const void *a, const void *b, long count, int prec, double *partials,
                          int nparts, double *out, cudaStream_t s);
 int norms_blocks(long count);
@@ -84,6 +87,7 @@ cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const
                              double *flux_x, double *wall_sums, cudaStream_t s);
 
 cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s);
+cudaError_t launch_add_f32(float *y, const float *x, long count, cudaStream_t s);
 cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s);
 
 // Host quadrature (quadrature.cpp)

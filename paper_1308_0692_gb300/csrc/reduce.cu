@@ -201,7 +201,19 @@ __global__ void widen_kernel(const float *src, double *dst, long count)
         dst[i] = (double)src[i];
 }
 
+__global__ void axpy_kernel(float *y, const float *x, long count)
+{
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) y[i] += x[i];
+}
+
 }  // namespace
+
+cudaError_t launch_add_f32(float *y, const float *x, long count, cudaStream_t s)
+{
+    axpy_kernel<<<152 * 8, 256, 0, s>>>(y, x, count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s)
 {
@@ -212,6 +224,13 @@ cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream
 cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s)
 {
     widen_kernel<<<152 * 8, 256, 0, s>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_pairs(const double *partials, int nparts, double *out, int nres,
+                                  cudaStream_t s)
+{
+    finalize_kernel<<<1, RED_BLOCK, 0, s>>>(partials, nparts, out, nres);
     return cudaGetLastError();
 }
 

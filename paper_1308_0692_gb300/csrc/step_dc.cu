@@ -8,30 +8,18 @@
 
 using namespace lbmk;
 
-cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, int *g_used, cudaStream_t s)
+cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s)
 {
-    if (m == 3) {
-        *g_used = 1;
-        return launch_one<float, double, 3, 1, false, false, true>(a, grid, s);
-    }
-    if (m == 4) {
-        *g_used = 1;
-        return launch_one<float, double, 4, 1, false, false, true>(a, grid, s);
-    }
-    if (m == 6) {
-        *g_used = 2;
-        return launch_one<float, double, 6, 2, false, false, true>(a, grid, s);
-    }
-    if (m == 8) {
-        *g_used = 4;
-        return launch_one<float, double, 8, 4, false, false, true>(a, grid, s);
-    }
-    if (m == 12) {
-        *g_used = 6;
-        return launch_one<float, double, 12, 6, false, false, true>(a, grid, s);
-    }
+    if (m == 3) return launch_one<float, double, 3, 1, false, false, true>(a, grid, s);
+    if (m == 4) return launch_one<float, double, 4, 1, false, false, true>(a, grid, s);
+    if (m == 6) return launch_one<float, double, 6, 2, false, false, true>(a, grid, s);
+    if (m == 8) return launch_one<float, double, 8, 4, false, false, true>(a, grid, s);
+    if (m == 12) return launch_one<float, double, 12, 6, false, false, true>(a, grid, s);
     return cudaErrorInvalidValue;
 }
+
+int defect_lanes(int m) { return m == 12 ? 6 : m == 8 ? 4 : m == 6 ? 2 : 1; }
+int correct_lanes(int m) { return m == 12 ? 4 : m == 8 ? 2 : 1; }
 
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s)
 {

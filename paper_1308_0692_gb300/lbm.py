@@ -34,6 +34,11 @@ class LBMError(RuntimeError):
         self.status = status
 
 
+class lbm_solve_info(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_long), ("correction_steps", ctypes.c_long), ("sweeps", ctypes.c_int),
+                ("residual", ctypes.c_double), ("defect", ctypes.c_double)]
+
+
 class lbm_problem(ctypes.Structure):
     _fields_ = [("geom", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("kn", ctypes.c_double), ("u_bottom", ctypes.c_double), ("u_top", ctypes.c_double),
@@ -65,6 +70,7 @@ def _load():
         "lbm_step": (st, [_vp, ctypes.c_long]),
         "lbm_residual": (st, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
         "lbm_set_variant": (st, [_vp, ctypes.c_int]),
+        "lbm_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.POINTER(lbm_solve_info)]),
         "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int)]),
         "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
@@ -73,6 +79,18 @@ def _load():
         "lbm_state_device": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_long)]),
         "lbm_norms_scratch_bytes": (st, [ctypes.c_long, ctypes.POINTER(ctypes.c_size_t)]),
         "lbm_norms": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp]),
+        "lbm_batch_bytes": (st, [_vp, ctypes.POINTER(lbm_problem), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+        "lbm_batch_init": (st, [_vp, ctypes.POINTER(lbm_problem), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
+                                ctypes.POINTER(_vp)]),
+        "lbm_batch_destroy": (None, [_vp]),
+        "lbm_batch_set_schedule": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "lbm_batch_get_schedule": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "lbm_batch_advance": (st, [_vp, ctypes.c_int, ctypes.c_double]),
+        "lbm_batch_set_timeout": (st, [_vp, ctypes.c_longlong]),
+        "lbm_batch_poll": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]),
+        "lbm_batch_status": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), _dp, ctypes.POINTER(ctypes.c_int)]),
+        "lbm_batch_get_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -200,6 +218,12 @@ def lbm_step(sim: Sim, nsteps: int):
     _check(_load().lbm_step(sim.handle, int(nsteps)))
 
 
+def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0) -> dict:
+    info = lbm_solve_info()
+    _check(_load().lbm_solve(sim.handle, float(tol), int(max_steps), int(refine_sweeps), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in lbm_solve_info._fields_}
+
+
 def lbm_set_variant(sim: Sim, lanes_per_cell: int):
     _check(_load().lbm_set_variant(sim.handle, int(lanes_per_cell)))
 
@@ -264,3 +288,88 @@ def lbm_norms(a_ptr: int, b_ptr: int | None, count: int, prec: int, scratch_ptr:
               scratch_bytes: int, out_ptr: int, stream=None):
     _check(_load().lbm_norms(a_ptr, b_ptr, int(count), prec, scratch_ptr, scratch_bytes, out_ptr,
                              _stream_handle(stream)))
+
+
+class Batch:
+    """Owner of an lbm_batch* and of its device buffer (if any)."""
+
+    def __init__(self, handle: int, probs, n_vel: int, keepalive=None):
+        self.handle = handle
+        self.probs = probs
+        self.n_vel = n_vel
+        self._keepalive = keepalive
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.lbm_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def _problem_array(probs):
+    arr = (lbm_problem * len(probs))()
+    for i, p in enumerate(probs):
+        arr[i] = p
+    return arr
+
+
+def lbm_batch_bytes(vs: VelocitySet, probs) -> int:
+    b = ctypes.c_size_t()
+    arr = _problem_array(probs)
+    _check(_load().lbm_batch_bytes(vs.handle, arr, len(probs), ctypes.byref(b)))
+    return b.value
+
+
+def lbm_batch_init(vs: VelocitySet, probs, device_buf=None, stream=None) -> Batch:
+    lib = _load()
+    arr = _problem_array(probs)
+    out = _vp()
+    buf_ptr, buf_bytes = None, 0
+    if device_buf is not None:
+        buf_ptr = device_buf.data_ptr()
+        buf_bytes = device_buf.numel() * device_buf.element_size()
+    _check(lib.lbm_batch_init(vs.handle, arr, len(probs), buf_ptr, buf_bytes, _stream_handle(stream),
+                              ctypes.byref(out)))
+    nv = ctypes.c_int()
+    _check(lib.lbm_vset_query(vs.handle, ctypes.byref(nv), None, None, None, None))
+    return Batch(out.value, list(probs), nv.value, keepalive=(device_buf, stream, vs))
+
+
+def lbm_batch_set_schedule(b: Batch, warps_per_segment: int, blocks_per_sm: int, order: int):
+    _check(_load().lbm_batch_set_schedule(b.handle, warps_per_segment, blocks_per_sm, order))
+
+
+def lbm_batch_get_schedule(b: Batch):
+    g, bp, o, gr = (ctypes.c_int() for _ in range(4))
+    _check(_load().lbm_batch_get_schedule(b.handle, ctypes.byref(g), ctypes.byref(bp), ctypes.byref(o),
+                                          ctypes.byref(gr)))
+    return {"warps_per_segment": g.value, "blocks_per_sm": bp.value, "order": o.value, "grid": gr.value}
+
+
+def lbm_batch_advance(b: Batch, nsteps: int, tol: float):
+    _check(_load().lbm_batch_advance(b.handle, int(nsteps), float(tol)))
+
+
+def lbm_batch_set_timeout(b: Batch, cycles: int):
+    _check(_load().lbm_batch_set_timeout(b.handle, int(cycles)))
+
+
+def lbm_batch_poll(b: Batch):
+    n, s = ctypes.c_int(), ctypes.c_long()
+    _check(_load().lbm_batch_poll(b.handle, ctypes.byref(n), ctypes.byref(s)))
+    return n.value, s.value
+
+
+def lbm_batch_status(b: Batch, i: int):
+    st, r, cv = ctypes.c_long(), ctypes.c_double(), ctypes.c_int()
+    _check(_load().lbm_batch_status(b.handle, int(i), ctypes.byref(st), ctypes.byref(r), ctypes.byref(cv)))
+    return {"steps": st.value, "residual": r.value, "converged": bool(cv.value)}
+
+
+def lbm_batch_get_state(b: Batch, i: int) -> np.ndarray:
+    p = b.probs[i]
+    h = np.empty((b.n_vel, p.nx * p.ny))
+    _check(_load().lbm_batch_get_state(b.handle, int(i), _ptr(h)))
+    return h

@@ -1,0 +1,113 @@
+"""Batched persistent sweep: every instance of a mixed batch against the FP64 oracle, the
+convergence bookkeeping, and the bounded-wait error path of the grid barrier."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.march import CAVITY, COUETTE, make_problem as oracle_problem
+from paper_1308_0692_gb300 import lbm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# per step the FP32 batch kernel differs from the FP64 oracle by single-precision rounding
+FP32_TOL_PER_STEP = 2e-6
+
+INSTANCES = [
+    # geom, nx, ny, kn, u_bottom, u_top
+    (COUETTE, 1, 64, 0.01, 0.01, -0.01),
+    (COUETTE, 1, 131, 0.5, 0.007, -0.007),
+    (COUETTE, 1, 97, 10.0, 0.02, -0.02),
+    (CAVITY, 33, 33, 0.1, 0.0, 0.01),
+    (CAVITY, 64, 64, 0.03, 0.0, 0.015),
+    (CAVITY, 40, 40, 2.0, 0.0, 0.005),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1308_0692_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _probs(residual_every=10):
+    return [lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP32_PERTURB, residual_every=residual_every)
+            for g, nx, ny, kn, ub, ut in INSTANCES]
+
+
+@pytest.mark.parametrize("schedule", [(4, 0, 0), (2, 0, 2), (1, 1, 1)])
+def test_batch_matches_oracle_per_instance(schedule):
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    b = lbm.lbm_batch_init(vs, _probs(), stream=torch.cuda.Stream())
+    lbm.lbm_batch_set_schedule(b, *schedule)
+    steps = 30
+    lbm.lbm_batch_advance(b, 13, 0.0)      # two launches, uneven split
+    lbm.lbm_batch_advance(b, steps - 13, 0.0)
+    n_active, step = lbm.lbm_batch_poll(b)
+    assert n_active == len(INSTANCES) and step == steps
+    for i, (g, nx, ny, kn, ub, ut) in enumerate(INSTANCES):
+        p = oracle_problem("half", 4, g, nx, ny, kn, ub, ut)
+        ref = p.step(p.zeros(), steps)
+        got = lbm.lbm_batch_get_state(b, i)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= FP32_TOL_PER_STEP * steps, (i, err)
+
+
+def test_batch_convergence_and_freezing():
+    """Instances converge at different step counts; each is frozen at the residual check that
+    first saw r < tol and its state stays put while the others march on."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    b = lbm.lbm_batch_init(vs, _probs(residual_every=50), stream=torch.cuda.Stream())
+    tol = 1e-6
+    for _ in range(400):
+        lbm.lbm_batch_advance(b, 500, tol)
+        n_active, step = lbm.lbm_batch_poll(b)
+        if n_active == 0:
+            break
+    assert n_active == 0
+    stats = [lbm.lbm_batch_status(b, i) for i in range(len(INSTANCES))]
+    assert all(s["converged"] and s["residual"] < tol for s in stats)
+    assert all(s["steps"] % 50 == 0 for s in stats)
+    assert len({s["steps"] for s in stats}) > 1            # they did converge at different times
+    # a frozen state does not move: one more launch leaves every state unchanged
+    before = [lbm.lbm_batch_get_state(b, i) for i in range(len(INSTANCES))]
+    lbm.lbm_batch_advance(b, 100, tol)
+    lbm.lbm_batch_poll(b)
+    for i in range(len(INSTANCES)):
+        np.testing.assert_array_equal(lbm.lbm_batch_get_state(b, i), before[i])
+    # the converged Couette state agrees with the single-simulation FP32 march of the same length
+    g, nx, ny, kn, ub, ut = INSTANCES[2]
+    sim = lbm.lbm_init(vs, lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP32_PERTURB, residual_every=50))
+    lbm.lbm_step(sim, stats[2]["steps"])
+    ref = lbm.lbm_get_state(sim)
+    assert np.abs(before[2] - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_batch_barrier_timeout_reports_error():
+    """A grid-barrier wait limit of a few cycles makes the waits give up: the kernel returns
+    and the next poll reports LBM_ETIMEOUT (no hang, the context stays usable)."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    b = lbm.lbm_batch_init(vs, _probs(), stream=torch.cuda.Stream())
+    lbm.lbm_batch_set_timeout(b, 1)
+    lbm.lbm_batch_advance(b, 50, 0.0)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_batch_poll(b)
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    # the device is still fine
+    x = torch.ones(10, device="cuda")
+    assert float(x.sum()) == 10.0
+
+
+def test_batch_rejects_mixed_or_unsupported():
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    probs = _probs()
+    probs[1].prec = lbm.LBM_FP64
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_batch_bytes(vs, probs)
+    assert e.value.status == lbm.LBM_EINVAL
+    vs6 = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_batch_bytes(vs6, _probs())
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
