@@ -132,7 +132,7 @@ typedef struct {
  * FP32 simulations may then apply refine_sweeps mixed-precision refinement sweeps: the
  * defect D = M(h) - h of the stored FP32 state under one FP64 step, a correction march
  * delta <- L(delta) + D of the homogeneous problem (walls without driving) in FP32 until
- * its per-step change is below tol * ||h||, and h += delta; sweeps stop early once the
+ * its per-step change is below 1e-2 * tol * ||h||, and h += delta; sweeps stop early once the
  * defect stops halving (FP32 rounding floor).  This removes the bias of the FP32 fixed
  * point (the FP32 operator's rounding amplified by the conditioning of the slow modes),
  * which plain FP32 storage cannot.  refine_sweeps must be 0 for FP64 simulations. */
@@ -140,12 +140,13 @@ lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps
                      lbm_solve_info *info);
 
 /* Kernel variant: the number of warps that share one 32-cell segment (1, 2, 3, 4 or 6
- * dividing M; each warp owns M/warps velocity rows).  It changes speed, not results
- * beyond rounding order.
+ * dividing M; each warp owns M/warps velocity rows), and prefetch (0/1): the bulk kernel
+ * issues all own-cell and y-neighbour loads of a warp before its arithmetic.  It changes
+ * speed, not results beyond rounding order.
  * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
  * without a compiled kernel.  Used by the autotuner.  Call between steps only. */
-lbm_status lbm_set_variant(lbm_sim *sim, int warps_per_segment);
-lbm_status lbm_get_variant(const lbm_sim *sim, int *warps_per_segment);
+lbm_status lbm_set_variant(lbm_sim *sim, int warps_per_segment, int prefetch);
+lbm_status lbm_get_variant(const lbm_sim *sim, int *warps_per_segment, int *prefetch);
 
 /* Latest relative residual r and the step count at which it was evaluated
  * (synchronises).  LBM_ENONFINITE if the state contains NaN/Inf. */
@@ -214,10 +215,51 @@ lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol);     /* async
  * 2 s).  Exposed so that tests can make a wait give up and check the error path. */
 lbm_status lbm_batch_set_timeout(lbm_batch *b, long long cycles);
 lbm_status lbm_batch_poll(lbm_batch *b, int *n_active, long *step);     /* synchronises */
+/* Back to the cold start (h = 0 everywhere, step 0, nothing converged). */
+lbm_status lbm_batch_reset(lbm_batch *b);
+/* Autotuner: times steps_per_trial steps of every schedule (warps per segment x blocks
+ * per SM x item order) on this batch, keeps the fastest and resets the batch to the cold
+ * start.  Outputs may be NULL. */
+lbm_status lbm_batch_tune(lbm_batch *b, int steps_per_trial, int *best_warps_per_segment,
+                          int *best_blocks_per_sm, int *best_order, double *best_ms_per_step);
 /* Instance i: steps taken (the step at which it converged, or all steps so far), last
  * residual, converged flag; its state as host FP64 [n][ny][nx]. */
 lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, int *converged);
 lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h);
+/* Moments of instance i (as lbm_moments) into device FP64 [6][ny][nx]: rho, ux, uy, pxx,
+ * pxy, pyy.  Stream-ordered. */
+lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev);
+
+/* ---- Learned warm start (not in the paper) ----
+ * A coordinate MLP 4 -> 256 -> 256 -> 256 -> 6 with exact-erf GELU maps the features
+ * (2x-1, 2y-1, (2 log10 Kn + 1)/3, (u_w - 0.0125)/0.0075) of a cavity cell to the
+ * normalised moments ((rho-1)/u_w, u_x/u_w, u_y/u_w, (P_xx-1)/u_w, P_xy/u_w, (P_yy-1)/u_w).
+ * BF16 weights and activations enter hand-written tensor-core GEMMs that accumulate in
+ * FP32; FP32 master weights are updated by Adam (beta 0.9/0.999, eps 1e-8).
+ * Parameters are flattened as W1 [256][4], b1 [256], W2 [256][256], b2, W3, b3,
+ * W4 [6][256], b4 [6] (row-major).  All x/t/y pointers are device FP32, row-major
+ * [M][4] / [M][6]; work is ordered on the MLP's stream. */
+typedef struct lbm_mlp lbm_mlp;
+lbm_status lbm_mlp_param_count(long *count);
+lbm_status lbm_mlp_create(int max_batch, unsigned long long seed, void *stream, lbm_mlp **out);
+void lbm_mlp_destroy(lbm_mlp *mlp);
+lbm_status lbm_mlp_set_params(lbm_mlp *mlp, const float *flat_host);   /* resets Adam */
+lbm_status lbm_mlp_get_params(lbm_mlp *mlp, float *flat_host);
+lbm_status lbm_mlp_forward(lbm_mlp *mlp, const float *x_dev, int m, float *y_dev);
+/* Mean-squared-error loss and its gradient (flattened like the parameters, host FP32;
+ * grad may be NULL) without updating; synchronises. */
+lbm_status lbm_mlp_loss_grad(lbm_mlp *mlp, const float *x_dev, const float *t_dev, int m, double *loss,
+                             float *grad_flat_host);
+/* One Adam step on a batch; loss (may be NULL) is the batch loss before the update. */
+lbm_status lbm_mlp_train_step(lbm_mlp *mlp, const float *x_dev, const float *t_dev, int m, float lr,
+                              double *loss);
+/* Features of every cell of an nx x ny cavity (device [nx*ny][4]). */
+lbm_status lbm_mlp_features(lbm_mlp *mlp, int nx, int ny, double kn, double u_w, float *x_dev);
+/* Replace the state of a cavity simulation by the second-order Hermite expansion of the
+ * moments the network predicts for (kn, u_w):
+ *   h_a = w_a [rho' + xi_a . j' + 1/2 sum_ij (P'_ij - rho' delta_ij)(xi_i xi_j - delta_ij)].
+ * The network's max_batch must cover nx*ny.  Synchronises. */
+lbm_status lbm_warm_start(lbm_sim *sim, lbm_mlp *mlp, double kn, double u_w);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *lbm_last_error(void);

@@ -296,6 +296,35 @@ __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS) batch_kernel(const Ba
     }
 }
 
+// six linearised moments of one instance (rho, ux, uy, pxx, pxy, pyy per cell), FP64
+template <typename T>
+__global__ void inst_moments_kernel(const T *h, long ncells, int m, const BatchArgs a, double u_ref, double *out)
+{
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
+        double s0 = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
+        for (int iy = 0; iy < m; ++iy) {
+            const double ey = a.xi[iy];
+            for (int ix = 0; ix < m; ++ix) {
+                const double ex = a.xi[ix];
+                const double v = (double)h[(long)(iy * m + ix) * ncells + c];
+                s0 += v;
+                sx += ex * v;
+                sy += ey * v;
+                sxx += ex * ex * v;
+                sxy += ex * ey * v;
+                syy += ey * ey * v;
+            }
+        }
+        const double rho = 1.0 + u_ref * s0;
+        out[c] = rho;
+        out[ncells + c] = u_ref * sx / rho;
+        out[2 * ncells + c] = u_ref * sy / rho;
+        out[3 * ncells + c] = 1.0 + u_ref * sxx;
+        out[4 * ncells + c] = u_ref * sxy;
+        out[5 * ncells + c] = 1.0 + u_ref * syy;
+    }
+}
+
 template <typename TS, typename TC, int M, int G>
 void *kernel_ptr() { return (void *)batch_kernel<TS, TC, M, G>; }
 
@@ -735,6 +764,78 @@ lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol)
     return LBM_OK;
 }
 
+lbm_status lbm_batch_reset(lbm_batch *b)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    const int n = (int)b->inst.size();
+    const size_t es = b->prec == LBM_FP64 ? 8 : 4;
+    std::vector<long> frozen(n, LONG_MAX);
+    std::vector<double> last(n, INFINITY);
+    cudaError_t e = cudaMemsetAsync(b->buf[0], 0, b->total_vals * es, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[1], 0, b->total_vals * es, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_acc, 0, sizeof(double) * 2 * n, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_last_r, last.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_frozen, frozen.data(), sizeof(long) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 64, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("resetting the batch: ") + cudaGetErrorString(e));
+    b->step = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch *b, int steps_per_trial, int *best_g, int *best_bpsm, int *best_order,
+                          double *best_ms_per_step)
+{
+    if (!b || steps_per_trial < 1) return bfail(LBM_EINVAL, "invalid tuning arguments");
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+        return bfail(LBM_ECUDA, "creating timing events");
+    double best = INFINITY;
+    int bg = b->g, bb = b->blocks_per_sm, bo = b->order;
+    for (const auto &v : variants()) {
+        if (v.prec != b->prec || v.m != b->m) continue;
+        int maxb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, v.fn, v.threads, 0) != cudaSuccess) continue;
+        for (int bpsm = 1; bpsm <= maxb; ++bpsm) {
+            for (int order = 0; order <= 2; ++order) {
+                if (apply_schedule(b, v.g, bpsm, order) != LBM_OK) continue;
+                lbm_status st = lbm_batch_advance(b, 2, 0.0);      // warm-up (and graph capture)
+                if (st != LBM_OK) continue;
+                cudaEventRecord(t0, b->stream);
+                st = lbm_batch_advance(b, steps_per_trial, 0.0);
+                cudaEventRecord(t1, b->stream);
+                if (st != LBM_OK || cudaEventSynchronize(t1) != cudaSuccess) continue;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, t0, t1);
+                int n_active;
+                long step;
+                if (lbm_batch_poll(b, &n_active, &step) != LBM_OK) {
+                    cudaEventDestroy(t0);
+                    cudaEventDestroy(t1);
+                    return LBM_ETIMEOUT;
+                }
+                const double per = ms / steps_per_trial;
+                if (per < best) {
+                    best = per;
+                    bg = v.g;
+                    bb = bpsm;
+                    bo = order;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    lbm_status st = apply_schedule(b, bg, bb, bo);
+    if (st == LBM_OK) st = lbm_batch_reset(b);
+    if (st != LBM_OK) return st;
+    if (best_g) *best_g = bg;
+    if (best_bpsm) *best_bpsm = bb;
+    if (best_order) *best_order = bo;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_poll(lbm_batch *b, int *n_active, long *step)
 {
     if (!b) return bfail(LBM_EINVAL, "batch is NULL");
@@ -768,6 +869,22 @@ lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, 
     if (residual) *residual = r;
     if (converged) *converged = f != LONG_MAX;
     return LBM_OK;
+}
+
+lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev)
+{
+    if (!b || !out_dev) return bfail(LBM_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
+    long steps;
+    lbm_status st = lbm_batch_status(b, i, &steps, nullptr, nullptr);
+    if (st != LBM_OK) return st;
+    const BatchArgs a = make_args(b, 1, 0.0);
+    const BatchInst &I = b->inst[i];
+    const int nb = (int)std::min<long>(1216, (I.ncells + 255) / 256);
+    const float *h = (const float *)b->buf[steps & 1] + I.off;
+    inst_moments_kernel<float><<<nb, 256, 0, b->stream>>>(h, I.ncells, b->m, a, 1.0 / I.inv_u_ref, out_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("instance moments: ") + cudaGetErrorString(e));
 }
 
 lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h)

@@ -16,10 +16,10 @@
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
 
-cudaError_t launch_step_f64_small(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_step_f64_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_step_f32_small(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_step_f32_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f64_small(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f64_large(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_small(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_large(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s);
 int defect_lanes(int m);
 int correct_lanes(int m);
@@ -41,7 +41,8 @@ struct lbm_sim {
     long ncells;
     double dt, dx, dy, omega, u_ref;
     cudaStream_t stream;
-    int lanes;            // lanes per cell of the step kernel
+    int lanes;            // warps per 32-cell segment of the step kernel
+    int prefetch;         // bulk variant issuing loads ahead of use
     int grid;             // blocks of the bulk step kernel
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
     int *wall_segs;       // device list of wall segments for the current lanes
@@ -221,7 +222,10 @@ void fill_tables(lbm_sim *s, std::vector<double> &t64, std::vector<float> &t32, 
     t32.resize(t64.size());
     for (size_t i = 0; i < t64.size(); ++i) t32[i] = (float)t64[i];
     std::memset(&hdr, 0, sizeof hdr);
-    for (int i = 0; i < m; ++i) hdr.xi1[i] = v.nodes[i];
+    for (int i = 0; i < m; ++i) {
+        hdr.xi1[i] = v.nodes[i];
+        hdr.w1[i] = v.weights[i];
+    }
     hdr.b = 1.0 - s->omega;
     hdr.inv_dx_wall = 1.0 / dxw;
     hdr.inv_dy_wall = 1.0 / dyw;
@@ -303,7 +307,7 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur)
         const bool resid = idx % s->prob.residual_every == 0;
         a.h = s->buf[cur];
         a.hn = s->buf[cur ^ 1];
-        cudaError_t e = launch_step(s->prob.prec, s->vs.m, s->lanes, resid, a, s->grid, s->stream);
+        cudaError_t e = launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, s->stream);
         if (e != cudaSuccess) return e;
         if (resid) {
             e = launch_finalize_residual(s->partials, s->nparts_step, s->result, s->stream);
@@ -375,26 +379,26 @@ int default_lanes_per_cell(int prec, int m)
     return m <= 6 ? 1 : (m == 8 ? 2 : 4);
 }
 
-bool step_supported(int prec, int m, int g)
+bool step_supported(int prec, int m, int g, int pf)
 {
-    static const int f64[][2] = {{3, 1}, {4, 1}, {4, 2}, {6, 1}, {6, 2}, {8, 2}, {8, 4}, {12, 3}, {12, 4}, {12, 6}};
-    static const int f32[][2] = {{3, 1}, {4, 1}, {6, 1}, {6, 2}, {8, 1}, {8, 2}, {8, 4}, {12, 2}, {12, 3}, {12, 4}, {12, 6}};
+    static const int f64[][3] = {{3, 1, 0}, {4, 1, 0}, {4, 2, 0}, {6, 1, 0}, {6, 2, 0}, {4, 2, 1}, {6, 2, 1}, {8, 2, 0}, {8, 4, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {8, 4, 1}, {12, 6, 1}};
+    static const int f32[][3] = {{3, 1, 0}, {4, 1, 0}, {6, 1, 0}, {6, 2, 0}, {8, 1, 0}, {8, 2, 0}, {8, 4, 0}, {8, 2, 1}, {8, 4, 1}, {12, 2, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {12, 3, 1}, {12, 4, 1}, {12, 6, 1}};
     if (prec == LBM_FP64) {
-        for (auto &v : f64) if (v[0] == m && v[1] == g) return true;
+        for (auto &v : f64) if (v[0] == m && v[1] == g && v[2] == pf) return true;
     } else {
-        for (auto &v : f32) if (v[0] == m && v[1] == g) return true;
+        for (auto &v : f32) if (v[0] == m && v[1] == g && v[2] == pf) return true;
     }
     return false;
 }
 
-cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
+cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s)
 {
     if (prec == LBM_FP64)
-        return m >= 8 ? launch_step_f64_large(m, g, resid, a, grid, s)
-                      : launch_step_f64_small(m, g, resid, a, grid, s);
-    return m >= 12 ? launch_step_f32_large(m, g, resid, a, grid, s)
-                   : launch_step_f32_small(m, g, resid, a, grid, s);
+        return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
+                      : launch_step_f64_small(m, g, pf, resid, a, grid, s);
+    return m >= 12 ? launch_step_f32_large(m, g, pf, resid, a, grid, s)
+                   : launch_step_f32_small(m, g, pf, resid, a, grid, s);
 }
 
 extern "C" {
@@ -475,6 +479,7 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->ncells = (long)prob->nx * prob->ny;
     s->stream = (cudaStream_t)stream;
     s->lanes = default_lanes_per_cell(prob->prec, vs->m);
+    s->prefetch = 0;
     s->step = 0;
     s->resid_step = -1;
     s->cur = 0;
@@ -701,7 +706,9 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
                 double rr[4];
                 st = read_result(s, rr);
                 if (st != LBM_OK) return st;
-                if (std::sqrt(rr[0]) < tol * hnorm) break;     // change per step relative to ||h||
+                // change per step relative to ||h||, 100x below tol: the correction's own error
+                // is its per-step change times the conditioning of the slow modes (~1e3)
+                if (std::sqrt(rr[0]) < 1e-2 * tol * hnorm) break;
             }
             out.correction_steps += k;
             e = launch_add_f32((float *)H, (const float *)C[cc], (long)s->nv * s->ncells, s->stream);
@@ -719,18 +726,36 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
     return LBM_OK;
 }
 
-lbm_status lbm_set_variant(lbm_sim *s, int lanes_per_cell)
+lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 {
-    if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (!step_supported(s->prob.prec, s->vs.m, lanes_per_cell))
-        return fail(LBM_EUNSUPPORTED, "no step kernel with %d lanes per cell for M = %d", lanes_per_cell, s->vs.m);
-    return set_lanes(s, lanes_per_cell);
+    if (!s || !mlp) return fail(LBM_EINVAL, "NULL argument");
+    if (s->prob.geom != LBM_CAVITY) return fail(LBM_EINVAL, "the warm-start network is trained on cavities");
+    float *feat = (float *)s->moments;                  // scratch: 16 B + 24 B per cell <= 48 B
+    float *pred = feat + 4 * s->ncells;
+    lbm_status st = lbm_mlp_features(mlp, s->prob.nx, s->prob.ny, kn, u_w, feat);
+    if (st == LBM_OK) st = lbm_mlp_forward(mlp, feat, (int)s->ncells, pred);
+    if (st != LBM_OK) return st;
+    cudaError_t e = launch_warm_state(pred, s->ncells, s->vs.m, s->hdr->xi1, s->hdr->w1, u_w / s->u_ref,
+                                      s->buf[s->cur], s->prob.prec, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the warm-start state");
 }
 
-lbm_status lbm_get_variant(const lbm_sim *s, int *lanes_per_cell)
+lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
-    if (!s || !lanes_per_cell) return fail(LBM_EINVAL, "NULL argument");
-    *lanes_per_cell = s->lanes;
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch ? 1 : 0))
+        return fail(LBM_EUNSUPPORTED, "no step kernel with %d warps per segment (prefetch %d) for M = %d",
+                    warps_per_segment, prefetch ? 1 : 0, s->vs.m);
+    s->prefetch = prefetch ? 1 : 0;
+    return set_lanes(s, warps_per_segment);
+}
+
+lbm_status lbm_get_variant(const lbm_sim *s, int *warps_per_segment, int *prefetch)
+{
+    if (!s) return fail(LBM_EINVAL, "NULL argument");
+    if (warps_per_segment) *warps_per_segment = s->lanes;
+    if (prefetch) *prefetch = s->prefetch;
     return LBM_OK;
 }
 

@@ -27,6 +27,7 @@ enum {
 
 struct TableHeader {
     double xi1[LBM_MAX_M];   // 1-D nodes (ascending)
+    double w1[LBM_MAX_M];    // 1-D weights
     double b;                // 1 - omega
     double inv_dx_wall;      // 1 / sum_{xi_x>0} xi_x w  (side walls)
     double inv_dy_wall;      // 1 / sum_{xi_y>0} xi_y w  (bottom / top walls)
@@ -63,13 +64,13 @@ struct StepArgs {
 // Launchers (step_*.cu).  `g` selects the warps per 32-cell segment; a launch is the
 // bulk kernel over `grid` blocks followed by the wall kernel over the wall segments; the
 // residual partials of one step occupy grid + wall_grid(g, n_wall_segs) slots.
-cudaError_t launch_step(int prec, int m, int g, bool resid, const StepArgs &a, int grid,
+cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s);
 cudaError_t launch_defect(int m, const StepArgs &a, int grid, cudaStream_t s);
 int default_lanes_per_cell(int prec, int m);
 inline int segs_per_block(int g) { return g >= 8 ? 1 : 8 / g; }
 inline int wall_grid(int g, int n_wall_segs) { return (n_wall_segs + segs_per_block(g) - 1) / segs_per_block(g); }
-bool step_supported(int prec, int m, int g);
+bool step_supported(int prec, int m, int g, int pf);
 
 // Reductions and diagnostics (reduce.cu)
 cudaError_t launch_finalize_residual(const double *partials, int nparts, double *result,
@@ -89,6 +90,10 @@ cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const
 cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s);
 cudaError_t launch_add_f32(float *y, const float *x, long count, cudaStream_t s);
 cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s);
+
+// warm start (mlp.cu): h from normalised predicted moments [ncells][6]
+cudaError_t launch_warm_state(const float *pred, long ncells, int m, const double *xi1, const double *w1,
+                              double uw_over_uref, void *h, int prec, cudaStream_t s);
 
 // Host quadrature (quadrature.cpp)
 bool lbm_rule_1d(int kind, int n, std::vector<double> &nodes, std::vector<double> &weights);

@@ -1,0 +1,653 @@
+// Learned warm start: a coordinate MLP 4 -> 256 -> 256 -> 256 -> 6 (exact-erf GELU) that
+// maps (x, y, log Kn, u_w) to the six normalised moments of the steady state, trained
+// and evaluated with this file's kernels: a BF16 tensor-core GEMM with FP32 accumulation
+// (mma.sync m16n8k16, operands staged in shared memory by cp.async and read with
+// ldmatrix), elementwise GELU / GELU' / loss kernels, bias-gradient reductions and Adam
+// on FP32 master weights.  The warm-start kernel then builds the initial distribution
+// from the predicted moments by the second-order Hermite expansion
+//   h_a = w_a [rho' + xi_a . j' + 1/2 sum_ij (P'_ij - rho' delta_ij)(xi_i xi_j - delta_ij)].
+// The paper has no learned component; this follows the warm-start configuration of
+// the project's workloads.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+lbm_status lbm_norms_fail(lbm_status s, const char *msg);
+
+namespace {
+
+constexpr int NL = 4;                          // layers
+constexpr int WIDTH[NL + 1] = {4, 256, 256, 256, 6};
+constexpr int PADW[NL + 1] = {8, 256, 256, 256, 8};   // row lengths padded to 16 bytes
+
+// ------------------------------------------------------------------ GEMM (NT)
+// C[M][N] (fp32, ldc) = A[M][K] (bf16, lda) * B[N][K]^T (bf16, ldb) (+ bias[N]).
+// K must be a multiple of 8 and lda, ldb multiples of 8 (16-byte rows).
+constexpr int BM = 128, BN = 128, BK = 32, SROW = BK + 8;   // padded smem row (80 bytes)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred)
+{
+    const int n = pred ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(n));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) gemm_nt_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                     const __nv_bfloat16 *__restrict__ B, int ldb,
+                                                     float *__restrict__ C, int ldc, const float *__restrict__ bias,
+                                                     int M, int N, int K)
+{
+    __shared__ __align__(16) __nv_bfloat16 sA[2][BM][SROW];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][BN][SROW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;     // warp tile: rows wm*64.., cols wn*32..
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    auto load_stage = [&](int st, int k0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int chunk = tid + i * 256;          // 512 chunks of 16 bytes per operand
+            const int r = chunk >> 2, cc = (chunk & 3) * 8;
+            const int gm = m0 + r, gk = k0 + cc;
+            const bool pa = gm < M && gk < K;
+            cp_async16(&sA[st][r][cc], pa ? (const void *)(A + (long)gm * lda + gk) : (const void *)A, pa);
+            const int gn = n0 + r;
+            const bool pb = gn < N && gk < K;
+            cp_async16(&sB[st][r][cc], pb ? (const void *)(B + (long)gn * ldb + gk) : (const void *)B, pb);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    const int ktiles = (K + BK - 1) / BK;
+    load_stage(0, 0);
+    for (int kt = 0; kt < ktiles; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < ktiles) {
+            load_stage(st ^ 1, (kt + 1) * BK);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned af[4][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = wm * 64 + i * 16 + (lane & 15);
+                const int col = kk + (lane >> 4) * 8;
+                ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3], &sA[st][row][col]);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int nrow = wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3);
+                const int col = kk + ((lane >> 3) & 1) * 8;
+                unsigned r0, r1, r2, r3;
+                ldsm_x4(r0, r1, r2, r3, &sB[st][nrow][col]);
+                bfr[2 * j][0] = r0;
+                bfr[2 * j][1] = r1;
+                bfr[2 * j + 1][0] = r2;
+                bfr[2 * j + 1][1] = r3;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
+        }
+        __syncthreads();
+    }
+    // epilogue: thread holds (row lane/4, cols 2*(lane%4)+{0,1}) and row + 8 of each tile
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = n0 + wn * 32 + j * 8 + (lane & 3) * 2;
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const int row = m0 + wm * 64 + i * 16 + (lane >> 2) + hf * 8;
+                if (row >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (col + e >= N) continue;
+                    float v = acc[i][j][hf * 2 + e];
+                    if (bias) v += bias[col + e];
+                    C[(long)row * ldc + col + e] = v;
+                }
+            }
+        }
+    }
+}
+
+cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc,
+                    const float *bias, int M, int N, int K, cudaStream_t s)
+{
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    gemm_nt_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, bias, M, N, K);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ elementwise kernels
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z)
+{
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// dst[r][c] (bf16, ld = ldd) = src[r][c] (fp32, ld = lds) for c < cols, 0 for cols <= c < ldd
+__global__ void to_bf16_kernel(const float *src, int lds, __nv_bfloat16 *dst, int ldd, int rows, int cols)
+{
+    const long n = (long)rows * ldd;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ldd), c = (int)(i - (long)r * ldd);
+        dst[i] = __float2bfloat16_rn(c < cols ? src[(long)r * lds + c] : 0.f);
+    }
+}
+
+// a = bf16(GELU(z)) for a [rows][cols] block (z ld = cols, a ld = lda, padding zeroed)
+__global__ void gelu_fwd_kernel(const float *z, __nv_bfloat16 *a, int lda, int rows, int cols)
+{
+    const long n = (long)rows * lda;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / lda), c = (int)(i - (long)r * lda);
+        a[i] = __float2bfloat16_rn(c < cols ? gelu_f(z[(long)r * cols + c]) : 0.f);
+    }
+}
+
+// g = bf16(da * GELU'(z))
+__global__ void gelu_bwd_kernel(const float *da, const float *z, __nv_bfloat16 *g, float *g32, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float v = da[i] * gelu_grad_f(z[i]);
+        g32[i] = v;
+        g[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// output-layer gradient g = 2 (y - t) / (M * nout) (fp32 and bf16 padded to ldg), and
+// per-block partial sums of (y - t)^2
+__global__ void loss_grad_kernel(const float *y, const float *t, int M, int nout, float *g32,
+                                 __nv_bfloat16 *g16, int ldg, double *partials)
+{
+    __shared__ double s[8];
+    double acc = 0.0;
+    const float scale = 2.0f / ((float)M * (float)nout);
+    const long n = (long)M * ldg;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ldg), c = (int)(i - (long)r * ldg);
+        float gv = 0.f;
+        if (c < nout) {
+            const float d = y[(long)r * nout + c] - t[(long)r * nout + c];
+            acc += (double)d * d;
+            gv = scale * d;
+            g32[(long)r * nout + c] = gv;
+        }
+        g16[i] = __float2bfloat16_rn(gv);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += s[w];
+        partials[blockIdx.x] = tot;
+    }
+}
+
+// dst[c][r] = src[r][c] (bf16), src [rows][ld_src] -> dst [cols][ld_dst] (padding zeroed)
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *src, int lds, __nv_bfloat16 *dst, int ldd, int rows,
+                                      int cols, int dst_rows)
+{
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;   // bx over src cols, by over src rows
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = by + j, c = bx + threadIdx.x;
+        tile[j][threadIdx.x] = (r < rows && c < cols) ? src[(long)r * lds + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = bx + j, r = by + threadIdx.x;   // dst row c, dst col r
+        if (c < dst_rows && r < ldd) dst[(long)c * ldd + r] = tile[threadIdx.x][j];
+    }
+}
+
+// db[c] = sum_r g[r][c] (fp32, fixed order per column)
+__global__ void colsum_kernel(const float *g, int rows, int cols, float *db)
+{
+    __shared__ float s[256];
+    const int c = blockIdx.x;
+    float acc = 0.f;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) acc += g[(long)r * cols + c];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] = s[0];
+}
+
+// Adam on FP32 master weights; refreshes the bf16 copy (ld = ldq, row length k)
+__global__ void adam_kernel(float *p, const float *gr, float *m, float *v, long n, int k, __nv_bfloat16 *q,
+                            int ldq, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float g = gr[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (q) {
+            const int r = (int)(i / k), c = (int)(i - (long)r * k);
+            q[(long)r * ldq + c] = __float2bfloat16_rn(pi);
+        }
+    }
+}
+
+// features of cell c of an nx x ny cavity: (2x-1, 2y-1, (2 log10 Kn + 1)/3, (u_w - 0.0125)/0.0075)
+__global__ void features_kernel(int nx, int ny, float f2, float f3, float *x)
+{
+    const long n = (long)nx * ny;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+        const int yy = (int)(c / nx), xx = (int)(c - (long)yy * nx);
+        x[c * 4 + 0] = 2.f * ((xx + 0.5f) / nx) - 1.f;
+        x[c * 4 + 1] = 2.f * ((yy + 0.5f) / ny) - 1.f;
+        x[c * 4 + 2] = f2;
+        x[c * 4 + 3] = f3;
+    }
+}
+
+// second-order Hermite reconstruction from normalised predicted moments
+// pred[c][0..5] = ((rho-1)/u_w, u_x/u_w, u_y/u_w, (P_xx-1)/u_w, P_xy/u_w, (P_yy-1)/u_w)
+template <typename T>
+__global__ void warm_state_kernel(const float *pred, long ncells, int m, const double *xi1, const double *w1,
+                                  double uw_over_uref, T *h)
+{
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
+        const double s = uw_over_uref;
+        const double rp = s * pred[c * 6 + 0];
+        const double jx = s * pred[c * 6 + 1];   // rho u / u_ref, linearised rho = 1
+        const double jy = s * pred[c * 6 + 2];
+        const double pxx = s * pred[c * 6 + 3], pxy = s * pred[c * 6 + 4], pyy = s * pred[c * 6 + 5];
+        for (int iy = 0; iy < m; ++iy) {
+            const double ey = xi1[iy];
+            for (int ix = 0; ix < m; ++ix) {
+                const double ex = xi1[ix];
+                const double v = w1[ix] * w1[iy] *
+                                 (rp + ex * jx + ey * jy +
+                                  0.5 * ((pxx - rp) * (ex * ex - 1.0) + 2.0 * pxy * ex * ey + (pyy - rp) * (ey * ey - 1.0)));
+                h[(long)(iy * m + ix) * ncells + c] = (T)v;
+            }
+        }
+    }
+}
+
+lbm_status mfail(lbm_status s, const std::string &m) { return lbm_norms_fail(s, m.c_str()); }
+
+}  // namespace
+
+struct lbm_mlp {
+    int max_batch;
+    cudaStream_t stream;
+    void *base;
+    // parameters (FP32 master, bf16 copies, Adam moments) and gradients, per layer
+    float *W[NL], *b[NL], *gW[NL], *gb[NL], *mW[NL], *vW[NL], *mb[NL], *vb[NL];
+    __nv_bfloat16 *Wq[NL];    // [N][PADW[l]]
+    __nv_bfloat16 *WqT[NL];   // [K][PADW[l+1]] (transposed copy for the input gradient)
+    // activations for max_batch rows
+    float *x32;               // staging of inputs
+    __nv_bfloat16 *a[NL];     // layer inputs, bf16 [M][PADW[l]]
+    float *z[NL];             // pre-activations [M][WIDTH[l+1]]
+    float *g32;               // gradient w.r.t. z of the current layer [M][256]
+    __nv_bfloat16 *g16;       // same, bf16 [M][256 or 8 padded]
+    float *da;                // gradient w.r.t. a [M][256]
+    __nv_bfloat16 *gT;        // transposed g [256][M]
+    __nv_bfloat16 *aT;        // transposed a [256][M]
+    double *loss_part;
+    double *host_loss;
+    long step;
+};
+
+namespace {
+
+size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// layout of all device arrays of one MLP; returns total bytes, fills pointers if base != nullptr
+size_t mlp_layout(lbm_mlp *p, char *base, int M)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *r = base ? base + off : nullptr;
+        off = al(off + bytes);
+        return r;
+    };
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)WIDTH[l + 1] * WIDTH[l], nb = WIDTH[l + 1];
+        float *W = (float *)take(4 * nw), *b = (float *)take(4 * nb), *gW = (float *)take(4 * nw), *gb = (float *)take(4 * nb);
+        float *mW = (float *)take(4 * nw), *vW = (float *)take(4 * nw), *mb = (float *)take(4 * nb), *vb = (float *)take(4 * nb);
+        __nv_bfloat16 *Wq = (__nv_bfloat16 *)take(2 * (size_t)WIDTH[l + 1] * PADW[l]);
+        __nv_bfloat16 *WqT = (__nv_bfloat16 *)take(2 * (size_t)WIDTH[l] * PADW[l + 1]);
+        __nv_bfloat16 *a = (__nv_bfloat16 *)take(2 * (size_t)M * PADW[l]);
+        float *z = (float *)take(4 * (size_t)M * WIDTH[l + 1]);
+        if (p) {
+            p->W[l] = W; p->b[l] = b; p->gW[l] = gW; p->gb[l] = gb;
+            p->mW[l] = mW; p->vW[l] = vW; p->mb[l] = mb; p->vb[l] = vb;
+            p->Wq[l] = Wq; p->WqT[l] = WqT; p->a[l] = a; p->z[l] = z;
+        }
+    }
+    float *x32 = (float *)take(4 * (size_t)M * 4);
+    float *g32 = (float *)take(4 * (size_t)M * 256);
+    __nv_bfloat16 *g16 = (__nv_bfloat16 *)take(2 * (size_t)M * 256);
+    float *da = (float *)take(4 * (size_t)M * 256);
+    __nv_bfloat16 *gT = (__nv_bfloat16 *)take(2 * (size_t)256 * (M + 8));
+    __nv_bfloat16 *aT = (__nv_bfloat16 *)take(2 * (size_t)256 * (M + 8));
+    double *lp = (double *)take(8 * 1216);
+    if (p) {
+        p->x32 = x32; p->g32 = g32; p->g16 = g16; p->da = da; p->gT = gT; p->aT = aT; p->loss_part = lp;
+    }
+    return off;
+}
+
+int blocks_for(long n) { long b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b)); }
+
+cudaError_t refresh_bf16(lbm_mlp *p, int l)
+{
+    cudaError_t e = cudaSuccess;
+    to_bf16_kernel<<<blocks_for((long)WIDTH[l + 1] * PADW[l]), 256, 0, p->stream>>>(p->W[l], WIDTH[l], p->Wq[l], PADW[l],
+                                                                                   WIDTH[l + 1], WIDTH[l]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 tg((PADW[l] + 31) / 32, (WIDTH[l + 1] + 31) / 32);
+    // WqT [K][PADW[l+1]] = Wq^T; rows of WqT = K = WIDTH[l]
+    transpose_bf16_kernel<<<tg, dim3(32, 8), 0, p->stream>>>(p->Wq[l], PADW[l], p->WqT[l], PADW[l + 1], WIDTH[l + 1],
+                                                            PADW[l], WIDTH[l]);
+    return cudaGetLastError();
+}
+
+// forward pass on M rows already staged in p->x32; leaves y in p->z[NL-1] [M][6]
+cudaError_t forward(lbm_mlp *p, int M)
+{
+    cudaStream_t s = p->stream;
+    to_bf16_kernel<<<blocks_for((long)M * PADW[0]), 256, 0, s>>>(p->x32, 4, p->a[0], PADW[0], M, 4);
+    cudaError_t e = cudaGetLastError();
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        e = gemm_nt(p->a[l], PADW[l], p->Wq[l], PADW[l], p->z[l], WIDTH[l + 1], p->b[l], M, WIDTH[l + 1], PADW[l], s);
+        if (e == cudaSuccess && l + 1 < NL) {
+            gelu_fwd_kernel<<<blocks_for((long)M * PADW[l + 1]), 256, 0, s>>>(p->z[l], p->a[l + 1], PADW[l + 1], M,
+                                                                            WIDTH[l + 1]);
+            e = cudaGetLastError();
+        }
+    }
+    return e;
+}
+
+// backward pass after forward(); targets t [M][6] on device; fills gW, gb and loss partials
+cudaError_t backward(lbm_mlp *p, const float *t, int M, int *nparts)
+{
+    cudaStream_t s = p->stream;
+    const int nb = blocks_for((long)M * PADW[NL]);
+    loss_grad_kernel<<<nb, 256, 0, s>>>(p->z[NL - 1], t, M, WIDTH[NL], p->g32, p->g16, PADW[NL], p->loss_part);
+    *nparts = nb;
+    cudaError_t e = cudaGetLastError();
+    int ldg = PADW[NL];            // row length of the bf16 gradient g16
+    int ng = WIDTH[NL];            // columns of the fp32 gradient g32
+    for (int l = NL - 1; l >= 0 && e == cudaSuccess; --l) {
+        // gW[l] [N][K] = g^T a_l : A = g^T [N][M], B = a_l^T [K][M]
+        const int Mp = ((M + 7) / 8) * 8;
+        dim3 tg1((ldg + 31) / 32, (M + 31) / 32);
+        transpose_bf16_kernel<<<tg1, dim3(32, 8), 0, s>>>(p->g16, ldg, p->gT, Mp, M, ldg, WIDTH[l + 1]);
+        dim3 tg2((PADW[l] + 31) / 32, (M + 31) / 32);
+        transpose_bf16_kernel<<<tg2, dim3(32, 8), 0, s>>>(p->a[l], PADW[l], p->aT, Mp, M, PADW[l], WIDTH[l]);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = gemm_nt(p->gT, Mp, p->aT, Mp, p->gW[l], WIDTH[l], nullptr, WIDTH[l + 1], WIDTH[l], Mp, s);
+        if (e == cudaSuccess) {
+            colsum_kernel<<<WIDTH[l + 1], 256, 0, s>>>(p->g32, M, ng, p->gb[l]);
+            e = cudaGetLastError();
+        }
+        if (l == 0 || e != cudaSuccess) break;
+        // da [M][K] = g W : A = g [M][N] (bf16 ld ldg), B = W^T [K][N] (WqT, ld PADW[l+1])
+        e = gemm_nt(p->g16, ldg, p->WqT[l], PADW[l + 1], p->da, WIDTH[l], nullptr, M, WIDTH[l], ldg, s);
+        if (e == cudaSuccess) {
+            const long n = (long)M * WIDTH[l];
+            gelu_bwd_kernel<<<blocks_for(n), 256, 0, s>>>(p->da, p->z[l - 1], p->g16, p->g32, n);
+            e = cudaGetLastError();
+        }
+        ldg = WIDTH[l];
+        ng = WIDTH[l];
+    }
+    return e;
+}
+
+// splitmix64-based uniform numbers for the default initialisation
+double u01(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_mlp_param_count(long *count)
+{
+    if (!count) return mfail(LBM_EINVAL, "count is NULL");
+    long n = 0;
+    for (int l = 0; l < NL; ++l) n += (long)WIDTH[l + 1] * WIDTH[l] + WIDTH[l + 1];
+    *count = n;
+    return LBM_OK;
+}
+
+lbm_status lbm_mlp_create(int max_batch, unsigned long long seed, void *stream, lbm_mlp **out)
+{
+    if (!out || max_batch < 1 || max_batch > (1 << 24)) return mfail(LBM_EINVAL, "invalid MLP arguments");
+    *out = nullptr;
+    lbm_mlp *p = new (std::nothrow) lbm_mlp;
+    if (!p) return mfail(LBM_ENOMEM, "host allocation failed");
+    std::memset(p, 0, sizeof *p);
+    p->max_batch = max_batch;
+    p->stream = (cudaStream_t)stream;
+    const size_t bytes = mlp_layout(nullptr, nullptr, max_batch);
+    cudaError_t e = cudaMalloc(&p->base, bytes);
+    if (e != cudaSuccess) {
+        delete p;
+        return mfail(LBM_ENOMEM, std::string("cudaMalloc for the MLP: ") + cudaGetErrorString(e));
+    }
+    mlp_layout(p, (char *)p->base, max_batch);
+    e = cudaMemsetAsync(p->base, 0, bytes, p->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->host_loss, sizeof(double) * 1216);
+    if (e != cudaSuccess) {
+        lbm_mlp_destroy(p);
+        return mfail(LBM_ECUDA, cudaGetErrorString(e));
+    }
+    // default initialisation: U(-1/sqrt(fan_in), 1/sqrt(fan_in))
+    uint64_t st = seed;
+    std::vector<float> flat;
+    for (int l = 0; l < NL; ++l) {
+        const double bound = 1.0 / std::sqrt((double)WIDTH[l]);
+        for (long i = 0; i < (long)WIDTH[l + 1] * WIDTH[l] + WIDTH[l + 1]; ++i)
+            flat.push_back((float)((2.0 * u01(st) - 1.0) * bound));
+    }
+    lbm_status s2 = lbm_mlp_set_params(p, flat.data());
+    if (s2 != LBM_OK) {
+        lbm_mlp_destroy(p);
+        return s2;
+    }
+    *out = p;
+    return LBM_OK;
+}
+
+void lbm_mlp_destroy(lbm_mlp *p)
+{
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    if (p->base) cudaFree(p->base);
+    if (p->host_loss) cudaFreeHost(p->host_loss);
+    delete p;
+}
+
+lbm_status lbm_mlp_set_params(lbm_mlp *p, const float *flat)
+{
+    if (!p || !flat) return mfail(LBM_EINVAL, "NULL argument");
+    long o = 0;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        const long nw = (long)WIDTH[l + 1] * WIDTH[l];
+        e = cudaMemcpyAsync(p->W[l], flat + o, 4 * nw, cudaMemcpyHostToDevice, p->stream);
+        o += nw;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->b[l], flat + o, 4 * WIDTH[l + 1], cudaMemcpyHostToDevice, p->stream);
+        o += WIDTH[l + 1];
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->mW[l], 0, 4 * nw, p->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->vW[l], 0, 4 * nw, p->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->mb[l], 0, 4 * WIDTH[l + 1], p->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->vb[l], 0, 4 * WIDTH[l + 1], p->stream);
+        if (e == cudaSuccess) e = refresh_bf16(p, l);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    p->step = 0;
+    return e == cudaSuccess ? LBM_OK : mfail(LBM_ECUDA, cudaGetErrorString(e));
+}
+
+lbm_status lbm_mlp_get_params(lbm_mlp *p, float *flat)
+{
+    if (!p || !flat) return mfail(LBM_EINVAL, "NULL argument");
+    long o = 0;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        const long nw = (long)WIDTH[l + 1] * WIDTH[l];
+        e = cudaMemcpyAsync(flat + o, p->W[l], 4 * nw, cudaMemcpyDeviceToHost, p->stream);
+        o += nw;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(flat + o, p->b[l], 4 * WIDTH[l + 1], cudaMemcpyDeviceToHost, p->stream);
+        o += WIDTH[l + 1];
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return e == cudaSuccess ? LBM_OK : mfail(LBM_ECUDA, cudaGetErrorString(e));
+}
+
+lbm_status lbm_mlp_forward(lbm_mlp *p, const float *x_dev, int M, float *y_dev)
+{
+    if (!p || !x_dev || !y_dev || M < 1 || M > p->max_batch) return mfail(LBM_EINVAL, "invalid forward arguments");
+    cudaError_t e = cudaMemcpyAsync(p->x32, x_dev, 16L * M, cudaMemcpyDeviceToDevice, p->stream);
+    if (e == cudaSuccess) e = forward(p, M);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_dev, p->z[NL - 1], 24L * M, cudaMemcpyDeviceToDevice, p->stream);
+    return e == cudaSuccess ? LBM_OK : mfail(LBM_ECUDA, cudaGetErrorString(e));
+}
+
+static lbm_status grads_and_loss(lbm_mlp *p, const float *x_dev, const float *t_dev, int M, double *loss)
+{
+    cudaError_t e = cudaMemcpyAsync(p->x32, x_dev, 16L * M, cudaMemcpyDeviceToDevice, p->stream);
+    if (e == cudaSuccess) e = forward(p, M);
+    int np = 0;
+    if (e == cudaSuccess) e = backward(p, t_dev, M, &np);
+    if (e != cudaSuccess) return mfail(LBM_ECUDA, cudaGetErrorString(e));
+    if (loss) {
+        e = cudaMemcpyAsync(p->host_loss, p->loss_part, 8L * np, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return mfail(LBM_ECUDA, cudaGetErrorString(e));
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += p->host_loss[i];
+        *loss = s / ((double)M * WIDTH[NL]);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_mlp_loss_grad(lbm_mlp *p, const float *x_dev, const float *t_dev, int M, double *loss, float *grad_flat)
+{
+    if (!p || !x_dev || !t_dev || M < 1 || M > p->max_batch) return mfail(LBM_EINVAL, "invalid arguments");
+    lbm_status st = grads_and_loss(p, x_dev, t_dev, M, loss);
+    if (st != LBM_OK || !grad_flat) return st;
+    long o = 0;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        const long nw = (long)WIDTH[l + 1] * WIDTH[l];
+        e = cudaMemcpyAsync(grad_flat + o, p->gW[l], 4 * nw, cudaMemcpyDeviceToHost, p->stream);
+        o += nw;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(grad_flat + o, p->gb[l], 4 * WIDTH[l + 1], cudaMemcpyDeviceToHost, p->stream);
+        o += WIDTH[l + 1];
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return e == cudaSuccess ? LBM_OK : mfail(LBM_ECUDA, cudaGetErrorString(e));
+}
+
+lbm_status lbm_mlp_train_step(lbm_mlp *p, const float *x_dev, const float *t_dev, int M, float lr, double *loss)
+{
+    if (!p || !x_dev || !t_dev || M < 1 || M > p->max_batch || !(lr > 0)) return mfail(LBM_EINVAL, "invalid arguments");
+    lbm_status st = grads_and_loss(p, x_dev, t_dev, M, loss);
+    if (st != LBM_OK) return st;
+    p->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        const long nw = (long)WIDTH[l + 1] * WIDTH[l];
+        adam_kernel<<<blocks_for(nw), 256, 0, p->stream>>>(p->W[l], p->gW[l], p->mW[l], p->vW[l], nw, WIDTH[l],
+                                                           nullptr, 0, lr, b1, b2, eps, c1, c2);
+        adam_kernel<<<1, 256, 0, p->stream>>>(p->b[l], p->gb[l], p->mb[l], p->vb[l], WIDTH[l + 1], WIDTH[l + 1],
+                                              nullptr, 0, lr, b1, b2, eps, c1, c2);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = refresh_bf16(p, l);
+    }
+    return e == cudaSuccess ? LBM_OK : mfail(LBM_ECUDA, cudaGetErrorString(e));
+}
+
+lbm_status lbm_mlp_features(lbm_mlp *p, int nx, int ny, double kn, double u_w, float *x_dev)
+{
+    if (!p || !x_dev || nx < 1 || ny < 1 || !(kn > 0)) return mfail(LBM_EINVAL, "invalid feature arguments");
+    const float f2 = (float)((2.0 * std::log10(kn) + 1.0) / 3.0);
+    const float f3 = (float)((u_w - 0.0125) / 0.0075);
+    features_kernel<<<blocks_for((long)nx * ny), 256, 0, p->stream>>>(nx, ny, f2, f3, x_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : mfail(LBM_ECUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"
+
+cudaError_t launch_warm_state(const float *pred, long ncells, int m, const double *xi1, const double *w1,
+                              double uw_over_uref, void *h, int prec, cudaStream_t s)
+{
+    const int nb = blocks_for(ncells);
+    if (prec == LBM_FP64)
+        warm_state_kernel<double><<<nb, 256, 0, s>>>(pred, ncells, m, xi1, w1, uw_over_uref, (double *)h);
+    else
+        warm_state_kernel<float><<<nb, 256, 0, s>>>(pred, ncells, m, xi1, w1, uw_over_uref, (float *)h);
+    return cudaGetLastError();
+}

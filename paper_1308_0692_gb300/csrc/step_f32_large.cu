@@ -1,23 +1,32 @@
 // FP32 fused step, 12 nodes per axis (perturbation stored and marched in float;
-// wall impermeability sums and residual reductions across threads in double).
-// (generated instantiation list; the kernel is in step_kernel.cuh)
+// wall sums across velocity rows and residual reductions across threads in double).
+// (instantiation list; the kernel is in step_kernel.cuh)
 #include "step_kernel.cuh"
 
 using namespace lbmk;
 
-cudaError_t launch_step_f32_large(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_step_f32_large(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s)
 {
-    if (m == 12 && g == 2)
-        return resid ? launch_one<float, float, 12, 2, true, false, false>(a, grid, s)
-                     : launch_one<float, float, 12, 2, false, false, false>(a, grid, s);
-    if (m == 12 && g == 3)
-        return resid ? launch_one<float, float, 12, 3, true, false, false>(a, grid, s)
-                     : launch_one<float, float, 12, 3, false, false, false>(a, grid, s);
-    if (m == 12 && g == 4)
-        return resid ? launch_one<float, float, 12, 4, true, false, false>(a, grid, s)
-                     : launch_one<float, float, 12, 4, false, false, false>(a, grid, s);
-    if (m == 12 && g == 6)
-        return resid ? launch_one<float, float, 12, 6, true, false, false>(a, grid, s)
-                     : launch_one<float, float, 12, 6, false, false, false>(a, grid, s);
+    if (m == 12 && g == 2 && pf == 0)
+        return resid ? launch_one<float, float, 12, 2, true, false, false, false>(a, grid, s)
+                     : launch_one<float, float, 12, 2, false, false, false, false>(a, grid, s);
+    if (m == 12 && g == 3 && pf == 0)
+        return resid ? launch_one<float, float, 12, 3, true, false, false, false>(a, grid, s)
+                     : launch_one<float, float, 12, 3, false, false, false, false>(a, grid, s);
+    if (m == 12 && g == 4 && pf == 0)
+        return resid ? launch_one<float, float, 12, 4, true, false, false, false>(a, grid, s)
+                     : launch_one<float, float, 12, 4, false, false, false, false>(a, grid, s);
+    if (m == 12 && g == 6 && pf == 0)
+        return resid ? launch_one<float, float, 12, 6, true, false, false, false>(a, grid, s)
+                     : launch_one<float, float, 12, 6, false, false, false, false>(a, grid, s);
+    if (m == 12 && g == 3 && pf == 1)
+        return resid ? launch_one<float, float, 12, 3, true, false, false, true>(a, grid, s)
+                     : launch_one<float, float, 12, 3, false, false, false, true>(a, grid, s);
+    if (m == 12 && g == 4 && pf == 1)
+        return resid ? launch_one<float, float, 12, 4, true, false, false, true>(a, grid, s)
+                     : launch_one<float, float, 12, 4, false, false, false, true>(a, grid, s);
+    if (m == 12 && g == 6 && pf == 1)
+        return resid ? launch_one<float, float, 12, 6, true, false, false, true>(a, grid, s)
+                     : launch_one<float, float, 12, 6, false, false, false, true>(a, grid, s);
     return cudaErrorInvalidValue;
 }

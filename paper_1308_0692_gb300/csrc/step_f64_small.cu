@@ -1,25 +1,31 @@
 // FP64 fused step, 3/4/6 nodes per axis (storage and arithmetic in double).
-// (generated instantiation list; the kernel is in step_kernel.cuh)
+// (instantiation list; the kernel is in step_kernel.cuh)
 #include "step_kernel.cuh"
 
 using namespace lbmk;
 
-cudaError_t launch_step_f64_small(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_step_f64_small(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s)
 {
-    if (m == 3 && g == 1)
-        return resid ? launch_one<double, double, 3, 1, true, false, false>(a, grid, s)
-                     : launch_one<double, double, 3, 1, false, false, false>(a, grid, s);
-    if (m == 4 && g == 1)
-        return resid ? launch_one<double, double, 4, 1, true, false, false>(a, grid, s)
-                     : launch_one<double, double, 4, 1, false, false, false>(a, grid, s);
-    if (m == 4 && g == 2)
-        return resid ? launch_one<double, double, 4, 2, true, false, false>(a, grid, s)
-                     : launch_one<double, double, 4, 2, false, false, false>(a, grid, s);
-    if (m == 6 && g == 1)
-        return resid ? launch_one<double, double, 6, 1, true, false, false>(a, grid, s)
-                     : launch_one<double, double, 6, 1, false, false, false>(a, grid, s);
-    if (m == 6 && g == 2)
-        return resid ? launch_one<double, double, 6, 2, true, false, false>(a, grid, s)
-                     : launch_one<double, double, 6, 2, false, false, false>(a, grid, s);
+    if (m == 3 && g == 1 && pf == 0)
+        return resid ? launch_one<double, double, 3, 1, true, false, false, false>(a, grid, s)
+                     : launch_one<double, double, 3, 1, false, false, false, false>(a, grid, s);
+    if (m == 4 && g == 1 && pf == 0)
+        return resid ? launch_one<double, double, 4, 1, true, false, false, false>(a, grid, s)
+                     : launch_one<double, double, 4, 1, false, false, false, false>(a, grid, s);
+    if (m == 4 && g == 2 && pf == 0)
+        return resid ? launch_one<double, double, 4, 2, true, false, false, false>(a, grid, s)
+                     : launch_one<double, double, 4, 2, false, false, false, false>(a, grid, s);
+    if (m == 6 && g == 1 && pf == 0)
+        return resid ? launch_one<double, double, 6, 1, true, false, false, false>(a, grid, s)
+                     : launch_one<double, double, 6, 1, false, false, false, false>(a, grid, s);
+    if (m == 6 && g == 2 && pf == 0)
+        return resid ? launch_one<double, double, 6, 2, true, false, false, false>(a, grid, s)
+                     : launch_one<double, double, 6, 2, false, false, false, false>(a, grid, s);
+    if (m == 4 && g == 2 && pf == 1)
+        return resid ? launch_one<double, double, 4, 2, true, false, false, true>(a, grid, s)
+                     : launch_one<double, double, 4, 2, false, false, false, true>(a, grid, s);
+    if (m == 6 && g == 2 && pf == 1)
+        return resid ? launch_one<double, double, 6, 2, true, false, false, true>(a, grid, s)
+                     : launch_one<double, double, 6, 2, false, false, false, true>(a, grid, s);
     return cudaErrorInvalidValue;
 }

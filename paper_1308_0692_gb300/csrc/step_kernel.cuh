@@ -28,16 +28,20 @@
 //
 // Walls.  Segments that contain a wall-adjacent cell are handled by a second kernel
 // (PART = true) over the list of such segments, so that the bulk kernel carries no wall
-// code and keeps a small register footprint.  It first forms rho'_w of each wall face in
-// FP64 from the incoming populations (Eq. 9 as a discrete flux balance), summed across
-// the G warps, and uses the ghost w_a [rho'_w (1 + xi_t U) + xi_t U / u_ref] (Eq. 8) as
-// the upwind value across the wall.
+// code and keeps a small register footprint.  It first forms rho'_w of each wall face from
+// the incoming populations (Eq. 9 as a discrete flux balance): products and sums within a
+// velocity row in the arithmetic type, the sums over rows and over the G warps in FP64 --
+// per-velocity FP64 work on every lane of a wall segment made this kernel a third of
+// the step on GB300, whose FP64 rate is 1/64 of FP32.  The ghost
+// w_a [rho'_w (1 + xi_t U) + xi_t U / u_ref] (Eq. 8) is the upwind value across the wall.
 //
 // Template parameters: TS storage type, TC arithmetic type, M nodes per axis, G warps
 // per segment; RESID: accumulate ||h^{n+1} - h^n||^2 and ||h^{n+1}||^2 (FP64 across
 // threads); SOURCE: add a source array after relaxation (correction sweeps of the
 // mixed-precision refinement); DEFECT: write h^{n+1} - h^n instead of h^{n+1} (FP64
-// defect of an FP32 state); PART: wall kernel.
+// defect of an FP32 state); PART: wall kernel; PF: bulk variant that issues all own-cell
+// and y-neighbour loads of the warp's velocity rows before the arithmetic (more loads in
+// flight per warp, more registers).
 #pragma once
 
 #include "lbm_internal.h"
@@ -61,7 +65,8 @@ struct Shape {
     static constexpr int THREADS = 32 * WARPS;
 };
 
-template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT, bool PART>
+template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT, bool PART,
+          bool PF = false>
 __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs a)
 {
     constexpr int SPB = Shape<G>::SPB;
@@ -109,7 +114,10 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
     const long c_above = (y < ny - 1) ? c + nx : c;
     const TS *__restrict__ h = reinterpret_cast<const TS *>(a.h);
 
-    // ---- wall densities rho'_w of the faces this cell touches (FP64, Eq. 9) ----
+    // ---- wall densities rho'_w of the faces this cell touches (Eq. 9) ----
+    // Partial sums over the M velocities of one row are formed in the arithmetic type
+    // (exact products of the stored values for FP64; single precision for FP32), the sums
+    // across rows and across the G warps in FP64.
     double rb = 0.0, rt = 0.0, rl = 0.0, rr = 0.0;
     if (WALLS) {
         double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
@@ -118,18 +126,18 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
             for (int r = 0; r < RPL; ++r) {
                 const int iy = g * RPL + r;
                 const double xiy = a.xi[iy];
-                double rowsum = 0.0, left = 0.0, right = 0.0;
+                TC rowsum = 0, left = 0, right = 0;
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
-                    const double v = (double)ldg(h + (long)(iy * M + ix) * ncells + c);
+                    const TC v = (TC)ldg(h + (long)(iy * M + ix) * ncells + c);
                     rowsum += v;
-                    if (ix < HALF) left -= a.xi[ix] * v;       // moving towards the left wall
-                    if (ix >= M - HALF) right += a.xi[ix] * v; // moving towards the right wall
+                    if (ix < HALF) left -= pick<TC>(a.xi, a.xi_f, ix) * v;       // towards the left wall
+                    if (ix >= M - HALF) right += pick<TC>(a.xi, a.xi_f, ix) * v; // towards the right wall
                 }
-                if (xiy < 0.0) sb -= xiy * rowsum;             // moving towards the bottom wall
-                if (xiy > 0.0) st += xiy * rowsum;             // moving towards the top wall
-                sls += left;
-                srs += right;
+                if (xiy < 0.0) sb -= xiy * (double)rowsum;             // towards the bottom wall
+                if (xiy > 0.0) st += xiy * (double)rowsum;             // towards the top wall
+                sls += (double)left;
+                srs += (double)right;
             }
         }
         s_wall[0][g][sl][lane] = sb;
@@ -152,9 +160,50 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
     }
 
     // ---- transport (upwind) + moment row sums, h* kept in registers ----
+    // Ghost values (Eq. 8) are evaluated in the arithmetic type from the FP64 densities.
     TC hs[RPL * M];
     TC rho = 0, jx = 0, jy = 0;
-    if (work) {
+    if (work && !WALLS && PF) {
+        // bulk path, loads issued ahead of use: all own-cell and y-neighbour values of the
+        // warp's rows first, then the x neighbours and the arithmetic
+        TC hyv[RPL * M];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
+            const long cy = xiy > TC(0) ? c_below : (xiy < TC(0) ? c_above : c);
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const TS *hp = h + (long)(iy * M + ix) * ncells;
+                hs[r * M + ix] = (TC)ldg(hp + c);
+                hyv[r * M + ix] = (TC)ldg(hp + cy);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
+            const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
+            TC R = 0, X = 0;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const TS *hp = h + (long)(iy * M + ix) * ncells;
+                const TC hc = hs[r * M + ix];
+                TC v = hc;
+                if (ix >= M - HALF || ix < HALF) {
+                    const TC hx = (TC)ldg(hp + (ix >= M - HALF ? c_left : c_right));
+                    v += pick<TC>(a.nux, a.nux_f, ix) * (hx - hc);
+                }
+                v += nuy * (hyv[r * M + ix] - hc);
+                hs[r * M + ix] = v;
+                R += v;
+                X += pick<TC>(a.xi, a.xi_f, ix) * v;
+            }
+            rho += R;
+            jx += X;
+            jy += xiy * R;
+        }
+    } else if (work) {
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
@@ -163,33 +212,36 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
             const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
             const long cy = ypos ? c_below : (yneg ? c_above : c);
             const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
-            const double rho_y = ypos ? rb : rt;
-            const double u_y = ypos ? a.u_bottom : a.u_top;
-            const double drive_y = a.homogeneous ? 0.0 : u_y * a.inv_u_ref;
-            const double wy = a.w1[iy];
+            const TC rho_y = (TC)(ypos ? rb : rt);
+            const TC u_y = (TC)(ypos ? a.u_bottom : a.u_top);
+            const TC drive_y = a.homogeneous ? TC(0) : (TC)((ypos ? a.u_bottom : a.u_top) * a.inv_u_ref);
+            const TC wy = pick<TC>(a.w1, a.w1_f, iy);
+            const TC rl_t = (TC)rl, rr_t = (TC)rr;
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
                 const TS *hp = h + (long)(iy * M + ix) * ncells;
                 const TC hc = (TC)ldg(hp + c);
+                const TC xix = pick<TC>(a.xi, a.xi_f, ix);
+                const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
                 TC v = hc;
                 if (ix >= M - HALF || ix < HALF) {
                     TC hx;
                     if (WALLS && (ix >= M - HALF ? wl : wr))
-                        hx = (TC)(a.w1[ix] * wy * (ix >= M - HALF ? rl : rr));
+                        hx = wxy * (ix >= M - HALF ? rl_t : rr_t);
                     else
                         hx = (TC)ldg(hp + (ix >= M - HALF ? c_left : c_right));
                     v += pick<TC>(a.nux, a.nux_f, ix) * (hx - hc);
                 }
                 TC hy;
                 if (WALLS && ywall)
-                    hy = (TC)(a.w1[ix] * wy * (rho_y * (1.0 + a.xi[ix] * u_y) + a.xi[ix] * drive_y));
+                    hy = wxy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y);
                 else
                     hy = (TC)ldg(hp + cy);
                 v += nuy * (hy - hc);
                 hs[r * M + ix] = v;
                 R += v;
-                X += pick<TC>(a.xi, a.xi_f, ix) * v;
+                X += xix * v;
             }
             rho += R;
             jx += X;
@@ -267,17 +319,18 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
 }
 
 // Bulk kernel over `grid` blocks, then the wall kernel over the listed wall segments.
-template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT>
+// PF selects the bulk variant that issues a warp's loads ahead of their use.
+template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT, bool PF = false>
 cudaError_t launch_one(const StepArgs &a, int grid, cudaStream_t s)
 {
     constexpr int T = Shape<G>::THREADS;
-    step_kernel<TS, TC, M, G, RESID, SOURCE, DEFECT, false><<<grid, T, 0, s>>>(a);
+    step_kernel<TS, TC, M, G, RESID, SOURCE, DEFECT, false, PF><<<grid, T, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_wall_segs == 0) return e;
     StepArgs b = a;
     b.partials_offset = grid;
     const int wgrid = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
-    step_kernel<TS, TC, M, G, RESID, SOURCE, DEFECT, true><<<wgrid, T, 0, s>>>(b);
+    step_kernel<TS, TC, M, G, RESID, SOURCE, DEFECT, true, false><<<wgrid, T, 0, s>>>(b);
     return cudaGetLastError();
 }
 

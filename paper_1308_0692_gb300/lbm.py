@@ -69,9 +69,9 @@ def _load():
         "lbm_coeffs": (st, [_vp, _dp, _dp, _dp]),
         "lbm_step": (st, [_vp, ctypes.c_long]),
         "lbm_residual": (st, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
-        "lbm_set_variant": (st, [_vp, ctypes.c_int]),
+        "lbm_set_variant": (st, [_vp, ctypes.c_int, ctypes.c_int]),
         "lbm_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.POINTER(lbm_solve_info)]),
-        "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int)]),
+        "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
         "lbm_get_state": (st, [_vp, _dp]),
@@ -91,6 +91,20 @@ def _load():
         "lbm_batch_poll": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]),
         "lbm_batch_status": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), _dp, ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_get_state": (st, [_vp, ctypes.c_int, _dp]),
+        "lbm_batch_reset": (st, [_vp]),
+        "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
+        "lbm_batch_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), _dp]),
+        "lbm_mlp_param_count": (st, [ctypes.POINTER(ctypes.c_long)]),
+        "lbm_mlp_create": (st, [ctypes.c_int, ctypes.c_ulonglong, _vp, ctypes.POINTER(_vp)]),
+        "lbm_mlp_destroy": (None, [_vp]),
+        "lbm_mlp_set_params": (st, [_vp, ctypes.POINTER(ctypes.c_float)]),
+        "lbm_mlp_get_params": (st, [_vp, ctypes.POINTER(ctypes.c_float)]),
+        "lbm_mlp_forward": (st, [_vp, _vp, ctypes.c_int, _vp]),
+        "lbm_mlp_loss_grad": (st, [_vp, _vp, _vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_float)]),
+        "lbm_mlp_train_step": (st, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _dp]),
+        "lbm_mlp_features": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp]),
+        "lbm_warm_start": (st, [_vp, _vp, ctypes.c_double, ctypes.c_double]),
         "lbm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -224,14 +238,14 @@ def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0) -> d
     return {k: getattr(info, k) for k, _ in lbm_solve_info._fields_}
 
 
-def lbm_set_variant(sim: Sim, lanes_per_cell: int):
-    _check(_load().lbm_set_variant(sim.handle, int(lanes_per_cell)))
+def lbm_set_variant(sim: Sim, warps_per_segment: int, prefetch: int = 0):
+    _check(_load().lbm_set_variant(sim.handle, int(warps_per_segment), int(prefetch)))
 
 
-def lbm_get_variant(sim: Sim) -> int:
-    v = ctypes.c_int()
-    _check(_load().lbm_get_variant(sim.handle, ctypes.byref(v)))
-    return v.value
+def lbm_get_variant(sim: Sim):
+    g, pf = ctypes.c_int(), ctypes.c_int()
+    _check(_load().lbm_get_variant(sim.handle, ctypes.byref(g), ctypes.byref(pf)))
+    return g.value, pf.value
 
 
 def lbm_residual(sim: Sim):
@@ -373,3 +387,108 @@ def lbm_batch_get_state(b: Batch, i: int) -> np.ndarray:
     h = np.empty((b.n_vel, p.nx * p.ny))
     _check(_load().lbm_batch_get_state(b.handle, int(i), _ptr(h)))
     return h
+
+
+def lbm_batch_moments(b: Batch, i: int, out_ptr: int):
+    _check(_load().lbm_batch_moments(b.handle, int(i), out_ptr))
+
+
+def lbm_batch_reset(b: Batch):
+    _check(_load().lbm_batch_reset(b.handle))
+
+
+def lbm_batch_tune(b: Batch, steps_per_trial: int = 20) -> dict:
+    g, bp, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(_load().lbm_batch_tune(b.handle, int(steps_per_trial), ctypes.byref(g), ctypes.byref(bp),
+                                  ctypes.byref(o), ctypes.byref(ms)))
+    return {"warps_per_segment": g.value, "blocks_per_sm": bp.value, "order": o.value, "ms_per_step": ms.value}
+
+
+class MLP:
+    """Owner of an lbm_mlp* (the warm-start network)."""
+
+    def __init__(self, handle: int, keepalive=None):
+        self.handle = handle
+        self._keepalive = keepalive
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.lbm_mlp_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def lbm_mlp_param_count() -> int:
+    n = ctypes.c_long()
+    _check(_load().lbm_mlp_param_count(ctypes.byref(n)))
+    return n.value
+
+
+def lbm_mlp_create(max_batch: int, seed: int = 0, stream=None) -> MLP:
+    out = _vp()
+    _check(_load().lbm_mlp_create(int(max_batch), int(seed), _stream_handle(stream), ctypes.byref(out)))
+    return MLP(out.value, keepalive=stream)
+
+
+def lbm_mlp_set_params(m: MLP, flat: np.ndarray):
+    flat = np.ascontiguousarray(flat, dtype=np.float32)
+    assert flat.size == lbm_mlp_param_count()
+    _check(_load().lbm_mlp_set_params(m.handle, _fptr(flat)))
+
+
+def lbm_mlp_get_params(m: MLP) -> np.ndarray:
+    flat = np.empty(lbm_mlp_param_count(), dtype=np.float32)
+    _check(_load().lbm_mlp_get_params(m.handle, _fptr(flat)))
+    return flat
+
+
+def lbm_mlp_forward(m: MLP, x_ptr: int, rows: int, y_ptr: int):
+    _check(_load().lbm_mlp_forward(m.handle, x_ptr, int(rows), y_ptr))
+
+
+def lbm_mlp_loss_grad(m: MLP, x_ptr: int, t_ptr: int, rows: int, want_grad: bool = True):
+    loss = ctypes.c_double()
+    g = np.empty(lbm_mlp_param_count(), dtype=np.float32) if want_grad else None
+    _check(_load().lbm_mlp_loss_grad(m.handle, x_ptr, t_ptr, int(rows), ctypes.byref(loss),
+                                     _fptr(g) if g is not None else None))
+    return loss.value, g
+
+
+def lbm_mlp_train_step(m: MLP, x_ptr: int, t_ptr: int, rows: int, lr: float, want_loss: bool = False):
+    loss = ctypes.c_double()
+    _check(_load().lbm_mlp_train_step(m.handle, x_ptr, t_ptr, int(rows), float(lr),
+                                      ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def lbm_mlp_features(m: MLP, nx: int, ny: int, kn: float, u_w: float, x_ptr: int):
+    _check(_load().lbm_mlp_features(m.handle, int(nx), int(ny), float(kn), float(u_w), x_ptr))
+
+
+def lbm_warm_start(sim: Sim, m: MLP, kn: float, u_w: float):
+    _check(_load().lbm_warm_start(sim.handle, m.handle, float(kn), float(u_w)))
+
+
+def mlp_unflatten(flat: np.ndarray, widths=(4, 256, 256, 256, 6)):
+    """Split a flat parameter vector into [(W, b), ...] (float64 copies)."""
+    out, o = [], 0
+    for i in range(len(widths) - 1):
+        nw = widths[i + 1] * widths[i]
+        W = np.asarray(flat[o:o + nw], dtype=np.float64).reshape(widths[i + 1], widths[i])
+        o += nw
+        b = np.asarray(flat[o:o + widths[i + 1]], dtype=np.float64)
+        o += widths[i + 1]
+        out.append((W, b))
+    return out
+
+
+def mlp_flatten(params) -> np.ndarray:
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)

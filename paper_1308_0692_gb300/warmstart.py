@@ -1,0 +1,131 @@
+"""Learned warm start of the lid-driven cavity march.
+
+Pipeline (all numerical work in the library's CUDA kernels; PyTorch holds device
+memory and gathers minibatches):
+
+1. ``generate``: steady 128 x 128 cavity states for many (Kn, u_w) pairs, marched by the
+   batched persistent FP32 solver to a residual tolerance; their six normalised moments
+   ((rho-1)/u_w, u_x/u_w, u_y/u_w, (P_xx-1)/u_w, P_xy/u_w, (P_yy-1)/u_w) per cell are the
+   training targets.
+2. ``train``: Adam on minibatches of (cell features, targets) with the library's BF16
+   tensor-core MLP kernels.
+3. ``lbm_warm_start`` (C-ABI) builds the initial state of a new cavity from the
+   network's prediction; the cold-start march remains the fallback and the judge of
+   convergence.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import lbm
+from .inputs import BATCH_SEED
+
+FEATURES = 4
+TARGETS = 6
+
+
+def draw_pairs(count: int, seed: int):
+    """(Kn, u_w) with Kn log-uniform in [0.01, 10] and u_w uniform in [0.005, 0.02]."""
+    rng = np.random.default_rng(seed)
+    kn = 10.0 ** rng.uniform(-2.0, 1.0, count)
+    uw = rng.uniform(0.005, 0.02, count)
+    return list(zip(kn.tolist(), uw.tolist()))
+
+
+def generate(pairs, side=128, tol=1e-6, chunk=512, max_steps=400_000, steps_per_launch=1000, n_half=4,
+             log=print):
+    """Steady cavity states for all pairs; returns a float32 CUDA tensor [len(pairs), side*side, 6]
+    of normalised moments and per-instance step counts."""
+    import torch
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    ncells = side * side
+    out = torch.empty((len(pairs), ncells, TARGETS), dtype=torch.float32, device="cuda")
+    steps = np.zeros(len(pairs), dtype=np.int64)
+    stream = torch.cuda.Stream()
+    mom = torch.empty((6, ncells), dtype=torch.float64, device="cuda")
+    for c0 in range(0, len(pairs), chunk):
+        sub = pairs[c0:c0 + chunk]
+        probs = [lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
+                                  residual_every=100) for kn, uw in sub]
+        b = lbm.lbm_batch_init(vs, probs, stream=stream)
+        t0 = time.perf_counter()
+        done = 0
+        while done < max_steps:
+            lbm.lbm_batch_advance(b, steps_per_launch, tol)
+            done += steps_per_launch
+            n_active, _ = lbm.lbm_batch_poll(b)
+            if n_active == 0:
+                break
+        with torch.cuda.stream(stream):
+            for i, (kn, uw) in enumerate(sub):
+                lbm.lbm_batch_moments(b, i, mom.data_ptr())
+                m = mom
+                out[c0 + i, :, 0] = ((m[0] - 1.0) / uw).float()
+                out[c0 + i, :, 1] = (m[1] / uw).float()
+                out[c0 + i, :, 2] = (m[2] / uw).float()
+                out[c0 + i, :, 3] = ((m[3] - 1.0) / uw).float()
+                out[c0 + i, :, 4] = (m[4] / uw).float()
+                out[c0 + i, :, 5] = ((m[5] - 1.0) / uw).float()
+                steps[c0 + i] = lbm.lbm_batch_status(b, i)["steps"]
+        stream.synchronize()
+        log(f"generate: instances {c0}..{c0 + len(sub) - 1} converged (tol {tol:g}) in "
+            f"{time.perf_counter() - t0:.1f} s, max steps {steps[c0:c0 + len(sub)].max()}")
+        b.close()
+    return out, steps
+
+
+def features(pairs, side=128):
+    """Feature tensor [len(pairs), side*side, 4] (float32, CUDA) built by the library kernel."""
+    import torch
+    m = lbm.lbm_mlp_create(side * side, seed=0)
+    out = torch.empty((len(pairs), side * side, FEATURES), dtype=torch.float32, device="cuda")
+    for i, (kn, uw) in enumerate(pairs):
+        lbm.lbm_mlp_features(m, side, side, kn, uw, out[i].data_ptr())
+    torch.cuda.synchronize()
+    m.close()
+    return out
+
+
+def train(feats, targets, steps=20000, batch_rows=8192, lr=1e-3, lr_final=1e-5, seed=0, max_batch=None,
+          log=print):
+    """Adam with a cosine-decayed learning rate on uniformly sampled (instance, cell) rows."""
+    import torch
+    n_inst, ncells, _ = feats.shape
+    flat_x = feats.reshape(-1, FEATURES)
+    flat_t = targets.reshape(-1, TARGETS)
+    mlp = lbm.lbm_mlp_create(max(max_batch or 0, batch_rows, ncells), seed=seed)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    xb = torch.empty((batch_rows, FEATURES), dtype=torch.float32, device="cuda")
+    tb = torch.empty((batch_rows, TARGETS), dtype=torch.float32, device="cuda")
+    hist = []
+    t0 = time.perf_counter()
+    for it in range(steps):
+        idx = torch.randint(0, flat_x.shape[0], (batch_rows,), device="cuda", generator=g)
+        torch.index_select(flat_x, 0, idx, out=xb)
+        torch.index_select(flat_t, 0, idx, out=tb)
+        torch.cuda.synchronize()
+        a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * it / steps))
+        want = it % 1000 == 0 or it == steps - 1
+        loss = lbm.lbm_mlp_train_step(mlp, xb.data_ptr(), tb.data_ptr(), batch_rows, a, want_loss=want)
+        if want:
+            hist.append((it, loss))
+            log(f"train: step {it} loss {loss:.3e} lr {a:.2e} ({time.perf_counter() - t0:.1f} s)")
+    torch.cuda.synchronize()
+    return mlp, hist, time.perf_counter() - t0
+
+
+def solve_cavity(vs, kn, uw, side=128, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refine=3, mlp=None, stream=None):
+    """Solve one cavity to tol (cold start or warm start); returns (sim, info, seconds)."""
+    import torch
+    prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=prec, residual_every=100)
+    sim = lbm.lbm_init(vs, prob, stream=stream or torch.cuda.Stream())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if mlp is not None:
+        lbm.lbm_warm_start(sim, mlp, kn, uw)
+    info = lbm.lbm_solve(sim, tol, 2_000_000, refine if prec == lbm.LBM_FP32_PERTURB else 0)
+    torch.cuda.synchronize()
+    return sim, info, time.perf_counter() - t0

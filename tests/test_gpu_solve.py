@@ -2,8 +2,8 @@
 
 Tolerances (from the spec requirements): reduced-precision forms within 1e-5 on
 steady velocity profiles (max |du| / u_w) and shear stress (relative p_xy); the FP64
-march converged to r < 1e-11 within 1e-8 (the residual bounds the error up to the
-conditioning of the slow modes, about 1e2-1e3 here).
+march converged to r < 1e-12 within 1e-8 (the residual bounds the error up to the
+conditioning of the slow modes, about 1e2-2e3 here).
 """
 import math
 
@@ -43,11 +43,12 @@ def _gpu_solve(geom, nx, ny, kn, ub, ut, prec, tol, refine, n_half=4, stream=Tru
 
 @pytest.mark.parametrize("kn", [0.1, 0.01, 10.0])
 def test_fp64_couette_steady_state(kn):
-    """Couette, ny = 100, 64 velocities, plates +0.01 / -0.01: the FP64 march to r < 1e-11
-    reproduces the oracle's direct steady solve."""
+    """Couette, ny = 100, 64 velocities, plates +0.01 / -0.01: the FP64 march to r < 1e-12
+    reproduces the oracle's direct steady solve (error <= r times the slow-mode
+    conditioning, about 2e3 at Kn = 0.01)."""
     u = 0.01
-    sim, info = _gpu_solve(lbm.LBM_COUETTE, 1, 100, kn, u, -u, lbm.LBM_FP64, 1e-11, 0)
-    assert info["residual"] < 1e-11
+    sim, info = _gpu_solve(lbm.LBM_COUETTE, 1, 100, kn, u, -u, lbm.LBM_FP64, 1e-12, 0)
+    assert info["residual"] < 1e-12
     ux_ref, flux_ref = _couette_reference(kn, u, -u)
     m = lbm.lbm_moments(sim)
     fy, _ = lbm.lbm_face_flux(sim)
@@ -58,7 +59,7 @@ def test_fp64_couette_steady_state(kn):
 @pytest.mark.parametrize("kn", [0.1, 0.01, 10.0])
 def test_fp32_refined_couette_meets_1e5(kn):
     """FP32 storage with FP64 defect correction meets 1e-5 on the steady profile and the
-    shear stress; the defect of the refined state is at least 4x below the plain FP32 one."""
+    shear stress, and is at least as close to the oracle as the plain FP32 march."""
     u = 0.01
     ux_ref, flux_ref = _couette_reference(kn, u, -u)
     sim, info = _gpu_solve(lbm.LBM_COUETTE, 1, 100, kn, u, -u, lbm.LBM_FP32_PERTURB, 1e-8, 3)
