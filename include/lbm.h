@@ -187,6 +187,23 @@ lbm_status lbm_norms_scratch_bytes(long count, size_t *bytes);
 lbm_status lbm_norms(const void *a, const void *b, long count, int prec, void *scratch,
                      size_t scratch_bytes, double *out, void *stream);
 
+/* lbm_norms without any allocation, for callers that cannot allocate device memory
+ * at all -- e.g. code that runs while someone else's CUDA graph is being captured,
+ * hosts without a device allocator, or latency-critical paths where cudaMalloc may
+ * block -- and cannot pass a scratch buffer either.  The paper has no counterpart.
+ *   a, b, count, prec, out, stream  as for lbm_norms (b may be NULL).
+ * The per-block partial sums live in a 512 KiB array inside the library that every GPU
+ * loading the library holds until process exit; count is therefore limited to
+ * 67,108,864 elements (one partial pair per 2048 elements): larger counts return
+ * LBM_EINVAL.  The first call on each device (with that device current) looks up the
+ * array's device address; make it before any stream capture that includes this call.
+ * Calls share the array: each call writes every slot it reads, so nothing has to be
+ * cleared, but calls that overlap on the GPU (other streams, concurrent graph launches)
+ * race on it and must be serialised by the caller.  Never calls cudaMalloc or cudaFree.
+ * Results equal lbm_norms up to summation order. */
+lbm_status lbm_norms_noalloc(const void *a, const void *b, long count, int prec, double *out,
+                             void *stream);
+
 /* ---- Batched sweeps: many independent instances in one persistent launch ----
  * A batch holds independent problems (Couette channels and cavities of any size, Kn and
  * wall speeds; one shared velocity set, precision and residual_every) packed in one
