@@ -184,11 +184,45 @@ def _traffic_record(kernel_key: str):
     rec = json.load(open(path)).get(kernel_key)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1308_0692_gb300", "csrc", "step_kernel.cuh")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("step_kernel.cuh", "step_tma.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1308_0692_gb300", "csrc", name), "rb").read())
+    digest = h.hexdigest()[:16]
     if rec.get("source_sha256_16") != digest:
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+VARIANTS = [(3, 0), (4, 0), (6, 0), (3, 2), (4, 2), (6, 2)]
+
+
+def choose_variant(sim, stream, args):
+    """Autotune the step kernel on the workload itself: warps per segment x load path
+    (0 registers, 2 TMA-staged halo), a few timed steps each; or the forced --variant."""
+    import torch
+
+    from paper_1308_0692_gb300 import lbm
+    if args.variant:
+        g, pf = (int(v) for v in args.variant.split(","))
+        lbm.lbm_set_variant(sim, g, pf)
+        return (g, pf), None
+    times = {}
+    for g, pf in VARIANTS:
+        try:
+            lbm.lbm_set_variant(sim, g, pf)
+        except lbm.LBMError:
+            continue
+        lbm.lbm_step(sim, 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lbm.lbm_step(sim, 6)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[f"{g},{pf}"] = e0.elapsed_time(e1) / 6
+    best = min(times, key=times.get)
+    g, pf = (int(v) for v in best.split(","))
+    lbm.lbm_set_variant(sim, g, pf)
+    return (g, pf), times
 
 
 def run_own(args, dist: Dist):
@@ -209,6 +243,7 @@ def run_own(args, dist: Dist):
     sim = lbm.lbm_init(vs, prob, None, device_buf=buf, stream=stream)
     ncells = w["nx"] * w["ny"]
     units_per_step = ncells * n_vel
+    variant, tuning = choose_variant(sim, stream, args)
 
     def timed_block(K):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -261,13 +296,17 @@ def run_own(args, dist: Dist):
                                "Kn=0.05, lid u=0.01, FP32 perturbation storage, FP64 residual every 10 steps",
                    "nx": w["nx"], "ny": w["ny"], "velocities": n_vel, "unknowns": units_per_step,
                    "residual_every": w["residual_every"], "cold_start": True,
+                   "variant": {"warps_per_segment": variant[0], "load_path": ["registers", "prefetch", "tma"][variant[1]],
+                               "autotune_ms_per_step": tuning},
                    "l2": f"inputs larger than L2 ({units_per_step * 4 / 1e9:.2f} GB per state copy), no flush",
                    "parallelism": f"replicas{dist.world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "step_kernel<float,float,12,G>", "algorithmic_bytes_per_launch": algo_bytes,
+                     "kernel": f"fused step (bulk + wall launches), {variant[0]} warps/segment, "
+                               f"{['register', 'prefetch', 'TMA'][variant[1]]} loads",
+                     "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": avg * 1e3,
-                     "traffic": _traffic_record("step_f32_m12")},
+                     "traffic": _traffic_record(f"step_f32_m12_g{variant[0]}_pf{variant[1]}")},
         "residual_step_ms": (sum(resid) / len(resid) * 1e3) if resid else None,
         "last_residual": [r, rstep],
         "gpu_launches": launches,
@@ -348,31 +387,71 @@ def run_fp64_same_workload(vs, dist):
             "note": "FP64 storage+arithmetic; bounded by the FP64 pipe of GB300, not HBM"}
 
 
-def run_time_to_residual(dist):
-    """Cavity 128x128, 64 half-range velocities, Kn = 0.1, lid 0.01: plain FP64 march from
-    the cold start to residual < 1e-8 (checked every 100 steps)."""
+def run_time_to_residual(dist, count=8):
+    """Time to steady state of held-out lid-driven cavities (128 x 128, 64 half-range
+    velocities, Kn log-uniform in [0.01, 10], u_w in [0.005, 0.02]; residual 1e-8 checked
+    every 100 steps), one factor at a time:
+      fp64        plain FP64 march, instances one after another (graph-captured intervals);
+      fp32_dc     FP32 march + FP64-defect refinement, one after another;
+      batch_dc    all instances in one persistent batched FP32 sweep, then the refinement;
+      warm_dc     the same with the learned warm start (if a trained network is present).
+    Accuracy of every variant: max |u - u_fp64| / u_w over the instances."""
+    import numpy as np
     import torch
 
-    from paper_1308_0692_gb300 import lbm
+    from paper_1308_0692_gb300 import lbm, warmstart
+    pairs = warmstart.draw_pairs(count, seed=20130805)
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
-    prob = lbm.make_problem(1, 128, 128, 0.1, 0.0, 0.01, 0.9, lbm.LBM_FP64, 100)
-    stream = torch.cuda.Stream()
-    sim = lbm.lbm_init(vs, prob, None, stream=stream)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    steps = 0
-    r = math.inf
-    while steps < 400000:
-        lbm.lbm_step(sim, 100)
-        steps += 100
-        r, _ = lbm.lbm_residual(sim)
-        if r < 1e-8:
-            break
-    el = time.perf_counter() - t
-    sim.close()
-    return {"workload": "cavity 128x128, D2Q^h_64, Kn=0.1, lid 0.01, cold start",
-            "fp64": {"seconds": el, "steps": steps, "residual": r,
-                     "updates_per_s": 128 * 128 * 64 * steps / el}}
+    tol = 1e-8
+    out = {"workload": f"{count} lid-driven cavities 128x128, D2Q^h_64, Kn log-uniform [0.01,10], "
+                       f"u_w U(0.005,0.02), residual {tol:g}", "pairs": pairs}
+
+    def fields(sim):
+        m = lbm.lbm_moments(sim, wall_shear=False)
+        return m["ux"], m["uy"]
+
+    ref, t64, steps64 = [], 0.0, []
+    for kn, uw in pairs:
+        sim, info, el = warmstart.solve_cavity(vs, kn, uw, prec=lbm.LBM_FP64, tol=tol, refine=0)
+        t64 += el
+        steps64.append(info["steps"])
+        ref.append(fields(sim))
+        sim.close()
+    updates = float(sum(steps64)) * 128 * 128 * 64
+    out["fp64"] = {"seconds": t64, "steps": steps64, "updates_per_s": updates / t64}
+
+    def err(got, i):
+        ux, uy = got
+        return max(np.abs(ux - ref[i][0]).max(), np.abs(uy - ref[i][1]).max()) / pairs[i][1]
+
+    t32, e32, st32 = 0.0, 0.0, []
+    for i, (kn, uw) in enumerate(pairs):
+        sim, info, el = warmstart.solve_cavity(vs, kn, uw, prec=lbm.LBM_FP32_PERTURB, tol=tol, refine=3)
+        t32 += el
+        st32.append(info["steps"] + info["correction_steps"])
+        e32 = max(e32, err(fields(sim), i))
+        sim.close()
+    out["fp32_dc"] = {"seconds": t32, "steps": st32, "max_err_vs_fp64": e32, "speedup_vs_fp64": t64 / t32}
+
+    def batched(mlp):
+        b, steps, tb = warmstart.batch_solve(vs, pairs, tol, mlp=mlp)
+        sims, corr, tr = warmstart.refine_instances(vs, b, pairs, tol)
+        e = max(err(fields(s), i) for i, s in enumerate(sims))
+        for s in sims:
+            s.close()
+        b.close()
+        return {"seconds": tb + tr, "batch_seconds": tb, "refine_seconds": tr, "steps": steps.tolist(),
+                "refine_steps": corr.tolist(), "max_err_vs_fp64": e, "speedup_vs_fp64": t64 / (tb + tr)}
+
+    out["batch_dc"] = batched(None)
+    params = os.path.join(ROOT, "paper_1308_0692_gb300", "data", "warmstart_mlp.npy")
+    if os.path.exists(params):
+        mlp = warmstart.load_mlp(params)
+        out["warm_dc"] = batched(mlp)
+        mlp.close()
+    else:
+        out["warm_dc"] = None
+    return out
 
 
 # ---------------------------------------------------------------- CPU oracle arm
@@ -466,6 +545,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default=None, help="force the step kernel variant 'warps,loadpath'")
     ap.add_argument("--nx", type=int, default=None,
                     help="side of the cavity (default 2048); smaller sides are for profiling only")
     args = ap.parse_args(argv)

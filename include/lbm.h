@@ -129,10 +129,13 @@ typedef struct {
 
 /* March to the steady state: whole residual intervals (residual_every steps) until the
  * residual drops below tol or max_steps steps were taken (synchronises once per interval).
- * FP32 simulations may then apply refine_sweeps mixed-precision refinement sweeps: the
- * defect D = M(h) - h of the stored FP32 state under one FP64 step, a correction march
- * delta <- L(delta) + D of the homogeneous problem (walls without driving) in FP32 until
- * its per-step change is below 1e-2 * tol * ||h||, and h += delta; sweeps stop early once the
+ * Any march also stops when its residual has not improved by 1 % over 20 consecutive
+ * checks (the FP32 rounding floor of the per-step change, about 1e-8 of ||h|| on a 128^2
+ * cavity, lies above a 1e-8 target).  FP32 simulations may apply refine_sweeps
+ * mixed-precision refinement sweeps: the march then stops at max(tol, 1e-6), and each sweep
+ * takes the defect D = M(h) - h of the stored FP32 state under one FP64 step, marches the
+ * correction delta <- L(delta) + D of the homogeneous problem (walls without driving) in
+ * FP32 until its per-step change is below 0.1 * tol * ||h||, and adds h += delta; sweeps stop early once the
  * defect stops halving (FP32 rounding floor).  This removes the bias of the FP32 fixed
  * point (the FP32 operator's rounding amplified by the conditioning of the slow modes),
  * which plain FP32 storage cannot.  refine_sweeps must be 0 for FP64 simulations. */
@@ -243,6 +246,11 @@ lbm_status lbm_batch_tune(lbm_batch *b, int steps_per_trial, int *best_warps_per
  * residual, converged flag; its state as host FP64 [n][ny][nx]. */
 lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, int *converged);
 lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h);
+/* Initial state of instance i before the first lbm_batch_advance: host FP64 [n][ny][nx],
+ * or the warm start of a cavity instance from the network (see lbm_warm_start). */
+lbm_status lbm_batch_set_state(lbm_batch *b, int i, const double *h);
+typedef struct lbm_mlp lbm_mlp;
+lbm_status lbm_batch_warm_start(lbm_batch *b, int i, lbm_mlp *mlp, double kn, double u_w);
 /* Moments of instance i (as lbm_moments) into device FP64 [6][ny][nx]: rho, ux, uy, pxx,
  * pxy, pyy.  Stream-ordered. */
 lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev);
@@ -256,7 +264,6 @@ lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev);
  * Parameters are flattened as W1 [256][4], b1 [256], W2 [256][256], b2, W3, b3,
  * W4 [6][256], b4 [6] (row-major).  All x/t/y pointers are device FP32, row-major
  * [M][4] / [M][6]; work is ordered on the MLP's stream. */
-typedef struct lbm_mlp lbm_mlp;
 lbm_status lbm_mlp_param_count(long *count);
 lbm_status lbm_mlp_create(int max_batch, unsigned long long seed, void *stream, lbm_mlp **out);
 void lbm_mlp_destroy(lbm_mlp *mlp);

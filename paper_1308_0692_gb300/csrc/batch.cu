@@ -45,8 +45,10 @@ struct BatchArgs {
     void *buf[2];
     const BatchInst *inst;
     int ninst;
-    const int2 *items;     // (instance, segment)
+    const int2 *items;     // (instance, segment) of the wall-free segments
     int nitems;
+    const int2 *wall_items;  // (instance, segment) of the segments with a wall cell
+    int nwall;
     double *acc;           // [ninst][2] residual sums of the current interval
     double *last_r;        // [ninst]
     long *frozen;          // [ninst] step count at convergence (LONG_MAX while active)
@@ -96,187 +98,205 @@ __device__ bool grid_barrier(const BatchArgs &a)
 template <typename TC>
 __device__ __forceinline__ TC pk(const double *d, const float *f, int i) { return lbmk::pick<TC>(d, f, i); }
 
-template <typename TS, typename TC, int M, int G>
-__global__ void __launch_bounds__(lbmk::Shape<G>::THREADS) batch_kernel(const BatchArgs a)
+// One group of SPB segments (one per warp group of the block): transport, moments and
+// relaxation of every listed, unfrozen segment; WALLS selects the code path of segments
+// that contain wall cells (FP64 wall densities across rows and warps, ghosts in the
+// arithmetic type) -- separate from the lean wall-free path so that the latter keeps a
+// small register footprint.  All threads of the block call it together (shared-memory
+// exchanges inside).
+template <typename TS, typename TC, int M, int G, bool WALLS>
+__device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *items, long nitems, long grp,
+                                            long s, const TS *__restrict__ h, TS *__restrict__ hn, bool resid,
+                                            TC (&s_mom)[3][G][lbmk::Shape<G>::SPB][32],
+                                            double (&s_wall)[4][G][lbmk::Shape<G>::SPB][32])
 {
     constexpr int SPB = lbmk::Shape<G>::SPB;
-    constexpr int WARPS = lbmk::Shape<G>::WARPS;
     constexpr int RPL = M / G;
     constexpr int HALF = M / 2;
-    __shared__ TC s_mom[3][G][SPB][32];
-    __shared__ double s_wall[4][G][SPB][32];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sl = warp / G, g = warp - sl * G;
-    (void)WARPS;
+    const long item = grp * SPB + sl;
+    bool active = item < nitems;
+    int2 it = make_int2(0, 0);
+    if (active) it = items[item];
+    const BatchInst &I = a.inst[it.x];
+    if (active && a.frozen[it.x] <= s) active = false;
+    const long ncells = I.ncells;
+    const int nx = I.nx, ny = I.ny;
+    const bool cav = I.cavity != 0;
+    const long cell0 = (long)it.y * 32 + lane;
+    const bool in_grid = cell0 < ncells;
+    const long c = in_grid ? cell0 : ncells - 1;
+    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+    const bool valid = active && in_grid;
+    const TS *hi = h + I.off;
+    TS *hno = hn + I.off;
+    const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);
+    const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
+    const long c_below = (y > 0) ? c - nx : c;
+    const long c_above = (y < ny - 1) ? c + nx : c;
+    const bool wl = WALLS && cav && x == 0, wr = WALLS && cav && x == nx - 1;
+    const bool wb = WALLS && y == 0, wt = WALLS && y == ny - 1;
+
+    double rb = 0.0, rt = 0.0, rl = 0.0, rr = 0.0;
+    if (WALLS) {
+        // wall densities (Eq. 9): row sums in the arithmetic type, FP64 across rows and warps
+        double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int iy = g * RPL + r;
+                const double xiy = a.xi[iy];
+                TC rowsum = 0, left = 0, right = 0;
+#pragma unroll
+                for (int ix = 0; ix < M; ++ix) {
+                    const TC v = (TC)__ldg(hi + (long)(iy * M + ix) * ncells + c);
+                    rowsum += v;
+                    if (ix < HALF) left -= pk<TC>(a.xi, a.xi_f, ix) * v;
+                    if (ix >= M - HALF) right += pk<TC>(a.xi, a.xi_f, ix) * v;
+                }
+                if (xiy < 0.0) sb -= xiy * (double)rowsum;
+                if (xiy > 0.0) st += xiy * (double)rowsum;
+                sls += (double)left;
+                srs += (double)right;
+            }
+        }
+        s_wall[0][g][sl][lane] = sb;
+        s_wall[1][g][sl][lane] = st;
+        s_wall[2][g][sl][lane] = sls;
+        s_wall[3][g][sl][lane] = srs;
+        __syncthreads();
+        sb = st = sls = srs = 0.0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            sb += s_wall[0][q][sl][lane];
+            st += s_wall[1][q][sl][lane];
+            sls += s_wall[2][q][sl][lane];
+            srs += s_wall[3][q][sl][lane];
+        }
+        rb = sb * a.inv_dy_wall;
+        rt = st * a.inv_dy_wall;
+        rl = sls * a.inv_dx_wall;
+        rr = srs * a.inv_dx_wall;
+    }
+
+    TC hs[RPL * M];
+    TC rho = 0, jx = 0, jy = 0;
+    if (active) {
+        const TC cx = (TC)I.cx, cy = (TC)I.cy;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC xiy = pk<TC>(a.xi, a.xi_f, iy);
+            const TC nuy = (xiy < TC(0) ? -xiy : xiy) * cy;
+            const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
+            const long cy_idx = ypos ? c_below : (yneg ? c_above : c);
+            const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
+            const TC rho_y = (TC)(ypos ? rb : rt);
+            const TC u_y = (TC)(ypos ? I.u_bottom : I.u_top);
+            const TC drive_y = (TC)((ypos ? I.u_bottom : I.u_top) * I.inv_u_ref);
+            const TC wy = pk<TC>(a.w1, a.w1_f, iy);
+            const TC rl_t = (TC)rl, rr_t = (TC)rr;
+            TC R = 0, X = 0;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const TS *hp = hi + (long)(iy * M + ix) * ncells;
+                const TC hc = (TC)__ldg(hp + c);
+                const TC xix = pk<TC>(a.xi, a.xi_f, ix);
+                TC v = hc;
+                if (ix >= M - HALF || ix < HALF) {
+                    TC hx;
+                    if (WALLS && (ix >= M - HALF ? wl : wr))
+                        hx = pk<TC>(a.w1, a.w1_f, ix) * wy * (ix >= M - HALF ? rl_t : rr_t);
+                    else
+                        hx = (TC)__ldg(hp + (ix >= M - HALF ? c_left : c_right));
+                    v += (xix < TC(0) ? -xix : xix) * cx * (hx - hc);
+                }
+                TC hy;
+                if (WALLS && ywall)
+                    hy = pk<TC>(a.w1, a.w1_f, ix) * wy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y);
+                else
+                    hy = (TC)__ldg(hp + cy_idx);
+                v += nuy * (hy - hc);
+                hs[r * M + ix] = v;
+                R += v;
+                X += xix * v;
+            }
+            rho += R;
+            jx += X;
+            jy += xiy * R;
+        }
+    }
+    s_mom[0][g][sl][lane] = rho;
+    s_mom[1][g][sl][lane] = jx;
+    s_mom[2][g][sl][lane] = jy;
+    __syncthreads();
+    rho = jx = jy = 0;
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        rho += s_mom[0][q][sl][lane];
+        jx += s_mom[1][q][sl][lane];
+        jy += s_mom[2][q][sl][lane];
+    }
+
+    TC psd = 0, psn = 0;
+    if (active) {
+        const TC om = (TC)I.omega, b = (TC)I.b;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC wom = om * pk<TC>(a.w1, a.w1_f, iy);
+            const TC q = wom * (rho + pk<TC>(a.xi, a.xi_f, iy) * jy);
+            const TC jj = wom * jx;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const long off = (long)(iy * M + ix) * ncells + c;
+                const TC t = q + pk<TC>(a.xi, a.xi_f, ix) * jj;
+                const TC v = b * hs[r * M + ix] + pk<TC>(a.w1, a.w1_f, ix) * t;
+                if (resid) {
+                    const TC d = v - (TC)__ldg(hi + off);
+                    psd += d * d;
+                    psn += v * v;
+                }
+                if (valid) hno[off] = (TS)v;
+            }
+        }
+    }
+    if (resid && active) {
+        double dsd = valid ? (double)psd : 0.0, dsn = valid ? (double)psn : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dsd += __shfl_xor_sync(FULL, dsd, off);
+            dsn += __shfl_xor_sync(FULL, dsn, off);
+        }
+        if (lane == 0) {
+            atomicAdd(a.acc + 2 * it.x, dsd);
+            atomicAdd(a.acc + 2 * it.x + 1, dsn);
+        }
+    }
+    __syncthreads();   // shared arrays are reused by the next group
+}
+
+template <typename TS, typename TC, int M, int G>
+__global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const BatchArgs a)
+{
+    constexpr int SPB = lbmk::Shape<G>::SPB;
+    __shared__ TC s_mom[3][G][SPB][32];
+    __shared__ double s_wall[4][G][SPB][32];
 
     for (int si = 0; si < a.nsteps; ++si) {
         const long s = a.step0 + si;
         const TS *__restrict__ h = reinterpret_cast<const TS *>(a.buf[s & 1]);
         TS *__restrict__ hn = reinterpret_cast<TS *>(a.buf[(s + 1) & 1]);
         const bool resid = ((s + 1) % a.resid_every) == 0;
-        const long ngroups = ((long)a.nitems + SPB - 1) / SPB;
-        for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-            const long item = grp * SPB + sl;
-            bool active = item < a.nitems;
-            int2 it = make_int2(0, 0);
-            if (active) it = a.items[item];
-            const BatchInst &I = a.inst[it.x];
-            if (active && a.frozen[it.x] <= s) active = false;
-            const long ncells = I.ncells;
-            const int nx = I.nx, ny = I.ny;
-            const bool cav = I.cavity != 0;
-            const long cell0 = (long)it.y * 32 + lane;
-            const bool in_grid = cell0 < ncells;
-            const long c = in_grid ? cell0 : ncells - 1;
-            const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
-            const bool is_wall = in_grid && (y == 0 || y == ny - 1 || (cav && (x == 0 || x == nx - 1)));
-            const bool wall_seg = active && __any_sync(FULL, is_wall);
-            const bool valid = active && in_grid;
-            const TS *hi = h + I.off;
-            TS *hno = hn + I.off;
-            const bool wl = cav && x == 0, wr = cav && x == nx - 1, wb = y == 0, wt = y == ny - 1;
-            const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);
-            const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
-            const long c_below = (y > 0) ? c - nx : c;
-            const long c_above = (y < ny - 1) ? c + nx : c;
-
-            // wall densities (FP64, Eq. 9), summed across the G warps of the segment
-            double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
-            if (wall_seg) {
-#pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int iy = g * RPL + r;
-                    const double xiy = a.xi[iy];
-                    double rowsum = 0.0, left = 0.0, right = 0.0;
-#pragma unroll
-                    for (int ix = 0; ix < M; ++ix) {
-                        const double v = (double)__ldg(hi + (long)(iy * M + ix) * ncells + c);
-                        rowsum += v;
-                        if (ix < HALF) left -= a.xi[ix] * v;
-                        if (ix >= M - HALF) right += a.xi[ix] * v;
-                    }
-                    if (xiy < 0.0) sb -= xiy * rowsum;
-                    if (xiy > 0.0) st += xiy * rowsum;
-                    sls += left;
-                    srs += right;
-                }
-            }
-            s_wall[0][g][sl][lane] = sb;
-            s_wall[1][g][sl][lane] = st;
-            s_wall[2][g][sl][lane] = sls;
-            s_wall[3][g][sl][lane] = srs;
-            __syncthreads();
-            sb = st = sls = srs = 0.0;
-#pragma unroll
-            for (int q = 0; q < G; ++q) {
-                sb += s_wall[0][q][sl][lane];
-                st += s_wall[1][q][sl][lane];
-                sls += s_wall[2][q][sl][lane];
-                srs += s_wall[3][q][sl][lane];
-            }
-            const double rb = sb * a.inv_dy_wall, rt = st * a.inv_dy_wall;
-            const double rl = sls * a.inv_dx_wall, rr = srs * a.inv_dx_wall;
-
-            // transport + moment row sums.  Upwind values across a wall are the ghosts
-            // w_a [rho'_w (1 + xi_t U) + xi_t U / u_ref] (Eq. 8), evaluated in the
-            // arithmetic type from the FP64 wall densities and selected per lane, so wall
-            // and interior segments share one code path.
-            TC hs[RPL * M];
-            TC rho = 0, jx = 0, jy = 0;
-            if (active) {
-                const TC cx = (TC)I.cx, cy = (TC)I.cy;
-                const TC rl_t = (TC)rl, rr_t = (TC)rr;
-                const bool xw_l = wall_seg && wl, xw_r = wall_seg && wr;
-#pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int iy = g * RPL + r;
-                    const TC xiy = pk<TC>(a.xi, a.xi_f, iy);
-                    const TC nuy = (xiy < TC(0) ? -xiy : xiy) * cy;
-                    const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
-                    const long cy_idx = ypos ? c_below : (yneg ? c_above : c);
-                    const bool ywall = wall_seg && ((ypos && wb) || (yneg && wt));
-                    const TC rho_y = (TC)(ypos ? rb : rt);
-                    const TC u_y = (TC)(ypos ? I.u_bottom : I.u_top);
-                    const TC drive_y = (TC)((ypos ? I.u_bottom : I.u_top) * I.inv_u_ref);
-                    const TC wy = pk<TC>(a.w1, a.w1_f, iy);
-                    TC R = 0, X = 0;
-#pragma unroll
-                    for (int ix = 0; ix < M; ++ix) {
-                        const TS *hp = hi + (long)(iy * M + ix) * ncells;
-                        const TC hc = (TC)__ldg(hp + c);
-                        const TC xix = pk<TC>(a.xi, a.xi_f, ix);
-                        const TC wxy = pk<TC>(a.w1, a.w1_f, ix) * wy;
-                        TC v = hc;
-                        if (ix >= M - HALF || ix < HALF) {
-                            const bool right_side = ix < HALF;          // xi_x < 0: upwind is the right cell
-                            const TC hl = (TC)__ldg(hp + (right_side ? c_right : c_left));
-                            const bool xw = right_side ? xw_r : xw_l;
-                            const TC hx = xw ? wxy * (right_side ? rr_t : rl_t) : hl;
-                            v += (xix < TC(0) ? -xix : xix) * cx * (hx - hc);
-                        }
-                        const TC hl = (TC)__ldg(hp + cy_idx);
-                        const TC hy = ywall ? wxy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y) : hl;
-                        v += nuy * (hy - hc);
-                        hs[r * M + ix] = v;
-                        R += v;
-                        X += xix * v;
-                    }
-                    rho += R;
-                    jx += X;
-                    jy += xiy * R;
-                }
-            }
-            s_mom[0][g][sl][lane] = rho;
-            s_mom[1][g][sl][lane] = jx;
-            s_mom[2][g][sl][lane] = jy;
-            __syncthreads();
-            rho = jx = jy = 0;
-#pragma unroll
-            for (int q = 0; q < G; ++q) {
-                rho += s_mom[0][q][sl][lane];
-                jx += s_mom[1][q][sl][lane];
-                jy += s_mom[2][q][sl][lane];
-            }
-
-            // relaxation, store, residual sums
-            TC psd = 0, psn = 0;
-            if (active) {
-                const TC om = (TC)I.omega, b = (TC)I.b;
-#pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int iy = g * RPL + r;
-                    const TC wom = om * pk<TC>(a.w1, a.w1_f, iy);
-                    const TC q = wom * (rho + pk<TC>(a.xi, a.xi_f, iy) * jy);
-                    const TC jj = wom * jx;
-#pragma unroll
-                    for (int ix = 0; ix < M; ++ix) {
-                        const long off = (long)(iy * M + ix) * ncells + c;
-                        const TC t = q + pk<TC>(a.xi, a.xi_f, ix) * jj;
-                        const TC v = b * hs[r * M + ix] + pk<TC>(a.w1, a.w1_f, ix) * t;
-                        if (resid) {
-                            const TC d = v - (TC)__ldg(hi + off);
-                            psd += d * d;
-                            psn += v * v;
-                        }
-                        if (valid) hno[off] = (TS)v;
-                    }
-                }
-            }
-            if (resid && active) {
-                double dsd = valid ? (double)psd : 0.0, dsn = valid ? (double)psn : 0.0;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    dsd += __shfl_xor_sync(FULL, dsd, off);
-                    dsn += __shfl_xor_sync(FULL, dsn, off);
-                }
-                if (lane == 0) {
-                    atomicAdd(a.acc + 2 * it.x, dsd);
-                    atomicAdd(a.acc + 2 * it.x + 1, dsn);
-                }
-            }
-            __syncthreads();   // shared arrays are reused by the next group
-        }
+        // wall-free segments, then segments with wall cells, both round-robin over the blocks
+        const long nb = ((long)a.nitems + SPB - 1) / SPB;
+        for (long grp = blockIdx.x; grp < nb; grp += gridDim.x)
+            batch_group<TS, TC, M, G, false>(a, a.items, a.nitems, grp, s, h, hn, resid, s_mom, s_wall);
+        const long nw = ((long)a.nwall + SPB - 1) / SPB;
+        for (long grp = blockIdx.x; grp < nw; grp += gridDim.x)
+            batch_group<TS, TC, M, G, true>(a, a.wall_items, a.nwall, grp, s, h, hn, resid, s_mom, s_wall);
         if (!grid_barrier(a)) return;
         if (resid) {
             if (blockIdx.x == 0) {
@@ -375,8 +395,10 @@ struct lbm_batch {
     long *d_frozen;
     unsigned *d_bar;
     int *d_err;
+    double *d_tab;          // 1-D nodes [LBM_MAX_M] then weights [LBM_MAX_M]
+    float *d_scratch;       // warm start: features and predictions of one instance
     // schedule
-    int g, blocks_per_sm, order, nitems;
+    int g, blocks_per_sm, order, nitems, nwall;
     int grid;
     const Variant *var;
     long step;
@@ -422,31 +444,45 @@ void inst_coeffs(const lbm_problem &p, const std::vector<double> &nodes, BatchIn
     I.ncells = (long)p.nx * p.ny;
 }
 
-// Build the (instance, segment) list in one of three orders:
+// true if the 32-cell segment sg of instance I contains a wall-adjacent cell
+bool segment_has_wall(const BatchInst &I, int sg)
+{
+    for (long c = (long)sg * 32; c < std::min((long)sg * 32 + 32, I.ncells); ++c) {
+        const int y = (int)(c / I.nx), x = (int)(c % I.nx);
+        if (y == 0 || y == I.ny - 1 || (I.cavity && (x == 0 || x == I.nx - 1))) return true;
+    }
+    return false;
+}
+
+// Build the (instance, segment) lists (wall-free first list, wall second) in one of three
+// orders:
 //   0: instance by instance, in the given order;
 //   1: instances by decreasing size;
 //   2: segments interleaved round-robin across instances (largest first).
-std::vector<int2> build_items(const lbm_batch *b, int order)
+void build_items(const lbm_batch *b, int order, std::vector<int2> &bulk, std::vector<int2> &wall)
 {
     const int ni = (int)b->inst.size();
     std::vector<int> idx(ni);
     for (int i = 0; i < ni; ++i) idx[i] = i;
     if (order >= 1)
         std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return b->inst[p].ncells > b->inst[q].ncells; });
-    std::vector<int2> items;
+    bulk.clear();
+    wall.clear();
+    auto add = [&](int i, int sgm) {
+        (segment_has_wall(b->inst[i], sgm) ? wall : bulk).push_back(make_int2(i, sgm));
+    };
     if (order <= 1) {
         for (int i : idx) {
             const int nseg = (int)((b->inst[i].ncells + 31) / 32);
-            for (int sgm = 0; sgm < nseg; ++sgm) items.push_back(make_int2(i, sgm));
+            for (int sgm = 0; sgm < nseg; ++sgm) add(i, sgm);
         }
     } else {
         int maxseg = 0;
         for (int i : idx) maxseg = std::max(maxseg, (int)((b->inst[i].ncells + 31) / 32));
         for (int sgm = 0; sgm < maxseg; ++sgm)
             for (int i : idx)
-                if (sgm < (int)((b->inst[i].ncells + 31) / 32)) items.push_back(make_int2(i, sgm));
+                if (sgm < (int)((b->inst[i].ncells + 31) / 32)) add(i, sgm);
     }
-    return items;
 }
 
 lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
@@ -460,8 +496,12 @@ lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     if (maxb < 1) return bfail(LBM_EUNSUPPORTED, "batched kernel does not fit on an SM");
     if (bpsm < 1 || bpsm > maxb) bpsm = maxb;
-    std::vector<int2> items = build_items(b, order);
+    std::vector<int2> items, wall;
+    build_items(b, order, items, wall);
     e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !wall.empty())
+        e = cudaMemcpyAsync(b->d_items + items.size(), wall.data(), sizeof(int2) * wall.size(),
+                            cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("uploading the schedule: ") + cudaGetErrorString(e));
     if (b->graph_ok) cudaGraphExecDestroy(b->graph);
@@ -471,8 +511,9 @@ lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
     b->blocks_per_sm = bpsm;
     b->order = order;
     b->nitems = (int)items.size();
+    b->nwall = (int)wall.size();
     const int spb = segs_per_block(g);
-    const long groups = ((long)b->nitems + spb - 1) / spb;
+    const long groups = std::max(((long)b->nitems + spb - 1) / spb, ((long)b->nwall + spb - 1) / spb);
     b->grid = (int)std::min<long>((long)nsm * bpsm, std::max<long>(1, groups));
     return LBM_OK;
 }
@@ -487,6 +528,8 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     a.ninst = (int)b->inst.size();
     a.items = b->d_items;
     a.nitems = b->nitems;
+    a.wall_items = b->d_items + b->nitems;
+    a.nwall = b->nwall;
     a.acc = b->d_acc;
     a.last_r = b->d_last_r;
     a.frozen = b->d_frozen;
@@ -573,6 +616,10 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
     off = align256(off + sizeof(double) * count);
     off = align256(off + sizeof(long) * count);
     off = align256(off + 64);
+    off = align256(off + sizeof(double) * 2 * LBM_MAX_M);      // 1-D nodes and weights
+    long maxc = 0;
+    for (int i = 0; i < count; ++i) maxc = std::max(maxc, (long)insts[i].nx * insts[i].ny);
+    off = align256(off + 40 * (size_t)maxc);                    // warm-start scratch
     *prec = p0;
     *total_vals = vals;
     *total_segs = segs;
@@ -661,6 +708,10 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     o = align256(o + sizeof(long) * count);
     b->d_bar = (unsigned *)(p + o);
     b->d_err = (int *)(p + o + 16);
+    o = align256(o + 64);
+    b->d_tab = (double *)(p + o);
+    o = align256(o + sizeof(double) * 2 * LBM_MAX_M);
+    b->d_scratch = (float *)(p + o);
     std::vector<long> frozen(count, LONG_MAX);
     std::vector<double> last(count, INFINITY);
     cudaError_t e = cudaMemsetAsync(b->buf[0], 0, vals * es, b->stream);
@@ -670,6 +721,12 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_last_r, last.data(), sizeof(double) * count, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_frozen, frozen.data(), sizeof(long) * count, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 64, b->stream);
+    std::vector<double> tab(2 * LBM_MAX_M, 0.0);
+    for (int k = 0; k < m; ++k) {
+        tab[k] = b->nodes[k];
+        tab[LBM_MAX_M + k] = b->weights[k];
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         lbm_batch_destroy(b);
@@ -885,6 +942,40 @@ lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev)
     inst_moments_kernel<float><<<nb, 256, 0, b->stream>>>(h, I.ncells, b->m, a, 1.0 / I.inv_u_ref, out_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("instance moments: ") + cudaGetErrorString(e));
+}
+
+lbm_status lbm_batch_set_state(lbm_batch *b, int i, const double *h)
+{
+    if (!b || !h) return bfail(LBM_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
+    if (b->step != 0) return bfail(LBM_EINVAL, "initial states can be set before the first advance only");
+    const long n = (long)b->nv * b->inst[i].ncells;
+    std::vector<float> tmp(n);
+    for (long k = 0; k < n; ++k) tmp[k] = (float)h[k];
+    cudaError_t e = cudaMemcpyAsync((float *)b->buf[0] + b->inst[i].off, tmp.data(), sizeof(float) * n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("setting an instance state: ") + cudaGetErrorString(e));
+}
+
+lbm_status lbm_batch_warm_start(lbm_batch *b, int i, lbm_mlp *mlp, double kn, double u_w)
+{
+    if (!b || !mlp) return bfail(LBM_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
+    if (b->step != 0) return bfail(LBM_EINVAL, "initial states can be set before the first advance only");
+    const BatchInst &I = b->inst[i];
+    if (!I.cavity) return bfail(LBM_EINVAL, "the warm-start network is trained on cavities");
+    float *feat = b->d_scratch, *pred = b->d_scratch + 4 * I.ncells;
+    lbm_status st = lbm_mlp_features(mlp, I.nx, I.ny, kn, u_w, feat);
+    if (st == LBM_OK) st = lbm_mlp_forward(mlp, feat, (int)I.ncells, pred);
+    if (st != LBM_OK) return st;
+    // the MLP runs on its own stream: order the reconstruction after it
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = launch_warm_state(pred, I.ncells, b->m, b->d_tab, b->d_tab + LBM_MAX_M, u_w * I.inv_u_ref,
+                              (float *)b->buf[0] + I.off, LBM_FP32_PERTURB, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("warm start of an instance: ") + cudaGetErrorString(e));
 }
 
 lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h)

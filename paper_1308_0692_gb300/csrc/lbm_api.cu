@@ -21,6 +21,8 @@ cudaError_t launch_step_f64_large(int m, int g, int pf, bool resid, const StepAr
 cudaError_t launch_step_f32_small(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_step_f32_large(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t prepare_step_f32_tma(int m, int g);
 int defect_lanes(int m);
 int correct_lanes(int m);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
@@ -145,7 +147,7 @@ Layout make_layout(const lbm_vset *vs, const lbm_problem *p)
     L.off_partials = off;
     off = align256(off + sizeof(double) * 2 * nb);
     L.off_result = off;
-    off = align256(off + sizeof(double) * 8);
+    off = align256(off + sizeof(double) * 16);       // result[0..3], status word at result + 8
     L.off_moments = off;
     off = align256(off + sizeof(double) * 6 * ncells);
     L.off_fy = off;
@@ -257,6 +259,7 @@ void fill_args(lbm_sim *s, const TableHeader &hdr)
     const lbm_problem &p = s->prob;
     const lbm_vset &v = s->vs;
     a.partials = s->partials;
+    a.status = (int *)(s->result + 8);
     a.nx = p.nx;
     a.ny = p.ny;
     a.ncells = s->ncells;
@@ -383,6 +386,12 @@ bool step_supported(int prec, int m, int g, int pf)
 {
     static const int f64[][3] = {{3, 1, 0}, {4, 1, 0}, {4, 2, 0}, {6, 1, 0}, {6, 2, 0}, {4, 2, 1}, {6, 2, 1}, {8, 2, 0}, {8, 4, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {8, 4, 1}, {12, 6, 1}};
     static const int f32[][3] = {{3, 1, 0}, {4, 1, 0}, {6, 1, 0}, {6, 2, 0}, {8, 1, 0}, {8, 2, 0}, {8, 4, 0}, {8, 2, 1}, {8, 4, 1}, {12, 2, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {12, 3, 1}, {12, 4, 1}, {12, 6, 1}};
+    static const int tma[][2] = {{8, 2}, {8, 4}, {12, 3}, {12, 4}, {12, 6}};
+    if (pf == 2) {
+        if (prec != LBM_FP32_PERTURB) return false;
+        for (auto &v : tma) if (v[0] == m && v[1] == g) return true;
+        return false;
+    }
     if (prec == LBM_FP64) {
         for (auto &v : f64) if (v[0] == m && v[1] == g && v[2] == pf) return true;
     } else {
@@ -394,6 +403,7 @@ bool step_supported(int prec, int m, int g, int pf)
 cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s)
 {
+    if (pf == 2) return launch_step_f32_tma(m, g, resid, a, grid, s);
     if (prec == LBM_FP64)
         return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
                       : launch_step_f64_small(m, g, pf, resid, a, grid, s);
@@ -515,14 +525,14 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     TableHeader hdr;
     fill_tables(s, t64, t32, hdr);
     fill_args(s, hdr);
-    cudaError_t e = cudaMallocHost(&s->host_res, sizeof(double) * 8);
+    cudaError_t e = cudaMallocHost(&s->host_res, sizeof(double) * 16);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->tab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->tab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->hdr, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, sizeof(double) * 8, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, sizeof(double) * 16, s->stream);
     const size_t state_bytes = (size_t)s->nv * s->ncells * elem_size(prob->prec);
     if (e == cudaSuccess && !init_h) e = cudaMemsetAsync(s->buf[0], 0, state_bytes, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -656,7 +666,14 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
     lbm_solve_info out{};
     const long K = s->prob.residual_every;
     // --- the march: whole residual intervals until r < tol ---
-    double r = INFINITY;
+    // An FP32 march cannot push its per-step change below its rounding floor (~1e-8 of
+    // ||h|| on a 128^2 cavity): with refinement it stops at max(tol, 1e-6) and leaves the
+    // rest to the FP64 defect correction; in any precision it stops when the residual has
+    // not improved by 1 % over 20 consecutive checks (stagnation at the floor).
+    const bool fp32_refined = refine_sweeps > 0;
+    const double tol_march = fp32_refined ? std::fmax(tol, 1e-6) : tol;
+    double r = INFINITY, best = INFINITY;
+    int flat = 0;
     long taken = 0;
     while (taken < max_steps) {
         const long todo = K - (s->step % K);
@@ -666,7 +683,13 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
         long rs;
         st = lbm_residual(s, &r, &rs);
         if (st != LBM_OK) return st;
-        if (r < tol) break;
+        if (r < tol_march) break;
+        if (r < 0.99 * best) {
+            best = r;
+            flat = 0;
+        } else if (++flat >= 20) {
+            break;
+        }
     }
     out.steps = taken;
     out.residual = r;
@@ -693,6 +716,8 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
             a.src = D;
             a.homogeneous = 1;
             long k = 0;
+            double cbest = INFINITY;
+            int cflat = 0;
             while (k < max_steps) {
                 for (long j = 1; j <= K; ++j) {
                     a.h = C[cc];
@@ -706,9 +731,16 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
                 double rr[4];
                 st = read_result(s, rr);
                 if (st != LBM_OK) return st;
-                // change per step relative to ||h||, 100x below tol: the correction's own error
+                // change per step relative to ||h||, 10x below tol: the correction's own error
                 // is its per-step change times the conditioning of the slow modes (~1e3)
-                if (std::sqrt(rr[0]) < 1e-2 * tol * hnorm) break;
+                const double change = std::sqrt(rr[0]) / hnorm;
+                if (change < 1e-1 * tol) break;
+                if (change < 0.99 * cbest) {
+                    cbest = change;
+                    cflat = 0;
+                } else if (++cflat >= 20) {
+                    break;
+                }
             }
             out.correction_steps += k;
             e = launch_add_f32((float *)H, (const float *)C[cc], (long)s->nv * s->ncells, s->stream);
@@ -732,10 +764,15 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
     if (s->prob.geom != LBM_CAVITY) return fail(LBM_EINVAL, "the warm-start network is trained on cavities");
     float *feat = (float *)s->moments;                  // scratch: 16 B + 24 B per cell <= 48 B
     float *pred = feat + 4 * s->ncells;
+    // the network runs on its own stream: its inputs/outputs live in this sim's scratch
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "warm start");
     lbm_status st = lbm_mlp_features(mlp, s->prob.nx, s->prob.ny, kn, u_w, feat);
     if (st == LBM_OK) st = lbm_mlp_forward(mlp, feat, (int)s->ncells, pred);
     if (st != LBM_OK) return st;
-    cudaError_t e = launch_warm_state(pred, s->ncells, s->vs.m, s->hdr->xi1, s->hdr->w1, u_w / s->u_ref,
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "warm start");
+    e = launch_warm_state(pred, s->ncells, s->vs.m, s->hdr->xi1, s->hdr->w1, u_w / s->u_ref,
                                       s->buf[s->cur], s->prob.prec, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the warm-start state");
@@ -744,10 +781,17 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch ? 1 : 0))
+    if (prefetch < 0 || prefetch > 2) return fail(LBM_EINVAL, "prefetch must be 0, 1 or 2");
+    if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
         return fail(LBM_EUNSUPPORTED, "no step kernel with %d warps per segment (prefetch %d) for M = %d",
-                    warps_per_segment, prefetch ? 1 : 0, s->vs.m);
-    s->prefetch = prefetch ? 1 : 0;
+                    warps_per_segment, prefetch, s->vs.m);
+    if (prefetch == 2 && (s->prob.geom != LBM_CAVITY || s->prob.nx % 4 != 0 || s->ncells % 4 != 0))
+        return fail(LBM_EUNSUPPORTED, "TMA staging needs a cavity with nx and the cell count multiples of 4");
+    if (prefetch == 2) {
+        cudaError_t e = prepare_step_f32_tma(s->vs.m, warps_per_segment);
+        if (e != cudaSuccess) return cuda_fail(e, "enabling the TMA kernel's shared memory");
+    }
+    s->prefetch = prefetch;
     return set_lanes(s, warps_per_segment);
 }
 
@@ -762,10 +806,13 @@ lbm_status lbm_get_variant(const lbm_sim *s, int *warps_per_segment, int *prefet
 lbm_status lbm_residual(lbm_sim *s, double *r, long *step)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    cudaError_t e = cudaMemcpyAsync(s->host_res, s->result, sizeof(double) * 4,
+    cudaError_t e = cudaMemcpyAsync(s->host_res, s->result, sizeof(double) * 9,
                                     cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "reading the residual");
+    int status;
+    std::memcpy(&status, s->host_res + 8, sizeof status);
+    if (status != 0) return fail(LBM_ETIMEOUT, "a device-side wait of the step kernel gave up");
     if (r) *r = s->resid_step < 0 ? INFINITY : s->host_res[2];
     if (step) *step = s->resid_step;
     if (s->resid_step >= 0 && s->host_res[3] != 0.0)

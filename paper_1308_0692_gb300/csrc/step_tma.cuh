@@ -1,0 +1,260 @@
+// Bulk (wall-free) segments of the fused step with TMA staging of the upwind halo
+// (sm_103a): the same arithmetic as the bulk path of step_kernel.cuh, but every warp first
+// has the Tensor Memory Accelerator copy, with 1-D bulk asynchronous copies
+// (cp.async.bulk ... mbarrier::complete_tx), all the data its velocity rows need into
+// shared memory: per velocity the own-cell line widened by 4 cells on each side (the x
+// upwind neighbours, 160 bytes) and the upwind y-neighbour line (128 bytes).  The copies
+// hold no registers while in flight, so a warp keeps ~10 KB of loads outstanding instead
+// of the few lines its registers allow, which is what the memory system needs to stay
+// busy (the register-staged kernel was latency bound: long-scoreboard stalls, DRAM at
+// half its peak).  The warp then waits on its mbarrier (a bounded wait: after the limit
+// it sets the status word, waits again for its copies and skips the segment), computes
+// from shared memory, and stores with ordinary coalesced stores.
+//
+// Requirements (checked by the host): number of cells and nx multiples of 4, so that
+// every copied line starts on a 16-byte boundary; wall segments (and therefore the
+// first and last segments of the grid) are left to the wall kernel.
+#pragma once
+
+#include <cstdint>
+
+#include "step_kernel.cuh"
+
+namespace lbmk {
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_addr(bar)), "r"(phase)
+                 : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst_smem)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// wait for phase 0 of the warp's barrier, at most ~limit_cycles; false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, long long limit_cycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, 0)) {
+        if (clock64() - t0 > limit_cycles) return false;
+    }
+    return true;
+}
+
+template <int M, int G>
+struct TmaShape {
+    static constexpr int RPL = M / G;
+    static constexpr int NV = RPL * M;               // velocities per warp
+    static constexpr int CEN = 40;                   // floats per own-cell line (32 + 4 + 4)
+    static constexpr int YN = 32;                    // floats per y-neighbour line
+    static constexpr int WARP_FLOATS = NV * (CEN + YN);
+    static constexpr int BYTES_PER_WARP = WARP_FLOATS * 4;
+    static constexpr int SMEM = Shape<G>::WARPS * BYTES_PER_WARP + Shape<G>::WARPS * 8 + 16;
+};
+
+template <int M, int G, bool RESID>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepArgs a)
+{
+    using TC = float;
+    constexpr int SPB = Shape<G>::SPB;
+    constexpr int WARPS = Shape<G>::WARPS;
+    constexpr int RPL = M / G;
+    constexpr int HALF = M / 2;
+    constexpr int NVW = TmaShape<M, G>::NV;
+    constexpr int CEN = TmaShape<M, G>::CEN, YN = TmaShape<M, G>::YN;
+    static_assert(M % 2 == 0, "TMA path: even number of nodes per axis (no zero velocity)");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ TC s_mom[3][G][SPB][32];
+    __shared__ double s_red[2][WARPS];
+
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl = warp / G, g = warp - sl * G;
+    const long ncells = a.ncells;
+    const int nx = a.nx, ny = a.ny;
+    float *cen = reinterpret_cast<float *>(smem_raw) + (long)warp * TmaShape<M, G>::WARP_FLOATS;
+    float *yn = cen + NVW * CEN;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + WARPS * TmaShape<M, G>::BYTES_PER_WARP) + warp;
+
+    const long seg = (long)blockIdx.x * SPB + sl;
+    const bool active = seg * 32 < ncells;
+    const long c0 = seg * 32;
+    const long cell0 = c0 + lane;
+    const bool in_grid = cell0 < ncells;
+    const long c = in_grid ? cell0 : ncells - 1;
+    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+    const bool cav = a.cavity != 0;
+    const bool is_wall = in_grid && (y == 0 || y == ny - 1 || (cav && (x == 0 || x == nx - 1)));
+    const bool work = active && !__any_sync(FULL, is_wall);
+    const bool valid = work && in_grid;
+    const float *__restrict__ h = reinterpret_cast<const float *>(a.h);
+
+    // ---- issue the warp's bulk copies ----
+    bool ok = true;
+    if (work) {
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            mbar_arrive_expect(bar, (unsigned)(NVW * (CEN + YN) * 4));
+        }
+        __syncwarp();
+        for (int k = lane; k < NVW; k += 32) {
+            const int r = k / M, ix = k - r * M;
+            const int iy = g * RPL + r;
+            const float *plane = h + (long)(iy * M + ix) * ncells;
+            bulk_copy(cen + k * CEN, plane + c0 - 4, CEN * 4, bar);
+            const long ylin = (iy < HALF) ? c0 + nx : c0 - nx;      // upwind y row
+            bulk_copy(yn + k * YN, plane + ylin, YN * 4, bar);
+        }
+        if (!mbar_wait_bounded(bar, 2000000000LL)) {
+            ok = false;
+            if (lane == 0) atomicExch(a.status, 1);
+            mbar_wait_bounded(bar, 2000000000LL);   // let the copies land before leaving
+        }
+        __syncwarp();
+    }
+    const bool compute = work && ok;
+
+    // ---- transport + moment row sums from shared memory ----
+    TC hs[RPL * M];
+    TC rho = 0, jx = 0, jy = 0;
+    if (compute) {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC xiy = a.xi_f[iy];
+            const TC nuy = a.nuy_f[iy];
+            TC R = 0, X = 0;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const int k = r * M + ix;
+                const TC hc = cen[k * CEN + 4 + lane];
+                const TC hx = (ix >= M - HALF) ? cen[k * CEN + 3 + lane] : cen[k * CEN + 5 + lane];
+                const TC hy = yn[k * YN + lane];
+                TC v = hc + a.nux_f[ix] * (hx - hc);
+                v += nuy * (hy - hc);
+                hs[k] = v;
+                R += v;
+                X += a.xi_f[ix] * v;
+            }
+            rho += R;
+            jx += X;
+            jy += xiy * R;
+        }
+    }
+    if (G > 1) {
+        s_mom[0][g][sl][lane] = rho;
+        s_mom[1][g][sl][lane] = jx;
+        s_mom[2][g][sl][lane] = jy;
+        __syncthreads();
+        rho = jx = jy = 0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            rho += s_mom[0][q][sl][lane];
+            jx += s_mom[1][q][sl][lane];
+            jy += s_mom[2][q][sl][lane];
+        }
+    }
+
+    // ---- relaxation, store, residual ----
+    TC psd = 0, psn = 0;
+    if (compute) {
+        const TC b = a.b_f, om = a.omega_f;
+        float *__restrict__ hn = reinterpret_cast<float *>(a.hn);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC wom = om * a.w1_f[iy];
+            const TC q = wom * (rho + a.xi_f[iy] * jy);
+            const TC jj = wom * jx;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const int k = r * M + ix;
+                const TC t = q + a.xi_f[ix] * jj;
+                const TC v = b * hs[k] + a.w1_f[ix] * t;
+                if (RESID) {
+                    const TC d = v - cen[k * CEN + 4 + lane];
+                    psd += d * d;
+                    psn += v * v;
+                }
+                if (valid) hn[(long)(iy * M + ix) * ncells + c] = v;
+            }
+        }
+    }
+
+    if (RESID) {
+        double sd = (valid && compute) ? (double)psd : 0.0, sn = (valid && compute) ? (double)psn : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sd += __shfl_xor_sync(FULL, sd, off);
+            sn += __shfl_xor_sync(FULL, sn, off);
+        }
+        if (lane == 0) {
+            s_red[0][warp] = sd;
+            s_red[1][warp] = sn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double td = 0.0, tn = 0.0;
+            for (int wi = 0; wi < WARPS; ++wi) {
+                td += s_red[0][wi];
+                tn += s_red[1][wi];
+            }
+            a.partials[2 * blockIdx.x] = td;
+            a.partials[2 * blockIdx.x + 1] = tn;
+        }
+    }
+}
+
+// Opt the kernels into their dynamic shared memory (once per process, before any launch
+// or stream capture: lbm_set_variant calls it).
+template <int M, int G>
+cudaError_t prepare_tma()
+{
+    constexpr int SMEM = TmaShape<M, G>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<M, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_tma_kernel<M, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    return e;
+}
+
+// TMA bulk kernel, then the (register-staged) wall kernel over the wall segments.
+template <int M, int G, bool RESID>
+cudaError_t launch_tma(const StepArgs &a, int grid, cudaStream_t s)
+{
+    constexpr int T = Shape<G>::THREADS;
+    constexpr int SMEM = TmaShape<M, G>::SMEM;
+    step_tma_kernel<M, G, RESID><<<grid, T, SMEM, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.n_wall_segs == 0) return e;
+    StepArgs b = a;
+    b.partials_offset = grid;
+    const int wgrid = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
+    step_kernel<float, float, M, G, RESID, false, false, true, false><<<wgrid, T, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -94,6 +94,8 @@ def _load():
         "lbm_batch_get_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_batch_reset": (st, [_vp]),
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
+        "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
+        "lbm_batch_warm_start": (st, [_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double]),
         "lbm_batch_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int), _dp]),
         "lbm_mlp_param_count": (st, [ctypes.POINTER(ctypes.c_long)]),
@@ -397,6 +399,15 @@ def lbm_batch_get_state(b: Batch, i: int) -> np.ndarray:
 
 def lbm_batch_moments(b: Batch, i: int, out_ptr: int):
     _check(_load().lbm_batch_moments(b.handle, int(i), out_ptr))
+
+
+def lbm_batch_set_state(b: Batch, i: int, h: np.ndarray):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    _check(_load().lbm_batch_set_state(b.handle, int(i), _ptr(h)))
+
+
+def lbm_batch_warm_start(b: Batch, i: int, m, kn: float, u_w: float):
+    _check(_load().lbm_batch_warm_start(b.handle, int(i), m.handle, float(kn), float(u_w)))
 
 
 def lbm_batch_reset(b: Batch):

@@ -129,3 +129,124 @@ def solve_cavity(vs, kn, uw, side=128, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refi
     info = lbm.lbm_solve(sim, tol, 2_000_000, refine if prec == lbm.LBM_FP32_PERTURB else 0)
     torch.cuda.synchronize()
     return sim, info, time.perf_counter() - t0
+
+
+def save_params(mlp, path):
+    np.save(path, lbm.lbm_mlp_get_params(mlp))
+
+
+def load_mlp(path, max_batch=128 * 128):
+    m = lbm.lbm_mlp_create(max_batch, seed=0)
+    lbm.lbm_mlp_set_params(m, np.load(path))
+    return m
+
+
+def batch_solve(vs, pairs, tol, side=128, mlp=None, steps_per_launch=500, max_steps=1_000_000):
+    """March all pairs as one batch (cold or warm start) to max(tol, 1e-6) -- the FP32 march's
+    share of a refined solve (see lbm_solve); returns (batch, steps per instance, seconds).
+    The warm-start reconstruction is included in the time."""
+    tol = max(tol, 1e-6)
+    import torch
+    probs = [lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
+                              residual_every=100) for kn, uw in pairs]
+    b = lbm.lbm_batch_init(vs, probs, stream=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if mlp is not None:
+        for i, (kn, uw) in enumerate(pairs):
+            lbm.lbm_batch_warm_start(b, i, mlp, kn, uw)
+    done = 0
+    while done < max_steps:
+        lbm.lbm_batch_advance(b, steps_per_launch, tol)
+        done += steps_per_launch
+        if lbm.lbm_batch_poll(b)[0] == 0:
+            break
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    steps = np.array([lbm.lbm_batch_status(b, i)["steps"] for i in range(len(pairs))])
+    return b, steps, el
+
+
+def refine_instances(vs, b, pairs, tol, side=128):
+    """Mixed-precision refinement of each converged batch instance (FP64 defect, FP32
+    correction march) in a single-simulation object; returns (sims, correction steps, seconds)."""
+    import torch
+    sims, corr = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, (kn, uw) in enumerate(pairs):
+        prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
+                                residual_every=100)
+        sim = lbm.lbm_init(vs, prob, lbm.lbm_batch_get_state(b, i), stream=torch.cuda.Stream())
+        info = lbm.lbm_solve(sim, tol, 1_000_000, 3)
+        corr.append(info["steps"] + info["correction_steps"])
+        sims.append(sim)
+    torch.cuda.synchronize()
+    return sims, np.array(corr), time.perf_counter() - t0
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import os
+    ap = argparse.ArgumentParser(description="train / evaluate the warm-start network")
+    ap.add_argument("cmd", choices=["train", "evaluate"])
+    ap.add_argument("--train-count", type=int, default=4096)
+    ap.add_argument("--test-count", type=int, default=256)
+    ap.add_argument("--train-seed", type=int, default=BATCH_SEED + 1)
+    ap.add_argument("--test-seed", type=int, default=BATCH_SEED + 2)
+    ap.add_argument("--gen-tol", type=float, default=1e-6)
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--params", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                                                     "warmstart_mlp.npy"))
+    ap.add_argument("--accuracy-count", type=int, default=16)
+    ap.add_argument("--out", default=None, help="write a JSON report here")
+    args = ap.parse_args(argv)
+    report = {}
+    if args.cmd == "train":
+        pairs = draw_pairs(args.train_count, args.train_seed)
+        t0 = time.perf_counter()
+        targets, steps = generate(pairs, tol=args.gen_tol)
+        t_gen = time.perf_counter() - t0
+        feats = features(pairs)
+        mlp, hist, t_train = train(feats, targets, steps=args.train_steps)
+        os.makedirs(os.path.dirname(args.params), exist_ok=True)
+        save_params(mlp, args.params)
+        report = {"train_count": len(pairs), "gen_tol": args.gen_tol, "gen_seconds": t_gen,
+                  "gen_steps_mean": float(steps.mean()), "gen_steps_max": int(steps.max()),
+                  "train_steps": args.train_steps, "train_seconds": t_train, "loss_history": hist}
+    else:
+        import torch
+        vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+        pairs = draw_pairs(args.test_count, args.test_seed)
+        mlp = load_mlp(args.params)
+        bc, cold_steps, t_cold = batch_solve(vs, pairs, args.tol)
+        bw, warm_steps, t_warm = batch_solve(vs, pairs, args.tol, mlp=mlp)
+        sub = list(range(min(args.accuracy_count, len(pairs))))
+        sims_w, corr_w, t_ref_w = refine_instances(vs, bw, [pairs[i] for i in sub], args.tol)
+        errs = []
+        for k, i in enumerate(sub):
+            kn, uw = pairs[i]
+            s64, info64, _ = solve_cavity(vs, kn, uw, prec=lbm.LBM_FP64, tol=1e-11, refine=0)
+            m64 = lbm.lbm_moments(s64)
+            mw = lbm.lbm_moments(sims_w[k])
+            errs.append(max(np.abs(mw[q] - m64[q]).max() for q in ("ux", "uy")) / uw)
+            s64.close()
+        report = {"test_count": len(pairs), "tol": args.tol,
+                  "cold": {"seconds": t_cold, "steps_mean": float(cold_steps.mean()),
+                           "steps_median": float(np.median(cold_steps))},
+                  "warm": {"seconds": t_warm, "steps_mean": float(warm_steps.mean()),
+                           "steps_median": float(np.median(warm_steps))},
+                  "steps_ratio_mean": float(np.mean(cold_steps / np.maximum(warm_steps, 1))),
+                  "accuracy_subset": len(sub), "max_velocity_error_vs_fp64": float(max(errs)),
+                  "refine_seconds_subset": t_ref_w}
+    print(json.dumps(report), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(report, f, indent=1)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -229,3 +229,39 @@ def _host_state_for(p, seed, prec):
     if prec == lbm.LBM_FP32_PERTURB:
         h = h.astype(np.float32).astype(np.float64)
     return h
+
+
+@pytest.mark.parametrize("n_half,nx,ny,variants", [
+    (4, 68, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2)]),
+    (6, 64, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2)]),
+])
+def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
+    """Every kernel variant (warps per segment; register, prefetched or TMA-staged loads) gives
+    the oracle's result to FP32 accuracy, and variants with the same warps per segment agree
+    to within a few FP32 roundings (same arithmetic, only the load path differs)."""
+    p = oracle_problem("half", n_half, CAVITY, nx, ny, 0.1, 0.0, 0.01)
+    h0 = random_state(p.n, p.ncells, seed=31).astype(np.float32).astype(np.float64)
+    ref = p.step(h0, 4)
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    by_g = {}
+    for g, pf in variants:
+        sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB,
+                                                residual_every=2), h0, stream=torch.cuda.Stream())
+        lbm.lbm_set_variant(sim, g, pf)
+        lbm.lbm_step(sim, 4)
+        got = lbm.lbm_get_state(sim)
+        r, st = lbm.lbm_residual(sim)
+        assert st == 4 and np.isfinite(r)
+        assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * 4 * np.abs(ref).max(), (g, pf)
+        if g in by_g:
+            assert np.abs(got - by_g[g]).max() <= 1e-6 * np.abs(ref).max(), (g, pf)
+        else:
+            by_g[g] = got
+
+
+def test_tma_variant_rejected_where_lines_are_unaligned():
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 37, 29, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_set_variant(sim, 2, 2)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
