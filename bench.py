@@ -387,7 +387,7 @@ def run_fp64_same_workload(vs, dist):
             "note": "FP64 storage+arithmetic; bounded by the FP64 pipe of GB300, not HBM"}
 
 
-def run_time_to_residual(dist, count=8):
+def run_time_to_residual(dist, count=32):
     """Time to steady state of held-out lid-driven cavities (128 x 128, 64 half-range
     velocities, Kn log-uniform in [0.01, 10], u_w in [0.005, 0.02]; residual 1e-8 checked
     every 100 steps), one factor at a time:

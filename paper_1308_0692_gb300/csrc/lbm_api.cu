@@ -370,6 +370,9 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     s->grid = grid_for(s->ncells, lanes);
     s->args.wall_segs = s->wall_segs;
     s->args.n_wall_segs = (int)segs.size();
+    // one merged launch when wall segments are more than a tenth of all segments
+    const long nseg_total = (s->ncells + 31) / 32;
+    s->args.merged = (long)segs.size() * 10 > nseg_total ? 1 : 0;
     s->nparts_step = s->grid + wall_grid(lanes, (int)segs.size());
     return LBM_OK;
 }

@@ -67,7 +67,7 @@ struct Shape {
 
 template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT, bool PART,
           bool PF = false>
-__global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs a)
+__device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
 {
     constexpr int SPB = Shape<G>::SPB;
     constexpr int WARPS = Shape<G>::WARPS;
@@ -89,11 +89,11 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
     long seg;
     bool active;
     if (PART) {
-        const long k = (long)blockIdx.x * SPB + sl;
+        const long k = (long)bid * SPB + sl;
         active = k < a.n_wall_segs;
         seg = active ? a.wall_segs[k] : 0;
     } else {
-        seg = (long)blockIdx.x * SPB + sl;
+        seg = (long)bid * SPB + sl;
         active = seg * 32 < ncells;
     }
     const long cell0 = seg * 32 + lane;
@@ -311,11 +311,31 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs 
                 td += s_red[0][wi];
                 tn += s_red[1][wi];
             }
-            const long slot = (PART ? a.partials_offset : 0) + blockIdx.x;
+            const long slot = (PART ? a.partials_offset : 0) + bid;
             a.partials[2 * slot] = td;
             a.partials[2 * slot + 1] = tn;
         }
     }
+}
+
+template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT, bool PART,
+          bool PF = false>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel(const StepArgs a)
+{
+    step_body<TS, TC, M, G, RESID, SOURCE, DEFECT, PART, PF>(a, blockIdx.x);
+}
+
+// Bulk and wall segments in one launch: blocks [0, bulk_blocks) take the wall-free
+// segments, the rest the wall segments (block-uniform branch).  Used when wall segments
+// are a large share of the grid (small grids), where two serialised launches would leave
+// the GPU half idle.
+template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_kernel_merged(const StepArgs a)
+{
+    if ((int)blockIdx.x < a.bulk_blocks)
+        step_body<TS, TC, M, G, RESID, SOURCE, DEFECT, false, false>(a, blockIdx.x);
+    else
+        step_body<TS, TC, M, G, RESID, SOURCE, DEFECT, true, false>(a, blockIdx.x - a.bulk_blocks);
 }
 
 // Bulk kernel over `grid` blocks, then the wall kernel over the listed wall segments.
@@ -324,6 +344,14 @@ template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool 
 cudaError_t launch_one(const StepArgs &a, int grid, cudaStream_t s)
 {
     constexpr int T = Shape<G>::THREADS;
+    if (a.merged && !PF) {
+        StepArgs b = a;
+        b.partials_offset = grid;
+        b.bulk_blocks = grid;
+        const int wgrid = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
+        step_kernel_merged<TS, TC, M, G, RESID, SOURCE, DEFECT><<<grid + wgrid, T, 0, s>>>(b);
+        return cudaGetLastError();
+    }
     step_kernel<TS, TC, M, G, RESID, SOURCE, DEFECT, false, PF><<<grid, T, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_wall_segs == 0) return e;

@@ -139,7 +139,12 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepA
     const bool compute = work && ok;
 
     // ---- transport + moment row sums from shared memory ----
-    TC hs[RPL * M];
+    // Velocities are processed in pairs (ix, ix+1) with the packed FP32x2 instructions of
+    // sm_100+ (one FFMA2 does two updates), which halves the arithmetic instructions of this
+    // issue-bound kernel.  Transport in the form (1 - nu_x - nu_y) h + nu_x h_x + nu_y h_y.
+    // A pair never straddles the sign change of xi_x (M/2 is even for M = 8, 12).
+    static_assert((M / 2) % 2 == 0, "velocity pairs must not straddle xi_x = 0");
+    float2 hs[RPL * M / 2];
     TC rho = 0, jx = 0, jy = 0;
     if (compute) {
 #pragma unroll
@@ -147,19 +152,26 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepA
             const int iy = g * RPL + r;
             const TC xiy = a.xi_f[iy];
             const TC nuy = a.nuy_f[iy];
-            TC R = 0, X = 0;
+            const float2 nuy2 = make_float2(nuy, nuy);
+            float2 R2 = make_float2(0.f, 0.f), X2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int ix = 0; ix < M; ++ix) {
+            for (int pp = 0; pp < M / 2; ++pp) {
+                const int ix = 2 * pp;
                 const int k = r * M + ix;
-                const TC hc = cen[k * CEN + 4 + lane];
-                const TC hx = (ix >= M - HALF) ? cen[k * CEN + 3 + lane] : cen[k * CEN + 5 + lane];
-                const TC hy = yn[k * YN + lane];
-                TC v = hc + a.nux_f[ix] * (hx - hc);
-                v += nuy * (hy - hc);
-                hs[k] = v;
-                R += v;
-                X += a.xi_f[ix] * v;
+                const int sx = (ix >= M - HALF) ? 3 : 5;          // upwind x neighbour in the line
+                const float2 hc = make_float2(cen[k * CEN + 4 + lane], cen[(k + 1) * CEN + 4 + lane]);
+                const float2 hx = make_float2(cen[k * CEN + sx + lane], cen[(k + 1) * CEN + sx + lane]);
+                const float2 hy = make_float2(yn[k * YN + lane], yn[(k + 1) * YN + lane]);
+                const float2 nux = make_float2(a.nux_f[ix], a.nux_f[ix + 1]);
+                const float2 a0 = make_float2(1.f - a.nux_f[ix] - nuy, 1.f - a.nux_f[ix + 1] - nuy);
+                float2 v = __fmul2_rn(a0, hc);
+                v = __ffma2_rn(nux, hx, v);
+                v = __ffma2_rn(nuy2, hy, v);
+                hs[r * (M / 2) + pp] = v;
+                R2 = __fadd2_rn(R2, v);
+                X2 = __ffma2_rn(make_float2(a.xi_f[ix], a.xi_f[ix + 1]), v, X2);
             }
+            const TC R = R2.x + R2.y, X = X2.x + X2.y;
             rho += R;
             jx += X;
             jy += xiy * R;
@@ -182,27 +194,39 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepA
     // ---- relaxation, store, residual ----
     TC psd = 0, psn = 0;
     if (compute) {
-        const TC b = a.b_f, om = a.omega_f;
+        const float2 b2 = make_float2(a.b_f, a.b_f);
+        const TC om = a.omega_f;
         float *__restrict__ hn = reinterpret_cast<float *>(a.hn);
+        float2 psd2 = make_float2(0.f, 0.f), psn2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
             const TC wom = om * a.w1_f[iy];
             const TC q = wom * (rho + a.xi_f[iy] * jy);
             const TC jj = wom * jx;
+            const float2 q2 = make_float2(q, q), jj2 = make_float2(jj, jj);
+            float *rowp = hn + (long)(iy * M) * ncells + c;
 #pragma unroll
-            for (int ix = 0; ix < M; ++ix) {
+            for (int pp = 0; pp < M / 2; ++pp) {
+                const int ix = 2 * pp;
                 const int k = r * M + ix;
-                const TC t = q + a.xi_f[ix] * jj;
-                const TC v = b * hs[k] + a.w1_f[ix] * t;
+                const float2 t = __ffma2_rn(make_float2(a.xi_f[ix], a.xi_f[ix + 1]), jj2, q2);
+                const float2 v = __ffma2_rn(make_float2(a.w1_f[ix], a.w1_f[ix + 1]), t,
+                                            __fmul2_rn(b2, hs[r * (M / 2) + pp]));
                 if (RESID) {
-                    const TC d = v - cen[k * CEN + 4 + lane];
-                    psd += d * d;
-                    psn += v * v;
+                    const float2 hc = make_float2(cen[k * CEN + 4 + lane], cen[(k + 1) * CEN + 4 + lane]);
+                    const float2 d = __fadd2_rn(v, make_float2(-hc.x, -hc.y));
+                    psd2 = __ffma2_rn(d, d, psd2);
+                    psn2 = __ffma2_rn(v, v, psn2);
                 }
-                if (valid) hn[(long)(iy * M + ix) * ncells + c] = v;
+                if (valid) {
+                    rowp[(long)ix * ncells] = v.x;
+                    rowp[(long)(ix + 1) * ncells] = v.y;
+                }
             }
         }
+        psd = psd2.x + psd2.y;
+        psn = psn2.x + psn2.y;
     }
 
     if (RESID) {

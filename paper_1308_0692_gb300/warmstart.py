@@ -167,20 +167,28 @@ def batch_solve(vs, pairs, tol, side=128, mlp=None, steps_per_launch=500, max_st
     return b, steps, el
 
 
-def refine_instances(vs, b, pairs, tol, side=128):
+def refine_instances(vs, b, pairs, tol, side=128, threads=32):
     """Mixed-precision refinement of each converged batch instance (FP64 defect, FP32
-    correction march) in a single-simulation object; returns (sims, correction steps, seconds)."""
+    correction march) in single-simulation objects, each on its own stream and driven by
+    its own host thread so that the instances' small kernels run concurrently; returns
+    (sims, march + correction steps, seconds)."""
+    import concurrent.futures as cf
+
     import torch
-    sims, corr = [], []
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    sims = []
     for i, (kn, uw) in enumerate(pairs):
         prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
                                 residual_every=100)
-        sim = lbm.lbm_init(vs, prob, lbm.lbm_batch_get_state(b, i), stream=torch.cuda.Stream())
+        sims.append(lbm.lbm_init(vs, prob, lbm.lbm_batch_get_state(b, i), stream=torch.cuda.Stream()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+
+    def one(sim):
         info = lbm.lbm_solve(sim, tol, 1_000_000, 3)
-        corr.append(info["steps"] + info["correction_steps"])
-        sims.append(sim)
+        return info["steps"] + info["correction_steps"]
+
+    with cf.ThreadPoolExecutor(max_workers=min(threads, len(sims))) as ex:
+        corr = list(ex.map(one, sims))
     torch.cuda.synchronize()
     return sims, np.array(corr), time.perf_counter() - t0
 
