@@ -135,21 +135,24 @@ typedef struct {
  * mixed-precision refinement sweeps: the march then stops at max(tol, 1e-6), and each sweep
  * takes the defect D = M(h) - h of the stored FP32 state under one FP64 step, marches the
  * correction delta <- L(delta) + D of the homogeneous problem (walls without driving) in
- * FP32 until its per-step change is below 0.1 * tol * ||h||, and adds h += delta; sweeps stop early once the
+ * FP32 until its per-step change is below refine_tol * ||h|| (refine_tol <= 0: 0.1 * tol),
+ * and adds h += delta; sweeps stop early once the
  * defect stops halving (FP32 rounding floor).  This removes the bias of the FP32 fixed
  * point (the FP32 operator's rounding amplified by the conditioning of the slow modes),
  * which plain FP32 storage cannot.  refine_sweeps must be 0 for FP64 simulations. */
-lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps,
+lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps, double refine_tol,
                      lbm_solve_info *info);
 
 /* Kernel variant: the number of warps that share one 32-cell segment (1, 2, 3, 4 or 6
- * dividing M; each warp owns M/warps velocity rows), and prefetch (0/1): the bulk kernel
- * issues all own-cell and y-neighbour loads of a warp before its arithmetic.  It changes
- * speed, not results beyond rounding order.
+ * dividing M; each warp owns M/warps velocity rows), and the load path of the wall-free
+ * segments: 0 registers, 1 registers with all loads issued ahead of the arithmetic,
+ * 2 TMA (bulk asynchronous copies into shared memory, FP32 cavities with nx and the cell
+ * count multiples of 4, M = 8 or 12), 3 as 2 with the wall segments in the same launch.
+ * It changes speed, not results beyond rounding order.
  * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
  * without a compiled kernel.  Used by the autotuner.  Call between steps only. */
-lbm_status lbm_set_variant(lbm_sim *sim, int warps_per_segment, int prefetch);
-lbm_status lbm_get_variant(const lbm_sim *sim, int *warps_per_segment, int *prefetch);
+lbm_status lbm_set_variant(lbm_sim *sim, int warps_per_segment, int load_path);
+lbm_status lbm_get_variant(const lbm_sim *sim, int *warps_per_segment, int *load_path);
 
 /* Latest relative residual r and the step count at which it was evaluated
  * (synchronises).  LBM_ENONFINITE if the state contains NaN/Inf. */

@@ -21,7 +21,8 @@ cudaError_t launch_step_f64_large(int m, int g, int pf, bool resid, const StepAr
 cudaError_t launch_step_f32_small(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_step_f32_large(int m, int g, int pf, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s,
+                               bool merged);
 cudaError_t prepare_step_f32_tma(int m, int g);
 int defect_lanes(int m);
 int correct_lanes(int m);
@@ -390,7 +391,7 @@ bool step_supported(int prec, int m, int g, int pf)
     static const int f64[][3] = {{3, 1, 0}, {4, 1, 0}, {4, 2, 0}, {6, 1, 0}, {6, 2, 0}, {4, 2, 1}, {6, 2, 1}, {8, 2, 0}, {8, 4, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {8, 4, 1}, {12, 6, 1}};
     static const int f32[][3] = {{3, 1, 0}, {4, 1, 0}, {6, 1, 0}, {6, 2, 0}, {8, 1, 0}, {8, 2, 0}, {8, 4, 0}, {8, 2, 1}, {8, 4, 1}, {12, 2, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {12, 3, 1}, {12, 4, 1}, {12, 6, 1}};
     static const int tma[][2] = {{8, 2}, {8, 4}, {12, 3}, {12, 4}, {12, 6}};
-    if (pf == 2) {
+    if (pf == 2 || pf == 3) {
         if (prec != LBM_FP32_PERTURB) return false;
         for (auto &v : tma) if (v[0] == m && v[1] == g) return true;
         return false;
@@ -406,7 +407,7 @@ bool step_supported(int prec, int m, int g, int pf)
 cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepArgs &a, int grid,
                         cudaStream_t s)
 {
-    if (pf == 2) return launch_step_f32_tma(m, g, resid, a, grid, s);
+    if (pf == 2 || pf == 3) return launch_step_f32_tma(m, g, resid, a, grid, s, pf == 3);
     if (prec == LBM_FP64)
         return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
                       : launch_step_f64_small(m, g, pf, resid, a, grid, s);
@@ -660,7 +661,8 @@ lbm_status defect_pass(lbm_sim *s, void *H, void *D, double *dsum, double *nsum)
 
 }  // namespace
 
-lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, lbm_solve_info *info)
+lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, double refine_tol,
+                     lbm_solve_info *info)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (!(tol > 0) || max_steps < 0 || refine_sweeps < 0) return fail(LBM_EINVAL, "invalid solve arguments");
@@ -708,6 +710,7 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
         const double hnorm = std::sqrt(nsum);
         const int g = correct_lanes(s->vs.m);
         const int grid = grid_for(s->ncells, g), nparts = nparts_for(s, g);
+        const double ctol = refine_tol > 0 ? refine_tol : 0.1 * tol;
         const size_t state_bytes = (size_t)s->nv * s->ncells * sizeof(float);
         for (int sw = 0; sw < refine_sweeps && r64 >= tol * 1e-2 && hnorm > 0; ++sw) {
             // correction march delta <- L(delta) + D from delta = 0 (homogeneous walls)
@@ -737,7 +740,7 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
                 // change per step relative to ||h||, 10x below tol: the correction's own error
                 // is its per-step change times the conditioning of the slow modes (~1e3)
                 const double change = std::sqrt(rr[0]) / hnorm;
-                if (change < 1e-1 * tol) break;
+                if (change < ctol) break;
                 if (change < 0.99 * cbest) {
                     cbest = change;
                     cflat = 0;
@@ -784,13 +787,13 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (prefetch < 0 || prefetch > 2) return fail(LBM_EINVAL, "prefetch must be 0, 1 or 2");
+    if (prefetch < 0 || prefetch > 3) return fail(LBM_EINVAL, "load path must be 0, 1, 2 or 3");
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
         return fail(LBM_EUNSUPPORTED, "no step kernel with %d warps per segment (prefetch %d) for M = %d",
                     warps_per_segment, prefetch, s->vs.m);
-    if (prefetch == 2 && (s->prob.geom != LBM_CAVITY || s->prob.nx % 4 != 0 || s->ncells % 4 != 0))
+    if (prefetch >= 2 && (s->prob.geom != LBM_CAVITY || s->prob.nx % 4 != 0 || s->ncells % 4 != 0))
         return fail(LBM_EUNSUPPORTED, "TMA staging needs a cavity with nx and the cell count multiples of 4");
-    if (prefetch == 2) {
+    if (prefetch >= 2) {
         cudaError_t e = prepare_step_f32_tma(s->vs.m, warps_per_segment);
         if (e != cudaSuccess) return cuda_fail(e, "enabling the TMA kernel's shared memory");
     }

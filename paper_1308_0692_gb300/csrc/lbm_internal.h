@@ -50,6 +50,7 @@ struct StepArgs {
     int *status;          // set to 1 by a device-side wait that gave up
     int merged;           // bulk and wall segments in one launch
     int bulk_blocks;      // merged launch: blocks taking the wall-free segments
+    int wall_blocks;      // merged TMA launch: leading blocks taking the wall segments
     // 1-D tables over the M nodes of one axis (velocity a = iy*M + ix)
     double xi[LBM_MAX_M];   // nodes
     double nux[LBM_MAX_M];  // |xi| dt / dx (0 for a single periodic Couette column)

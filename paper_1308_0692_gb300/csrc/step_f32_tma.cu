@@ -4,10 +4,11 @@
 
 using namespace lbmk;
 
-cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s,
+                               bool merged)
 {
 #define LBM_TMA(M_, G_) \
-    if (m == M_ && g == G_) return resid ? launch_tma<M_, G_, true>(a, grid, s) : launch_tma<M_, G_, false>(a, grid, s);
+    if (m == M_ && g == G_) return resid ? launch_tma<M_, G_, true>(a, grid, s, merged) : launch_tma<M_, G_, false>(a, grid, s, merged);
     LBM_TMA(8, 2)
     LBM_TMA(8, 4)
     LBM_TMA(12, 3)

@@ -75,7 +75,7 @@ struct TmaShape {
 };
 
 template <int M, int G, bool RESID>
-__global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepArgs a)
+__device__ __forceinline__ void tma_body(const StepArgs &a, const int bid)
 {
     using TC = float;
     constexpr int SPB = Shape<G>::SPB;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepA
     float *yn = cen + NVW * CEN;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + WARPS * TmaShape<M, G>::BYTES_PER_WARP) + warp;
 
-    const long seg = (long)blockIdx.x * SPB + sl;
+    const long seg = (long)bid * SPB + sl;
     const bool active = seg * 32 < ncells;
     const long c0 = seg * 32;
     const long cell0 = c0 + lane;
@@ -247,10 +247,28 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepA
                 td += s_red[0][wi];
                 tn += s_red[1][wi];
             }
-            a.partials[2 * blockIdx.x] = td;
-            a.partials[2 * blockIdx.x + 1] = tn;
+            a.partials[2 * bid] = td;
+            a.partials[2 * bid + 1] = tn;
         }
     }
+}
+
+template <int M, int G, bool RESID>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_kernel(const StepArgs a)
+{
+    tma_body<M, G, RESID>(a, blockIdx.x);
+}
+
+// One launch for the whole step: the wall segments first (blocks [0, wall_blocks), the
+// register-staged wall path), then the TMA-staged wall-free segments, so that the wall
+// work overlaps the bulk instead of following it in a second launch.
+template <int M, int G, bool RESID>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_tma_merged_kernel(const StepArgs a)
+{
+    if ((int)blockIdx.x < a.wall_blocks)
+        step_body<float, float, M, G, RESID, false, false, true, false>(a, blockIdx.x);
+    else
+        tma_body<M, G, RESID>(a, blockIdx.x - a.wall_blocks);
 }
 
 // Opt the kernels into their dynamic shared memory (once per process, before any launch
@@ -262,15 +280,26 @@ cudaError_t prepare_tma()
     cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<M, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(step_tma_kernel<M, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_tma_merged_kernel<M, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_tma_merged_kernel<M, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     return e;
 }
 
 // TMA bulk kernel, then the (register-staged) wall kernel over the wall segments.
 template <int M, int G, bool RESID>
-cudaError_t launch_tma(const StepArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_tma(const StepArgs &a, int grid, cudaStream_t s, bool merged)
 {
     constexpr int T = Shape<G>::THREADS;
     constexpr int SMEM = TmaShape<M, G>::SMEM;
+    if (merged && a.n_wall_segs > 0) {
+        StepArgs b = a;
+        b.partials_offset = grid;        // wall partials after the bulk blocks' slots
+        b.wall_blocks = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
+        step_tma_merged_kernel<M, G, RESID><<<grid + b.wall_blocks, T, SMEM, s>>>(b);
+        return cudaGetLastError();
+    }
     step_tma_kernel<M, G, RESID><<<grid, T, SMEM, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_wall_segs == 0) return e;

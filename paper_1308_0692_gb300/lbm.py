@@ -70,7 +70,8 @@ def _load():
         "lbm_step": (st, [_vp, ctypes.c_long]),
         "lbm_residual": (st, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
         "lbm_set_variant": (st, [_vp, ctypes.c_int, ctypes.c_int]),
-        "lbm_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.POINTER(lbm_solve_info)]),
+        "lbm_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.c_double,
+                           ctypes.POINTER(lbm_solve_info)]),
         "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
@@ -235,9 +236,10 @@ def lbm_step(sim: Sim, nsteps: int):
     _check(_load().lbm_step(sim.handle, int(nsteps)))
 
 
-def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0) -> dict:
+def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0, refine_tol: float = 0.0) -> dict:
     info = lbm_solve_info()
-    _check(_load().lbm_solve(sim.handle, float(tol), int(max_steps), int(refine_sweeps), ctypes.byref(info)))
+    _check(_load().lbm_solve(sim.handle, float(tol), int(max_steps), int(refine_sweeps), float(refine_tol),
+                             ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in lbm_solve_info._fields_}
 
 

@@ -1,0 +1,134 @@
+"""Batched parameter sweep: 512 seed-drawn independent instances (256 Couette channels with
+ny uniform in {64..512}, 256 lid-driven cavities with side in {64, 96, 128, 192, 256}; Kn
+log-uniform in [0.01, 10], u_w uniform in [0.005, 0.02]; 64 half-range velocities) marched
+together in the persistent batched FP32 kernel with an autotuned schedule, refined with the
+FP64 defect correction, and each instance's error reported against an FP64 steady state
+(the FP64 GPU march, whose steps are parity-checked against the CPU oracle; every Couette
+channel, and the cavities up to a size limit).
+
+    python -m paper_1308_0692_gb300.sweep [--count 512] [--out report.json]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import time
+
+import numpy as np
+
+from . import lbm
+from .inputs import BATCH_SEED, batch_table
+
+
+def _problem(inst, prec):
+    geom = lbm.LBM_COUETTE if inst["geom"] == "couette" else lbm.LBM_CAVITY
+    if geom == lbm.LBM_COUETTE:   # plates +u_w at y = 0 and -u_w at y = 1
+        return lbm.make_problem(geom, 1, inst["ny"], inst["kn"], inst["u_w"], -inst["u_w"], prec=prec,
+                                residual_every=100)
+    return lbm.make_problem(geom, inst["nx"], inst["ny"], inst["kn"], 0.0, inst["u_w"], prec=prec,
+                            residual_every=100)
+
+
+def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=32, log=print):
+    import torch
+    table = batch_table(count, seed)
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    probs = [_problem(t, lbm.LBM_FP32_PERTURB) for t in table]
+    unknowns = sum(p.nx * p.ny for p in probs) * 64
+    b = lbm.lbm_batch_init(vs, probs, stream=torch.cuda.Stream())
+    t0 = time.perf_counter()
+    best = lbm.lbm_batch_tune(b, 10)
+    t_tune = time.perf_counter() - t0
+    log(f"sweep: {count} instances, {unknowns / 1e6:.1f} M unknowns, schedule {best} (tuned in {t_tune:.1f} s)")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tol32 = max(tol, 1e-6)
+    steps_done = 0
+    while True:
+        lbm.lbm_batch_advance(b, 1000, tol32)
+        steps_done += 1000
+        n_active, _ = lbm.lbm_batch_poll(b)
+        if n_active == 0 or steps_done >= 2_000_000:
+            break
+    t_batch = time.perf_counter() - t0
+    steps = np.array([lbm.lbm_batch_status(b, i)["steps"] for i in range(count)])
+    cells = np.array([p.nx * p.ny for p in probs])
+    log(f"sweep: FP32 batch march to {tol32:g} in {t_batch:.1f} s ({steps_done} steps launched, "
+        f"{(steps * cells * 64).sum() / t_batch / 1e9:.1f} G updates/s on active instances)")
+
+    # refinement of every instance, one stream and host thread each
+    sims = []
+    for i, p in enumerate(probs):
+        sims.append(lbm.lbm_init(vs, p, lbm.lbm_batch_get_state(b, i), stream=torch.cuda.Stream()))
+    b.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+
+    def refine(sim):
+        info = lbm.lbm_solve(sim, tol, 2_000_000, 3, tol)
+        return info["correction_steps"], info["defect"]
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        ref_info = list(ex.map(refine, sims))
+    torch.cuda.synchronize()
+    t_refine = time.perf_counter() - t0
+    log(f"sweep: refinement of all instances in {t_refine:.1f} s")
+
+    # FP64 references (GPU march), concurrently
+    idx = [i for i, p in enumerate(probs) if p.nx * p.ny <= ref_max_cells]
+
+    def reference(i):
+        p64 = _problem(table[i], lbm.LBM_FP64)
+        s64 = lbm.lbm_init(vs, p64, stream=torch.cuda.Stream())
+        lbm.lbm_solve(s64, tol * 1e-2, 5_000_000, 0)
+        m = lbm.lbm_moments(s64)
+        s64.close()
+        return m
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        refs = dict(zip(idx, ex.map(reference, idx)))
+    t_ref = time.perf_counter() - t0
+    errs = {}
+    for i in idx:
+        m32 = lbm.lbm_moments(sims[i])
+        m64 = refs[i]
+        uw = table[i]["u_w"]
+        errs[i] = {"u": float(max(np.abs(m32["ux"] - m64["ux"]).max(), np.abs(m32["uy"] - m64["uy"]).max()) / uw),
+                   "wall_shear": float(np.abs(m32["wall_shear"] - m64["wall_shear"]).max()
+                                       / max(np.abs(m64["wall_shear"]).max(), 1e-300))}
+    for s in sims:
+        s.close()
+    report = {
+        "count": count, "seed": seed, "unknowns": int(unknowns), "schedule": best, "tune_seconds": t_tune,
+        "batch_seconds": t_batch, "refine_seconds": t_refine, "reference_seconds": t_ref,
+        "steps_min": int(steps.min()), "steps_median": float(np.median(steps)), "steps_max": int(steps.max()),
+        "instances_checked": len(errs),
+        "max_velocity_error": max(e["u"] for e in errs.values()),
+        "max_wall_shear_error": max(e["wall_shear"] for e in errs.values()),
+        "per_instance": [{**table[i], "steps": int(steps[i]), "correction_steps": int(ref_info[i][0]),
+                          "defect": float(ref_info[i][1]), **({"err": errs[i]} if i in errs else {})}
+                         for i in range(count)],
+    }
+    return report
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--ref-max-cells", type=int, default=128 * 128)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    rep = run(args.count, tol=args.tol, ref_max_cells=args.ref_max_cells)
+    short = {k: v for k, v in rep.items() if k != "per_instance"}
+    print(json.dumps(short), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(rep, f, indent=1)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -117,7 +117,8 @@ def train(feats, targets, steps=20000, batch_rows=8192, lr=1e-3, lr_final=1e-5, 
     return mlp, hist, time.perf_counter() - t0
 
 
-def solve_cavity(vs, kn, uw, side=128, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refine=3, mlp=None, stream=None):
+def solve_cavity(vs, kn, uw, side=128, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refine=3, mlp=None, stream=None,
+                 refine_tol=0.0):
     """Solve one cavity to tol (cold start or warm start); returns (sim, info, seconds)."""
     import torch
     prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=prec, residual_every=100)
@@ -126,7 +127,7 @@ def solve_cavity(vs, kn, uw, side=128, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refi
     t0 = time.perf_counter()
     if mlp is not None:
         lbm.lbm_warm_start(sim, mlp, kn, uw)
-    info = lbm.lbm_solve(sim, tol, 2_000_000, refine if prec == lbm.LBM_FP32_PERTURB else 0)
+    info = lbm.lbm_solve(sim, tol, 2_000_000, refine if prec == lbm.LBM_FP32_PERTURB else 0, refine_tol)
     torch.cuda.synchronize()
     return sim, info, time.perf_counter() - t0
 
@@ -167,7 +168,7 @@ def batch_solve(vs, pairs, tol, side=128, mlp=None, steps_per_launch=500, max_st
     return b, steps, el
 
 
-def refine_instances(vs, b, pairs, tol, side=128, threads=32):
+def refine_instances(vs, b, pairs, tol, side=128, threads=32, refine_tol=0.0):
     """Mixed-precision refinement of each converged batch instance (FP64 defect, FP32
     correction march) in single-simulation objects, each on its own stream and driven by
     its own host thread so that the instances' small kernels run concurrently; returns
@@ -184,7 +185,7 @@ def refine_instances(vs, b, pairs, tol, side=128, threads=32):
     t0 = time.perf_counter()
 
     def one(sim):
-        info = lbm.lbm_solve(sim, tol, 1_000_000, 3)
+        info = lbm.lbm_solve(sim, tol, 1_000_000, 3, refine_tol)
         return info["steps"] + info["correction_steps"]
 
     with cf.ThreadPoolExecutor(max_workers=min(threads, len(sims))) as ex:

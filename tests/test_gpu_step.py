@@ -232,8 +232,8 @@ def _host_state_for(p, seed, prec):
 
 
 @pytest.mark.parametrize("n_half,nx,ny,variants", [
-    (4, 68, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2)]),
-    (6, 64, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2)]),
+    (4, 68, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2), (2, 3), (4, 3)]),
+    (6, 64, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2), (3, 3), (6, 3)]),
 ])
 def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
     """Every kernel variant (warps per segment; register, prefetched or TMA-staged loads) gives
