@@ -185,7 +185,7 @@ def _traffic_record(kernel_key: str):
     if not rec:
         return None
     h = hashlib.sha256()
-    for name in ("step_kernel.cuh", "step_tma.cuh"):
+    for name in ("step_kernel.cuh", "step_tma.cuh", "step_march.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1308_0692_gb300", "csrc", name), "rb").read())
     digest = h.hexdigest()[:16]
     if rec.get("source_sha256_16") != digest:
@@ -193,12 +193,15 @@ def _traffic_record(kernel_key: str):
     return rec.get("dram_bytes_per_launch")
 
 
-VARIANTS = [(4, 0), (6, 0), (4, 2), (6, 2), (4, 3), (6, 3)]
+VARIANTS = [(4, 0), (6, 0), (4, 2), (6, 2), (4, 3), (6, 3), (6, 4), (6, 5), (12, 4), (12, 5)]
+LOAD_PATHS = ["registers", "prefetch", "tma", "tma+walls merged", "column march (4 row slots)",
+              "column march (5 row slots)"]
 
 
 def choose_variant(sim, stream, args):
     """Autotune the step kernel on the workload itself: warps per segment x load path
-    (0 registers, 2 TMA-staged halo), a few timed steps each; or the forced --variant."""
+    (0 registers, 2 TMA-staged halo, 3 the same with the walls in one launch, 4/5 the
+    TMA column march), a few timed steps each; or the forced --variant."""
     import torch
 
     from paper_1308_0692_gb300 import lbm
@@ -286,7 +289,8 @@ def run_own(args, dist: Dist):
     peak, peak_kind = _peaks()
     achieved = algo_bytes / avg / 1e9
     n_resid = len(resid)
-    launches = args.steps + n_resid        # step kernels + residual finalisations
+    per_step = 1 if variant[1] == 3 else 2  # interior and wall kernels (one merged launch for path 3)
+    launches = args.steps * per_step + n_resid   # + residual finalisations
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
@@ -296,14 +300,14 @@ def run_own(args, dist: Dist):
                                "Kn=0.05, lid u=0.01, FP32 perturbation storage, FP64 residual every 10 steps",
                    "nx": w["nx"], "ny": w["ny"], "velocities": n_vel, "unknowns": units_per_step,
                    "residual_every": w["residual_every"], "cold_start": True,
-                   "variant": {"warps_per_segment": variant[0], "load_path": ["registers", "prefetch", "tma", "tma+walls merged"][variant[1]],
+                   "variant": {"warps_per_segment": variant[0], "load_path": LOAD_PATHS[variant[1]],
                                "autotune_ms_per_step": tuning},
                    "l2": f"inputs larger than L2 ({units_per_step * 4 / 1e9:.2f} GB per state copy), no flush",
                    "parallelism": f"replicas{dist.world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": f"fused step (bulk + wall launches), {variant[0]} warps/segment, "
-                               f"{['register', 'prefetch', 'TMA', 'TMA (walls merged)'][variant[1]]} loads",
+                     "kernel": f"fused step (interior + wall launches), {variant[0]} warps/segment, "
+                               f"{LOAD_PATHS[variant[1]]} loads",
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": avg * 1e3,
                      "traffic": _traffic_record(f"step_f32_m12_g{variant[0]}_pf{variant[1]}")},
@@ -427,7 +431,7 @@ def run_time_to_residual(dist, count=32):
     sims64 = []
     for kn, uw in pairs:
         prob = lbm.make_problem(lbm.LBM_CAVITY, 128, 128, kn, 0.0, uw, prec=lbm.LBM_FP64, residual_every=100)
-        sims64.append(lbm.lbm_init(vs, prob, stream=torch.cuda.Stream()))
+        sims64.append(lbm.lbm_init(vs, prob, stream=lbm.PrivateStream()))
     torch.cuda.synchronize()
     tc0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=count) as ex:

@@ -147,7 +147,11 @@ lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps
  * dividing M; each warp owns M/warps velocity rows), and the load path of the wall-free
  * segments: 0 registers, 1 registers with all loads issued ahead of the arithmetic,
  * 2 TMA (bulk asynchronous copies into shared memory, FP32 cavities with nx and the cell
- * count multiples of 4, M = 8 or 12), 3 as 2 with the wall segments in the same launch.
+ * count multiples of 4, M = 8 or 12), 3 as 2 with the wall segments in the same launch,
+ * 4 and 5 the interior as a column march (persistent blocks march 64-cell strips row by
+ * row, each row's lines copied once by TMA into a ring of 4 (path 4) or 5 (path 5) row
+ * slots; FP32 cavities with nx a multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12
+ * warps, M = 8 with 2 or 4 warps (path 5)).
  * It changes speed, not results beyond rounding order.
  * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
  * without a compiled kernel.  Used by the autotuner.  Call between steps only. */
@@ -287,6 +291,14 @@ lbm_status lbm_mlp_features(lbm_mlp *mlp, int nx, int ny, double kn, double u_w,
  *   h_a = w_a [rho' + xi_a . j' + 1/2 sum_ij (P'_ij - rho' delta_ij)(xi_i xi_j - delta_ij)].
  * The network's max_batch must cover nx*ny.  Synchronises. */
 lbm_status lbm_warm_start(lbm_sim *sim, lbm_mlp *mlp, double kn, double u_w);
+
+/* A non-blocking CUDA stream owned by the caller, created and destroyed through the library
+ * (no counterpart in the paper: plumbing for callers whose stream sources are pooled, so
+ * that concurrent simulations driven from several host threads get streams of their own).
+ * lbm_stream_create writes the cudaStream_t to *stream; lbm_stream_destroy synchronises
+ * and destroys it (NULL is ignored). */
+lbm_status lbm_stream_create(void **stream);
+void lbm_stream_destroy(void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *lbm_last_error(void);

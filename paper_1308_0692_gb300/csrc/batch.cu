@@ -405,6 +405,7 @@ struct lbm_batch {
     int resid_every;
     cudaGraphExec_t graph;
     bool graph_ok;
+    cudaStream_t cap_stream;   // private capture stream (created on first use)
     long long timeout_cycles;
 };
 
@@ -560,14 +561,14 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     return a;
 }
 
-cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a)
+cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a, cudaStream_t st)
 {
     void *args[] = {(void *)&a};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(b->grid);
     cfg.blockDim = dim3(b->var->threads);
-    cfg.stream = b->stream;
+    cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -679,6 +680,7 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     b->step = 0;
     b->resid_every = insts[0].residual_every;
     b->graph_ok = false;
+    b->cap_stream = nullptr;
     b->timeout_cycles = 4000000000LL;   // about 2 s at the GB300 SM clock
     if (b->owns) {
         cudaError_t e = cudaMalloc(&b->base, bytes);
@@ -747,6 +749,7 @@ void lbm_batch_destroy(lbm_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->owns && b->base) cudaFree(b->base);
     delete b;
 }
@@ -783,14 +786,18 @@ lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol)
     BatchArgs a = make_args(b, nsteps, tol);
     cudaError_t e;
     // the graph holds the launch arguments by value: re-capture whenever they change
-    // (the start step does; so the captured graph covers whole blocks of nsteps steps from
-    // an even start, replayed with the start step patched through a kernel-node update)
+    // (the start step does; the executable graph is updated in place).  The capture runs
+    // on a stream private to the batch (a caller's stream may be shared with other
+    // threads, whose work would otherwise land in the graph); the launch on the caller's.
     if (b->stream) {
         cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        e = cudaSuccess;
+        if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) b->cap_stream = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = launch_batch(b, a);
-            e = cudaStreamEndCapture(b->stream, &g);
+            cudaError_t e2 = launch_batch(b, a, b->cap_stream);
+            e = cudaStreamEndCapture(b->cap_stream, &g);
             if (e2 != cudaSuccess) e = e2;
         }
         if (e == cudaSuccess) {
@@ -811,10 +818,10 @@ lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol)
         if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
         if (e != cudaSuccess) {        // fall back to a direct cooperative launch
             cudaGetLastError();
-            e = launch_batch(b, a);
+            e = launch_batch(b, a, b->stream);
         }
     } else {
-        e = launch_batch(b, a);
+        e = launch_batch(b, a, b->stream);
     }
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("launching the batched kernel: ") + cudaGetErrorString(e));
     b->step += nsteps;

@@ -24,6 +24,9 @@ cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s
 cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s,
                                bool merged);
 cudaError_t prepare_step_f32_tma(int m, int g);
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t prepare_step_f32_march(int m, int g, int slots, int *grid);
+bool march_supported(int m, int g, int slots);
 int defect_lanes(int m);
 int correct_lanes(int m);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
@@ -45,8 +48,9 @@ struct lbm_sim {
     double dt, dx, dy, omega, u_ref;
     cudaStream_t stream;
     int lanes;            // warps per 32-cell segment of the step kernel
-    int prefetch;         // bulk variant issuing loads ahead of use
+    int prefetch;         // load path of the wall-free cells (lbm_set_variant)
     int grid;             // blocks of the bulk step kernel
+    int march_grid;       // persistent blocks of the column-march kernel (load paths 4, 5)
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
     int *wall_segs;       // device list of wall segments for the current lanes
     int wall_cap;
@@ -69,6 +73,7 @@ struct lbm_sim {
     StepArgs args;        // launch arguments except the buffer pointers
     cudaGraphExec_t graph[2];  // residual_every steps starting from buffer 0 / 1
     bool graph_ok[2];
+    cudaStream_t cap_stream;   // private stream the graphs are captured on (created on first use)
     long step;
     long resid_step;
 };
@@ -302,8 +307,8 @@ void drop_graphs(lbm_sim *s)
     }
 }
 
-// Enqueue steps [first, first + count) starting from buffer `cur` (no bookkeeping).
-cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur)
+// Enqueue steps [first, first + count) starting from buffer `cur` on `st` (no bookkeeping).
+cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur, cudaStream_t st)
 {
     StepArgs a = s->args;
     for (long i = 0; i < count; ++i) {
@@ -311,10 +316,10 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur)
         const bool resid = idx % s->prob.residual_every == 0;
         a.h = s->buf[cur];
         a.hn = s->buf[cur ^ 1];
-        cudaError_t e = launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, s->stream);
+        cudaError_t e = launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, st);
         if (e != cudaSuccess) return e;
         if (resid) {
-            e = launch_finalize_residual(s->partials, s->nparts_step, s->result, s->stream);
+            e = launch_finalize_residual(s->partials, s->nparts_step, s->result, st);
             if (e != cudaSuccess) return e;
         }
         cur ^= 1;
@@ -322,15 +327,24 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur)
     return cudaSuccess;
 }
 
-// CUDA graph of residual_every steps from buffer `cur`, captured on the sim's stream.
+// CUDA graph of residual_every steps from buffer `cur`.  Captured on a stream private to
+// the sim, never on the caller's: a caller's stream may be shared (stream pools hand the
+// same stream to several users), and any work another thread enqueued on it during the
+// capture would land in this graph.  The graph is launched on the caller's stream.
 cudaError_t make_graph(lbm_sim *s, int cur)
 {
+    cudaError_t e = cudaSuccess;
+    if (!s->cap_stream) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        s->cap_stream = nullptr;
+        return e;
+    }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     const long K = s->prob.residual_every;
-    cudaError_t e2 = enqueue_steps(s, 1, K, cur);   // indices 1..K: residual on the last
-    e = cudaStreamEndCapture(s->stream, &g);
+    cudaError_t e2 = enqueue_steps(s, 1, K, cur, s->cap_stream);   // indices 1..K: residual on the last
+    e = cudaStreamEndCapture(s->cap_stream, &g);
     if (e2 != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return e2 != cudaSuccess ? e2 : e;
@@ -374,6 +388,21 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     // one merged launch when wall segments are more than a tenth of all segments
     const long nseg_total = (s->ncells + 31) / 32;
     s->args.merged = (long)segs.size() * 10 > nseg_total ? 1 : 0;
+    if (s->prefetch >= 4) {
+        // column march over the interior: 64-cell strips x in [32, nx - 32), the rows
+        // [1, ny - 2] cut into chunks of 8 to ~32 rows, enough items for 4 per block
+        const int strips = (nx - 64) / 64, rows = ny - 2;
+        int chunks = rows / 32;
+        const int want = (4 * s->march_grid + strips - 1) / strips;
+        if (chunks < want) chunks = want;
+        if (chunks > rows / 8) chunks = rows / 8;
+        if (chunks < 1) chunks = 1;
+        s->grid = s->march_grid;
+        s->args.march_strips = strips;
+        s->args.march_chunks = chunks;
+        s->args.counters = (int *)(s->result + 12);
+        s->args.merged = 0;
+    }
     s->nparts_step = s->grid + wall_grid(lanes, (int)segs.size());
     return LBM_OK;
 }
@@ -396,6 +425,7 @@ bool step_supported(int prec, int m, int g, int pf)
         for (auto &v : tma) if (v[0] == m && v[1] == g) return true;
         return false;
     }
+    if (pf == 4 || pf == 5) return prec == LBM_FP32_PERTURB && march_supported(m, g, pf);
     if (prec == LBM_FP64) {
         for (auto &v : f64) if (v[0] == m && v[1] == g && v[2] == pf) return true;
     } else {
@@ -408,6 +438,7 @@ cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepAr
                         cudaStream_t s)
 {
     if (pf == 2 || pf == 3) return launch_step_f32_tma(m, g, resid, a, grid, s, pf == 3);
+    if (pf == 4 || pf == 5) return launch_step_f32_march(m, g, pf, resid, a, grid, s);
     if (prec == LBM_FP64)
         return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
                       : launch_step_f64_small(m, g, pf, resid, a, grid, s);
@@ -418,6 +449,23 @@ cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepAr
 extern "C" {
 
 const char *lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_stream_create(void **stream)
+{
+    if (!stream) return fail(LBM_EINVAL, "stream is NULL");
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "creating a stream");
+    *stream = st;
+    return LBM_OK;
+}
+
+void lbm_stream_destroy(void *stream)
+{
+    if (!stream) return;
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaStreamDestroy((cudaStream_t)stream);
+}
 
 lbm_status lbm_make_velocity_set(int kind, int n, lbm_vset **out)
 {
@@ -494,11 +542,13 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->stream = (cudaStream_t)stream;
     s->lanes = default_lanes_per_cell(prob->prec, vs->m);
     s->prefetch = 0;
+    s->march_grid = 0;
     s->step = 0;
     s->resid_step = -1;
     s->cur = 0;
     s->host_res = nullptr;
     s->graph_ok[0] = s->graph_ok[1] = false;
+    s->cap_stream = nullptr;
     s->owns = device_buf == nullptr;
     s->bytes = L.total;
     if (s->owns) {
@@ -567,6 +617,7 @@ void lbm_destroy(lbm_sim *s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     drop_graphs(s);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->owns && s->base) cudaFree(s->base);
     if (s->host_res) cudaFreeHost(s->host_res);
     delete s;
@@ -613,7 +664,7 @@ lbm_status lbm_step(lbm_sim *s, long nsteps)
             continue;
         }
         const long idx = s->step + 1;
-        cudaError_t e = enqueue_steps(s, idx, 1, s->cur);
+        cudaError_t e = enqueue_steps(s, idx, 1, s->cur, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the step kernels");
         if (idx % K == 0) s->resid_step = idx;
         s->cur ^= 1;
@@ -787,15 +838,24 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (prefetch < 0 || prefetch > 3) return fail(LBM_EINVAL, "load path must be 0, 1, 2 or 3");
+    if (prefetch < 0 || prefetch > 5) return fail(LBM_EINVAL, "load path must be 0 to 5");
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
         return fail(LBM_EUNSUPPORTED, "no step kernel with %d warps per segment (prefetch %d) for M = %d",
                     warps_per_segment, prefetch, s->vs.m);
     if (prefetch >= 2 && (s->prob.geom != LBM_CAVITY || s->prob.nx % 4 != 0 || s->ncells % 4 != 0))
         return fail(LBM_EUNSUPPORTED, "TMA staging needs a cavity with nx and the cell count multiples of 4");
-    if (prefetch >= 2) {
+    if (prefetch >= 4 && (s->prob.nx % 64 != 0 || s->prob.nx < 128 || s->prob.ny < 10))
+        return fail(LBM_EUNSUPPORTED, "the column march needs nx a multiple of 64, nx >= 128 and ny >= 10");
+    if (prefetch == 2 || prefetch == 3) {
         cudaError_t e = prepare_step_f32_tma(s->vs.m, warps_per_segment);
         if (e != cudaSuccess) return cuda_fail(e, "enabling the TMA kernel's shared memory");
+    }
+    if (prefetch >= 4) {
+        int grid = 0;
+        cudaError_t e = prepare_step_f32_march(s->vs.m, warps_per_segment, prefetch, &grid);
+        if (e != cudaSuccess) return cuda_fail(e, "enabling the column-march kernel's shared memory");
+        if (grid <= 0) return fail(LBM_EUNSUPPORTED, "the column-march kernel does not fit on an SM");
+        s->march_grid = grid;
     }
     s->prefetch = prefetch;
     return set_lanes(s, warps_per_segment);

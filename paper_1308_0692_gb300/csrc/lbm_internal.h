@@ -51,6 +51,9 @@ struct StepArgs {
     int merged;           // bulk and wall segments in one launch
     int bulk_blocks;      // merged launch: blocks taking the wall-free segments
     int wall_blocks;      // merged TMA launch: leading blocks taking the wall segments
+    int *counters;        // column march: [0] next item, [1] finished blocks (zero between launches)
+    int march_strips;     // column march: 64-cell strips of the interior
+    int march_chunks;     // column march: chunks of the interior rows
     // 1-D tables over the M nodes of one axis (velocity a = iy*M + ix)
     double xi[LBM_MAX_M];   // nodes
     double nux[LBM_MAX_M];  // |xi| dt / dx (0 for a single periodic Couette column)

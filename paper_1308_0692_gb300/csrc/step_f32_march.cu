@@ -1,0 +1,42 @@
+// FP32 step with the interior as a TMA-staged column march (instantiation list; the kernel
+// is in step_march.cuh).  Load path 4 keeps two rows of copies in flight per warp (ring of
+// four row slots), load path 5 three (ring of five).
+#include "step_march.cuh"
+
+using namespace lbmk;
+
+#define LBM_MARCH_LIST(X) \
+    X(12, 6, 4)           \
+    X(12, 6, 5)           \
+    X(12, 12, 4)          \
+    X(12, 12, 5)          \
+    X(8, 4, 5)            \
+    X(8, 2, 5)
+
+bool march_supported(int m, int g, int slots)
+{
+#define LBM_MARCH_HAVE(M_, G_, S_) \
+    if (m == M_ && g == G_ && slots == S_) return true;
+    LBM_MARCH_LIST(LBM_MARCH_HAVE)
+#undef LBM_MARCH_HAVE
+    return false;
+}
+
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool resid, const StepArgs &a, int grid, cudaStream_t s)
+{
+#define LBM_MARCH_LAUNCH(M_, G_, S_)                                                  \
+    if (m == M_ && g == G_ && slots == S_)                                            \
+        return resid ? launch_march<M_, G_, S_, true>(a, grid, s) : launch_march<M_, G_, S_, false>(a, grid, s);
+    LBM_MARCH_LIST(LBM_MARCH_LAUNCH)
+#undef LBM_MARCH_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_step_f32_march(int m, int g, int slots, int *grid)
+{
+#define LBM_MARCH_PREP(M_, G_, S_) \
+    if (m == M_ && g == G_ && slots == S_) return prepare_march<M_, G_, S_>(grid);
+    LBM_MARCH_LIST(LBM_MARCH_PREP)
+#undef LBM_MARCH_PREP
+    return cudaErrorInvalidValue;
+}

@@ -1,0 +1,345 @@
+// Interior of the FP32 step as a column march with TMA staging (sm_103a).
+//
+// The same update as the bulk path of step_kernel.cuh (first-order upwind transport, then
+// relaxation towards w_a (rho' + xi_a . j'), Eqs. 5-7 with the scheme's discretisation),
+// organised so that every value of the old state crosses the L2 -> SM path about once:
+//
+//   * A block owns a strip of 64 cells in x (lane = 2 neighbouring cells, packed FP32x2
+//     arithmetic along x) and marches it row by row through a chunk of rows.  Its G warps
+//     split the M velocity rows iy as in the segment kernels (warp g owns M/G rows, all
+//     with the same sign of xi_y).
+//   * Per row and velocity the warp copies one 288-byte line (the 64 cells and 4 cells of
+//     x halo on each side) into shared memory with a 1-D bulk asynchronous copy
+//     (cp.async.bulk ... mbarrier::complete_tx).  A ring of S row slots per warp keeps the
+//     rows y-1, y, y+1 resident, so the upwind y neighbour of row y is a line that was
+//     copied for row y-1 or y+1 anyway: no second read of it, unlike the segment kernels
+//     (which read every line twice: once as own cells, once as a neighbour row).  S-2 rows
+//     of copies stay in flight ahead of the arithmetic.
+//   * The interior is cut into items (strip, chunk of rows), numbered chunk-major so that
+//     blocks running at the same time work on neighbouring strips of the same rows (their
+//     x halos are then L2 hits).  The grid is persistent (one or more blocks per SM); a
+//     block takes items from an atomic counter, and the copies of its next item are
+//     issued while it finishes the current one.  The last block to finish resets the
+//     counter for the next launch.
+//
+// Cells covered: x in [32, nx - 32), y in [1, ny - 2]; the wall kernel handles the rest
+// (rows 0 and ny-1 and the 32-cell segments at x = 0 and x = nx - 32 of every inner row,
+// exactly the wall-segment list when nx is a multiple of 32).  Host-checked requirements:
+// FP32 state, cavity, nx a multiple of 64 and at least 128, chunks at least S rows long.
+//
+// Every wait on a copy is bounded: after the limit the warp sets the status word and a
+// block-wide abort flag, all warps leave the march at the next row barrier, wait (again
+// bounded) for the copies they still have in flight, and return.
+#pragma once
+
+#include <cstdint>
+
+#include "step_tma.cuh"
+
+namespace lbmk {
+
+template <int M, int G, int S>
+struct MarchShape {
+    static constexpr int RPL = M / G;              // velocity rows per warp
+    static constexpr int NV = RPL * M;             // velocities per warp
+    static constexpr int LINE = 72;                // floats per staged line (64 + 4 + 4)
+    static constexpr int SLOT = NV * LINE;         // floats of one warp's row slot
+    static constexpr int THREADS = 32 * G;
+    static constexpr int SMEM = S * G * SLOT * 4 + S * G * 8;
+};
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// first row of chunk k of the interior rows [1, ny - 2] cut into nchunks near-equal chunks
+__device__ __forceinline__ int march_row0(int k, int rows, int nchunks)
+{
+    return 1 + (int)(((long)k * rows) / nchunks);
+}
+
+template <int M, int G, int S, bool RESID>
+__global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_kernel(const StepArgs a)
+{
+    using Sh = MarchShape<M, G, S>;
+    constexpr int RPL = Sh::RPL, NV = Sh::NV, LINE = Sh::LINE, HALF = M / 2;
+    static_assert(M % 2 == 0 && (M / 2) % 2 == 0, "even M with velocity pairs on one side of xi = 0");
+    static_assert(HALF % RPL == 0, "the velocity rows of a warp share the sign of xi_y");
+    static_assert(NV <= 32, "one bulk copy per lane and row");
+    static_assert(S >= 3, "rows y-1, y, y+1 resident");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ float2 s_mom[2][3][G][32];
+    __shared__ int s_items[4];
+    __shared__ int s_abort;
+    __shared__ double s_red[2][G];
+
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const long ncells = a.ncells;
+    const int nx = a.nx;
+    const int nstrips = a.march_strips, nchunks = a.march_chunks;
+    const int nitems = nstrips * nchunks;
+    const int rows = a.ny - 2;
+    const bool ypos = g * RPL >= HALF;   // xi_y > 0: upwind row y - 1; else y + 1
+    float *slots = reinterpret_cast<float *>(smem_raw) + (long)g * S * Sh::SLOT;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (long)S * G * Sh::SLOT * 4) + g * S;
+    const float *__restrict__ h = reinterpret_cast<const float *>(a.h);
+    float *__restrict__ hn = reinterpret_cast<float *>(a.hn);
+
+    if (threadIdx.x == 0) {
+        s_items[0] = atomicAdd(a.counters, 1);
+        s_items[1] = atomicAdd(a.counters, 1);
+        s_items[2] = atomicAdd(a.counters, 1);
+        s_abort = 0;
+    }
+    if (lane == 0) {
+        for (int j = 0; j < S; ++j) mbar_init(&bars[j], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    // per-warp coefficients of the transport of its velocities (velocity k = r*M + ix)
+    float a0r[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int r = k / M, ix = k - r * M;
+        a0r[k] = 1.f - a.nux_f[ix] - a.nuy_f[g * RPL + r];
+    }
+    // plane offset of this lane's copy (lanes < NV issue one line each per row)
+    const int kc = lane < NV ? lane : 0;
+    const float *src_plane = h + (long)((g * RPL + kc / M) * M + (kc % M)) * ncells;
+
+    // loader state (uniform within the warp)
+    int l_pos = 0, l_item = s_items[0], l_i = 0;
+    int l_row0 = 0, l_len = 0, l_strip = 0;
+    auto l_decode = [&]() {
+        const int k = l_item / nstrips;
+        l_strip = l_item - k * nstrips;
+        l_row0 = march_row0(k, rows, nchunks);
+        l_len = march_row0(k + 1, rows, nchunks) - l_row0;
+    };
+    if (l_item < nitems) l_decode();
+    long nl = 0;       // copies issued (row slots)
+    long waited = 0;   // row slots [0, waited) have landed
+
+    auto issue = [&]() {
+        const int slot = (int)(nl % S);
+        const int row = l_row0 - (ypos ? 1 : 0) + l_i;
+        if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * LINE * 4));
+        __syncwarp();
+        fence_proxy_async_smem();   // this slot's earlier generic reads before the async writes
+        if (lane < NV)
+            bulk_copy(slots + slot * Sh::SLOT + lane * LINE,
+                      src_plane + (long)row * nx + 28 + 64L * l_strip, LINE * 4, &bars[slot]);
+        ++nl;
+        if (++l_i > l_len) {
+            l_i = 0;
+            ++l_pos;
+            l_item = s_items[l_pos & 3];
+            if (l_item < nitems) l_decode();
+        }
+    };
+    bool ok = true;
+    auto wait_through = [&](long j_last) {
+        for (; waited <= j_last; ++waited) {
+            if (!mbar_wait_bounded(&bars[waited % S], (unsigned)((waited / S) & 1), 2000000000LL)) {
+                ok = false;
+                return;
+            }
+        }
+    };
+
+    // compute state
+    int c_pos = 0, c_item = s_items[0], c_u = 0;
+    int c_row0 = 0, c_len = 0, c_strip = 0;
+    auto c_decode = [&]() {
+        const int k = c_item / nstrips;
+        c_strip = c_item - k * nstrips;
+        c_row0 = march_row0(k, rows, nchunks);
+        c_len = march_row0(k + 1, rows, nchunks) - c_row0;
+    };
+    if (c_item < nitems) c_decode();
+    long gb = 0;       // row-slot index of load 0 of the item being computed
+    int par = 0;
+    const float om = a.omega_f;
+    const float2 b2 = make_float2(a.b_f, a.b_f);
+    double psd = 0.0, psn = 0.0;
+
+    while (c_item < nitems) {
+        // keep S - 2 rows of copies ahead of the rows being computed
+        while (l_item < nitems && nl <= gb + c_u + S - 1) issue();
+        if (ok) wait_through(gb + c_u + 1);
+        ok = __all_sync(FULL, ok);      // one verdict per warp
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(a.status, 1);
+                s_abort = 1;
+            }
+        }
+        const long jo = ypos ? gb + c_u + 1 : gb + c_u;      // own row y
+        const long jy = ypos ? gb + c_u : gb + c_u + 1;      // upwind row y -/+ 1
+        const float *own = slots + (int)(jo % S) * Sh::SLOT;
+        const float *ynb = slots + (int)(jy % S) * Sh::SLOT;
+
+        // ---- transport + moment sums (two cells per lane) ----
+        float2 hs[NV];
+        float2 rho2 = make_float2(0.f, 0.f), jx2 = rho2, jy2 = rho2;
+        if (ok) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int iy = g * RPL + r;
+                const float nuy = a.nuy_f[iy];
+                const float2 nuy2 = make_float2(nuy, nuy);
+                float2 R2 = make_float2(0.f, 0.f), X2 = R2;
+#pragma unroll
+                for (int ix = 0; ix < M; ++ix) {
+                    const int k = r * M + ix;
+                    const float *lo = own + k * LINE;
+                    const float2 hc = *reinterpret_cast<const float2 *>(lo + 4 + 2 * lane);
+                    const float2 hx = (ix >= M - HALF) ? make_float2(lo[3 + 2 * lane], hc.x)     // xi_x > 0: x - 1
+                                                       : make_float2(hc.y, lo[6 + 2 * lane]);    // xi_x < 0: x + 1
+                    const float2 hy = *reinterpret_cast<const float2 *>(ynb + k * LINE + 4 + 2 * lane);
+                    const float nux = a.nux_f[ix];
+                    float2 v = __fmul2_rn(make_float2(a0r[k], a0r[k]), hc);
+                    v = __ffma2_rn(make_float2(nux, nux), hx, v);
+                    v = __ffma2_rn(nuy2, hy, v);
+                    hs[k] = v;
+                    R2 = __fadd2_rn(R2, v);
+                    const float xi = a.xi_f[ix];
+                    X2 = __ffma2_rn(make_float2(xi, xi), v, X2);
+                }
+                const float xiy = a.xi_f[iy];
+                rho2 = __fadd2_rn(rho2, R2);
+                jx2 = __fadd2_rn(jx2, X2);
+                jy2 = __ffma2_rn(make_float2(xiy, xiy), R2, jy2);
+            }
+        }
+        s_mom[par][0][g][lane] = rho2;
+        s_mom[par][1][g][lane] = jx2;
+        s_mom[par][2][g][lane] = jy2;
+        __syncthreads();
+        if (s_abort) break;
+        rho2 = jx2 = jy2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            rho2 = __fadd2_rn(rho2, s_mom[par][0][q][lane]);
+            jx2 = __fadd2_rn(jx2, s_mom[par][1][q][lane]);
+            jy2 = __fadd2_rn(jy2, s_mom[par][2][q][lane]);
+        }
+        par ^= 1;
+
+        // ---- relaxation, store, residual ----
+        const int y = c_row0 + c_u;
+        const long cell = (long)y * nx + 32 + 64L * c_strip + 2 * lane;
+        float2 psd2 = make_float2(0.f, 0.f), psn2 = psd2;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const float wom = om * a.w1_f[iy];
+            const float xiy = a.xi_f[iy];
+            const float2 q2 = __fmul2_rn(make_float2(wom, wom), __ffma2_rn(make_float2(xiy, xiy), jy2, rho2));
+            const float2 jj2 = __fmul2_rn(make_float2(wom, wom), jx2);
+            float *rowp = hn + (long)(iy * M) * ncells + cell;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const int k = r * M + ix;
+                const float xi = a.xi_f[ix], w = a.w1_f[ix];
+                const float2 t = __ffma2_rn(make_float2(xi, xi), jj2, q2);
+                const float2 v = __ffma2_rn(make_float2(w, w), t, __fmul2_rn(b2, hs[k]));
+                if (RESID) {
+                    const float2 hc = *reinterpret_cast<const float2 *>(own + k * LINE + 4 + 2 * lane);
+                    const float2 d = __fadd2_rn(v, make_float2(-hc.x, -hc.y));
+                    psd2 = __ffma2_rn(d, d, psd2);
+                    psn2 = __ffma2_rn(v, v, psn2);
+                }
+                *reinterpret_cast<float2 *>(rowp + (long)ix * ncells) = v;
+            }
+        }
+        if (RESID) {
+            psd += (double)psd2.x + (double)psd2.y;
+            psn += (double)psn2.x + (double)psn2.y;
+        }
+
+        // ---- next row / item ----
+        if (++c_u == c_len) {
+            gb += c_len + 1;
+            c_u = 0;
+            ++c_pos;
+            c_item = s_items[c_pos & 3];
+            if (c_item < nitems) c_decode();
+            if (threadIdx.x == 0) s_items[(c_pos + 2) & 3] = atomicAdd(a.counters, 1);
+        }
+    }
+
+    // copies still in flight (abort path) must land before the block's shared memory goes
+    for (; waited < nl; ++waited) mbar_wait_bounded(&bars[waited % S], (unsigned)((waited / S) & 1), 2000000000LL);
+
+    if (RESID) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            psd += __shfl_xor_sync(FULL, psd, off);
+            psn += __shfl_xor_sync(FULL, psn, off);
+        }
+        if (lane == 0) {
+            s_red[0][g] = psd;
+            s_red[1][g] = psn;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (RESID) {
+            double td = 0.0, tn = 0.0;
+            for (int q = 0; q < G; ++q) {
+                td += s_red[0][q];
+                tn += s_red[1][q];
+            }
+            a.partials[2 * blockIdx.x] = td;
+            a.partials[2 * blockIdx.x + 1] = tn;
+        }
+        // the last block to finish resets the item counter for the next launch
+        __threadfence();
+        if (atomicAdd(a.counters + 1, 1) == (int)gridDim.x - 1) {
+            a.counters[0] = 0;
+            a.counters[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int M, int G, int S>
+cudaError_t prepare_march(int *grid)
+{
+    constexpr int SMEM = MarchShape<M, G, S>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false>,
+                                                          MarchShape<M, G, S>::THREADS, SMEM);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) *grid = per_sm > 0 ? per_sm * sms : 0;
+    return e;
+}
+
+// March kernel over `grid` persistent blocks, then the wall kernel over the wall segments.
+template <int M, int G, int S, bool RESID>
+cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
+{
+    constexpr int SMEM = MarchShape<M, G, S>::SMEM;
+    step_march_kernel<M, G, S, RESID><<<grid, MarchShape<M, G, S>::THREADS, SMEM, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.n_wall_segs == 0) return e;
+    StepArgs b = a;
+    b.partials_offset = grid;
+    const int wgrid = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
+    step_kernel<float, float, M, G, RESID, false, false, true, false><<<wgrid, Shape<G>::THREADS, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

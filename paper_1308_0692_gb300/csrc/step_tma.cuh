@@ -35,12 +35,15 @@ __device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, unsigned bytes
                  : "memory");
 }
 
+// Test for completion of the phase with the given parity; a thread whose phase is not
+// complete may be suspended until it completes or for at most the time hint (10 ms), so
+// a waiting warp does not spin on the issue slots the computing warps need.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
 {
     unsigned done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done)
-                 : "r"(smem_addr(bar)), "r"(phase)
+                 : "r"(smem_addr(bar)), "r"(phase), "r"(10000000u)
                  : "memory");
     return done != 0;
 }
@@ -53,14 +56,19 @@ __device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, unsig
                  : "memory");
 }
 
-// wait for phase 0 of the warp's barrier, at most ~limit_cycles; false on timeout
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, long long limit_cycles)
+// wait for the phase of the given parity of a barrier, at most ~limit_cycles; false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit_cycles)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, 0)) {
+    while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > limit_cycles) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, long long limit_cycles)
+{
+    return mbar_wait_bounded(bar, 0u, limit_cycles);
 }
 
 template <int M, int G>

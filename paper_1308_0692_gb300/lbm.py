@@ -109,6 +109,8 @@ def _load():
         "lbm_mlp_train_step": (st, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _dp]),
         "lbm_mlp_features": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp]),
         "lbm_warm_start": (st, [_vp, _vp, ctypes.c_double, ctypes.c_double]),
+        "lbm_stream_create": (st, [ctypes.POINTER(_vp)]),
+        "lbm_stream_destroy": (None, [_vp]),
         "lbm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -142,6 +144,31 @@ def _stream_handle(stream) -> int | None:
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+class PrivateStream:
+    """A CUDA stream of the caller's own (lbm_stream_create), usable wherever a torch stream
+    is (``.torch`` is a torch.cuda.ExternalStream over it; ``cuda_stream`` the handle).
+    torch.cuda.Stream() hands out streams from a small pool, so simulations driven from
+    many host threads can end up sharing one; these never are."""
+
+    def __init__(self):
+        import torch
+        p = _vp()
+        _check(_load().lbm_stream_create(ctypes.byref(p)))
+        self.cuda_stream = p.value
+        self.torch = torch.cuda.ExternalStream(p.value)
+
+    def close(self):
+        if self.cuda_stream and _lib is not None:
+            _lib.lbm_stream_destroy(self.cuda_stream)
+        self.cuda_stream = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class VelocitySet:

@@ -30,7 +30,11 @@ def _problem(inst, prec):
                             residual_every=100)
 
 
-def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=32, log=print):
+def _log(*a):
+    print(*a, flush=True)
+
+
+def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=32, log=_log):
     import torch
     table = batch_table(count, seed)
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
@@ -53,6 +57,7 @@ def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=3
             break
     t_batch = time.perf_counter() - t0
     steps = np.array([lbm.lbm_batch_status(b, i)["steps"] for i in range(count)])
+    log(f"sweep: batch march done, {int((steps < steps_done).sum())} of {count} instances converged")
     cells = np.array([p.nx * p.ny for p in probs])
     log(f"sweep: FP32 batch march to {tol32:g} in {t_batch:.1f} s ({steps_done} steps launched, "
         f"{(steps * cells * 64).sum() / t_batch / 1e9:.1f} G updates/s on active instances)")
@@ -60,7 +65,7 @@ def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=3
     # refinement of every instance, one stream and host thread each
     sims = []
     for i, p in enumerate(probs):
-        sims.append(lbm.lbm_init(vs, p, lbm.lbm_batch_get_state(b, i), stream=torch.cuda.Stream()))
+        sims.append(lbm.lbm_init(vs, p, lbm.lbm_batch_get_state(b, i), stream=lbm.PrivateStream()))
     b.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -80,7 +85,7 @@ def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=3
 
     def reference(i):
         p64 = _problem(table[i], lbm.LBM_FP64)
-        s64 = lbm.lbm_init(vs, p64, stream=torch.cuda.Stream())
+        s64 = lbm.lbm_init(vs, p64, stream=lbm.PrivateStream())
         lbm.lbm_solve(s64, tol * 1e-2, 5_000_000, 0)
         m = lbm.lbm_moments(s64)
         s64.close()

@@ -122,7 +122,7 @@ def solve_cavity(vs, kn, uw, side=128, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refi
     """Solve one cavity to tol (cold start or warm start); returns (sim, info, seconds)."""
     import torch
     prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=prec, residual_every=100)
-    sim = lbm.lbm_init(vs, prob, stream=stream or torch.cuda.Stream())
+    sim = lbm.lbm_init(vs, prob, stream=stream or lbm.PrivateStream())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if mlp is not None:
@@ -180,7 +180,7 @@ def refine_instances(vs, b, pairs, tol, side=128, threads=32, refine_tol=0.0):
     for i, (kn, uw) in enumerate(pairs):
         prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
                                 residual_every=100)
-        sims.append(lbm.lbm_init(vs, prob, lbm.lbm_batch_get_state(b, i), stream=torch.cuda.Stream()))
+        sims.append(lbm.lbm_init(vs, prob, lbm.lbm_batch_get_state(b, i), stream=lbm.PrivateStream()))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
 

@@ -146,6 +146,32 @@ def test_caller_buffer_and_stream_give_identical_bits():
     np.testing.assert_array_equal(a, b)       # deterministic: no atomics, fixed order
 
 
+def test_sims_sharing_a_stream_from_two_threads():
+    """Two simulations on one stream, stepped from two host threads at once, give the bits
+    they give one after the other: each sim captures its step graphs on a private stream, so
+    neither capture can swallow the other thread's launches on the shared stream."""
+    import concurrent.futures as cf
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    probs = [lbm.make_problem(CAVITY, 96, 80, kn, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB, residual_every=5)
+             for kn in (0.1, 0.03)]
+    h0 = [random_state(64, 96 * 80, seed=s) for s in (5, 6)]
+
+    def run(args):
+        prob, h, stream = args
+        sim = lbm.lbm_init(vs, prob, h, stream=stream)
+        for _ in range(8):
+            lbm.lbm_step(sim, 10)
+        r = lbm.lbm_residual(sim)
+        return lbm.lbm_get_state(sim), r
+
+    alone = [run((p, h, lbm.PrivateStream())) for p, h in zip(probs, h0)]
+    shared = torch.cuda.Stream()
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        both = list(ex.map(run, [(p, h, shared) for p, h in zip(probs, h0)]))
+    for (ga, ra), (gb, rb) in zip(alone, both):
+        assert np.array_equal(ga, gb) and ra == rb
+
+
 def test_zero_steps_and_set_get_roundtrip():
     kind, n, geom, nx, ny, kn, ub, ut = "half", 4, CAVITY, 9, 7, 0.1, 0.0, 0.01
     h0 = random_state(64, 63, seed=9)
@@ -224,6 +250,55 @@ def test_full_size_sampled_step(case):
     assert np.abs(g - ref).max() <= tol * np.abs(ref).max()
 
 
+@pytest.fixture(scope="module")
+def bench_case():
+    """The benchmark's workload (cavity 2048 x 2048, D2Q^h_144, Kn 0.05, lid 0.01, FP32):
+    one FP32-representable state and the oracle's step at 400 sampled cells."""
+    p = oracle_problem("half", 6, CAVITY, 2048, 2048, 0.05, 0.0, 0.01)
+    h0 = _host_state_for(p, seed=77, prec=lbm.LBM_FP32_PERTURB)
+    nx, ny = 2048, 2048
+    corners = [0, nx - 1, (ny - 1) * nx, ny * nx - 1, 31 * nx + 31, 32 * nx + 32, nx + 32, 2 * nx - 33,
+               (ny - 2) * nx + 32, (ny - 2) * nx + nx - 33, (ny // 2) * nx + 95, (ny // 2) * nx + 96]
+    cells = random_cells(p.ncells, 400, seed=79, include=corners)
+    return p, h0, cells, p.step_cells(h0, cells)
+
+
+def _bench_variants():
+    import bench
+    return bench.VARIANTS
+
+
+@pytest.mark.parametrize("variant", _bench_variants(), ids=lambda v: f"g{v[0]}-path{v[1]}")
+def test_full_size_bench_variants(bench_case, variant):
+    """Every kernel variant the benchmark may choose, at the benchmark's size, on sampled
+    cells (walls, corners, strip and chunk edges of the column march), for the step with
+    and without the residual."""
+    p, h0, cells, ref = bench_case
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
+    idx = torch.as_tensor(np.asarray(cells, dtype=np.int64), device="cuda")
+    rs = []
+    for residual_every in (1, 2):
+        prob = lbm.make_problem(CAVITY, 2048, 2048, 0.05, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB,
+                                residual_every=residual_every)
+        buf = torch.empty(lbm.lbm_sim_bytes(vs, prob), dtype=torch.uint8, device="cuda")
+        sim = lbm.lbm_init(vs, prob, h0, device_buf=buf, stream=torch.cuda.Stream())
+        lbm.lbm_set_variant(sim, *variant)
+        lbm.lbm_step(sim, 1)
+        ptr, nbytes = lbm.lbm_state_device(sim)
+        off = ptr - buf.data_ptr()
+        torch.cuda.synchronize()
+        state = buf[off:off + nbytes].view(torch.float32).view(p.n, p.ncells)
+        got = state[:, idx].double().cpu().numpy().T
+        assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * np.abs(ref).max(), (variant, residual_every)
+        if residual_every == 1:
+            r, st = lbm.lbm_residual(sim)
+            assert st == 1 and np.isfinite(r) and r > 0
+            rs.append(r)
+        sim.close()
+        del buf, state
+    torch.cuda.empty_cache()
+
+
 def _host_state_for(p, seed, prec):
     h = random_state(p.n, p.ncells, seed=seed)
     if prec == lbm.LBM_FP32_PERTURB:
@@ -257,6 +332,52 @@ def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
             assert np.abs(got - by_g[g]).max() <= 1e-6 * np.abs(ref).max(), (g, pf)
         else:
             by_g[g] = got
+
+
+@pytest.mark.parametrize("n_half,nx,ny,variants", [
+    # 2 strips x 5 chunks: fewer items than blocks (most blocks find no work)
+    (6, 192, 45, [(6, 0), (6, 4), (6, 5), (12, 4), (12, 5)]),
+    # 5 strips x 65 chunks of 8 rows: more items than blocks, item-to-item pipelining
+    (6, 384, 522, [(6, 0), (6, 4), (6, 5), (12, 5)]),
+    (4, 256, 70, [(2, 0), (2, 5), (4, 0), (4, 5)]),
+])
+def test_fp32_column_march_matches_oracle(n_half, nx, ny, variants):
+    """The column-march interior (load paths 4, 5) gives the oracle's result to FP32 accuracy
+    over several steps, with and without the residual, and agrees with the segment kernels
+    to within a few FP32 roundings."""
+    p = oracle_problem("half", n_half, CAVITY, nx, ny, 0.07, 0.002, 0.01)
+    h0 = random_state(p.n, p.ncells, seed=41).astype(np.float32).astype(np.float64)
+    steps = 3
+    ref = p.step(h0, steps)
+    ref_r = oracle_residual(ref, p.step(h0, steps - 1))
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    base = None
+    for g, pf in variants:
+        sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.07, 0.002, 0.01, prec=lbm.LBM_FP32_PERTURB,
+                                                residual_every=steps), h0, stream=torch.cuda.Stream())
+        lbm.lbm_set_variant(sim, g, pf)
+        assert lbm.lbm_get_variant(sim) == (g, pf)
+        lbm.lbm_step(sim, steps)
+        got = lbm.lbm_get_state(sim)
+        r, st = lbm.lbm_residual(sim)
+        assert st == steps and abs(r - ref_r) <= 1e-4 * ref_r, (g, pf, r, ref_r)
+        assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * steps * np.abs(ref).max(), (g, pf)
+        if base is None:
+            base = got
+        else:
+            assert np.abs(got - base).max() <= 1e-6 * np.abs(ref).max(), (g, pf)
+
+
+def test_column_march_rejected_where_strips_do_not_fit():
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
+    for nx, ny in [(160, 64), (64, 64), (128, 9)]:
+        sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_set_variant(sim, 6, 4)
+        assert e.value.status == lbm.LBM_EUNSUPPORTED
+    sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 128, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP64))
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_variant(sim, 6, 4)
 
 
 def test_tma_variant_rejected_where_lines_are_unaligned():
