@@ -284,8 +284,10 @@ def test_full_size_bench_variants(bench_case, variant):
         sim = lbm.lbm_init(vs, prob, h0, device_buf=buf, stream=torch.cuda.Stream())
         lbm.lbm_set_variant(sim, *variant)
         lbm.lbm_step(sim, 1)
-        ptr, nbytes = lbm.lbm_state_device(sim)
+        ptr, step = lbm.lbm_state_device(sim)
+        assert step == 1
         off = ptr - buf.data_ptr()
+        nbytes = 4 * p.n * p.ncells
         torch.cuda.synchronize()
         state = buf[off:off + nbytes].view(torch.float32).view(p.n, p.ncells)
         got = state[:, idx].double().cpu().numpy().T
