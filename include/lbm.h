@@ -180,6 +180,16 @@ lbm_status lbm_face_flux(lbm_sim *sim, double *flux_y, double *flux_x);
 lbm_status lbm_get_state(lbm_sim *sim, double *h);
 lbm_status lbm_set_state(lbm_sim *sim, const double *h);
 
+/* Replace the current state by the one with the given moments per cell: moments is host
+ * FP64 [6][ny][nx] = rho, u_x, u_y, P_xx, P_xy, P_yy in Eq. (1) units (what lbm_moments
+ * returns).  The populations are the second-order Hermite expansion about the rest
+ * equilibrium, h_a = w_a [rho' + xi_a . j' + 1/2 sum_ij (P'_ij - rho' delta_ij)(xi_i xi_j -
+ * delta_ij)], rho' = (rho - 1)/u_ref, j' = rho u / u_ref, P' = (P - I)/u_ref, whose moments
+ * are the given ones on velocity sets exact to degree 4 (half-range N >= 3, full-range
+ * M >= 3).  The initial condition in moment form; lbm_init's init_h is the full state.
+ * Synchronises. */
+lbm_status lbm_set_moments(lbm_sim *sim, const double *moments);
+
 /* Device pointer of the current state (FP64 or FP32 elements per the precision) and
  * the step counter.  The pointer changes after every step (double buffering). */
 lbm_status lbm_state_device(lbm_sim *sim, void **ptr, long *step);

@@ -390,13 +390,27 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     s->args.merged = (long)segs.size() * 10 > nseg_total ? 1 : 0;
     if (s->prefetch >= 4) {
         // column march over the interior: 64-cell strips x in [32, nx - 32), the rows
-        // [1, ny - 2] cut into chunks of 8 to ~32 rows, enough items for 4 per block
-        const int strips = (nx - 64) / 64, rows = ny - 2;
-        int chunks = rows / 32;
-        const int want = (4 * s->march_grid + strips - 1) / strips;
-        if (chunks < want) chunks = want;
-        if (chunks > rows / 8) chunks = rows / 8;
-        if (chunks < 1) chunks = 1;
+        // [1, ny - 2] cut into chunks (items = strips x chunks).  Chunks of at least 8 rows
+        // (16 where the grid allows) and, where the grid allows, at least 4 items per block;
+        // among those the count that minimises (rounds of items x blocks) / items, the idle
+        // share of the last round, times (1 + 1 / rows per chunk), the share of rows read
+        // twice at chunk boundaries.
+        const int strips = (nx - 64) / 64, rows = ny - 2, G = s->march_grid;
+        const int lo_len = rows >= 16 * 4 ? 16 : 8;
+        int cmax = rows / lo_len, cmin = (4 * G + strips - 1) / strips;
+        if (cmax < 1) cmax = 1;
+        if (cmin > cmax) cmin = cmax;
+        int chunks = cmax;
+        double best = 1e300;
+        for (int c = cmin; c <= cmax; ++c) {
+            const long items = (long)strips * c;
+            const long rounds = (items + G - 1) / G;
+            const double cost = (double)(rounds * G) / items * (1.0 + (double)c / rows);
+            if (cost < best - 1e-12) {
+                best = cost;
+                chunks = c;
+            }
+        }
         s->grid = s->march_grid;
         s->args.march_strips = strips;
         s->args.march_chunks = chunks;
@@ -972,6 +986,18 @@ lbm_status lbm_set_state(lbm_sim *s, const double *h)
 {
     if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
     return upload_state(s, h, s->buf[s->cur]);
+}
+
+lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
+{
+    if (!s || !moments) return fail(LBM_EINVAL, "NULL argument");
+    cudaError_t e = cudaMemcpyAsync(s->moments, moments, sizeof(double) * 6 * s->ncells, cudaMemcpyHostToDevice,
+                                    s->stream);
+    if (e == cudaSuccess)
+        e = launch_moments_state(s->prob.prec, s->moments, s->ncells, s->vs.m, s->hdr, s->u_ref, s->buf[s->cur],
+                                 s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the state from moments");
 }
 
 lbm_status lbm_state_device(lbm_sim *s, void **ptr, long *step)

@@ -95,6 +95,9 @@ cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const
                              double *flux_x, double *wall_sums, cudaStream_t s);
 
 cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s);
+// state h from device FP64 moments [6][ncells] (rho, u_x, u_y, P_xx, P_xy, P_yy)
+cudaError_t launch_moments_state(int prec, const double *mom, long ncells, int m, const TableHeader *hdr,
+                                 double u_ref, void *h, cudaStream_t s);
 cudaError_t launch_add_f32(float *y, const float *x, long count, cudaStream_t s);
 cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s);
 

@@ -4,6 +4,7 @@
 // face the upwind value is the Maxwell ghost of Eqs. 8-9).  All accumulation in FP64.
 #include <cmath>
 
+#include "../../include/lbm.h"
 #include "lbm_internal.h"
 
 namespace {
@@ -201,6 +202,34 @@ __global__ void widen_kernel(const float *src, double *dst, long count)
         dst[i] = (double)src[i];
 }
 
+// h from the six moments of each cell, mom [6][ncells] = rho, u_x, u_y, P_xx, P_xy, P_yy:
+// the second-order Hermite expansion h_a = w_a [rho' + xi_a . j' + 1/2 sum_ij (P'_ij -
+// rho' delta_ij)(xi_i xi_j - delta_ij)] with rho' = (rho - 1)/u_ref, j' = rho u / u_ref,
+// P' = (P - I)/u_ref (the inverse of the moment map of lbm_moments on sets exact to degree 4).
+template <typename T>
+__global__ void moments_state_kernel(const double *mom, long ncells, int m, const TableHeader *hdr,
+                                     double inv_u_ref, T *h)
+{
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += stride) {
+        const double rho = mom[c];
+        const double rp = (rho - 1.0) * inv_u_ref;
+        const double jx = rho * mom[ncells + c] * inv_u_ref, jy = rho * mom[2 * ncells + c] * inv_u_ref;
+        const double pxx = (mom[3 * ncells + c] - 1.0) * inv_u_ref, pxy = mom[4 * ncells + c] * inv_u_ref;
+        const double pyy = (mom[5 * ncells + c] - 1.0) * inv_u_ref;
+        for (int iy = 0; iy < m; ++iy) {
+            const double ey = hdr->xi1[iy];
+            for (int ix = 0; ix < m; ++ix) {
+                const double ex = hdr->xi1[ix];
+                const double v = hdr->w1[ix] * hdr->w1[iy] *
+                                 (rp + ex * jx + ey * jy +
+                                  0.5 * ((pxx - rp) * (ex * ex - 1.0) + 2.0 * pxy * ex * ey + (pyy - rp) * (ey * ey - 1.0)));
+                h[(long)(iy * m + ix) * ncells + c] = (T)v;
+            }
+        }
+    }
+}
+
 __global__ void axpy_kernel(float *y, const float *x, long count)
 {
     const long stride = (long)gridDim.x * blockDim.x;
@@ -208,6 +237,16 @@ __global__ void axpy_kernel(float *y, const float *x, long count)
 }
 
 }  // namespace
+
+cudaError_t launch_moments_state(int prec, const double *mom, long ncells, int m, const TableHeader *hdr,
+                                 double u_ref, void *h, cudaStream_t s)
+{
+    if (prec == LBM_FP64)
+        moments_state_kernel<double><<<152 * 8, 256, 0, s>>>(mom, ncells, m, hdr, 1.0 / u_ref, (double *)h);
+    else
+        moments_state_kernel<float><<<152 * 8, 256, 0, s>>>(mom, ncells, m, hdr, 1.0 / u_ref, (float *)h);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_add_f32(float *y, const float *x, long count, cudaStream_t s)
 {

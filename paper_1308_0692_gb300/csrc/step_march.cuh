@@ -18,7 +18,8 @@
 //   * The interior is cut into items (strip, chunk of rows), numbered chunk-major so that
 //     blocks running at the same time work on neighbouring strips of the same rows (their
 //     x halos are then L2 hits).  The grid is persistent (one or more blocks per SM); a
-//     block takes items from an atomic counter, and the copies of its next item are
+//     block's first three items are fixed (b, grid + b, 2 grid + b), later ones come from
+//     an atomic counter as blocks finish items, and the copies of a block's next item are
 //     issued while it finishes the current one.  The last block to finish resets the
 //     counter for the next launch.
 //
@@ -33,6 +34,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 
 #include "step_tma.cuh"
 
@@ -88,10 +90,14 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
     const float *__restrict__ h = reinterpret_cast<const float *>(a.h);
     float *__restrict__ hn = reinterpret_cast<float *>(a.hn);
 
+    // the first three items of every block are fixed (block b takes b, grid + b, 2 grid + b),
+    // so that the blocks start on consecutive items (neighbouring strips of the same rows);
+    // items from 3 grid on are handed out by the counter as blocks finish items
+    const int first_dyn = 3 * (int)gridDim.x;
     if (threadIdx.x == 0) {
-        s_items[0] = atomicAdd(a.counters, 1);
-        s_items[1] = atomicAdd(a.counters, 1);
-        s_items[2] = atomicAdd(a.counters, 1);
+        s_items[0] = (int)blockIdx.x;
+        s_items[1] = (int)gridDim.x + (int)blockIdx.x;
+        s_items[2] = 2 * (int)gridDim.x + (int)blockIdx.x;
         s_abort = 0;
     }
     if (lane == 0) {
@@ -99,6 +105,9 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    // the wall kernel of this step (a programmatic dependent launch) may start now and run
+    // beside the march on the SM resources the march leaves free
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 
     // per-warp coefficients of the transport of its velocities (velocity k = r*M + ix)
     float a0r[NV];
@@ -269,7 +278,7 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
             ++c_pos;
             c_item = s_items[c_pos & 3];
             if (c_item < nitems) c_decode();
-            if (threadIdx.x == 0) s_items[(c_pos + 2) & 3] = atomicAdd(a.counters, 1);
+            if (threadIdx.x == 0) s_items[(c_pos + 2) & 3] = first_dyn + atomicAdd(a.counters, 1);
         }
     }
 
@@ -327,7 +336,20 @@ cudaError_t prepare_march(int *grid)
     return e;
 }
 
-// March kernel over `grid` persistent blocks, then the wall kernel over the wall segments.
+// Wall segments of a step whose interior is marched by step_march_kernel, launched as its
+// programmatic dependent: the two grids run side by side (they read the same old state and
+// write disjoint cells of the new one).  Block 0 waits for the march grid before it exits,
+// so that this grid completes only after the march has completed and its writes are
+// visible: work the stream orders after this launch sees the whole step.
+template <int M, int G, bool RESID>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_wall_beside_march_kernel(const StepArgs a)
+{
+    step_body<float, float, M, G, RESID, false, false, true, false>(a, blockIdx.x);
+    if (blockIdx.x == 0) asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+// March kernel over `grid` persistent blocks, and beside it the wall kernel over the wall
+// segments (programmatic dependent launch).
 template <int M, int G, int S, bool RESID>
 cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
 {
@@ -337,9 +359,18 @@ cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
     if (e != cudaSuccess || a.n_wall_segs == 0) return e;
     StepArgs b = a;
     b.partials_offset = grid;
-    const int wgrid = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
-    step_kernel<float, float, M, G, RESID, false, false, true, false><<<wgrid, Shape<G>::THREADS, 0, s>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB);
+    cfg.blockDim = dim3(Shape<G>::THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_wall_beside_march_kernel<M, G, RESID>, b);
 }
 
 }  // namespace lbmk

@@ -77,6 +77,7 @@ def _load():
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
         "lbm_get_state": (st, [_vp, _dp]),
         "lbm_set_state": (st, [_vp, _dp]),
+        "lbm_set_moments": (st, [_vp, _dp]),
         "lbm_state_device": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_long)]),
         "lbm_norms_scratch_bytes": (st, [ctypes.c_long, ctypes.POINTER(ctypes.c_size_t)]),
         "lbm_norms": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp]),
@@ -304,6 +305,15 @@ def lbm_face_flux(sim: Sim):
     fx = np.empty(ny * (nx + 1)) if sim.prob.geom == LBM_CAVITY else None
     _check(_load().lbm_face_flux(sim.handle, _ptr(fy), _ptr(fx)))
     return fy.reshape(ny + 1, nx), (None if fx is None else fx.reshape(ny, nx + 1))
+
+
+def lbm_set_moments(sim: Sim, moments) -> None:
+    """moments: dict with rho, ux, uy, pxx, pxy, pyy ([ny][nx] each) or an array [6][ny][nx]."""
+    if isinstance(moments, dict):
+        moments = np.stack([np.asarray(moments[k], dtype=np.float64).reshape(-1)
+                            for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy")])
+    m = np.ascontiguousarray(np.asarray(moments, dtype=np.float64).reshape(6, sim.ncells))
+    _check(_load().lbm_set_moments(sim.handle, _ptr(m)))
 
 
 def lbm_get_state(sim: Sim) -> np.ndarray:

@@ -6,6 +6,12 @@ FP64 defect correction, and each instance's error reported against an FP64 stead
 (the FP64 GPU march, whose steps are parity-checked against the CPU oracle; every Couette
 channel, and the cavities up to a size limit).
 
+Tolerance: a state whose residual (or FP64 defect) is r is off the discrete steady state by
+about r / (1 - lambda), lambda the slowest mode's per-step factor; for the Kn ~ 0.01
+channels of 500 cells that factor is ~3e3, so a 1e-8 target leaves errors of a few 1e-5.
+The refinement therefore targets 1e-10 (the FP32 batch march still stops at 1e-6), and the
+FP64 references are marched to 1e-11.
+
     python -m paper_1308_0692_gb300.sweep [--count 512] [--out report.json]
 """
 from __future__ import annotations
@@ -34,7 +40,7 @@ def _log(*a):
     print(*a, flush=True)
 
 
-def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=32, log=_log):
+def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=32, log=_log):
     import torch
     table = batch_table(count, seed)
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
@@ -86,7 +92,7 @@ def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=3
     def reference(i):
         p64 = _problem(table[i], lbm.LBM_FP64)
         s64 = lbm.lbm_init(vs, p64, stream=lbm.PrivateStream())
-        lbm.lbm_solve(s64, tol * 1e-2, 5_000_000, 0)
+        lbm.lbm_solve(s64, tol * 1e-1, 5_000_000, 0)
         m = lbm.lbm_moments(s64)
         s64.close()
         return m
@@ -122,7 +128,7 @@ def run(count=512, seed=BATCH_SEED, tol=1e-8, ref_max_cells=128 * 128, threads=3
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=512)
-    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--ref-max-cells", type=int, default=128 * 128)
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)

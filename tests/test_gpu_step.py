@@ -172,6 +172,28 @@ def test_sims_sharing_a_stream_from_two_threads():
         assert np.array_equal(ga, gb) and ra == rb
 
 
+@pytest.mark.parametrize("prec,tol", [(lbm.LBM_FP64, 1e-13), (lbm.LBM_FP32_PERTURB, 1e-6)])
+def test_set_moments_matches_oracle_and_round_trips(prec, tol):
+    """lbm_set_moments builds the oracle's Hermite state from six moment fields, and
+    lbm_moments gives the fields back (the set D2Q^h_64 is exact to degree 4)."""
+    from oracle.mlp import moments_to_h
+    nx, ny, u_ref = 40, 30, 0.01
+    p = oracle_problem("half", 4, CAVITY, nx, ny, 0.1, 0.0, u_ref)
+    y, x = np.mgrid[0:ny, 0:nx] / np.array([[[ny]], [[nx]]])
+    mom = {"rho": 1 + u_ref * 0.3 * np.sin(3 * x) * np.cos(2 * y), "ux": u_ref * 0.8 * np.cos(4 * y),
+           "uy": -u_ref * 0.5 * np.sin(5 * x), "pxx": 1 + u_ref * 0.2 * x * y, "pxy": u_ref * 0.4 * (x - y),
+           "pyy": 1 - u_ref * 0.25 * np.cos(x + y)}
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.1, 0.0, u_ref, prec=prec), stream=torch.cuda.Stream())
+    lbm.lbm_set_moments(sim, mom)
+    got = lbm.lbm_get_state(sim)
+    ref = moments_to_h({k: v.reshape(-1) for k, v in mom.items()}, p.xi_x, p.xi_y, p.w, u_ref)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    back = lbm.lbm_moments(sim, wall_shear=False)
+    for k in mom:
+        assert np.abs(back[k] - mom[k]).max() <= 10 * tol * u_ref, k
+
+
 def test_zero_steps_and_set_get_roundtrip():
     kind, n, geom, nx, ny, kn, ub, ut = "half", 4, CAVITY, 9, 7, 0.1, 0.0, 0.01
     h0 = random_state(64, 63, seed=9)
@@ -342,6 +364,8 @@ def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
     # 5 strips x 65 chunks of 8 rows: more items than blocks, item-to-item pipelining
     (6, 384, 522, [(6, 0), (6, 4), (6, 5), (12, 5)]),
     (4, 256, 70, [(2, 0), (2, 5), (4, 0), (4, 5)]),
+    # 15 strips x 41+ chunks: items beyond the fixed first three per block come from the counter
+    (6, 1024, 1000, [(6, 0), (6, 4), (12, 5)]),
 ])
 def test_fp32_column_march_matches_oracle(n_half, nx, ny, variants):
     """The column-march interior (load paths 4, 5) gives the oracle's result to FP32 accuracy
