@@ -302,6 +302,12 @@ lbm_status lbm_mlp_features(lbm_mlp *mlp, int nx, int ny, double kn, double u_w,
  * The network's max_batch must cover nx*ny.  Synchronises. */
 lbm_status lbm_warm_start(lbm_sim *sim, lbm_mlp *mlp, double kn, double u_w);
 
+/* Work split of the column-march interior kernel (load paths 4, 5) for an nx x ny cavity
+ * run by `blocks` persistent blocks (host logic only, no GPU needed): the number of 64-cell
+ * strips and of row chunks; items = strips x chunks.  LBM_EUNSUPPORTED where the march does
+ * not apply (nx not a multiple of 64, nx < 128 or ny < 10). */
+lbm_status lbm_march_plan(int nx, int ny, int blocks, int *strips, int *chunks);
+
 /* A non-blocking CUDA stream owned by the caller, created and destroyed through the library
  * (no counterpart in the paper: plumbing for callers whose stream sources are pooled, so
  * that concurrent simulations driven from several host threads get streams of their own).

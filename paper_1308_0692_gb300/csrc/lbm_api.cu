@@ -389,28 +389,8 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     const long nseg_total = (s->ncells + 31) / 32;
     s->args.merged = (long)segs.size() * 10 > nseg_total ? 1 : 0;
     if (s->prefetch >= 4) {
-        // column march over the interior: 64-cell strips x in [32, nx - 32), the rows
-        // [1, ny - 2] cut into chunks (items = strips x chunks).  Chunks of at least 8 rows
-        // (16 where the grid allows) and, where the grid allows, at least 4 items per block;
-        // among those the count that minimises (rounds of items x blocks) / items, the idle
-        // share of the last round, times (1 + 1 / rows per chunk), the share of rows read
-        // twice at chunk boundaries.
-        const int strips = (nx - 64) / 64, rows = ny - 2, G = s->march_grid;
-        const int lo_len = rows >= 16 * 4 ? 16 : 8;
-        int cmax = rows / lo_len, cmin = (4 * G + strips - 1) / strips;
-        if (cmax < 1) cmax = 1;
-        if (cmin > cmax) cmin = cmax;
-        int chunks = cmax;
-        double best = 1e300;
-        for (int c = cmin; c <= cmax; ++c) {
-            const long items = (long)strips * c;
-            const long rounds = (items + G - 1) / G;
-            const double cost = (double)(rounds * G) / items * (1.0 + (double)c / rows);
-            if (cost < best - 1e-12) {
-                best = cost;
-                chunks = c;
-            }
-        }
+        int strips = 0, chunks = 0;
+        lbm_march_plan(nx, ny, s->march_grid, &strips, &chunks);
         s->grid = s->march_grid;
         s->args.march_strips = strips;
         s->args.march_chunks = chunks;
@@ -463,6 +443,37 @@ cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepAr
 extern "C" {
 
 const char *lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_march_plan(int nx, int ny, int blocks, int *strips, int *chunks)
+{
+    if (!strips || !chunks) return fail(LBM_EINVAL, "NULL argument");
+    if (nx % 64 != 0 || nx < 128 || ny < 10 || blocks < 1)
+        return fail(LBM_EUNSUPPORTED, "the column march needs nx a multiple of 64, nx >= 128 and ny >= 10");
+    // 64-cell strips x in [32, nx - 32); the rows [1, ny - 2] cut into chunks of at least 8
+    // rows (16 where the grid allows) and, where the grid allows, at least 4 items per block;
+    // among those the count minimising (rounds of items x blocks) / items, the idle share of
+    // the last round, times (1 + chunks / rows), the share of rows copied twice at chunk
+    // boundaries
+    const int S = (nx - 64) / 64, rows = ny - 2, G = blocks;
+    const int lo_len = rows >= 16 * 4 ? 16 : 8;
+    int cmax = rows / lo_len, cmin = (4 * G + S - 1) / S;
+    if (cmax < 1) cmax = 1;
+    if (cmin > cmax) cmin = cmax;
+    int best_c = cmax;
+    double best = 1e300;
+    for (int c = cmin; c <= cmax; ++c) {
+        const long items = (long)S * c;
+        const long rounds = (items + G - 1) / G;
+        const double cost = (double)(rounds * G) / items * (1.0 + (double)c / rows);
+        if (cost < best - 1e-12) {
+            best = cost;
+            best_c = c;
+        }
+    }
+    *strips = S;
+    *chunks = best_c;
+    return LBM_OK;
+}
 
 lbm_status lbm_stream_create(void **stream)
 {

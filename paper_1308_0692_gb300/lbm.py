@@ -110,6 +110,8 @@ def _load():
         "lbm_mlp_train_step": (st, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _dp]),
         "lbm_mlp_features": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp]),
         "lbm_warm_start": (st, [_vp, _vp, ctypes.c_double, ctypes.c_double]),
+        "lbm_march_plan": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]),
         "lbm_stream_create": (st, [ctypes.POINTER(_vp)]),
         "lbm_stream_destroy": (None, [_vp]),
         "lbm_last_error": (ctypes.c_char_p, []),
@@ -145,6 +147,13 @@ def _stream_handle(stream) -> int | None:
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+def lbm_march_plan(nx: int, ny: int, blocks: int):
+    """(strips, chunks) of the column-march kernel's work split (host logic, no GPU)."""
+    a, c = ctypes.c_int(), ctypes.c_int()
+    _check(_load().lbm_march_plan(int(nx), int(ny), int(blocks), ctypes.byref(a), ctypes.byref(c)))
+    return a.value, c.value
 
 
 class PrivateStream:

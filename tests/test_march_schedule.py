@@ -1,0 +1,147 @@
+"""Host-side model of the column-march kernel's schedule (step_march.cuh), checked on CPU.
+
+The model replays, for one block and each kind of warp (upwind row y-1 or y+1), the order
+in which the kernel issues row copies into its ring of S slots and consumes them, with the
+kernel's item numbering (chunk-major, first three items per block fixed, the rest from a
+counter) and the host's choice of the chunk count.  It checks what a GPU run could only
+show as a fault or a wrong answer: every copy starts 16-byte aligned inside one grid row,
+a slot is refilled only after its last use, each row computed finds its own row and its
+upwind row in the slots, an item id is read only after the barrier that published it,
+and the interior x in [32, nx-32), y in [1, ny-2] is written exactly once.
+"""
+import pytest
+
+
+def march_row0(k, rows, nchunks):
+    return 1 + (k * rows) // nchunks
+
+
+def choose_chunks(nx, ny, grid):
+    strips, rows = (nx - 64) // 64, ny - 2
+    lo_len = 16 if rows >= 64 else 8
+    cmax = max(rows // lo_len, 1)
+    cmin = min((4 * grid + strips - 1) // strips, cmax)
+    chunks, best = cmax, 1e300
+    for c in range(cmin, cmax + 1):
+        items = strips * c
+        rounds = (items + grid - 1) // grid
+        cost = rounds * grid / items * (1.0 + c / rows)
+        if cost < best - 1e-12:
+            best, chunks = cost, c
+    return strips, chunks
+
+
+def simulate(nx, ny, S, grid):
+    strips, nchunks = choose_chunks(nx, ny, grid)
+    rows, nitems, ncells = ny - 2, strips * nchunks, nx * ny
+    written = {}
+    counter = [3 * grid]
+
+    def decode(it):
+        k = it // strips
+        r0 = march_row0(k, rows, nchunks)
+        return it - k * strips, r0, march_row0(k + 1, rows, nchunks) - r0
+
+    for b in range(grid):
+        fetched = []                       # dynamic ids of this block, in fetch order
+        for ypos in (False, True):
+            items = {0: b, 1: grid + b, 2: 2 * grid + b}
+            visible = {0, 1, 2}
+            pending = []
+            dyn = iter(fetched) if ypos else None
+            l_pos, l_i, nl = 0, 0, 0
+            l_item = items[0]
+            if l_item < nitems:
+                l_strip, l_row0, l_len = decode(l_item)
+            loads = []
+            c_pos, c_u, gb = 0, 0, 0
+            c_item = items[0]
+            if c_item < nitems:
+                c_strip, c_row0, c_len = decode(c_item)
+            while c_item < nitems:
+                while l_item < nitems and nl <= gb + c_u + S - 1:
+                    if nl - S >= 0:
+                        assert nl - S < gb + c_u            # slot's previous row no longer needed
+                    row = l_row0 - (1 if ypos else 0) + l_i
+                    start = row * nx + 28 + 64 * l_strip
+                    assert start % 4 == 0 and start >= 0 and start + 72 <= ncells
+                    assert start // nx == row and (start + 71) // nx == row
+                    loads.append((row, l_strip))
+                    nl += 1
+                    l_i += 1
+                    if l_i > l_len:
+                        l_i, l_pos = 0, l_pos + 1
+                        assert l_pos in visible
+                        l_item = items[l_pos]
+                        if l_item < nitems:
+                            l_strip, l_row0, l_len = decode(l_item)
+                assert gb + c_u + 1 < nl
+                jo = gb + c_u + (1 if ypos else 0)
+                jy = gb + c_u + (0 if ypos else 1)
+                y = c_row0 + c_u
+                assert loads[jo] == (y, c_strip)
+                assert loads[jy] == (y - 1 if ypos else y + 1, c_strip)
+                assert nl - 1 < min(jo, jy) + S                 # both still in the ring
+                visible |= set(pending)                          # the row barrier
+                pending = []
+                if not ypos:
+                    for xx in range(64):
+                        c = y * nx + 32 + 64 * c_strip + xx
+                        written[c] = written.get(c, 0) + 1
+                c_u += 1
+                if c_u == c_len:
+                    gb, c_u, c_pos = gb + c_len + 1, 0, c_pos + 1
+                    assert c_pos in visible
+                    c_item = items[c_pos]
+                    if c_item < nitems:
+                        c_strip, c_row0, c_len = decode(c_item)
+                    if ypos:
+                        items[c_pos + 2] = next(dyn)
+                    else:
+                        items[c_pos + 2] = counter[0]
+                        counter[0] += 1
+                        fetched.append(items[c_pos + 2])
+                    pending.append(c_pos + 2)
+    interior = {y * nx + x for y in range(1, ny - 1) for x in range(32, nx - 32)}
+    assert set(written) == interior and all(v == 1 for v in written.values())
+    return strips, nchunks
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 10), (192, 45), (256, 70), (384, 522), (640, 33), (1024, 1000),
+                                   (2048, 2048)])
+@pytest.mark.parametrize("slots", [4, 5])
+@pytest.mark.parametrize("grid", [7, 152, 304])
+def test_march_schedule_covers_interior_once(nx, ny, slots, grid):
+    simulate(nx, ny, slots, grid)
+
+
+def _library():
+    from paper_1308_0692_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 10), (192, 45), (256, 70), (384, 522), (640, 33), (1024, 1000),
+                                   (1024, 1024), (2048, 2048), (4096, 1030)])
+@pytest.mark.parametrize("grid", [7, 152, 304])
+def test_library_plan_equals_model(nx, ny, grid):
+    assert _library().lbm_march_plan(nx, ny, grid) == choose_chunks(nx, ny, grid)
+
+
+def test_library_plan_rejects_unfit_grids():
+    lbm = _library()
+    for nx, ny in [(160, 64), (64, 64), (128, 9)]:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_march_plan(nx, ny, 152)
+        assert e.value.status == lbm.LBM_EUNSUPPORTED
+
+
+def test_chunk_choice_fills_rounds():
+    # 2048^2 on 152 blocks: 31 strips x 44 chunks = 1364 items = 8.97 rounds of 152
+    assert choose_chunks(2048, 2048, 152) == (31, 44)
+    strips, c = choose_chunks(1024, 1024, 152)
+    items = strips * c
+    assert items % 152 == 0 or items % 152 > 0.9 * 152
+    for nx, ny, g in [(2048, 2048, 152), (1024, 1024, 152), (384, 522, 152), (256, 70, 304)]:
+        _, c = choose_chunks(nx, ny, g)
+        assert (ny - 2) // c >= 8
