@@ -109,12 +109,20 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
     // beside the march on the SM resources the march leaves free
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 
-    // per-warp coefficients of the transport of its velocities (velocity k = r*M + ix)
-    float a0r[NV];
+    // coefficients as FP32x2 pairs (both halves equal: one coefficient, two cells), set
+    // once: per velocity of the warp 1 - nu_x - nu_y (k = r*M + ix), per ix nu_x, xi, w
+    float2 a0r[NV], nux2[M], xi2[M], w2[M];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const int r = k / M, ix = k - r * M;
-        a0r[k] = 1.f - a.nux_f[ix] - a.nuy_f[g * RPL + r];
+        const float v = 1.f - a.nux_f[ix] - a.nuy_f[g * RPL + r];
+        a0r[k] = make_float2(v, v);
+    }
+#pragma unroll
+    for (int ix = 0; ix < M; ++ix) {
+        nux2[ix] = make_float2(a.nux_f[ix], a.nux_f[ix]);
+        xi2[ix] = make_float2(a.xi_f[ix], a.xi_f[ix]);
+        w2[ix] = make_float2(a.w1_f[ix], a.w1_f[ix]);
     }
     // plane offset of this lane's copy (lanes < NV issue one line each per row)
     const int kc = lane < NV ? lane : 0;
@@ -201,7 +209,11 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
                 const int iy = g * RPL + r;
                 const float nuy = a.nuy_f[iy];
                 const float2 nuy2 = make_float2(nuy, nuy);
-                float2 R2 = make_float2(0.f, 0.f), X2 = R2;
+                // row sums in NACC independent partial sums (short dependency chains)
+                constexpr int NACC = 4;
+                float2 R2[NACC], X2[NACC];
+#pragma unroll
+                for (int q = 0; q < NACC; ++q) R2[q] = X2[q] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
                     const int k = r * M + ix;
@@ -210,19 +222,19 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
                     const float2 hx = (ix >= M - HALF) ? make_float2(lo[3 + 2 * lane], hc.x)     // xi_x > 0: x - 1
                                                        : make_float2(hc.y, lo[6 + 2 * lane]);    // xi_x < 0: x + 1
                     const float2 hy = *reinterpret_cast<const float2 *>(ynb + k * LINE + 4 + 2 * lane);
-                    const float nux = a.nux_f[ix];
-                    float2 v = __fmul2_rn(make_float2(a0r[k], a0r[k]), hc);
-                    v = __ffma2_rn(make_float2(nux, nux), hx, v);
+                    float2 v = __fmul2_rn(a0r[k], hc);
+                    v = __ffma2_rn(nux2[ix], hx, v);
                     v = __ffma2_rn(nuy2, hy, v);
                     hs[k] = v;
-                    R2 = __fadd2_rn(R2, v);
-                    const float xi = a.xi_f[ix];
-                    X2 = __ffma2_rn(make_float2(xi, xi), v, X2);
+                    R2[ix % NACC] = __fadd2_rn(R2[ix % NACC], v);
+                    X2[ix % NACC] = __ffma2_rn(xi2[ix], v, X2[ix % NACC]);
                 }
+                const float2 R = __fadd2_rn(__fadd2_rn(R2[0], R2[1]), __fadd2_rn(R2[2], R2[3]));
+                const float2 X = __fadd2_rn(__fadd2_rn(X2[0], X2[1]), __fadd2_rn(X2[2], X2[3]));
                 const float xiy = a.xi_f[iy];
-                rho2 = __fadd2_rn(rho2, R2);
-                jx2 = __fadd2_rn(jx2, X2);
-                jy2 = __ffma2_rn(make_float2(xiy, xiy), R2, jy2);
+                rho2 = __fadd2_rn(rho2, R);
+                jx2 = __fadd2_rn(jx2, X);
+                jy2 = __ffma2_rn(make_float2(xiy, xiy), R, jy2);
             }
         }
         s_mom[par][0][g][lane] = rho2;
@@ -254,9 +266,8 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
                 const int k = r * M + ix;
-                const float xi = a.xi_f[ix], w = a.w1_f[ix];
-                const float2 t = __ffma2_rn(make_float2(xi, xi), jj2, q2);
-                const float2 v = __ffma2_rn(make_float2(w, w), t, __fmul2_rn(b2, hs[k]));
+                const float2 t = __ffma2_rn(xi2[ix], jj2, q2);
+                const float2 v = __ffma2_rn(w2[ix], t, __fmul2_rn(b2, hs[k]));
                 if (RESID) {
                     const float2 hc = *reinterpret_cast<const float2 *>(own + k * LINE + 4 + 2 * lane);
                     const float2 d = __fadd2_rn(v, make_float2(-hc.x, -hc.y));

@@ -1,5 +1,9 @@
-"""The paper's comparison of half-range and full-range velocity sets (Figs. 1-2 and the
-Kn = 1 shear-stress statement), computed with the library's FP64 march.
+"""The paper's comparison of half-range and full-range velocity sets, computed with the
+library's FP64 march: the Couette Kn sweep (Figs. 1-2), the Couette profile and shear
+stress at Kn = 1 (Fig. 3 and the statement on the number of full-range nodes), and the
+driven cavity's centre-line profile, lid drag D and vortex flow rate G (Fig. 4, Table 2).
+
+    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2} --out r.json
 
 Couette flow between plates at -u_w and +u_w: for each Knudsen number and velocity set the
 steady state is marched on the GPU to a residual tolerance, and the shear stress (the
@@ -56,3 +60,133 @@ def kn_sweep(kns=(0.01, 0.03, 0.1, 0.3, 1.0, 3.0, 10.0), ny=200, sets=("D2Q^h_16
             "max_abs_err_slip": max(abs(a["slip"] - b["slip"]) for a, b in zip(res[name], ref)),
         }
     return {"kns": list(kns), "ny": ny, "results": res, "vs_reference": summary}
+
+
+# ---------------------------------------------------------------- Couette at Kn = 1 (Fig. 3)
+
+def couette_profile(kind: int, n: int, kn: float = 1.0, ny: int = 200, u_w: float = 0.01, tol: float = 1e-11,
+                    stream=None):
+    """Steady Couette u_x(y)/u_w over the channel (cell centres) and p_xy / p_fm."""
+    vs = lbm.lbm_make_velocity_set(kind, n)
+    prob = lbm.make_problem(lbm.LBM_COUETTE, 1, ny, kn, -u_w, u_w, prec=lbm.LBM_FP64, residual_every=100)
+    sim = lbm.lbm_init(vs, prob, stream=stream)
+    info = lbm.lbm_solve(sim, tol, 5_000_000, 0)
+    fy, _ = lbm.lbm_face_flux(sim)
+    m = lbm.lbm_moments(sim, wall_shear=False)
+    p_fm = -math.sqrt(2.0 / math.pi) * u_w
+    out = {"kn": kn, "ny": ny, "u_over_uw": (m["ux"][:, 0] / u_w).tolist(),
+           "pxy_over_pfm": float(fy[:, 0].mean() / p_fm), "steps": info["steps"]}
+    sim.close()
+    return out
+
+
+def couette_kn1_study(ny: int = 200):
+    """Fig. 3 and the Kn = 1 shear-stress statement: profiles for D2Q^h_16, D2Q_16 and the
+    converged half-range D2Q^h_144; p_xy error of D2Q^h_16 against D2Q^h_144, and of the
+    full-range sets D2Q_{M^2}, M = 4, 6, 8, 12, to find how many full-range nodes per axis
+    reach the half-range 16-velocity accuracy."""
+    import torch
+    stream = torch.cuda.Stream()
+    ref = couette_profile(lbm.LBM_HALF_RANGE_GH, 6, ny=ny, stream=stream)
+    res = {"D2Q^h_144": ref}
+    res["D2Q^h_16"] = couette_profile(lbm.LBM_HALF_RANGE_GH, 2, ny=ny, stream=stream)
+    res["D2Q^h_64"] = couette_profile(lbm.LBM_HALF_RANGE_GH, 4, ny=ny, stream=stream)
+    for mm in (4, 6, 8, 12):
+        res[f"D2Q_{mm * mm}"] = couette_profile(lbm.LBM_FULL_RANGE_GH, mm, ny=ny, stream=stream)
+    u_ref = np.array(ref["u_over_uw"])
+    summary = {}
+    for name, r in res.items():
+        u = np.array(r["u_over_uw"])
+        summary[name] = {"pxy_over_pfm": r["pxy_over_pfm"],
+                         "rel_err_pxy_vs_D2Q^h_144": abs(r["pxy_over_pfm"] - ref["pxy_over_pfm"]) / abs(ref["pxy_over_pfm"]),
+                         "max_abs_err_u_vs_D2Q^h_144": float(np.abs(u - u_ref).max()),
+                         "slip_upper": float(1.0 - u[-1])}
+    return {"kn": 1.0, "ny": ny, "profiles": res, "summary": summary}
+
+
+# ---------------------------------------------------------------- driven cavity (Fig. 4, Table 2)
+
+TABLE2 = {  # Kn: (D BGKW, D D2Q^h_16, D D2Q_16, G BGKW, G D2Q^h_16, G D2Q_16), as printed
+    0.05: (0.258, 0.256, 0.270, 0.154, 0.153, 0.162),
+    0.1: (0.328, 0.327, 0.350, 0.136, 0.128, 0.153),
+    0.2: (0.425, 0.417, 0.467, 0.121, 0.109, 0.148),
+    0.4: (0.385, 0.384, 0.421, 0.110, 0.0961, 0.145),
+}
+
+
+def cavity_solution(kind: int, n: int, kn: float, side: int = 128, u_w: float = 0.01, tol: float = 1e-10,
+                    stream=None):
+    """Steady lid-driven cavity (FP64): the vertical centre-line u_x(1/2, y)/u_w (mean of the
+    two middle columns), the lid's mean shear |p_xy|/u_w, and the flow rate of the main
+    vortex G = integral of u_x/u_w from the vortex centre (the sign change of u_x on the
+    centre line) to the lid."""
+    vs = lbm.lbm_make_velocity_set(kind, n)
+    prob = lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, u_w, prec=lbm.LBM_FP64, residual_every=100)
+    sim = lbm.lbm_init(vs, prob, stream=stream)
+    info = lbm.lbm_solve(sim, tol, 5_000_000, 0)
+    m = lbm.lbm_moments(sim)
+    sim.close()
+    ux = m["ux"] / u_w
+    c = side // 2
+    line = 0.5 * (ux[:, c - 1] + ux[:, c]) if side % 2 == 0 else ux[:, c]
+    y = (np.arange(side) + 0.5) / side
+    # vortex centre: last sign change (negative -> positive) of u_x going up the centre line
+    k = max(i for i in range(side - 1) if line[i] <= 0.0 < line[i + 1])
+    yc = y[k] - line[k] * (y[k + 1] - y[k]) / (line[k + 1] - line[k])
+    ys = np.concatenate([[yc], y[k + 1:], [1.0]])
+    us = np.concatenate([[0.0], line[k + 1:], [line[-1]]])   # the last cell value up to the lid
+    G = float(np.sum(0.5 * (us[1:] + us[:-1]) * np.diff(ys)))   # trapezoid rule
+    return {"kn": kn, "side": side, "steps": info["steps"], "centreline": line.tolist(),
+            "lid_shear_over_uw": float(abs(m["wall_shear"][1]) / u_w), "vortex_centre_y": float(yc), "G": G}
+
+
+def cavity_table2_study(side: int = 128, kns=(0.05, 0.1, 0.2, 0.4)):
+    """Table 2 (D, G) and Fig. 4 (centre-line profiles, L1 distances): D2Q^h_16 and D2Q_16,
+    D2Q^h_64 and D2Q_64, against the library's own D2Q^h_144 solution (the BGKW solutions
+    of the paper's reference are not available here).  The printed Table 2 values are
+    returned beside the computed ones; their normalisation is not stated in the paper, so
+    the ratio computed / printed is reported per column rather than a pass/fail."""
+    import torch
+    stream = torch.cuda.Stream()
+    sets = {"D2Q^h_16": (lbm.LBM_HALF_RANGE_GH, 2), "D2Q_16": (lbm.LBM_FULL_RANGE_GH, 4),
+            "D2Q^h_64": (lbm.LBM_HALF_RANGE_GH, 4), "D2Q_64": (lbm.LBM_FULL_RANGE_GH, 8),
+            "D2Q^h_144": (lbm.LBM_HALF_RANGE_GH, 6)}
+    out = {"side": side, "kns": list(kns), "table2_printed": {str(k): v for k, v in TABLE2.items()}, "runs": {}}
+    for kn in kns:
+        runs = {name: cavity_solution(kind, n, kn, side=side, stream=stream) for name, (kind, n) in sets.items()}
+        ref = np.array(runs["D2Q^h_144"]["centreline"])
+        for r in runs.values():
+            line = np.array(r["centreline"])
+            r["L1_vs_D2Q^h_144"] = float(np.mean(np.abs(line - ref)))
+        out["runs"][str(kn)] = runs
+        if kn in TABLE2:
+            t = TABLE2[kn]
+            out["runs"][str(kn)]["ratios_to_printed"] = {
+                "D_h16": runs["D2Q^h_16"]["lid_shear_over_uw"] / t[1], "D_f16": runs["D2Q_16"]["lid_shear_over_uw"] / t[2],
+                "G_h16": runs["D2Q^h_16"]["G"] / t[4], "G_f16": runs["D2Q_16"]["G"] / t[5]}
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2"])
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--side", type=int, default=128)
+    args = ap.parse_args(argv)
+    if args.study == "kn_sweep":
+        r = kn_sweep()
+    elif args.study == "couette_kn1":
+        r = couette_kn1_study()
+    else:
+        r = cavity_table2_study(side=args.side)
+    with open(args.out, "w") as f:
+        json.dump(r, f, indent=1)
+    short = r.get("summary") or r.get("vs_reference") or {k: v.get("ratios_to_printed") for k, v in r["runs"].items()}
+    print(json.dumps(short), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
