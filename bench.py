@@ -321,6 +321,8 @@ def run_own(args, dist: Dist):
     if not args.no_extras:
         out["fp64"] = run_fp64_same_workload(vs, dist)
         out["time_to_residual"] = run_time_to_residual(dist)
+        if dist.rank == 0:
+            out["configs_time_to_residual"] = run_configs_time_to_residual()
     sim.close()
     del buf
     return out
@@ -478,6 +480,50 @@ def run_time_to_residual(dist, count=32):
     return out
 
 
+def run_configs_time_to_residual():
+    """The small configurations solved to their residual tolerance three ways: the CPU oracle
+    (FP64, all host cores), the GPU FP64 march, and the GPU FP32 march with FP64 defect
+    correction; steps, seconds and the GPU results' distance to the oracle's (max |du|/u_w).
+    Couette ny = 100 (D2Q^h_64, plates +-0.01, Kn 0.1 / 0.01 / 10, r < 1e-10); cavity 128^2
+    (lid 0.01, D2Q^h_64 at Kn 0.1 and 1, D2Q9 at Kn 0.1, r < 1e-8); cold starts, residual
+    checked every 100 steps."""
+    import numpy as np
+    import torch
+
+    from oracle import march as om
+    from paper_1308_0692_gb300 import lbm
+    om.build()
+    cases = [("couette", "half", 4, om.COUETTE, 1, 100, kn, 0.01, -0.01, 1e-10) for kn in (0.1, 0.01, 10.0)]
+    cases += [("cavity", "half", 4, om.CAVITY, 128, 128, kn, 0.0, 0.01, 1e-8) for kn in (0.1, 1.0)]
+    cases += [("cavity", "full", 3, om.CAVITY, 128, 128, 0.1, 0.0, 0.01, 1e-8)]
+    out = []
+    for name, kind, n, geom, nx, ny, kn, ub, ut, tol in cases:
+        uw = max(abs(ub), abs(ut))
+        p = om.make_problem(kind, n, geom, nx, ny, kn, ub, ut)
+        t0 = time.perf_counter()
+        h, steps_cpu, _ = p.march(p.zeros(), 5_000_000, every=100, tol=tol)
+        t_cpu = time.perf_counter() - t0
+        m_cpu = p.moments(h)
+        vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH if kind == "half" else lbm.LBM_FULL_RANGE_GH, n)
+        rec = {"case": f"{name} {nx}x{ny} {'D2Q^h' if kind == 'half' else 'D2Q'}_{p.n} Kn={kn}", "tol": tol,
+               "oracle": {"seconds": t_cpu, "steps": steps_cpu, "threads": os.cpu_count()}}
+        for label, prec, refine in (("gpu_fp64", lbm.LBM_FP64, 0), ("gpu_fp32_dc", lbm.LBM_FP32_PERTURB, 3)):
+            prob = lbm.make_problem(geom, nx, ny, kn, ub, ut, prec=prec, residual_every=100)
+            sim = lbm.lbm_init(vs, prob, stream=lbm.PrivateStream())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = lbm.lbm_solve(sim, tol, 5_000_000, refine, tol)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            m = lbm.lbm_moments(sim, wall_shear=False)
+            err = max(np.abs(m["ux"] - m_cpu["ux"]).max(), np.abs(m["uy"] - m_cpu["uy"]).max()) / uw
+            rec[label] = {"seconds": el, "steps": info["steps"] + info["correction_steps"],
+                          "max_du_over_uw_vs_oracle": float(err), "speedup_vs_oracle": t_cpu / el}
+            sim.close()
+        out.append(rec)
+    return out
+
+
 # ---------------------------------------------------------------- CPU oracle arm
 def _oracle_setup(rows: int):
     import numpy as np
@@ -590,10 +636,12 @@ def main(argv=None):
         if dist.world == 1 and not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             ups, sample = oracle_sample(12.0, threads)
+            ups1, sample1 = oracle_sample(4.0, 1)
             out["cpu_baseline"] = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
                                    "sample": f"oracle FP64 step on {sample['cells_per_pass']} cells "
                                              f"(8 middle rows) of the 2048x2048 x 144 workload, "
-                                             f"{sample['passes']} passes in {sample['seconds']:.1f} s"}
+                                             f"{sample['passes']} passes in {sample['seconds']:.1f} s",
+                                   "single_thread_value": ups1}
         print(json.dumps(out), flush=True)
     dist.close()
     return 0
