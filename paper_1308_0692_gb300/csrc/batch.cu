@@ -979,8 +979,8 @@ lbm_status lbm_batch_warm_start(lbm_batch *b, int i, lbm_mlp *mlp, double kn, do
     // the MLP runs on its own stream: order the reconstruction after it
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
-        e = launch_warm_state(pred, I.ncells, b->m, b->d_tab, b->d_tab + LBM_MAX_M, u_w * I.inv_u_ref,
-                              (float *)b->buf[0] + I.off, LBM_FP32_PERTURB, b->stream);
+        e = launch_warm_state(pred, I.nx, I.ny, I.ncells, I.nx, b->m, b->d_tab, b->d_tab + LBM_MAX_M,
+                              u_w * I.inv_u_ref, (float *)b->buf[0] + I.off, LBM_FP32_PERTURB, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("warm start of an instance: ") + cudaGetErrorString(e));
 }

@@ -239,18 +239,29 @@ void fill_tables(lbm_sim *s, std::vector<double> &t64, std::vector<float> &t32, 
     hdr.inv_dy_wall = 1.0 / dyw;
 }
 
+bool planar(const lbm_sim *s) { return s->args.pa == s->ncells; }
+
+// FP64 staging area for host transfers of the state: the two spare float arrays (adjacent,
+// 8 bytes per value) of an FP32 simulation, the other state buffer of an FP64 one
+double *staging(lbm_sim *s, const void *state)
+{
+    if (s->prob.prec != LBM_FP64) return (double *)s->buf[2];
+    return (double *)(state == s->buf[0] ? s->buf[1] : s->buf[0]);
+}
+
+// host FP64 [n][ny][nx] -> device state `dst` in the simulation's layout and precision
 lbm_status upload_state(lbm_sim *s, const double *h, void *dst)
 {
     const size_t nvals = (size_t)s->nv * s->ncells;
     cudaError_t e;
-    if (s->prob.prec == LBM_FP64) {
+    if (s->prob.prec == LBM_FP64 && planar(s)) {
         e = cudaMemcpyAsync(dst, h, nvals * sizeof(double), cudaMemcpyHostToDevice, s->stream);
     } else {
-        // FP64 host values staged in the two spare float arrays (adjacent, 8 bytes per
-        // value in total), rounded to float on the device
-        double *stage = (double *)s->buf[2];
+        double *stage = staging(s, dst);
         e = cudaMemcpyAsync(stage, h, nvals * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = launch_convert(stage, (float *)dst, (long)nvals, s->stream);
+        if (e == cudaSuccess)
+            e = launch_relayout(s->prob.prec, true, stage, dst, s->nv, s->prob.nx, s->prob.ny, s->args.pa,
+                                s->args.py, s->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "uploading the state");
@@ -269,6 +280,17 @@ void fill_args(lbm_sim *s, const TableHeader &hdr)
     a.nx = p.nx;
     a.ny = p.ny;
     a.ncells = s->ncells;
+    // rows of the velocity planes interleaved ([y][a][x]) for grids with rows of 64 cells or
+    // more: a row step of the interior march then touches one contiguous stretch of memory
+    // instead of one stretch in each of n planes; planar [a][y][x] otherwise (a Couette
+    // column has one cell per row)
+    if (p.nx >= 64) {
+        a.pa = p.nx;
+        a.py = (long)v.m * v.m * p.nx;
+    } else {
+        a.pa = s->ncells;
+        a.py = p.nx;
+    }
     a.cavity = p.geom == LBM_CAVITY;
     a.homogeneous = 0;
     const bool column = p.geom == LBM_COUETTE && p.nx == 1;
@@ -854,8 +876,8 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
     if (st != LBM_OK) return st;
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "warm start");
-    e = launch_warm_state(pred, s->ncells, s->vs.m, s->hdr->xi1, s->hdr->w1, u_w / s->u_ref,
-                                      s->buf[s->cur], s->prob.prec, s->stream);
+    e = launch_warm_state(pred, s->prob.nx, s->prob.ny, s->args.pa, s->args.py, s->vs.m, s->hdr->xi1, s->hdr->w1,
+                          u_w / s->u_ref, s->buf[s->cur], s->prob.prec, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the warm-start state");
 }
@@ -869,6 +891,8 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
                     warps_per_segment, prefetch, s->vs.m);
     if (prefetch >= 2 && (s->prob.geom != LBM_CAVITY || s->prob.nx % 4 != 0 || s->ncells % 4 != 0))
         return fail(LBM_EUNSUPPORTED, "TMA staging needs a cavity with nx and the cell count multiples of 4");
+    if ((prefetch == 2 || prefetch == 3) && !planar(s))
+        return fail(LBM_EUNSUPPORTED, "the TMA segment kernels need the planar state layout (nx < 64)");
     if (prefetch >= 4 && (s->prob.nx % 64 != 0 || s->prob.nx < 128 || s->prob.ny < 10))
         return fail(LBM_EUNSUPPORTED, "the column march needs nx a multiple of 64, nx >= 128 and ny >= 10");
     if (prefetch == 2 || prefetch == 3) {
@@ -916,8 +940,8 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     const int m = s->vs.m;
-    cudaError_t e = launch_moments(s->prob.prec, s->buf[s->cur], s->tab64, s->hdr, m, s->prob.nx,
-                                   s->prob.ny, s->u_ref, s->moments, s->stream);
+    cudaError_t e = launch_moments(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m,
+                                   s->prob.nx, s->prob.ny, s->u_ref, s->moments, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the moments kernel");
     double *outs[6] = {rho, ux, uy, pxx, pxy, pyy};
     for (int k = 0; k < 6; ++k) {
@@ -929,8 +953,8 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
     if (wall_shear) {
         const int nx = s->prob.nx, ny = s->prob.ny;
         const bool cav = s->prob.geom == LBM_CAVITY;
-        e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->tab64, s->hdr, m, nx, ny, cav,
-                             s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+        e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
+                             cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
         std::vector<double> fy((size_t)(ny + 1) * nx), fx(cav ? (size_t)ny * (nx + 1) : 0);
         e = cudaMemcpyAsync(fy.data(), s->flux_y, sizeof(double) * fy.size(), cudaMemcpyDeviceToHost, s->stream);
@@ -963,8 +987,8 @@ lbm_status lbm_face_flux(lbm_sim *s, double *flux_y, double *flux_x)
     const int nx = s->prob.nx, ny = s->prob.ny;
     const bool cav = s->prob.geom == LBM_CAVITY;
     if (flux_x && !cav) return fail(LBM_EINVAL, "flux_x is defined for the cavity only");
-    cudaError_t e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->tab64, s->hdr, s->vs.m, nx,
-                                     ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+    cudaError_t e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr,
+                                     s->vs.m, nx, ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
     if (flux_y)
         e = cudaMemcpyAsync(flux_y, s->flux_y, sizeof(double) * (size_t)(ny + 1) * nx,
@@ -981,11 +1005,14 @@ lbm_status lbm_get_state(lbm_sim *s, double *h)
     if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
     const size_t nvals = (size_t)s->nv * s->ncells;
     cudaError_t e;
-    if (s->prob.prec == LBM_FP64) {
+    if (s->prob.prec == LBM_FP64 && planar(s)) {
         e = cudaMemcpyAsync(h, s->buf[s->cur], nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     } else {
-        double *stage = (double *)s->buf[2];
-        e = launch_widen((const float *)s->buf[s->cur], stage, (long)nvals, s->stream);
+        // the staging area of an FP64 simulation is its other state buffer, which the next
+        // step overwrites anyway
+        double *stage = staging(s, s->buf[s->cur]);
+        e = launch_relayout(s->prob.prec, false, stage, s->buf[s->cur], s->nv, s->prob.nx, s->prob.ny, s->args.pa,
+                            s->args.py, s->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h, stage, nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     }
@@ -1005,7 +1032,8 @@ lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
     cudaError_t e = cudaMemcpyAsync(s->moments, moments, sizeof(double) * 6 * s->ncells, cudaMemcpyHostToDevice,
                                     s->stream);
     if (e == cudaSuccess)
-        e = launch_moments_state(s->prob.prec, s->moments, s->ncells, s->vs.m, s->hdr, s->u_ref, s->buf[s->cur],
+        e = launch_moments_state(s->prob.prec, s->moments, s->prob.nx, s->prob.ny, s->args.pa, s->args.py, s->vs.m,
+                                 s->hdr, s->u_ref, s->buf[s->cur],
                                  s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the state from moments");
@@ -1016,6 +1044,14 @@ lbm_status lbm_state_device(lbm_sim *s, void **ptr, long *step)
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (ptr) *ptr = s->buf[s->cur];
     if (step) *step = s->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_state_layout(const lbm_sim *s, long *plane_pitch, long *row_pitch)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (plane_pitch) *plane_pitch = s->args.pa;
+    if (row_pitch) *row_pitch = s->args.py;
     return LBM_OK;
 }
 

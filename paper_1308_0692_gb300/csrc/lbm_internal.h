@@ -42,6 +42,9 @@ struct StepArgs {
     double *partials;     // per-block residual partial sums [2 * gridDim.x]
     int nx, ny;
     long ncells;
+    // state layout: value (velocity a, cell x, y) at a * pa + y * py + x; planar
+    // [a][y][x] (pa = ncells, py = nx) or row-interleaved [y][a][x] (pa = nx, py = n nx)
+    long pa, py;
     int cavity;
     int homogeneous;      // drop the wall driving terms (correction sweeps)
     const int *wall_segs; // segments (32 consecutive cells) that contain a wall cell
@@ -88,22 +91,26 @@ cudaError_t launch_finalize_pairs(const double *partials, int nparts, double *ou
 cudaError_t launch_norms(const void *a, const void *b, long count, int prec, double *partials,
                          int nparts, double *out, cudaStream_t s);
 int norms_blocks(long count);
-cudaError_t launch_moments(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+cudaError_t launch_moments(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
                            int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s);
-cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+cudaError_t launch_face_flux(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
                              int m, int nx, int ny, int cavity, double u_ref, double *flux_y,
                              double *flux_x, double *wall_sums, cudaStream_t s);
+// copy between the host-order planar FP64 state [a][y][x] and a device state of the given
+// layout and precision (to_layout: planar FP64 -> layout; else layout -> planar FP64)
+cudaError_t launch_relayout(int prec, bool to_layout, double *planar, void *state, int n, int nx, int ny,
+                            long pa, long py, cudaStream_t s);
 
 cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s);
 // state h from device FP64 moments [6][ncells] (rho, u_x, u_y, P_xx, P_xy, P_yy)
-cudaError_t launch_moments_state(int prec, const double *mom, long ncells, int m, const TableHeader *hdr,
-                                 double u_ref, void *h, cudaStream_t s);
+cudaError_t launch_moments_state(int prec, const double *mom, int nx, int ny, long pa, long py, int m,
+                                 const TableHeader *hdr, double u_ref, void *h, cudaStream_t s);
 cudaError_t launch_add_f32(float *y, const float *x, long count, cudaStream_t s);
 cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t s);
 
 // warm start (mlp.cu): h from normalised predicted moments [ncells][6]
-cudaError_t launch_warm_state(const float *pred, long ncells, int m, const double *xi1, const double *w1,
-                              double uw_over_uref, void *h, int prec, cudaStream_t s);
+cudaError_t launch_warm_state(const float *pred, int nx, int ny, long pa, long py, int m, const double *xi1,
+                              const double *w1, double uw_over_uref, void *h, int prec, cudaStream_t s);
 
 // Host quadrature (quadrature.cpp)
 bool lbm_rule_1d(int kind, int n, std::vector<double> &nodes, std::vector<double> &weights);

@@ -295,10 +295,11 @@ __global__ void features_kernel(int nx, int ny, float f2, float f3, float *x)
 // second-order Hermite reconstruction from normalised predicted moments
 // pred[c][0..5] = ((rho-1)/u_w, u_x/u_w, u_y/u_w, (P_xx-1)/u_w, P_xy/u_w, (P_yy-1)/u_w)
 template <typename T>
-__global__ void warm_state_kernel(const float *pred, long ncells, int m, const double *xi1, const double *w1,
-                                  double uw_over_uref, T *h)
+__global__ void warm_state_kernel(const float *pred, int nx, long ncells, long pa, long py, int m, const double *xi1,
+                                  const double *w1, double uw_over_uref, T *h)
 {
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
+        const long y = c / nx, co = y * py + (c - y * nx);
         const double s = uw_over_uref;
         const double rp = s * pred[c * 6 + 0];
         const double jx = s * pred[c * 6 + 1];   // rho u / u_ref, linearised rho = 1
@@ -311,7 +312,7 @@ __global__ void warm_state_kernel(const float *pred, long ncells, int m, const d
                 const double v = w1[ix] * w1[iy] *
                                  (rp + ex * jx + ey * jy +
                                   0.5 * ((pxx - rp) * (ex * ex - 1.0) + 2.0 * pxy * ex * ey + (pyy - rp) * (ey * ey - 1.0)));
-                h[(long)(iy * m + ix) * ncells + c] = (T)v;
+                h[(long)(iy * m + ix) * pa + co] = (T)v;
             }
         }
     }
@@ -641,13 +642,14 @@ lbm_status lbm_mlp_features(lbm_mlp *p, int nx, int ny, double kn, double u_w, f
 
 }  // extern "C"
 
-cudaError_t launch_warm_state(const float *pred, long ncells, int m, const double *xi1, const double *w1,
-                              double uw_over_uref, void *h, int prec, cudaStream_t s)
+cudaError_t launch_warm_state(const float *pred, int nx, int ny, long pa, long py, int m, const double *xi1,
+                              const double *w1, double uw_over_uref, void *h, int prec, cudaStream_t s)
 {
+    const long ncells = (long)nx * ny;
     const int nb = blocks_for(ncells);
     if (prec == LBM_FP64)
-        warm_state_kernel<double><<<nb, 256, 0, s>>>(pred, ncells, m, xi1, w1, uw_over_uref, (double *)h);
+        warm_state_kernel<double><<<nb, 256, 0, s>>>(pred, nx, ncells, pa, py, m, xi1, w1, uw_over_uref, (double *)h);
     else
-        warm_state_kernel<float><<<nb, 256, 0, s>>>(pred, ncells, m, xi1, w1, uw_over_uref, (float *)h);
+        warm_state_kernel<float><<<nb, 256, 0, s>>>(pred, nx, ncells, pa, py, m, xi1, w1, uw_over_uref, (float *)h);
     return cudaGetLastError();
 }

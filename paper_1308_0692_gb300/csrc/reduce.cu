@@ -84,17 +84,18 @@ __global__ void __launch_bounds__(256) norms_kernel(const T *a, const T *b, long
 
 // Per cell: rho, ux, uy, pxx, pxy, pyy (linearised, Eq. (1) units).
 template <typename T>
-__global__ void moments_kernel(const T *h, const TableHeader *hdr, int m, long ncells,
+__global__ void moments_kernel(const T *h, long pa, long py, int nx, const TableHeader *hdr, int m, long ncells,
                                double u_ref, double *out)
 {
     const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
+    const long y = c / nx, co = y * py + (c - y * nx);
     double s0 = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
     for (int iy = 0; iy < m; ++iy) {
         const double ey = hdr->xi1[iy];
         for (int ix = 0; ix < m; ++ix) {
             const double ex = hdr->xi1[ix];
-            const double v = (double)h[(long)(iy * m + ix) * ncells + c];
+            const double v = (double)h[(long)(iy * m + ix) * pa + co];
             s0 += v;
             sx += ex * v;
             sy += ey * v;
@@ -112,33 +113,32 @@ __global__ void moments_kernel(const T *h, const TableHeader *hdr, int m, long n
     out[5 * ncells + c] = 1.0 + u_ref * syy;
 }
 
-// rho'_w of a wall face of cell c; dir: 0 bottom, 1 top, 2 left, 3 right
+// rho'_w of a wall face of the cell at plane offset co; dir: 0 bottom, 1 top, 2 left, 3 right
 template <typename T>
-__device__ double wall_rho(const T *h, const TableHeader *hdr, int m, long ncells, long c, int dir)
+__device__ double wall_rho(const T *h, const TableHeader *hdr, int m, long pa, long co, int dir)
 {
     double s = 0.0;
     for (int iy = 0; iy < m; ++iy) {
         for (int ix = 0; ix < m; ++ix) {
             const double xn = (dir == 0) ? hdr->xi1[iy] : (dir == 1) ? -hdr->xi1[iy]
                             : (dir == 2) ? hdr->xi1[ix] : -hdr->xi1[ix];
-            if (xn < 0.0) s -= xn * (double)h[(long)(iy * m + ix) * ncells + c];
+            if (xn < 0.0) s -= xn * (double)h[(long)(iy * m + ix) * pa + co];
         }
     }
     return s * ((dir < 2) ? hdr->inv_dy_wall : hdr->inv_dx_wall);
 }
 
 template <typename T>
-__global__ void face_flux_y_kernel(const T *h, const double *tab, const TableHeader *hdr, int m,
+__global__ void face_flux_y_kernel(const T *h, long pa, long py, const double *tab, const TableHeader *hdr, int m,
                                    int nx, int ny, double u_ref, double *out)
 {
     const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nfaces = (long)(ny + 1) * nx;
     if (f >= nfaces) return;
-    const long ncells = (long)nx * ny;
     const int j = (int)(f / nx), x = (int)(f - (long)j * nx);
-    const long below = (long)(j - 1) * nx + x, above = (long)j * nx + x;
-    const double rb = (j == 0) ? wall_rho(h, hdr, m, ncells, above, 0) : 0.0;
-    const double rt = (j == ny) ? wall_rho(h, hdr, m, ncells, below, 1) : 0.0;
+    const long below = (long)(j - 1) * py + x, above = (long)j * py + x;
+    const double rb = (j == 0) ? wall_rho(h, hdr, m, pa, above, 0) : 0.0;
+    const double rt = (j == ny) ? wall_rho(h, hdr, m, pa, below, 1) : 0.0;
     double s = 0.0;
     for (int iy = 0; iy < m; ++iy) {
         const double ey = hdr->xi1[iy];
@@ -148,10 +148,10 @@ __global__ void face_flux_y_kernel(const T *h, const double *tab, const TableHea
             double v;
             if (ey > 0.0)
                 v = (j == 0) ? rb * tab[TAB_GB_LIN * LBM_MAX_V + al] + tab[TAB_GB_C * LBM_MAX_V + al]
-                             : (double)h[(long)al * ncells + below];
+                             : (double)h[(long)al * pa + below];
             else
                 v = (j == ny) ? rt * tab[TAB_GT_LIN * LBM_MAX_V + al] + tab[TAB_GT_C * LBM_MAX_V + al]
-                              : (double)h[(long)al * ncells + above];
+                              : (double)h[(long)al * pa + above];
             s += hdr->xi1[ix] * ey * v;
         }
     }
@@ -159,17 +159,16 @@ __global__ void face_flux_y_kernel(const T *h, const double *tab, const TableHea
 }
 
 template <typename T>
-__global__ void face_flux_x_kernel(const T *h, const double *tab, const TableHeader *hdr, int m,
+__global__ void face_flux_x_kernel(const T *h, long pa, long py, const double *tab, const TableHeader *hdr, int m,
                                    int nx, int ny, double u_ref, double *out)
 {
     const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nfaces = (long)ny * (nx + 1);
     if (f >= nfaces) return;
-    const long ncells = (long)nx * ny;
     const int y = (int)(f / (nx + 1)), i = (int)(f - (long)y * (nx + 1));
-    const long left = (long)y * nx + i - 1, right = (long)y * nx + i;
-    const double rl = (i == 0) ? wall_rho(h, hdr, m, ncells, right, 2) : 0.0;
-    const double rr = (i == nx) ? wall_rho(h, hdr, m, ncells, left, 3) : 0.0;
+    const long left = (long)y * py + i - 1, right = (long)y * py + i;
+    const double rl = (i == 0) ? wall_rho(h, hdr, m, pa, right, 2) : 0.0;
+    const double rr = (i == nx) ? wall_rho(h, hdr, m, pa, left, 3) : 0.0;
     double s = 0.0;
     for (int iy = 0; iy < m; ++iy) {
         const double ey = hdr->xi1[iy];
@@ -179,9 +178,9 @@ __global__ void face_flux_x_kernel(const T *h, const double *tab, const TableHea
             const int al = iy * m + ix;
             double v;
             if (ex > 0.0)
-                v = (i == 0) ? rl * tab[TAB_W * LBM_MAX_V + al] : (double)h[(long)al * ncells + left];
+                v = (i == 0) ? rl * tab[TAB_W * LBM_MAX_V + al] : (double)h[(long)al * pa + left];
             else
-                v = (i == nx) ? rr * tab[TAB_W * LBM_MAX_V + al] : (double)h[(long)al * ncells + right];
+                v = (i == nx) ? rr * tab[TAB_W * LBM_MAX_V + al] : (double)h[(long)al * pa + right];
             s += ex * ey * v;
         }
     }
@@ -207,11 +206,12 @@ __global__ void widen_kernel(const float *src, double *dst, long count)
 // rho' delta_ij)(xi_i xi_j - delta_ij)] with rho' = (rho - 1)/u_ref, j' = rho u / u_ref,
 // P' = (P - I)/u_ref (the inverse of the moment map of lbm_moments on sets exact to degree 4).
 template <typename T>
-__global__ void moments_state_kernel(const double *mom, long ncells, int m, const TableHeader *hdr,
-                                     double inv_u_ref, T *h)
+__global__ void moments_state_kernel(const double *mom, int nx, long ncells, long pa, long py, int m,
+                                     const TableHeader *hdr, double inv_u_ref, T *h)
 {
     const long stride = (long)gridDim.x * blockDim.x;
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += stride) {
+        const long y = c / nx, co = y * py + (c - y * nx);
         const double rho = mom[c];
         const double rp = (rho - 1.0) * inv_u_ref;
         const double jx = rho * mom[ncells + c] * inv_u_ref, jy = rho * mom[2 * ncells + c] * inv_u_ref;
@@ -224,9 +224,26 @@ __global__ void moments_state_kernel(const double *mom, long ncells, int m, cons
                 const double v = hdr->w1[ix] * hdr->w1[iy] *
                                  (rp + ex * jx + ey * jy +
                                   0.5 * ((pxx - rp) * (ex * ex - 1.0) + 2.0 * pxy * ex * ey + (pyy - rp) * (ey * ey - 1.0)));
-                h[(long)(iy * m + ix) * ncells + c] = (T)v;
+                h[(long)(iy * m + ix) * pa + co] = (T)v;
             }
         }
+    }
+}
+
+// planar FP64 [a][c] <-> state of layout (pa, py) and type T
+template <typename T>
+__global__ void relayout_kernel(bool to_layout, double *planar, T *state, int n, int nx, long ncells, long pa,
+                                long py)
+{
+    const long total = (long)n * ncells, stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const long al = i / ncells, c = i - al * ncells;
+        const long y = c / nx;
+        const long o = al * pa + y * py + (c - y * nx);
+        if (to_layout)
+            state[o] = (T)planar[i];
+        else
+            planar[i] = (double)state[o];
     }
 }
 
@@ -238,13 +255,25 @@ __global__ void axpy_kernel(float *y, const float *x, long count)
 
 }  // namespace
 
-cudaError_t launch_moments_state(int prec, const double *mom, long ncells, int m, const TableHeader *hdr,
-                                 double u_ref, void *h, cudaStream_t s)
+cudaError_t launch_moments_state(int prec, const double *mom, int nx, int ny, long pa, long py, int m,
+                                 const TableHeader *hdr, double u_ref, void *h, cudaStream_t s)
 {
+    const long ncells = (long)nx * ny;
     if (prec == LBM_FP64)
-        moments_state_kernel<double><<<152 * 8, 256, 0, s>>>(mom, ncells, m, hdr, 1.0 / u_ref, (double *)h);
+        moments_state_kernel<double><<<152 * 8, 256, 0, s>>>(mom, nx, ncells, pa, py, m, hdr, 1.0 / u_ref, (double *)h);
     else
-        moments_state_kernel<float><<<152 * 8, 256, 0, s>>>(mom, ncells, m, hdr, 1.0 / u_ref, (float *)h);
+        moments_state_kernel<float><<<152 * 8, 256, 0, s>>>(mom, nx, ncells, pa, py, m, hdr, 1.0 / u_ref, (float *)h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout(int prec, bool to_layout, double *planar, void *state, int n, int nx, int ny,
+                            long pa, long py, cudaStream_t s)
+{
+    const long ncells = (long)nx * ny;
+    if (prec == LBM_FP64)
+        relayout_kernel<double><<<152 * 8, 256, 0, s>>>(to_layout, planar, (double *)state, n, nx, ncells, pa, py);
+    else
+        relayout_kernel<float><<<152 * 8, 256, 0, s>>>(to_layout, planar, (float *)state, n, nx, ncells, pa, py);
     return cudaGetLastError();
 }
 
@@ -303,20 +332,20 @@ cudaError_t launch_norms(const void *a, const void *b, long count, int prec, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+cudaError_t launch_moments(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
                            int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s)
 {
     (void)tab64;
     const long ncells = (long)nx * ny;
     const int grid = (int)((ncells + 255) / 256);
     if (prec == 0)
-        moments_kernel<double><<<grid, 256, 0, s>>>((const double *)h, hdr, m, ncells, u_ref, out6);
+        moments_kernel<double><<<grid, 256, 0, s>>>((const double *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
     else
-        moments_kernel<float><<<grid, 256, 0, s>>>((const float *)h, hdr, m, ncells, u_ref, out6);
+        moments_kernel<float><<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
     return cudaGetLastError();
 }
 
-cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const TableHeader *hdr,
+cudaError_t launch_face_flux(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
                              int m, int nx, int ny, int cavity, double u_ref, double *flux_y,
                              double *flux_x, double *wall_sums, cudaStream_t s)
 {
@@ -325,17 +354,17 @@ cudaError_t launch_face_flux(int prec, const void *h, const double *tab64, const
     const long nx_faces = (long)ny * (nx + 1);
     if (prec == 0)
         face_flux_y_kernel<double><<<(int)((ny_faces + 255) / 256), 256, 0, s>>>(
-            (const double *)h, tab64, hdr, m, nx, ny, u_ref, flux_y);
+            (const double *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_y);
     else
         face_flux_y_kernel<float><<<(int)((ny_faces + 255) / 256), 256, 0, s>>>(
-            (const float *)h, tab64, hdr, m, nx, ny, u_ref, flux_y);
+            (const float *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_y);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !cavity || !flux_x) return e;
     if (prec == 0)
         face_flux_x_kernel<double><<<(int)((nx_faces + 255) / 256), 256, 0, s>>>(
-            (const double *)h, tab64, hdr, m, nx, ny, u_ref, flux_x);
+            (const double *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_x);
     else
         face_flux_x_kernel<float><<<(int)((nx_faces + 255) / 256), 256, 0, s>>>(
-            (const float *)h, tab64, hdr, m, nx, ny, u_ref, flux_x);
+            (const float *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_x);
     return cudaGetLastError();
 }

@@ -79,6 +79,7 @@ def _load():
         "lbm_set_state": (st, [_vp, _dp]),
         "lbm_set_moments": (st, [_vp, _dp]),
         "lbm_state_device": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_long)]),
+        "lbm_state_layout": (st, [_vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
         "lbm_norms_scratch_bytes": (st, [ctypes.c_long, ctypes.POINTER(ctypes.c_size_t)]),
         "lbm_norms": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp]),
         "lbm_norms_noalloc": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, _vp]),
@@ -341,6 +342,13 @@ def lbm_state_device(sim: Sim):
     p, s = _vp(), ctypes.c_long()
     _check(_load().lbm_state_device(sim.handle, ctypes.byref(p), ctypes.byref(s)))
     return p.value, s.value
+
+
+def lbm_state_layout(sim: Sim):
+    """(plane_pitch, row_pitch) of the device state: element a * plane_pitch + y * row_pitch + x."""
+    pa, py = ctypes.c_long(), ctypes.c_long()
+    _check(_load().lbm_state_layout(sim.handle, ctypes.byref(pa), ctypes.byref(py)))
+    return pa.value, py.value
 
 
 def lbm_norms_scratch_bytes(count: int) -> int:

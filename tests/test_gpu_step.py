@@ -60,6 +60,8 @@ CASES = [
     ("half", 6, CAVITY, 45, 38, 0.05, 0.0, 0.01),          # D2Q^h_144
     ("half", 4, CAVITY, 2, 2, 0.1, 0.0, 0.01),             # smallest cavity
     ("half", 4, COUETTE, 1, 2, 0.1, 0.01, -0.01),          # smallest channel
+    ("half", 2, COUETTE, 70, 20, 0.2, 0.01, -0.01),        # periodic rows of >= 64 cells (interleaved rows)
+    ("half", 6, CAVITY, 96, 33, 0.05, 0.0, 0.01),          # D2Q^h_144, interleaved rows
 ]
 
 
@@ -172,12 +174,14 @@ def test_sims_sharing_a_stream_from_two_threads():
         assert np.array_equal(ga, gb) and ra == rb
 
 
+@pytest.mark.parametrize("nx,ny", [(40, 30), (96, 70)])
 @pytest.mark.parametrize("prec,tol", [(lbm.LBM_FP64, 1e-13), (lbm.LBM_FP32_PERTURB, 1e-6)])
-def test_set_moments_matches_oracle_and_round_trips(prec, tol):
+def test_set_moments_matches_oracle_and_round_trips(prec, tol, nx, ny):
     """lbm_set_moments builds the oracle's Hermite state from six moment fields, and
-    lbm_moments gives the fields back (the set D2Q^h_64 is exact to degree 4)."""
+    lbm_moments gives the fields back (the set D2Q^h_64 is exact to degree 4); planar and
+    row-interleaved state layouts."""
     from oracle.mlp import moments_to_h
-    nx, ny, u_ref = 40, 30, 0.01
+    u_ref = 0.01
     p = oracle_problem("half", 4, CAVITY, nx, ny, 0.1, 0.0, u_ref)
     y, x = np.mgrid[0:ny, 0:nx] / np.array([[[ny]], [[nx]]])
     mom = {"rho": 1 + u_ref * 0.3 * np.sin(3 * x) * np.cos(2 * y), "ux": u_ref * 0.8 * np.cos(4 * y),
@@ -308,11 +312,15 @@ def test_full_size_bench_variants(bench_case, variant):
         lbm.lbm_step(sim, 1)
         ptr, step = lbm.lbm_state_device(sim)
         assert step == 1
+        pa, py = lbm.lbm_state_layout(sim)
+        assert (pa, py) == (2048, 144 * 2048)          # rows of the planes interleaved
         off = ptr - buf.data_ptr()
         nbytes = 4 * p.n * p.ncells
         torch.cuda.synchronize()
-        state = buf[off:off + nbytes].view(torch.float32).view(p.n, p.ncells)
-        got = state[:, idx].double().cpu().numpy().T
+        state = buf[off:off + nbytes].view(torch.float32)
+        cy, cx = idx // 2048, idx % 2048
+        elems = torch.arange(p.n, device="cuda")[:, None] * pa + (cy * py + cx)[None, :]
+        got = state[elems].double().cpu().numpy().T
         assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * np.abs(ref).max(), (variant, residual_every)
         if residual_every == 1:
             r, st = lbm.lbm_residual(sim)
@@ -331,8 +339,11 @@ def _host_state_for(p, seed, prec):
 
 
 @pytest.mark.parametrize("n_half,nx,ny,variants", [
-    (4, 68, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2), (2, 3), (4, 3)]),
-    (6, 64, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2), (3, 3), (6, 3)]),
+    # planar state layout (nx < 64): every segment variant incl. the TMA-staged ones
+    (4, 60, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2), (2, 3), (4, 3)]),
+    (6, 60, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2), (3, 3), (6, 3)]),
+    # rows of the planes interleaved (nx >= 64): register-path segment variants
+    (6, 100, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1)]),
 ])
 def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
     """Every kernel variant (warps per segment; register, prefetched or TMA-staged loads) gives
@@ -404,6 +415,18 @@ def test_column_march_rejected_where_strips_do_not_fit():
     sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 128, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP64))
     with pytest.raises(lbm.LBMError):
         lbm.lbm_set_variant(sim, 6, 4)
+
+
+def test_tma_segment_variants_rejected_for_interleaved_rows():
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
+    sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 128, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
+    assert lbm.lbm_state_layout(sim) == (128, 144 * 128)
+    for pf in (2, 3):
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_set_variant(sim, 6, pf)
+        assert e.value.status == lbm.LBM_EUNSUPPORTED
+    small = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 60, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
+    assert lbm.lbm_state_layout(small) == (60 * 64, 60)
 
 
 def test_tma_variant_rejected_where_lines_are_unaligned():
