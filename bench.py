@@ -193,7 +193,7 @@ def _traffic_record(kernel_key: str):
     return rec.get("dram_bytes_per_launch")
 
 
-VARIANTS = [(4, 0), (6, 0), (6, 4), (6, 5), (12, 4), (12, 5)]
+VARIANTS = [(4, 0), (6, 0), (6, 2), (6, 3), (6, 4), (6, 5), (12, 4), (12, 5)]
 LOAD_PATHS = ["registers", "prefetch", "tma", "tma+walls merged", "column march (4 row slots)",
               "column march (5 row slots)"]
 

@@ -147,8 +147,8 @@ lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps
  * dividing M; each warp owns M/warps velocity rows), and the load path of the wall-free
  * segments: 0 registers, 1 registers with all loads issued ahead of the arithmetic,
  * 2 TMA (bulk asynchronous copies into shared memory, FP32 cavities with nx and the cell
- * count multiples of 4 and the planar state layout, i.e. nx < 64; M = 8 or 12), 3 as 2 with
- * the wall segments in the same launch,
+ * count multiples of 4 and the planar state layout; M = 8 or 12), 3 as 2 with the wall
+ * segments in the same launch,
  * 4 and 5 the interior as a column march (persistent blocks march 64-cell strips row by
  * row, each row's lines copied once by TMA into a ring of 4 (path 4) or 5 (path 5) row
  * slots; FP32 cavities with nx a multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12
@@ -194,9 +194,10 @@ lbm_status lbm_set_moments(lbm_sim *sim, const double *moments);
 /* Device pointer of the current state (FP64 or FP32 elements per the precision) and
  * the step counter.  The pointer changes after every step (double buffering).  The value
  * of velocity a at cell (x, y) is at element a * plane_pitch + y * row_pitch + x
- * (lbm_state_layout): planar [a][y][x] (plane_pitch = nx ny, row_pitch = nx) for nx < 64,
- * rows interleaved [y][a][x] (plane_pitch = nx, row_pitch = n nx) for nx >= 64.  Host
- * arrays of the ABI (lbm_init, lbm_get_state, lbm_set_state) are always planar. */
+ * (lbm_state_layout); the library currently keeps every state planar [a][y][x]
+ * (plane_pitch = nx ny, row_pitch = nx), but callers that address the device state should
+ * take the pitches from lbm_state_layout.  Host arrays of the ABI (lbm_init,
+ * lbm_get_state, lbm_set_state) are planar. */
 lbm_status lbm_state_device(lbm_sim *sim, void **ptr, long *step);
 lbm_status lbm_state_layout(const lbm_sim *sim, long *plane_pitch, long *row_pitch);
 

@@ -60,8 +60,8 @@ CASES = [
     ("half", 6, CAVITY, 45, 38, 0.05, 0.0, 0.01),          # D2Q^h_144
     ("half", 4, CAVITY, 2, 2, 0.1, 0.0, 0.01),             # smallest cavity
     ("half", 4, COUETTE, 1, 2, 0.1, 0.01, -0.01),          # smallest channel
-    ("half", 2, COUETTE, 70, 20, 0.2, 0.01, -0.01),        # periodic rows of >= 64 cells (interleaved rows)
-    ("half", 6, CAVITY, 96, 33, 0.05, 0.0, 0.01),          # D2Q^h_144, interleaved rows
+    ("half", 2, COUETTE, 70, 20, 0.2, 0.01, -0.01),        # several periodic columns, longer rows
+    ("half", 6, CAVITY, 96, 33, 0.05, 0.0, 0.01),          # D2Q^h_144, 3 segments per row
 ]
 
 
@@ -178,8 +178,7 @@ def test_sims_sharing_a_stream_from_two_threads():
 @pytest.mark.parametrize("prec,tol", [(lbm.LBM_FP64, 1e-13), (lbm.LBM_FP32_PERTURB, 1e-6)])
 def test_set_moments_matches_oracle_and_round_trips(prec, tol, nx, ny):
     """lbm_set_moments builds the oracle's Hermite state from six moment fields, and
-    lbm_moments gives the fields back (the set D2Q^h_64 is exact to degree 4); planar and
-    row-interleaved state layouts."""
+    lbm_moments gives the fields back (the set D2Q^h_64 is exact to degree 4)."""
     from oracle.mlp import moments_to_h
     u_ref = 0.01
     p = oracle_problem("half", 4, CAVITY, nx, ny, 0.1, 0.0, u_ref)
@@ -313,7 +312,6 @@ def test_full_size_bench_variants(bench_case, variant):
         ptr, step = lbm.lbm_state_device(sim)
         assert step == 1
         pa, py = lbm.lbm_state_layout(sim)
-        assert (pa, py) == (2048, 144 * 2048)          # rows of the planes interleaved
         off = ptr - buf.data_ptr()
         nbytes = 4 * p.n * p.ncells
         torch.cuda.synchronize()
@@ -339,11 +337,9 @@ def _host_state_for(p, seed, prec):
 
 
 @pytest.mark.parametrize("n_half,nx,ny,variants", [
-    # planar state layout (nx < 64): every segment variant incl. the TMA-staged ones
-    (4, 60, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2), (2, 3), (4, 3)]),
-    (6, 60, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2), (3, 3), (6, 3)]),
-    # rows of the planes interleaved (nx >= 64): register-path segment variants
-    (6, 100, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1)]),
+    (4, 68, 40, [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1), (2, 2), (4, 2), (2, 3), (4, 3)]),
+    (6, 64, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (3, 2), (4, 2), (6, 2), (3, 3), (6, 3)]),
+    (6, 100, 36, [(2, 0), (3, 0), (4, 0), (6, 0), (3, 1), (4, 1), (6, 1), (6, 2), (6, 3)]),
 ])
 def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
     """Every kernel variant (warps per segment; register, prefetched or TMA-staged loads) gives
@@ -415,18 +411,6 @@ def test_column_march_rejected_where_strips_do_not_fit():
     sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 128, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP64))
     with pytest.raises(lbm.LBMError):
         lbm.lbm_set_variant(sim, 6, 4)
-
-
-def test_tma_segment_variants_rejected_for_interleaved_rows():
-    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
-    sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 128, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
-    assert lbm.lbm_state_layout(sim) == (128, 144 * 128)
-    for pf in (2, 3):
-        with pytest.raises(lbm.LBMError) as e:
-            lbm.lbm_set_variant(sim, 6, pf)
-        assert e.value.status == lbm.LBM_EUNSUPPORTED
-    small = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 60, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
-    assert lbm.lbm_state_layout(small) == (60 * 64, 60)
 
 
 def test_tma_variant_rejected_where_lines_are_unaligned():
