@@ -41,13 +41,24 @@ struct BatchInst {
     double u_bottom, u_top, inv_u_ref;
 };
 
+// One work item: a 32-cell segment of one instance, with the instance's addressing (first
+// 32 bytes: fetched one item group ahead, so that the state loads of a group do not wait
+// for a chain of dependent metadata loads) and its step coefficients (second 32 bytes).
+struct __align__(16) BatchItem {
+    long off;            // element offset of the instance's state [n][ncells] in each array
+    int ncells, inst, seg, nx, ny, cavity;
+    float cx, cy, omega, b;                              // dt/dx (0: one periodic column), dt/dy, omega, 1 - omega
+    float u_bottom, u_top, drive_bottom, drive_top;      // wall speeds, wall speed / u_ref
+};
+static_assert(sizeof(BatchItem) == 64, "two 32-byte halves");
+
 struct BatchArgs {
     void *buf[2];
     const BatchInst *inst;
     int ninst;
-    const int2 *items;     // (instance, segment) of the wall-free segments
+    const BatchItem *items;       // the wall-free segments of the unconverged instances
     int nitems;
-    const int2 *wall_items;  // (instance, segment) of the segments with a wall cell
+    const BatchItem *wall_items;  // the segments with a wall cell
     int nwall;
     double *acc;           // [ninst][2] residual sums of the current interval
     double *last_r;        // [ninst]
@@ -98,15 +109,45 @@ __device__ bool grid_barrier(const BatchArgs &a)
 template <typename TC>
 __device__ __forceinline__ TC pk(const double *d, const float *f, int i) { return lbmk::pick<TC>(d, f, i); }
 
+// Addressing half of an item (zeros past the end of the list).
+struct ItemAddr {
+    long off;
+    int ncells, inst, seg, nx, ny, cavity;
+    bool valid;
+};
+
+__device__ __forceinline__ ItemAddr load_addr(const BatchItem *items, long nitems, long item)
+{
+    ItemAddr r;
+    r.valid = item < nitems;
+    int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 1, 1, 1);
+    if (r.valid) {
+        const int4 *p = reinterpret_cast<const int4 *>(items + item);
+        q0 = __ldg(p);
+        q1 = __ldg(p + 1);
+    }
+    r.off = (long)(((unsigned long long)(unsigned)q0.y << 32) | (unsigned)q0.x);
+    r.ncells = q0.z;
+    r.inst = q0.w;
+    r.seg = q1.x;
+    r.nx = q1.y;
+    r.ny = q1.z;
+    r.cavity = q1.w;
+    return r;
+}
+
 // One group of SPB segments (one per warp group of the block): transport, moments and
-// relaxation of every listed, unfrozen segment; WALLS selects the code path of segments
-// that contain wall cells (FP64 wall densities across rows and warps, ghosts in the
-// arithmetic type) -- separate from the lean wall-free path so that the latter keeps a
-// small register footprint.  All threads of the block call it together (shared-memory
-// exchanges inside).
+// relaxation of the listed segments; WALLS selects the code path of segments that contain
+// wall cells (FP64 wall densities across rows and warps, ghosts in the arithmetic type) --
+// separate from the lean wall-free path so that the latter keeps a small register
+// footprint.  The item's addressing `A` was fetched one group earlier; its coefficients and
+// the instance's convergence flag are fetched here together with the state.  A segment of
+// an instance that converged since the item list was built is read but not written.  All
+// threads of the block call it together (shared-memory exchanges inside).
 template <typename TS, typename TC, int M, int G, bool WALLS>
-__device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *items, long nitems, long grp,
-                                            long s, const TS *__restrict__ h, TS *__restrict__ hn, bool resid,
+__device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem *items, long grp,
+                                            const ItemAddr &A, long s, const TS *__restrict__ h,
+                                            TS *__restrict__ hn, bool resid,
                                             TC (&s_mom)[3][G][lbmk::Shape<G>::SPB][32],
                                             double (&s_wall)[4][G][lbmk::Shape<G>::SPB][32])
 {
@@ -117,21 +158,24 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *item
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sl = warp / G, g = warp - sl * G;
     const long item = grp * SPB + sl;
-    bool active = item < nitems;
-    int2 it = make_int2(0, 0);
-    if (active) it = items[item];
-    const BatchInst &I = a.inst[it.x];
-    if (active && a.frozen[it.x] <= s) active = false;
-    const long ncells = I.ncells;
-    const int nx = I.nx, ny = I.ny;
-    const bool cav = I.cavity != 0;
-    const long cell0 = (long)it.y * 32 + lane;
+    const bool active = A.valid;
+    float4 k0 = make_float4(0.f, 0.f, 1.f, 0.f), k1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool live = false;
+    if (active) {
+        const float4 *p = reinterpret_cast<const float4 *>(items + item) + 2;
+        k0 = __ldg(p);
+        k1 = __ldg(p + 1);
+        live = a.frozen[A.inst] > s;
+    }
+    const long ncells = A.ncells;
+    const int nx = A.nx, ny = A.ny;
+    const bool cav = A.cavity != 0;
+    const long cell0 = (long)A.seg * 32 + lane;
     const bool in_grid = cell0 < ncells;
     const long c = in_grid ? cell0 : ncells - 1;
     const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
-    const bool valid = active && in_grid;
-    const TS *hi = h + I.off;
-    TS *hno = hn + I.off;
+    const TS *hi = h + A.off;
+    TS *hno = hn + A.off;
     const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);
     const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
     const long c_below = (y > 0) ? c - nx : c;
@@ -184,7 +228,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *item
     TC hs[RPL * M];
     TC rho = 0, jx = 0, jy = 0;
     if (active) {
-        const TC cx = (TC)I.cx, cy = (TC)I.cy;
+        const TC cx = (TC)k0.x, cy = (TC)k0.y;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
@@ -194,8 +238,8 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *item
             const long cy_idx = ypos ? c_below : (yneg ? c_above : c);
             const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
             const TC rho_y = (TC)(ypos ? rb : rt);
-            const TC u_y = (TC)(ypos ? I.u_bottom : I.u_top);
-            const TC drive_y = (TC)((ypos ? I.u_bottom : I.u_top) * I.inv_u_ref);
+            const TC u_y = (TC)(ypos ? k1.x : k1.y);
+            const TC drive_y = (TC)(ypos ? k1.z : k1.w);
             const TC wy = pk<TC>(a.w1, a.w1_f, iy);
             const TC rl_t = (TC)rl, rr_t = (TC)rr;
             TC R = 0, X = 0;
@@ -241,8 +285,9 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *item
     }
 
     TC psd = 0, psn = 0;
+    const bool valid = live && in_grid;
     if (active) {
-        const TC om = (TC)I.omega, b = (TC)I.b;
+        const TC om = (TC)k0.z, b = (TC)k0.w;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
@@ -263,7 +308,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *item
             }
         }
     }
-    if (resid && active) {
+    if (resid && live) {
         double dsd = valid ? (double)psd : 0.0, dsn = valid ? (double)psn : 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -271,8 +316,8 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const int2 *item
             dsn += __shfl_xor_sync(FULL, dsn, off);
         }
         if (lane == 0) {
-            atomicAdd(a.acc + 2 * it.x, dsd);
-            atomicAdd(a.acc + 2 * it.x + 1, dsn);
+            atomicAdd(a.acc + 2 * A.inst, dsd);
+            atomicAdd(a.acc + 2 * A.inst + 1, dsn);
         }
     }
     __syncthreads();   // shared arrays are reused by the next group
@@ -290,13 +335,23 @@ __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const
         const TS *__restrict__ h = reinterpret_cast<const TS *>(a.buf[s & 1]);
         TS *__restrict__ hn = reinterpret_cast<TS *>(a.buf[(s + 1) & 1]);
         const bool resid = ((s + 1) % a.resid_every) == 0;
-        // wall-free segments, then segments with wall cells, both round-robin over the blocks
+        // wall-free segments, then segments with wall cells, both round-robin over the blocks;
+        // the addressing of the next group is fetched before the current group runs
+        const int sl = (int)(threadIdx.x >> 5) / G;
         const long nb = ((long)a.nitems + SPB - 1) / SPB;
-        for (long grp = blockIdx.x; grp < nb; grp += gridDim.x)
-            batch_group<TS, TC, M, G, false>(a, a.items, a.nitems, grp, s, h, hn, resid, s_mom, s_wall);
+        ItemAddr cur = load_addr(a.items, a.nitems, (long)blockIdx.x * SPB + sl);
+        for (long grp = blockIdx.x; grp < nb; grp += gridDim.x) {
+            const ItemAddr nxt = load_addr(a.items, a.nitems, (grp + gridDim.x) * SPB + sl);
+            batch_group<TS, TC, M, G, false>(a, a.items, grp, cur, s, h, hn, resid, s_mom, s_wall);
+            cur = nxt;
+        }
         const long nw = ((long)a.nwall + SPB - 1) / SPB;
-        for (long grp = blockIdx.x; grp < nw; grp += gridDim.x)
-            batch_group<TS, TC, M, G, true>(a, a.wall_items, a.nwall, grp, s, h, hn, resid, s_mom, s_wall);
+        cur = load_addr(a.wall_items, a.nwall, (long)blockIdx.x * SPB + sl);
+        for (long grp = blockIdx.x; grp < nw; grp += gridDim.x) {
+            const ItemAddr nxt = load_addr(a.wall_items, a.nwall, (grp + gridDim.x) * SPB + sl);
+            batch_group<TS, TC, M, G, true>(a, a.wall_items, grp, cur, s, h, hn, resid, s_mom, s_wall);
+            cur = nxt;
+        }
         if (!grid_barrier(a)) return;
         if (resid) {
             if (blockIdx.x == 0) {
@@ -390,7 +445,8 @@ struct lbm_batch {
     // device pointers
     void *buf[2];
     BatchInst *d_inst;
-    int2 *d_items;
+    BatchItem *d_items;
+    std::vector<char> live;     // instances in the current item lists (not yet converged)
     double *d_acc, *d_last_r;
     long *d_frozen;
     unsigned *d_bar;
@@ -460,17 +516,40 @@ bool segment_has_wall(const BatchInst &I, int sg)
 //   0: instance by instance, in the given order;
 //   1: instances by decreasing size;
 //   2: segments interleaved round-robin across instances (largest first).
-void build_items(const lbm_batch *b, int order, std::vector<int2> &bulk, std::vector<int2> &wall)
+BatchItem make_item(const BatchInst &I, int inst, int seg)
+{
+    BatchItem t;
+    std::memset(&t, 0, sizeof t);
+    t.off = I.off;
+    t.ncells = (int)I.ncells;
+    t.inst = inst;
+    t.seg = seg;
+    t.nx = I.nx;
+    t.ny = I.ny;
+    t.cavity = I.cavity;
+    t.cx = (float)I.cx;
+    t.cy = (float)I.cy;
+    t.omega = (float)I.omega;
+    t.b = (float)I.b;
+    t.u_bottom = (float)I.u_bottom;
+    t.u_top = (float)I.u_top;
+    t.drive_bottom = (float)(I.u_bottom * I.inv_u_ref);
+    t.drive_top = (float)(I.u_top * I.inv_u_ref);
+    return t;
+}
+
+void build_items(const lbm_batch *b, int order, std::vector<BatchItem> &bulk, std::vector<BatchItem> &wall)
 {
     const int ni = (int)b->inst.size();
-    std::vector<int> idx(ni);
-    for (int i = 0; i < ni; ++i) idx[i] = i;
+    std::vector<int> idx;
+    for (int i = 0; i < ni; ++i)
+        if (b->live[i]) idx.push_back(i);
     if (order >= 1)
         std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return b->inst[p].ncells > b->inst[q].ncells; });
     bulk.clear();
     wall.clear();
     auto add = [&](int i, int sgm) {
-        (segment_has_wall(b->inst[i], sgm) ? wall : bulk).push_back(make_int2(i, sgm));
+        (segment_has_wall(b->inst[i], sgm) ? wall : bulk).push_back(make_item(b->inst[i], i, sgm));
     };
     if (order <= 1) {
         for (int i : idx) {
@@ -497,11 +576,14 @@ lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     if (maxb < 1) return bfail(LBM_EUNSUPPORTED, "batched kernel does not fit on an SM");
     if (bpsm < 1 || bpsm > maxb) bpsm = maxb;
-    std::vector<int2> items, wall;
+    std::vector<BatchItem> items, wall;
     build_items(b, order, items, wall);
-    e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    e = cudaSuccess;
+    if (!items.empty())
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess && !wall.empty())
-        e = cudaMemcpyAsync(b->d_items + items.size(), wall.data(), sizeof(int2) * wall.size(),
+        e = cudaMemcpyAsync(b->d_items + items.size(), wall.data(), sizeof(BatchItem) * wall.size(),
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("uploading the schedule: ") + cudaGetErrorString(e));
@@ -612,7 +694,7 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
     off = align256(off + vals * es);          // buffer 0
     off = align256(off + vals * es);          // buffer 1
     off = align256(off + sizeof(BatchInst) * count);
-    off = align256(off + sizeof(int2) * segs);
+    off = align256(off + sizeof(BatchItem) * segs);
     off = align256(off + sizeof(double) * 2 * count);
     off = align256(off + sizeof(double) * count);
     off = align256(off + sizeof(long) * count);
@@ -667,6 +749,7 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     }
     b->probs.assign(insts, insts + count);
     b->inst.resize(count);
+    b->live.assign(count, 1);
     long off = 0;
     for (int i = 0; i < count; ++i) {
         inst_coeffs(insts[i], b->nodes, b->inst[i]);
@@ -700,8 +783,8 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     o = align256(o + vals * es);
     b->d_inst = (BatchInst *)(p + o);
     o = align256(o + sizeof(BatchInst) * count);
-    b->d_items = (int2 *)(p + o);
-    o = align256(o + sizeof(int2) * segs);
+    b->d_items = (BatchItem *)(p + o);
+    o = align256(o + sizeof(BatchItem) * segs);
     b->d_acc = (double *)(p + o);
     o = align256(o + sizeof(double) * 2 * count);
     b->d_last_r = (double *)(p + o);
@@ -844,6 +927,10 @@ lbm_status lbm_batch_reset(lbm_batch *b)
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("resetting the batch: ") + cudaGetErrorString(e));
     b->step = 0;
+    if (std::count(b->live.begin(), b->live.end(), 0) > 0) {
+        b->live.assign(n, 1);
+        return apply_schedule(b, b->g, b->blocks_per_sm, b->order);
+    }
     return LBM_OK;
 }
 
@@ -913,9 +1000,19 @@ lbm_status lbm_batch_poll(lbm_batch *b, int *n_active, long *step)
     if (err == 1) return bfail(LBM_ETIMEOUT, "a grid barrier of the batched kernel timed out");
     if (err == 2) return bfail(LBM_ENONFINITE, "non-finite residual in the batch");
     int act = 0;
-    for (long f : frozen) act += f == LONG_MAX;
+    bool changed = false;
+    for (int i = 0; i < n; ++i) {
+        const char l = frozen[i] == LONG_MAX;
+        act += l;
+        changed |= l != b->live[i];
+    }
     if (n_active) *n_active = act;
     if (step) *step = b->step;
+    // drop the items of instances that converged since the lists were built
+    if (changed && act > 0) {
+        for (int i = 0; i < n; ++i) b->live[i] = frozen[i] == LONG_MAX;
+        return apply_schedule(b, b->g, b->blocks_per_sm, b->order);
+    }
     return LBM_OK;
 }
 
