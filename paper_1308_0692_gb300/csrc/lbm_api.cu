@@ -280,10 +280,10 @@ void fill_args(lbm_sim *s, const TableHeader &hdr)
     a.nx = p.nx;
     a.ny = p.ny;
     a.ncells = s->ncells;
-    // planar state layout [a][y][x].  The kernels take the layout as two pitches; a
-    // row-interleaved layout [y][a][x] (pa = nx, py = n nx), which makes a row step of the
-    // interior march touch one contiguous stretch of memory, measured the same march time
-    // at 2048^2 x 144 (0.9325 against 0.9316 ms per step) and 1-4 % slower segment kernels.
+    // planar state layout [a][y][x].  A row-interleaved layout [y][a][x] (pa = nx, py = n nx),
+    // which makes a row step of the interior march touch one contiguous stretch of memory,
+    // measured the same march time at 2048^2 x 144, and addressing the step kernels through
+    // run-time pitches cost 4-8 % of their speed, so they index the planar layout directly.
     (void)v;
     a.pa = s->ncells;
     a.py = p.nx;

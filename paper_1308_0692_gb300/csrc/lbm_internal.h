@@ -42,8 +42,9 @@ struct StepArgs {
     double *partials;     // per-block residual partial sums [2 * gridDim.x]
     int nx, ny;
     long ncells;
-    // state layout: value (velocity a, cell x, y) at a * pa + y * py + x; planar
-    // [a][y][x] (pa = ncells, py = nx) or row-interleaved [y][a][x] (pa = nx, py = n nx)
+    // state layout: value (velocity a, cell x, y) at a * pa + y * py + x.  Every state is
+    // planar [a][y][x] (pa = ncells, py = nx): the step kernels index it as a * ncells + c,
+    // the diagnostics and the host-transfer relayout take the pitches
     long pa, py;
     int cavity;
     int homogeneous;      // drop the wall driving terms (correction sweeps)

@@ -108,13 +108,10 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
 
     const bool wl = WALLS && cav && x == 0, wr = WALLS && cav && x == nx - 1;
     const bool wb = WALLS && y == 0, wt = WALLS && y == ny - 1;
-    // offsets within a velocity plane (state layout a * pa + y * py + x)
-    const long pa = a.pa, py = a.py;
-    const long co = (long)y * py + x;
-    const long c_left = (x > 0) ? co - 1 : (cav ? co : co + nx - 1);        // periodic in Couette
-    const long c_right = (x < nx - 1) ? co + 1 : (cav ? co : co - (nx - 1));
-    const long c_below = (y > 0) ? co - py : co;
-    const long c_above = (y < ny - 1) ? co + py : co;
+    const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);        // periodic in Couette
+    const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
+    const long c_below = (y > 0) ? c - nx : c;
+    const long c_above = (y < ny - 1) ? c + nx : c;
     const TS *__restrict__ h = reinterpret_cast<const TS *>(a.h);
 
     // ---- wall densities rho'_w of the faces this cell touches (Eq. 9) ----
@@ -132,7 +129,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
                 TC rowsum = 0, left = 0, right = 0;
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
-                    const TC v = (TC)ldg(h + (long)(iy * M + ix) * pa + co);
+                    const TC v = (TC)ldg(h + (long)(iy * M + ix) * ncells + c);
                     rowsum += v;
                     if (ix < HALF) left -= pick<TC>(a.xi, a.xi_f, ix) * v;       // towards the left wall
                     if (ix >= M - HALF) right += pick<TC>(a.xi, a.xi_f, ix) * v; // towards the right wall
@@ -174,11 +171,11 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
             const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
-            const long cy = xiy > TC(0) ? c_below : (xiy < TC(0) ? c_above : co);
+            const long cy = xiy > TC(0) ? c_below : (xiy < TC(0) ? c_above : c);
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * pa;
-                hs[r * M + ix] = (TC)ldg(hp + co);
+                const TS *hp = h + (long)(iy * M + ix) * ncells;
+                hs[r * M + ix] = (TC)ldg(hp + c);
                 hyv[r * M + ix] = (TC)ldg(hp + cy);
             }
         }
@@ -190,7 +187,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * pa;
+                const TS *hp = h + (long)(iy * M + ix) * ncells;
                 const TC hc = hs[r * M + ix];
                 TC v = hc;
                 if (ix >= M - HALF || ix < HALF) {
@@ -213,7 +210,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
             const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
             const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
-            const long cy = ypos ? c_below : (yneg ? c_above : co);
+            const long cy = ypos ? c_below : (yneg ? c_above : c);
             const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
             const TC rho_y = (TC)(ypos ? rb : rt);
             const TC u_y = (TC)(ypos ? a.u_bottom : a.u_top);
@@ -223,8 +220,8 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * pa;
-                const TC hc = (TC)ldg(hp + co);
+                const TS *hp = h + (long)(iy * M + ix) * ncells;
+                const TC hc = (TC)ldg(hp + c);
                 const TC xix = pick<TC>(a.xi, a.xi_f, ix);
                 const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
                 TC v = hc;
@@ -280,7 +277,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             const TC jj = wom * jx;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const long off = (long)(iy * M + ix) * pa + co;
+                const long off = (long)(iy * M + ix) * ncells + c;
                 const TC t = q + pick<TC>(a.xi, a.xi_f, ix) * jj;
                 TC v = b * hs[r * M + ix] + pick<TC>(a.w1, a.w1_f, ix) * t;
                 if (SOURCE) v += (TC)ldg(src + off);

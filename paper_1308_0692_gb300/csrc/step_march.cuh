@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
 
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const long pa = a.pa, py = a.py;   // state layout: a * pa + y * py + x
+    const long ncells = a.ncells;
+    const int nx = a.nx;
     const int nstrips = a.march_strips, nchunks = a.march_chunks;
     const int nitems = nstrips * nchunks;
     const int rows = a.ny - 2;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
     }
     // plane offset of this lane's copy (lanes < NV issue one line each per row)
     const int kc = lane < NV ? lane : 0;
-    const float *src_plane = h + (long)((g * RPL + kc / M) * M + (kc % M)) * pa;
+    const float *src_plane = h + (long)((g * RPL + kc / M) * M + (kc % M)) * ncells;
 
     // loader state (uniform within the warp)
     int l_pos = 0, l_item = s_items[0], l_i = 0;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
         fence_proxy_async_smem();   // this slot's earlier generic reads before the async writes
         if (lane < NV)
             bulk_copy(slots + slot * Sh::SLOT + lane * LINE,
-                      src_plane + (long)row * py + 28 + 64L * l_strip, LINE * 4, &bars[slot]);
+                      src_plane + (long)row * nx + 28 + 64L * l_strip, LINE * 4, &bars[slot]);
         ++nl;
         if (++l_i > l_len) {
             l_i = 0;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
 
         // ---- relaxation, store, residual ----
         const int y = c_row0 + c_u;
-        const long cell = (long)y * py + 32 + 64L * c_strip + 2 * lane;
+        const long cell = (long)y * nx + 32 + 64L * c_strip + 2 * lane;
         float2 psd2 = make_float2(0.f, 0.f), psn2 = psd2;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
             const float xiy = a.xi_f[iy];
             const float2 q2 = __fmul2_rn(make_float2(wom, wom), __ffma2_rn(make_float2(xiy, xiy), jy2, rho2));
             const float2 jj2 = __fmul2_rn(make_float2(wom, wom), jx2);
-            float *rowp = hn + (long)(iy * M) * pa + cell;
+            float *rowp = hn + (long)(iy * M) * ncells + cell;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
                 const int k = r * M + ix;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
                     psd2 = __ffma2_rn(d, d, psd2);
                     psn2 = __ffma2_rn(v, v, psn2);
                 }
-                *reinterpret_cast<float2 *>(rowp + (long)ix * pa) = v;
+                *reinterpret_cast<float2 *>(rowp + (long)ix * ncells) = v;
             }
         }
         if (RESID) {
