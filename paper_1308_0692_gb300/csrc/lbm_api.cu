@@ -349,14 +349,18 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur, cudaStrea
 // the sim, never on the caller's: a caller's stream may be shared (stream pools hand the
 // same stream to several users), and any work another thread enqueued on it during the
 // capture would land in this graph.  The graph is launched on the caller's stream.
+cudaError_t make_capture_stream(lbm_sim *s)
+{
+    if (s->cap_stream) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) s->cap_stream = nullptr;
+    return e;
+}
+
 cudaError_t make_graph(lbm_sim *s, int cur)
 {
-    cudaError_t e = cudaSuccess;
-    if (!s->cap_stream) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        s->cap_stream = nullptr;
-        return e;
-    }
+    cudaError_t e = make_capture_stream(s);
+    if (e != cudaSuccess) return e;
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -815,22 +819,60 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
             StepArgs a = s->args;
             a.src = D;
             a.homogeneous = 1;
+            // one interval of K correction steps (+ the residual finalisation) from C[p]
+            auto enqueue_interval = [&](int p, cudaStream_t st) -> cudaError_t {
+                int q = p;
+                for (long j = 1; j <= K; ++j) {
+                    StepArgs b = a;
+                    b.h = C[q];
+                    b.hn = C[q ^ 1];
+                    cudaError_t err = launch_correct_f32(s->vs.m, g, j == K, b, grid, st);
+                    if (err == cudaSuccess && j == K)
+                        err = launch_finalize_residual(s->partials, nparts, s->result, st);
+                    if (err != cudaSuccess) return err;
+                    q ^= 1;
+                }
+                return cudaSuccess;
+            };
+            // the intervals replay CUDA graphs (captured on the private stream, one per
+            // starting buffer); direct launches if a capture fails
+            cudaGraphExec_t cg[2] = {nullptr, nullptr};
+            bool use_graphs = K >= 2 && make_capture_stream(s) == cudaSuccess;
             long k = 0;
             double cbest = INFINITY;
             int cflat = 0;
             while (k < max_steps) {
-                for (long j = 1; j <= K; ++j) {
-                    a.h = C[cc];
-                    a.hn = C[cc ^ 1];
-                    e = launch_correct_f32(s->vs.m, g, j == K, a, grid, s->stream);
-                    if (e == cudaSuccess && j == K) e = launch_finalize_residual(s->partials, nparts, s->result, s->stream);
-                    if (e != cudaSuccess) return cuda_fail(e, "launching the correction march");
-                    cc ^= 1;
+                if (use_graphs && !cg[cc]) {
+                    cudaGraph_t gr = nullptr;
+                    cudaError_t ec = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+                    if (ec == cudaSuccess) {
+                        cudaError_t e2 = enqueue_interval(cc, s->cap_stream);
+                        ec = cudaStreamEndCapture(s->cap_stream, &gr);
+                        if (e2 != cudaSuccess) ec = e2;
+                    }
+                    if (ec == cudaSuccess) ec = cudaGraphInstantiate(&cg[cc], gr, 0);
+                    if (gr) cudaGraphDestroy(gr);
+                    if (ec != cudaSuccess) {
+                        cudaGetLastError();
+                        cg[cc] = nullptr;
+                        use_graphs = false;
+                    }
                 }
+                e = use_graphs ? cudaGraphLaunch(cg[cc], s->stream) : enqueue_interval(cc, s->stream);
+                if (e != cudaSuccess) {
+                    for (auto &x : cg)
+                        if (x) cudaGraphExecDestroy(x);
+                    return cuda_fail(e, "launching the correction march");
+                }
+                cc ^= (int)(K & 1);
                 k += K;
                 double rr[4];
                 st = read_result(s, rr);
-                if (st != LBM_OK) return st;
+                if (st != LBM_OK) {
+                    for (auto &x : cg)
+                        if (x) cudaGraphExecDestroy(x);
+                    return st;
+                }
                 // change per step relative to ||h||, 10x below tol: the correction's own error
                 // is its per-step change times the conditioning of the slow modes (~1e3)
                 const double change = std::sqrt(rr[0]) / hnorm;
@@ -842,6 +884,8 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
                     break;
                 }
             }
+            for (auto &x : cg)
+                if (x) cudaGraphExecDestroy(x);
             out.correction_steps += k;
             e = launch_add_f32((float *)H, (const float *)C[cc], (long)s->nv * s->ncells, s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "applying the correction");
