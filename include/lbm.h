@@ -143,6 +143,21 @@ typedef struct {
 lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps, double refine_tol,
                      lbm_solve_info *info);
 
+/* Time splitting of transport and relaxation.  LBM_SPLIT_LIE (default; the paper's
+ * first-order splitting): transport then relaxation, the stored state is h^n.
+ * LBM_SPLIT_STRANG (symmetric second-order splitting, an extension the paper points to):
+ * relaxation over dt/2, transport over dt, relaxation over dt/2 (explicit Euler half steps).
+ * The library stores g^n = R(dt/2) h^n, whose step is transport then one relaxation with
+ * the factor (1 - omega/2)^2 (two half relaxations share their equilibrium, which
+ * relaxation does not change); lbm_get_state/lbm_state_device/the residual and the face
+ * fluxes refer to g, lbm_moments and lbm_set_moments to the physical h (rho and u are the
+ * same; the non-equilibrium part of P is scaled by 1/(1 - omega/2)).  Call before the
+ * first step (else LBM_EINVAL). */
+#define LBM_SPLIT_LIE 0
+#define LBM_SPLIT_STRANG 1
+lbm_status lbm_set_splitting(lbm_sim *sim, int scheme);
+lbm_status lbm_get_splitting(const lbm_sim *sim, int *scheme);
+
 /* Kernel variant: the number of warps that share one 32-cell segment (1, 2, 3, 4 or 6
  * dividing M; each warp owns M/warps velocity rows), and the load path of the wall-free
  * segments: 0 registers, 1 registers with all loads issued ahead of the arithmetic,

@@ -211,6 +211,34 @@ void orc_step(const orc_problem *p, const orc_coeffs *c, const double *h, double
     }
 }
 
+/*
+ * Relaxation alone over a fraction of the time step: out_a = h_a - frac * omega *
+ * (h_a - w_a (rho' + xi_a . j')) at every cell, with the moments of h (explicit Euler over
+ * frac * dt).  With frac = 1/2 it is the half step of the symmetric (Strang) splitting
+ * relaxation(dt/2) - transport(dt) - relaxation(dt/2), which the caller composes with
+ * orc_step run on coefficients whose omega is halved.
+ */
+void orc_relax(const orc_problem *p, const orc_coeffs *c, const double *h, double *out, double frac)
+{
+    const long ncells = (long)p->nx * p->ny;
+    const int n = p->n;
+    const double om = frac * c->omega;
+    for (long cell = 0; cell < ncells; ++cell) {
+        double rho = 0, jx = 0, jy = 0;
+        for (int a = 0; a < n; ++a) {
+            const double v = h[(long)a * ncells + cell];
+            rho += v;
+            jx += p->xi_x[a] * v;
+            jy += p->xi_y[a] * v;
+        }
+        for (int a = 0; a < n; ++a) {
+            const double v = h[(long)a * ncells + cell];
+            const double heq = p->w[a] * (rho + p->xi_x[a] * jx + p->xi_y[a] * jy);
+            out[(long)a * ncells + cell] = v - om * (v - heq);
+        }
+    }
+}
+
 /* The step's result at selected cells only: out[k * n + a] for cells[k]. */
 void orc_step_cells(const orc_problem *p, const orc_coeffs *c, const double *h,
                     const long *cells, long ncell_list, double *out)

@@ -62,6 +62,8 @@ def _load():
         lib.orc_coeffs_compute.restype = ctypes.c_int
         lib.orc_step.argtypes = [P, C, dp, dp]
         lib.orc_step.restype = None
+        lib.orc_relax.argtypes = [P, C, dp, dp, ctypes.c_double]
+        lib.orc_relax.restype = None
         lib.orc_step_cells.argtypes = [P, C, dp, lp, ctypes.c_long, dp]
         lib.orc_step_cells.restype = None
         lib.orc_residual.argtypes = [dp, dp, ctypes.c_long, dp, dp]
@@ -122,14 +124,37 @@ class Problem:
     def zeros(self) -> np.ndarray:
         return np.zeros((self.n, self.ncells), dtype=np.float64)
 
-    def step(self, h: np.ndarray, nsteps: int = 1) -> np.ndarray:
-        """Return the state after `nsteps` steps (h is not modified)."""
+    def step(self, h: np.ndarray, nsteps: int = 1, omega: float | None = None) -> np.ndarray:
+        """Return the state after `nsteps` steps (h is not modified); `omega` replaces the
+        relaxation factor dt/Kn of the relaxation sub-step if given."""
         lib = _load()
+        c = self._c
+        if omega is not None:
+            c = _Coeffs()
+            ctypes.pointer(c)[0] = self._c
+            c.omega = float(omega)
         cur = np.ascontiguousarray(h, dtype=np.float64).copy()
         nxt = np.empty_like(cur)
         for _ in range(nsteps):
-            lib.orc_step(ctypes.byref(self._p), ctypes.byref(self._c), _dp(cur), _dp(nxt))
+            lib.orc_step(ctypes.byref(self._p), ctypes.byref(c), _dp(cur), _dp(nxt))
             cur, nxt = nxt, cur
+        return cur
+
+    def relax(self, h: np.ndarray, frac: float) -> np.ndarray:
+        """Relaxation alone over frac * dt (explicit Euler, cell-local)."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        out = np.empty_like(h)
+        _load().orc_relax(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h), _dp(out), float(frac))
+        return out
+
+    def step_strang(self, h: np.ndarray, nsteps: int = 1) -> np.ndarray:
+        """`nsteps` steps of the symmetric splitting relaxation(dt/2), transport(dt),
+        relaxation(dt/2), composed literally from the relaxation and transport operators of
+        this oracle (the transport+relaxation step run with omega halved supplies the
+        transport and the second half step)."""
+        cur = np.ascontiguousarray(h, dtype=np.float64).copy()
+        for _ in range(nsteps):
+            cur = self.step(self.relax(cur, 0.5), 1, omega=0.5 * self._c.omega)
         return cur
 
     def step_cells(self, h: np.ndarray, cells) -> np.ndarray:

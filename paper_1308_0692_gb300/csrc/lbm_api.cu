@@ -49,6 +49,7 @@ struct lbm_sim {
     cudaStream_t stream;
     int lanes;            // warps per 32-cell segment of the step kernel
     int prefetch;         // load path of the wall-free cells (lbm_set_variant)
+    int splitting;        // LBM_SPLIT_LIE (stored state h) or LBM_SPLIT_STRANG (stored g = R(dt/2) h)
     int grid;             // blocks of the bulk step kernel
     int march_grid;       // persistent blocks of the column-march kernel (load paths 4, 5)
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
@@ -589,6 +590,7 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->stream = (cudaStream_t)stream;
     s->lanes = default_lanes_per_cell(prob->prec, vs->m);
     s->prefetch = 0;
+    s->splitting = LBM_SPLIT_LIE;
     s->march_grid = 0;
     s->step = 0;
     s->resid_step = -1;
@@ -950,6 +952,33 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
     return set_lanes(s, warps_per_segment);
 }
 
+lbm_status lbm_set_splitting(lbm_sim *s, int scheme)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (scheme != LBM_SPLIT_LIE && scheme != LBM_SPLIT_STRANG)
+        return fail(LBM_EINVAL, "splitting must be LBM_SPLIT_LIE or LBM_SPLIT_STRANG");
+    if (s->step != 0) return fail(LBM_EINVAL, "the splitting is chosen before the first step");
+    s->splitting = scheme;
+    // relaxation factor of the stored state per step: Lie h' = (1 - w) h* + w E(h*);
+    // Strang, stored g = R(dt/2) h, two half relaxations around each transport:
+    // g' = (1 - w/2)^2 g* + (1 - (1 - w/2)^2) E(g*), relaxation conserving rho' and j'
+    const double w = s->omega;
+    const double b = scheme == LBM_SPLIT_STRANG ? (1.0 - 0.5 * w) * (1.0 - 0.5 * w) : 1.0 - w;
+    s->args.b = b;
+    s->args.omega = 1.0 - b;
+    s->args.b_f = (float)b;
+    s->args.omega_f = (float)(1.0 - b);
+    drop_graphs(s);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_splitting(const lbm_sim *s, int *scheme)
+{
+    if (!s || !scheme) return fail(LBM_EINVAL, "NULL argument");
+    *scheme = s->splitting;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_variant(const lbm_sim *s, int *warps_per_segment, int *prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "NULL argument");
@@ -984,11 +1013,31 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
                                    s->prob.nx, s->prob.ny, s->u_ref, s->moments, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the moments kernel");
     double *outs[6] = {rho, ux, uy, pxx, pxy, pyy};
-    for (int k = 0; k < 6; ++k) {
-        if (!outs[k]) continue;
-        e = cudaMemcpyAsync(outs[k], s->moments + (size_t)k * s->ncells, sizeof(double) * s->ncells,
-                            cudaMemcpyDeviceToHost, s->stream);
+    std::vector<double> tmp;
+    const bool strang = s->splitting == LBM_SPLIT_STRANG;
+    if (strang && (pxx || pxy || pyy)) {
+        // physical P from the stored half-relaxed state: non-equilibrium part / (1 - omega/2)
+        tmp.resize((size_t)6 * s->ncells);
+        e = cudaMemcpyAsync(tmp.data(), s->moments, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "copying moments");
+        const long n = s->ncells;
+        const double f = 1.0 / (1.0 - 0.5 * s->omega);
+        for (long c = 0; c < n; ++c) {
+            const double r = tmp[c];
+            tmp[3 * n + c] = r + f * (tmp[3 * n + c] - r);
+            tmp[4 * n + c] = f * tmp[4 * n + c];
+            tmp[5 * n + c] = r + f * (tmp[5 * n + c] - r);
+        }
+        for (int k = 0; k < 6; ++k)
+            if (outs[k]) std::memcpy(outs[k], tmp.data() + (size_t)k * n, sizeof(double) * n);
+    } else {
+        for (int k = 0; k < 6; ++k) {
+            if (!outs[k]) continue;
+            e = cudaMemcpyAsync(outs[k], s->moments + (size_t)k * s->ncells, sizeof(double) * s->ncells,
+                                cudaMemcpyDeviceToHost, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copying moments");
+        }
     }
     if (wall_shear) {
         const int nx = s->prob.nx, ny = s->prob.ny;
@@ -1069,6 +1118,21 @@ lbm_status lbm_set_state(lbm_sim *s, const double *h)
 lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
 {
     if (!s || !moments) return fail(LBM_EINVAL, "NULL argument");
+    std::vector<double> conv;
+    if (s->splitting == LBM_SPLIT_STRANG) {
+        // the stored state is the half-relaxed one: its non-equilibrium part of P is
+        // (1 - omega/2) times the physical one (rho and j are not changed by relaxation)
+        const long n = s->ncells;
+        const double f = 1.0 - 0.5 * s->omega;
+        conv.assign(moments, moments + 6 * n);
+        for (long c = 0; c < n; ++c) {
+            const double rho = conv[c];
+            conv[3 * n + c] = rho + f * (conv[3 * n + c] - rho);
+            conv[4 * n + c] = f * conv[4 * n + c];
+            conv[5 * n + c] = rho + f * (conv[5 * n + c] - rho);
+        }
+        moments = conv.data();
+    }
     cudaError_t e = cudaMemcpyAsync(s->moments, moments, sizeof(double) * 6 * s->ncells, cudaMemcpyHostToDevice,
                                     s->stream);
     if (e == cudaSuccess)

@@ -73,6 +73,8 @@ def _load():
         "lbm_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.c_double,
                            ctypes.POINTER(lbm_solve_info)]),
         "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "lbm_set_splitting": (st, [_vp, ctypes.c_int]),
+        "lbm_get_splitting": (st, [_vp, ctypes.POINTER(ctypes.c_int)]),
         "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
         "lbm_get_state": (st, [_vp, _dp]),
@@ -283,6 +285,19 @@ def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0, refi
 
 def lbm_set_variant(sim: Sim, warps_per_segment: int, prefetch: int = 0):
     _check(_load().lbm_set_variant(sim.handle, int(warps_per_segment), int(prefetch)))
+
+
+LBM_SPLIT_LIE, LBM_SPLIT_STRANG = 0, 1
+
+
+def lbm_set_splitting(sim: Sim, scheme: int):
+    _check(_load().lbm_set_splitting(sim.handle, int(scheme)))
+
+
+def lbm_get_splitting(sim: Sim) -> int:
+    v = ctypes.c_int()
+    _check(_load().lbm_get_splitting(sim.handle, ctypes.byref(v)))
+    return v.value
 
 
 def lbm_get_variant(sim: Sim):

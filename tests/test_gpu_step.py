@@ -197,6 +197,49 @@ def test_set_moments_matches_oracle_and_round_trips(prec, tol, nx, ny):
         assert np.abs(back[k] - mom[k]).max() <= 10 * tol * u_ref, k
 
 
+@pytest.mark.parametrize("prec,tol,variant", [(lbm.LBM_FP64, FP64_TOL, None),
+                                              (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, None),
+                                              (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, (6, 4))])
+def test_strang_splitting_matches_oracle(prec, tol, variant):
+    """Symmetric splitting: the library's stored state g = R(dt/2) h after 6 steps equals the
+    oracle's literal composition relaxation(dt/2), transport(dt), relaxation(dt/2), and the
+    physical moments (lbm_moments) equal the oracle's moments of h."""
+    n_half, nx, ny = (6, 192, 40) if variant else (4, 50, 37)
+    p = oracle_problem("half", n_half, CAVITY, nx, ny, 0.08, 0.0, 0.01)
+    h0 = random_state(p.n, p.ncells, seed=61)
+    g0 = p.relax(h0, 0.5)
+    if prec == lbm.LBM_FP32_PERTURB:
+        g0 = g0.astype(np.float32).astype(np.float64)
+        h0 = None
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.08, 0.0, 0.01, prec=prec, residual_every=3), g0,
+                       stream=torch.cuda.Stream())
+    lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG)
+    assert lbm.lbm_get_splitting(sim) == lbm.LBM_SPLIT_STRANG
+    if variant:
+        lbm.lbm_set_variant(sim, *variant)
+    lbm.lbm_step(sim, 6)
+    # oracle: undo the first half relaxation to get h0 from g0 only in FP64; in FP32 start
+    # from the rounded g0 through the g form (the identity is pinned on the CPU)
+    w = p.coeffs["omega"]
+    if h0 is not None:
+        ref_g = p.relax(p.step_strang(h0, 6), 0.5)
+        ref_h = p.step_strang(h0, 6)
+    else:
+        ref_g = p.step(g0, 6, omega=1.0 - (1.0 - 0.5 * w) ** 2)
+        eq = p.relax(ref_g, 1.0 / w)
+        ref_h = eq + (ref_g - eq) / (1.0 - 0.5 * w)
+    got = lbm.lbm_get_state(sim)
+    assert np.abs(got - ref_g).max() <= tol * np.abs(ref_g).max()
+    m = lbm.lbm_moments(sim, wall_shear=False)
+    mr = p.moments(ref_h)
+    for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy"):
+        scale = np.abs(mr[k] - (1.0 if k in ("rho", "pxx", "pyy") else 0.0)).max()
+        assert np.abs(m[k] - mr[k]).max() <= max(tol, 1e-12) * 10 * scale, k
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_LIE)       # only before the first step
+
+
 def test_zero_steps_and_set_get_roundtrip():
     kind, n, geom, nx, ny, kn, ub, ut = "half", 4, CAVITY, 9, 7, 0.1, 0.0, 0.01
     h0 = random_state(64, 63, seed=9)

@@ -215,3 +215,41 @@ def test_residual_definition():
     assert residual(a, b) == 1.0
     assert residual(b, b) == 0.0
     assert abs(residual(a, a * 0.5) - 0.5) < 1e-16
+
+
+# ---- symmetric (Strang) splitting: relaxation(dt/2), transport(dt), relaxation(dt/2) ----
+
+@pytest.mark.parametrize("geom,nx,ny", [(COUETTE, 1, 12), (CAVITY, 6, 5)])
+def test_strang_without_collisions_is_the_lie_step(geom, nx, ny):
+    p = make_problem("half", 2, geom, nx, ny, math.inf, 0.0 if geom == CAVITY else 0.01, 0.01)
+    h = random_state(p.n, p.ncells, seed=3)
+    np.testing.assert_array_equal(p.step_strang(h, 4), p.step(h, 4))
+
+
+@pytest.mark.parametrize("geom,nx,ny", [(COUETTE, 1, 12), (CAVITY, 6, 5)])
+def test_strang_conserves_mass(geom, nx, ny):
+    p = make_problem("half", 4, geom, nx, ny, 0.05, 0.0 if geom == CAVITY else 0.01, 0.01)
+    h = random_state(p.n, p.ncells, seed=4)
+    assert abs(p.step_strang(h, 5).sum() - h.sum()) <= 1e-12 * np.abs(h).sum()
+
+
+@pytest.mark.parametrize("kn", [0.03, 0.4])
+def test_strang_stored_state_is_a_lie_march_with_squared_half_factor(kn):
+    """The identity the library's Strang mode rests on: with g = R(dt/2) h, one Strang step
+    of h is g' = transport then a relaxation with factor (1 - omega/2)^2 (the two half
+    relaxations share their equilibrium, which relaxation leaves unchanged)."""
+    p = make_problem("half", 4, CAVITY, 7, 6, kn, 0.0, 0.01)
+    w = p.coeffs["omega"]
+    h0 = random_state(p.n, p.ncells, seed=5)
+    literal = p.relax(p.step_strang(h0, 6), 0.5)
+    g_form = p.step(p.relax(h0, 0.5), 6, omega=1.0 - (1.0 - 0.5 * w) ** 2)
+    assert np.abs(literal - g_form).max() <= 1e-13 * np.abs(literal).max()
+
+
+def test_relaxation_half_steps_compose_to_squared_factor_on_non_equilibrium():
+    p = make_problem("half", 4, CAVITY, 5, 4, 0.1, 0.0, 0.01)
+    h = random_state(p.n, p.ncells, seed=6)
+    w = p.coeffs["omega"]
+    twice = p.relax(p.relax(h, 0.5), 0.5)
+    eq = p.relax(h, 1.0 / w)          # relaxing over dt/omega (= Kn) lands on the equilibrium
+    np.testing.assert_allclose(twice - eq, (1 - 0.5 * w) ** 2 * (h - eq), rtol=0, atol=1e-14)
