@@ -239,6 +239,161 @@ void orc_relax(const orc_problem *p, const orc_coeffs *c, const double *h, doubl
     }
 }
 
+/*
+ * Relaxation alone over frac * dt, exact for the linear relaxation equation:
+ * out_a = E_a + exp(-frac * omega) (h_a - E_a), E_a = w_a (rho' + xi_a . j') (rho', j' of h,
+ * which relaxation does not change).  Two of these over dt/2 make one over dt exactly.
+ */
+void orc_relax_exp(const orc_problem *p, const orc_coeffs *c, const double *h, double *out, double frac)
+{
+    const long ncells = (long)p->nx * p->ny;
+    const int n = p->n;
+    const double decay = exp(-frac * c->omega);
+    for (long cell = 0; cell < ncells; ++cell) {
+        double rho = 0, jx = 0, jy = 0;
+        for (int a = 0; a < n; ++a) {
+            const double v = h[(long)a * ncells + cell];
+            rho += v;
+            jx += p->xi_x[a] * v;
+            jy += p->xi_y[a] * v;
+        }
+        for (int a = 0; a < n; ++a) {
+            const double heq = p->w[a] * (rho + p->xi_x[a] * jx + p->xi_y[a] * jy);
+            out[(long)a * ncells + cell] = heq + decay * (h[(long)a * ncells + cell] - heq);
+        }
+    }
+}
+
+/*
+ * Second-order transport alone (an extension of the scheme, not the paper's first-order
+ * upwind): finite-volume update h*_i = h_i - (F_out - F_in) per direction with the
+ * upwind-biased second-order (Beam-Warming) face flux
+ *     F = nu [h_u + (1 - nu)/2 (h_u - h_uu)],
+ * h_u the upwind cell of the face and h_uu the next one upwind.  Where h_uu would lie beyond
+ * a wall the face flux is first order, F = nu h_u; across a wall face the inflow is
+ * nu times the wall-emitted population (Eq. 8).  The wall density of Eq. (9) balances the
+ * outflow through the wall face as this flux computes it, i.e. it is formed from the face
+ * values h_u + (1 - nu)/2 (h_u - h_uu) of the wall-adjacent cell (h_uu: the next cell
+ * inward), so that the walls stay impermeable.  Periodic in x for Couette.
+ */
+
+/* h at (x, y) of velocity a, x periodic in Couette; caller keeps y in range */
+static double hat(const orc_problem *p, const double *h, int a, int x, int y)
+{
+    const int nx = p->nx;
+    if (p->geom == ORC_COUETTE) x = ((x % nx) + nx) % nx;
+    return h[(long)a * nx * p->ny + (long)y * nx + x];
+}
+
+/* face value of the outflow through the wall face of wall-adjacent cell (x, y) for
+ * velocity a moving towards the wall; (dx, dy) = step from the cell into the gas */
+static double wall_face_value(const orc_problem *p, const double *h, int a, int x, int y, int dx, int dy,
+                              double nu)
+{
+    const double hu = hat(p, h, a, x, y);
+    const int xi = x + dx, yi = y + dy;
+    if (xi < 0 || xi >= p->nx || yi < 0 || yi >= p->ny) return hu;   /* one-cell-wide domain */
+    const double huu = hat(p, h, a, xi, yi);
+    return hu + 0.5 * (1.0 - nu) * (hu - huu);
+}
+
+static double wall_density2(const orc_problem *p, const orc_coeffs *c, const double *h, int x, int y, int face)
+{
+    double s = 0;
+    for (int a = 0; a < p->n; ++a) {
+        double xn;
+        int dx = 0, dy = 0;
+        switch (face) {
+        case FACE_BOTTOM: xn = p->xi_y[a]; dy = 1; break;
+        case FACE_TOP:    xn = -p->xi_y[a]; dy = -1; break;
+        case FACE_LEFT:   xn = p->xi_x[a]; dx = 1; break;
+        default:          xn = -p->xi_x[a]; dx = -1; break;
+        }
+        if (xn < 0) {
+            const double nu = -xn * c->dt / ((face == FACE_BOTTOM || face == FACE_TOP) ? c->dy : c->dx);
+            s += -xn * wall_face_value(p, h, a, x, y, dx, dy, nu);
+        }
+    }
+    return s / ((face == FACE_BOTTOM || face == FACE_TOP) ? c->d_y : c->d_x);
+}
+
+/* inflow/outflow fluxes along one axis for velocity a at cell position i (0..len-1) of
+ * that axis, moving towards increasing index with Courant number nu; get(k) returns h at
+ * index k of the axis (k may wrap if periodic); walls: ghost value g_lo at the low end */
+static double flux_difference(double nu, int i, int len, int periodic, double g_lo, double (*get)(const void *, int),
+                              const void *ctx)
+{
+    double fin, fout;
+    const double hi = get(ctx, i);
+    /* face i - 1/2 */
+    if (!periodic && i == 0) {
+        fin = nu * g_lo;
+    } else {
+        const double hu = get(ctx, i - 1);
+        if (!periodic && i == 1) fin = nu * hu;
+        else fin = nu * (hu + 0.5 * (1.0 - nu) * (hu - get(ctx, i - 2)));
+    }
+    /* face i + 1/2 */
+    if (!periodic && i == 0) fout = nu * hi;
+    else fout = nu * (hi + 0.5 * (1.0 - nu) * (hi - get(ctx, i - 1)));
+    (void)len;
+    return fout - fin;
+}
+
+typedef struct {
+    const orc_problem *p;
+    const double *h;
+    int a, x, y, axis, dir;   /* axis 0: x, 1: y; dir +1: transport towards increasing index */
+} axis_ctx;
+
+/* h along the axis in transport order: index k counts from the upwind end */
+static double axis_get(const void *v, int k)
+{
+    const axis_ctx *q = (const axis_ctx *)v;
+    const int len = q->axis == 0 ? q->p->nx : q->p->ny;
+    const int pos = q->dir > 0 ? k : len - 1 - k;
+    return q->axis == 0 ? hat(q->p, q->h, q->a, pos, q->y) : hat(q->p, q->h, q->a, q->x, pos);
+}
+
+void orc_transport2(const orc_problem *p, const orc_coeffs *c, const double *h, double *out)
+{
+    const int n = p->n, nx = p->nx, ny = p->ny;
+    const long ncells = (long)nx * ny;
+    const int cavity = p->geom == ORC_CAVITY;
+    const int xmove = !(p->geom == ORC_COUETTE && nx == 1);
+#pragma omp parallel for schedule(static)
+    for (long cell = 0; cell < ncells; ++cell) {
+        const int x = (int)(cell % nx), y = (int)(cell / nx);
+        double rho_b = 0, rho_t = 0, rho_l = 0, rho_r = 0;
+        if (y == 0) rho_b = wall_density2(p, c, h, x, y, FACE_BOTTOM);
+        if (y == ny - 1) rho_t = wall_density2(p, c, h, x, y, FACE_TOP);
+        if (cavity && x == 0) rho_l = wall_density2(p, c, h, x, y, FACE_LEFT);
+        if (cavity && x == nx - 1) rho_r = wall_density2(p, c, h, x, y, FACE_RIGHT);
+        for (int a = 0; a < n; ++a) {
+            double v = h[(long)a * ncells + cell];
+            axis_ctx q = {p, h, a, x, y, 0, 1};
+            if (xmove && p->xi_x[a] != 0) {
+                const double nu = fabs(p->xi_x[a]) * c->dt / c->dx;
+                q.axis = 0;
+                q.dir = p->xi_x[a] > 0 ? 1 : -1;
+                const int i = q.dir > 0 ? x : nx - 1 - x;
+                const double g = cavity ? (q.dir > 0 ? ghost(p, c, FACE_LEFT, a, rho_l) : ghost(p, c, FACE_RIGHT, a, rho_r))
+                                        : 0.0;
+                v -= flux_difference(nu, i, nx, !cavity, g, axis_get, &q);
+            }
+            if (p->xi_y[a] != 0) {
+                const double nu = fabs(p->xi_y[a]) * c->dt / c->dy;
+                q.axis = 1;
+                q.dir = p->xi_y[a] > 0 ? 1 : -1;
+                const int i = q.dir > 0 ? y : ny - 1 - y;
+                const double g = q.dir > 0 ? ghost(p, c, FACE_BOTTOM, a, rho_b) : ghost(p, c, FACE_TOP, a, rho_t);
+                v -= flux_difference(nu, i, ny, 0, g, axis_get, &q);
+            }
+            out[(long)a * ncells + cell] = v;
+        }
+    }
+}
+
 /* The step's result at selected cells only: out[k * n + a] for cells[k]. */
 void orc_step_cells(const orc_problem *p, const orc_coeffs *c, const double *h,
                     const long *cells, long ncell_list, double *out)
@@ -379,6 +534,70 @@ void orc_face_flux_x(const orc_problem *p, const orc_coeffs *c, const double *h,
                     v = 0.0;
                 s += p->xi_x[a] * p->xi_y[a] * v;
             }
+            out[(long)y * (nx + 1) + i] = c->u_ref * s;
+        }
+    }
+}
+
+/*
+ * Momentum fluxes through the cell faces for the second-order transport: the upwind face
+ * value of orc_transport2 (second-order reconstruction, first order where the next upwind
+ * cell lies beyond a wall, the wall-emitted population on a wall face), weighted by
+ * xi_x xi_y.  At a steady state this flux is the same through every face of a Couette
+ * channel.  Layout as orc_face_flux_y / orc_face_flux_x.
+ */
+static double face_value2(const orc_problem *p, const orc_coeffs *c, const double *h, int a, int axis,
+                          int x, int y, int j, double rho_lo, double rho_hi)
+{
+    /* face j on `axis` between cells j-1 and j of the line through (x, y); j = 0..len */
+    const int len = axis == 0 ? p->nx : p->ny;
+    const double xi = axis == 0 ? p->xi_x[a] : p->xi_y[a];
+    const double nu = fabs(xi) * c->dt / (axis == 0 ? c->dx : c->dy);
+    const int periodic = axis == 0 && p->geom == ORC_COUETTE;
+#define H_AT(k) (axis == 0 ? hat(p, h, a, (k), y) : hat(p, h, a, x, (k)))
+    if (xi > 0) {
+        if (!periodic && j == 0)
+            return ghost(p, c, axis == 0 ? FACE_LEFT : FACE_BOTTOM, a, rho_lo);
+        const double hu = H_AT(j - 1);
+        if (!periodic && j == 1) return hu;
+        return hu + 0.5 * (1.0 - nu) * (hu - H_AT(j - 2));
+    }
+    if (xi < 0) {
+        if (!periodic && j == len)
+            return ghost(p, c, axis == 0 ? FACE_RIGHT : FACE_TOP, a, rho_hi);
+        const double hu = H_AT(j);
+        if (!periodic && j == len - 1) return hu;
+        return hu + 0.5 * (1.0 - nu) * (hu - H_AT(j + 1));
+    }
+#undef H_AT
+    return 0.0;
+}
+
+void orc_face_flux2_y(const orc_problem *p, const orc_coeffs *c, const double *h, double *out)
+{
+    const int nx = p->nx, ny = p->ny;
+    for (int x = 0; x < nx; ++x) {
+        const double rb = wall_density2(p, c, h, x, 0, FACE_BOTTOM);
+        const double rt = wall_density2(p, c, h, x, ny - 1, FACE_TOP);
+        for (int j = 0; j <= ny; ++j) {
+            double s = 0;
+            for (int a = 0; a < p->n; ++a)
+                s += p->xi_x[a] * p->xi_y[a] * face_value2(p, c, h, a, 1, x, 0, j, rb, rt);
+            out[(long)j * nx + x] = c->u_ref * s;
+        }
+    }
+}
+
+void orc_face_flux2_x(const orc_problem *p, const orc_coeffs *c, const double *h, double *out)
+{
+    const int nx = p->nx, ny = p->ny;
+    for (int y = 0; y < ny; ++y) {
+        const double rl = wall_density2(p, c, h, 0, y, FACE_LEFT);
+        const double rr = wall_density2(p, c, h, nx - 1, y, FACE_RIGHT);
+        for (int i = 0; i <= nx; ++i) {
+            double s = 0;
+            for (int a = 0; a < p->n; ++a)
+                s += p->xi_x[a] * p->xi_y[a] * face_value2(p, c, h, a, 0, 0, y, i, rl, rr);
             out[(long)y * (nx + 1) + i] = c->u_ref * s;
         }
     }

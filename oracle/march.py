@@ -64,6 +64,14 @@ def _load():
         lib.orc_step.restype = None
         lib.orc_relax.argtypes = [P, C, dp, dp, ctypes.c_double]
         lib.orc_relax.restype = None
+        lib.orc_relax_exp.argtypes = [P, C, dp, dp, ctypes.c_double]
+        lib.orc_relax_exp.restype = None
+        lib.orc_transport2.argtypes = [P, C, dp, dp]
+        lib.orc_transport2.restype = None
+        lib.orc_face_flux2_y.argtypes = [P, C, dp, dp]
+        lib.orc_face_flux2_y.restype = None
+        lib.orc_face_flux2_x.argtypes = [P, C, dp, dp]
+        lib.orc_face_flux2_x.restype = None
         lib.orc_step_cells.argtypes = [P, C, dp, lp, ctypes.c_long, dp]
         lib.orc_step_cells.restype = None
         lib.orc_residual.argtypes = [dp, dp, ctypes.c_long, dp, dp]
@@ -155,6 +163,43 @@ class Problem:
         cur = np.ascontiguousarray(h, dtype=np.float64).copy()
         for _ in range(nsteps):
             cur = self.step(self.relax(cur, 0.5), 1, omega=0.5 * self._c.omega)
+        return cur
+
+    def relax_exp(self, h: np.ndarray, frac: float) -> np.ndarray:
+        """Relaxation alone over frac * dt, exact exponential decay to the equilibrium."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        out = np.empty_like(h)
+        _load().orc_relax_exp(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h), _dp(out), float(frac))
+        return out
+
+    def transport2(self, h: np.ndarray) -> np.ndarray:
+        """Second-order (Beam-Warming flux) transport alone over dt."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        out = np.empty_like(h)
+        _load().orc_transport2(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h), _dp(out))
+        return out
+
+    def face_flux2_y(self, h: np.ndarray) -> np.ndarray:
+        """x-momentum flux through horizontal faces with the second-order transport's face
+        values, shape (ny+1, nx)."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        out = np.empty((self.ny + 1) * self.nx)
+        _load().orc_face_flux2_y(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h), _dp(out))
+        return out.reshape(self.ny + 1, self.nx)
+
+    def face_flux2_x(self, h: np.ndarray) -> np.ndarray:
+        """Same through vertical faces (cavity), shape (ny, nx+1)."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        out = np.empty(self.ny * (self.nx + 1))
+        _load().orc_face_flux2_x(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h), _dp(out))
+        return out.reshape(self.ny, self.nx + 1)
+
+    def step_second_order(self, h: np.ndarray, nsteps: int = 1) -> np.ndarray:
+        """`nsteps` steps of the second-order variant: exact relaxation over dt/2, second-order
+        transport over dt, exact relaxation over dt/2 (symmetric splitting)."""
+        cur = np.ascontiguousarray(h, dtype=np.float64).copy()
+        for _ in range(nsteps):
+            cur = self.relax_exp(self.transport2(self.relax_exp(cur, 0.5)), 0.5)
         return cur
 
     def step_cells(self, h: np.ndarray, cells) -> np.ndarray:

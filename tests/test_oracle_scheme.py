@@ -253,3 +253,64 @@ def test_relaxation_half_steps_compose_to_squared_factor_on_non_equilibrium():
     twice = p.relax(p.relax(h, 0.5), 0.5)
     eq = p.relax(h, 1.0 / w)          # relaxing over dt/omega (= Kn) lands on the equilibrium
     np.testing.assert_allclose(twice - eq, (1 - 0.5 * w) ** 2 * (h - eq), rtol=0, atol=1e-14)
+
+
+# ---- second-order variant: exact relaxation halves around a second-order transport ----
+
+def _march_second_order(p, tol=1e-13, chunk=100, max_chunks=4000):
+    g = p.zeros()
+    for _ in range(max_chunks):
+        g2 = p.step_second_order(g, chunk)
+        r = np.linalg.norm(g2 - g) / max(np.linalg.norm(g2), 1e-300)
+        g = g2
+        if r < tol:
+            return g
+    raise AssertionError("no steady state")
+
+
+def test_exact_relaxation_composes_and_conserves():
+    p = make_problem("half", 4, CAVITY, 5, 4, 0.07, 0.0, 0.01)
+    h = random_state(p.n, p.ncells, seed=8)
+    np.testing.assert_allclose(p.relax_exp(p.relax_exp(h, 0.3), 0.45), p.relax_exp(h, 0.75), rtol=0, atol=1e-14)
+    r = p.relax_exp(h, 0.5)
+    m0, m1 = p.moments(h), p.moments(r)
+    for k in ("rho", "ux", "uy"):
+        np.testing.assert_allclose(m1[k], m0[k], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("geom,nx,ny", [(COUETTE, 1, 9), (COUETTE, 4, 6), (CAVITY, 7, 6)])
+def test_second_order_transport_conserves_mass(geom, nx, ny):
+    p = make_problem("half", 4, geom, nx, ny, 0.1, 0.0 if geom == CAVITY else 0.01, 0.01)
+    h = random_state(p.n, p.ncells, seed=9)
+    assert abs(p.transport2(h).sum() - h.sum()) <= 1e-12 * np.abs(h).sum()
+    assert abs(p.step_second_order(h, 3).sum() - h.sum()) <= 1e-12 * np.abs(h).sum()
+
+
+@pytest.mark.parametrize("n_half", [2, 4])
+def test_second_order_free_molecular_shear_is_exact(n_half):
+    """Without collisions every population is uniform at steady state; the second-order face
+    values reproduce it, so p_xy = (U_b - U_t)/sqrt(2 pi) on every face (as for first order)."""
+    ub, ut = 0.01, -0.01
+    p = make_problem("half", n_half, COUETTE, 1, 16, math.inf, ub, ut)
+    g = _march_second_order(p, tol=1e-14)
+    f = p.face_flux2_y(g)[:, 0]
+    np.testing.assert_allclose(f, free_molecular_pxy(ub, ut), rtol=1e-11, atol=0)
+
+
+@pytest.mark.slow
+def test_second_order_variant_converges_at_second_order():
+    """Couette, D2Q^h_16, Kn = 0.1: the steady shear of the second-order variant converges to
+    the semi-discrete (space- and time-continuous) value with error ratios near 4 per halving
+    of dy (first-order upwind: near 2, test above), and the momentum flux is the same through
+    every face (the discrete x-momentum balance of the scheme)."""
+    x, w = _one_d("half", 2)
+    exact = couette_semidiscrete(x, w, 0.1, -1.0, 1.0)["pxy"]
+    errs = []
+    for ny in (25, 50, 100):
+        p = make_problem("half", 2, COUETTE, 1, ny, 0.1, -1.0, 1.0)
+        g = _march_second_order(p)
+        f = p.face_flux2_y(p.relax_exp(g, 0.5))[:, 0]      # the transported state
+        assert np.ptp(f) < 1e-11 * abs(exact)
+        errs.append(abs(f.mean() - exact))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.2 < r < 4.6 for r in ratios), (errs, ratios)
