@@ -155,8 +155,23 @@ lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps
  * first step (else LBM_EINVAL). */
 #define LBM_SPLIT_LIE 0
 #define LBM_SPLIT_STRANG 1
+/* as LBM_SPLIT_STRANG with exact half relaxations g -> E + exp(-omega/2) (g - E): the stored
+ * state then advances with the factor exp(-omega), and P converts with exp(omega/2) */
+#define LBM_SPLIT_STRANG_EXACT 2
 lbm_status lbm_set_splitting(lbm_sim *sim, int scheme);
 lbm_status lbm_get_splitting(const lbm_sim *sim, int *scheme);
+
+/* Transport order.  1 (default): the paper's first-order upwind.  2: a second-order
+ * finite-volume transport (an extension of the paper's scheme): per direction the face flux
+ * nu [h_u + (1 - nu)/2 (h_u - h_uu)] (h_u, h_uu the two upwind cells; first order where h_uu
+ * lies beyond a wall; nu times the wall-emitted population across a wall face), wall
+ * densities (Eq. 9) balancing that outflow.  With LBM_SPLIT_STRANG_EXACT the steady state
+ * converges at second order in the grid spacing.  Order 2 runs one register-path kernel per
+ * velocity-set size (lbm_set_variant returns LBM_EUNSUPPORTED), has no FP32 refinement
+ * (lbm_solve with refine_sweeps > 0 returns LBM_EUNSUPPORTED), and lbm_face_flux and the
+ * wall shear of lbm_moments use its face values.  Call before the first step. */
+lbm_status lbm_set_transport(lbm_sim *sim, int order);
+lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
 
 /* Kernel variant: the number of warps that share one 32-cell segment (1, 2, 3, 4 or 6
  * dividing M; each warp owns M/warps velocity rows), and the load path of the wall-free

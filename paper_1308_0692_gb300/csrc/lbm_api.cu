@@ -26,6 +26,7 @@ cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int
 cudaError_t prepare_step_f32_tma(int m, int g);
 cudaError_t launch_step_f32_march(int m, int g, int slots, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 cudaError_t prepare_step_f32_march(int m, int g, int slots, int *grid);
+cudaError_t launch_step_so(int prec, int m, bool resid, const StepArgs &a, int grid, cudaStream_t s);
 bool march_supported(int m, int g, int slots);
 int defect_lanes(int m);
 int correct_lanes(int m);
@@ -49,7 +50,8 @@ struct lbm_sim {
     cudaStream_t stream;
     int lanes;            // warps per 32-cell segment of the step kernel
     int prefetch;         // load path of the wall-free cells (lbm_set_variant)
-    int splitting;        // LBM_SPLIT_LIE (stored state h) or LBM_SPLIT_STRANG (stored g = R(dt/2) h)
+    int splitting;        // LBM_SPLIT_LIE (stored state h) or LBM_SPLIT_STRANG[_EXACT] (stored g = R(dt/2) h)
+    int order;            // transport order: 1 (first-order upwind, the paper's) or 2
     int grid;             // blocks of the bulk step kernel
     int march_grid;       // persistent blocks of the column-march kernel (load paths 4, 5)
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
@@ -242,6 +244,14 @@ void fill_tables(lbm_sim *s, std::vector<double> &t64, std::vector<float> &t32, 
 
 bool planar(const lbm_sim *s) { return s->args.pa == s->ncells; }
 
+// factor of the non-equilibrium part from h to the stored g = R(dt/2) h
+double half_relax_factor(const lbm_sim *s)
+{
+    if (s->splitting == LBM_SPLIT_STRANG_EXACT) return std::exp(-0.5 * s->omega);
+    if (s->splitting == LBM_SPLIT_STRANG) return 1.0 - 0.5 * s->omega;
+    return 1.0;
+}
+
 // FP64 staging area for host transfers of the state: the two spare float arrays (adjacent,
 // 8 bytes per value) of an FP32 simulation, the other state buffer of an FP64 one
 double *staging(lbm_sim *s, const void *state)
@@ -335,7 +345,8 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur, cudaStrea
         const bool resid = idx % s->prob.residual_every == 0;
         a.h = s->buf[cur];
         a.hn = s->buf[cur ^ 1];
-        cudaError_t e = launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, st);
+        cudaError_t e = s->order == 2 ? launch_step_so(s->prob.prec, s->vs.m, resid, a, s->grid, st)
+                                      : launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, st);
         if (e != cudaSuccess) return e;
         if (resid) {
             e = launch_finalize_residual(s->partials, s->nparts_step, s->result, st);
@@ -591,6 +602,7 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->lanes = default_lanes_per_cell(prob->prec, vs->m);
     s->prefetch = 0;
     s->splitting = LBM_SPLIT_LIE;
+    s->order = 1;
     s->march_grid = 0;
     s->step = 0;
     s->resid_step = -1;
@@ -768,6 +780,8 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
     if (!(tol > 0) || max_steps < 0 || refine_sweeps < 0) return fail(LBM_EINVAL, "invalid solve arguments");
     if (refine_sweeps > 0 && s->prob.prec != LBM_FP32_PERTURB)
         return fail(LBM_EINVAL, "refinement sweeps apply to the FP32 precision only");
+    if (refine_sweeps > 0 && s->order == 2)
+        return fail(LBM_EUNSUPPORTED, "the refinement kernels implement the first-order transport only");
     lbm_solve_info out{};
     const long K = s->prob.residual_every;
     // --- the march: whole residual intervals until r < tol ---
@@ -928,6 +942,8 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (prefetch < 0 || prefetch > 5) return fail(LBM_EINVAL, "load path must be 0 to 5");
+    if (s->order == 2)
+        return fail(LBM_EUNSUPPORTED, "the second-order transport has one kernel variant (lbm_set_transport)");
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
         return fail(LBM_EUNSUPPORTED, "no step kernel with %d warps per segment (prefetch %d) for M = %d",
                     warps_per_segment, prefetch, s->vs.m);
@@ -955,20 +971,39 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 lbm_status lbm_set_splitting(lbm_sim *s, int scheme)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (scheme != LBM_SPLIT_LIE && scheme != LBM_SPLIT_STRANG)
-        return fail(LBM_EINVAL, "splitting must be LBM_SPLIT_LIE or LBM_SPLIT_STRANG");
+    if (scheme != LBM_SPLIT_LIE && scheme != LBM_SPLIT_STRANG && scheme != LBM_SPLIT_STRANG_EXACT)
+        return fail(LBM_EINVAL, "splitting must be LBM_SPLIT_LIE, LBM_SPLIT_STRANG or LBM_SPLIT_STRANG_EXACT");
     if (s->step != 0) return fail(LBM_EINVAL, "the splitting is chosen before the first step");
     s->splitting = scheme;
     // relaxation factor of the stored state per step: Lie h' = (1 - w) h* + w E(h*);
     // Strang, stored g = R(dt/2) h, two half relaxations around each transport:
     // g' = (1 - w/2)^2 g* + (1 - (1 - w/2)^2) E(g*), relaxation conserving rho' and j'
+    // exact half relaxations: g' = E + exp(-omega) (g* - E)
     const double w = s->omega;
-    const double b = scheme == LBM_SPLIT_STRANG ? (1.0 - 0.5 * w) * (1.0 - 0.5 * w) : 1.0 - w;
+    const double b = scheme == LBM_SPLIT_STRANG ? (1.0 - 0.5 * w) * (1.0 - 0.5 * w)
+                   : scheme == LBM_SPLIT_STRANG_EXACT ? std::exp(-w) : 1.0 - w;
     s->args.b = b;
     s->args.omega = 1.0 - b;
     s->args.b_f = (float)b;
     s->args.omega_f = (float)(1.0 - b);
     drop_graphs(s);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_transport(lbm_sim *s, int order)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (order != 1 && order != 2) return fail(LBM_EINVAL, "transport order must be 1 or 2");
+    if (s->step != 0) return fail(LBM_EINVAL, "the transport order is chosen before the first step");
+    s->order = order;
+    s->prefetch = 0;
+    return set_lanes(s, default_lanes_per_cell(s->prob.prec, s->vs.m));
+}
+
+lbm_status lbm_get_transport(const lbm_sim *s, int *order)
+{
+    if (!s || !order) return fail(LBM_EINVAL, "NULL argument");
+    *order = s->order;
     return LBM_OK;
 }
 
@@ -1014,7 +1049,7 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
     if (e != cudaSuccess) return cuda_fail(e, "launching the moments kernel");
     double *outs[6] = {rho, ux, uy, pxx, pxy, pyy};
     std::vector<double> tmp;
-    const bool strang = s->splitting == LBM_SPLIT_STRANG;
+    const bool strang = s->splitting != LBM_SPLIT_LIE;
     if (strang && (pxx || pxy || pyy)) {
         // physical P from the stored half-relaxed state: non-equilibrium part / (1 - omega/2)
         tmp.resize((size_t)6 * s->ncells);
@@ -1022,7 +1057,7 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "copying moments");
         const long n = s->ncells;
-        const double f = 1.0 / (1.0 - 0.5 * s->omega);
+        const double f = 1.0 / half_relax_factor(s);
         for (long c = 0; c < n; ++c) {
             const double r = tmp[c];
             tmp[3 * n + c] = r + f * (tmp[3 * n + c] - r);
@@ -1042,8 +1077,11 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
     if (wall_shear) {
         const int nx = s->prob.nx, ny = s->prob.ny;
         const bool cav = s->prob.geom == LBM_CAVITY;
-        e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
-                             cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+        e = s->order == 2
+            ? launch_face_flux2(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
+                                cav, s->u_ref, s->flux_y, s->flux_x, s->stream)
+            : launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
+                               cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
         std::vector<double> fy((size_t)(ny + 1) * nx), fx(cav ? (size_t)ny * (nx + 1) : 0);
         e = cudaMemcpyAsync(fy.data(), s->flux_y, sizeof(double) * fy.size(), cudaMemcpyDeviceToHost, s->stream);
@@ -1076,8 +1114,11 @@ lbm_status lbm_face_flux(lbm_sim *s, double *flux_y, double *flux_x)
     const int nx = s->prob.nx, ny = s->prob.ny;
     const bool cav = s->prob.geom == LBM_CAVITY;
     if (flux_x && !cav) return fail(LBM_EINVAL, "flux_x is defined for the cavity only");
-    cudaError_t e = launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr,
-                                     s->vs.m, nx, ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+    cudaError_t e = s->order == 2
+        ? launch_face_flux2(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, s->vs.m, nx, ny,
+                            cav, s->u_ref, s->flux_y, s->flux_x, s->stream)
+        : launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr,
+                           s->vs.m, nx, ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
     if (flux_y)
         e = cudaMemcpyAsync(flux_y, s->flux_y, sizeof(double) * (size_t)(ny + 1) * nx,
@@ -1119,11 +1160,12 @@ lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
 {
     if (!s || !moments) return fail(LBM_EINVAL, "NULL argument");
     std::vector<double> conv;
-    if (s->splitting == LBM_SPLIT_STRANG) {
+    if (s->splitting != LBM_SPLIT_LIE) {
         // the stored state is the half-relaxed one: its non-equilibrium part of P is
-        // (1 - omega/2) times the physical one (rho and j are not changed by relaxation)
+        // (1 - omega/2) (Euler) or exp(-omega/2) (exact) times the physical one (rho and j
+        // are not changed by relaxation)
         const long n = s->ncells;
-        const double f = 1.0 - 0.5 * s->omega;
+        const double f = half_relax_factor(s);
         conv.assign(moments, moments + 6 * n);
         for (long c = 0; c < n; ++c) {
             const double rho = conv[c];

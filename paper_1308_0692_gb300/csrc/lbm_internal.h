@@ -97,6 +97,10 @@ cudaError_t launch_moments(int prec, const void *h, long pa, long py, const doub
 cudaError_t launch_face_flux(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
                              int m, int nx, int ny, int cavity, double u_ref, double *flux_y,
                              double *flux_x, double *wall_sums, cudaStream_t s);
+// face fluxes with the second-order transport's face values (step_so.cuh)
+cudaError_t launch_face_flux2(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
+                              int m, int nx, int ny, int cavity, double u_ref, double *flux_y, double *flux_x,
+                              cudaStream_t s);
 // copy between the host-order planar FP64 state [a][y][x] and a device state of the given
 // layout and precision (to_layout: planar FP64 -> layout; else layout -> planar FP64)
 cudaError_t launch_relayout(int prec, bool to_layout, double *planar, void *state, int n, int nx, int ny,

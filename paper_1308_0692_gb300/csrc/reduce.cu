@@ -187,6 +187,110 @@ __global__ void face_flux_x_kernel(const T *h, long pa, long py, const double *t
     out[f] = u_ref * s;
 }
 
+// Face values of the second-order transport (step_so.cuh): the upwind reconstruction
+// h_u + (1 - nu)/2 (h_u - h_uu), first order where h_uu lies beyond a wall, the wall ghost
+// on a wall face with the wall density balancing the second-order outflow.
+template <typename T>
+__device__ double wall_rho2(const T *h, long pa, long py, const double *tab, const TableHeader *hdr, int m, int nx,
+                            int ny, int x, int y, int dir)
+{
+    // dir: 0 bottom (inner y + 1), 1 top (y - 1), 2 left (x + 1), 3 right (x - 1)
+    double s = 0.0;
+    const long co = (long)y * py + x;
+    const long ci = dir == 0 ? co + (ny > 1 ? py : 0) : dir == 1 ? co - (ny > 1 ? py : 0)
+                  : dir == 2 ? co + (nx > 1 ? 1 : 0) : co - (nx > 1 ? 1 : 0);
+    for (int iy = 0; iy < m; ++iy) {
+        for (int ix = 0; ix < m; ++ix) {
+            const int al = iy * m + ix;
+            const double xn = (dir == 0) ? hdr->xi1[iy] : (dir == 1) ? -hdr->xi1[iy]
+                            : (dir == 2) ? hdr->xi1[ix] : -hdr->xi1[ix];
+            if (xn < 0.0) {
+                const double nu = tab[(dir < 2 ? TAB_NUY : TAB_NUX) * LBM_MAX_V + al];
+                const double hu = (double)h[(long)al * pa + co], huu = (double)h[(long)al * pa + ci];
+                s -= xn * (hu + 0.5 * (1.0 - nu) * (hu - huu));
+            }
+        }
+    }
+    return s * ((dir < 2) ? hdr->inv_dy_wall : hdr->inv_dx_wall);
+}
+
+template <typename T>
+__global__ void face_flux2_y_kernel(const T *h, long pa, long py, const double *tab, const TableHeader *hdr, int m,
+                                    int nx, int ny, double u_ref, double *out)
+{
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nfaces = (long)(ny + 1) * nx;
+    if (f >= nfaces) return;
+    const int j = (int)(f / nx), x = (int)(f - (long)j * nx);
+    const double rb = (j == 0) ? wall_rho2(h, pa, py, tab, hdr, m, nx, ny, x, 0, 0) : 0.0;
+    const double rt = (j == ny) ? wall_rho2(h, pa, py, tab, hdr, m, nx, ny, x, ny - 1, 1) : 0.0;
+    double s = 0.0;
+    for (int iy = 0; iy < m; ++iy) {
+        const double ey = hdr->xi1[iy];
+        if (ey == 0.0) continue;
+        for (int ix = 0; ix < m; ++ix) {
+            const int al = iy * m + ix;
+            const double nu = tab[TAB_NUY * LBM_MAX_V + al];
+            const T *ha = h + (long)al * pa;
+            double v;
+            if (ey > 0.0) {
+                if (j == 0) v = rb * tab[TAB_GB_LIN * LBM_MAX_V + al] + tab[TAB_GB_C * LBM_MAX_V + al];
+                else {
+                    const double hu = (double)ha[(long)(j - 1) * py + x];
+                    v = (j == 1) ? hu : hu + 0.5 * (1.0 - nu) * (hu - (double)ha[(long)(j - 2) * py + x]);
+                }
+            } else {
+                if (j == ny) v = rt * tab[TAB_GT_LIN * LBM_MAX_V + al] + tab[TAB_GT_C * LBM_MAX_V + al];
+                else {
+                    const double hu = (double)ha[(long)j * py + x];
+                    v = (j == ny - 1) ? hu : hu + 0.5 * (1.0 - nu) * (hu - (double)ha[(long)(j + 1) * py + x]);
+                }
+            }
+            s += hdr->xi1[ix] * ey * v;
+        }
+    }
+    out[f] = u_ref * s;
+}
+
+template <typename T>
+__global__ void face_flux2_x_kernel(const T *h, long pa, long py, const double *tab, const TableHeader *hdr, int m,
+                                    int nx, int ny, double u_ref, double *out)
+{
+    const long f = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nfaces = (long)ny * (nx + 1);
+    if (f >= nfaces) return;
+    const int y = (int)(f / (nx + 1)), i = (int)(f - (long)y * (nx + 1));
+    const double rl = (i == 0) ? wall_rho2(h, pa, py, tab, hdr, m, nx, ny, 0, y, 2) : 0.0;
+    const double rr = (i == nx) ? wall_rho2(h, pa, py, tab, hdr, m, nx, ny, nx - 1, y, 3) : 0.0;
+    double s = 0.0;
+    for (int iy = 0; iy < m; ++iy) {
+        const double ey = hdr->xi1[iy];
+        for (int ix = 0; ix < m; ++ix) {
+            const double ex = hdr->xi1[ix];
+            if (ex == 0.0) continue;
+            const int al = iy * m + ix;
+            const double nu = tab[TAB_NUX * LBM_MAX_V + al];
+            const T *ha = h + (long)al * pa + (long)y * py;
+            double v;
+            if (ex > 0.0) {
+                if (i == 0) v = rl * tab[TAB_W * LBM_MAX_V + al];
+                else {
+                    const double hu = (double)ha[i - 1];
+                    v = (i == 1) ? hu : hu + 0.5 * (1.0 - nu) * (hu - (double)ha[i - 2]);
+                }
+            } else {
+                if (i == nx) v = rr * tab[TAB_W * LBM_MAX_V + al];
+                else {
+                    const double hu = (double)ha[i];
+                    v = (i == nx - 1) ? hu : hu + 0.5 * (1.0 - nu) * (hu - (double)ha[i + 1]);
+                }
+            }
+            s += ex * ey * v;
+        }
+    }
+    out[f] = u_ref * s;
+}
+
 __global__ void convert_kernel(const double *src, float *dst, long count)
 {
     const long stride = (long)gridDim.x * blockDim.x;
@@ -342,6 +446,28 @@ cudaError_t launch_moments(int prec, const void *h, long pa, long py, const doub
         moments_kernel<double><<<grid, 256, 0, s>>>((const double *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
     else
         moments_kernel<float><<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_flux2(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
+                              int m, int nx, int ny, int cavity, double u_ref, double *flux_y, double *flux_x,
+                              cudaStream_t s)
+{
+    const long ny_faces = (long)(ny + 1) * nx, nx_faces = (long)ny * (nx + 1);
+    if (prec == LBM_FP64)
+        face_flux2_y_kernel<double><<<(int)((ny_faces + 255) / 256), 256, 0, s>>>(
+            (const double *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_y);
+    else
+        face_flux2_y_kernel<float><<<(int)((ny_faces + 255) / 256), 256, 0, s>>>(
+            (const float *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !cavity || !flux_x) return e;
+    if (prec == LBM_FP64)
+        face_flux2_x_kernel<double><<<(int)((nx_faces + 255) / 256), 256, 0, s>>>(
+            (const double *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_x);
+    else
+        face_flux2_x_kernel<float><<<(int)((nx_faces + 255) / 256), 256, 0, s>>>(
+            (const float *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_x);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,289 @@
+// Second-order variant of the fused step (an extension of the paper's scheme): the
+// transport is the finite-volume update h*_i = h_i - (F_out - F_in) per direction with the
+// upwind-biased second-order (Beam-Warming) face flux
+//     F = nu [h_u + (1 - nu)/2 (h_u - h_uu)]      (h_u upwind cell, h_uu the next one),
+// first order (F = nu h_u) where h_uu would lie beyond a wall, nu times the wall-emitted
+// population (Eq. 8) across a wall face.  The wall density of Eq. (9) balances the outflow
+// through the wall face as this flux computes it: it is formed from the face values
+// h + (1 - nu)/2 (h - h_inner) of the wall-adjacent cell.  Paired with symmetric splitting
+// and exact relaxation (relaxation factor exp(-omega) on the stored half-relaxed state,
+// set by the host), the steady state converges at second order in the grid spacing.
+//
+// Same decomposition as step_kernel.cuh (32-cell segments, G warps per segment owning M/G
+// velocity rows, moments through shared memory, wall segments in a second kernel), with
+// register loads of the two upwind neighbours per direction.
+#pragma once
+
+#include "step_kernel.cuh"
+
+namespace lbmk {
+
+template <typename TS, typename TC, int M, int G, bool RESID, bool PART>
+__device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
+{
+    constexpr int SPB = Shape<G>::SPB;
+    constexpr int WARPS = Shape<G>::WARPS;
+    constexpr int RPL = M / G;
+    constexpr int HALF = M / 2;   // ix < HALF: xi < 0; ix >= M - HALF: xi > 0
+    static_assert(M % G == 0, "warps per segment must divide M");
+
+    __shared__ TC s_mom[3][G][SPB][32];
+    __shared__ double s_wall[PART ? 4 : 1][G][SPB][32];
+    __shared__ double s_red[2][WARPS];
+
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl = warp / G, g = warp - sl * G;
+    const long ncells = a.ncells;
+    const int nx = a.nx, ny = a.ny;
+    long seg;
+    bool active;
+    if (PART) {
+        const long k = (long)bid * SPB + sl;
+        active = k < a.n_wall_segs;
+        seg = active ? a.wall_segs[k] : 0;
+    } else {
+        seg = (long)bid * SPB + sl;
+        active = seg * 32 < ncells;
+    }
+    const long cell0 = seg * 32 + lane;
+    const bool in_grid = cell0 < ncells;
+    const long c = in_grid ? cell0 : ncells - 1;
+    const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
+    const bool cav = a.cavity != 0;
+    const bool xmove = cav || nx > 1;
+    const bool is_wall = in_grid && (y == 0 || y == ny - 1 || (cav && (x == 0 || x == nx - 1)));
+    const bool work = PART ? active : (active && !__any_sync(FULL, is_wall));
+    const bool valid = work && in_grid;
+    const TS *__restrict__ h = reinterpret_cast<const TS *>(a.h);
+
+    // neighbour cells along x (periodic in Couette, clamped in the cavity) and y (clamped);
+    // a clamped index is only ever read where its value is not used
+    auto xcell = [&](int k) -> long {
+        int xx = x + k;
+        if (!cav) xx = ((xx % nx) + nx) % nx;
+        else xx = xx < 0 ? 0 : (xx > nx - 1 ? nx - 1 : xx);
+        return (long)y * nx + xx;
+    };
+    auto ycell = [&](int k) -> long {
+        int yy = y + k;
+        yy = yy < 0 ? 0 : (yy > ny - 1 ? ny - 1 : yy);
+        return (long)yy * nx + x;
+    };
+    const long cxm1 = xcell(-1), cxm2 = xcell(-2), cxp1 = xcell(1), cxp2 = xcell(2);
+    const long cym1 = ycell(-1), cym2 = ycell(-2), cyp1 = ycell(1), cyp2 = ycell(2);
+
+    // ---- wall densities (Eq. 9) balancing the second-order outflow through each wall face ----
+    double rb = 0.0, rt = 0.0, rl = 0.0, rr = 0.0;
+    if (PART) {
+        double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
+        if (work) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int iy = g * RPL + r;
+                const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
+                const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
+                TC sy = 0, left = 0, right = 0;
+#pragma unroll
+                for (int ix = 0; ix < M; ++ix) {
+                    const TS *hp = h + (long)(iy * M + ix) * ncells;
+                    const TC v = (TC)ldg(hp + c);
+                    // towards the bottom wall (xi_y < 0): inner cell y + 1; top: y - 1
+                    if (xiy != TC(0)) {
+                        const TC inner = (TC)ldg(hp + (xiy < TC(0) ? cyp1 : cym1));
+                        sy += v + TC(0.5) * (TC(1) - nuy) * (v - inner);
+                    }
+                    if (ix < HALF || ix >= M - HALF) {
+                        const TC nux = pick<TC>(a.nux, a.nux_f, ix);
+                        const TC xix = pick<TC>(a.xi, a.xi_f, ix);
+                        const TC inner = (TC)ldg(hp + (ix < HALF ? cxp1 : cxm1));
+                        const TC fv = v + TC(0.5) * (TC(1) - nux) * (v - inner);
+                        if (ix < HALF) left -= xix * fv;       // towards the left wall
+                        else right += xix * fv;                // towards the right wall
+                    }
+                }
+                if (xiy < TC(0)) sb -= (double)xiy * (double)sy;
+                if (xiy > TC(0)) st += (double)xiy * (double)sy;
+                sls += (double)left;
+                srs += (double)right;
+            }
+        }
+        s_wall[0][g][sl][lane] = sb;
+        s_wall[PART ? 1 : 0][g][sl][lane] = st;
+        s_wall[PART ? 2 : 0][g][sl][lane] = sls;
+        s_wall[PART ? 3 : 0][g][sl][lane] = srs;
+        __syncthreads();
+        sb = st = sls = srs = 0.0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            sb += s_wall[0][q][sl][lane];
+            st += s_wall[PART ? 1 : 0][q][sl][lane];
+            sls += s_wall[PART ? 2 : 0][q][sl][lane];
+            srs += s_wall[PART ? 3 : 0][q][sl][lane];
+        }
+        rb = sb * a.inv_dy_wall;
+        rt = st * a.inv_dy_wall;
+        rl = sls * a.inv_dx_wall;
+        rr = srs * a.inv_dx_wall;
+    }
+
+    // ---- second-order transport + moment row sums ----
+    // position along the transport direction, counted from the upwind end: 0 is the
+    // wall-adjacent cell (inflow across the wall face), 1 the next (first-order inflow)
+    const int ixp = x, ixn = nx - 1 - x, iyp = y, iyn = ny - 1 - y;
+    TC hs[RPL * M];
+    TC rho = 0, jx = 0, jy = 0;
+    if (work) {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
+            const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
+            const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
+            const int jpos = ypos ? iyp : iyn;
+            const TC rho_y = (TC)(ypos ? rb : rt);
+            const TC u_y = (TC)(ypos ? a.u_bottom : a.u_top);
+            const TC drive_y = a.homogeneous ? TC(0) : (TC)((ypos ? a.u_bottom : a.u_top) * a.inv_u_ref);
+            const TC wy = pick<TC>(a.w1, a.w1_f, iy);
+            TC R = 0, X = 0;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const TS *hp = h + (long)(iy * M + ix) * ncells;
+                const TC hc = (TC)ldg(hp + c);
+                const TC xix = pick<TC>(a.xi, a.xi_f, ix);
+                const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
+                TC v = hc;
+                if (xmove && (ix >= M - HALF || ix < HALF)) {
+                    const bool xpos = ix >= M - HALF;
+                    const TC nu = pick<TC>(a.nux, a.nux_f, ix);
+                    const TC h1 = (TC)ldg(hp + (xpos ? cxm1 : cxp1));
+                    const int i = xpos ? ixp : ixn;
+                    TC fin, fout;
+                    if (cav && i == 0) {
+                        // ghost of the side wall (at rest): w_a rho'_w
+                        fin = nu * (wxy * (TC)(xpos ? rl : rr));
+                        fout = nu * hc;
+                    } else {
+                        if (cav && i == 1) {
+                            fin = nu * h1;
+                        } else {
+                            const TC h2 = (TC)ldg(hp + (xpos ? cxm2 : cxp2));
+                            fin = nu * (h1 + TC(0.5) * (TC(1) - nu) * (h1 - h2));
+                        }
+                        fout = nu * (hc + TC(0.5) * (TC(1) - nu) * (hc - h1));
+                    }
+                    v -= fout - fin;
+                }
+                if (ypos || yneg) {
+                    const TC h1 = (TC)ldg(hp + (ypos ? cym1 : cyp1));
+                    TC fin, fout;
+                    if (jpos == 0) {
+                        fin = nuy * (wxy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y));
+                        fout = nuy * hc;
+                    } else {
+                        if (jpos == 1) {
+                            fin = nuy * h1;
+                        } else {
+                            const TC h2 = (TC)ldg(hp + (ypos ? cym2 : cyp2));
+                            fin = nuy * (h1 + TC(0.5) * (TC(1) - nuy) * (h1 - h2));
+                        }
+                        fout = nuy * (hc + TC(0.5) * (TC(1) - nuy) * (hc - h1));
+                    }
+                    v -= fout - fin;
+                }
+                hs[r * M + ix] = v;
+                R += v;
+                X += xix * v;
+            }
+            rho += R;
+            jx += X;
+            jy += xiy * R;
+        }
+    }
+    if (G > 1) {
+        s_mom[0][g][sl][lane] = rho;
+        s_mom[1][g][sl][lane] = jx;
+        s_mom[2][g][sl][lane] = jy;
+        __syncthreads();
+        rho = jx = jy = 0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            rho += s_mom[0][q][sl][lane];
+            jx += s_mom[1][q][sl][lane];
+            jy += s_mom[2][q][sl][lane];
+        }
+    }
+
+    // ---- relaxation (factor from the host: exp(-omega) for exact symmetric splitting) ----
+    TC psd = 0, psn = 0;
+    if (work) {
+        const TC b = pick<TC>(&a.b, &a.b_f, 0);
+        const TC om = pick<TC>(&a.omega, &a.omega_f, 0);
+        TS *__restrict__ hn = reinterpret_cast<TS *>(a.hn);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const TC wom = om * pick<TC>(a.w1, a.w1_f, iy);
+            const TC q = wom * (rho + pick<TC>(a.xi, a.xi_f, iy) * jy);
+            const TC jj = wom * jx;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const long off = (long)(iy * M + ix) * ncells + c;
+                const TC t = q + pick<TC>(a.xi, a.xi_f, ix) * jj;
+                const TC v = b * hs[r * M + ix] + pick<TC>(a.w1, a.w1_f, ix) * t;
+                if (RESID) {
+                    const TC d = v - (TC)ldg(h + off);
+                    psd += d * d;
+                    psn += v * v;
+                }
+                if (valid) hn[off] = (TS)v;
+            }
+        }
+    }
+    if (RESID) {
+        double sd = valid ? (double)psd : 0.0, sn = valid ? (double)psn : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sd += __shfl_xor_sync(FULL, sd, off);
+            sn += __shfl_xor_sync(FULL, sn, off);
+        }
+        if (lane == 0) {
+            s_red[0][warp] = sd;
+            s_red[1][warp] = sn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double td = 0.0, tn = 0.0;
+            for (int wi = 0; wi < WARPS; ++wi) {
+                td += s_red[0][wi];
+                tn += s_red[1][wi];
+            }
+            const long slot = (PART ? a.partials_offset : 0) + bid;
+            a.partials[2 * slot] = td;
+            a.partials[2 * slot + 1] = tn;
+        }
+    }
+}
+
+template <typename TS, typename TC, int M, int G, bool RESID, bool PART>
+__global__ void __launch_bounds__(Shape<G>::THREADS) step_so_kernel(const StepArgs a)
+{
+    step_so_body<TS, TC, M, G, RESID, PART>(a, blockIdx.x);
+}
+
+// bulk kernel over `grid` blocks, then the wall kernel over the wall segments
+template <typename TS, typename TC, int M, int G, bool RESID>
+cudaError_t launch_so(const StepArgs &a, int grid, cudaStream_t s)
+{
+    constexpr int T = Shape<G>::THREADS;
+    step_so_kernel<TS, TC, M, G, RESID, false><<<grid, T, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.n_wall_segs == 0) return e;
+    StepArgs b = a;
+    b.partials_offset = grid;
+    const int wgrid = (a.n_wall_segs + Shape<G>::SPB - 1) / Shape<G>::SPB;
+    step_so_kernel<TS, TC, M, G, RESID, true><<<wgrid, T, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -173,11 +173,46 @@ def cavity_table2_study(side: int = 128, kns=(0.05, 0.1, 0.2, 0.4)):
     return out
 
 
+# ---------------------------------------------------------------- transport order (NEXT-3)
+
+def order_study(kns=(0.01, 0.1, 1.0), nys=(50, 100, 200, 400), n_half=4):
+    """Steady Couette shear of the paper's first-order scheme and of the second-order variant
+    (second-order transport, symmetric splitting with exact half relaxations), FP64 on the
+    GPU, against the semi-discrete (space- and time-continuous) solution of the same
+    velocity set; relative errors and their ratios per halving of dy."""
+    from oracle import quadrature as q
+    from oracle.couette_exact import couette_semidiscrete
+    import torch
+    nodes, weights = q.halfrange_1d(n_half)
+    x, w = [float(v) for v in nodes], [float(v) for v in weights]
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    stream = torch.cuda.Stream()
+    out = {"n_half": n_half, "runs": []}
+    for kn in kns:
+        exact = couette_semidiscrete(x, w, kn, -0.01, 0.01)["pxy"]
+        for order in (1, 2):
+            prev = None
+            for ny in nys:
+                sim = lbm.lbm_init(vs, lbm.make_problem(lbm.LBM_COUETTE, 1, ny, kn, -0.01, 0.01, prec=lbm.LBM_FP64,
+                                                        residual_every=100), stream=stream)
+                if order == 2:
+                    lbm.lbm_set_transport(sim, 2)
+                    lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG_EXACT)
+                info = lbm.lbm_solve(sim, 1e-13, 20_000_000, 0)
+                fy, _ = lbm.lbm_face_flux(sim)
+                err = float((fy[:, 0].mean() - exact) / exact)
+                out["runs"].append({"kn": kn, "order": order, "ny": ny, "pxy": float(fy[:, 0].mean()), "exact": exact,
+                                    "rel_err": err, "ratio": (prev / err) if prev else None, "steps": info["steps"]})
+                prev = err
+                sim.close()
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2"])
+    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order"])
     ap.add_argument("--out", required=True)
     ap.add_argument("--side", type=int, default=128)
     args = ap.parse_args(argv)
@@ -185,11 +220,16 @@ def main(argv=None):
         r = kn_sweep()
     elif args.study == "couette_kn1":
         r = couette_kn1_study()
+    elif args.study == "order":
+        r = order_study()
     else:
         r = cavity_table2_study(side=args.side)
     with open(args.out, "w") as f:
         json.dump(r, f, indent=1)
-    short = r.get("summary") or r.get("vs_reference") or {k: v.get("ratios_to_printed") for k, v in r["runs"].items()}
+    if args.study == "order":
+        short = [(x["kn"], x["order"], x["ny"], round(x["rel_err"], 6), x["ratio"] and round(x["ratio"], 2)) for x in r["runs"]]
+    else:
+        short = r.get("summary") or r.get("vs_reference") or {k: v.get("ratios_to_printed") for k, v in r["runs"].items()}
     print(json.dumps(short), flush=True)
     return 0
 

@@ -75,6 +75,8 @@ def _load():
         "lbm_get_variant": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_set_splitting": (st, [_vp, ctypes.c_int]),
         "lbm_get_splitting": (st, [_vp, ctypes.POINTER(ctypes.c_int)]),
+        "lbm_set_transport": (st, [_vp, ctypes.c_int]),
+        "lbm_get_transport": (st, [_vp, ctypes.POINTER(ctypes.c_int)]),
         "lbm_moments": (st, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
         "lbm_get_state": (st, [_vp, _dp]),
@@ -287,7 +289,17 @@ def lbm_set_variant(sim: Sim, warps_per_segment: int, prefetch: int = 0):
     _check(_load().lbm_set_variant(sim.handle, int(warps_per_segment), int(prefetch)))
 
 
-LBM_SPLIT_LIE, LBM_SPLIT_STRANG = 0, 1
+LBM_SPLIT_LIE, LBM_SPLIT_STRANG, LBM_SPLIT_STRANG_EXACT = 0, 1, 2
+
+
+def lbm_set_transport(sim: Sim, order: int):
+    _check(_load().lbm_set_transport(sim.handle, int(order)))
+
+
+def lbm_get_transport(sim: Sim) -> int:
+    v = ctypes.c_int()
+    _check(_load().lbm_get_transport(sim.handle, ctypes.byref(v)))
+    return v.value
 
 
 def lbm_set_splitting(sim: Sim, scheme: int):
