@@ -91,3 +91,35 @@ def test_warm_start_state_is_the_hermite_expansion():
     xi_x, xi_y, w = (np.array(v) for v in q.velocity_set_2d("half", 4))
     ref = omlp.moments_to_h(mom, xi_x, xi_y, w, uw)
     assert np.abs(h - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_trained_network_shortens_the_march_at_equal_accuracy():
+    """What the learned part gains: with the committed trained network, held-out cavities
+    (128^2, D2Q^h_64, pairs from a seed the training never saw) reach the FP32 march target in
+    fewer steps than from the cold start f = w, and the refined fields agree with the cold
+    start's and with an FP64 solve within 1e-5 of u_w."""
+    import os
+
+    from paper_1308_0692_gb300 import warmstart
+    path = os.path.join(os.path.dirname(warmstart.__file__), "data", "warmstart_mlp.npy")
+    mlp = warmstart.load_mlp(path)
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    pairs = warmstart.draw_pairs(4, seed=99173)
+    cold_steps, warm_steps = [], []
+    for kn, uw in pairs:
+        runs = {}
+        for name, net in (("cold", None), ("warm", mlp)):
+            sim, info, _ = warmstart.solve_cavity(vs, kn, uw, prec=lbm.LBM_FP32_PERTURB, tol=1e-8, refine=3,
+                                                  mlp=net, refine_tol=1e-8)
+            runs[name] = (info, lbm.lbm_moments(sim, wall_shear=False))
+            sim.close()
+        s64, _, _ = warmstart.solve_cavity(vs, kn, uw, prec=lbm.LBM_FP64, tol=1e-10, refine=0)
+        m64 = lbm.lbm_moments(s64, wall_shear=False)
+        s64.close()
+        for name, (info, m) in runs.items():
+            err = max(np.abs(m["ux"] - m64["ux"]).max(), np.abs(m["uy"] - m64["uy"]).max()) / uw
+            assert err < 1e-5, (kn, uw, name, err)
+        cold_steps.append(runs["cold"][0]["steps"])
+        warm_steps.append(runs["warm"][0]["steps"])
+    assert sum(warm_steps) < 0.8 * sum(cold_steps), (cold_steps, warm_steps)
+    mlp.close()
