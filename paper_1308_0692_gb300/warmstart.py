@@ -10,8 +10,8 @@ memory and gathers minibatches):
 2. ``train``: Adam on minibatches of (cell features, targets) with the library's BF16
    tensor-core MLP kernels.
 3. ``lbm_warm_start`` (C-ABI) builds the initial state of a new cavity from the
-   network's prediction; the cold-start march remains the fallback and the judge of
-   convergence.
+   network's prediction; the march from there (the same march as from a cold start)
+   decides convergence, and the cold start remains the fallback.
 """
 from __future__ import annotations
 
