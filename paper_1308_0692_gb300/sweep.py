@@ -13,6 +13,11 @@ The refinement therefore targets 1e-10 (the FP32 batch march still stops at 1e-6
 FP64 references are marched to 1e-11.
 
     python -m paper_1308_0692_gb300.sweep [--count 512] [--out report.json]
+
+Several GPUs (one process per GPU, torchrun): the instances are dealt round-robin to the
+ranks (shard), each rank runs its share as its own batch on its own GPU with no
+communication, and rank 0 gathers the per-instance records (merge_reports): the sweep's
+wall time is the slowest rank's.
 """
 from __future__ import annotations
 
@@ -40,9 +45,41 @@ def _log(*a):
     print(*a, flush=True)
 
 
-def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=32, log=_log):
+def shard(count: int, rank: int, world: int) -> list[int]:
+    """Instance indices of one rank: round-robin, so every rank gets the same mix of sizes."""
+    return list(range(rank, count, world))
+
+
+def merge_reports(reports: list[dict]) -> dict:
+    """One report from the ranks' reports (instances disjoint): times are the slowest
+    rank's, counts add up, per-instance records are merged in index order."""
+    per = sorted((r for rep in reports for r in rep["per_instance"]), key=lambda r: r["index"])
+    checked = [r["err"] for r in per if "err" in r]
+    steps = np.array([r["steps"] for r in per])
+    out = {k: reports[0][k] for k in ("seed",)}
+    out.update({
+        "count": len(per), "ranks": len(reports), "unknowns": int(sum(rep["unknowns"] for rep in reports)),
+        "schedule": [rep["schedule"] for rep in reports],
+        "tune_seconds": max(rep["tune_seconds"] for rep in reports),
+        "batch_seconds": max(rep["batch_seconds"] for rep in reports),
+        "refine_seconds": max(rep["refine_seconds"] for rep in reports),
+        "reference_seconds": max(rep["reference_seconds"] for rep in reports),
+        "steps_min": int(steps.min()), "steps_median": float(np.median(steps)), "steps_max": int(steps.max()),
+        "instances_checked": len(checked),
+        "max_velocity_error": max((e["u"] for e in checked), default=None),
+        "max_wall_shear_error": max((e["wall_shear"] for e in checked), default=None),
+        "per_instance": per,
+    })
+    return out
+
+
+def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=32, log=_log, indices=None):
+    """Sweep over the instances `indices` of the seed-drawn table of `count` (all by default)."""
     import torch
-    table = batch_table(count, seed)
+    full = batch_table(count, seed)
+    indices = list(range(count)) if indices is None else list(indices)
+    table = [full[i] for i in indices]
+    count_local = len(table)
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
     probs = [_problem(t, lbm.LBM_FP32_PERTURB) for t in table]
     unknowns = sum(p.nx * p.ny for p in probs) * 64
@@ -50,7 +87,7 @@ def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=
     t0 = time.perf_counter()
     best = lbm.lbm_batch_tune(b, 10)
     t_tune = time.perf_counter() - t0
-    log(f"sweep: {count} instances, {unknowns / 1e6:.1f} M unknowns, schedule {best} (tuned in {t_tune:.1f} s)")
+    log(f"sweep: {count_local} instances, {unknowns / 1e6:.1f} M unknowns, schedule {best} (tuned in {t_tune:.1f} s)")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tol32 = max(tol, 1e-6)
@@ -62,8 +99,8 @@ def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=
         if n_active == 0 or steps_done >= 2_000_000:
             break
     t_batch = time.perf_counter() - t0
-    steps = np.array([lbm.lbm_batch_status(b, i)["steps"] for i in range(count)])
-    log(f"sweep: batch march done, {int((steps < steps_done).sum())} of {count} instances converged")
+    steps = np.array([lbm.lbm_batch_status(b, i)["steps"] for i in range(count_local)])
+    log(f"sweep: batch march done, {int((steps < steps_done).sum())} of {count_local} instances converged")
     cells = np.array([p.nx * p.ny for p in probs])
     log(f"sweep: FP32 batch march to {tol32:g} in {t_batch:.1f} s ({steps_done} steps launched, "
         f"{(steps * cells * 64).sum() / t_batch / 1e9:.1f} G updates/s on active instances)")
@@ -112,15 +149,16 @@ def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=
     for s in sims:
         s.close()
     report = {
-        "count": count, "seed": seed, "unknowns": int(unknowns), "schedule": best, "tune_seconds": t_tune,
+        "count": count_local, "seed": seed, "unknowns": int(unknowns), "schedule": best, "tune_seconds": t_tune,
         "batch_seconds": t_batch, "refine_seconds": t_refine, "reference_seconds": t_ref,
         "steps_min": int(steps.min()), "steps_median": float(np.median(steps)), "steps_max": int(steps.max()),
         "instances_checked": len(errs),
         "max_velocity_error": max(e["u"] for e in errs.values()),
         "max_wall_shear_error": max(e["wall_shear"] for e in errs.values()),
-        "per_instance": [{**table[i], "steps": int(steps[i]), "correction_steps": int(ref_info[i][0]),
-                          "defect": float(ref_info[i][1]), **({"err": errs[i]} if i in errs else {})}
-                         for i in range(count)],
+        "per_instance": [{"index": indices[i], **table[i], "steps": int(steps[i]),
+                          "correction_steps": int(ref_info[i][0]), "defect": float(ref_info[i][1]),
+                          **({"err": errs[i]} if i in errs else {})}
+                         for i in range(count_local)],
     }
     return report
 
@@ -132,12 +170,29 @@ def main(argv=None):
     ap.add_argument("--ref-max-cells", type=int, default=128 * 128)
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
-    rep = run(args.count, tol=args.tol, ref_max_cells=args.ref_max_cells)
-    short = {k: v for k, v in rep.items() if k != "per_instance"}
-    print(json.dumps(short), flush=True)
-    if args.out:
-        with open(args.out, "w") as f:
-            json.dump(rep, f, indent=1)
+    import os
+    world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend="gloo")   # only the final gather of Python records
+    rep = run(args.count, tol=args.tol, ref_max_cells=args.ref_max_cells, indices=shard(args.count, rank, world),
+              log=_log if rank == 0 else (lambda *a: None))
+    if dist is not None:
+        reps = [None] * world
+        dist.all_gather_object(reps, rep)
+        rep = merge_reports(reps)
+        dist.destroy_process_group()
+    else:
+        rep = merge_reports([rep])
+    if rank == 0:
+        short = {k: v for k, v in rep.items() if k != "per_instance"}
+        print(json.dumps(short), flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(rep, f, indent=1)
     return 0
 
 
