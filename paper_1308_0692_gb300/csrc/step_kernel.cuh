@@ -121,7 +121,36 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
     double rb = 0.0, rt = 0.0, rl = 0.0, rr = 0.0;
     if (WALLS) {
         double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
-        if (work) {
+        // Segments in the bottom or top row need the y-wall sums of every lane.  The other
+        // wall segments (a cavity's side walls) hold one or two wall cells: their sums are
+        // formed cooperatively for those cells only, the velocities dealt to the lanes (products in the
+        // arithmetic type, the sum in FP64).
+        const bool rows_wall = __any_sync(FULL, in_grid && (y == 0 || y == ny - 1));
+        if (work && !rows_wall && cav) {
+            constexpr int NSIDE = RPL * HALF;          // velocities of this warp towards one side wall
+            for (int side = 0; side < 2; ++side) {
+                unsigned m = __ballot_sync(FULL, in_grid && (side == 0 ? x == 0 : x == nx - 1));
+                while (m) {
+                    const int L = __ffs(m) - 1;
+                    m &= m - 1;
+                    const long cL = __shfl_sync(FULL, c, L);
+                    double part = 0.0;
+                    for (int k = lane; k < NSIDE; k += 32) {
+                        const int r = k / HALF, q = k - r * HALF;
+                        const int iy = g * RPL + r, ix = side == 0 ? q : M - HALF + q;
+                        const TC v = (TC)ldg(h + (long)(iy * M + ix) * ncells + cL);
+                        const TC xv = pick<TC>(a.xi, a.xi_f, ix) * v;
+                        part += side == 0 ? -(double)xv : (double)xv;
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
+                    if (lane == L) {
+                        if (side == 0) sls = part;
+                        else srs = part;
+                    }
+                }
+            }
+        } else if (work) {
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
                 const int iy = g * RPL + r;
