@@ -131,3 +131,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "liblbm.so"))
     with pytest.raises(RuntimeError, match="not built"):
         lbm.lbm_make_velocity_set(0, 4)
+
+
+def test_grid_beyond_the_index_range_is_rejected():
+    """Cell indices are 32-bit in the segment lists: grids of more than 2^31 cells are refused."""
+    prob = lbm.make_problem(lbm.LBM_CAVITY, 65536, 32769, 0.1, 0.0, 0.01)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_sim_bytes(_vs(), prob)
+    assert e.value.status == lbm.LBM_EINVAL
+    ok = lbm.make_problem(lbm.LBM_CAVITY, 65536, 32768, 0.1, 0.0, 0.01)
+    assert lbm.lbm_sim_bytes(_vs(), ok) > 8 * 64 * 65536 * 32768
