@@ -136,8 +136,9 @@ typedef struct {
  * takes the defect D = M(h) - h of the stored FP32 state under one FP64 step, marches the
  * correction delta <- L(delta) + D of the homogeneous problem (walls without driving) in
  * FP32 until its per-step change is below refine_tol * ||h|| (refine_tol <= 0: 0.1 * tol),
- * and adds h += delta; sweeps stop early once the
- * defect stops halving (FP32 rounding floor).  This removes the bias of the FP32 fixed
+ * and adds h += delta; sweeps stop once the FP64 defect ||D|| / ||M(h)|| -- the FP64
+ * march's residual evaluated on the refined state -- is below tol, or when it stops halving
+ * (FP32 rounding floor).  This removes the bias of the FP32 fixed
  * point (the FP32 operator's rounding amplified by the conditioning of the slow modes),
  * which plain FP32 storage cannot.  refine_sweeps must be 0 for FP64 simulations. */
 lbm_status lbm_solve(lbm_sim *sim, double tol, long max_steps, int refine_sweeps, double refine_tol,
@@ -308,6 +309,27 @@ lbm_status lbm_batch_warm_start(lbm_batch *b, int i, lbm_mlp *mlp, double kn, do
 /* Moments of instance i (as lbm_moments) into device FP64 [6][ny][nx]: rho, ux, uy, pxx,
  * pxy, pyy.  Stream-ordered. */
 lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev);
+/* Mixed-precision refinement of every instance, all instances at once (the batched form of
+ * lbm_solve's refinement sweeps; not in the paper).  Each sweep evaluates the defect
+ * D = M(h) - h of the stored FP32 state under one step in FP64 arithmetic (Eqs. 1, 5-9 of
+ * the linearised scheme), marches the corrections delta <- L(delta) + D of the homogeneous
+ * problems (walls without driving) in FP32 in one persistent launch per 5 * residual_every
+ * steps until each instance's per-step change is below refine_tol * ||M(h)|| (refine_tol
+ * <= 0: 0.1 * tol; an instance whose change has not improved by 1 % over 20 residual checks,
+ * or that reached max_steps correction steps, stops there), and adds h += delta.  An
+ * instance takes sweeps until its FP64 defect ||D|| / ||M(h)|| is below tol, the defect
+ * stops halving (the FP32 rounding floor), or max_sweeps.  Refines the state each instance
+ * stands at (its convergence step, or the current step) in place; step counts and
+ * convergence flags are unchanged.  info (may be NULL) receives one record per instance.
+ * The first call allocates a workspace of four state copies (freed with the batch).
+ * Synchronises the batch's stream. */
+typedef struct {
+    long correction_steps;   /* correction steps over all sweeps */
+    int sweeps;              /* sweeps taken (0: the defect was already below tol) */
+    double defect;           /* final FP64 defect ||M(h) - h|| / ||M(h)|| */
+} lbm_batch_refine_info;
+lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double refine_tol, long max_steps,
+                            lbm_batch_refine_info *info);
 
 /* ---- Learned warm start (not in the paper) ----
  * A coordinate MLP 4 -> 256 -> 256 -> 256 -> 6 with exact-erf GELU maps the features

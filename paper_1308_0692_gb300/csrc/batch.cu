@@ -11,6 +11,13 @@
 // instances below the tolerance are frozen: from then on their items are skipped and
 // their state stays in the buffer of the step at which they converged.
 //
+// The same kernel, in two more modes, refines converged FP32 instances all at once
+// (lbm_batch_refine): BATCH_DEFECT evaluates one step in FP64 arithmetic on the FP32 state
+// and stores the change M(h) - h; BATCH_CORRECT marches the correction delta <- L(delta) +
+// D of the homogeneous problem (wall driving removed, the defect added after relaxation),
+// freezing each instance once its per-step change is below the tolerance relative to the
+// norm of its state.
+//
 // Every wait in the grid barrier is bounded (clock64 against a limit); a barrier that
 // gives up sets an error word that all blocks check after each barrier, so the kernel
 // returns and the host reports LBM_ETIMEOUT.
@@ -30,6 +37,8 @@
 lbm_status lbm_norms_fail(lbm_status s, const char *msg);
 
 namespace {
+
+enum { BATCH_MARCH = 0, BATCH_CORRECT = 1, BATCH_DEFECT = 2 };
 
 struct BatchInst {
     long off;           // element offset of the instance's state [n][ncells] in each array
@@ -70,6 +79,8 @@ struct BatchArgs {
     int nsteps;
     int resid_every;
     double tol;
+    const float *src;      // BATCH_CORRECT: the defect, added after relaxation
+    const double *ref_n2;  // BATCH_CORRECT: squared norm of each instance's state (residual scale)
     long long timeout_cycles;
     double xi[LBM_MAX_M], w1[LBM_MAX_M];
     float xi_f[LBM_MAX_M], w1_f[LBM_MAX_M];
@@ -144,7 +155,7 @@ __device__ __forceinline__ ItemAddr load_addr(const BatchItem *items, long nitem
 // the instance's convergence flag are fetched here together with the state.  A segment of
 // an instance that converged since the item list was built is read but not written.  All
 // threads of the block call it together (shared-memory exchanges inside).
-template <typename TS, typename TC, int M, int G, bool WALLS>
+template <typename TS, typename TC, int M, int G, bool WALLS, int MODE>
 __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem *items, long grp,
                                             const ItemAddr &A, long s, const TS *__restrict__ h,
                                             TS *__restrict__ hn, bool resid,
@@ -159,12 +170,34 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
     const int sl = warp / G, g = warp - sl * G;
     const long item = grp * SPB + sl;
     const bool active = A.valid;
-    float4 k0 = make_float4(0.f, 0.f, 1.f, 0.f), k1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // step coefficients: dt/dx, dt/dy, omega, 1 - omega, wall speeds, wall speeds / u_ref --
+    // FP32 from the item, except in the FP64 defect pass, which takes the instance's FP64 values
+    TC k_cx = 0, k_cy = 0, k_om = 1, k_b = 0, k_ub = 0, k_ut = 0, k_db = 0, k_dt = 0;
     bool live = false;
     if (active) {
-        const float4 *p = reinterpret_cast<const float4 *>(items + item) + 2;
-        k0 = __ldg(p);
-        k1 = __ldg(p + 1);
+        if (MODE == BATCH_DEFECT) {
+            const BatchInst &I = a.inst[A.inst];
+            k_cx = (TC)I.cx;
+            k_cy = (TC)I.cy;
+            k_om = (TC)I.omega;
+            k_b = (TC)I.b;
+            k_ub = (TC)I.u_bottom;
+            k_ut = (TC)I.u_top;
+            k_db = (TC)(I.u_bottom * I.inv_u_ref);
+            k_dt = (TC)(I.u_top * I.inv_u_ref);
+        } else {
+            const float4 *p = reinterpret_cast<const float4 *>(items + item) + 2;
+            const float4 k0 = __ldg(p), k1 = __ldg(p + 1);
+            k_cx = (TC)k0.x;
+            k_cy = (TC)k0.y;
+            k_om = (TC)k0.z;
+            k_b = (TC)k0.w;
+            k_ub = (TC)k1.x;
+            k_ut = (TC)k1.y;
+            // homogeneous walls in the correction march: no driving term
+            k_db = MODE == BATCH_CORRECT ? TC(0) : (TC)k1.z;
+            k_dt = MODE == BATCH_CORRECT ? TC(0) : (TC)k1.w;
+        }
         live = a.frozen[A.inst] > s;
     }
     const long ncells = A.ncells;
@@ -258,7 +291,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
     TC hs[RPL * M];
     TC rho = 0, jx = 0, jy = 0;
     if (active) {
-        const TC cx = (TC)k0.x, cy = (TC)k0.y;
+        const TC cx = k_cx, cy = k_cy;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
@@ -268,8 +301,8 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
             const long cy_idx = ypos ? c_below : (yneg ? c_above : c);
             const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
             const TC rho_y = (TC)(ypos ? rb : rt);
-            const TC u_y = (TC)(ypos ? k1.x : k1.y);
-            const TC drive_y = (TC)(ypos ? k1.z : k1.w);
+            const TC u_y = ypos ? k_ub : k_ut;
+            const TC drive_y = ypos ? k_db : k_dt;
             const TC wy = pk<TC>(a.w1, a.w1_f, iy);
             const TC rl_t = (TC)rl, rr_t = (TC)rr;
             TC R = 0, X = 0;
@@ -317,7 +350,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
     TC psd = 0, psn = 0;
     const bool valid = live && in_grid;
     if (active) {
-        const TC om = (TC)k0.z, b = (TC)k0.w;
+        const TC om = k_om, b = k_b;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
@@ -328,13 +361,15 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
             for (int ix = 0; ix < M; ++ix) {
                 const long off = (long)(iy * M + ix) * ncells + c;
                 const TC t = q + pk<TC>(a.xi, a.xi_f, ix) * jj;
-                const TC v = b * hs[r * M + ix] + pk<TC>(a.w1, a.w1_f, ix) * t;
+                TC v = b * hs[r * M + ix] + pk<TC>(a.w1, a.w1_f, ix) * t;
+                if (MODE == BATCH_CORRECT) v += (TC)__ldg(a.src + A.off + off);
+                TC d = 0;
                 if (resid) {
-                    const TC d = v - (TC)__ldg(hi + off);
+                    d = v - (TC)__ldg(hi + off);
                     psd += d * d;
                     psn += v * v;
                 }
-                if (valid) hno[off] = (TS)v;
+                if (valid) hno[off] = (TS)(MODE == BATCH_DEFECT ? d : v);
             }
         }
     }
@@ -353,7 +388,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
     __syncthreads();   // shared arrays are reused by the next group
 }
 
-template <typename TS, typename TC, int M, int G>
+template <typename TS, typename TC, int M, int G, int MODE>
 __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const BatchArgs a)
 {
     constexpr int SPB = lbmk::Shape<G>::SPB;
@@ -364,7 +399,7 @@ __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const
         const long s = a.step0 + si;
         const TS *__restrict__ h = reinterpret_cast<const TS *>(a.buf[s & 1]);
         TS *__restrict__ hn = reinterpret_cast<TS *>(a.buf[(s + 1) & 1]);
-        const bool resid = ((s + 1) % a.resid_every) == 0;
+        const bool resid = MODE == BATCH_DEFECT || ((s + 1) % a.resid_every) == 0;
         // wall-free segments, then segments with wall cells, both round-robin over the blocks;
         // the addressing of the next group is fetched before the current group runs
         const int sl = (int)(threadIdx.x >> 5) / G;
@@ -372,22 +407,25 @@ __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const
         ItemAddr cur = load_addr(a.items, a.nitems, (long)blockIdx.x * SPB + sl);
         for (long grp = blockIdx.x; grp < nb; grp += gridDim.x) {
             const ItemAddr nxt = load_addr(a.items, a.nitems, (grp + gridDim.x) * SPB + sl);
-            batch_group<TS, TC, M, G, false>(a, a.items, grp, cur, s, h, hn, resid, s_mom, s_wall);
+            batch_group<TS, TC, M, G, false, MODE>(a, a.items, grp, cur, s, h, hn, resid, s_mom, s_wall);
             cur = nxt;
         }
         const long nw = ((long)a.nwall + SPB - 1) / SPB;
         cur = load_addr(a.wall_items, a.nwall, (long)blockIdx.x * SPB + sl);
         for (long grp = blockIdx.x; grp < nw; grp += gridDim.x) {
             const ItemAddr nxt = load_addr(a.wall_items, a.nwall, (grp + gridDim.x) * SPB + sl);
-            batch_group<TS, TC, M, G, true>(a, a.wall_items, grp, cur, s, h, hn, resid, s_mom, s_wall);
+            batch_group<TS, TC, M, G, true, MODE>(a, a.wall_items, grp, cur, s, h, hn, resid, s_mom, s_wall);
             cur = nxt;
         }
+        if (MODE == BATCH_DEFECT) continue;    // one pass; the host reads the sums
         if (!grid_barrier(a)) return;
         if (resid) {
             if (blockIdx.x == 0) {
                 for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
                     if (a.frozen[i] <= s) continue;
-                    const double sd = a.acc[2 * i], sn = a.acc[2 * i + 1];
+                    const double sd = a.acc[2 * i];
+                    // the correction's change is measured against the state it corrects
+                    const double sn = MODE == BATCH_CORRECT ? a.ref_n2[i] : a.acc[2 * i + 1];
                     const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
                     a.last_r[i] = r;
                     if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
@@ -430,25 +468,40 @@ __global__ void inst_moments_kernel(const T *h, long ncells, int m, const BatchA
     }
 }
 
-template <typename TS, typename TC, int M, int G>
-void *kernel_ptr() { return (void *)batch_kernel<TS, TC, M, G>; }
+template <typename TS, typename TC, int M, int G, int MODE>
+void *kernel_ptr() { return (void *)batch_kernel<TS, TC, M, G, MODE>; }
 
+// A march kernel and its correction-mode twin per (precision, M, warps per segment); the
+// FP64 defect pass has one shape per M (any item list runs with any warps per segment).
 struct Variant {
     int prec, m, g;
-    void *fn;
+    void *fn, *fn_correct;
     int threads;
 };
 
+template <int M, int G>
+Variant make_variant()
+{
+    return {LBM_FP32_PERTURB, M, G, kernel_ptr<float, float, M, G, BATCH_MARCH>(),
+            kernel_ptr<float, float, M, G, BATCH_CORRECT>(), lbmk::Shape<G>::THREADS};
+}
+
 const std::vector<Variant> &variants()
 {
-    static const std::vector<Variant> v = {
-        {LBM_FP32_PERTURB, 8, 1, kernel_ptr<float, float, 8, 1>(), lbmk::Shape<1>::THREADS},
-        {LBM_FP32_PERTURB, 8, 2, kernel_ptr<float, float, 8, 2>(), lbmk::Shape<2>::THREADS},
-        {LBM_FP32_PERTURB, 8, 4, kernel_ptr<float, float, 8, 4>(), lbmk::Shape<4>::THREADS},
-        {LBM_FP32_PERTURB, 4, 1, kernel_ptr<float, float, 4, 1>(), lbmk::Shape<1>::THREADS},
-        {LBM_FP32_PERTURB, 4, 2, kernel_ptr<float, float, 4, 2>(), lbmk::Shape<2>::THREADS},
-    };
+    static const std::vector<Variant> v = {make_variant<8, 1>(), make_variant<8, 2>(), make_variant<8, 4>(),
+                                           make_variant<4, 1>(), make_variant<4, 2>()};
     return v;
+}
+
+struct DefectShape {
+    void *fn;
+    int g, threads;
+};
+
+DefectShape defect_shape(int m)
+{
+    if (m == 8) return {kernel_ptr<float, double, 8, 4, BATCH_DEFECT>(), 4, lbmk::Shape<4>::THREADS};
+    return {kernel_ptr<float, double, 4, 2, BATCH_DEFECT>(), 2, lbmk::Shape<2>::THREADS};
 }
 
 const Variant *find_variant(int prec, int m, int g)
@@ -493,6 +546,13 @@ struct lbm_batch {
     bool graph_ok;
     cudaStream_t cap_stream;   // private capture stream (created on first use)
     long long timeout_cycles;
+    // refinement workspace (allocated by the first lbm_batch_refine): the states being
+    // refined, the defect, two correction buffers, then per-instance sums and flags
+    void *ref_base;
+    float *r_h, *r_d, *r_c[2];
+    double *r_acc, *r_last, *r_n2;
+    long *r_frozen;
+    int *r_list;
 };
 
 namespace {
@@ -673,20 +733,127 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     return a;
 }
 
-cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a, cudaStream_t st)
+cudaError_t launch_coop(void *fn, int grid, int threads, const BatchArgs &a, cudaStream_t st)
 {
     void *args[] = {(void *)&a};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
-    cfg.gridDim = dim3(b->grid);
-    cfg.blockDim = dim3(b->var->threads);
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, b->var->fn, args);
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a, cudaStream_t st)
+{
+    return launch_coop(b->var->fn, b->grid, b->var->threads, a, st);
+}
+
+// Co-resident grid of a kernel of this batch for the current item lists.
+int coop_grid(const lbm_batch *b, void *fn, int threads, int g)
+{
+    int dev = 0, nsm = 0, maxb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, fn, threads, 0) != cudaSuccess || maxb < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int spb = segs_per_block(g);
+    const long groups = std::max(((long)b->nitems + spb - 1) / spb, ((long)b->nwall + spb - 1) / spb);
+    return (int)std::min<long>((long)nsm * std::min(maxb, std::max(1, b->blocks_per_sm)), std::max<long>(1, groups));
+}
+
+// h[i] += c[parity of instance i's final correction step][i] for the instances in the list
+__global__ void batch_apply_kernel(float *h, const float *c0, const float *c1, const BatchInst *inst,
+                                   const long *frozen, const int *list, int nv)
+{
+    const int i = list[blockIdx.y];
+    const long n = (long)nv * inst[i].ncells, off = inst[i].off;
+    const float *c = (frozen[i] & 1) ? c1 : c0;
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        h[off + k] += c[off + k];
+}
+
+lbm_status refine_alloc(lbm_batch *b)
+{
+    if (b->ref_base) return LBM_OK;
+    const int n = (int)b->inst.size();
+    const size_t sb = align256(sizeof(float) * b->total_vals);
+    const size_t bytes = 4 * sb + align256(sizeof(double) * 2 * n) + 2 * align256(sizeof(double) * n) +
+                         align256(sizeof(long) * n) + align256(sizeof(int) * n);
+    cudaError_t e = cudaMalloc(&b->ref_base, bytes);
+    if (e != cudaSuccess) {
+        b->ref_base = nullptr;
+        return bfail(LBM_ENOMEM, std::string("cudaMalloc for the refinement workspace: ") + cudaGetErrorString(e));
+    }
+    char *p = (char *)b->ref_base;
+    b->r_h = (float *)p;
+    b->r_d = (float *)(p + sb);
+    b->r_c[0] = (float *)(p + 2 * sb);
+    b->r_c[1] = (float *)(p + 3 * sb);
+    size_t o = 4 * sb;
+    b->r_acc = (double *)(p + o);
+    o += align256(sizeof(double) * 2 * n);
+    b->r_last = (double *)(p + o);
+    o += align256(sizeof(double) * n);
+    b->r_n2 = (double *)(p + o);
+    o += align256(sizeof(double) * n);
+    b->r_frozen = (long *)(p + o);
+    o += align256(sizeof(long) * n);
+    b->r_list = (int *)(p + o);
+    return LBM_OK;
+}
+
+lbm_status check_err(lbm_batch *b)
+{
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("refinement: ") + cudaGetErrorString(e));
+    if (err == 1) return bfail(LBM_ETIMEOUT, "a grid barrier of the batched kernel timed out");
+    if (err == 2) return bfail(LBM_ENONFINITE, "non-finite residual in the batch");
+    return LBM_OK;
+}
+
+// Instances in `sel` into the item lists (the schedule otherwise unchanged).
+lbm_status select_items(lbm_batch *b, const std::vector<char> &sel)
+{
+    b->live = sel;
+    return apply_schedule(b, b->g, b->blocks_per_sm, b->order);
+}
+
+// FP64 defect of the states in the workspace for the instances in the item lists:
+// r_d = M64(r_h) - r_h (float); per-instance sums ||D||^2 and ||M64(H)||^2 to the host.
+lbm_status refine_defect(lbm_batch *b, std::vector<double> &sums)
+{
+    const int n = (int)b->inst.size();
+    std::vector<long> open(n, LONG_MAX);
+    BatchArgs a = make_args(b, 1, 0.0);
+    a.buf[0] = b->r_h;
+    a.buf[1] = b->r_d;
+    a.acc = b->r_acc;
+    a.last_r = b->r_last;
+    a.frozen = b->r_frozen;
+    a.step0 = 0;
+    const DefectShape ds = defect_shape(b->m);
+    const int grid = coop_grid(b, ds.fn, ds.threads, ds.g);
+    if (grid < 1) return bfail(LBM_EUNSUPPORTED, "defect kernel does not fit on an SM");
+    cudaError_t e = cudaMemsetAsync(b->r_acc, 0, sizeof(double) * 2 * n, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->r_frozen, open.data(), sizeof(long) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && (b->nitems > 0 || b->nwall > 0)) e = launch_coop(ds.fn, grid, ds.threads, a, b->stream);
+    sums.assign(2 * n, 0.0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sums.data(), b->r_acc, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("defect pass of the batch: ") + cudaGetErrorString(e));
+    return check_err(b);
 }
 
 }  // namespace
@@ -795,6 +962,7 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     b->graph_ok = false;
     b->cap_stream = nullptr;
     b->timeout_cycles = 4000000000LL;   // about 2 s at the GB300 SM clock
+    b->ref_base = nullptr;
     if (b->owns) {
         cudaError_t e = cudaMalloc(&b->base, bytes);
         if (e != cudaSuccess) {
@@ -863,6 +1031,7 @@ void lbm_batch_destroy(lbm_batch *b)
     else cudaDeviceSynchronize();
     if (b->graph_ok) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->ref_base) cudaFree(b->ref_base);
     if (b->owns && b->base) cudaFree(b->base);
     delete b;
 }
@@ -1135,6 +1304,165 @@ lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h)
             for (long k = 0; k < n; ++k) h[k] = tmp[k];
     }
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("reading instance state: ") + cudaGetErrorString(e));
+}
+
+lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double refine_tol, long max_steps,
+                            lbm_batch_refine_info *info)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (!(tol > 0) || max_sweeps < 0 || max_steps < 1 || refine_tol < 0)
+        return bfail(LBM_EINVAL, "invalid refinement arguments");
+    const int n = (int)b->inst.size();
+    lbm_status st = refine_alloc(b);
+    if (st != LBM_OK) return st;
+    // the step each instance stands at (its state is in buffer step & 1), into the workspace
+    std::vector<long> fro(n), at(n);
+    cudaError_t e = cudaMemcpyAsync(fro.data(), b->d_frozen, sizeof(long) * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        at[i] = fro[i] == LONG_MAX ? b->step : fro[i];
+        const size_t bytes = sizeof(float) * b->nv * b->inst[i].ncells;
+        e = cudaMemcpyAsync(b->r_h + b->inst[i].off, (const float *)b->buf[at[i] & 1] + b->inst[i].off, bytes,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    }
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("refinement: ") + cudaGetErrorString(e));
+    const std::vector<char> live0 = b->live;
+    std::vector<double> sums, r64(n, 0.0), n2(n, 0.0);
+    std::vector<int> sweeps(n, 0);
+    std::vector<long> csteps(n, 0);
+    std::vector<char> todo(n, 1);
+    auto restore = [&](lbm_status s0) {
+        lbm_status s1 = select_items(b, live0);
+        return s0 != LBM_OK ? s0 : s1;
+    };
+    st = select_items(b, todo);
+    if (st == LBM_OK) st = refine_defect(b, sums);
+    if (st != LBM_OK) return restore(st);
+    for (int i = 0; i < n; ++i) {
+        n2[i] = sums[2 * i + 1];
+        r64[i] = n2[i] > 0 ? std::sqrt(sums[2 * i] / n2[i]) : 0.0;
+        todo[i] = max_sweeps > 0 && n2[i] > 0 && r64[i] >= tol;
+    }
+    const double ctol = refine_tol > 0 ? refine_tol : 0.1 * tol;
+    const int every = std::max(1, b->resid_every);
+    const int chunk = 5 * every;
+    const size_t state_bytes = sizeof(float) * b->total_vals;
+    std::vector<double> last(n);
+    std::vector<int> list;
+    while (std::count(todo.begin(), todo.end(), 1) > 0) {
+        // --- correction march delta <- L(delta) + D from delta = 0, all open instances at once ---
+        std::vector<char> open = todo;
+        for (int i = 0; i < n; ++i) fro[i] = todo[i] ? LONG_MAX : 0;
+        std::vector<double> best(n, INFINITY);
+        std::vector<int> flat(n, 0);
+        st = select_items(b, open);
+        if (st != LBM_OK) return restore(st);
+        e = cudaMemsetAsync(b->r_c[0], 0, state_bytes, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->r_acc, 0, sizeof(double) * 2 * n, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->r_n2, n2.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->r_frozen, fro.data(), sizeof(long) * n, cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return restore(bfail(LBM_ECUDA, std::string("refinement: ") + cudaGetErrorString(e)));
+        long k = 0;
+        for (;;) {
+            BatchArgs a = make_args(b, chunk, ctol);
+            a.buf[0] = b->r_c[0];
+            a.buf[1] = b->r_c[1];
+            a.src = b->r_d;
+            a.ref_n2 = b->r_n2;
+            a.acc = b->r_acc;
+            a.last_r = b->r_last;
+            a.frozen = b->r_frozen;
+            a.step0 = k;
+            const int grid = coop_grid(b, b->var->fn_correct, b->var->threads, b->g);
+            if (grid < 1) return restore(bfail(LBM_EUNSUPPORTED, "correction kernel does not fit on an SM"));
+            e = launch_coop(b->var->fn_correct, grid, b->var->threads, a, b->stream);
+            k += chunk;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(fro.data(), b->r_frozen, sizeof(long) * n, cudaMemcpyDeviceToHost, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(last.data(), b->r_last, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess)
+                return restore(bfail(LBM_ECUDA, std::string("correction march of the batch: ") + cudaGetErrorString(e)));
+            st = check_err(b);
+            if (st != LBM_OK) return restore(st);
+            // converged instances leave the lists; those whose change has not improved by 1 %
+            // over 20 residual checks (the FP32 rounding floor), or that reached max_steps,
+            // are stopped at the current step
+            bool changed = false, forced = false;
+            for (int i = 0; i < n; ++i) {
+                if (!open[i]) continue;
+                if (fro[i] != LONG_MAX) {
+                    open[i] = 0;
+                    changed = true;
+                    continue;
+                }
+                if (last[i] < 0.99 * best[i]) {
+                    best[i] = last[i];
+                    flat[i] = 0;
+                } else {
+                    flat[i] += chunk / every;
+                }
+                if (flat[i] >= 20 || k >= max_steps) {
+                    fro[i] = k;
+                    open[i] = 0;
+                    changed = forced = true;
+                }
+            }
+            if (forced) {
+                e = cudaMemcpyAsync(b->r_frozen, fro.data(), sizeof(long) * n, cudaMemcpyHostToDevice, b->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+                if (e != cudaSuccess) return restore(bfail(LBM_ECUDA, std::string("refinement: ") + cudaGetErrorString(e)));
+            }
+            if (std::count(open.begin(), open.end(), 1) == 0) break;
+            if (changed) {
+                st = select_items(b, open);
+                if (st != LBM_OK) return restore(st);
+            }
+        }
+        // --- h += delta, then the FP64 defect of the corrected states ---
+        list.clear();
+        long maxv = 0;
+        for (int i = 0; i < n; ++i)
+            if (todo[i]) {
+                list.push_back(i);
+                csteps[i] += fro[i];
+                sweeps[i] += 1;
+                maxv = std::max(maxv, (long)b->nv * b->inst[i].ncells);
+            }
+        e = cudaMemcpyAsync(b->r_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) {
+            const int bx = (int)std::min<long>(1024, (maxv + 1023) / 1024);
+            batch_apply_kernel<<<dim3(bx, (unsigned)list.size()), 256, 0, b->stream>>>(
+                b->r_h, b->r_c[0], b->r_c[1], b->d_inst, b->r_frozen, b->r_list, b->nv);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return restore(bfail(LBM_ECUDA, std::string("applying the corrections: ") + cudaGetErrorString(e)));
+        st = select_items(b, todo);
+        if (st == LBM_OK) st = refine_defect(b, sums);
+        if (st != LBM_OK) return restore(st);
+        for (int i : list) {
+            const double prev = r64[i];
+            r64[i] = sums[2 * i + 1] > 0 ? std::sqrt(sums[2 * i] / sums[2 * i + 1]) : 0.0;
+            // done below tol, at the FP32 rounding floor (the defect stopped halving), or
+            // after max_sweeps
+            if (r64[i] < tol || r64[i] > 0.5 * prev || sweeps[i] >= max_sweeps) todo[i] = 0;
+        }
+    }
+    // refined states back to the buffer each instance's step points at
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        if (sweeps[i] > 0)
+            e = cudaMemcpyAsync((float *)b->buf[at[i] & 1] + b->inst[i].off, b->r_h + b->inst[i].off,
+                                sizeof(float) * b->nv * b->inst[i].ncells, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return restore(bfail(LBM_ECUDA, std::string("refinement: ") + cudaGetErrorString(e)));
+    if (info)
+        for (int i = 0; i < n; ++i) {
+            info[i].correction_steps = csteps[i];
+            info[i].sweeps = sweeps[i];
+            info[i].defect = r64[i];
+        }
+    return restore(LBM_OK);
 }
 
 }  // extern "C"

@@ -826,7 +826,9 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
         const int grid = grid_for(s->ncells, g), nparts = nparts_for(s, g);
         const double ctol = refine_tol > 0 ? refine_tol : 0.1 * tol;
         const size_t state_bytes = (size_t)s->nv * s->ncells * sizeof(float);
-        for (int sw = 0; sw < refine_sweeps && r64 >= tol * 1e-2 && hnorm > 0; ++sw) {
+        // sweeps until the FP64 defect -- the FP64 march's own residual, evaluated on the
+        // refined state -- is below tol
+        for (int sw = 0; sw < refine_sweeps && r64 >= tol && hnorm > 0; ++sw) {
             // correction march delta <- L(delta) + D from delta = 0 (homogeneous walls)
             void *C[2] = {s->buf[s->cur ^ 1], s->buf[3]};
             int cc = 0;

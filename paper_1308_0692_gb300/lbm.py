@@ -101,6 +101,7 @@ def _load():
         "lbm_batch_get_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_batch_reset": (st, [_vp]),
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
+        "lbm_batch_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, _vp]),
         "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_batch_warm_start": (st, [_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double]),
         "lbm_batch_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -482,6 +483,19 @@ def lbm_batch_get_state(b: Batch, i: int) -> np.ndarray:
 
 def lbm_batch_moments(b: Batch, i: int, out_ptr: int):
     _check(_load().lbm_batch_moments(b.handle, int(i), out_ptr))
+
+
+class BatchRefineInfo(ctypes.Structure):
+    _fields_ = [("correction_steps", ctypes.c_long), ("sweeps", ctypes.c_int), ("defect", ctypes.c_double)]
+
+
+def lbm_batch_refine(b: Batch, tol: float, max_sweeps: int = 3, refine_tol: float = 0.0,
+                     max_steps: int = 1_000_000) -> list:
+    """Batched mixed-precision refinement of every instance; one dict per instance."""
+    info = (BatchRefineInfo * len(b.probs))()
+    _check(_load().lbm_batch_refine(b.handle, float(tol), int(max_sweeps), float(refine_tol), int(max_steps),
+                                    ctypes.cast(info, ctypes.c_void_p)))
+    return [{"correction_steps": r.correction_steps, "sweeps": r.sweeps, "defect": r.defect} for r in info]
 
 
 def lbm_batch_set_state(b: Batch, i: int, h: np.ndarray):

@@ -194,6 +194,29 @@ def refine_instances(vs, b, pairs, tol, side=128, threads=32, refine_tol=0.0):
     return sims, np.array(corr), time.perf_counter() - t0
 
 
+def refine_batch(b, tol, refine_tol=0.0, max_sweeps=3):
+    """Mixed-precision refinement of every batch instance in place, all instances in one
+    persistent launch per chunk of correction steps (lbm_batch_refine); returns (per-instance
+    records, seconds)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = lbm.lbm_batch_refine(b, tol, max_sweeps, refine_tol)
+    torch.cuda.synchronize()
+    return info, time.perf_counter() - t0
+
+
+def batch_fields(b, i):
+    """(u_x, u_y) of batch instance i, host FP64 [ny][nx]."""
+    import torch
+    p = b.probs[i]
+    mom = torch.empty(6 * p.nx * p.ny, dtype=torch.float64, device="cuda")
+    lbm.lbm_batch_moments(b, i, mom.data_ptr())
+    torch.cuda.synchronize()
+    m = mom.view(6, p.ny, p.nx).cpu().numpy()
+    return m[1], m[2]
+
+
 def main(argv=None):
     import argparse
     import json

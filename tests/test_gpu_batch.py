@@ -111,3 +111,64 @@ def test_batch_rejects_mixed_or_unsupported():
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_batch_bytes(vs6, _probs())
     assert e.value.status == lbm.LBM_EUNSUPPORTED
+
+
+def _fp64_steady(vs, g, nx, ny, kn, ub, ut):
+    sim = lbm.lbm_init(vs, lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP64, residual_every=100),
+                       stream=torch.cuda.Stream())
+    info = lbm.lbm_solve(sim, 1e-12, 2_000_000, 0)
+    assert info["residual"] < 1e-12
+    m = lbm.lbm_moments(sim)
+    return m["ux"], m["uy"]
+
+
+@pytest.mark.parametrize("n_half", [4, 2])
+def test_batch_refine_meets_1e5_per_instance(n_half):
+    """Batched FP32 march to 1e-6, then the batched refinement (FP64 defect, FP32 correction
+    march of all instances in one launch) to a defect target of 1e-10: every instance's
+    steady velocity field is within 1e-5 of the FP64 steady state (max |du| / u_w); step
+    counts and convergence flags are unchanged; and max_sweeps = 0 changes nothing."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    b = lbm.lbm_batch_init(vs, _probs(residual_every=100), stream=torch.cuda.Stream())
+    for _ in range(400):
+        lbm.lbm_batch_advance(b, 500, 1e-6)
+        if lbm.lbm_batch_poll(b)[0] == 0:
+            break
+    stats = [lbm.lbm_batch_status(b, i) for i in range(len(INSTANCES))]
+    assert all(s["converged"] for s in stats)
+    before = [lbm.lbm_batch_get_state(b, i) for i in range(len(INSTANCES))]
+    info0 = lbm.lbm_batch_refine(b, 1e-10, 0)
+    assert all(r["sweeps"] == 0 and r["correction_steps"] == 0 for r in info0)
+    for i in range(len(INSTANCES)):
+        np.testing.assert_array_equal(lbm.lbm_batch_get_state(b, i), before[i])
+    info = lbm.lbm_batch_refine(b, 1e-10, 3)
+    assert [lbm.lbm_batch_status(b, i) for i in range(len(INSTANCES))] == stats
+    for i, (g, nx, ny, kn, ub, ut) in enumerate(INSTANCES):
+        assert info[i]["sweeps"] >= 1 and info[i]["correction_steps"] > 0, (i, info[i])
+        assert info[i]["defect"] < info0[i]["defect"], (i, info[i], info0[i])
+        uw = max(abs(ub), abs(ut))
+        m = oracle_problem("half", n_half, g, nx, ny, kn, ub, ut).moments(lbm.lbm_batch_get_state(b, i))
+        ux, uy = _fp64_steady(vs, g, nx, ny, kn, ub, ut)
+        err = max(np.abs(m["ux"] - ux).max(), np.abs(m["uy"] - uy).max()) / uw
+        assert err < 1e-5, (i, err, info[i])
+
+
+def test_batch_refine_matches_single_simulation_refinement():
+    """The batched refinement and lbm_solve's refinement of the same converged FP32 state
+    (lbm_solve marches one more residual interval first) take about the same number of
+    sweeps and end within FP32 rounding of each other."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    g, nx, ny, kn, ub, ut = INSTANCES[4]
+    prob = lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP32_PERTURB, residual_every=100)
+    b = lbm.lbm_batch_init(vs, [prob], stream=torch.cuda.Stream())
+    for _ in range(400):
+        lbm.lbm_batch_advance(b, 500, 1e-6)
+        if lbm.lbm_batch_poll(b)[0] == 0:
+            break
+    h0 = lbm.lbm_batch_get_state(b, 0)
+    sim = lbm.lbm_init(vs, prob, h0, stream=torch.cuda.Stream())
+    sinfo = lbm.lbm_solve(sim, 1e-10, 1_000_000, 3)
+    binfo = lbm.lbm_batch_refine(b, 1e-10, 3)[0]
+    assert abs(binfo["sweeps"] - sinfo["sweeps"]) <= 1
+    hb, hs = lbm.lbm_batch_get_state(b, 0), lbm.lbm_get_state(sim)
+    assert np.abs(hb - hs).max() <= 1e-5 * np.abs(hs).max()

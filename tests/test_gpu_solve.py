@@ -62,7 +62,9 @@ def test_fp32_refined_couette_meets_1e5(kn):
     shear stress, and is at least as close to the oracle as the plain FP32 march."""
     u = 0.01
     ux_ref, flux_ref = _couette_reference(kn, u, -u)
-    sim, info = _gpu_solve(lbm.LBM_COUETTE, 1, 100, kn, u, -u, lbm.LBM_FP32_PERTURB, 1e-8, 3)
+    # the error to the steady state is the residual times the conditioning (up to ~2e3
+    # here): 1e-5 on the profile takes a defect below ~5e-9, so the target is 1e-10
+    sim, info = _gpu_solve(lbm.LBM_COUETTE, 1, 100, kn, u, -u, lbm.LBM_FP32_PERTURB, 1e-10, 3)
     assert info["sweeps"] >= 1
     m = lbm.lbm_moments(sim)
     fy, _ = lbm.lbm_face_flux(sim)
@@ -86,7 +88,7 @@ def test_fp32_refined_cavity_matches_oracle_steady_state():
     assert r < 1e-12
     mref = p.moments(href)
     lid_ref = p.face_flux_y(href)[-1].mean()
-    sim, info = _gpu_solve(lbm.LBM_CAVITY, n, n, 0.1, 0.0, u, lbm.LBM_FP32_PERTURB, 1e-8, 3)
+    sim, info = _gpu_solve(lbm.LBM_CAVITY, n, n, 0.1, 0.0, u, lbm.LBM_FP32_PERTURB, 1e-10, 3)
     m = lbm.lbm_moments(sim)
     for k in ("ux", "uy"):
         assert np.abs(m[k] - mref[k]).max() / u < 1e-5, k
