@@ -400,7 +400,7 @@ def run_fp64_same_workload(vs, dist):
 
 # refinement design behind the time-to-residual headline: "per_instance" (one simulation per
 # instance on concurrent streams) or "batched" (lbm_batch_refine)
-REFINE_HEADLINE = "per_instance"
+REFINE_HEADLINE = "batched"
 
 
 def run_time_to_residual(dist, count=32):

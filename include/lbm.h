@@ -285,6 +285,16 @@ void lbm_batch_destroy(lbm_batch *b);
 lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int blocks_per_sm, int order);
 lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, int *blocks_per_sm,
                                   int *order, int *grid);
+/* Column march of cavity instances (on by default where the velocity set has 4 or 8 nodes
+ * per axis): cavity instances are advanced by a second persistent kernel in which a block
+ * of eight warps marches a 32-column strip up a chunk of rows, one warp per velocity row,
+ * keeping the upwind rows in registers (each value read once per step) and forming the
+ * wall densities inline; Couette instances always take the segment kernel.  on = 0 puts
+ * every instance on the segment kernel (same results up to FP32 summation order).
+ * lbm_batch_get_march reports the switch, the rows per chunk chosen for the current item
+ * lists, the number of march items and the march kernel's grid (outputs may be NULL). */
+lbm_status lbm_batch_set_march(lbm_batch *b, int on);
+lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid);
 lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol);     /* asynchronous */
 /* Limit of every bounded wait in the grid barrier, in SM clock cycles (default 4e9, about
  * 2 s).  Exposed so that tests can make a wait give up and check the error path. */

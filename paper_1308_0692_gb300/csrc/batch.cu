@@ -61,6 +61,16 @@ struct __align__(16) BatchItem {
 };
 static_assert(sizeof(BatchItem) == 64, "two 32-byte halves");
 
+// One work item of the column march (cavity instances): a strip of 32 columns [x0, x0 + 32)
+// of rows [y0, y1) of one instance, and the instance's step coefficients.
+struct __align__(16) MarchItem {
+    long off;            // element offset of the instance's state [n][ncells] in each array
+    int inst, nx, ny, x0, y0, y1;
+    float cx, cy, omega, b;
+    float u_bottom, u_top, drive_bottom, drive_top;
+};
+static_assert(sizeof(MarchItem) == 64, "four 16-byte loads");
+
 struct BatchArgs {
     void *buf[2];
     const BatchInst *inst;
@@ -81,15 +91,23 @@ struct BatchArgs {
     double tol;
     const float *src;      // BATCH_CORRECT: the defect, added after relaxation
     const double *ref_n2;  // BATCH_CORRECT: squared norm of each instance's state (residual scale)
+    const MarchItem *mitems;        // column-march items (cavity instances)
+    int nmitems;
+    const unsigned char *kind;      // [ninst] 1: marched by the column-march kernel, 0: by segments
+    int kind_sel;                   // the kind whose residuals this launch reduces
     long long timeout_cycles;
     double xi[LBM_MAX_M], w1[LBM_MAX_M];
     float xi_f[LBM_MAX_M], w1_f[LBM_MAX_M];
     double inv_dx_wall, inv_dy_wall;
+    float inv_dx_wall_f, inv_dy_wall_f;
 };
 
-// Grid-wide barrier with a bounded wait; returns false once any block has given up.
+// Grid-wide barrier with a bounded wait; returns false once any block has given up.  The
+// verdict is read once per block (thread 0) and shared, so that every thread of a block
+// takes the same branch (the column march's named barriers need all of a block's warps).
 __device__ bool grid_barrier(const BatchArgs &a)
 {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *gen = a.bar_gen;
@@ -112,9 +130,10 @@ __device__ bool grid_barrier(const BatchArgs &a)
             }
         }
         __threadfence();
+        s_ok = *(volatile int *)a.err == 0;
     }
     __syncthreads();
-    return *(volatile int *)a.err == 0;
+    return s_ok != 0;
 }
 
 template <typename TC>
@@ -422,9 +441,367 @@ __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const
         if (resid) {
             if (blockIdx.x == 0) {
                 for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
-                    if (a.frozen[i] <= s) continue;
+                    if (a.frozen[i] <= s || a.kind[i] != a.kind_sel) continue;
                     const double sd = a.acc[2 * i];
                     // the correction's change is measured against the state it corrects
+                    const double sn = MODE == BATCH_CORRECT ? a.ref_n2[i] : a.acc[2 * i + 1];
+                    const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
+                    a.last_r[i] = r;
+                    if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
+                    if (r < a.tol) a.frozen[i] = s + 1;
+                    a.acc[2 * i] = 0.0;
+                    a.acc[2 * i + 1] = 0.0;
+                }
+            }
+            if (!grid_barrier(a)) return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Compensated FP32 summation (Knuth's TwoSum error-free transformation): the pair (s, c)
+// carries the sum and its rounding error, so that short sums come out as accurate as FP64
+// ones -- FP64 arithmetic itself runs at a small fraction of the FP32 rate on this GPU.
+// Plain IEEE additions (no reassociation; the library is built without fast-math).
+__device__ __forceinline__ void comp_add(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+
+// Column march over cavity instances.  A sub-block of M warps takes one item (a 32-column
+// strip of a chunk of rows); warp iy owns the M velocities of velocity row iy (one xi_y, so
+// its upwind y neighbour is the row below when xi_y > 0, the row above otherwise), lane l
+// owns column x0 + l.  The strip marches up its rows through a ring of four row slots per
+// warp in shared memory, filled by cp.async two rows ahead (the in-flight rows hold no
+// registers): every value is read from memory once per step, plus one extra row per chunk
+// and the two edge columns of each row (served by L2), and the x and y neighbours are read
+// from the ring.  Per row the warps exchange their moment partials through shared memory
+// (one named barrier per row, double-buffered), and with them the wall-density partials
+// of the next row (Eq. 9: side walls from the wall cells' outgoing velocities, the top
+// wall at the last row), so that the ghosts of the next row are known before its
+// transport; the bottom wall's are formed before the first row of a chunk that starts at
+// y = 0.  Arithmetic in FP32 with the same operations in the
+// same order as batch_group; the wall sums and the residual sums are compensated FP32
+// (comp_add), which keeps FP64-grade sums off the slow FP64 pipe.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int M>
+struct MarchShared {
+    static constexpr int SUB = 8 / M;    // items per block of 8 warps
+    static constexpr int NS = 4;         // row slots per warp
+    static constexpr int RW = 34;        // a row line: left edge, 32 cells, right edge
+    float4 mom[SUB][2][M][32];           // [item][row parity][warp][lane]: (rho, jx, jy, -) partials
+    float2 side[SUB][2][2][M];           // [item][parity][left, right][warp]: (sum, error)
+    float2 tb[SUB][2][M][32];            // [item][parity][warp][lane]: bottom or top wall row
+    float2 ring[8][NS][M / 2][RW];       // [warp][slot][velocity pair][line]: velocities (2j, 2j + 1)
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+// nodes and 1-D weights of the velocity pair (2j, 2j + 1)
+__device__ __forceinline__ float2 xi2(const BatchArgs &a, int j) { return make_float2(a.xi_f[2 * j], a.xi_f[2 * j + 1]); }
+__device__ __forceinline__ float2 w2(const BatchArgs &a, int j) { return make_float2(a.w1_f[2 * j], a.w1_f[2 * j + 1]); }
+
+template <int M, int MODE>
+__device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *mi, long s, const float *h,
+                                           float *hn, bool resid, MarchShared<M> &sh)
+{
+    constexpr int HALF = M / 2, P = M / 2, PH = P / 2;    // velocity pairs; pairs j >= PH move right
+    constexpr int SUB = MarchShared<M>::SUB, NS = MarchShared<M>::NS, RW = MarchShared<M>::RW;
+    static_assert(SUB * M == 8 && M <= 16 && HALF % 2 == 0, "eight warps per block; pairs on one side");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = warp / M, iy = warp - sub * M;
+    const int bar_id = 1 + sub, bar_n = 32 * M;
+
+    const int4 *q = reinterpret_cast<const int4 *>(mi);
+    const int4 q0 = __ldg(q), q1 = __ldg(q + 1);
+    const float4 k0 = __ldg(reinterpret_cast<const float4 *>(q + 2)),
+                 k1 = __ldg(reinterpret_cast<const float4 *>(q + 3));
+    const long off = (long)(((unsigned long long)(unsigned)q0.y << 32) | (unsigned)q0.x);
+    const int inst = q0.z, nx = q0.w, ny = q1.x, x0 = q1.y, y0 = q1.z, y1 = q1.w;
+    if (a.frozen[inst] <= s) return;          // converged: its state stays put
+    const int nc = nx * ny;                   // cells of the instance (its state < 2^31 values)
+    const float cx = k0.x, cy = k0.y, om = k0.z, bb = k0.w;
+
+    const float xiy = a.xi_f[iy], wy = a.w1_f[iy];
+    const bool up = xiy > 0.f;                // upwind neighbour below; ghost at the bottom wall
+    const float nuy = (xiy < 0.f ? -xiy : xiy) * cy;
+    float2 nux2[P];                           // |xi_x| dt / dx per velocity pair
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const float u0 = a.xi_f[2 * j], u1 = a.xi_f[2 * j + 1];
+        nux2[j] = make_float2((u0 < 0.f ? -u0 : u0) * cx, (u1 < 0.f ? -u1 : u1) * cx);
+    }
+    const int x = x0 + lane;
+    const bool valid = x < nx;
+    const bool wl = x == 0, wr = x == nx - 1;
+    const bool side_l = x0 == 0, side_r = x0 + 32 >= nx, side = side_l || side_r;
+    const int lr = nx - 1 - x0;               // lane of the right-wall cell when side_r
+    const float *hb = h + off + (long)(iy * M) * nc;
+    float *ho = hn + off + (long)(iy * M) * nc;
+    float2 (*ring)[P][RW] = sh.ring[warp];
+
+    // copy row r of this warp's M velocities into slot r mod NS: the 32 cells (clamped into
+    // the row), and in one more copy the edge columns x0 - 1 (lanes 0..M-1, one velocity
+    // each) and x0 + 32 (lanes 16..16+M-1); one commit group per call
+    const int xc = valid ? x : nx - 1;
+    const bool edge_l = lane < M, edge_r = lane >= 16 && lane < 16 + M;
+    const int e_ix = edge_l ? lane : lane - 16;
+    const int e_x = edge_l ? (x0 > 0 ? x0 - 1 : 0) : min(x0 + 32, nx - 1);
+    auto copy_row = [&](int r, bool issue) {
+        if (issue) {
+            float2 (*slot)[RW] = ring[r & (NS - 1)];
+            const float *src = hb + (r * nx + xc);
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix)
+                cp_async4(reinterpret_cast<float *>(&slot[ix >> 1][1 + lane]) + (ix & 1), src + ix * nc);
+            if (edge_l || edge_r)
+                cp_async4(reinterpret_cast<float *>(&slot[e_ix >> 1][edge_l ? 0 : RW - 1]) + (e_ix & 1),
+                          hb + (e_ix * nc + r * nx + e_x));
+        }
+        cp_async_commit();
+    };
+    // moving up: rows r - 1, r in hand and r + 1, r + 2 in flight at row r; moving down:
+    // r, r + 1 in hand and r + 2, r + 3 in flight.  The last row a warp reads:
+    const int lim = up ? y1 - 1 : min(y1, ny - 1);
+    if (up) {
+        if (y0 > 0) copy_row(y0 - 1, true);
+        copy_row(y0, true);
+        copy_row(y0 + 1, y0 + 1 <= lim);
+    } else {
+        copy_row(y0, true);
+        copy_row(y0 + 1, y0 + 1 <= lim);
+        copy_row(y0 + 2, y0 + 2 <= lim);
+    }
+    auto wait_in_hand = [&]() {               // all groups but the newest have landed
+        cp_async_wait<1>();
+        __syncwarp();
+    };
+
+    // Eq. 9 sums: the outgoing velocities' normal fluxes at the wall cells of row r
+    auto wall_partials = [&](int r, int p) {
+        const float2 (*row)[RW] = ring[r & (NS - 1)];
+        if (side_l && lane == 0) {
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int j = 0; j < PH; ++j) {
+                const float2 u = row[j][1];
+                comp_add(hi, lo, -(a.xi_f[2 * j] * u.x));
+                comp_add(hi, lo, -(a.xi_f[2 * j + 1] * u.y));
+            }
+            sh.side[sub][p][0][iy] = make_float2(hi, lo);
+        }
+        if (side_r && lane == lr) {
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int j = PH; j < P; ++j) {
+                const float2 u = row[j][1 + lr];
+                comp_add(hi, lo, a.xi_f[2 * j] * u.x);
+                comp_add(hi, lo, a.xi_f[2 * j + 1] * u.y);
+            }
+            sh.side[sub][p][1][iy] = make_float2(hi, lo);
+        }
+        if (r == 0 || r == ny - 1) {
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const float2 u = row[j][1 + lane];
+                comp_add(hi, lo, u.x);
+                comp_add(hi, lo, u.y);
+            }
+            // |xi_y| times the row sum, with the product's rounding error (FMA) kept;
+            // bottom wall: velocities moving down (xi_y < 0); top wall: moving up
+            const float ax = xiy < 0.f ? -xiy : xiy;
+            const float ph = ax * hi, pl = fmaf(ax, hi, -ph) + ax * lo;
+            const bool in = r == 0 ? !up : up;
+            sh.tb[sub][p][iy][lane] = in ? make_float2(ph, pl) : make_float2(0.f, 0.f);
+        }
+    };
+    float rho_l = 0.f, rho_r = 0.f, rho_w = 0.f;    // side walls; bottom or top wall of a wall row
+    auto total = [&](const float2 *t, int stride, float inv) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int w = 0; w < M; ++w) {
+            const float2 u = t[w * stride];
+            comp_add(hi, lo, u.x);
+            lo += u.y;
+        }
+        return fmaf(hi, inv, lo * inv);
+    };
+    auto read_walls = [&](int r, int p) {
+        if (side_l) rho_l = total(&sh.side[sub][p][0][0], 1, a.inv_dx_wall_f);
+        if (side_r) rho_r = total(&sh.side[sub][p][1][0], 1, a.inv_dx_wall_f);
+        if (r == 0 || r == ny - 1) rho_w = total(&sh.tb[sub][p][0][lane], 32, a.inv_dy_wall_f);
+    };
+    wait_in_hand();
+    {
+        const int p0 = (y0 + 1) & 1;
+        wall_partials(y0, p0);
+        named_barrier(bar_id, bar_n);
+        read_walls(y0, p0);
+    }
+    // wall speed and driving term of the wall this warp's velocities come from (Eq. 8)
+    const float uw = up ? k1.x : k1.y;
+    const float dw = MODE == BATCH_CORRECT ? 0.f : (up ? k1.z : k1.w);
+    const float *sb = MODE == BATCH_CORRECT ? a.src + off + (long)(iy * M) * nc : nullptr;
+
+    float2 v[P];
+    // transport (Eqs. 1, 8-9) of row r into v[] (FP32x2 over velocity pairs, per velocity the
+    // same operations as batch_group); SIDE: a side-wall cell in the strip, WROW: the y ghost
+    // of a wall row.  Returns the partial moments (rho, jx).
+    // (called with literal flags: each call site is inlined and specialised)
+    auto transport = [&](bool SIDE, bool WROW, const float2 (*cur)[RW], const float2 (*yrow)[RW]) {
+        float2 R2 = make_float2(0.f, 0.f), X2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const float2 hc = cur[j][1 + lane];
+            float2 xn = cur[j][j >= PH ? lane : lane + 2];
+            if (SIDE) {
+                const float2 wa = __fmul2_rn(w2(a, j), splat(wy));
+                if (j >= PH && wl) xn = __fmul2_rn(wa, splat(rho_l));
+                if (j < PH && wr) xn = __fmul2_rn(wa, splat(rho_r));
+            }
+            float2 yn;
+            if (WROW) {
+                const float2 wa = __fmul2_rn(w2(a, j), splat(wy));
+                const float2 g = __ffma2_rn(xi2(a, j), splat(uw), splat(1.f));
+                yn = __fmul2_rn(wa, __ffma2_rn(xi2(a, j), splat(dw), __fmul2_rn(splat(rho_w), g)));
+            } else {
+                yn = yrow[j][1 + lane];
+            }
+            float2 t = __ffma2_rn(nux2[j], __fadd2_rn(xn, neg2(hc)), hc);
+            t = __ffma2_rn(splat(nuy), __fadd2_rn(yn, neg2(hc)), t);
+            v[j] = t;
+            R2 = __fadd2_rn(R2, t);
+            X2 = __ffma2_rn(xi2(a, j), t, X2);
+        }
+        return make_float2(R2.x + R2.y, X2.x + X2.y);
+    };
+    float psd = 0.f, psd_c = 0.f, psn = 0.f, psn_c = 0.f;
+    // relaxation (Eqs. 5-7) towards w_a (rho + xi.j) and the store; RESID: residual sums
+    auto relax = [&](bool RESID, const float2 (*cur)[RW], float qq, float jj, int o) {
+        float2 sd = make_float2(0.f, 0.f), sn = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const float2 t = __ffma2_rn(xi2(a, j), splat(jj), splat(qq));
+            float2 nv = __ffma2_rn(w2(a, j), t, __fmul2_rn(splat(bb), v[j]));
+            if (MODE == BATCH_CORRECT && valid) {
+                nv.x += __ldg(sb + ((2 * j) * nc + o));
+                nv.y += __ldg(sb + ((2 * j + 1) * nc + o));
+            }
+            if (RESID) {
+                const float2 d = __fadd2_rn(nv, neg2(cur[j][1 + lane]));
+                sd = __ffma2_rn(d, d, sd);
+                sn = __ffma2_rn(nv, nv, sn);
+            }
+            if (valid) {
+                ho[(2 * j) * nc + o] = nv.x;
+                ho[(2 * j + 1) * nc + o] = nv.y;
+            }
+        }
+        if (RESID && valid) {
+            comp_add(psd, psd_c, sd.x + sd.y);
+            comp_add(psn, psn_c, sn.x + sn.y);
+        }
+    };
+
+    for (int r = y0; r < y1; ++r) {
+        const int p = r & 1;
+        if (r > y0) wait_in_hand();
+        // refill: the slot of row r - 2 (moving up) or r - 1 (moving down), read by now
+        if (up) copy_row(r + 2, r + 2 <= lim);
+        else copy_row(r + 3, r + 3 <= lim);
+        const float2 (*cur)[RW] = ring[r & (NS - 1)];
+        const float2 (*yrow)[RW] = ring[(up ? r - 1 : r + 1) & (NS - 1)];
+        // the y ghost of a wall row: bottom for warps moving up, top for warps moving down
+        const bool wrow = up ? r == 0 : r == ny - 1;
+        float2 rx;
+        if (wrow) rx = side ? transport(true, true, cur, yrow) : transport(false, true, cur, yrow);
+        else rx = side ? transport(true, false, cur, yrow) : transport(false, false, cur, yrow);
+        sh.mom[sub][p][iy][lane] = make_float4(rx.x, rx.y, xiy * rx.x, 0.f);
+        // the next row's wall sums travel with this row's moments
+        if (r + 1 < y1 && (side || r + 1 == ny - 1)) {
+            cp_async_wait<1>();               // row r + 1 (moving up: the older group in flight)
+            __syncwarp();
+            wall_partials(r + 1, p);
+        }
+        named_barrier(bar_id, bar_n);
+        float rho = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+        for (int w = 0; w < M; ++w) {
+            const float4 u = sh.mom[sub][p][w][lane];
+            rho += u.x;
+            jx += u.y;
+            jy += u.z;
+        }
+        const float wom = om * wy;
+        const float qq = wom * (rho + xiy * jy);
+        const float jj = wom * jx;
+        if (resid) relax(true, cur, qq, jj, r * nx + x);
+        else relax(false, cur, qq, jj, r * nx + x);
+        if (r + 1 < y1) read_walls(r + 1, p);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    if (resid) {
+        double dd = (double)psd + (double)psd_c, dn = (double)psn + (double)psn_c;
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            dd += __shfl_xor_sync(FULL, dd, o2);
+            dn += __shfl_xor_sync(FULL, dn, o2);
+        }
+        if (lane == 0) {
+            atomicAdd(a.acc + 2 * inst, dd);
+            atomicAdd(a.acc + 2 * inst + 1, dn);
+        }
+    }
+}
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(256, 3) batch_march_kernel(const BatchArgs a)
+{
+    constexpr int SUB = MarchShared<M>::SUB;
+    __shared__ MarchShared<M> sh;
+    const int sub = (int)(threadIdx.x >> 5) / M;
+    for (int si = 0; si < a.nsteps; ++si) {
+        const long s = a.step0 + si;
+        const float *h = reinterpret_cast<const float *>(a.buf[s & 1]);
+        float *hn = reinterpret_cast<float *>(a.buf[(s + 1) & 1]);
+        const bool resid = ((s + 1) % a.resid_every) == 0;
+        const long ngroups = ((long)a.nmitems + SUB - 1) / SUB;
+        for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+            const long item = grp * SUB + sub;
+            if (item < a.nmitems) march_item<M, MODE>(a, a.mitems + item, s, h, hn, resid, sh);
+        }
+        if (!grid_barrier(a)) return;
+        if (resid) {
+            if (blockIdx.x == 0) {
+                for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
+                    if (a.frozen[i] <= s || a.kind[i] != a.kind_sel) continue;
+                    const double sd = a.acc[2 * i];
                     const double sn = MODE == BATCH_CORRECT ? a.ref_n2[i] : a.acc[2 * i + 1];
                     const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
                     a.last_r[i] = r;
@@ -493,6 +870,18 @@ const std::vector<Variant> &variants()
     return v;
 }
 
+// column-march kernels (cavity instances): M = 4 or 8 nodes per axis
+struct MarchFns {
+    void *march, *correct;
+};
+
+MarchFns march_fns(int m)
+{
+    if (m == 8) return {(void *)batch_march_kernel<8, BATCH_MARCH>, (void *)batch_march_kernel<8, BATCH_CORRECT>};
+    if (m == 4) return {(void *)batch_march_kernel<4, BATCH_MARCH>, (void *)batch_march_kernel<4, BATCH_CORRECT>};
+    return {nullptr, nullptr};
+}
+
 struct DefectShape {
     void *fn;
     int g, threads;
@@ -529,6 +918,12 @@ struct lbm_batch {
     void *buf[2];
     BatchInst *d_inst;
     BatchItem *d_items;
+    MarchItem *d_mitems;        // column-march items (cavity instances when the march is on)
+    unsigned char *d_kind;      // [count] 1: cavity instance marched by columns
+    bool march;                 // cavity instances by the column-march kernel
+    int nmitems, mgrid, mchunk; // march items, their co-resident grid, rows per chunk
+    std::vector<std::pair<void *, int>> occ;   // resident blocks per SM of each kernel used
+    int nsm;
     std::vector<char> live;     // instances in the current item lists (not yet converged)
     double *d_acc, *d_last_r;
     long *d_frozen;
@@ -628,12 +1023,14 @@ BatchItem make_item(const BatchInst &I, int inst, int seg)
     return t;
 }
 
-void build_items(const lbm_batch *b, int order, std::vector<BatchItem> &bulk, std::vector<BatchItem> &wall)
+bool marched(const lbm_batch *b, int i, bool march) { return march && b->inst[i].cavity; }
+
+void build_items(const lbm_batch *b, int order, bool march, std::vector<BatchItem> &bulk, std::vector<BatchItem> &wall)
 {
     const int ni = (int)b->inst.size();
     std::vector<int> idx;
     for (int i = 0; i < ni; ++i)
-        if (b->live[i]) idx.push_back(i);
+        if (b->live[i] && !marched(b, i, march)) idx.push_back(i);
     if (order >= 1)
         std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return b->inst[p].ncells > b->inst[q].ncells; });
     bulk.clear();
@@ -655,27 +1052,160 @@ void build_items(const lbm_batch *b, int order, std::vector<BatchItem> &bulk, st
     }
 }
 
+// Column-march items of the live cavity instances with chunks of about `chunk` rows:
+// chunk-major across instances (item k of every instance, then item k + 1, ...), so that
+// the static round-robin deal gives each block a mix of instances.
+void build_march_items(const lbm_batch *b, int chunk, std::vector<MarchItem> &out)
+{
+    out.clear();
+    const int ni = (int)b->inst.size();
+    std::vector<std::vector<MarchItem>> per(ni);
+    size_t most = 0;
+    for (int i = 0; i < ni; ++i) {
+        if (!b->live[i] || !b->inst[i].cavity) continue;
+        const BatchInst &I = b->inst[i];
+        const int nch = std::max(1, (I.ny + chunk - 1) / chunk);
+        for (int k = 0; k < nch; ++k)
+            for (int x0 = 0; x0 < I.nx; x0 += 32) {
+                MarchItem t;
+                std::memset(&t, 0, sizeof t);
+                t.off = I.off;
+                t.inst = i;
+                t.nx = I.nx;
+                t.ny = I.ny;
+                t.x0 = x0;
+                t.y0 = (int)((long)I.ny * k / nch);
+                t.y1 = (int)((long)I.ny * (k + 1) / nch);
+                t.cx = (float)I.cx;
+                t.cy = (float)I.cy;
+                t.omega = (float)I.omega;
+                t.b = (float)I.b;
+                t.u_bottom = (float)I.u_bottom;
+                t.u_top = (float)I.u_top;
+                t.drive_bottom = (float)(I.u_bottom * I.inv_u_ref);
+                t.drive_top = (float)(I.u_top * I.inv_u_ref);
+                per[i].push_back(t);
+            }
+        most = std::max(most, per[i].size());
+    }
+    for (size_t k = 0; k < most; ++k)
+        for (int i = 0; i < ni; ++i)
+            if (k < per[i].size()) out.push_back(per[i][k]);
+}
+
+// Resident blocks per SM of a kernel of this batch (queried once per kernel) and the SM count.
+cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks)
+{
+    if (b->nsm == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) {
+            b->nsm = 0;
+            return e;
+        }
+    }
+    *nsm = b->nsm;
+    for (const auto &o : b->occ)
+        if (o.first == fn) {
+            *blocks = o.second;
+            return cudaSuccess;
+        }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, 0);
+    if (e == cudaSuccess) b->occ.emplace_back(fn, *blocks);
+    return e;
+}
+
+// Rows per chunk of the column march: the candidate whose static round-robin deal over
+// `slots` item slots has the smallest makespan, an item costing its rows plus the halo row
+// and a fixed start-up (initial loads, wall prologue) of about three rows.
+int march_chunk_plan(const lbm_batch *b, long slots)
+{
+    static const int cand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024, 2048, 4096};
+    std::vector<int> idx;
+    int max_ny = 0;
+    for (int i = 0; i < (int)b->inst.size(); ++i)
+        if (b->live[i] && b->inst[i].cavity) {
+            idx.push_back(i);
+            max_ny = std::max(max_ny, b->inst[i].ny);
+        }
+    int best_h = 32;
+    if (idx.empty()) return best_h;
+    double best = INFINITY;
+    std::vector<double> load;
+    std::vector<int> nch(idx.size()), nit(idx.size());
+    for (int hc : cand) {
+        // the deal of build_march_items (chunk-major across instances), costs only
+        long total = 0;
+        int most = 0;
+        for (size_t u = 0; u < idx.size(); ++u) {
+            const BatchInst &I = b->inst[idx[u]];
+            nch[u] = std::max(1, (I.ny + hc - 1) / hc);
+            nit[u] = nch[u] * ((I.nx + 31) / 32);
+            total += nit[u];
+            most = std::max(most, nit[u]);
+        }
+        load.assign((size_t)std::max<long>(1, std::min<long>(slots, total)), 0.0);
+        size_t k = 0;
+        for (int it = 0; it < most; ++it)
+            for (size_t u = 0; u < idx.size(); ++u) {
+                if (it >= nit[u]) continue;
+                const BatchInst &I = b->inst[idx[u]];
+                const int c = it / ((I.nx + 31) / 32);
+                const long rows = (long)I.ny * (c + 1) / nch[u] - (long)I.ny * c / nch[u];
+                load[k++ % load.size()] += rows + 4.0;
+            }
+        const double span = *std::max_element(load.begin(), load.end());
+        if (span < best * 0.999) {
+            best = span;
+            best_h = hc;
+        }
+        if (hc >= max_ny) break;          // every instance is one chunk from here on
+    }
+    return best_h;
+}
+
+lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool march);
+
 lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
+{
+    return apply_schedule_march(b, g, bpsm, order, b->march);
+}
+
+lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool march)
 {
     const Variant *v = find_variant(b->prec, b->m, g);
     if (!v) return bfail(LBM_EUNSUPPORTED, "no batched kernel for this precision / velocity set / warps per segment");
-    int dev = 0, nsm = 0, maxb = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, v->fn, v->threads, 0);
+    int nsm = 0, maxb = 0, mb = 0;
+    cudaError_t e = occupancy(b, v->fn, v->threads, &nsm, &maxb);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     if (maxb < 1) return bfail(LBM_EUNSUPPORTED, "batched kernel does not fit on an SM");
     if (bpsm < 1 || bpsm > maxb) bpsm = maxb;
     std::vector<BatchItem> items, wall;
-    build_items(b, order, items, wall);
+    build_items(b, order, march, items, wall);
+    std::vector<MarchItem> mitems;
+    int mgrid = 0, mchunk = 0;
+    const MarchFns mf = march_fns(b->m);
+    if (march && mf.march) {
+        e = occupancy(b, mf.march, 256, &nsm, &mb);
+        if (e != cudaSuccess || mb < 1)
+            return bfail(LBM_EUNSUPPORTED, "column-march kernel does not fit on an SM");
+        const int sub = 8 / b->m;
+        mchunk = march_chunk_plan(b, (long)nsm * mb * sub);
+        build_march_items(b, mchunk, mitems);
+        mgrid = (int)std::min<long>((long)nsm * mb, std::max<long>(1, ((long)mitems.size() + sub - 1) / sub));
+    }
+    // stream-ordered uploads (pageable sources are staged before the calls return)
     e = cudaSuccess;
-    if (!items.empty())
+    if (!mitems.empty())
+        e = cudaMemcpyAsync(b->d_mitems, mitems.data(), sizeof(MarchItem) * mitems.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !items.empty())
         e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess && !wall.empty())
         e = cudaMemcpyAsync(b->d_items + items.size(), wall.data(), sizeof(BatchItem) * wall.size(),
                             cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("uploading the schedule: ") + cudaGetErrorString(e));
     if (b->graph_ok) cudaGraphExecDestroy(b->graph);
     b->graph_ok = false;
@@ -685,6 +1215,9 @@ lbm_status apply_schedule(lbm_batch *b, int g, int bpsm, int order)
     b->order = order;
     b->nitems = (int)items.size();
     b->nwall = (int)wall.size();
+    b->nmitems = (int)mitems.size();
+    b->mgrid = mgrid;
+    b->mchunk = mchunk;
     const int spb = segs_per_block(g);
     const long groups = std::max(((long)b->nitems + spb - 1) / spb, ((long)b->nwall + spb - 1) / spb);
     b->grid = (int)std::min<long>((long)nsm * bpsm, std::max<long>(1, groups));
@@ -703,6 +1236,9 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     a.nitems = b->nitems;
     a.wall_items = b->d_items + b->nitems;
     a.nwall = b->nwall;
+    a.mitems = b->d_mitems;
+    a.nmitems = b->nmitems;
+    a.kind = b->d_kind;
     a.acc = b->d_acc;
     a.last_r = b->d_last_r;
     a.frozen = b->d_frozen;
@@ -730,6 +1266,8 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
         }
     a.inv_dx_wall = 1.0 / sx;
     a.inv_dy_wall = 1.0 / sy;
+    a.inv_dx_wall_f = (float)a.inv_dx_wall;
+    a.inv_dy_wall_f = (float)a.inv_dy_wall;
     return a;
 }
 
@@ -749,18 +1287,34 @@ cudaError_t launch_coop(void *fn, int grid, int threads, const BatchArgs &a, cud
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
+// One advance: the column-march kernel over the cavity items, then the segment kernel over
+// the other instances' items (each launched only when it has items).
+cudaError_t launch_pair(lbm_batch *b, const BatchArgs &a0, void *mfn, void *sfn, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    if (b->nmitems > 0) {
+        BatchArgs a = a0;
+        a.kind_sel = 1;
+        e = launch_coop(mfn, b->mgrid, 256, a, st);
+    }
+    if (e == cudaSuccess && (b->nitems > 0 || b->nwall > 0)) {
+        BatchArgs a = a0;
+        a.kind_sel = 0;
+        e = launch_coop(sfn, b->grid, b->var->threads, a, st);
+    }
+    return e;
+}
+
 cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a, cudaStream_t st)
 {
-    return launch_coop(b->var->fn, b->grid, b->var->threads, a, st);
+    return launch_pair(b, a, march_fns(b->m).march, b->var->fn, st);
 }
 
 // Co-resident grid of a kernel of this batch for the current item lists.
-int coop_grid(const lbm_batch *b, void *fn, int threads, int g)
+int coop_grid(lbm_batch *b, void *fn, int threads, int g)
 {
-    int dev = 0, nsm = 0, maxb = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, fn, threads, 0) != cudaSuccess || maxb < 1) {
+    int nsm = 0, maxb = 0;
+    if (occupancy(b, fn, threads, &nsm, &maxb) != cudaSuccess || maxb < 1) {
         cudaGetLastError();
         return 0;
     }
@@ -822,10 +1376,10 @@ lbm_status check_err(lbm_batch *b)
 }
 
 // Instances in `sel` into the item lists (the schedule otherwise unchanged).
-lbm_status select_items(lbm_batch *b, const std::vector<char> &sel)
+lbm_status select_items(lbm_batch *b, const std::vector<char> &sel, bool march)
 {
     b->live = sel;
-    return apply_schedule(b, b->g, b->blocks_per_sm, b->order);
+    return apply_schedule_march(b, b->g, b->blocks_per_sm, b->order, march);
 }
 
 // FP64 defect of the states in the workspace for the instances in the item lists:
@@ -865,14 +1419,14 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
                           size_t buf_bytes, void *stream, lbm_batch **out);
 
 static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int count, int *prec,
-                               long *total_vals, long *total_segs, size_t *bytes)
+                               long *total_vals, long *total_segs, long *total_mitems, size_t *bytes)
 {
     int nv = 0, m = 0;
     lbm_status st = lbm_vset_query(vs, &nv, &m, nullptr, nullptr, nullptr);
     if (st != LBM_OK) return st;
     if (!insts || count < 1) return bfail(LBM_EINVAL, "batch needs at least one instance");
     const int p0 = insts[0].prec;
-    long vals = 0, segs = 0;
+    long vals = 0, segs = 0, mits = 0;
     for (int i = 0; i < count; ++i) {
         size_t one;
         st = lbm_sim_bytes(vs, &insts[i], &one);   // validates the instance
@@ -883,6 +1437,8 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
         const long nc = (long)insts[i].nx * insts[i].ny;
         vals += (long)nv * nc;
         segs += (nc + 31) / 32;
+        if (insts[i].geom == LBM_CAVITY)     // column-march items: chunks of at least 4 rows
+            mits += (long)((insts[i].nx + 31) / 32) * ((insts[i].ny + 3) / 4);
     }
     if (p0 != LBM_FP32_PERTURB || !find_variant(p0, m, 1))
         return bfail(LBM_EUNSUPPORTED, "batched kernels exist for FP32 with 4 or 8 nodes per axis");
@@ -892,6 +1448,8 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
     off = align256(off + vals * es);          // buffer 1
     off = align256(off + sizeof(BatchInst) * count);
     off = align256(off + sizeof(BatchItem) * segs);
+    off = align256(off + sizeof(MarchItem) * std::max(1L, mits));
+    off = align256(off + (size_t)count);                        // instance kinds
     off = align256(off + sizeof(double) * 2 * count);
     off = align256(off + sizeof(double) * count);
     off = align256(off + sizeof(long) * count);
@@ -903,6 +1461,7 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
     *prec = p0;
     *total_vals = vals;
     *total_segs = segs;
+    *total_mitems = mits;
     *bytes = off;
     return LBM_OK;
 }
@@ -911,8 +1470,8 @@ lbm_status lbm_batch_bytes(const lbm_vset *vs, const lbm_problem *insts, int cou
 {
     if (!bytes) return bfail(LBM_EINVAL, "bytes is NULL");
     int prec;
-    long vals, segs;
-    return batch_layout(vs, insts, count, &prec, &vals, &segs, bytes);
+    long vals, segs, mits;
+    return batch_layout(vs, insts, count, &prec, &vals, &segs, &mits, bytes);
 }
 
 lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int count, void *device_buf,
@@ -921,9 +1480,9 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     if (!out) return bfail(LBM_EINVAL, "out is NULL");
     *out = nullptr;
     int prec;
-    long vals, segs;
+    long vals, segs, mits;
     size_t bytes;
-    lbm_status st = batch_layout(vs, insts, count, &prec, &vals, &segs, &bytes);
+    lbm_status st = batch_layout(vs, insts, count, &prec, &vals, &segs, &mits, &bytes);
     if (st != LBM_OK) return st;
     if (device_buf && buf_bytes < bytes) return bfail(LBM_ENOMEM, "device buffer too small for the batch");
     if (device_buf && ((uintptr_t)device_buf & 255)) return bfail(LBM_EINVAL, "device buffer must be 256-byte aligned");
@@ -963,6 +1522,9 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     b->cap_stream = nullptr;
     b->timeout_cycles = 4000000000LL;   // about 2 s at the GB300 SM clock
     b->ref_base = nullptr;
+    b->march = march_fns(m).march != nullptr;
+    b->nmitems = b->mgrid = b->mchunk = 0;
+    b->nsm = 0;
     if (b->owns) {
         cudaError_t e = cudaMalloc(&b->base, bytes);
         if (e != cudaSuccess) {
@@ -983,6 +1545,10 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     o = align256(o + sizeof(BatchInst) * count);
     b->d_items = (BatchItem *)(p + o);
     o = align256(o + sizeof(BatchItem) * segs);
+    b->d_mitems = (MarchItem *)(p + o);
+    o = align256(o + sizeof(MarchItem) * std::max(1L, mits));
+    b->d_kind = (unsigned char *)(p + o);
+    o = align256(o + (size_t)count);
     b->d_acc = (double *)(p + o);
     o = align256(o + sizeof(double) * 2 * count);
     b->d_last_r = (double *)(p + o);
@@ -1004,6 +1570,9 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_last_r, last.data(), sizeof(double) * count, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_frozen, frozen.data(), sizeof(long) * count, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 64, b->stream);
+    std::vector<unsigned char> kind(count);
+    for (int i = 0; i < count; ++i) kind[i] = marched(b, i, b->march) ? 1 : 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_kind, kind.data(), count, cudaMemcpyHostToDevice, b->stream);
     std::vector<double> tab(2 * LBM_MAX_M, 0.0);
     for (int k = 0; k < m; ++k) {
         tab[k] = b->nodes[k];
@@ -1041,6 +1610,30 @@ lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int block
     if (!b) return bfail(LBM_EINVAL, "batch is NULL");
     if (order < 0 || order > 2) return bfail(LBM_EINVAL, "order must be 0, 1 or 2");
     return apply_schedule(b, warps_per_segment, blocks_per_sm, order);
+}
+
+lbm_status lbm_batch_set_march(lbm_batch *b, int on)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (on && !march_fns(b->m).march) return bfail(LBM_EUNSUPPORTED, "no column-march kernel for this velocity set");
+    b->march = on != 0;
+    const int n = (int)b->inst.size();
+    std::vector<unsigned char> kind(n);
+    for (int i = 0; i < n; ++i) kind[i] = marched(b, i, b->march) ? 1 : 0;
+    cudaError_t e = cudaMemcpyAsync(b->d_kind, kind.data(), n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("setting the march: ") + cudaGetErrorString(e));
+    return apply_schedule(b, b->g, b->blocks_per_sm, b->order);
+}
+
+lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid)
+{
+    if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+    if (on) *on = b->march;
+    if (rows_per_chunk) *rows_per_chunk = b->mchunk;
+    if (items) *items = b->nmitems;
+    if (grid) *grid = b->mgrid;
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, int *blocks_per_sm, int *order,
@@ -1332,10 +1925,10 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
     std::vector<long> csteps(n, 0);
     std::vector<char> todo(n, 1);
     auto restore = [&](lbm_status s0) {
-        lbm_status s1 = select_items(b, live0);
+        lbm_status s1 = select_items(b, live0, b->march);
         return s0 != LBM_OK ? s0 : s1;
     };
-    st = select_items(b, todo);
+    st = select_items(b, todo, false);      // the FP64 defect pass runs on segment items
     if (st == LBM_OK) st = refine_defect(b, sums);
     if (st != LBM_OK) return restore(st);
     for (int i = 0; i < n; ++i) {
@@ -1355,7 +1948,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
         for (int i = 0; i < n; ++i) fro[i] = todo[i] ? LONG_MAX : 0;
         std::vector<double> best(n, INFINITY);
         std::vector<int> flat(n, 0);
-        st = select_items(b, open);
+        st = select_items(b, open, b->march);
         if (st != LBM_OK) return restore(st);
         e = cudaMemsetAsync(b->r_c[0], 0, state_bytes, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->r_acc, 0, sizeof(double) * 2 * n, b->stream);
@@ -1373,9 +1966,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
             a.last_r = b->r_last;
             a.frozen = b->r_frozen;
             a.step0 = k;
-            const int grid = coop_grid(b, b->var->fn_correct, b->var->threads, b->g);
-            if (grid < 1) return restore(bfail(LBM_EUNSUPPORTED, "correction kernel does not fit on an SM"));
-            e = launch_coop(b->var->fn_correct, grid, b->var->threads, a, b->stream);
+            e = launch_pair(b, a, march_fns(b->m).correct, b->var->fn_correct, b->stream);
             k += chunk;
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(fro.data(), b->r_frozen, sizeof(long) * n, cudaMemcpyDeviceToHost, b->stream);
@@ -1416,7 +2007,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
             }
             if (std::count(open.begin(), open.end(), 1) == 0) break;
             if (changed) {
-                st = select_items(b, open);
+                st = select_items(b, open, b->march);
                 if (st != LBM_OK) return restore(st);
             }
         }
@@ -1438,7 +2029,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return restore(bfail(LBM_ECUDA, std::string("applying the corrections: ") + cudaGetErrorString(e)));
-        st = select_items(b, todo);
+        st = select_items(b, todo, false);
         if (st == LBM_OK) st = refine_defect(b, sums);
         if (st != LBM_OK) return restore(st);
         for (int i : list) {

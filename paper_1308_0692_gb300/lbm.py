@@ -102,6 +102,9 @@ def _load():
         "lbm_batch_reset": (st, [_vp]),
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
         "lbm_batch_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, _vp]),
+        "lbm_batch_set_march": (st, [_vp, ctypes.c_int]),
+        "lbm_batch_get_march": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_batch_warm_start": (st, [_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double]),
         "lbm_batch_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -452,6 +455,17 @@ def lbm_batch_get_schedule(b: Batch):
     _check(_load().lbm_batch_get_schedule(b.handle, ctypes.byref(g), ctypes.byref(bp), ctypes.byref(o),
                                           ctypes.byref(gr)))
     return {"warps_per_segment": g.value, "blocks_per_sm": bp.value, "order": o.value, "grid": gr.value}
+
+
+def lbm_batch_set_march(b: Batch, on: bool):
+    _check(_load().lbm_batch_set_march(b.handle, int(bool(on))))
+
+
+def lbm_batch_get_march(b: Batch) -> dict:
+    on, ch, it, gr = (ctypes.c_int() for _ in range(4))
+    _check(_load().lbm_batch_get_march(b.handle, ctypes.byref(on), ctypes.byref(ch), ctypes.byref(it),
+                                       ctypes.byref(gr)))
+    return {"on": bool(on.value), "rows_per_chunk": ch.value, "items": it.value, "grid": gr.value}
 
 
 def lbm_batch_advance(b: Batch, nsteps: int, tol: float):

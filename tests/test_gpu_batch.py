@@ -37,11 +37,23 @@ def _probs(residual_every=10):
             for g, nx, ny, kn, ub, ut in INSTANCES]
 
 
+# cavities of awkward shapes for the column march: ragged strips, one- and two-row chunks,
+# a strip narrower than a warp, a non-zero bottom-wall speed
+ODD = [
+    (CAVITY, 70, 9, 0.2, 0.0, 0.01),
+    (CAVITY, 3, 2, 1.0, 0.0, 0.02),
+    (CAVITY, 97, 131, 0.05, 0.004, 0.012),
+    (COUETTE, 1, 7, 0.3, 0.01, -0.01),
+]
+
+
 @pytest.mark.parametrize("schedule", [(4, 0, 0), (2, 0, 2), (1, 1, 1)])
-def test_batch_matches_oracle_per_instance(schedule):
+@pytest.mark.parametrize("march", [True, False])
+def test_batch_matches_oracle_per_instance(schedule, march):
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
     b = lbm.lbm_batch_init(vs, _probs(), stream=torch.cuda.Stream())
     lbm.lbm_batch_set_schedule(b, *schedule)
+    lbm.lbm_batch_set_march(b, march)
     steps = 30
     lbm.lbm_batch_advance(b, 13, 0.0)      # two launches, uneven split
     lbm.lbm_batch_advance(b, steps - 13, 0.0)
@@ -49,6 +61,27 @@ def test_batch_matches_oracle_per_instance(schedule):
     assert n_active == len(INSTANCES) and step == steps
     for i, (g, nx, ny, kn, ub, ut) in enumerate(INSTANCES):
         p = oracle_problem("half", 4, g, nx, ny, kn, ub, ut)
+        ref = p.step(p.zeros(), steps)
+        got = lbm.lbm_batch_get_state(b, i)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= FP32_TOL_PER_STEP * steps, (i, err)
+
+
+@pytest.mark.parametrize("n_half", [2, 4])
+def test_batch_column_march_odd_shapes(n_half):
+    """The column march on ragged strips, short chunks and tiny cavities agrees with the FP64
+    oracle step by step (and the Couette instance beside them with the segment kernel)."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    probs = [lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP32_PERTURB, residual_every=10)
+             for g, nx, ny, kn, ub, ut in ODD]
+    b = lbm.lbm_batch_init(vs, probs, stream=torch.cuda.Stream())
+    info = lbm.lbm_batch_get_march(b)
+    assert info["on"] and info["items"] > 0
+    steps = 25
+    lbm.lbm_batch_advance(b, steps, 0.0)
+    assert lbm.lbm_batch_poll(b) == (len(ODD), steps)
+    for i, (g, nx, ny, kn, ub, ut) in enumerate(ODD):
+        p = oracle_problem("half", n_half, g, nx, ny, kn, ub, ut)
         ref = p.step(p.zeros(), steps)
         got = lbm.lbm_batch_get_state(b, i)
         err = np.abs(got - ref).max() / np.abs(ref).max()
