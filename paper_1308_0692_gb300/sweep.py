@@ -56,7 +56,7 @@ def merge_reports(reports: list[dict]) -> dict:
     per = sorted((r for rep in reports for r in rep["per_instance"]), key=lambda r: r["index"])
     checked = [r["err"] for r in per if "err" in r]
     steps = np.array([r["steps"] for r in per])
-    out = {k: reports[0][k] for k in ("seed",)}
+    out = {k: reports[0][k] for k in ("seed", "refinement") if k in reports[0]}
     out.update({
         "count": len(per), "ranks": len(reports), "unknowns": int(sum(rep["unknowns"] for rep in reports)),
         "schedule": [rep["schedule"] for rep in reports],
@@ -73,8 +73,12 @@ def merge_reports(reports: list[dict]) -> dict:
     return out
 
 
-def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=32, log=_log, indices=None):
-    """Sweep over the instances `indices` of the seed-drawn table of `count` (all by default)."""
+def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=32, log=_log, indices=None,
+        refine="batched"):
+    """Sweep over the instances `indices` of the seed-drawn table of `count` (all by default).
+    refine: "batched" (lbm_batch_refine: every instance's FP64 defect and FP32 correction march
+    in the batch's persistent kernels) or "per_instance" (one simulation per instance, each on
+    its own stream and host thread)."""
     import torch
     full = batch_table(count, seed)
     indices = list(range(count)) if indices is None else list(indices)
@@ -105,26 +109,37 @@ def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=
     log(f"sweep: FP32 batch march to {tol32:g} in {t_batch:.1f} s ({steps_done} steps launched, "
         f"{(steps * cells * 64).sum() / t_batch / 1e9:.1f} G updates/s on active instances)")
 
-    # refinement of every instance, one stream and host thread each
-    sims = []
-    for i, p in enumerate(probs):
-        sims.append(lbm.lbm_init(vs, p, lbm.lbm_batch_get_state(b, i), stream=lbm.PrivateStream()))
-    b.close()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    idx = [i for i, p in enumerate(probs) if p.nx * p.ny <= ref_max_cells]
+    if refine == "batched":
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = lbm.lbm_batch_refine(b, tol, 3, tol, 2_000_000)
+        torch.cuda.synchronize()
+        t_refine = time.perf_counter() - t0
+        ref_info = [(r["correction_steps"], r["defect"]) for r in info]
+        # the refined states of the checked instances into simulations for the diagnostics
+        sims = {i: lbm.lbm_init(vs, probs[i], lbm.lbm_batch_get_state(b, i), stream=lbm.PrivateStream())
+                for i in idx}
+        b.close()
+    else:
+        # refinement of every instance, one stream and host thread each
+        sims = {i: lbm.lbm_init(vs, p, lbm.lbm_batch_get_state(b, i), stream=lbm.PrivateStream())
+                for i, p in enumerate(probs)}
+        b.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
 
-    def refine(sim):
-        info = lbm.lbm_solve(sim, tol, 2_000_000, 3, tol)
-        return info["correction_steps"], info["defect"]
+        def refine_one(sim):
+            info = lbm.lbm_solve(sim, tol, 2_000_000, 3, tol)
+            return info["correction_steps"], info["defect"]
 
-    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        ref_info = list(ex.map(refine, sims))
-    torch.cuda.synchronize()
-    t_refine = time.perf_counter() - t0
-    log(f"sweep: refinement of all instances in {t_refine:.1f} s")
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            ref_info = list(ex.map(refine_one, [sims[i] for i in range(count_local)]))
+        torch.cuda.synchronize()
+        t_refine = time.perf_counter() - t0
+    log(f"sweep: {refine} refinement of all instances in {t_refine:.1f} s")
 
     # FP64 references (GPU march), concurrently
-    idx = [i for i, p in enumerate(probs) if p.nx * p.ny <= ref_max_cells]
 
     def reference(i):
         p64 = _problem(table[i], lbm.LBM_FP64)
@@ -146,11 +161,11 @@ def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=
         errs[i] = {"u": float(max(np.abs(m32["ux"] - m64["ux"]).max(), np.abs(m32["uy"] - m64["uy"]).max()) / uw),
                    "wall_shear": float(np.abs(m32["wall_shear"] - m64["wall_shear"]).max()
                                        / max(np.abs(m64["wall_shear"]).max(), 1e-300))}
-    for s in sims:
+    for s in sims.values():
         s.close()
     report = {
         "count": count_local, "seed": seed, "unknowns": int(unknowns), "schedule": best, "tune_seconds": t_tune,
-        "batch_seconds": t_batch, "refine_seconds": t_refine, "reference_seconds": t_ref,
+        "batch_seconds": t_batch, "refinement": refine, "refine_seconds": t_refine, "reference_seconds": t_ref,
         "steps_min": int(steps.min()), "steps_median": float(np.median(steps)), "steps_max": int(steps.max()),
         "instances_checked": len(errs),
         "max_velocity_error": max(e["u"] for e in errs.values()),
@@ -168,6 +183,7 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--ref-max-cells", type=int, default=128 * 128)
+    ap.add_argument("--refine", choices=["batched", "per_instance"], default="batched")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     import os
@@ -179,7 +195,7 @@ def main(argv=None):
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group(backend="gloo")   # only the final gather of Python records
     rep = run(args.count, tol=args.tol, ref_max_cells=args.ref_max_cells, indices=shard(args.count, rank, world),
-              log=_log if rank == 0 else (lambda *a: None))
+              log=_log if rank == 0 else (lambda *a: None), refine=args.refine)
     if dist is not None:
         reps = [None] * world
         dist.all_gather_object(reps, rep)
