@@ -291,9 +291,12 @@ lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, in
  * keeping the upwind rows in registers (each value read once per step) and forming the
  * wall densities inline; Couette instances always take the segment kernel.  on = 0 puts
  * every instance on the segment kernel (same results up to FP32 summation order).
- * lbm_batch_get_march reports the switch, the rows per chunk chosen for the current item
- * lists, the number of march items and the march kernel's grid (outputs may be NULL). */
-lbm_status lbm_batch_set_march(lbm_batch *b, int on);
+ * The warp groups take items from a per-step counter (dynamic balance across SMs).
+ * rows_per_chunk: rows of one march item (>= 4), or 0 to let the library plan it at every
+ * rebuild of the item lists (about four items per resident warp group, 4 to 64 rows).
+ * lbm_batch_get_march reports the switch, the rows per chunk in use, the number of march
+ * items and the march kernel's grid (outputs may be NULL). */
+lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk);
 lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid);
 lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol);     /* asynchronous */
 /* Limit of every bounded wait in the grid barrier, in SM clock cycles (default 4e9, about

@@ -84,6 +84,7 @@ struct BatchArgs {
     long *frozen;          // [ninst] step count at convergence (LONG_MAX while active)
     unsigned *bar_count;
     unsigned *bar_gen;
+    unsigned *mcount;      // column march: next item of the step, per step parity [2]
     int *err;
     long step0;
     int nsteps;
@@ -702,16 +703,14 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     };
     float psd = 0.f, psd_c = 0.f, psn = 0.f, psn_c = 0.f;
     // relaxation (Eqs. 5-7) towards w_a (rho + xi.j) and the store; RESID: residual sums
+    float2 src[MODE == BATCH_CORRECT ? P : 1];   // the correction's source of the current row
     auto relax = [&](bool RESID, const float2 (*cur)[RW], float qq, float jj, int o) {
         float2 sd = make_float2(0.f, 0.f), sn = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < P; ++j) {
             const float2 t = __ffma2_rn(xi2(a, j), splat(jj), splat(qq));
             float2 nv = __ffma2_rn(w2(a, j), t, __fmul2_rn(splat(bb), v[j]));
-            if (MODE == BATCH_CORRECT && valid) {
-                nv.x += __ldg(sb + ((2 * j) * nc + o));
-                nv.y += __ldg(sb + ((2 * j + 1) * nc + o));
-            }
+            if (MODE == BATCH_CORRECT) nv = __fadd2_rn(nv, src[j]);
             if (RESID) {
                 const float2 d = __fadd2_rn(nv, neg2(cur[j][1 + lane]));
                 sd = __ffma2_rn(d, d, sd);
@@ -736,6 +735,13 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         else copy_row(r + 3, r + 3 <= lim);
         const float2 (*cur)[RW] = ring[r & (NS - 1)];
         const float2 (*yrow)[RW] = ring[(up ? r - 1 : r + 1) & (NS - 1)];
+        if (MODE == BATCH_CORRECT) {          // issued now, used after the moment exchange
+            const int o = r * nx + (valid ? x : nx - 1);
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                src[j] = valid ? make_float2(__ldg(sb + ((2 * j) * nc + o)), __ldg(sb + ((2 * j + 1) * nc + o)))
+                               : make_float2(0.f, 0.f);
+        }
         // the y ghost of a wall row: bottom for warps moving up, top for warps moving down
         const bool wrow = up ? r == 0 : r == ny - 1;
         float2 rx;
@@ -785,16 +791,25 @@ __global__ void __launch_bounds__(256, 3) batch_march_kernel(const BatchArgs a)
 {
     constexpr int SUB = MarchShared<M>::SUB;
     __shared__ MarchShared<M> sh;
-    const int sub = (int)(threadIdx.x >> 5) / M;
+    __shared__ int s_item[SUB][2];            // fetched item of each warp group, double-buffered
+    const int warp = (int)(threadIdx.x >> 5), sub = warp / M;
+    const bool fetcher = warp == sub * M && (threadIdx.x & 31) == 0;
     for (int si = 0; si < a.nsteps; ++si) {
         const long s = a.step0 + si;
         const float *h = reinterpret_cast<const float *>(a.buf[s & 1]);
         float *hn = reinterpret_cast<float *>(a.buf[(s + 1) & 1]);
         const bool resid = ((s + 1) % a.resid_every) == 0;
-        const long ngroups = ((long)a.nmitems + SUB - 1) / SUB;
-        for (long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-            const long item = grp * SUB + sub;
-            if (item < a.nmitems) march_item<M, MODE>(a, a.mitems + item, s, h, hn, resid, sh);
+        // items are taken from a counter per step parity (the next step's is cleared here:
+        // its last use ended at the previous grid barrier); each warp group takes one item
+        // at a time, so that groups on less loaded SMs take more
+        unsigned *next = a.mcount + (s & 1);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.mcount[(s + 1) & 1] = 0u;
+        for (int k = 0;; ++k) {
+            if (fetcher) s_item[sub][k & 1] = (int)atomicAdd(next, 1u);
+            named_barrier(1 + sub, 32 * M);
+            const int item = s_item[sub][k & 1];
+            if (item >= a.nmitems) break;
+            march_item<M, MODE>(a, a.mitems + item, s, h, hn, resid, sh);
         }
         if (!grid_barrier(a)) return;
         if (resid) {
@@ -922,6 +937,7 @@ struct lbm_batch {
     unsigned char *d_kind;      // [count] 1: cavity instance marched by columns
     bool march;                 // cavity instances by the column-march kernel
     int nmitems, mgrid, mchunk; // march items, their co-resident grid, rows per chunk
+    int mchunk_fixed;           // rows per chunk set by the caller (0: planned per rebuild)
     std::vector<std::pair<void *, int>> occ;   // resident blocks per SM of each kernel used
     int nsm;
     std::vector<char> live;     // instances in the current item lists (not yet converged)
@@ -1116,53 +1132,16 @@ cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks
     return e;
 }
 
-// Rows per chunk of the column march: the candidate whose static round-robin deal over
-// `slots` item slots has the smallest makespan, an item costing its rows plus the halo row
-// and a fixed start-up (initial loads, wall prologue) of about three rows.
+// Rows per chunk of the column march: items are fetched dynamically, so the chunks only
+// have to be many enough to balance the SMs (about four per resident warp group) and long
+// enough to amortise an item's start (its first rows' copies and the wall prologue).
 int march_chunk_plan(const lbm_batch *b, long slots)
 {
-    static const int cand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024, 2048, 4096};
-    std::vector<int> idx;
-    int max_ny = 0;
+    long strip_rows = 0;
     for (int i = 0; i < (int)b->inst.size(); ++i)
-        if (b->live[i] && b->inst[i].cavity) {
-            idx.push_back(i);
-            max_ny = std::max(max_ny, b->inst[i].ny);
-        }
-    int best_h = 32;
-    if (idx.empty()) return best_h;
-    double best = INFINITY;
-    std::vector<double> load;
-    std::vector<int> nch(idx.size()), nit(idx.size());
-    for (int hc : cand) {
-        // the deal of build_march_items (chunk-major across instances), costs only
-        long total = 0;
-        int most = 0;
-        for (size_t u = 0; u < idx.size(); ++u) {
-            const BatchInst &I = b->inst[idx[u]];
-            nch[u] = std::max(1, (I.ny + hc - 1) / hc);
-            nit[u] = nch[u] * ((I.nx + 31) / 32);
-            total += nit[u];
-            most = std::max(most, nit[u]);
-        }
-        load.assign((size_t)std::max<long>(1, std::min<long>(slots, total)), 0.0);
-        size_t k = 0;
-        for (int it = 0; it < most; ++it)
-            for (size_t u = 0; u < idx.size(); ++u) {
-                if (it >= nit[u]) continue;
-                const BatchInst &I = b->inst[idx[u]];
-                const int c = it / ((I.nx + 31) / 32);
-                const long rows = (long)I.ny * (c + 1) / nch[u] - (long)I.ny * c / nch[u];
-                load[k++ % load.size()] += rows + 4.0;
-            }
-        const double span = *std::max_element(load.begin(), load.end());
-        if (span < best * 0.999) {
-            best = span;
-            best_h = hc;
-        }
-        if (hc >= max_ny) break;          // every instance is one chunk from here on
-    }
-    return best_h;
+        if (b->live[i] && b->inst[i].cavity) strip_rows += (long)((b->inst[i].nx + 31) / 32) * b->inst[i].ny;
+    const long h = strip_rows / std::max(1L, 4 * slots);
+    return (int)std::max(4L, std::min(64L, h));
 }
 
 lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool march);
@@ -1191,7 +1170,7 @@ lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool m
         if (e != cudaSuccess || mb < 1)
             return bfail(LBM_EUNSUPPORTED, "column-march kernel does not fit on an SM");
         const int sub = 8 / b->m;
-        mchunk = march_chunk_plan(b, (long)nsm * mb * sub);
+        mchunk = b->mchunk_fixed > 0 ? b->mchunk_fixed : march_chunk_plan(b, (long)nsm * mb * sub);
         build_march_items(b, mchunk, mitems);
         mgrid = (int)std::min<long>((long)nsm * mb, std::max<long>(1, ((long)mitems.size() + sub - 1) / sub));
     }
@@ -1244,6 +1223,7 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     a.frozen = b->d_frozen;
     a.bar_count = b->d_bar;
     a.bar_gen = b->d_bar + 1;
+    a.mcount = b->d_bar + 8;
     a.err = b->d_err;
     a.step0 = b->step;
     a.nsteps = nsteps;
@@ -1295,7 +1275,8 @@ cudaError_t launch_pair(lbm_batch *b, const BatchArgs &a0, void *mfn, void *sfn,
     if (b->nmitems > 0) {
         BatchArgs a = a0;
         a.kind_sel = 1;
-        e = launch_coop(mfn, b->mgrid, 256, a, st);
+        e = cudaMemsetAsync(a.mcount, 0, 2 * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = launch_coop(mfn, b->mgrid, 256, a, st);
     }
     if (e == cudaSuccess && (b->nitems > 0 || b->nwall > 0)) {
         BatchArgs a = a0;
@@ -1525,6 +1506,7 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     b->march = march_fns(m).march != nullptr;
     b->nmitems = b->mgrid = b->mchunk = 0;
     b->nsm = 0;
+    b->mchunk_fixed = 0;
     if (b->owns) {
         cudaError_t e = cudaMalloc(&b->base, bytes);
         if (e != cudaSuccess) {
@@ -1612,11 +1594,13 @@ lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int block
     return apply_schedule(b, warps_per_segment, blocks_per_sm, order);
 }
 
-lbm_status lbm_batch_set_march(lbm_batch *b, int on)
+lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk)
 {
     if (!b) return bfail(LBM_EINVAL, "batch is NULL");
     if (on && !march_fns(b->m).march) return bfail(LBM_EUNSUPPORTED, "no column-march kernel for this velocity set");
+    if (rows_per_chunk != 0 && rows_per_chunk < 4) return bfail(LBM_EINVAL, "rows per chunk must be 0 or >= 4");
     b->march = on != 0;
+    b->mchunk_fixed = rows_per_chunk;
     const int n = (int)b->inst.size();
     std::vector<unsigned char> kind(n);
     for (int i = 0; i < n; ++i) kind[i] = marched(b, i, b->march) ? 1 : 0;

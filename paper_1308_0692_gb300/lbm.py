@@ -102,7 +102,7 @@ def _load():
         "lbm_batch_reset": (st, [_vp]),
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
         "lbm_batch_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, _vp]),
-        "lbm_batch_set_march": (st, [_vp, ctypes.c_int]),
+        "lbm_batch_set_march": (st, [_vp, ctypes.c_int, ctypes.c_int]),
         "lbm_batch_get_march": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
@@ -457,8 +457,8 @@ def lbm_batch_get_schedule(b: Batch):
     return {"warps_per_segment": g.value, "blocks_per_sm": bp.value, "order": o.value, "grid": gr.value}
 
 
-def lbm_batch_set_march(b: Batch, on: bool):
-    _check(_load().lbm_batch_set_march(b.handle, int(bool(on))))
+def lbm_batch_set_march(b: Batch, on: bool, rows_per_chunk: int = 0):
+    _check(_load().lbm_batch_set_march(b.handle, int(bool(on)), int(rows_per_chunk)))
 
 
 def lbm_batch_get_march(b: Batch) -> dict:
