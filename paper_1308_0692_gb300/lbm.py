@@ -103,6 +103,18 @@ def _load():
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
         "lbm_batch_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, _vp]),
         "lbm_batch_set_march": (st, [_vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_hybrid_init": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
+        "lbm_hybrid_destroy": (None, [_vp]),
+        "lbm_hybrid_query": (st, [_vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_double)]),
+        "lbm_hybrid_set_state": (st, [_vp, _vp]),
+        "lbm_hybrid_get_state": (st, [_vp, _vp]),
+        "lbm_hybrid_step": (st, [_vp, ctypes.c_long]),
+        "lbm_hybrid_residual": (st, [_vp, ctypes.POINTER(ctypes.c_double)]),
+        "lbm_hybrid_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.POINTER(ctypes.c_long),
+                                  ctypes.POINTER(ctypes.c_double)]),
+        "lbm_hybrid_profile": (st, [_vp, _vp, _vp]),
         "lbm_batch_get_march": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
@@ -620,3 +632,71 @@ def mlp_unflatten(flat: np.ndarray, widths=(4, 256, 256, 256, 6)):
 
 def mlp_flatten(params) -> np.ndarray:
     return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)
+
+
+class Hybrid:
+    """Owner of an lbm_hybrid* (hybrid half-range / full-range Couette channel)."""
+
+    def __init__(self, handle: int, ny: int, keepalive=None):
+        self.handle = handle
+        self.ny = ny
+        self._keepalive = keepalive
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.lbm_hybrid_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def lbm_hybrid_init(n_half: int, ny: int, kn: float, u_bottom: float, u_top: float, layer: int,
+                    cfl: float = 0.9, stream=None) -> Hybrid:
+    out = _vp()
+    _check(_load().lbm_hybrid_init(int(n_half), int(ny), float(kn), float(u_bottom), float(u_top), int(layer),
+                                   float(cfl), _stream_handle(stream), ctypes.byref(out)))
+    return Hybrid(out.value, ny, keepalive=stream)
+
+
+def lbm_hybrid_query(hb: Hybrid) -> dict:
+    n, c, dt = ctypes.c_long(), ctypes.c_int(), ctypes.c_double()
+    _check(_load().lbm_hybrid_query(hb.handle, ctypes.byref(n), ctypes.byref(c), ctypes.byref(dt)))
+    return {"unknowns": n.value, "half_range_cells": c.value, "dt": dt.value}
+
+
+def lbm_hybrid_set_state(hb: Hybrid, h: np.ndarray):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    if h.size != lbm_hybrid_query(hb)["unknowns"]:
+        raise ValueError("state size does not match the hybrid channel")
+    _check(_load().lbm_hybrid_set_state(hb.handle, _ptr(h)))
+
+
+def lbm_hybrid_get_state(hb: Hybrid) -> np.ndarray:
+    h = np.empty(lbm_hybrid_query(hb)["unknowns"])
+    _check(_load().lbm_hybrid_get_state(hb.handle, _ptr(h)))
+    return h
+
+
+def lbm_hybrid_step(hb: Hybrid, nsteps: int):
+    _check(_load().lbm_hybrid_step(hb.handle, int(nsteps)))
+
+
+def lbm_hybrid_residual(hb: Hybrid) -> float:
+    r = ctypes.c_double()
+    _check(_load().lbm_hybrid_residual(hb.handle, ctypes.byref(r)))
+    return r.value
+
+
+def lbm_hybrid_solve(hb: Hybrid, tol: float, max_steps: int, every: int = 100) -> dict:
+    s, r = ctypes.c_long(), ctypes.c_double()
+    _check(_load().lbm_hybrid_solve(hb.handle, float(tol), int(max_steps), int(every), ctypes.byref(s),
+                                    ctypes.byref(r)))
+    return {"steps": s.value, "residual": r.value}
+
+
+def lbm_hybrid_profile(hb: Hybrid):
+    """(u_x per cell [ny], x-momentum flux through the faces [ny + 1])."""
+    ux, pxy = np.empty(hb.ny), np.empty(hb.ny + 1)
+    _check(_load().lbm_hybrid_profile(hb.handle, _ptr(ux), _ptr(pxy)))
+    return ux, pxy

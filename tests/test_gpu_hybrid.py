@@ -1,0 +1,106 @@
+"""Hybrid half-range / full-range Couette channel on the GPU (lbm_hybrid_*) against the FP64
+numpy oracle (oracle/hybrid.py): state after a number of steps from seeded random and cold
+states (FP64, 1e-12 relative), steady profiles, conservation and the error paths."""
+import numpy as np
+import pytest
+
+from oracle import hybrid as hy
+from paper_1308_0692_gb300 import lbm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # n_half, ny, kn, u_bottom, u_top, layer
+    (4, 30, 0.1, 0.01, -0.01, 6),
+    (2, 17, 1.0, 0.02, 0.005, 3),      # odd ny, plates not antisymmetric
+    (6, 20, 0.5, 0.01, -0.01, 4),      # 36 Hermite coefficients, 144 half-range velocities
+    (3, 12, 0.2, 0.0, 0.015, 0),       # all full-range
+    (3, 12, 0.2, 0.015, 0.0, 6),       # all half-range
+    (4, 9, 0.05, 0.01, -0.01, 8),      # layer > ny / 2
+    (4, 2, 0.3, 0.01, -0.01, 1),       # two cells
+    (4, 25, 10.0, 0.01, -0.01, 1),     # one half-range cell per plate
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1308_0692_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _pack(h):
+    return np.concatenate([np.asarray(v, dtype=np.float64) for v in h])
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("start", ["cold", "random"])
+def test_hybrid_steps_match_oracle(case, start):
+    n, ny, kn, ub, ut, layer = case
+    p = hy.HybridCouette(n, ny, kn, ub, ut, layer)
+    hb = lbm.lbm_hybrid_init(n, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    q = lbm.lbm_hybrid_query(hb)
+    assert q["unknowns"] == p.unknowns()
+    assert q["half_range_cells"] == sum(p.half)
+    assert q["dt"] == pytest.approx(p.dt, rel=1e-15)
+    if start == "random":
+        rng = np.random.default_rng(ny * 100 + layer)
+        h0 = [rng.standard_normal(p.vset(j).n) * 1e-2 for j in range(ny)]
+        lbm.lbm_hybrid_set_state(hb, _pack(h0))
+    else:
+        h0 = p.zeros()
+    steps = 37
+    lbm.lbm_hybrid_step(hb, 20)
+    lbm.lbm_hybrid_step(hb, steps - 20)
+    got = lbm.lbm_hybrid_get_state(hb)
+    want = _pack(p.step(h0, steps))
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # the residual of the last step, and the profile of the state reached
+    prev = _pack(p.step(h0, steps - 1))
+    r = lbm.lbm_hybrid_residual(hb)
+    r_want = np.linalg.norm(want - prev) / np.linalg.norm(want)
+    assert r == pytest.approx(r_want, rel=1e-9)
+    ux, pxy = lbm.lbm_hybrid_profile(hb)
+    hw = p.step(h0, steps)
+    np.testing.assert_allclose(ux, p.ux(hw), rtol=0, atol=1e-13 * max(np.abs(p.ux(hw)).max(), 1e-300))
+    fw = p.face_flux(hw)
+    np.testing.assert_allclose(pxy, fw, rtol=0, atol=1e-12 * max(np.abs(fw).max(), 1e-300))
+    hb.close()
+
+
+def test_hybrid_steady_state_matches_oracle_and_conserves():
+    n, ny, kn, ub, ut, layer = 4, 30, 0.3, 0.01, -0.01, 6
+    p = hy.HybridCouette(n, ny, kn, ub, ut, layer)
+    href, _, r = p.march(p.zeros(), 200000, 100, 1e-12)
+    assert r < 1e-12
+    hb = lbm.lbm_hybrid_init(n, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    info = lbm.lbm_hybrid_solve(hb, 1e-12, 200000, 100)
+    assert info["residual"] < 1e-12
+    ux, pxy = lbm.lbm_hybrid_profile(hb)
+    assert np.abs(ux - p.ux(href)).max() / 0.01 < 1e-9
+    fr = p.face_flux(href)
+    assert np.abs(pxy - fr).max() / np.abs(fr).max() < 1e-9
+    assert (pxy.max() - pxy.min()) <= 1e-8 * np.abs(pxy).max()      # constant through every face
+    # mass conservation from a random state
+    rng = np.random.default_rng(5)
+    h0 = [rng.standard_normal(p.vset(j).n) * 1e-2 for j in range(ny)]
+    lbm.lbm_hybrid_set_state(hb, _pack(h0))
+    lbm.lbm_hybrid_step(hb, 200)
+    assert abs(lbm.lbm_hybrid_get_state(hb).sum() - _pack(h0).sum()) < 1e-14
+    hb.close()
+
+
+def test_hybrid_rejects_invalid_arguments():
+    for args in [(1, 10, 0.1, 0.0, 0.01, 2), (7, 10, 0.1, 0.0, 0.01, 2), (4, 1, 0.1, 0.0, 0.01, 0),
+                 (4, 10, 0.0, 0.0, 0.01, 2), (4, 10, 0.1, 0.0, 0.01, -1)]:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_hybrid_init(*args)
+        assert e.value.status == lbm.LBM_EINVAL
+    hb = lbm.lbm_hybrid_init(4, 10, 0.1, 0.0, 0.01, 2)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_hybrid_residual(hb)           # no step taken yet
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(ValueError):
+        lbm.lbm_hybrid_set_state(hb, np.zeros(3))
+    hb.close()
