@@ -3,7 +3,7 @@ library's FP64 march: the Couette Kn sweep (Figs. 1-2), the Couette profile and 
 stress at Kn = 1 (Fig. 3 and the statement on the number of full-range nodes), and the
 driven cavity's centre-line profile, lid drag D and vortex flow rate G (Fig. 4, Table 2).
 
-    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2} --out r.json
+    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2,order,hybrid} --out r.json
 
 Couette flow between plates at -u_w and +u_w: for each Knudsen number and velocity set the
 steady state is marched on the GPU to a residual tolerance, and the shear stress (the
@@ -208,11 +208,53 @@ def order_study(kns=(0.01, 0.1, 1.0), nys=(50, 100, 200, 400), n_half=4):
     return out
 
 
+# ---------------------------------------------------------------- hybrid coupling (conclusion)
+
+def hybrid_study(kns=(0.1, 1.0, 10.0), ny=200, n_half=4, layers=(0, 5, 10, 20, 40), u_w=0.01, tol=1e-11):
+    """The hybrid channel (lbm_hybrid_*: D2Q^h_{(2N)^2} within `layer` cells of each plate,
+    the full-range D2Q_{N^2} between) against the pure half-range march (layer = ny/2) and
+    the 144-velocity half-range reference: p_xy / p_fm, wall slip, unknowns, steps and GPU
+    seconds for each Kn and layer depth."""
+    import time
+
+    import torch
+    stream = torch.cuda.Stream()
+    p_fm = -math.sqrt(2.0 / math.pi) * u_w
+    out = {"ny": ny, "n_half": n_half, "runs": []}
+    for kn in kns:
+        ref144 = couette_shear(lbm.LBM_HALF_RANGE_GH, 6, kn, ny=ny, u_w=u_w, tol=tol, stream=stream)
+        rows = []
+        for layer in list(layers) + [ny // 2]:
+            hb = lbm.lbm_hybrid_init(n_half, ny, kn, -u_w, u_w, layer, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = lbm.lbm_hybrid_solve(hb, tol, 5_000_000, 100)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            ux, pxy = lbm.lbm_hybrid_profile(hb)
+            q = lbm.lbm_hybrid_query(hb)
+            rows.append({"layer": layer, "unknowns": q["unknowns"], "steps": info["steps"],
+                         "residual": info["residual"], "seconds": el,
+                         "pxy_over_pfm": float(pxy.mean() / p_fm), "pxy_face_spread": float((pxy.max() - pxy.min()) / abs(pxy).max()),
+                         "slip": float(1.0 - ux[-1] / u_w), "ux": ux.tolist()})
+            hb.close()
+        half = rows[-1]
+        for r in rows:
+            r["rel_err_pxy_vs_half_range"] = abs(r["pxy_over_pfm"] - half["pxy_over_pfm"]) / abs(half["pxy_over_pfm"])
+            r["max_du_vs_half_range"] = float(np.abs(np.array(r["ux"]) - np.array(half["ux"])).max() / u_w)
+            r["rel_err_pxy_vs_d2qh144"] = abs(r["pxy_over_pfm"] - ref144["pxy_over_pfm"]) / abs(ref144["pxy_over_pfm"])
+            del r["ux"]
+        out["runs"].append({"kn": kn, "d2qh144": ref144, "layers": rows})
+    out["summary"] = [[run["kn"], [(r["layer"], r["unknowns"], round(r["rel_err_pxy_vs_half_range"], 5),
+                                    round(r["max_du_vs_half_range"], 5)) for r in run["layers"]]] for run in out["runs"]]
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order"])
+    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order", "hybrid"])
     ap.add_argument("--out", required=True)
     ap.add_argument("--side", type=int, default=128)
     args = ap.parse_args(argv)
@@ -222,6 +264,8 @@ def main(argv=None):
         r = couette_kn1_study()
     elif args.study == "order":
         r = order_study()
+    elif args.study == "hybrid":
+        r = hybrid_study()
     else:
         r = cavity_table2_study(side=args.side)
     with open(args.out, "w") as f:
