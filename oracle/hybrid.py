@@ -22,10 +22,13 @@ is this project's reading of that proposal for the Couette channel (the scheme o
   * the flux through an interface face is the half-range one: both half-space fluxes are
     summed in H, the full-range side taken as its projection onto H.  The half-range cell
     sees exactly that exchange; the full-range cell's transported state gets the correction
-    (lam + mu xi_x) w_b with which its mass and x-momentum exchange through that face
-    equals the half-range one (its own quadrature's half-space integrals are the
+    (lam + mu_x xi_x + mu_y xi_y) w_b with which its mass and momentum exchange through that
+    face equals the half-range one (its own quadrature's half-space integrals are the
     inaccurate ones: sum over xi_y > 0 of xi_y w is 0.444 for N = 4 against 1/sqrt(2 pi)).
-    Mass and x-momentum cross the interface exactly, and a state at rest stays at rest.
+    Mass and momentum cross the interface exactly, and a state at rest stays at rest.
+  * `HybridCavity` is the same coupling in the lid-driven cavity: half-range cells within
+    L cells of any wall, unsplit upwind transport in x and y, the correction on every
+    interface face (x or y).
 
 Pins (tests): L >= ny/2 reduces to the half-range march and L = 0 to the full-range march
 of the C oracle; the projection is exact on F data and on polynomials of degree <= N - 1
@@ -140,37 +143,28 @@ class HybridCouette:
             return h[k]
         return project(h[k], sk, sj, self.order)
 
+    @staticmethod
+    def _face_moments(s: VelocitySet, v: np.ndarray, upward: bool):
+        """(mass, x-momentum, y-momentum) flux sum |xi_y| (1, xi_x, xi_y) v over the velocities
+        of s moving up (upward) or down."""
+        m = (s.xi_y > 0) if upward else (s.xi_y < 0)
+        t = np.where(m, np.abs(s.xi_y) * v, 0.0)
+        return np.array([np.sum(t), np.sum(t * s.xi_x), np.sum(t * s.xi_y)])
+
     def half_fluxes_h(self, h: list, k: int):
         """Face k (between cells k - 1 and k, 1 <= k <= ny - 1) evaluated in the half-range
-        set: (mass, x-momentum) carried upward and downward, sum |xi_y| phi h over the
-        velocities crossing, each side's distribution in H (projected when full-range)."""
+        set: the (mass, x-momentum, y-momentum) fluxes carried upward and downward, each
+        side's distribution in H (projected when full-range)."""
         H = self.H
         lo = h[k - 1] if self.half[k - 1] else project(h[k - 1], self.F, H, self.order)
         hi = h[k] if self.half[k] else project(h[k], self.F, H, self.order)
-        ay = np.abs(H.xi_y)
-        up = (np.sum(np.where(H.xi_y > 0, ay * lo, 0.0)), np.sum(np.where(H.xi_y > 0, ay * H.xi_x * lo, 0.0)))
-        dn = (np.sum(np.where(H.xi_y < 0, ay * hi, 0.0)), np.sum(np.where(H.xi_y < 0, ay * H.xi_x * hi, 0.0)))
-        return up, dn
-
-    def half_fluxes_own(self, h: list, k: int, cell: int):
-        """Face k seen by the transport of `cell` (k - 1 or k) in its own set: the (mass,
-        x-momentum) half-space fluxes it receives and sends through that face."""
-        s = self.vset(cell)
-        ay = np.abs(s.xi_y)
-        if cell == k:     # the upper cell: receives the upward velocities from below
-            recv = self.upwind_from(h, cell, k - 1)
-            rmask, smask = s.xi_y > 0, s.xi_y < 0
-        else:             # the lower cell: receives the downward velocities from above
-            recv = self.upwind_from(h, cell, k)
-            rmask, smask = s.xi_y < 0, s.xi_y > 0
-        got = (np.sum(np.where(rmask, ay * recv, 0.0)), np.sum(np.where(rmask, ay * s.xi_x * recv, 0.0)))
-        sent = (np.sum(np.where(smask, ay * h[cell], 0.0)), np.sum(np.where(smask, ay * s.xi_x * h[cell], 0.0)))
-        return got, sent
+        return self._face_moments(H, lo, True), self._face_moments(H, hi, False)
 
     def interface_correction(self, h: list, j: int) -> np.ndarray:
         """Correction added to the transported state of full-range cell j next to half-range
-        cells: (lam + mu xi_x) w with which its net (mass, x-momentum) exchange through each
-        interface face equals the half-range evaluation of that face."""
+        cells: (lam + mu_x xi_x + mu_y xi_y) w with which its net mass and momentum exchange
+        through each interface face equals the half-range evaluation of that face
+        (sum w = sum xi_x^2 w = sum xi_y^2 w = 1, cross sums 0, for the full-range rule)."""
         s = self.vset(j)
         corr = np.zeros(s.n)
         if self.half[j]:
@@ -179,13 +173,15 @@ class HybridCouette:
             if other < 0 or other >= self.ny or not self.half[other]:
                 continue
             up, dn = self.half_fluxes_h(h, k)
-            got, sent = self.half_fluxes_own(h, k, j)
-            # net gain of cell j through face k: half-range evaluation minus its own
-            want = [u - d for u, d in zip(up, dn)] if k == j else [d - u for u, d in zip(up, dn)]
-            have = [g - t for g, t in zip(got, sent)]
-            fac = self.dt / self.dy
-            # sum_b w_b = 1 and sum_b xi_x,b^2 w_b = 1 for the full-range rule
-            corr += fac * ((want[0] - have[0]) + (want[1] - have[1]) * s.xi_x) * s.w
+            recv = self.upwind_from(h, j, other)
+            if k == j:    # j is above the face: receives the upward velocities, sends the downward
+                want = up - dn
+                have = self._face_moments(s, recv, True) - self._face_moments(s, h[j], False)
+            else:         # j is below the face
+                want = dn - up
+                have = self._face_moments(s, recv, False) - self._face_moments(s, h[j], True)
+            d = want - have
+            corr += self.dt / self.dy * (d[0] + d[1] * s.xi_x + d[2] * s.xi_y) * s.w
         return corr
 
     def step(self, h: list, nsteps: int = 1) -> list:
@@ -271,3 +267,138 @@ class HybridCouette:
                 down = np.sum(np.where(s.xi_y < 0, s.xi_x * s.xi_y * h[k], 0.0))
             out[k] = self.u_ref * (up + down)
         return out
+
+
+class HybridCavity:
+    """Lid-driven cavity (nx x ny cells, walls on all four faces, the bottom moving at
+    u_bottom and the top at u_top, the sides at rest) with half-range cells within `layer`
+    cells of any wall and full-range cells inside.  Unsplit first-order upwind transport in x
+    and y on each cell's own set; at an interface face (x or y) the upwind values are the
+    projection of the neighbour, the face flux is the half-range evaluation, and the
+    full-range cell's transported state gets (lam + mu_x xi_x + mu_y xi_y) w so that its
+    mass and momentum exchange through the face equals it (sum w = sum xi_x^2 w =
+    sum xi_y^2 w = 1, the cross sums 0, for the full-range rule)."""
+
+    def __init__(self, n_half: int, nx: int, ny: int, kn: float, u_bottom: float, u_top: float, layer: int,
+                 cfl: float = 0.9):
+        if nx < 2 or ny < 2 or layer < 0 or not (kn > 0) or n_half < 1:
+            raise ValueError("invalid hybrid problem")
+        self.order = n_half - 1
+        self.H = VelocitySet("half", n_half, self.order)
+        self.F = VelocitySet("full", n_half, self.order)
+        for s in (self.H, self.F):
+            s.d_x = float(np.sum(np.where(s.xi_x > 0, s.xi_x * s.w, 0.0)))
+        self.nx, self.ny, self.kn, self.layer = nx, ny, kn, layer
+        self.u_bottom, self.u_top = u_bottom, u_top
+        self.half = [min(x, nx - 1 - x, y, ny - 1 - y) < layer for y in range(ny) for x in range(nx)]
+        present = [s for s, used in ((self.H, any(self.half)), (self.F, not all(self.half))) if used]
+        self.dx, self.dy = 1.0 / nx, 1.0 / ny
+        mx = max(float(np.max(np.abs(s.xi_x))) for s in present)
+        my = max(float(np.max(np.abs(s.xi_y))) for s in present)
+        self.dt = cfl / (mx / self.dx + my / self.dy)
+        if math.isfinite(kn) and self.dt > kn:
+            self.dt = kn
+        self.omega = self.dt / kn if math.isfinite(kn) else 0.0
+        ur = max(abs(u_bottom), abs(u_top))
+        self.u_ref = ur if ur > 0 else 1.0
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny
+
+    def vset(self, c: int) -> VelocitySet:
+        return self.H if self.half[c] else self.F
+
+    def zeros(self) -> list:
+        return [np.zeros(self.vset(c).n) for c in range(self.ncells)]
+
+    def unknowns(self) -> int:
+        return sum(self.vset(c).n for c in range(self.ncells))
+
+    def mass(self, h: list) -> float:
+        return float(sum(np.sum(v) for v in h))
+
+    def _ghost(self, s: VelocitySet, h: np.ndarray, face: str) -> np.ndarray:
+        """Eq. 8 ghost for the velocities leaving wall `face` (rho_w by Eq. 9 over the cell's
+        own set, normal into the gas)."""
+        if face in ("bottom", "top"):
+            xn = s.xi_y if face == "bottom" else -s.xi_y
+            d, xt, u = s.d_y, s.xi_x, (self.u_bottom if face == "bottom" else self.u_top)
+        else:
+            xn = s.xi_x if face == "left" else -s.xi_x
+            d, xt, u = s.d_x, s.xi_y, 0.0
+        rho_w = float(np.sum(np.where(xn < 0, -xn * h, 0.0))) / d
+        return s.w * (rho_w * (1.0 + xt * u) + xt * u / self.u_ref)
+
+    def seen(self, h: list, c: int, k: int) -> np.ndarray:
+        """Cell k's values in cell c's set."""
+        sc, sk = self.vset(c), self.vset(k)
+        return h[k] if sc is sk else project(h[k], sk, sc, self.order)
+
+    def _face_moments(self, s: VelocitySet, v: np.ndarray, axis: int, positive: bool):
+        """(mass, x-momentum, y-momentum) flux sum |xi_d| (1, xi_x, xi_y) v over the velocities
+        of s moving along +axis (positive) or -axis."""
+        xd = s.xi_x if axis == 0 else s.xi_y
+        m = (xd > 0) if positive else (xd < 0)
+        t = np.where(m, np.abs(xd) * v, 0.0)
+        return np.array([np.sum(t), np.sum(t * s.xi_x), np.sum(t * s.xi_y)])
+
+    def correction(self, h: list, c: int, recv: dict) -> np.ndarray:
+        """Correction of full-range cell c for its interface faces; recv[(axis, side)] are the
+        values it received through that face (its own set)."""
+        s = self.vset(c)
+        corr = np.zeros(s.n)
+        if self.half[c]:
+            return corr
+        x, y = c % self.nx, c // self.nx
+        for axis, side, k in ((0, -1, c - 1 if x > 0 else -1), (0, 1, c + 1 if x < self.nx - 1 else -1),
+                              (1, -1, c - self.nx if y > 0 else -1), (1, 1, c + self.nx if y < self.ny - 1 else -1)):
+            if k < 0 or not self.half[k]:
+                continue
+            H = self.H
+            mine_h = project(h[c], s, H, self.order)
+            lo, hi = (h[k], mine_h) if side < 0 else (mine_h, h[k])
+            up = self._face_moments(H, lo, axis, True)     # along +axis, from the lower-side cell
+            dn = self._face_moments(H, hi, axis, False)    # along -axis, from the upper-side cell
+            want = up - dn if side < 0 else dn - up
+            got = self._face_moments(s, recv[(axis, side)], axis, side < 0)
+            sent = self._face_moments(s, h[c], axis, side > 0)
+            diff = want - (got - sent)
+            fac = self.dt / (self.dx if axis == 0 else self.dy)
+            corr += fac * (diff[0] + diff[1] * s.xi_x + diff[2] * s.xi_y) * s.w
+        return corr
+
+    def step(self, h: list, nsteps: int = 1) -> list:
+        cur = [np.array(v, dtype=np.float64) for v in h]
+        nx, ny = self.nx, self.ny
+        for _ in range(nsteps):
+            nxt = []
+            for c in range(self.ncells):
+                s = self.vset(c)
+                hc = cur[c]
+                x, y = c % nx, c // nx
+                left = self.seen(cur, c, c - 1) if x > 0 else self._ghost(s, hc, "left")
+                right = self.seen(cur, c, c + 1) if x < nx - 1 else self._ghost(s, hc, "right")
+                below = self.seen(cur, c, c - nx) if y > 0 else self._ghost(s, hc, "bottom")
+                above = self.seen(cur, c, c + nx) if y < ny - 1 else self._ghost(s, hc, "top")
+                hx = np.where(s.xi_x > 0, left, np.where(s.xi_x < 0, right, hc))
+                hy = np.where(s.xi_y > 0, below, np.where(s.xi_y < 0, above, hc))
+                nux = np.abs(s.xi_x) * self.dt / self.dx
+                nuy = np.abs(s.xi_y) * self.dt / self.dy
+                recv = {(0, -1): left, (0, 1): right, (1, -1): below, (1, 1): above}
+                hs = hc - nux * (hc - hx) - nuy * (hc - hy) + self.correction(cur, c, recv)
+                rho, jx, jy = np.sum(hs), np.sum(s.xi_x * hs), np.sum(s.xi_y * hs)
+                heq = s.w * (rho + s.xi_x * jx + s.xi_y * jy)
+                nxt.append(hs - self.omega * (hs - heq))
+            cur = nxt
+        return cur
+
+    def velocity(self, h: list):
+        """(u_x, u_y) per cell [ny][nx] from each cell's own set."""
+        ux, uy = np.empty(self.ncells), np.empty(self.ncells)
+        for c in range(self.ncells):
+            s = self.vset(c)
+            rho = 1.0 + self.u_ref * np.sum(h[c])
+            ux[c] = self.u_ref * np.sum(s.xi_x * h[c]) / rho
+            uy[c] = self.u_ref * np.sum(s.xi_y * h[c]) / rho
+        return ux.reshape(self.ny, self.nx), uy.reshape(self.ny, self.nx)

@@ -1,7 +1,8 @@
-"""Pins of the hybrid half-range / full-range Couette oracle (oracle/hybrid.py): reductions
-to the C oracle's pure half-range and pure full-range marches, exactness of the Hermite
-projection, conservation, the state at rest, the Couette antisymmetry and the constancy of
-the face momentum flux at the steady state."""
+"""Pins of the hybrid half-range / full-range oracle (oracle/hybrid.py), Couette channel and
+lid-driven cavity: reductions to the C oracle's pure half-range and pure full-range
+marches, exactness of the Hermite projection, conservation, the state at rest, the Couette
+antisymmetry and the constancy of the face momentum flux at the steady state, the
+cavity's mirror symmetry at a small lid speed."""
 import math
 
 import numpy as np
@@ -109,3 +110,38 @@ def test_interfaces_move_the_result_between_the_two_models():
     e = [abs(pxy(L) - half) for L in (2, 6)]
     assert e[1] < e[0] < abs(full - half)
     assert math.copysign(1, pxy(6) - half) == math.copysign(1, full - half)
+
+
+@pytest.mark.parametrize("layer,kind", [(4, "half"), (0, "full")])
+def test_cavity_reduces_to_pure_marches(layer, kind):
+    """All cells half-range (layer beyond the half width) or all full-range: the C oracle's
+    cavity march on that set."""
+    p = hy.HybridCavity(3, 7, 6, 0.2, 0.0, 0.01, layer)
+    got = np.array(p.step(p.zeros(), 12)).T
+    from oracle.march import CAVITY
+    ref = make_problem(kind, 3, CAVITY, 7, 6, 0.2, 0.0, 0.01)
+    want = ref.step(ref.zeros(), 12)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_cavity_mass_conserved_and_rest_state_kept():
+    p = hy.HybridCavity(3, 9, 8, 0.2, 0.003, 0.01, 2)
+    rng = np.random.default_rng(2)
+    h = [rng.standard_normal(p.vset(c).n) * 1e-2 for c in range(p.ncells)]
+    assert abs(p.mass(p.step(h, 15)) - p.mass(h)) < 1e-14
+    r = hy.HybridCavity(3, 9, 8, 0.2, 0.0, 0.0, 2)
+    h = [0.2 * r.vset(c).w for c in range(r.ncells)]
+    for a, b in zip(r.step(h, 6), h):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-16)
+
+
+def test_cavity_mirror_symmetry_at_small_lid_speed():
+    """u_x(1 - x, y) = u_x(x, y) and u_y(1 - x, y) = -u_y(x, y), broken only at O(u_w) by the
+    wall product rho_w u_w (Eq. 8): checked at u_w = 1e-8 with half-range layers placed
+    symmetrically."""
+    p = hy.HybridCavity(3, 10, 9, 0.3, 0.0, 1e-8, 3)
+    ux, uy = p.velocity(p.step(p.zeros(), 30))
+    scale = max(np.abs(ux).max(), np.abs(uy).max())
+    np.testing.assert_allclose(ux, ux[:, ::-1], rtol=0, atol=1e-6 * scale)
+    np.testing.assert_allclose(uy, -uy[:, ::-1], rtol=0, atol=1e-6 * scale)
+    assert scale > 0
