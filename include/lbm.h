@@ -344,29 +344,33 @@ typedef struct {
 lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double refine_tol, long max_steps,
                             lbm_batch_refine_info *info);
 
-/* ---- Hybrid half-range / full-range Couette channel (not in the paper's algorithms) ----
+/* ---- Hybrid half-range / full-range coupling (not in the paper's algorithms) ----
  * The coupling the paper's conclusion proposes (half-range sets accurate in the Knudsen
  * layers, the full-range set with 2^d times fewer velocities they reduce to in the bulk),
- * in this project's reading, for the Couette channel of Eqs. 1, 5-9 (one periodic column
- * of ny cells, plates u_bottom at y = 0 and u_top at y = 1): cells j < layer and
- * j >= ny - layer carry D2Q^h_{(2N)^2}, the others the full-range Gauss-Hermite set of N
- * nodes per axis (D2Q_{N^2}).  Across an interface the upwind values are the tensor Hermite
- * projection (order N - 1) of the neighbour's distribution; the flux through an interface
- * face is the half-range one (both half-spaces summed in the half-range set), and the
- * full-range cell's transported state is corrected by (lam + mu xi_x) w so that its mass
- * and x-momentum exchange equals it: mass and x-momentum are conserved exactly, a state
- * at rest stays at rest.  layer = 0 is the full-range march, layer >= ny/2 the half-range
- * march.  dt = cfl dy / max |xi_y| over the sets present, dt <= Kn.  FP64 throughout.
- * State layout (host FP64, packed): cell after cell, each cell's values in its own set's
- * order a = iy * M + ix (M = 2N half-range, N full-range); lbm_hybrid_query reports the
- * total.  2 <= N <= 6.  lbm_hybrid_step is stream-ordered; lbm_hybrid_residual returns
- * ||h^{n+1} - h^n|| / ||h^{n+1}|| of the last step taken (synchronises);
- * lbm_hybrid_solve marches in blocks of `every` steps until that residual is below tol or
- * max_steps; lbm_hybrid_profile writes u_x per cell (host [ny]) and the x-momentum flux
- * through the ny + 1 faces (host [ny + 1], interface faces in the half-range evaluation). */
+ * in this project's reading, for the Couette channel (geom LBM_COUETTE, one periodic
+ * column, nx = 1, plates u_bottom at y = 0 and u_top at y = 1) and the lid-driven cavity
+ * (LBM_CAVITY, nx x ny, bottom u_bottom, lid u_top, sides at rest) of Eqs. 1, 5-9: cells
+ * within `layer` cells of a wall carry D2Q^h_{(2N)^2}, the others the full-range
+ * Gauss-Hermite set of N nodes per axis (D2Q_{N^2}).  Across an interface the upwind
+ * values are the tensor Hermite projection (order N - 1) of the neighbour's distribution;
+ * the flux through an interface face is the half-range one (both half-spaces summed in the
+ * half-range set), and the full-range cell's transported state is corrected by
+ * (lam + mu_x xi_x + mu_y xi_y) w so that its mass and momentum exchange through that face
+ * equals it: mass and momentum are conserved exactly, a state at rest stays at rest.
+ * layer = 0 is the full-range march, a layer beyond the half width the half-range march.
+ * dt = cfl / (max|xi_x|/dx + max|xi_y|/dy) over the sets present (the x term dropped for the
+ * column), dt <= Kn.  FP64 throughout.  State layout (host FP64, packed): cell after cell
+ * (c = y * nx + x), each cell's values in its own set's order a = iy * M + ix (M = 2N
+ * half-range, N full-range); lbm_hybrid_query reports the total.  2 <= N <= 6.
+ * lbm_hybrid_step is stream-ordered; lbm_hybrid_residual returns ||h^{n+1} - h^n|| /
+ * ||h^{n+1}|| of the last step taken (synchronises); lbm_hybrid_solve marches in blocks of
+ * `every` steps until that residual is below tol or max_steps; lbm_hybrid_velocity writes
+ * (u_x, u_y) per cell (host [ny][nx]); lbm_hybrid_face_flux (column only) the x-momentum
+ * flux through the ny + 1 faces (host [ny + 1], interface faces in the half-range
+ * evaluation; LBM_EUNSUPPORTED for the cavity). */
 typedef struct lbm_hybrid lbm_hybrid;
-lbm_status lbm_hybrid_init(int n_half, int ny, double kn, double u_bottom, double u_top, int layer, double cfl,
-                           void *stream, lbm_hybrid **out);
+lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, double u_bottom, double u_top, int layer,
+                           double cfl, void *stream, lbm_hybrid **out);
 void lbm_hybrid_destroy(lbm_hybrid *hb);
 lbm_status lbm_hybrid_query(const lbm_hybrid *hb, long *unknowns, int *half_range_cells, double *dt);
 lbm_status lbm_hybrid_set_state(lbm_hybrid *hb, const double *h);
@@ -374,7 +378,8 @@ lbm_status lbm_hybrid_get_state(lbm_hybrid *hb, double *h);
 lbm_status lbm_hybrid_step(lbm_hybrid *hb, long nsteps);
 lbm_status lbm_hybrid_residual(lbm_hybrid *hb, double *r);
 lbm_status lbm_hybrid_solve(lbm_hybrid *hb, double tol, long max_steps, int every, long *steps, double *r);
-lbm_status lbm_hybrid_profile(lbm_hybrid *hb, double *ux, double *pxy);
+lbm_status lbm_hybrid_velocity(lbm_hybrid *hb, double *ux, double *uy);
+lbm_status lbm_hybrid_face_flux(lbm_hybrid *hb, double *pxy);
 
 /* ---- Learned warm start (not in the paper) ----
  * A coordinate MLP 4 -> 256 -> 256 -> 256 -> 6 with exact-erf GELU maps the features

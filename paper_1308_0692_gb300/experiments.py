@@ -225,13 +225,14 @@ def hybrid_study(kns=(0.1, 1.0, 10.0), ny=200, n_half=4, layers=(0, 5, 10, 20, 4
         ref144 = couette_shear(lbm.LBM_HALF_RANGE_GH, 6, kn, ny=ny, u_w=u_w, tol=tol, stream=stream)
         rows = []
         for layer in list(layers) + [ny // 2]:
-            hb = lbm.lbm_hybrid_init(n_half, ny, kn, -u_w, u_w, layer, stream=stream)
+            hb = lbm.lbm_hybrid_init(lbm.LBM_COUETTE, n_half, 1, ny, kn, -u_w, u_w, layer, stream=stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             info = lbm.lbm_hybrid_solve(hb, tol, 5_000_000, 100)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            ux, pxy = lbm.lbm_hybrid_profile(hb)
+            ux = lbm.lbm_hybrid_velocity(hb)[0][:, 0]
+            pxy = lbm.lbm_hybrid_face_flux(hb)
             q = lbm.lbm_hybrid_query(hb)
             rows.append({"layer": layer, "unknowns": q["unknowns"], "steps": info["steps"],
                          "residual": info["residual"], "seconds": el,

@@ -103,8 +103,9 @@ def _load():
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
         "lbm_batch_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, _vp]),
         "lbm_batch_set_march": (st, [_vp, ctypes.c_int, ctypes.c_int]),
-        "lbm_hybrid_init": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                 ctypes.c_int, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
+        "lbm_hybrid_init": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, _vp,
+                                 ctypes.POINTER(_vp)]),
         "lbm_hybrid_destroy": (None, [_vp]),
         "lbm_hybrid_query": (st, [_vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_double)]),
@@ -114,7 +115,8 @@ def _load():
         "lbm_hybrid_residual": (st, [_vp, ctypes.POINTER(ctypes.c_double)]),
         "lbm_hybrid_solve": (st, [_vp, ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.POINTER(ctypes.c_long),
                                   ctypes.POINTER(ctypes.c_double)]),
-        "lbm_hybrid_profile": (st, [_vp, _vp, _vp]),
+        "lbm_hybrid_velocity": (st, [_vp, _vp, _vp]),
+        "lbm_hybrid_face_flux": (st, [_vp, _vp]),
         "lbm_batch_get_march": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
@@ -635,11 +637,11 @@ def mlp_flatten(params) -> np.ndarray:
 
 
 class Hybrid:
-    """Owner of an lbm_hybrid* (hybrid half-range / full-range Couette channel)."""
+    """Owner of an lbm_hybrid* (hybrid half-range / full-range Couette column or cavity)."""
 
-    def __init__(self, handle: int, ny: int, keepalive=None):
+    def __init__(self, handle: int, nx: int, ny: int, keepalive=None):
         self.handle = handle
-        self.ny = ny
+        self.nx, self.ny = nx, ny
         self._keepalive = keepalive
 
     def close(self):
@@ -651,12 +653,12 @@ class Hybrid:
         self.close()
 
 
-def lbm_hybrid_init(n_half: int, ny: int, kn: float, u_bottom: float, u_top: float, layer: int,
-                    cfl: float = 0.9, stream=None) -> Hybrid:
+def lbm_hybrid_init(geom: int, n_half: int, nx: int, ny: int, kn: float, u_bottom: float, u_top: float,
+                    layer: int, cfl: float = 0.9, stream=None) -> Hybrid:
     out = _vp()
-    _check(_load().lbm_hybrid_init(int(n_half), int(ny), float(kn), float(u_bottom), float(u_top), int(layer),
-                                   float(cfl), _stream_handle(stream), ctypes.byref(out)))
-    return Hybrid(out.value, ny, keepalive=stream)
+    _check(_load().lbm_hybrid_init(int(geom), int(n_half), int(nx), int(ny), float(kn), float(u_bottom),
+                                   float(u_top), int(layer), float(cfl), _stream_handle(stream), ctypes.byref(out)))
+    return Hybrid(out.value, nx, ny, keepalive=stream)
 
 
 def lbm_hybrid_query(hb: Hybrid) -> dict:
@@ -668,7 +670,7 @@ def lbm_hybrid_query(hb: Hybrid) -> dict:
 def lbm_hybrid_set_state(hb: Hybrid, h: np.ndarray):
     h = np.ascontiguousarray(h, dtype=np.float64)
     if h.size != lbm_hybrid_query(hb)["unknowns"]:
-        raise ValueError("state size does not match the hybrid channel")
+        raise ValueError("state size does not match the hybrid grid")
     _check(_load().lbm_hybrid_set_state(hb.handle, _ptr(h)))
 
 
@@ -695,8 +697,15 @@ def lbm_hybrid_solve(hb: Hybrid, tol: float, max_steps: int, every: int = 100) -
     return {"steps": s.value, "residual": r.value}
 
 
-def lbm_hybrid_profile(hb: Hybrid):
-    """(u_x per cell [ny], x-momentum flux through the faces [ny + 1])."""
-    ux, pxy = np.empty(hb.ny), np.empty(hb.ny + 1)
-    _check(_load().lbm_hybrid_profile(hb.handle, _ptr(ux), _ptr(pxy)))
-    return ux, pxy
+def lbm_hybrid_velocity(hb: Hybrid):
+    """(u_x, u_y) per cell, each [ny][nx]."""
+    ux, uy = np.empty(hb.nx * hb.ny), np.empty(hb.nx * hb.ny)
+    _check(_load().lbm_hybrid_velocity(hb.handle, _ptr(ux), _ptr(uy)))
+    return ux.reshape(hb.ny, hb.nx), uy.reshape(hb.ny, hb.nx)
+
+
+def lbm_hybrid_face_flux(hb: Hybrid) -> np.ndarray:
+    """Couette column: x-momentum flux through the ny + 1 faces."""
+    pxy = np.empty(hb.ny + 1)
+    _check(_load().lbm_hybrid_face_flux(hb.handle, _ptr(pxy)))
+    return pxy

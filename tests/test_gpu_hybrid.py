@@ -1,6 +1,7 @@
-"""Hybrid half-range / full-range Couette channel on the GPU (lbm_hybrid_*) against the FP64
-numpy oracle (oracle/hybrid.py): state after a number of steps from seeded random and cold
-states (FP64, 1e-12 relative), steady profiles, conservation and the error paths."""
+"""Hybrid half-range / full-range coupling on the GPU (lbm_hybrid_*), Couette column and
+lid-driven cavity, against the FP64 numpy oracle (oracle/hybrid.py): state after a number
+of steps from seeded random and cold states (FP64, 1e-12 relative), steady profiles,
+conservation and the error paths."""
 import numpy as np
 import pytest
 
@@ -39,7 +40,7 @@ def _pack(h):
 def test_hybrid_steps_match_oracle(case, start):
     n, ny, kn, ub, ut, layer = case
     p = hy.HybridCouette(n, ny, kn, ub, ut, layer)
-    hb = lbm.lbm_hybrid_init(n, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    hb = lbm.lbm_hybrid_init(lbm.LBM_COUETTE, n, 1, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
     q = lbm.lbm_hybrid_query(hb)
     assert q["unknowns"] == p.unknowns()
     assert q["half_range_cells"] == sum(p.half)
@@ -61,7 +62,8 @@ def test_hybrid_steps_match_oracle(case, start):
     r = lbm.lbm_hybrid_residual(hb)
     r_want = np.linalg.norm(want - prev) / np.linalg.norm(want)
     assert r == pytest.approx(r_want, rel=1e-9)
-    ux, pxy = lbm.lbm_hybrid_profile(hb)
+    ux = lbm.lbm_hybrid_velocity(hb)[0][:, 0]
+    pxy = lbm.lbm_hybrid_face_flux(hb)
     hw = p.step(h0, steps)
     np.testing.assert_allclose(ux, p.ux(hw), rtol=0, atol=1e-13 * max(np.abs(p.ux(hw)).max(), 1e-300))
     fw = p.face_flux(hw)
@@ -74,10 +76,11 @@ def test_hybrid_steady_state_matches_oracle_and_conserves():
     p = hy.HybridCouette(n, ny, kn, ub, ut, layer)
     href, _, r = p.march(p.zeros(), 200000, 100, 1e-12)
     assert r < 1e-12
-    hb = lbm.lbm_hybrid_init(n, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    hb = lbm.lbm_hybrid_init(lbm.LBM_COUETTE, n, 1, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
     info = lbm.lbm_hybrid_solve(hb, 1e-12, 200000, 100)
     assert info["residual"] < 1e-12
-    ux, pxy = lbm.lbm_hybrid_profile(hb)
+    ux = lbm.lbm_hybrid_velocity(hb)[0][:, 0]
+    pxy = lbm.lbm_hybrid_face_flux(hb)
     assert np.abs(ux - p.ux(href)).max() / 0.01 < 1e-9
     fr = p.face_flux(href)
     assert np.abs(pxy - fr).max() / np.abs(fr).max() < 1e-9
@@ -91,13 +94,60 @@ def test_hybrid_steady_state_matches_oracle_and_conserves():
     hb.close()
 
 
+CAVITY_CASES = [
+    # n_half, nx, ny, kn, u_bottom, u_top, layer
+    (3, 9, 8, 0.2, 0.003, 0.01, 2),
+    (4, 12, 12, 0.1, 0.0, 0.01, 3),
+    (2, 11, 7, 1.0, 0.0, 0.02, 1),
+    (3, 7, 6, 0.2, 0.0, 0.01, 0),      # all full-range
+    (3, 7, 6, 0.2, 0.0, 0.01, 4),      # all half-range
+    (6, 6, 5, 0.5, 0.0, 0.01, 1),      # 144 half-range velocities next to 36 full-range
+]
+
+
+@pytest.mark.parametrize("case", CAVITY_CASES)
+@pytest.mark.parametrize("start", ["cold", "random"])
+def test_hybrid_cavity_steps_match_oracle(case, start):
+    n, nx, ny, kn, ub, ut, layer = case
+    p = hy.HybridCavity(n, nx, ny, kn, ub, ut, layer)
+    hb = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n, nx, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    q = lbm.lbm_hybrid_query(hb)
+    assert q["unknowns"] == p.unknowns() and q["half_range_cells"] == sum(p.half)
+    assert q["dt"] == pytest.approx(p.dt, rel=1e-15)
+    if start == "random":
+        rng = np.random.default_rng(nx * 31 + layer)
+        h0 = [rng.standard_normal(p.vset(c).n) * 1e-2 for c in range(p.ncells)]
+        lbm.lbm_hybrid_set_state(hb, _pack(h0))
+    else:
+        h0 = p.zeros()
+    steps = 23
+    lbm.lbm_hybrid_step(hb, steps)
+    got = lbm.lbm_hybrid_get_state(hb)
+    hw = p.step(h0, steps)
+    want = _pack(hw)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    ux, uy = lbm.lbm_hybrid_velocity(hb)
+    wx, wy = p.velocity(hw)
+    scale = max(np.abs(wx).max(), np.abs(wy).max())
+    np.testing.assert_allclose(ux, wx, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(uy, wy, rtol=0, atol=1e-12 * scale)
+    if start == "random":
+        assert abs(got.sum() - _pack(h0).sum()) < 1e-13
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_hybrid_face_flux(hb)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    hb.close()
+
+
 def test_hybrid_rejects_invalid_arguments():
-    for args in [(1, 10, 0.1, 0.0, 0.01, 2), (7, 10, 0.1, 0.0, 0.01, 2), (4, 1, 0.1, 0.0, 0.01, 0),
-                 (4, 10, 0.0, 0.0, 0.01, 2), (4, 10, 0.1, 0.0, 0.01, -1)]:
+    C, V = lbm.LBM_COUETTE, lbm.LBM_CAVITY
+    for args in [(C, 1, 1, 10, 0.1, 0.0, 0.01, 2), (C, 7, 1, 10, 0.1, 0.0, 0.01, 2), (C, 4, 1, 1, 0.1, 0.0, 0.01, 0),
+                 (C, 4, 1, 10, 0.0, 0.0, 0.01, 2), (C, 4, 1, 10, 0.1, 0.0, 0.01, -1), (C, 4, 3, 10, 0.1, 0.0, 0.01, 2),
+                 (V, 4, 1, 10, 0.1, 0.0, 0.01, 2), (5, 4, 8, 8, 0.1, 0.0, 0.01, 2)]:
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_hybrid_init(*args)
         assert e.value.status == lbm.LBM_EINVAL
-    hb = lbm.lbm_hybrid_init(4, 10, 0.1, 0.0, 0.01, 2)
+    hb = lbm.lbm_hybrid_init(C, 4, 1, 10, 0.1, 0.0, 0.01, 2)
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_hybrid_residual(hb)           # no step taken yet
     assert e.value.status == lbm.LBM_EINVAL
