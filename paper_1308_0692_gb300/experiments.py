@@ -3,7 +3,7 @@ library's FP64 march: the Couette Kn sweep (Figs. 1-2), the Couette profile and 
 stress at Kn = 1 (Fig. 3 and the statement on the number of full-range nodes), and the
 driven cavity's centre-line profile, lid drag D and vortex flow rate G (Fig. 4, Table 2).
 
-    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2,order,hybrid} --out r.json
+    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2,order,hybrid,cavity_hybrid} --out r.json
 
 Couette flow between plates at -u_w and +u_w: for each Knudsen number and velocity set the
 steady state is marched on the GPU to a residual tolerance, and the shear stress (the
@@ -251,11 +251,49 @@ def hybrid_study(kns=(0.1, 1.0, 10.0), ny=200, n_half=4, layers=(0, 5, 10, 20, 4
     return out
 
 
+def cavity_hybrid_study(kns=(0.1, 1.0), side=128, n_half=4, layers=(0, 4, 8, 16, 32), u_w=0.01, tol=1e-10):
+    """The hybrid cavity (half-range cells within `layer` cells of any wall, full-range inside)
+    against the pure half-range march of the same N (layer = side/2): max |du|/u_w over the
+    cavity, the vertical centre-line u_x, unknowns, steps and GPU seconds."""
+    import time
+
+    import torch
+    stream = torch.cuda.Stream()
+    out = {"side": side, "n_half": n_half, "runs": []}
+    for kn in kns:
+        rows = []
+        for layer in list(layers) + [side // 2]:
+            hb = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n_half, side, side, kn, 0.0, u_w, layer, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = lbm.lbm_hybrid_solve(hb, tol, 5_000_000, 100)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            ux, uy = lbm.lbm_hybrid_velocity(hb)
+            q = lbm.lbm_hybrid_query(hb)
+            rows.append({"layer": layer, "unknowns": q["unknowns"], "steps": info["steps"],
+                         "residual": info["residual"], "seconds": el, "ms_per_step": 1e3 * el / info["steps"],
+                         "ux": ux, "uy": uy})
+            hb.close()
+        half = rows[-1]
+        mid = side // 2
+        for r in rows:
+            du = max(np.abs(r["ux"] - half["ux"]).max(), np.abs(r["uy"] - half["uy"]).max()) / u_w
+            r["max_du_vs_half_range"] = float(du)
+            r["centreline_ux"] = (0.5 * (r["ux"][:, mid - 1] + r["ux"][:, mid]) / u_w).tolist()
+            del r["ux"], r["uy"]
+        out["runs"].append({"kn": kn, "layers": rows})
+    out["summary"] = [[run["kn"], [(r["layer"], r["unknowns"], round(r["max_du_vs_half_range"], 5),
+                                    round(r["ms_per_step"], 3)) for r in run["layers"]]] for run in out["runs"]]
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order", "hybrid"])
+    ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order", "hybrid",
+                                           "cavity_hybrid"])
     ap.add_argument("--out", required=True)
     ap.add_argument("--side", type=int, default=128)
     args = ap.parse_args(argv)
@@ -267,6 +305,8 @@ def main(argv=None):
         r = order_study()
     elif args.study == "hybrid":
         r = hybrid_study()
+    elif args.study == "cavity_hybrid":
+        r = cavity_hybrid_study(side=args.side)
     else:
         r = cavity_table2_study(side=args.side)
     with open(args.out, "w") as f:
