@@ -205,3 +205,27 @@ def test_batch_refine_matches_single_simulation_refinement():
     assert abs(binfo["sweeps"] - sinfo["sweeps"]) <= 1
     hb, hs = lbm.lbm_batch_get_state(b, 0), lbm.lbm_get_state(sim)
     assert np.abs(hb - hs).max() <= 1e-5 * np.abs(hs).max()
+
+
+def test_batch_chunk_height_does_not_change_results():
+    """Any rows-per-chunk choice of the column march (planned or fixed) gives the same states:
+    the items tile each cavity exactly and every item's arithmetic is independent of its
+    chunk; heights below 4 are rejected."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    states = []
+    for rows in (0, 4, 7, 64):
+        b = lbm.lbm_batch_init(vs, _probs(), stream=torch.cuda.Stream())
+        lbm.lbm_batch_set_march(b, True, rows)
+        info = lbm.lbm_batch_get_march(b)
+        assert info["on"] and (rows == 0 or info["rows_per_chunk"] == rows)
+        lbm.lbm_batch_advance(b, 15, 0.0)
+        lbm.lbm_batch_poll(b)
+        states.append([lbm.lbm_batch_get_state(b, i) for i in range(len(INSTANCES))])
+        if rows == 64:
+            with pytest.raises(lbm.LBMError) as e:
+                lbm.lbm_batch_set_march(b, True, 3)
+            assert e.value.status == lbm.LBM_EINVAL
+        b.close()
+    for other in states[1:]:
+        for a, c in zip(states[0], other):
+            np.testing.assert_array_equal(a, c)
