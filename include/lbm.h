@@ -132,7 +132,7 @@ typedef struct {
  * Any march also stops when its residual has not improved by 1 % over 20 consecutive
  * checks (the FP32 rounding floor of the per-step change, about 1e-8 of ||h|| on a 128^2
  * cavity, lies above a 1e-8 target).  FP32 simulations may apply refine_sweeps
- * mixed-precision refinement sweeps: the march then stops at max(tol, 1e-6), and each sweep
+ * mixed-precision refinement sweeps: the march then stops at max(tol, 5e-8), and each sweep
  * takes the defect D = M(h) - h of the stored FP32 state under one FP64 step, marches the
  * correction delta <- L(delta) + D of the homogeneous problem (walls without driving) in
  * FP32 until its per-step change is below refine_tol * ||h|| (refine_tol <= 0: 0.1 * tol),
@@ -270,7 +270,9 @@ lbm_status lbm_norms_noalloc(const void *a, const void *b, long count, int prec,
  * unconverged instance by nsteps time steps: work items are (instance, 32-cell segment)
  * pairs taken round-robin by the resident blocks, a grid-wide barrier with a bounded wait
  * separates steps, and every residual_every steps instances whose residual is below tol
- * are frozen (their items are skipped from then on).  Supported: FP32 perturbation
+ * are frozen (their items are skipped from then on); with tol > 0 so is an instance whose
+ * residual has not improved by 1 % over 20 checks (the FP32 rounding floor: its status
+ * then reports converged with the residual it reached).  Supported: FP32 perturbation
  * storage with 4 or 8 nodes per axis (D2Q^h_16 / D2Q16, D2Q^h_64); wall densities are
  * summed in FP64, the ghosts evaluated in FP32.  A barrier that gives up makes the next
  * lbm_batch_poll return LBM_ETIMEOUT. */

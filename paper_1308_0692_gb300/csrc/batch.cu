@@ -81,6 +81,8 @@ struct BatchArgs {
     int nwall;
     double *acc;           // [ninst][2] residual sums of the current interval
     double *last_r;        // [ninst]
+    double *best_r;        // [ninst] lowest residual so far (march mode; nullptr: no stagnation rule)
+    int *flat;             // [ninst] residual checks since it last improved by 1 %
     long *frozen;          // [ninst] step count at convergence (LONG_MAX while active)
     unsigned *bar_count;
     unsigned *bar_gen;
@@ -449,7 +451,17 @@ __global__ void __launch_bounds__(lbmk::Shape<G>::THREADS, 2) batch_kernel(const
                     const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
                     a.last_r[i] = r;
                     if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
-                    if (r < a.tol) a.frozen[i] = s + 1;
+                    if (r < a.tol) {
+                        a.frozen[i] = s + 1;
+                    } else if (a.best_r && a.tol > 0) {
+                        // the FP32 rounding floor: no 1 % improvement over 20 checks freezes too
+                        if (r < 0.99 * a.best_r[i]) {
+                            a.best_r[i] = r;
+                            a.flat[i] = 0;
+                        } else if (++a.flat[i] >= 20) {
+                            a.frozen[i] = s + 1;
+                        }
+                    }
                     a.acc[2 * i] = 0.0;
                     a.acc[2 * i + 1] = 0.0;
                 }
@@ -821,7 +833,17 @@ __global__ void __launch_bounds__(256, 3) batch_march_kernel(const BatchArgs a)
                     const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
                     a.last_r[i] = r;
                     if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
-                    if (r < a.tol) a.frozen[i] = s + 1;
+                    if (r < a.tol) {
+                        a.frozen[i] = s + 1;
+                    } else if (a.best_r && a.tol > 0) {
+                        // the FP32 rounding floor: no 1 % improvement over 20 checks freezes too
+                        if (r < 0.99 * a.best_r[i]) {
+                            a.best_r[i] = r;
+                            a.flat[i] = 0;
+                        } else if (++a.flat[i] >= 20) {
+                            a.frozen[i] = s + 1;
+                        }
+                    }
                     a.acc[2 * i] = 0.0;
                     a.acc[2 * i + 1] = 0.0;
                 }
@@ -941,7 +963,8 @@ struct lbm_batch {
     std::vector<std::pair<void *, int>> occ;   // resident blocks per SM of each kernel used
     int nsm;
     std::vector<char> live;     // instances in the current item lists (not yet converged)
-    double *d_acc, *d_last_r;
+    double *d_acc, *d_last_r, *d_best;
+    int *d_flat;
     long *d_frozen;
     unsigned *d_bar;
     int *d_err;
@@ -1220,6 +1243,8 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     a.kind = b->d_kind;
     a.acc = b->d_acc;
     a.last_r = b->d_last_r;
+    a.best_r = b->d_best;
+    a.flat = b->d_flat;
     a.frozen = b->d_frozen;
     a.bar_count = b->d_bar;
     a.bar_gen = b->d_bar + 1;
@@ -1374,6 +1399,8 @@ lbm_status refine_defect(lbm_batch *b, std::vector<double> &sums)
     a.buf[1] = b->r_d;
     a.acc = b->r_acc;
     a.last_r = b->r_last;
+    a.best_r = nullptr;          // the refinement keeps its own stagnation rule
+    a.flat = nullptr;
     a.frozen = b->r_frozen;
     a.step0 = 0;
     const DefectShape ds = defect_shape(b->m);
@@ -1432,7 +1459,9 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
     off = align256(off + sizeof(MarchItem) * std::max(1L, mits));
     off = align256(off + (size_t)count);                        // instance kinds
     off = align256(off + sizeof(double) * 2 * count);
-    off = align256(off + sizeof(double) * count);
+    off = align256(off + sizeof(double) * count);     // last residual
+    off = align256(off + sizeof(double) * count);     // best residual
+    off = align256(off + sizeof(int) * count);        // checks without improvement
     off = align256(off + sizeof(long) * count);
     off = align256(off + 64);
     off = align256(off + sizeof(double) * 2 * LBM_MAX_M);      // 1-D nodes and weights
@@ -1535,6 +1564,10 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     o = align256(o + sizeof(double) * 2 * count);
     b->d_last_r = (double *)(p + o);
     o = align256(o + sizeof(double) * count);
+    b->d_best = (double *)(p + o);
+    o = align256(o + sizeof(double) * count);
+    b->d_flat = (int *)(p + o);
+    o = align256(o + sizeof(int) * count);
     b->d_frozen = (long *)(p + o);
     o = align256(o + sizeof(long) * count);
     b->d_bar = (unsigned *)(p + o);
@@ -1550,6 +1583,8 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_acc, 0, sizeof(double) * 2 * count, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_last_r, last.data(), sizeof(double) * count, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_best, last.data(), sizeof(double) * count, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flat, 0, sizeof(int) * count, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_frozen, frozen.data(), sizeof(long) * count, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 64, b->stream);
     std::vector<unsigned char> kind(count);
@@ -1698,6 +1733,8 @@ lbm_status lbm_batch_reset(lbm_batch *b)
     if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[1], 0, b->total_vals * es, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_acc, 0, sizeof(double) * 2 * n, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_last_r, last.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_best, last.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flat, 0, sizeof(int) * n, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_frozen, frozen.data(), sizeof(long) * n, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 64, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1948,6 +1985,8 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
             a.ref_n2 = b->r_n2;
             a.acc = b->r_acc;
             a.last_r = b->r_last;
+    a.best_r = nullptr;          // the refinement keeps its own stagnation rule
+    a.flat = nullptr;
             a.frozen = b->r_frozen;
             a.step0 = k;
             e = launch_pair(b, a, march_fns(b->m).correct, b->var->fn_correct, b->stream);

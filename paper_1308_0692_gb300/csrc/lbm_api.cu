@@ -786,11 +786,12 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
     const long K = s->prob.residual_every;
     // --- the march: whole residual intervals until r < tol ---
     // An FP32 march cannot push its per-step change below its rounding floor (~1e-8 of
-    // ||h|| on a 128^2 cavity): with refinement it stops at max(tol, 1e-6) and leaves the
-    // rest to the FP64 defect correction; in any precision it stops when the residual has
-    // not improved by 1 % over 20 consecutive checks (stagnation at the floor).
+    // ||h|| on a 128^2 cavity): with refinement it stops at max(tol, 5e-8) -- as deep as the
+    // FP32 march goes without stalling, since its steps are cheaper than the correction's --
+    // and leaves the rest to the FP64 defect correction; in any precision it stops when the
+    // residual has not improved by 1 % over 20 consecutive checks (stagnation at the floor).
     const bool fp32_refined = refine_sweeps > 0;
-    const double tol_march = fp32_refined ? std::fmax(tol, 1e-6) : tol;
+    const double tol_march = fp32_refined ? std::fmax(tol, 5e-8) : tol;
     double r = INFINITY, best = INFINITY;
     int flat = 0;
     long taken = 0;

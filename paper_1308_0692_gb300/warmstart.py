@@ -143,10 +143,10 @@ def load_mlp(path, max_batch=128 * 128):
 
 
 def batch_solve(vs, pairs, tol, side=128, mlp=None, steps_per_launch=500, max_steps=1_000_000):
-    """March all pairs as one batch (cold or warm start) to max(tol, 1e-6) -- the FP32 march's
+    """March all pairs as one batch (cold or warm start) to max(tol, 5e-8) -- the FP32 march's
     share of a refined solve (see lbm_solve); returns (batch, steps per instance, seconds).
     The warm-start reconstruction is included in the time."""
-    tol = max(tol, 1e-6)
+    tol = max(tol, 5e-8)
     import torch
     probs = [lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
                               residual_every=100) for kn, uw in pairs]

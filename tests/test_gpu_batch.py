@@ -229,3 +229,23 @@ def test_batch_chunk_height_does_not_change_results():
     for other in states[1:]:
         for a, c in zip(states[0], other):
             np.testing.assert_array_equal(a, c)
+
+
+def test_batch_freezes_instances_at_the_fp32_floor():
+    """A tolerance below the FP32 rounding floor of the per-step change: every instance still
+    freezes -- by the stagnation rule (no 1 % improvement over 20 checks) at its floor, or by
+    the tolerance where its FP32 state stops changing altogether -- in finitely many steps."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    b = lbm.lbm_batch_init(vs, _probs(residual_every=50), stream=torch.cuda.Stream())
+    tol = 1e-13
+    done = 0
+    while done < 400_000:
+        lbm.lbm_batch_advance(b, 1000, tol)
+        done += 1000
+        if lbm.lbm_batch_poll(b)[0] == 0:
+            break
+    stats = [lbm.lbm_batch_status(b, i) for i in range(len(INSTANCES))]
+    assert all(s["converged"] for s in stats), stats
+    assert all(s["residual"] < 1e-6 for s in stats), [s["residual"] for s in stats]
+    assert any(s["residual"] > tol for s in stats), [s["residual"] for s in stats]
+    assert max(s["steps"] for s in stats) < done
