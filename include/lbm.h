@@ -295,11 +295,14 @@ lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, in
  * every instance on the segment kernel (same results up to FP32 summation order).
  * The warp groups take items from a per-step counter (dynamic balance across SMs).
  * rows_per_chunk: rows of one march item (>= 4), or 0 to let the library plan it at every
- * rebuild of the item lists (about four items per resident warp group, 4 to 64 rows).
- * lbm_batch_get_march reports the switch, the rows per chunk in use, the number of march
- * items and the march kernel's grid (outputs may be NULL). */
-lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk);
-lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid);
+ * rebuild of the item lists (about three items per resident warp group, 4 to 64 rows).
+ * warps_per_item: M (one velocity row per warp), M / 2 (two rows per warp, two items per
+ * block; the default, 0) .  lbm_batch_get_march reports the switch, the rows per chunk
+ * in use, the number of march items, the march kernel's grid and its warps per item
+ * (outputs may be NULL). */
+lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk, int warps_per_item);
+lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid,
+                               int *warps_per_item);
 lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol);     /* asynchronous */
 /* Limit of every bounded wait in the grid barrier, in SM clock cycles (default 4e9, about
  * 2 s).  Exposed so that tests can make a wait give up and check the error path. */

@@ -21,6 +21,7 @@ def main(argv=None):
     ap.add_argument("--n-half", type=int, default=4)
     ap.add_argument("--march", choices=["on", "off"], default="on")
     ap.add_argument("--rows-per-chunk", type=int, default=0, help="0: planned by the library")
+    ap.add_argument("--warps-per-item", type=int, default=0, help="M, M/2 or 0 (library default)")
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--launches", type=int, default=1)
@@ -34,7 +35,8 @@ def main(argv=None):
                               residual_every=100) for kn, uw in pairs]
     stream = torch.cuda.Stream()
     b = lbm.lbm_batch_init(vs, probs, stream=stream)
-    lbm.lbm_batch_set_march(b, args.march == "on", args.rows_per_chunk if args.march == "on" else 0)
+    lbm.lbm_batch_set_march(b, args.march == "on", args.rows_per_chunk if args.march == "on" else 0,
+                            args.warps_per_item if args.march == "on" else 0)
     if args.warmup > 0:
         lbm.lbm_batch_advance(b, args.warmup, 0.0)
         lbm.lbm_batch_poll(b)

@@ -505,15 +505,17 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <int M>
+template <int M, int G>
 struct MarchShared {
-    static constexpr int SUB = 8 / M;    // items per block of 8 warps
+    static constexpr int RPL = M / G;    // velocity rows per warp
+    static constexpr int SUB = 8 / G;    // items per block of 8 warps
     static constexpr int NS = 4;         // row slots per warp
     static constexpr int RW = 34;        // a row line: left edge, 32 cells, right edge
-    float4 mom[SUB][2][M][32];           // [item][row parity][warp][lane]: (rho, jx, jy, -) partials
-    float2 side[SUB][2][2][M];           // [item][parity][left, right][warp]: (sum, error)
-    float2 tb[SUB][2][M][32];            // [item][parity][warp][lane]: bottom or top wall row
-    float2 ring[8][NS][M / 2][RW];       // [warp][slot][velocity pair][line]: velocities (2j, 2j + 1)
+    static constexpr int PW = RPL * M / 2;   // velocity pairs per warp
+    float4 mom[SUB][2][G][32];           // [item][row parity][warp][lane]: (rho, jx, jy, -) partials
+    float2 side[SUB][2][2][G];           // [item][parity][left, right][warp]: (sum, error)
+    float2 tb[SUB][2][G][32];            // [item][parity][warp][lane]: bottom or top wall row
+    float2 ring[8][NS][PW][RW];          // [warp][slot][velocity pair][line]: velocities (2q, 2q + 1)
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p)
@@ -537,17 +539,18 @@ __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 xi2(const BatchArgs &a, int j) { return make_float2(a.xi_f[2 * j], a.xi_f[2 * j + 1]); }
 __device__ __forceinline__ float2 w2(const BatchArgs &a, int j) { return make_float2(a.w1_f[2 * j], a.w1_f[2 * j + 1]); }
 
-template <int M, int MODE>
+template <int M, int G, int MODE>
 __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *mi, long s, const float *h,
-                                           float *hn, bool resid, MarchShared<M> &sh)
+                                           float *hn, bool resid, MarchShared<M, G> &sh)
 {
-    constexpr int HALF = M / 2, P = M / 2, PH = P / 2;    // velocity pairs; pairs j >= PH move right
-    constexpr int SUB = MarchShared<M>::SUB, NS = MarchShared<M>::NS, RW = MarchShared<M>::RW;
-    static_assert(SUB * M == 8 && M <= 16 && HALF % 2 == 0, "eight warps per block; pairs on one side");
+    using Sh = MarchShared<M, G>;
+    constexpr int P = M / 2, PH = P / 2;                  // pairs per velocity row; j >= PH move right
+    constexpr int RPL = Sh::RPL, SUB = Sh::SUB, NS = Sh::NS, RW = Sh::RW, PW = Sh::PW;
+    static_assert(SUB * G == 8 && RPL * M <= 16 && (M / 2) % 2 == 0, "eight warps per block; edge lanes; pairs on one side");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sub = warp / M, iy = warp - sub * M;
-    const int bar_id = 1 + sub, bar_n = 32 * M;
+    const int sub = warp / G, g = warp - sub * G;
+    const int bar_id = 1 + sub, bar_n = 32 * G;
 
     const int4 *q = reinterpret_cast<const int4 *>(mi);
     const int4 q0 = __ldg(q), q1 = __ldg(q + 1);
@@ -559,9 +562,16 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     const int nc = nx * ny;                   // cells of the instance (its state < 2^31 values)
     const float cx = k0.x, cy = k0.y, om = k0.z, bb = k0.w;
 
-    const float xiy = a.xi_f[iy], wy = a.w1_f[iy];
-    const bool up = xiy > 0.f;                // upwind neighbour below; ghost at the bottom wall
-    const float nuy = (xiy < 0.f ? -xiy : xiy) * cy;
+    // this warp's velocity rows iy0 .. iy0 + RPL - 1 share the sign of xi_y
+    const int iy0 = g * RPL;
+    float xiyr[RPL], wyr[RPL], nuyr[RPL];
+#pragma unroll
+    for (int rr = 0; rr < RPL; ++rr) {
+        xiyr[rr] = a.xi_f[iy0 + rr];
+        wyr[rr] = a.w1_f[iy0 + rr];
+        nuyr[rr] = (xiyr[rr] < 0.f ? -xiyr[rr] : xiyr[rr]) * cy;
+    }
+    const bool up = xiyr[0] > 0.f;            // upwind neighbour below; ghost at the bottom wall
     float2 nux2[P];                           // |xi_x| dt / dx per velocity pair
 #pragma unroll
     for (int j = 0; j < P; ++j) {
@@ -573,27 +583,28 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     const bool wl = x == 0, wr = x == nx - 1;
     const bool side_l = x0 == 0, side_r = x0 + 32 >= nx, side = side_l || side_r;
     const int lr = nx - 1 - x0;               // lane of the right-wall cell when side_r
-    const float *hb = h + off + (long)(iy * M) * nc;
-    float *ho = hn + off + (long)(iy * M) * nc;
-    float2 (*ring)[P][RW] = sh.ring[warp];
+    const float *hb = h + off + (long)(iy0 * M) * nc;
+    float *ho = hn + off + (long)(iy0 * M) * nc;
+    float2 (*ring)[PW][RW] = sh.ring[warp];
 
-    // copy row r of this warp's M velocities into slot r mod NS: the 32 cells (clamped into
-    // the row), and in one more copy the edge columns x0 - 1 (lanes 0..M-1, one velocity
-    // each) and x0 + 32 (lanes 16..16+M-1); one commit group per call
+    // copy row r of this warp's RPL * M velocities (local index k = rr * M + ix) into slot
+    // r mod NS: the 32 cells (clamped into the row), and in one more copy the edge columns
+    // x0 - 1 (lanes 0..RPL*M-1, one velocity each) and x0 + 32 (lanes 16..16+RPL*M-1); one
+    // commit group per call
     const int xc = valid ? x : nx - 1;
-    const bool edge_l = lane < M, edge_r = lane >= 16 && lane < 16 + M;
-    const int e_ix = edge_l ? lane : lane - 16;
+    const bool edge_l = lane < RPL * M, edge_r = lane >= 16 && lane < 16 + RPL * M;
+    const int e_k = edge_l ? lane : lane - 16;
     const int e_x = edge_l ? (x0 > 0 ? x0 - 1 : 0) : min(x0 + 32, nx - 1);
     auto copy_row = [&](int r, bool issue) {
         if (issue) {
             float2 (*slot)[RW] = ring[r & (NS - 1)];
             const float *src = hb + (r * nx + xc);
 #pragma unroll
-            for (int ix = 0; ix < M; ++ix)
-                cp_async4(reinterpret_cast<float *>(&slot[ix >> 1][1 + lane]) + (ix & 1), src + ix * nc);
+            for (int k = 0; k < RPL * M; ++k)
+                cp_async4(reinterpret_cast<float *>(&slot[k >> 1][1 + lane]) + (k & 1), src + k * nc);
             if (edge_l || edge_r)
-                cp_async4(reinterpret_cast<float *>(&slot[e_ix >> 1][edge_l ? 0 : RW - 1]) + (e_ix & 1),
-                          hb + (e_ix * nc + r * nx + e_x));
+                cp_async4(reinterpret_cast<float *>(&slot[e_k >> 1][edge_l ? 0 : RW - 1]) + (e_k & 1),
+                          hb + (e_k * nc + r * nx + e_x));
         }
         cp_async_commit();
     };
@@ -620,44 +631,54 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         if (side_l && lane == 0) {
             float hi = 0.f, lo = 0.f;
 #pragma unroll
-            for (int j = 0; j < PH; ++j) {
-                const float2 u = row[j][1];
-                comp_add(hi, lo, -(a.xi_f[2 * j] * u.x));
-                comp_add(hi, lo, -(a.xi_f[2 * j + 1] * u.y));
-            }
-            sh.side[sub][p][0][iy] = make_float2(hi, lo);
+            for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+                for (int j = 0; j < PH; ++j) {
+                    const float2 u = row[rr * P + j][1];
+                    comp_add(hi, lo, -(a.xi_f[2 * j] * u.x));
+                    comp_add(hi, lo, -(a.xi_f[2 * j + 1] * u.y));
+                }
+            sh.side[sub][p][0][g] = make_float2(hi, lo);
         }
         if (side_r && lane == lr) {
             float hi = 0.f, lo = 0.f;
 #pragma unroll
-            for (int j = PH; j < P; ++j) {
-                const float2 u = row[j][1 + lr];
-                comp_add(hi, lo, a.xi_f[2 * j] * u.x);
-                comp_add(hi, lo, a.xi_f[2 * j + 1] * u.y);
-            }
-            sh.side[sub][p][1][iy] = make_float2(hi, lo);
+            for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+                for (int j = PH; j < P; ++j) {
+                    const float2 u = row[rr * P + j][1 + lr];
+                    comp_add(hi, lo, a.xi_f[2 * j] * u.x);
+                    comp_add(hi, lo, a.xi_f[2 * j + 1] * u.y);
+                }
+            sh.side[sub][p][1][g] = make_float2(hi, lo);
         }
         if (r == 0 || r == ny - 1) {
-            float hi = 0.f, lo = 0.f;
+            // sum over the warp's rows of |xi_y| times the row sum, each product with its
+            // rounding error (FMA) kept; bottom wall: velocities moving down, top: moving up
+            float th = 0.f, tl = 0.f;
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                const float2 u = row[j][1 + lane];
-                comp_add(hi, lo, u.x);
-                comp_add(hi, lo, u.y);
+            for (int rr = 0; rr < RPL; ++rr) {
+                float hi = 0.f, lo = 0.f;
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const float2 u = row[rr * P + j][1 + lane];
+                    comp_add(hi, lo, u.x);
+                    comp_add(hi, lo, u.y);
+                }
+                const float ax = xiyr[rr] < 0.f ? -xiyr[rr] : xiyr[rr];
+                const float ph = ax * hi, pl = fmaf(ax, hi, -ph) + ax * lo;
+                comp_add(th, tl, ph);
+                tl += pl;
             }
-            // |xi_y| times the row sum, with the product's rounding error (FMA) kept;
-            // bottom wall: velocities moving down (xi_y < 0); top wall: moving up
-            const float ax = xiy < 0.f ? -xiy : xiy;
-            const float ph = ax * hi, pl = fmaf(ax, hi, -ph) + ax * lo;
             const bool in = r == 0 ? !up : up;
-            sh.tb[sub][p][iy][lane] = in ? make_float2(ph, pl) : make_float2(0.f, 0.f);
+            sh.tb[sub][p][g][lane] = in ? make_float2(th, tl) : make_float2(0.f, 0.f);
         }
     };
     float rho_l = 0.f, rho_r = 0.f, rho_w = 0.f;    // side walls; bottom or top wall of a wall row
     auto total = [&](const float2 *t, int stride, float inv) {
         float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int w = 0; w < M; ++w) {
+        for (int w = 0; w < G; ++w) {
             const float2 u = t[w * stride];
             comp_add(hi, lo, u.x);
             lo += u.y;
@@ -679,58 +700,75 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     // wall speed and driving term of the wall this warp's velocities come from (Eq. 8)
     const float uw = up ? k1.x : k1.y;
     const float dw = MODE == BATCH_CORRECT ? 0.f : (up ? k1.z : k1.w);
-    const float *sb = MODE == BATCH_CORRECT ? a.src + off + (long)(iy * M) * nc : nullptr;
+    const float *sb = MODE == BATCH_CORRECT ? a.src + off + (long)(iy0 * M) * nc : nullptr;
 
-    float2 v[P];
+    float2 v[PW];
     // transport (Eqs. 1, 8-9) of row r into v[] (FP32x2 over velocity pairs, per velocity the
     // same operations as batch_group); SIDE: a side-wall cell in the strip, WROW: the y ghost
-    // of a wall row.  Returns the partial moments (rho, jx).
+    // of a wall row.  Returns the partial moments (rho, jx, jy) of the warp's velocities.
     // (called with literal flags: each call site is inlined and specialised)
     auto transport = [&](bool SIDE, bool WROW, const float2 (*cur)[RW], const float2 (*yrow)[RW]) {
-        float2 R2 = make_float2(0.f, 0.f), X2 = make_float2(0.f, 0.f);
+        float R = 0.f, X = 0.f, Y = 0.f;
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const float2 hc = cur[j][1 + lane];
-            float2 xn = cur[j][j >= PH ? lane : lane + 2];
-            if (SIDE) {
-                const float2 wa = __fmul2_rn(w2(a, j), splat(wy));
-                if (j >= PH && wl) xn = __fmul2_rn(wa, splat(rho_l));
-                if (j < PH && wr) xn = __fmul2_rn(wa, splat(rho_r));
+        for (int rr = 0; rr < RPL; ++rr) {
+            float2 R2 = make_float2(0.f, 0.f), X2 = make_float2(0.f, 0.f);
+            const float2 wyy = splat(wyr[rr]);
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int qq = rr * P + j;
+                const float2 hc = cur[qq][1 + lane];
+                float2 xn = cur[qq][j >= PH ? lane : lane + 2];
+                if (SIDE) {
+                    const float2 wa = __fmul2_rn(w2(a, j), wyy);
+                    if (j >= PH && wl) xn = __fmul2_rn(wa, splat(rho_l));
+                    if (j < PH && wr) xn = __fmul2_rn(wa, splat(rho_r));
+                }
+                float2 yn;
+                if (WROW) {
+                    const float2 wa = __fmul2_rn(w2(a, j), wyy);
+                    const float2 gg = __ffma2_rn(xi2(a, j), splat(uw), splat(1.f));
+                    yn = __fmul2_rn(wa, __ffma2_rn(xi2(a, j), splat(dw), __fmul2_rn(splat(rho_w), gg)));
+                } else {
+                    yn = yrow[qq][1 + lane];
+                }
+                float2 t = __ffma2_rn(nux2[j], __fadd2_rn(xn, neg2(hc)), hc);
+                t = __ffma2_rn(splat(nuyr[rr]), __fadd2_rn(yn, neg2(hc)), t);
+                v[qq] = t;
+                R2 = __fadd2_rn(R2, t);
+                X2 = __ffma2_rn(xi2(a, j), t, X2);
             }
-            float2 yn;
-            if (WROW) {
-                const float2 wa = __fmul2_rn(w2(a, j), splat(wy));
-                const float2 g = __ffma2_rn(xi2(a, j), splat(uw), splat(1.f));
-                yn = __fmul2_rn(wa, __ffma2_rn(xi2(a, j), splat(dw), __fmul2_rn(splat(rho_w), g)));
-            } else {
-                yn = yrow[j][1 + lane];
-            }
-            float2 t = __ffma2_rn(nux2[j], __fadd2_rn(xn, neg2(hc)), hc);
-            t = __ffma2_rn(splat(nuy), __fadd2_rn(yn, neg2(hc)), t);
-            v[j] = t;
-            R2 = __fadd2_rn(R2, t);
-            X2 = __ffma2_rn(xi2(a, j), t, X2);
+            const float Rr = R2.x + R2.y;
+            R += Rr;
+            X += X2.x + X2.y;
+            Y += xiyr[rr] * Rr;
         }
-        return make_float2(R2.x + R2.y, X2.x + X2.y);
+        return make_float3(R, X, Y);
     };
     float psd = 0.f, psd_c = 0.f, psn = 0.f, psn_c = 0.f;
     // relaxation (Eqs. 5-7) towards w_a (rho + xi.j) and the store; RESID: residual sums
-    float2 src[MODE == BATCH_CORRECT ? P : 1];   // the correction's source of the current row
-    auto relax = [&](bool RESID, const float2 (*cur)[RW], float qq, float jj, int o) {
+    float2 src[MODE == BATCH_CORRECT ? PW : 1];   // the correction's source of the current row
+    auto relax = [&](bool RESID, const float2 (*cur)[RW], float rho, float jx, float jy, int o) {
         float2 sd = make_float2(0.f, 0.f), sn = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const float2 t = __ffma2_rn(xi2(a, j), splat(jj), splat(qq));
-            float2 nv = __ffma2_rn(w2(a, j), t, __fmul2_rn(splat(bb), v[j]));
-            if (MODE == BATCH_CORRECT) nv = __fadd2_rn(nv, src[j]);
-            if (RESID) {
-                const float2 d = __fadd2_rn(nv, neg2(cur[j][1 + lane]));
-                sd = __ffma2_rn(d, d, sd);
-                sn = __ffma2_rn(nv, nv, sn);
-            }
-            if (valid) {
-                ho[(2 * j) * nc + o] = nv.x;
-                ho[(2 * j + 1) * nc + o] = nv.y;
+        for (int rr = 0; rr < RPL; ++rr) {
+            const float wom = om * wyr[rr];
+            const float qv = wom * (rho + xiyr[rr] * jy);
+            const float jj = wom * jx;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int qq = rr * P + j;
+                const float2 t = __ffma2_rn(xi2(a, j), splat(jj), splat(qv));
+                float2 nv = __ffma2_rn(w2(a, j), t, __fmul2_rn(splat(bb), v[qq]));
+                if (MODE == BATCH_CORRECT) nv = __fadd2_rn(nv, src[qq]);
+                if (RESID) {
+                    const float2 d = __fadd2_rn(nv, neg2(cur[qq][1 + lane]));
+                    sd = __ffma2_rn(d, d, sd);
+                    sn = __ffma2_rn(nv, nv, sn);
+                }
+                if (valid) {
+                    ho[(rr * M + 2 * j) * nc + o] = nv.x;
+                    ho[(rr * M + 2 * j + 1) * nc + o] = nv.y;
+                }
             }
         }
         if (RESID && valid) {
@@ -750,16 +788,16 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         if (MODE == BATCH_CORRECT) {          // issued now, used after the moment exchange
             const int o = r * nx + (valid ? x : nx - 1);
 #pragma unroll
-            for (int j = 0; j < P; ++j)
-                src[j] = valid ? make_float2(__ldg(sb + ((2 * j) * nc + o)), __ldg(sb + ((2 * j + 1) * nc + o)))
+            for (int k = 0; k < PW; ++k)
+                src[k] = valid ? make_float2(__ldg(sb + ((2 * k) * nc + o)), __ldg(sb + ((2 * k + 1) * nc + o)))
                                : make_float2(0.f, 0.f);
         }
         // the y ghost of a wall row: bottom for warps moving up, top for warps moving down
         const bool wrow = up ? r == 0 : r == ny - 1;
-        float2 rx;
+        float3 rx;
         if (wrow) rx = side ? transport(true, true, cur, yrow) : transport(false, true, cur, yrow);
         else rx = side ? transport(true, false, cur, yrow) : transport(false, false, cur, yrow);
-        sh.mom[sub][p][iy][lane] = make_float4(rx.x, rx.y, xiy * rx.x, 0.f);
+        sh.mom[sub][p][g][lane] = make_float4(rx.x, rx.y, rx.z, 0.f);
         // the next row's wall sums travel with this row's moments
         if (r + 1 < y1 && (side || r + 1 == ny - 1)) {
             cp_async_wait<1>();               // row r + 1 (moving up: the older group in flight)
@@ -769,17 +807,14 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         named_barrier(bar_id, bar_n);
         float rho = 0.f, jx = 0.f, jy = 0.f;
 #pragma unroll
-        for (int w = 0; w < M; ++w) {
+        for (int w = 0; w < G; ++w) {
             const float4 u = sh.mom[sub][p][w][lane];
             rho += u.x;
             jx += u.y;
             jy += u.z;
         }
-        const float wom = om * wy;
-        const float qq = wom * (rho + xiy * jy);
-        const float jj = wom * jx;
-        if (resid) relax(true, cur, qq, jj, r * nx + x);
-        else relax(false, cur, qq, jj, r * nx + x);
+        if (resid) relax(true, cur, rho, jx, jy, r * nx + x);
+        else relax(false, cur, rho, jx, jy, r * nx + x);
         if (r + 1 < y1) read_walls(r + 1, p);
     }
     cp_async_wait<0>();
@@ -798,14 +833,16 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     }
 }
 
-template <int M, int MODE>
-__global__ void __launch_bounds__(256, 3) batch_march_kernel(const BatchArgs a)
+template <int M, int G, int MODE>
+__global__ void __launch_bounds__(256, G == M ? 3 : 2) batch_march_kernel(const BatchArgs a)
 {
-    constexpr int SUB = MarchShared<M>::SUB;
-    __shared__ MarchShared<M> sh;
+    using Sh = MarchShared<M, G>;
+    constexpr int SUB = Sh::SUB;
+    extern __shared__ __align__(16) unsigned char march_smem[];   // Sh, sized at launch
+    Sh &sh = *reinterpret_cast<Sh *>(march_smem);
     __shared__ int s_item[SUB][2];            // fetched item of each warp group, double-buffered
-    const int warp = (int)(threadIdx.x >> 5), sub = warp / M;
-    const bool fetcher = warp == sub * M && (threadIdx.x & 31) == 0;
+    const int warp = (int)(threadIdx.x >> 5), sub = warp / G;
+    const bool fetcher = warp == sub * G && (threadIdx.x & 31) == 0;
     for (int si = 0; si < a.nsteps; ++si) {
         const long s = a.step0 + si;
         const float *h = reinterpret_cast<const float *>(a.buf[s & 1]);
@@ -818,10 +855,10 @@ __global__ void __launch_bounds__(256, 3) batch_march_kernel(const BatchArgs a)
         if (blockIdx.x == 0 && threadIdx.x == 0) a.mcount[(s + 1) & 1] = 0u;
         for (int k = 0;; ++k) {
             if (fetcher) s_item[sub][k & 1] = (int)atomicAdd(next, 1u);
-            named_barrier(1 + sub, 32 * M);
+            named_barrier(1 + sub, 32 * G);
             const int item = s_item[sub][k & 1];
             if (item >= a.nmitems) break;
-            march_item<M, MODE>(a, a.mitems + item, s, h, hn, resid, sh);
+            march_item<M, G, MODE>(a, a.mitems + item, s, h, hn, resid, sh);
         }
         if (!grid_barrier(a)) return;
         if (resid) {
@@ -907,17 +944,32 @@ const std::vector<Variant> &variants()
     return v;
 }
 
-// column-march kernels (cavity instances): M = 4 or 8 nodes per axis
+// column-march kernels (cavity instances): M = 4 or 8 nodes per axis, G warps per item
+// (one velocity row per warp with G = M, two with G = M / 2); dynamic shared memory
 struct MarchFns {
     void *march, *correct;
+    int g;
+    size_t smem;
 };
 
-MarchFns march_fns(int m)
+template <int M, int G>
+MarchFns march_fns_of()
 {
-    if (m == 8) return {(void *)batch_march_kernel<8, BATCH_MARCH>, (void *)batch_march_kernel<8, BATCH_CORRECT>};
-    if (m == 4) return {(void *)batch_march_kernel<4, BATCH_MARCH>, (void *)batch_march_kernel<4, BATCH_CORRECT>};
-    return {nullptr, nullptr};
+    return {(void *)batch_march_kernel<M, G, BATCH_MARCH>, (void *)batch_march_kernel<M, G, BATCH_CORRECT>, G,
+            sizeof(MarchShared<M, G>)};
 }
+
+// g <= 0: the default shape, two velocity rows per warp (G = M / 2: 21 % faster than one
+// row per warp on 32 cavities of 128^2 -- the per-row fixed costs and the moment exchange
+// are shared by twice the updates)
+MarchFns march_fns(int m, int g = 0)
+{
+    if (m == 8) return g == 8 ? march_fns_of<8, 8>() : march_fns_of<8, 4>();
+    if (m == 4) return g == 4 ? march_fns_of<4, 4>() : march_fns_of<4, 2>();
+    return {nullptr, nullptr, 0, 0};
+}
+
+bool march_shape_ok(int m, int g) { return g <= 0 || (m == 8 && (g == 8 || g == 4)) || (m == 4 && (g == 4 || g == 2)); }
 
 struct DefectShape {
     void *fn;
@@ -960,6 +1012,7 @@ struct lbm_batch {
     bool march;                 // cavity instances by the column-march kernel
     int nmitems, mgrid, mchunk; // march items, their co-resident grid, rows per chunk
     int mchunk_fixed;           // rows per chunk set by the caller (0: planned per rebuild)
+    int mg;                     // warps per march item (0: the default shape)
     std::vector<std::pair<void *, int>> occ;   // resident blocks per SM of each kernel used
     int nsm;
     std::vector<char> live;     // instances in the current item lists (not yet converged)
@@ -1133,7 +1186,7 @@ void build_march_items(const lbm_batch *b, int chunk, std::vector<MarchItem> &ou
 }
 
 // Resident blocks per SM of a kernel of this batch (queried once per kernel) and the SM count.
-cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks)
+cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks, size_t smem = 0)
 {
     if (b->nsm == 0) {
         int dev = 0;
@@ -1150,20 +1203,22 @@ cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks
             *blocks = o.second;
             return cudaSuccess;
         }
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, 0);
+    cudaError_t e = cudaSuccess;
+    if (smem > 0) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, threads, smem);
     if (e == cudaSuccess) b->occ.emplace_back(fn, *blocks);
     return e;
 }
 
 // Rows per chunk of the column march: items are fetched dynamically, so the chunks only
-// have to be many enough to balance the SMs (about four per resident warp group) and long
+// have to be many enough to balance the SMs (about three per resident warp group) and long
 // enough to amortise an item's start (its first rows' copies and the wall prologue).
 int march_chunk_plan(const lbm_batch *b, long slots)
 {
     long strip_rows = 0;
     for (int i = 0; i < (int)b->inst.size(); ++i)
         if (b->live[i] && b->inst[i].cavity) strip_rows += (long)((b->inst[i].nx + 31) / 32) * b->inst[i].ny;
-    const long h = strip_rows / std::max(1L, 4 * slots);
+    const long h = strip_rows / std::max(1L, 3 * slots);
     return (int)std::max(4L, std::min(64L, h));
 }
 
@@ -1187,12 +1242,15 @@ lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool m
     build_items(b, order, march, items, wall);
     std::vector<MarchItem> mitems;
     int mgrid = 0, mchunk = 0;
-    const MarchFns mf = march_fns(b->m);
+    const MarchFns mf = march_fns(b->m, b->mg);
     if (march && mf.march) {
-        e = occupancy(b, mf.march, 256, &nsm, &mb);
-        if (e != cudaSuccess || mb < 1)
+        int mbc = 0;
+        e = occupancy(b, mf.march, 256, &nsm, &mb, mf.smem);
+        if (e == cudaSuccess) e = occupancy(b, mf.correct, 256, &nsm, &mbc, mf.smem);
+        if (e != cudaSuccess || mb < 1 || mbc < 1)
             return bfail(LBM_EUNSUPPORTED, "column-march kernel does not fit on an SM");
-        const int sub = 8 / b->m;
+        mb = std::min(mb, mbc);                // one grid serves the march and the correction
+        const int sub = 8 / mf.g;
         mchunk = b->mchunk_fixed > 0 ? b->mchunk_fixed : march_chunk_plan(b, (long)nsm * mb * sub);
         build_march_items(b, mchunk, mitems);
         mgrid = (int)std::min<long>((long)nsm * mb, std::max<long>(1, ((long)mitems.size() + sub - 1) / sub));
@@ -1276,13 +1334,14 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     return a;
 }
 
-cudaError_t launch_coop(void *fn, int grid, int threads, const BatchArgs &a, cudaStream_t st)
+cudaError_t launch_coop(void *fn, int grid, int threads, const BatchArgs &a, cudaStream_t st, size_t smem = 0)
 {
     void *args[] = {(void *)&a};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1301,7 +1360,7 @@ cudaError_t launch_pair(lbm_batch *b, const BatchArgs &a0, void *mfn, void *sfn,
         BatchArgs a = a0;
         a.kind_sel = 1;
         e = cudaMemsetAsync(a.mcount, 0, 2 * sizeof(unsigned), st);
-        if (e == cudaSuccess) e = launch_coop(mfn, b->mgrid, 256, a, st);
+        if (e == cudaSuccess) e = launch_coop(mfn, b->mgrid, 256, a, st, march_fns(b->m, b->mg).smem);
     }
     if (e == cudaSuccess && (b->nitems > 0 || b->nwall > 0)) {
         BatchArgs a = a0;
@@ -1313,7 +1372,7 @@ cudaError_t launch_pair(lbm_batch *b, const BatchArgs &a0, void *mfn, void *sfn,
 
 cudaError_t launch_batch(lbm_batch *b, const BatchArgs &a, cudaStream_t st)
 {
-    return launch_pair(b, a, march_fns(b->m).march, b->var->fn, st);
+    return launch_pair(b, a, march_fns(b->m, b->mg).march, b->var->fn, st);
 }
 
 // Co-resident grid of a kernel of this batch for the current item lists.
@@ -1536,6 +1595,7 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     b->nmitems = b->mgrid = b->mchunk = 0;
     b->nsm = 0;
     b->mchunk_fixed = 0;
+    b->mg = 0;
     if (b->owns) {
         cudaError_t e = cudaMalloc(&b->base, bytes);
         if (e != cudaSuccess) {
@@ -1629,13 +1689,16 @@ lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int block
     return apply_schedule(b, warps_per_segment, blocks_per_sm, order);
 }
 
-lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk)
+lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk, int warps_per_item)
 {
     if (!b) return bfail(LBM_EINVAL, "batch is NULL");
     if (on && !march_fns(b->m).march) return bfail(LBM_EUNSUPPORTED, "no column-march kernel for this velocity set");
     if (rows_per_chunk != 0 && rows_per_chunk < 4) return bfail(LBM_EINVAL, "rows per chunk must be 0 or >= 4");
+    if (!march_shape_ok(b->m, warps_per_item))
+        return bfail(LBM_EINVAL, "warps per march item must be 0, M or M / 2 (M = 4 or 8)");
     b->march = on != 0;
     b->mchunk_fixed = rows_per_chunk;
+    b->mg = warps_per_item;
     const int n = (int)b->inst.size();
     std::vector<unsigned char> kind(n);
     for (int i = 0; i < n; ++i) kind[i] = marched(b, i, b->march) ? 1 : 0;
@@ -1645,10 +1708,12 @@ lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk)
     return apply_schedule(b, b->g, b->blocks_per_sm, b->order);
 }
 
-lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid)
+lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid,
+                               int *warps_per_item)
 {
     if (!b) return bfail(LBM_EINVAL, "batch is NULL");
     if (on) *on = b->march;
+    if (warps_per_item) *warps_per_item = march_fns(b->m, b->mg).g;
     if (rows_per_chunk) *rows_per_chunk = b->mchunk;
     if (items) *items = b->nmitems;
     if (grid) *grid = b->mgrid;
@@ -1989,7 +2054,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
     a.flat = nullptr;
             a.frozen = b->r_frozen;
             a.step0 = k;
-            e = launch_pair(b, a, march_fns(b->m).correct, b->var->fn_correct, b->stream);
+            e = launch_pair(b, a, march_fns(b->m, b->mg).correct, b->var->fn_correct, b->stream);
             k += chunk;
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(fro.data(), b->r_frozen, sizeof(long) * n, cudaMemcpyDeviceToHost, b->stream);

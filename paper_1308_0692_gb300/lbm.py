@@ -102,7 +102,7 @@ def _load():
         "lbm_batch_reset": (st, [_vp]),
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
         "lbm_batch_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, _vp]),
-        "lbm_batch_set_march": (st, [_vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_batch_set_march": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "lbm_hybrid_init": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, _vp,
                                  ctypes.POINTER(_vp)]),
@@ -118,7 +118,8 @@ def _load():
         "lbm_hybrid_velocity": (st, [_vp, _vp, _vp]),
         "lbm_hybrid_face_flux": (st, [_vp, _vp]),
         "lbm_batch_get_march": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_set_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_batch_warm_start": (st, [_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double]),
         "lbm_batch_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -471,15 +472,16 @@ def lbm_batch_get_schedule(b: Batch):
     return {"warps_per_segment": g.value, "blocks_per_sm": bp.value, "order": o.value, "grid": gr.value}
 
 
-def lbm_batch_set_march(b: Batch, on: bool, rows_per_chunk: int = 0):
-    _check(_load().lbm_batch_set_march(b.handle, int(bool(on)), int(rows_per_chunk)))
+def lbm_batch_set_march(b: Batch, on: bool, rows_per_chunk: int = 0, warps_per_item: int = 0):
+    _check(_load().lbm_batch_set_march(b.handle, int(bool(on)), int(rows_per_chunk), int(warps_per_item)))
 
 
 def lbm_batch_get_march(b: Batch) -> dict:
-    on, ch, it, gr = (ctypes.c_int() for _ in range(4))
+    on, ch, it, gr, wg = (ctypes.c_int() for _ in range(5))
     _check(_load().lbm_batch_get_march(b.handle, ctypes.byref(on), ctypes.byref(ch), ctypes.byref(it),
-                                       ctypes.byref(gr)))
-    return {"on": bool(on.value), "rows_per_chunk": ch.value, "items": it.value, "grid": gr.value}
+                                       ctypes.byref(gr), ctypes.byref(wg)))
+    return {"on": bool(on.value), "rows_per_chunk": ch.value, "items": it.value, "grid": gr.value,
+            "warps_per_item": wg.value}
 
 
 def lbm_batch_advance(b: Batch, nsteps: int, tol: float):

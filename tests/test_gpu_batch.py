@@ -68,15 +68,18 @@ def test_batch_matches_oracle_per_instance(schedule, march):
 
 
 @pytest.mark.parametrize("n_half", [2, 4])
-def test_batch_column_march_odd_shapes(n_half):
+@pytest.mark.parametrize("two_rows", [False, True])
+def test_batch_column_march_odd_shapes(n_half, two_rows):
     """The column march on ragged strips, short chunks and tiny cavities agrees with the FP64
     oracle step by step (and the Couette instance beside them with the segment kernel)."""
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
     probs = [lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP32_PERTURB, residual_every=10)
              for g, nx, ny, kn, ub, ut in ODD]
     b = lbm.lbm_batch_init(vs, probs, stream=torch.cuda.Stream())
+    m = 2 * n_half
+    lbm.lbm_batch_set_march(b, True, 0, m // 2 if two_rows else m)     # warps per item
     info = lbm.lbm_batch_get_march(b)
-    assert info["on"] and info["items"] > 0
+    assert info["on"] and info["items"] > 0 and info["warps_per_item"] == (m // 2 if two_rows else m)
     steps = 25
     lbm.lbm_batch_advance(b, steps, 0.0)
     assert lbm.lbm_batch_poll(b) == (len(ODD), steps)
@@ -155,14 +158,16 @@ def _fp64_steady(vs, g, nx, ny, kn, ub, ut):
     return m["ux"], m["uy"]
 
 
-@pytest.mark.parametrize("n_half", [4, 2])
-def test_batch_refine_meets_1e5_per_instance(n_half):
+@pytest.mark.parametrize("n_half,two_rows", [(4, False), (2, False), (4, True)])
+def test_batch_refine_meets_1e5_per_instance(n_half, two_rows):
     """Batched FP32 march to 1e-6, then the batched refinement (FP64 defect, FP32 correction
     march of all instances in one launch) to a defect target of 1e-10: every instance's
     steady velocity field is within 1e-5 of the FP64 steady state (max |du| / u_w); step
     counts and convergence flags are unchanged; and max_sweeps = 0 changes nothing."""
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
     b = lbm.lbm_batch_init(vs, _probs(residual_every=100), stream=torch.cuda.Stream())
+    if two_rows:
+        lbm.lbm_batch_set_march(b, True, 0, n_half)
     for _ in range(400):
         lbm.lbm_batch_advance(b, 500, 1e-6)
         if lbm.lbm_batch_poll(b)[0] == 0:
@@ -224,6 +229,9 @@ def test_batch_chunk_height_does_not_change_results():
         if rows == 64:
             with pytest.raises(lbm.LBMError) as e:
                 lbm.lbm_batch_set_march(b, True, 3)
+            assert e.value.status == lbm.LBM_EINVAL
+            with pytest.raises(lbm.LBMError) as e:
+                lbm.lbm_batch_set_march(b, True, 0, 3)        # warps per item: 8 or 4 here
             assert e.value.status == lbm.LBM_EINVAL
         b.close()
     for other in states[1:]:
