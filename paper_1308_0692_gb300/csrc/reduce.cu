@@ -113,6 +113,76 @@ __global__ void moments_kernel(const T *h, long pa, long py, int nx, const Table
     out[5 * ncells + c] = 1.0 + u_ref * syy;
 }
 
+// The same moments of an FP32 state with the inner (x) sums in double-float arithmetic:
+// each product xi_x v keeps its FMA rounding residual (xi_x itself carried as hi + lo) and
+// each sum its TwoSum error, so the row sums are FP64-accurate; the outer (y) sums are FP64.
+// FP64 accumulation of all 6 x M^2 products per cell is bound by this GPU's slow FP64 pipe
+// (about 10 ms for 2048^2 x 144); this form does a ninth of the FP64 work.
+struct DFAcc {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(DFAcc &a, float x)
+{
+    const float t = a.hi + x;
+    const float z = t - a.hi;
+    a.lo += (a.hi - (t - z)) + (x - z);
+    a.hi = t;
+}
+
+// a += (xh + xl) v
+__device__ __forceinline__ void df_add_prod(DFAcc &a, float xh, float xl, float v)
+{
+    const float p = xh * v;
+    const float e = fmaf(xh, v, -p) + xl * v;
+    df_add(a, p);
+    a.lo += e;
+}
+
+__global__ void moments_f32_kernel(const float *h, long pa, long py, int nx, const TableHeader *hdr, int m, long ncells,
+                                   double u_ref, double *out)
+{
+    __shared__ float s_x[LBM_MAX_M][4];   // xi hi, lo; xi^2 hi, lo
+    if (threadIdx.x < m) {
+        const double x = hdr->xi1[threadIdx.x], x2 = x * x;
+        const float xh = (float)x, x2h = (float)x2;
+        s_x[threadIdx.x][0] = xh;
+        s_x[threadIdx.x][1] = (float)(x - (double)xh);
+        s_x[threadIdx.x][2] = x2h;
+        s_x[threadIdx.x][3] = (float)(x2 - (double)x2h);
+    }
+    __syncthreads();
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const long y = c / nx, co = y * py + (c - y * nx);
+    double s0 = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
+    for (int iy = 0; iy < m; ++iy) {
+        DFAcc r0 = {0.f, 0.f}, r1 = {0.f, 0.f}, r2 = {0.f, 0.f};
+        for (int ix = 0; ix < m; ++ix) {
+            const float v = h[(long)(iy * m + ix) * pa + co];
+            df_add(r0, v);
+            df_add_prod(r1, s_x[ix][0], s_x[ix][1], v);
+            df_add_prod(r2, s_x[ix][2], s_x[ix][3], v);
+        }
+        const double ey = hdr->xi1[iy];
+        const double a0 = (double)r0.hi + (double)r0.lo, a1 = (double)r1.hi + (double)r1.lo,
+                     a2 = (double)r2.hi + (double)r2.lo;
+        s0 += a0;
+        sx += a1;
+        sy += ey * a0;
+        sxx += a2;
+        sxy += ey * a1;
+        syy += ey * ey * a0;
+    }
+    const double rho = 1.0 + u_ref * s0;
+    out[c] = rho;
+    out[ncells + c] = u_ref * sx / rho;
+    out[2 * ncells + c] = u_ref * sy / rho;
+    out[3 * ncells + c] = 1.0 + u_ref * sxx;
+    out[4 * ncells + c] = u_ref * sxy;
+    out[5 * ncells + c] = 1.0 + u_ref * syy;
+}
+
 // rho'_w of a wall face of the cell at plane offset co; dir: 0 bottom, 1 top, 2 left, 3 right
 template <typename T>
 __device__ double wall_rho(const T *h, const TableHeader *hdr, int m, long pa, long co, int dir)
@@ -445,7 +515,7 @@ cudaError_t launch_moments(int prec, const void *h, long pa, long py, const doub
     if (prec == 0)
         moments_kernel<double><<<grid, 256, 0, s>>>((const double *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
     else
-        moments_kernel<float><<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
+        moments_f32_kernel<<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
     return cudaGetLastError();
 }
 
