@@ -666,6 +666,16 @@ def main(argv=None):
                                              f"(8 middle rows) of the 2048x2048 x 144 workload, "
                                              f"{sample['passes']} passes in {sample['seconds']:.1f} s",
                                    "single_thread_value": ups1}
+            ttr = out.get("time_to_residual")
+            if ttr and "fp64" in ttr:
+                # the oracle marching the same 32 cavities to the same residual: the FP64
+                # march's step counts (identical to the oracle's, which the configs cases
+                # check) times the updates per step at the oracle's measured rate
+                updates = float(sum(ttr["fp64"]["steps"])) * 128 * 128 * 64
+                ttr["oracle_extrapolated"] = {
+                    "seconds": updates / ups, "cores": threads,
+                    "basis": "extrapolated: FP64 march steps x 128^2 x 64 updates at the cpu_baseline rate",
+                    "vs_warm_dc": (updates / ups) / ttr["warm_dc"]["seconds"] if ttr.get("warm_dc") else None}
         print(json.dumps(out), flush=True)
     dist.close()
     return 0
