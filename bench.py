@@ -349,25 +349,38 @@ def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
     uy = torch.empty(ncells, dtype=torch.float64).pin_memory()
     dp = ctypes.POINTER(ctypes.c_double)
 
-    def one():
+    def one(rec=None):
+        t0 = time.perf_counter()
         lbm._check(lib.lbm_set_state(sim.handle, ctypes.cast(host_h.data_ptr(), dp)))
+        t1 = time.perf_counter()
         lbm.lbm_step(sim, E2E_STEPS)
-        lbm.lbm_residual(sim)
+        lbm.lbm_residual(sim)               # waits for the march
+        t2 = time.perf_counter()
         lbm._check(lib.lbm_moments(sim.handle, None, ctypes.cast(ux.data_ptr(), dp),
                                    ctypes.cast(uy.data_ptr(), dp), None, None, None, None))
+        t3 = time.perf_counter()
+        if rec is not None:
+            rec.append((t1 - t0, t2 - t1, t3 - t2))
 
     one()
-    reps = 3
+    reps = 5
+    rec = []
     dist.barrier()
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(reps):
-        one()
+        one(rec)
     torch.cuda.synchronize()
     el = time.perf_counter() - t
     value, _ = aggregate(float(nvals) * E2E_STEPS * reps, el, dist)
+    # each call's parts by the host clock (every part ends synchronised); the upload's share
+    # moves with the host<->device copy rate of the machine
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nvals * 8,
             "d2h_bytes_per_step": 2 * ncells * 8 + 32,
+            "ms_per_call": el / reps * 1e3,
+            "calls_ms": [{"set_state": round(p[0] * 1e3, 2), "step_and_residual": round(p[1] * 1e3, 2),
+                          "moments": round(p[2] * 1e3, 2)} for p in rec],
+            "h2d_gbs_in_set_state": nvals * 8 / min(p[0] for p in rec) / 1e9,
             "definition": f"one API call = lbm_set_state(host FP64, pinned) + lbm_step({E2E_STEPS}) + "
                           "lbm_residual + lbm_moments(ux, uy); value counts the marched updates"}
 
