@@ -195,14 +195,15 @@ def _traffic_record(kernel_key: str):
     return rec.get("dram_bytes_per_launch")
 
 
-VARIANTS = [(4, 0), (6, 0), (6, 2), (6, 3), (6, 4), (6, 5), (12, 4), (12, 5)]
+VARIANTS = [(4, 0), (6, 0), (6, 2), (6, 3), (6, 4), (6, 5), (6, 6), (6, 7), (12, 4), (12, 5)]
 LOAD_PATHS = ["registers", "prefetch", "tma", "tma+walls merged", "column march (4 row slots)",
-              "column march (5 row slots)"]
+              "column march (5 row slots)", "column march (2 row slots, 2 blocks per SM)",
+              "column march (4 row slots, relaxation deferred by one row)"]
 
 
 def choose_variant(sim, stream, args):
     """Autotune the step kernel on the workload itself: warps per segment x load path
-    (0 registers, 2 TMA-staged halo, 3 the same with the walls in one launch, 4/5 the
+    (0 registers, 2 TMA-staged halo, 3 the same with the walls in one launch, 4 to 7 the
     TMA column march), a few timed steps each; or the forced --variant."""
     import torch
 

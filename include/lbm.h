@@ -180,10 +180,13 @@ lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
  * 2 TMA (bulk asynchronous copies into shared memory, FP32 cavities with nx and the cell
  * count multiples of 4 and the planar state layout; M = 8 or 12), 3 as 2 with the wall
  * segments in the same launch,
- * 4 and 5 the interior as a column march (persistent blocks march 64-cell strips row by
- * row, each row's lines copied once by TMA into a ring of 4 (path 4) or 5 (path 5) row
- * slots; FP32 cavities with nx a multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12
- * warps, M = 8 with 2 or 4 warps (path 5)).
+ * 4 to 7 the interior as a column march (persistent blocks march 64-cell strips row by
+ * row, each row's lines copied once by TMA into a ring of 4 (path 4), 5 (path 5) or 2
+ * (path 6, two blocks per SM) row slots; path 7 is path 4 with each row's relaxation
+ * deferred until after the next row's transport, its moments exchanged through mbarrier
+ * phases instead of a block barrier (steps without the residual); FP32 cavities with nx a
+ * multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12 warps (6 only for paths 6 and
+ * 7), M = 8 with 2 or 4 warps (path 5)).
  * It changes speed, not results beyond rounding order.
  * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
  * without a compiled kernel.  Used by the autotuner.  Call between steps only. */

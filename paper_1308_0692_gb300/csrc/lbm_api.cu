@@ -24,10 +24,11 @@ cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s
 cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s,
                                bool merged);
 cudaError_t prepare_step_f32_tma(int m, int g);
-cudaError_t launch_step_f32_march(int m, int g, int slots, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-cudaError_t prepare_step_f32_march(int m, int g, int slots, int *grid);
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool resid, const StepArgs &a, int grid,
+                                  cudaStream_t s);
+cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int *grid);
 cudaError_t launch_step_so(int prec, int m, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-bool march_supported(int m, int g, int slots);
+bool march_supported(int m, int g, int slots, bool defer);
 int defect_lanes(int m);
 int correct_lanes(int m);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
@@ -53,7 +54,7 @@ struct lbm_sim {
     int splitting;        // LBM_SPLIT_LIE (stored state h) or LBM_SPLIT_STRANG[_EXACT] (stored g = R(dt/2) h)
     int order;            // transport order: 1 (first-order upwind, the paper's) or 2
     int grid;             // blocks of the bulk step kernel
-    int march_grid;       // persistent blocks of the column-march kernel (load paths 4, 5)
+    int march_grid;       // persistent blocks of the column-march kernel (load paths 4 to 7)
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
     int *wall_segs;       // device list of wall segments for the current lanes
     int wall_cap;
@@ -443,6 +444,11 @@ int default_lanes_per_cell(int prec, int m)
     return m <= 6 ? 1 : (m == 8 ? 2 : 4);
 }
 
+// row slots of the column march's ring for load paths 4 (four), 5 (five), 6 (two slots,
+// two blocks per SM) and 7 (four, relaxation deferred by one row)
+static int march_slots(int pf) { return pf == 6 ? 2 : pf == 7 ? 4 : pf; }
+static bool march_defer(int pf) { return pf == 7; }
+
 bool step_supported(int prec, int m, int g, int pf)
 {
     static const int f64[][3] = {{3, 1, 0}, {4, 1, 0}, {4, 2, 0}, {6, 1, 0}, {6, 2, 0}, {4, 2, 1}, {6, 2, 1}, {8, 2, 0}, {8, 4, 0}, {12, 3, 0}, {12, 4, 0}, {12, 6, 0}, {8, 4, 1}, {12, 6, 1}};
@@ -453,7 +459,7 @@ bool step_supported(int prec, int m, int g, int pf)
         for (auto &v : tma) if (v[0] == m && v[1] == g) return true;
         return false;
     }
-    if (pf == 4 || pf == 5) return prec == LBM_FP32_PERTURB && march_supported(m, g, pf);
+    if (pf >= 4 && pf <= 7) return prec == LBM_FP32_PERTURB && march_supported(m, g, march_slots(pf), march_defer(pf));
     if (prec == LBM_FP64) {
         for (auto &v : f64) if (v[0] == m && v[1] == g && v[2] == pf) return true;
     } else {
@@ -466,7 +472,7 @@ cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepAr
                         cudaStream_t s)
 {
     if (pf == 2 || pf == 3) return launch_step_f32_tma(m, g, resid, a, grid, s, pf == 3);
-    if (pf == 4 || pf == 5) return launch_step_f32_march(m, g, pf, resid, a, grid, s);
+    if (pf >= 4 && pf <= 7) return launch_step_f32_march(m, g, march_slots(pf), march_defer(pf), resid, a, grid, s);
     if (prec == LBM_FP64)
         return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
                       : launch_step_f64_small(m, g, pf, resid, a, grid, s);
@@ -944,7 +950,7 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (prefetch < 0 || prefetch > 5) return fail(LBM_EINVAL, "load path must be 0 to 5");
+    if (prefetch < 0 || prefetch > 7) return fail(LBM_EINVAL, "load path must be 0 to 7");
     if (s->order == 2)
         return fail(LBM_EUNSUPPORTED, "the second-order transport has one kernel variant (lbm_set_transport)");
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
@@ -962,7 +968,8 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
     }
     if (prefetch >= 4) {
         int grid = 0;
-        cudaError_t e = prepare_step_f32_march(s->vs.m, warps_per_segment, prefetch, &grid);
+        cudaError_t e = prepare_step_f32_march(s->vs.m, warps_per_segment, march_slots(prefetch), march_defer(prefetch),
+                                               &grid);
         if (e != cudaSuccess) return cuda_fail(e, "enabling the column-march kernel's shared memory");
         if (grid <= 0) return fail(LBM_EUNSUPPORTED, "the column-march kernel does not fit on an SM");
         s->march_grid = grid;

@@ -1,41 +1,46 @@
 // FP32 step with the interior as a TMA-staged column march (instantiation list; the kernel
 // is in step_march.cuh).  Load path 4 keeps two rows of copies in flight per warp (ring of
-// four row slots), load path 5 three (ring of five).
+// four row slots), load path 5 three (ring of five), load path 6 none (ring of two, two
+// blocks per SM), load path 7 is path 4 with the relaxation of each row deferred until
+// after the next row's transport (steps without the residual).
 #include "step_march.cuh"
 
 using namespace lbmk;
 
 #define LBM_MARCH_LIST(X) \
-    X(12, 6, 4)           \
-    X(12, 6, 5)           \
-    X(12, 12, 4)          \
-    X(12, 12, 5)          \
-    X(8, 4, 5)            \
-    X(8, 2, 5)
+    X(12, 6, 4, false)    \
+    X(12, 6, 5, false)    \
+    X(12, 6, 2, false)    \
+    X(12, 6, 4, true)     \
+    X(12, 12, 4, false)   \
+    X(12, 12, 5, false)   \
+    X(8, 4, 5, false)     \
+    X(8, 2, 5, false)
 
-bool march_supported(int m, int g, int slots)
+bool march_supported(int m, int g, int slots, bool defer)
 {
-#define LBM_MARCH_HAVE(M_, G_, S_) \
-    if (m == M_ && g == G_ && slots == S_) return true;
+#define LBM_MARCH_HAVE(M_, G_, S_, D_) \
+    if (m == M_ && g == G_ && slots == S_ && defer == D_) return true;
     LBM_MARCH_LIST(LBM_MARCH_HAVE)
 #undef LBM_MARCH_HAVE
     return false;
 }
 
-cudaError_t launch_step_f32_march(int m, int g, int slots, bool resid, const StepArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool resid, const StepArgs &a, int grid,
+                                  cudaStream_t s)
 {
-#define LBM_MARCH_LAUNCH(M_, G_, S_)                                                  \
-    if (m == M_ && g == G_ && slots == S_)                                            \
-        return resid ? launch_march<M_, G_, S_, true>(a, grid, s) : launch_march<M_, G_, S_, false>(a, grid, s);
+#define LBM_MARCH_LAUNCH(M_, G_, S_, D_)                                                          \
+    if (m == M_ && g == G_ && slots == S_ && defer == D_)                                         \
+        return resid ? launch_march<M_, G_, S_, D_, true>(a, grid, s) : launch_march<M_, G_, S_, D_, false>(a, grid, s);
     LBM_MARCH_LIST(LBM_MARCH_LAUNCH)
 #undef LBM_MARCH_LAUNCH
     return cudaErrorInvalidValue;
 }
 
-cudaError_t prepare_step_f32_march(int m, int g, int slots, int *grid)
+cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int *grid)
 {
-#define LBM_MARCH_PREP(M_, G_, S_) \
-    if (m == M_ && g == G_ && slots == S_) return prepare_march<M_, G_, S_>(grid);
+#define LBM_MARCH_PREP(M_, G_, S_, D_) \
+    if (m == M_ && g == G_ && slots == S_ && defer == D_) return prepare_march<M_, G_, S_, D_>(grid);
     LBM_MARCH_LIST(LBM_MARCH_PREP)
 #undef LBM_MARCH_PREP
     return cudaErrorInvalidValue;

@@ -14,7 +14,8 @@
 //     rows y-1, y, y+1 resident, so the upwind y neighbour of row y is a line that was
 //     copied for row y-1 or y+1 anyway: no second read of it, unlike the segment kernels
 //     (which read every line twice: once as own cells, once as a neighbour row).  S-2 rows
-//     of copies stay in flight ahead of the arithmetic.
+//     of copies stay in flight ahead of the arithmetic; with S = 2 none do, and two blocks
+//     share an SM instead.
 //   * The interior is cut into items (strip, chunk of rows), numbered chunk-major so that
 //     blocks running at the same time work on neighbouring strips of the same rows (their
 //     x halos are then L2 hits).  The grid is persistent (one or more blocks per SM); a
@@ -48,11 +49,19 @@ struct MarchShape {
     static constexpr int SLOT = NV * LINE;         // floats of one warp's row slot
     static constexpr int THREADS = 32 * G;
     static constexpr int SMEM = S * G * SLOT * 4 + S * G * 8;
+    // a ring of two slots (the own row and its upwind row, nothing in flight ahead) is small
+    // enough for two blocks per SM: the second block computes while the first waits
+    static constexpr int MIN_BLOCKS = S == 2 ? 2 : 1;
 };
 
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // first row of chunk k of the interior rows [1, ny - 2] cut into nchunks near-equal chunks
@@ -61,18 +70,28 @@ __device__ __forceinline__ int march_row0(int k, int rows, int nchunks)
     return 1 + (int)(((long)k * rows) / nchunks);
 }
 
-template <int M, int G, int S, bool RESID>
-__global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_kernel(const StepArgs a)
+template <int M, int G, int S, bool RESID, bool DEFER>
+__global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, MarchShape<M, G, S>::MIN_BLOCKS)
+step_march_kernel(const StepArgs a)
 {
     using Sh = MarchShape<M, G, S>;
+    // deferred relaxation (steps without the residual): row t's moment partials are published
+    // through an mbarrier phase and row t - 1 is relaxed after row t's transport, so a warp
+    // meets the slowest warp's partials one transport later than at a block barrier
+    constexpr bool DEF = DEFER && !RESID;
+    constexpr int NMOM = DEF ? 4 : 2;
     constexpr int RPL = Sh::RPL, NV = Sh::NV, LINE = Sh::LINE, HALF = M / 2;
     static_assert(M % 2 == 0 && (M / 2) % 2 == 0, "even M with velocity pairs on one side of xi = 0");
     static_assert(HALF % RPL == 0, "the velocity rows of a warp share the sign of xi_y");
     static_assert(NV <= 32, "one bulk copy per lane and row");
-    static_assert(S >= 3, "rows y-1, y, y+1 resident");
+    // the velocities of a warp share the sign of xi_y, so it reads two rows per step (y and
+    // its upwind neighbour); a copy overwrites the slot of the row before those two, which the
+    // warp finished reading in its previous row step
+    static_assert(S >= 2, "own row and upwind row resident");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ float2 s_mom[2][3][G][32];
+    __shared__ float2 s_mom[NMOM][3][G][32];
+    __shared__ uint64_t s_mbar[2];
     __shared__ int s_items[4];
     __shared__ int s_abort;
     __shared__ double s_red[2][G];
@@ -99,6 +118,11 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
         s_items[1] = (int)gridDim.x + (int)blockIdx.x;
         s_items[2] = 2 * (int)gridDim.x + (int)blockIdx.x;
         s_abort = 0;
+        if (DEF) {
+            mbar_init(&s_mbar[0], Sh::THREADS);
+            mbar_init(&s_mbar[1], Sh::THREADS);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
     }
     if (lane == 0) {
         for (int j = 0; j < S; ++j) mbar_init(&bars[j], 1);
@@ -183,6 +207,35 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
     const float om = a.omega_f;
     const float2 b2 = make_float2(a.b_f, a.b_f);
     double psd = 0.0, psn = 0.0;
+    // deferred relaxation: the transported row waiting for its moments, its first cell
+    float2 hp[NV];
+    long pcell = 0;
+    long t = 0;        // rows transported by this block
+    // relaxation and store of the deferred row from the moment partials in buffer bt
+    auto relax_deferred = [&](int bt, long cell) {
+        float2 r2 = make_float2(0.f, 0.f), x2 = r2, y2 = r2;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            r2 = __fadd2_rn(r2, s_mom[bt][0][q][lane]);
+            x2 = __fadd2_rn(x2, s_mom[bt][1][q][lane]);
+            y2 = __fadd2_rn(y2, s_mom[bt][2][q][lane]);
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const float wom = om * a.w1_f[iy];
+            const float xiy = a.xi_f[iy];
+            const float2 q2 = __fmul2_rn(make_float2(wom, wom), __ffma2_rn(make_float2(xiy, xiy), y2, r2));
+            const float2 jj2 = __fmul2_rn(make_float2(wom, wom), x2);
+            float *rowp = hn + (long)(iy * M) * ncells + cell;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const int k = r * M + ix;
+                const float2 tt = __ffma2_rn(xi2[ix], jj2, q2);
+                *reinterpret_cast<float2 *>(rowp + (long)ix * ncells) = __ffma2_rn(w2[ix], tt, __fmul2_rn(b2, hp[k]));
+            }
+        }
+    };
 
     while (c_item < nitems) {
         // keep S - 2 rows of copies ahead of the rows being computed
@@ -194,6 +247,8 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
                 atomicExch(a.status, 1);
                 s_abort = 1;
             }
+            // deferred: leave now (the other warps' next moment wait runs out and they leave)
+            if (DEF) break;
         }
         const long jo = ypos ? gb + c_u + 1 : gb + c_u;      // own row y
         const long jy = ypos ? gb + c_u : gb + c_u + 1;      // upwind row y -/+ 1
@@ -222,9 +277,18 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
                     const float2 hx = (ix >= M - HALF) ? make_float2(lo[3 + 2 * lane], hc.x)     // xi_x > 0: x - 1
                                                        : make_float2(hc.y, lo[6 + 2 * lane]);    // xi_x < 0: x + 1
                     const float2 hy = *reinterpret_cast<const float2 *>(ynb + k * LINE + 4 + 2 * lane);
-                    float2 v = __fmul2_rn(a0r[k], hc);
-                    v = __ffma2_rn(nux2[ix], hx, v);
-                    v = __ffma2_rn(nuy2, hy, v);
+                    float2 v;
+                    if constexpr (DEF) {
+                        // h + nu_x (h_x - h) + nu_y (h_y - h): no per-velocity coefficient held
+                        // in registers (they hold the deferred row instead)
+                        const float2 m1 = make_float2(-1.f, -1.f);     // x - h as fma(h, -1, x)
+                        v = __ffma2_rn(nux2[ix], __ffma2_rn(hc, m1, hx), hc);
+                        v = __ffma2_rn(nuy2, __ffma2_rn(hc, m1, hy), v);
+                    } else {
+                        v = __fmul2_rn(a0r[k], hc);
+                        v = __ffma2_rn(nux2[ix], hx, v);
+                        v = __ffma2_rn(nuy2, hy, v);
+                    }
                     hs[k] = v;
                     R2[ix % NACC] = __fadd2_rn(R2[ix % NACC], v);
                     X2[ix % NACC] = __ffma2_rn(xi2[ix], v, X2[ix % NACC]);
@@ -236,6 +300,41 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
                 jx2 = __fadd2_rn(jx2, X);
                 jy2 = __ffma2_rn(make_float2(xiy, xiy), R, jy2);
             }
+        }
+        if constexpr (DEF) {
+            // publish row t, then relax row t - 1 (its partials were published one transport ago)
+            const int bt = (int)(t & 3);
+            s_mom[bt][0][g][lane] = rho2;
+            s_mom[bt][1][g][lane] = jx2;
+            s_mom[bt][2][g][lane] = jy2;
+            mbar_arrive(&s_mbar[t & 1]);
+            if (t > 0) {
+                const long tp = t - 1;
+                ok = mbar_wait_bounded(&s_mbar[tp & 1], (unsigned)((tp >> 1) & 1), 2000000000LL);
+                ok = __all_sync(FULL, ok);
+                if (!ok) {
+                    if (lane == 0) {
+                        atomicExch(a.status, 1);
+                        s_abort = 1;
+                    }
+                    break;
+                }
+                relax_deferred((int)(tp & 3), pcell);
+            }
+            const int y = c_row0 + c_u;
+            pcell = (long)y * nx + 32 + 64L * c_strip + 2 * lane;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) hp[k] = hs[k];
+            ++t;
+            if (++c_u == c_len) {
+                gb += c_len + 1;
+                c_u = 0;
+                ++c_pos;
+                c_item = s_items[c_pos & 3];
+                if (c_item < nitems) c_decode();
+                if (threadIdx.x == 0) s_items[(c_pos + 2) & 3] = first_dyn + atomicAdd(a.counters, 1);
+            }
+            continue;
         }
         s_mom[par][0][g][lane] = rho2;
         s_mom[par][1][g][lane] = jx2;
@@ -293,6 +392,14 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
         }
     }
 
+    // the last deferred row
+    if (DEF && ok && t > 0) {
+        const long tp = t - 1;
+        ok = __all_sync(FULL, mbar_wait_bounded(&s_mbar[tp & 1], (unsigned)((tp >> 1) & 1), 2000000000LL));
+        if (ok) relax_deferred((int)(tp & 3), pcell);
+        else if (lane == 0) atomicExch(a.status, 1);
+    }
+
     // copies still in flight (abort path) must land before the block's shared memory goes
     for (; waited < nl; ++waited) mbar_wait_bounded(&bars[waited % S], (unsigned)((waited / S) & 1), 2000000000LL);
 
@@ -328,19 +435,25 @@ __global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, 1) step_march_ke
     }
 }
 
-template <int M, int G, int S>
+template <int M, int G, int S, bool DEFER>
 cudaError_t prepare_march(int *grid)
 {
     constexpr int SMEM = MarchShape<M, G, S>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true>,
+    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true, DEFER>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM);
+        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false, DEFER>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     int per_sm = 0, dev = 0, sms = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false, DEFER>,
                                                           MarchShape<M, G, S>::THREADS, SMEM);
+    if (e == cudaSuccess && DEFER) {
+        int per_sm_resid = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, step_march_kernel<M, G, S, true, DEFER>,
+                                                          MarchShape<M, G, S>::THREADS, SMEM);
+        if (per_sm_resid < per_sm) per_sm = per_sm_resid;
+    }
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) *grid = per_sm > 0 ? per_sm * sms : 0;
@@ -361,11 +474,11 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_wall_beside_march_kern
 
 // March kernel over `grid` persistent blocks, and beside it the wall kernel over the wall
 // segments (programmatic dependent launch).
-template <int M, int G, int S, bool RESID>
+template <int M, int G, int S, bool DEFER, bool RESID>
 cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
 {
     constexpr int SMEM = MarchShape<M, G, S>::SMEM;
-    step_march_kernel<M, G, S, RESID><<<grid, MarchShape<M, G, S>::THREADS, SMEM, s>>>(a);
+    step_march_kernel<M, G, S, RESID, DEFER><<<grid, MarchShape<M, G, S>::THREADS, SMEM, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_wall_segs == 0) return e;
     StepArgs b = a;
