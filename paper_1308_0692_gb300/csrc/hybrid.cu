@@ -14,8 +14,10 @@
 //     exchange through that face equals it (sum w = sum xi_x^2 w = 1 for the full-range
 //     rule);
 //   * relaxation towards w (rho + xi . j) in the cell's own set (Eqs. 1, 5-7).
-// One warp per cell; the state is packed cell after cell, each cell's values in its own
-// set's velocity order (a = iy * M + ix).  dt = cfl dy / max |xi_y| over the sets present,
+// Cells with an interface face: one warp per cell (projections in shared memory); all other
+// cells: a lane group per cell, several cells per warp, the upwind values read directly.  The
+// state is packed cell after cell, each cell's values in its own set's velocity order
+// (a = iy * M + ix).  dt = cfl dy / max |xi_y| over the sets present,
 // dt <= Kn.
 #include <algorithm>
 #include <cmath>
@@ -38,14 +40,21 @@ constexpr int HWARPS = 4;      // cells per block
 
 struct HybSet {
     int n;
+    int lanes;                 // lanes per cell in the plain-cell kernel: n rounded up to a power of two, <= 32
     double xi_x[HMAXV], xi_y[HMAXV], w[HMAXV];
     double he_x[HMAXQ + 1][HMAXV], he_y[HMAXQ + 1][HMAXV];
     double d_x, d_y;           // sums over xi > 0 of xi w per axis (wall-flux normalisers, Eq. 9)
+    double nux[HMAXV], nuy[HMAXV];  // |xi_x| dt / dx, |xi_y| dt / dy (set on the host once dt is known)
 };
+
+constexpr int HMAXF = 36;      // full-range N <= 6
 
 struct HybTables {
     HybSet set[2];             // 0: half-range, 1: full-range
     double inv_fact[HMAXQ + 1];
+    // projection matrices, transposed: pt[t][a * n_s + b] = w_b sum_{m,n} He_m(xi_x,a) He_n(xi_y,a)
+    // He_m(xi_x,b) He_n(xi_y,b) / (m! n!), a a velocity of set t, b of the other set s = 1 - t
+    double pt[2][HMAXV * HMAXF];
 };
 
 struct HybArgs {
@@ -68,32 +77,43 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Hermite coefficients of distribution h (set T) into coef[(order+1)^2] (lane-parallel: one
-// coefficient per lane, summed over the velocities in order), then the projection onto the
-// velocities of S into out[]: out_b = w_b sum c_mn He_m(xi_x,b) He_n(xi_y,b).
-__device__ void project_warp(const HybTables &tb, const HybSet &T, const double *h, const HybSet &S, int order,
-                             double *coef, double *out)
+// Tensor Hermite projection of order N - 1 of distribution h (set ti) onto the other set,
+// into out[]: out_b = w_b sum_{m,n} c_mn He_m(xi_x,b) He_n(xi_y,b) with
+// c_mn = sum_a h_a He_m(xi_x,a) He_n(xi_y,a) / (m! n!), applied as the precomputed matrix.
+// Target sets of more than 16 velocities: each lane whole sums for outputs lane, lane + 32,
+// ...; smaller ones: the source velocities split over 32 / lanes lane groups, the partial sums
+// combined by shuffles (every lane of the warp calls this).
+__device__ void project_warp(const HybTables &tb, int ti, const double *h, double *out)
 {
-    const int lane = threadIdx.x & 31, nq = order + 1;
-    for (int l = lane; l < nq * nq; l += 32) {
-        const int m = l / nq, n = l - m * nq;
-        double c = 0.0;
-        for (int a = 0; a < T.n; ++a) c += h[a] * T.he_x[m][a] * T.he_y[n][a];
-        coef[l] = c * tb.inv_fact[m] * tb.inv_fact[n];
-    }
-    __syncwarp();
-    for (int b = lane; b < S.n; b += 32) {
-        double v = 0.0;
-        for (int m = 0; m < nq; ++m)
-            for (int n = 0; n < nq; ++n) v += coef[m * nq + n] * S.he_x[m][b] * S.he_y[n][b];
-        out[b] = S.w[b] * v;
+    const int lane = threadIdx.x & 31;
+    const HybSet &T = tb.set[ti], &S = tb.set[ti ^ 1];
+    const double *pt = tb.pt[ti];
+    const int nt = T.n, ns = S.n;
+    if (ns > 16) {
+        for (int b = lane; b < ns; b += 32) {
+            double s4[4] = {0.0, 0.0, 0.0, 0.0};
+            int a = 0;
+            for (; a + 4 <= nt; a += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s4[q] += pt[(a + q) * ns + b] * h[a + q];
+            }
+            for (; a < nt; ++a) s4[0] += pt[a * ns + b] * h[a];
+            out[b] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+        }
+    } else {
+        const int ls = S.lanes, parts = 32 / ls, part = lane / ls, b = lane - part * ls;
+        double acc = 0.0;
+        if (b < ns)
+            for (int a = part; a < nt; a += parts) acc += pt[a * ns + b] * h[a];
+        for (int o = ls; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (part == 0 && b < ns) out[b] = acc;
     }
     __syncwarp();
 }
 
 // Values of neighbour cell k as seen by a cell of set sj, into buf[0..S.n): its own values
 // for the same set, else their projection.
-__device__ void neighbour_values(const HybArgs &a, int k, int sj, double *coef, double *buf)
+__device__ void neighbour_values(const HybArgs &a, int k, int sj, double *buf)
 {
     const HybTables &tb = *a.tab;
     const HybSet &S = tb.set[sj];
@@ -103,7 +123,7 @@ __device__ void neighbour_values(const HybArgs &a, int k, int sj, double *coef, 
         for (int b = threadIdx.x & 31; b < S.n; b += 32) buf[b] = hk[b];
         __syncwarp();
     } else {
-        project_warp(tb, tb.set[sk], hk, S, a.order, coef, buf);
+        project_warp(tb, sk, hk, buf);
     }
 }
 
@@ -146,39 +166,36 @@ __device__ void face_moments(const HybSet &S, const double *v, int axis, bool po
 }
 
 struct HybShared {
-    double coef[HWARPS][(HMAXQ + 1) * (HMAXQ + 1)];
     double nbv[HWARPS][4][HMAXV];   // left, right, below, above: upwind values in the cell's set
     double ph[HWARPS][HMAXV], nb[HWARPS][HMAXV];
 };
 
-__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, double dt, double dx, double dy,
-                                                                   int resid)
+// A cell with an interface face (a neighbour in the other set): one warp, warp `wi` of the
+// block's shared buffers.
+__device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, double dt, double dx, double dy,
+                               int resid)
 {
-    __shared__ HybShared sh;
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int c = blockIdx.x * HWARPS + wi;
+    const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny;
-    if (c >= nx * ny) return;                    // whole warps; only warp-level sync below
     const HybTables &tb = *a.tab;
     const int sj = a.half[c] ? 0 : 1;
     const HybSet &S = tb.set[sj];
     const HybSet &H = tb.set[0];
     const double *hc = a.h + a.off[c];
     const int x = c % nx, y = c / nx;
-    double *coef = sh.coef[wi];
     double(*nbv)[HMAXV] = sh.nbv[wi];
     // upwind values: x (cavity only) and y neighbours in this cell's set, or the walls' ghosts;
     // the four faces as (axis, side, neighbour or -1)
     int nbc[4] = {-1, -1, -1, -1};
     if (a.cavity) {
-        if (x > 0) neighbour_values(a, nbc[0] = c - 1, sj, coef, nbv[0]);
+        if (x > 0) neighbour_values(a, nbc[0] = c - 1, sj, nbv[0]);
         else wall_ghost(a, S, hc, 2, nbv[0]);
-        if (x < nx - 1) neighbour_values(a, nbc[1] = c + 1, sj, coef, nbv[1]);
+        if (x < nx - 1) neighbour_values(a, nbc[1] = c + 1, sj, nbv[1]);
         else wall_ghost(a, S, hc, 3, nbv[1]);
     }
-    if (y > 0) neighbour_values(a, nbc[2] = c - nx, sj, coef, nbv[2]);
+    if (y > 0) neighbour_values(a, nbc[2] = c - nx, sj, nbv[2]);
     else wall_ghost(a, S, hc, 0, nbv[2]);
-    if (y < ny - 1) neighbour_values(a, nbc[3] = c + nx, sj, coef, nbv[3]);
+    if (y < ny - 1) neighbour_values(a, nbc[3] = c + nx, sj, nbv[3]);
     else wall_ghost(a, S, hc, 1, nbv[3]);
     // interface faces of a full-range cell: mass and momentum exchange made equal to the
     // half-range evaluation of the face
@@ -188,12 +205,12 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs 
         for (int f = 0; f < 4; ++f) any_if |= nbc[f] >= 0 && a.half[nbc[f]];
     if (any_if) {
         double *ph = sh.ph[wi], *nb = sh.nb[wi];
-        project_warp(tb, S, hc, H, a.order, coef, ph);          // this cell seen in H
+        project_warp(tb, 1, hc, ph);                            // this cell seen in H
         for (int f = 0; f < 4; ++f) {
             if (nbc[f] < 0 || !a.half[nbc[f]]) continue;
             const int axis = f >> 1;
             const bool lower = (f & 1) == 0;                  // the neighbour is on the lower side
-            neighbour_values(a, nbc[f], 0, coef, nb);         // its own half-range values
+            neighbour_values(a, nbc[f], 0, nb);               // its own half-range values
             double up[3], dn[3], got[3], sent[3];
             face_moments(H, lower ? nb : ph, axis, true, up);
             face_moments(H, lower ? ph : nb, axis, false, dn);
@@ -219,10 +236,10 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs 
             double hx = h0, nux = 0.0;
             if (a.cavity) {
                 hx = ex > 0 ? nbv[0][b] : (ex < 0 ? nbv[1][b] : h0);
-                nux = fabs(ex) * dt / dx;
+                nux = S.nux[b];
             }
             const double hy = ey > 0 ? nbv[2][b] : (ey < 0 ? nbv[3][b] : h0);
-            const double nuy = fabs(ey) * dt / dy;
+            const double nuy = S.nuy[b];
             v = h0 - nux * (h0 - hx) - nuy * (h0 - hy);
             if (any_if) v += (cr[0] + cr[1] * ex + cr[2] * ey) * S.w[b];
             rho += v;
@@ -258,17 +275,154 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs 
     }
 }
 
-// residual sums in cell order
-__global__ void hybrid_finalize_kernel(const double *part, int ny, double *out)
+// sum over the `width` lanes of an aligned lane group (width a power of two <= 32)
+__device__ __forceinline__ double group_sum(double v, int width)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double d = 0.0, n = 0.0;
-        for (int j = 0; j < ny; ++j) {
-            d += part[2 * j];
-            n += part[2 * j + 1];
+    for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int HMAXPL = (HMAXV + 31) / 32;     // velocities per lane in the plain-cell kernel
+
+// Cells whose existing neighbours all carry the cell's own set (no interface face): the
+// same update as hybrid_step_kernel without projections.  A warp takes a task, a run of
+// consecutive cells of one set (contiguous in the packed state); a group of S.lanes lanes
+// takes a cell, lane g its velocities g, g + lanes, ...; the upwind values are read straight
+// from the neighbour cells, the wall densities and moments are sums over the group.
+__device__ void plain_task(const HybArgs &a, const int2 tk, int resid)
+{
+    const int lane = threadIdx.x & 31;
+    const HybTables &tb = *a.tab;
+    const HybSet &S = tb.set[a.half[tk.x] ? 0 : 1];
+    const int n = S.n, L = S.lanes;
+    const int sub = lane / L, g = lane - sub * L;
+    const bool on = sub < tk.y;
+    const int c = tk.x + (on ? sub : 0);         // idle groups repeat the first cell and store nothing
+    const int nx = a.nx, ny = a.ny, x = c % nx, y = c / nx;
+    const double *hc = a.h + a.off[c];
+    const bool cav = a.cavity != 0;
+    const bool wl = cav && x == 0, wr = cav && x == nx - 1, wb = y == 0, wt = y == ny - 1;
+    const double *hl = (cav && !wl) ? a.h + a.off[c - 1] : hc;
+    const double *hr = (cav && !wr) ? a.h + a.off[c + 1] : hc;
+    const double *hd = !wb ? a.h + a.off[c - nx] : hc;
+    const double *hu = !wt ? a.h + a.off[c + nx] : hc;
+    double hv[HMAXPL];
+    double pw[4] = {0.0, 0.0, 0.0, 0.0};         // outflow through the bottom, top, left, right walls
+#pragma unroll
+    for (int i = 0; i < HMAXPL; ++i) {
+        const int b = g + L * i;
+        hv[i] = 0.0;
+        if (b < n) {
+            const double v = hc[b], ex = S.xi_x[b], ey = S.xi_y[b];
+            hv[i] = v;
+            if (ey < 0) pw[0] -= ey * v;
+            if (ey > 0) pw[1] += ey * v;
+            if (ex < 0) pw[2] -= ex * v;
+            if (ex > 0) pw[3] += ex * v;
         }
-        out[0] = d;
-        out[1] = n;
+    }
+    // wall densities (Eq. 9 as a flux balance over the cell's set)
+    double rw[4] = {0.0, 0.0, 0.0, 0.0};
+    if (__any_sync(0xffffffffu, wl || wr || wb || wt)) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) rw[f] = group_sum(pw[f], L) / (f < 2 ? S.d_y : S.d_x);
+    }
+    const double ub = a.u_bottom, ut = a.u_top;
+    double hs[HMAXPL];
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int i = 0; i < HMAXPL; ++i) {
+        const int b = g + L * i;
+        double v = 0.0;
+        if (b < n) {
+            const double ex = S.xi_x[b], ey = S.xi_y[b], wb_ = S.w[b];
+            const double h0 = hv[i];
+            double hx = h0, nux = 0.0;
+            if (cav) {
+                if (ex > 0) hx = wl ? wb_ * rw[2] : hl[b];          // side walls at rest
+                else if (ex < 0) hx = wr ? wb_ * rw[3] : hr[b];
+                nux = S.nux[b];
+            }
+            double hy = h0;
+            if (ey > 0) hy = wb ? wb_ * (rw[0] * (1.0 + ex * ub) + ex * ub / a.u_ref) : hd[b];
+            else if (ey < 0) hy = wt ? wb_ * (rw[1] * (1.0 + ex * ut) + ex * ut / a.u_ref) : hu[b];
+            const double nuy = S.nuy[b];
+            v = h0 - nux * (h0 - hx) - nuy * (h0 - hy);
+            rho += v;
+            jx += ex * v;
+            jy += ey * v;
+        }
+        hs[i] = v;
+    }
+    rho = group_sum(rho, L);
+    jx = group_sum(jx, L);
+    jy = group_sum(jy, L);
+    double *out = a.hn + a.off[c];
+    double pd = 0.0, pn = 0.0;
+#pragma unroll
+    for (int i = 0; i < HMAXPL; ++i) {
+        const int b = g + L * i;
+        if (b < n) {
+            const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
+            const double o = hs[i] - a.omega * (hs[i] - heq);
+            if (on) out[b] = o;
+            const double d = o - hv[i];
+            pd += d * d;
+            pn += o * o;
+        }
+    }
+    if (resid) {
+        pd = group_sum(pd, L);
+        pn = group_sum(pn, L);
+        if (on && g == 0) {
+            a.part[2 * c] = pd;
+            a.part[2 * c + 1] = pn;
+        }
+    }
+}
+
+// One step: the blocks for the interface cells first (their projections are the long
+// latency chains), then the plain-cell tasks, so that both run side by side in one launch.
+__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, const int *cells, int ncells,
+                                                                   const int2 *tasks, int ntasks, double dt, double dx,
+                                                                   double dy, int resid)
+{
+    __shared__ HybShared sh;
+    const int wi = threadIdx.x >> 5;
+    const int if_blocks = (ncells + HWARPS - 1) / HWARPS;
+    if ((int)blockIdx.x < if_blocks) {
+        const int ci = (int)blockIdx.x * HWARPS + wi;
+        if (ci < ncells) interface_cell(a, sh, wi, cells[ci], dt, dx, dy, resid);     // whole warps
+    } else {
+        const int t = ((int)blockIdx.x - if_blocks) * HWARPS + wi;
+        if (t < ntasks) plain_task(a, tasks[t], resid);
+    }
+}
+
+// residual sums over the cells: one block, each thread a fixed stride of cells, then a fixed
+// tree (the same order every call)
+constexpr int HFIN = 1024;
+__global__ void __launch_bounds__(HFIN) hybrid_finalize_kernel(const double *part, int ncells, double *out)
+{
+    __shared__ double sd[HFIN], sn[HFIN];
+    double d = 0.0, n = 0.0;
+    for (int j = threadIdx.x; j < ncells; j += HFIN) {
+        d += part[2 * j];
+        n += part[2 * j + 1];
+    }
+    sd[threadIdx.x] = d;
+    sn[threadIdx.x] = n;
+    __syncthreads();
+    for (int w = HFIN / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sd[threadIdx.x] += sd[threadIdx.x + w];
+            sn[threadIdx.x] += sn[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sd[0];
+        out[1] = sn[0];
     }
 }
 
@@ -281,12 +435,12 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const Hyb
     const int k = blockIdx.x * HWARPS + wi;
     if (k > a.ny) return;
     const HybTables &tb = *a.tab;
-    double *coef = sh.coef[wi], *lo = sh.nbv[wi][0], *hi = sh.nbv[wi][1];
+    double *lo = sh.nbv[wi][0], *hi = sh.nbv[wi][1];
     double up = 0.0, dn = 0.0;
     if (k > 0 && k < a.ny && a.half[k - 1] != a.half[k]) {
         const HybSet &H = tb.set[0];
-        neighbour_values(a, k - 1, 0, coef, lo);
-        neighbour_values(a, k, 0, coef, hi);
+        neighbour_values(a, k - 1, 0, lo);
+        neighbour_values(a, k, 0, hi);
         double mu[3], md[3];
         face_moments(H, lo, 1, true, mu);
         face_moments(H, hi, 1, false, md);
@@ -356,6 +510,9 @@ struct lbm_hybrid {
     double *h_res;           // pinned
     int cur;
     bool have_resid;
+    int n_if, n_tasks;       // interface cells, plain-cell tasks
+    int *d_if;               // [n_if] cells with an interface face
+    int2 *d_tasks;           // [n_tasks] runs of plain cells (first cell, count)
 };
 
 namespace {
@@ -369,6 +526,8 @@ bool fill_set(HybSet &S, int kind, int n, int order, double &max_y)
     const int m = (int)x.size();
     S.n = m * m;
     if (S.n > HMAXV) return false;
+    S.lanes = 1;
+    while (S.lanes < S.n && S.lanes < 32) S.lanes *= 2;
     S.d_x = S.d_y = 0.0;
     max_y = 0.0;
     for (int iy = 0; iy < m; ++iy)
@@ -450,8 +609,11 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     hb->d_h[0] = hb->d_h[1] = nullptr;
     hb->d_part = hb->d_res = nullptr;
     hb->h_res = nullptr;
-    HybTables tab;
-    std::memset(&tab, 0, sizeof tab);
+    hb->d_if = nullptr;
+    hb->d_tasks = nullptr;
+    hb->n_if = hb->n_tasks = 0;
+    std::vector<HybTables> tabv(1);     // ~130 KB: on the heap, zero-initialised
+    HybTables &tab = tabv[0];
     double my_h = 0, my_f = 0;
     if (!fill_set(tab.set[0], LBM_HALF_RANGE_GH, n_half, hb->order, my_h) ||
         !fill_set(tab.set[1], LBM_FULL_RANGE_GH, n_half, hb->order, my_f)) {
@@ -462,6 +624,23 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     for (int k = 0; k <= HMAXQ; ++k) {
         if (k > 0) f *= k;
         tab.inv_fact[k] = 1.0 / f;
+    }
+    if (tab.set[1].n > HMAXF) {
+        delete hb;
+        return hfail(LBM_EINVAL, "full-range set too large for the hybrid projection");
+    }
+    // the projections as matrices (transposed, source velocity major)
+    for (int t = 0; t < 2; ++t) {
+        const HybSet &T = tab.set[t], &S = tab.set[1 - t];
+        for (int a = 0; a < T.n; ++a)
+            for (int b = 0; b < S.n; ++b) {
+                double v = 0.0;
+                for (int m = 0; m <= hb->order; ++m)
+                    for (int n = 0; n <= hb->order; ++n)
+                        v += tab.inv_fact[m] * tab.inv_fact[n] * T.he_x[m][a] * T.he_y[n][a] * S.he_x[m][b] *
+                             S.he_y[n][b];
+                tab.pt[t][a * S.n + b] = S.w[b] * v;
+            }
     }
     const long nc = (long)nx * ny;
     hb->half.resize(nc);
@@ -479,6 +658,31 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     }
     hb->off[nc] = (int)o;
     hb->unknowns = o;
+    // cells with a neighbour in the other set go to the projecting kernel; runs of the others
+    // (consecutive cells of one set, as many as fill a warp) to the plain-cell kernel
+    std::vector<int> if_cells;
+    std::vector<int2> tasks;
+    for (long c = 0; c < nc; ++c) {
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        const unsigned char hc_ = hb->half[c];
+        bool iface = (y > 0 && hb->half[c - nx] != hc_) || (y < ny - 1 && hb->half[c + nx] != hc_);
+        if (geom == LBM_CAVITY) iface = iface || (x > 0 && hb->half[c - 1] != hc_) || (x < nx - 1 && hb->half[c + 1] != hc_);
+        if (iface) {
+            if_cells.push_back((int)c);
+            continue;
+        }
+        const int cap = 32 / tab.set[hc_ ? 0 : 1].lanes;
+        if (!tasks.empty()) {
+            int2 &tk = tasks.back();
+            if (tk.x + tk.y == c && hb->half[tk.x] == hc_ && tk.y < cap) {
+                ++tk.y;
+                continue;
+            }
+        }
+        tasks.push_back(make_int2((int)c, 1));
+    }
+    hb->n_if = (int)if_cells.size();
+    hb->n_tasks = (int)tasks.size();
     // dt = cfl / (max|xi_x|/dx + max|xi_y|/dy) over the sets present (the x term dropped for
     // the Couette column), dt <= Kn; the sets are symmetric, so max |xi_x| = max |xi_y|
     hb->dy = 1.0 / ny;
@@ -487,6 +691,13 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     hb->dt = cfl / (my / hb->dy + (geom == LBM_CAVITY ? my / hb->dx : 0.0));
     if (std::isfinite(kn) && hb->dt > kn) hb->dt = kn;
     hb->omega = std::isfinite(kn) ? hb->dt / kn : 0.0;
+    for (int k = 0; k < 2; ++k) {
+        HybSet &S = tab.set[k];
+        for (int b = 0; b < S.n; ++b) {
+            S.nux[b] = std::fabs(S.xi_x[b]) * hb->dt / hb->dx;
+            S.nuy[b] = std::fabs(S.xi_y[b]) * hb->dt / hb->dy;
+        }
+    }
     const double ur = std::max(std::fabs(u_bottom), std::fabs(u_top));
     hb->u_ref = ur > 0 ? ur : 1.0;
     cudaError_t e = cudaMalloc(&hb->d_tab, sizeof(HybTables));
@@ -497,6 +708,13 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_part, sizeof(double) * 2 * nc);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_res, sizeof(double) * 2);
     if (e == cudaSuccess) e = cudaMallocHost(&hb->h_res, sizeof(double) * 2);
+    if (e == cudaSuccess && hb->n_if > 0) e = cudaMalloc(&hb->d_if, sizeof(int) * hb->n_if);
+    if (e == cudaSuccess && hb->n_tasks > 0) e = cudaMalloc(&hb->d_tasks, sizeof(int2) * hb->n_tasks);
+    if (e == cudaSuccess && hb->n_if > 0)
+        e = cudaMemcpyAsync(hb->d_if, if_cells.data(), sizeof(int) * hb->n_if, cudaMemcpyHostToDevice, hb->stream);
+    if (e == cudaSuccess && hb->n_tasks > 0)
+        e = cudaMemcpyAsync(hb->d_tasks, tasks.data(), sizeof(int2) * hb->n_tasks, cudaMemcpyHostToDevice,
+                            hb->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb->d_tab, &tab, sizeof tab, cudaMemcpyHostToDevice, hb->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hb->d_off, hb->off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, hb->stream);
@@ -523,6 +741,8 @@ void lbm_hybrid_destroy(lbm_hybrid *hb)
     cudaFree(hb->d_h[1]);
     cudaFree(hb->d_part);
     cudaFree(hb->d_res);
+    cudaFree(hb->d_if);
+    cudaFree(hb->d_tasks);
     if (hb->h_res) cudaFreeHost(hb->h_res);
     delete hb;
 }
@@ -563,13 +783,14 @@ lbm_status lbm_hybrid_step(lbm_hybrid *hb, long nsteps)
 {
     if (!hb || nsteps < 0) return hfail(LBM_EINVAL, "invalid step arguments");
     const int nc = hb->nx * hb->ny;
-    const int grid = (nc + HWARPS - 1) / HWARPS;
     for (long s = 0; s < nsteps; ++s) {
         const bool last = s == nsteps - 1;
-        hybrid_step_kernel<<<grid, 32 * HWARPS, 0, hb->stream>>>(hargs(hb), hb->dt, hb->dx, hb->dy, last ? 1 : 0);
+        const int blocks = (hb->n_if + HWARPS - 1) / HWARPS + (hb->n_tasks + HWARPS - 1) / HWARPS;
+        hybrid_step_kernel<<<blocks, 32 * HWARPS, 0, hb->stream>>>(hargs(hb), hb->d_if, hb->n_if, hb->d_tasks,
+                                                                   hb->n_tasks, hb->dt, hb->dx, hb->dy, last ? 1 : 0);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess && last) {
-            hybrid_finalize_kernel<<<1, 32, 0, hb->stream>>>(hb->d_part, nc, hb->d_res);
+            hybrid_finalize_kernel<<<1, HFIN, 0, hb->stream>>>(hb->d_part, nc, hb->d_res);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return hfail(LBM_ECUDA, std::string("launching the hybrid step: ") + cudaGetErrorString(e));
