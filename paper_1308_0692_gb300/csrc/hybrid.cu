@@ -45,6 +45,9 @@ struct HybSet {
     double he_x[HMAXQ + 1][HMAXV], he_y[HMAXQ + 1][HMAXV];
     double d_x, d_y;           // sums over xi > 0 of xi w per axis (wall-flux normalisers, Eq. 9)
     double nux[HMAXV], nuy[HMAXV];  // |xi_x| dt / dx, |xi_y| dt / dy (set on the host once dt is known)
+    // signs of xi_x, xi_y (-1, 0, 1): the upwind and half-space tests as integer compares (an
+    // FP64 compare takes the FP64 pipe, the bound of these kernels)
+    signed char sx[HMAXV], sy[HMAXV];
 };
 
 constexpr int HMAXF = 36;      // full-range N <= 6
@@ -134,8 +137,11 @@ __device__ void wall_ghost(const HybArgs &a, const HybSet &S, const double *hc, 
     const int lane = threadIdx.x & 31;
     double part = 0.0;
     for (int b = lane; b < S.n; b += 32) {
-        const double xn = face == 0 ? S.xi_y[b] : face == 1 ? -S.xi_y[b] : face == 2 ? S.xi_x[b] : -S.xi_x[b];
-        if (xn < 0) part += -xn * hc[b];
+        const int sn = face == 0 ? S.sy[b] : face == 1 ? -S.sy[b] : face == 2 ? S.sx[b] : -S.sx[b];
+        if (sn < 0) {
+            const double xn = face == 0 ? S.xi_y[b] : face == 1 ? -S.xi_y[b] : face == 2 ? S.xi_x[b] : -S.xi_x[b];
+            part += -xn * hc[b];
+        }
     }
     const double rho_w = warp_sum(part) / (face < 2 ? S.d_y : S.d_x);
     const double u = face == 0 ? a.u_bottom : face == 1 ? a.u_top : 0.0;
@@ -152,8 +158,9 @@ __device__ void face_moments(const HybSet &S, const double *v, int axis, bool po
 {
     double p0 = 0.0, p1 = 0.0, p2 = 0.0;
     for (int b = threadIdx.x & 31; b < S.n; b += 32) {
-        const double xd = axis == 0 ? S.xi_x[b] : S.xi_y[b];
-        if (positive ? xd > 0 : xd < 0) {
+        const int sd = axis == 0 ? S.sx[b] : S.sy[b];
+        if (positive ? sd > 0 : sd < 0) {
+            const double xd = axis == 0 ? S.xi_x[b] : S.xi_y[b];
             const double t = fabs(xd) * v[b];
             p0 += t;
             p1 += t * S.xi_x[b];
@@ -234,11 +241,12 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
             const double ex = S.xi_x[b], ey = S.xi_y[b];
             const double h0 = hc[b];
             double hx = h0, nux = 0.0;
+            const int sgx = S.sx[b], sgy = S.sy[b];
             if (a.cavity) {
-                hx = ex > 0 ? nbv[0][b] : (ex < 0 ? nbv[1][b] : h0);
+                hx = sgx > 0 ? nbv[0][b] : (sgx < 0 ? nbv[1][b] : h0);
                 nux = S.nux[b];
             }
-            const double hy = ey > 0 ? nbv[2][b] : (ey < 0 ? nbv[3][b] : h0);
+            const double hy = sgy > 0 ? nbv[2][b] : (sgy < 0 ? nbv[3][b] : h0);
             const double nuy = S.nuy[b];
             v = h0 - nux * (h0 - hx) - nuy * (h0 - hy);
             if (any_if) v += (cr[0] + cr[1] * ex + cr[2] * ey) * S.w[b];
@@ -260,9 +268,11 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
             const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
             const double o = hs[i] - a.omega * (hs[i] - heq);
             out[b] = o;
-            const double d = o - hc[b];
-            pd += d * d;
-            pn += o * o;
+            if (resid) {
+                const double d = o - hc[b];
+                pd += d * d;
+                pn += o * o;
+            }
         }
     }
     if (resid) {
@@ -308,22 +318,27 @@ __device__ void plain_task(const HybArgs &a, const int2 tk, int resid)
     const double *hu = !wt ? a.h + a.off[c + nx] : hc;
     double hv[HMAXPL];
     double pw[4] = {0.0, 0.0, 0.0, 0.0};         // outflow through the bottom, top, left, right walls
+    const bool walls = __any_sync(0xffffffffu, wl || wr || wb || wt);
 #pragma unroll
     for (int i = 0; i < HMAXPL; ++i) {
         const int b = g + L * i;
         hv[i] = 0.0;
         if (b < n) {
-            const double v = hc[b], ex = S.xi_x[b], ey = S.xi_y[b];
+            const double v = hc[b];
             hv[i] = v;
-            if (ey < 0) pw[0] -= ey * v;
-            if (ey > 0) pw[1] += ey * v;
-            if (ex < 0) pw[2] -= ex * v;
-            if (ex > 0) pw[3] += ex * v;
+            if (walls) {
+                const double ex = S.xi_x[b], ey = S.xi_y[b];
+                const int sgx = S.sx[b], sgy = S.sy[b];
+                if (sgy < 0) pw[0] -= ey * v;
+                if (sgy > 0) pw[1] += ey * v;
+                if (sgx < 0) pw[2] -= ex * v;
+                if (sgx > 0) pw[3] += ex * v;
+            }
         }
     }
     // wall densities (Eq. 9 as a flux balance over the cell's set)
     double rw[4] = {0.0, 0.0, 0.0, 0.0};
-    if (__any_sync(0xffffffffu, wl || wr || wb || wt)) {
+    if (walls) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) rw[f] = group_sum(pw[f], L) / (f < 2 ? S.d_y : S.d_x);
     }
@@ -337,15 +352,16 @@ __device__ void plain_task(const HybArgs &a, const int2 tk, int resid)
         if (b < n) {
             const double ex = S.xi_x[b], ey = S.xi_y[b], wb_ = S.w[b];
             const double h0 = hv[i];
+            const int sgx = S.sx[b], sgy = S.sy[b];
             double hx = h0, nux = 0.0;
             if (cav) {
-                if (ex > 0) hx = wl ? wb_ * rw[2] : hl[b];          // side walls at rest
-                else if (ex < 0) hx = wr ? wb_ * rw[3] : hr[b];
+                if (sgx > 0) hx = wl ? wb_ * rw[2] : hl[b];          // side walls at rest
+                else if (sgx < 0) hx = wr ? wb_ * rw[3] : hr[b];
                 nux = S.nux[b];
             }
             double hy = h0;
-            if (ey > 0) hy = wb ? wb_ * (rw[0] * (1.0 + ex * ub) + ex * ub / a.u_ref) : hd[b];
-            else if (ey < 0) hy = wt ? wb_ * (rw[1] * (1.0 + ex * ut) + ex * ut / a.u_ref) : hu[b];
+            if (sgy > 0) hy = wb ? wb_ * (rw[0] * (1.0 + ex * ub) + ex * ub / a.u_ref) : hd[b];
+            else if (sgy < 0) hy = wt ? wb_ * (rw[1] * (1.0 + ex * ut) + ex * ut / a.u_ref) : hu[b];
             const double nuy = S.nuy[b];
             v = h0 - nux * (h0 - hx) - nuy * (h0 - hy);
             rho += v;
@@ -366,9 +382,11 @@ __device__ void plain_task(const HybArgs &a, const int2 tk, int resid)
             const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
             const double o = hs[i] - a.omega * (hs[i] - heq);
             if (on) out[b] = o;
-            const double d = o - hv[i];
-            pd += d * d;
-            pn += o * o;
+            if (resid) {
+                const double d = o - hv[i];
+                pd += d * d;
+                pn += o * o;
+            }
         }
     }
     if (resid) {
@@ -383,7 +401,7 @@ __device__ void plain_task(const HybArgs &a, const int2 tk, int resid)
 
 // One step: the blocks for the interface cells first (their projections are the long
 // latency chains), then the plain-cell tasks, so that both run side by side in one launch.
-__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, const int *cells, int ncells,
+__global__ void __launch_bounds__(32 * HWARPS, 5) hybrid_step_kernel(const HybArgs a, const int *cells, int ncells,
                                                                    const int2 *tasks, int ntasks, double dt, double dx,
                                                                    double dy, int resid)
 {
@@ -536,6 +554,8 @@ bool fill_set(HybSet &S, int kind, int n, int order, double &max_y)
             S.xi_x[a] = x[ix];
             S.xi_y[a] = x[iy];
             S.w[a] = w[ix] * w[iy];
+            S.sx[a] = (signed char)((x[ix] > 0) - (x[ix] < 0));
+            S.sy[a] = (signed char)((x[iy] > 0) - (x[iy] < 0));
             if (x[iy] > 0) S.d_y += x[iy] * S.w[a];
             if (x[ix] > 0) S.d_x += x[ix] * S.w[a];
             max_y = std::max(max_y, std::fabs(x[iy]));
