@@ -20,6 +20,8 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import contextlib
+import gc
 import hashlib
 import json
 import math
@@ -106,6 +108,22 @@ def aggregate(units_per_rank: float, seconds_per_rank: float, dist: Dist):
     t = dist.max(seconds_per_rank)
     u = dist.sum(units_per_rank)
     return u / t, t
+
+
+# ---------------------------------------------------------------- timing helpers
+@contextlib.contextmanager
+def gc_paused():
+    """A full pass of Python's cyclic garbage collector takes tens of ms with torch loaded and
+    falls at a fixed point of the allocation count: collect before a timed region and pause
+    the collector inside it, as timeit does."""
+    gc.collect()
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 # ---------------------------------------------------------------- clocks
@@ -261,13 +279,14 @@ def run_own(args, dist: Dist):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for i in range(K):
-            starts[i].record(stream)
-            lbm.lbm_step(sim, 1)
-            ends[i].record(stream)
-        t1.record(stream)
-        torch.cuda.synchronize()
+        with gc_paused():
+            t0.record(stream)
+            for i in range(K):
+                starts[i].record(stream)
+                lbm.lbm_step(sim, 1)
+                ends[i].record(stream)
+            t1.record(stream)
+            torch.cuda.synchronize()
         dist.barrier()
         total = t0.elapsed_time(t1) / 1e3
         per = [s.elapsed_time(e) / 1e3 for s, e in zip(starts, ends)]
@@ -368,11 +387,12 @@ def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
     rec = []
     dist.barrier()
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(reps):
-        one(rec)
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t
+    with gc_paused():
+        t = time.perf_counter()
+        for _ in range(reps):
+            one(rec)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
     value, _ = aggregate(float(nvals) * E2E_STEPS * reps, el, dist)
     # each call's parts by the host clock (every part ends synchronised); the upload's share
     # moves with the host<->device copy rate of the machine
@@ -383,7 +403,8 @@ def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
                           "moments": round(p[2] * 1e3, 2)} for p in rec],
             "h2d_gbs_in_set_state": nvals * 8 / min(p[0] for p in rec) / 1e9,
             "definition": f"one API call = lbm_set_state(host FP64, pinned) + lbm_step({E2E_STEPS}) + "
-                          "lbm_residual + lbm_moments(ux, uy); value counts the marched updates"}
+                          "lbm_residual + lbm_moments(ux, uy); value counts the marched updates; Python's "
+                          "cyclic garbage collector paused during the timed calls (as timeit does)"}
 
 
 def run_fp64_same_workload(vs, dist):
