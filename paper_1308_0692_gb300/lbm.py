@@ -305,6 +305,8 @@ def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0, refi
 
 
 def lbm_set_variant(sim: Sim, warps_per_segment: int, prefetch: int = 0):
+    """Step kernel: warps per 32-cell segment and load path (0 registers, 1 prefetch, 2/3 TMA
+    segments, 4 to 7 the column march; the C header lists which combinations exist)."""
     _check(_load().lbm_set_variant(sim.handle, int(warps_per_segment), int(prefetch)))
 
 
