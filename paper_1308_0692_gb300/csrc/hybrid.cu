@@ -20,6 +20,7 @@
 // (a = iy * M + ix).  dt = cfl dy / max |xi_y| over the sets present,
 // dt <= Kn.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -673,8 +674,12 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
                                              : std::min(y, ny - 1 - y);
         hb->half[c] = dwall < layer ? 1 : 0;
         (hb->half[c] ? any_h : any_f) = true;
-        hb->off[c] = (int)o;
+        hb->off[c] = (int)std::min(o, (long)INT_MAX);      // checked below
         o += hb->half[c] ? tab.set[0].n : tab.set[1].n;
+    }
+    if (o > (long)INT_MAX) {
+        delete hb;
+        return hfail(LBM_EINVAL, "too many unknowns for the hybrid's 32-bit cell offsets");
     }
     hb->off[nc] = (int)o;
     hb->unknowns = o;

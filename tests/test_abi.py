@@ -141,3 +141,16 @@ def test_grid_beyond_the_index_range_is_rejected():
     assert e.value.status == lbm.LBM_EINVAL
     ok = lbm.make_problem(lbm.LBM_CAVITY, 65536, 32768, 0.1, 0.0, 0.01)
     assert lbm.lbm_sim_bytes(_vs(), ok) > 8 * 64 * 65536 * 32768
+
+
+def test_hybrid_init_argument_checks_need_no_device():
+    """lbm_hybrid_init refuses invalid problems before it touches the device: N outside
+    [2, 6], a Couette channel wider than one column, a grid beyond 16M cells, and a state
+    beyond the 32-bit cell offsets (4000 x 4000 cells of D2Q^h_144: 2.3e9 unknowns)."""
+    C, V = lbm.LBM_COUETTE, lbm.LBM_CAVITY
+    for args in [(C, 1, 1, 10, 0.1, 0.0, 0.01, 2), (C, 7, 1, 10, 0.1, 0.0, 0.01, 2),
+                 (C, 4, 3, 10, 0.1, 0.0, 0.01, 2), (V, 4, 5000, 4000, 0.1, 0.0, 0.01, 2),
+                 (V, 6, 4000, 4000, 0.1, 0.0, 0.01, 2000)]:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_hybrid_init(*args)
+        assert e.value.status == lbm.LBM_EINVAL, args
