@@ -3,7 +3,9 @@
 The model replays, for one block and each kind of warp (upwind row y-1 or y+1), the order
 in which the kernel issues row copies into its ring of S slots and consumes them, with the
 kernel's item numbering (chunk-major, first three items per block fixed, the rest from a
-counter) and the host's choice of the chunk count.  It checks what a GPU run could only
+counter) and the host's choice of the chunk count, for rings of 2, 4 and 5 slots and for the
+deferred-relaxation variant (item ids published through mbarrier phases, visible one row
+later than at a block barrier).  It checks what a GPU run could only
 show as a fault or a wrong answer: every copy starts 16-byte aligned inside one grid row,
 a slot is refilled only after its last use, each row computed finds its own row and its
 upwind row in the slots, an item id is read only after the barrier that published it,
@@ -31,7 +33,7 @@ def choose_chunks(nx, ny, grid):
     return strips, chunks
 
 
-def simulate(nx, ny, S, grid):
+def simulate(nx, ny, S, grid, defer=False):
     strips, nchunks = choose_chunks(nx, ny, grid)
     rows, nitems, ncells = ny - 2, strips * nchunks, nx * ny
     written = {}
@@ -48,6 +50,7 @@ def simulate(nx, ny, S, grid):
             items = {0: b, 1: grid + b, 2: 2 * grid + b}
             visible = {0, 1, 2}
             pending = []
+            pending_old = []
             dyn = iter(fetched) if ypos else None
             l_pos, l_i, nl = 0, 0, 0
             l_item = items[0]
@@ -82,8 +85,15 @@ def simulate(nx, ny, S, grid):
                 assert loads[jo] == (y, c_strip)
                 assert loads[jy] == (y - 1 if ypos else y + 1, c_strip)
                 assert nl - 1 < min(jo, jy) + S                 # both still in the ring
-                visible |= set(pending)                          # the row barrier
-                pending = []
+                if defer:
+                    # deferred relaxation: an id written after row t's moments were published
+                    # is released with row t+1's and acquired at the wait for row t+1, which
+                    # follows row t+2's copies: visible one row later than at a block barrier
+                    visible |= set(pending_old)
+                    pending_old, pending = pending, []
+                else:
+                    visible |= set(pending)                      # the row barrier
+                    pending = []
                 if not ypos:
                     for xx in range(64):
                         c = y * nx + 32 + 64 * c_strip + xx
@@ -109,10 +119,12 @@ def simulate(nx, ny, S, grid):
 
 @pytest.mark.parametrize("nx,ny", [(128, 10), (192, 45), (256, 70), (384, 522), (640, 33), (1024, 1000),
                                    (2048, 2048)])
-@pytest.mark.parametrize("slots", [4, 5])
+@pytest.mark.parametrize("slots,defer", [(4, False), (5, False), (2, False), (4, True)])
 @pytest.mark.parametrize("grid", [7, 152, 304])
-def test_march_schedule_covers_interior_once(nx, ny, slots, grid):
-    simulate(nx, ny, slots, grid)
+def test_march_schedule_covers_interior_once(nx, ny, slots, defer, grid):
+    """Load paths 4, 5 (rings of 4 and 5 slots), 6 (a ring of 2: nothing read ahead) and 7
+    (ring of 4, relaxation deferred by one row)."""
+    simulate(nx, ny, slots, grid, defer)
 
 
 def _library():
