@@ -314,3 +314,35 @@ def test_second_order_variant_converges_at_second_order():
         errs.append(abs(f.mean() - exact))
     ratios = [errs[i] / errs[i + 1] for i in range(2)]
     assert all(3.2 < r < 4.6 for r in ratios), (errs, ratios)
+
+
+def _transpose_state(p, h):
+    """The state mirrored in the diagonal x = y: cells (x, y) -> (y, x), each velocity to the
+    one with xi_x and xi_y swapped (found by exact node equality)."""
+    perm = np.array([int(np.flatnonzero((p.xi_x == p.xi_y[a]) & (p.xi_y == p.xi_x[a]))[0]) for a in range(p.n)])
+    out = np.empty_like(h)
+    out[perm] = h.reshape(p.n, p.ny, p.nx).transpose(0, 2, 1).reshape(p.n, -1)
+    return out
+
+
+@pytest.mark.parametrize("kind,n", [("half", 2), ("half", 3), ("full", 3), ("full", 4)])
+def test_square_cavity_at_rest_is_symmetric_under_transposition(kind, n):
+    """With every wall at rest a square cavity is its own mirror image in the diagonal x = y:
+    the step (first-order transport, walls, relaxation) and the second-order transport
+    commute with the mirror, and the momentum flux sum xi_x xi_y h_upwind through the
+    vertical faces equals that through the horizontal faces of the mirrored state (first and
+    second order).  An x-transport or x-wall term that differed from its y counterpart (a
+    sign, an upwind side, a wall density, an index) breaks the step's equality; a wrong
+    upwind side or index in an x-face flux breaks the flux equality.  (A wall at rest emits
+    w_a rho_w, whose xi_x xi_y moment vanishes, so the wall faces' fluxes are checked by
+    their interior neighbours' values only.)"""
+    p = make_problem(kind, n, CAVITY, 7, 7, 0.2, 0.0, 0.0)
+    h = random_state(p.n, p.ncells, seed=20 + n)
+    hT = _transpose_state(p, h)
+    tol = 1e-14
+    for f in (lambda v: p.step(v, 3), p.transport2, lambda v: p.step_second_order(v, 2)):
+        a, b = _transpose_state(p, f(h)), f(hT)
+        assert np.abs(a - b).max() <= tol * np.abs(a).max()
+    for fx, fy in ((p.face_flux_x, p.face_flux_y), (p.face_flux2_x, p.face_flux2_y)):
+        a, b = fx(h), fy(hT).T
+        assert a.shape == b.shape and np.abs(a - b).max() <= tol * np.abs(a).max()
