@@ -346,3 +346,35 @@ def test_square_cavity_at_rest_is_symmetric_under_transposition(kind, n):
     for fx, fy in ((p.face_flux_x, p.face_flux_y), (p.face_flux2_x, p.face_flux2_y)):
         a, b = fx(h), fy(hT).T
         assert a.shape == b.shape and np.abs(a - b).max() <= tol * np.abs(a).max()
+
+
+@pytest.mark.parametrize("n_half,geom,nx,ny,xi_max", [
+    (4, COUETTE, 1, 100, 3.19989079049),      # largest node of the N = 4 half-range rule (Table 1)
+    (4, CAVITY, 128, 128, 3.19989079049),
+    (6, CAVITY, 2048, 2048, 4.29471226994),   # largest node of the N = 6 rule
+    (4, COUETTE, 3, 40, 3.19989079049),       # a Couette channel several columns wide keeps the x term
+])
+def test_time_step_and_coefficients_closed_forms(n_half, geom, nx, ny, xi_max):
+    """dt = CFL / sum_d (max |xi_d| / dx_d) with CFL 0.9 (the single Couette column has no x
+    term), dx = 1/nx, dy = 1/ny (the Couette column's dx = dy), omega = dt / Kn, u_ref the
+    larger wall speed; the half-range wall-flux normalisers sum_{xi_d > 0} xi_d w equal
+    1/sqrt(2 pi) (the factor of Eq. 9) on both axes."""
+    p = make_problem("half", n_half, geom, nx, ny, 0.1, 0.004, -0.01)
+    c = p.coeffs
+    column = geom == COUETTE and nx == 1
+    rate = xi_max * ny + (0.0 if column else xi_max * (ny if geom == COUETTE else nx))
+    assert c["dt"] == pytest.approx(0.9 / rate, rel=1e-10)
+    assert c["omega"] == pytest.approx(c["dt"] / 0.1, rel=1e-15)
+    assert c["u_ref"] == 0.01
+    assert c["d_x"] == pytest.approx(1.0 / math.sqrt(2.0 * math.pi), rel=1e-14)
+    assert c["d_y"] == pytest.approx(1.0 / math.sqrt(2.0 * math.pi), rel=1e-14)
+
+
+def test_time_step_is_clamped_to_kn_and_walls_at_rest_give_unit_reference_speed():
+    p = make_problem("half", 2, CAVITY, 8, 8, 1e-4, 0.0, 0.0)
+    c = p.coeffs
+    assert c["dt"] == 1e-4 and c["omega"] == 1.0 and c["u_ref"] == 1.0
+    # the time steps of the benchmark workloads to 5 significant digits, computed by hand
+    assert make_problem("half", 4, COUETTE, 1, 100, 0.1, 0.01, -0.01).coeffs["dt"] == pytest.approx(2.8126e-3, rel=2e-5)
+    assert make_problem("half", 4, CAVITY, 128, 128, 0.1, 0.0, 0.01).coeffs["dt"] == pytest.approx(1.0987e-3, rel=5e-5)
+    assert make_problem("half", 6, CAVITY, 2048, 2048, 0.05, 0.0, 0.01).coeffs["dt"] == pytest.approx(5.116e-5, rel=1e-4)
