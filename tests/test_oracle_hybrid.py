@@ -145,3 +145,34 @@ def test_cavity_mirror_symmetry_at_small_lid_speed():
     np.testing.assert_allclose(ux, ux[:, ::-1], rtol=0, atol=1e-6 * scale)
     np.testing.assert_allclose(uy, -uy[:, ::-1], rtol=0, atol=1e-6 * scale)
     assert scale > 0
+
+
+def _mirror_diagonal(p, h):
+    """Cell (x, y) -> (y, x) of a square hybrid cavity, each cell's velocities permuted so
+    that xi_x and xi_y swap (the layers are symmetric, so every cell keeps its set)."""
+    out = [None] * p.ncells
+    for y in range(p.ny):
+        for x in range(p.nx):
+            c, cm = y * p.nx + x, x * p.nx + y
+            s = p.vset(c)
+            assert p.vset(cm) is s
+            perm = [int(np.flatnonzero((s.xi_x == s.xi_y[a]) & (s.xi_y == s.xi_x[a]))[0]) for a in range(s.n)]
+            v = np.empty(s.n)
+            v[perm] = h[c]
+            out[cm] = v
+    return out
+
+
+@pytest.mark.parametrize("n_half,layer", [(2, 1), (3, 2), (4, 3)])
+def test_cavity_at_rest_is_symmetric_under_transposition(n_half, layer):
+    """With every wall at rest a square hybrid cavity is its own mirror image in the diagonal
+    x = y: stepping a random state commutes with the mirror, so the x-interface projections,
+    face fluxes and full-range corrections match their y counterparts term by term."""
+    p = hy.HybridCavity(n_half, 8, 8, 0.2, 0.0, 0.0, layer)
+    rng = np.random.default_rng(40 + n_half)
+    h = [rng.standard_normal(p.vset(c).n) * 1e-2 for c in range(p.ncells)]
+    a = _mirror_diagonal(p, p.step(h, 5))
+    b = p.step(_mirror_diagonal(p, h), 5)
+    scale = max(np.abs(v).max() for v in a)
+    for va, vb in zip(a, b):
+        np.testing.assert_allclose(va, vb, rtol=0, atol=1e-14 * scale)
