@@ -1,0 +1,116 @@
+"""Host logic of bench.py on CPU: the clock record taken during the timed region and the rule
+that rejects a throttled run, the DRAM-traffic record's tie to the kernel sources, the
+roofline peak's source, and the garbage-collector pause around timed regions."""
+import gc
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler_with(tmp_path, lines):
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    with open(s.path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    s.fh = open(str(tmp_path / "unused.csv"), "w")
+    s.proc = _FakeProc()
+    return s
+
+
+def test_clock_record_median_max_and_active_reasons(tmp_path):
+    """nvidia-smi csv,noheader,nounits lines: index, clocks.sm, clocks.max.sm, power, the
+    active mask, then hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap."""
+    lines = ["0, 2070, 2070, 912.40, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 2055, 2070, 1390.12, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1201.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "malformed line",
+             "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    clk = _sampler_with(tmp_path, lines).stop()
+    assert clk == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not bench.clocks_bad(clk)
+
+
+def test_clock_record_without_samples(tmp_path):
+    assert _sampler_with(tmp_path, ["garbage"]).stop()["reasons"] == ["no samples"]
+    s = bench.ClockSampler(0)
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+@pytest.mark.parametrize("clk,bad", [
+    ({"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": []}, False),
+    ({"sm_mhz": 1900, "sm_max_mhz": 2070, "reasons": ["sw_power_cap"]}, False),
+    ({"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": ["hw_slowdown"]}, True),
+    ({"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": ["hw_thermal_slowdown", "sw_power_cap"]}, True),
+    ({"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": ["sw_thermal_slowdown"]}, True),
+    ({"sm_mhz": 1000, "sm_max_mhz": 2070, "reasons": []}, True),              # a leftover clock lock
+    ({"sm_mhz": 1000, "sm_max_mhz": 2070, "reasons": ["sw_power_cap"]}, False),
+    ({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}, False),
+])
+def test_throttled_runs_are_rejected(clk, bad):
+    assert bench.clocks_bad(clk) is bad
+
+
+def _copy_tree(tmp_path):
+    root = tmp_path / "root"
+    src = os.path.join(bench.ROOT, "paper_1308_0692_gb300", "csrc")
+    os.makedirs(root / "paper_1308_0692_gb300" / "csrc")
+    for name in ("step_kernel.cuh", "step_tma.cuh", "step_march.cuh"):
+        shutil.copy(os.path.join(src, name), root / "paper_1308_0692_gb300" / "csrc" / name)
+    os.makedirs(root / "profiles")
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
+    return root
+
+
+def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The committed record matches the current sources; editing a kernel source, or a record
+    taken from other sources, drops it (the bench then reports traffic null)."""
+    key = "step_f32_m12_g6_pf4"
+    got = bench._traffic_record(key)
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))[key]
+    assert got == rec["dram_bytes_per_launch"] and got > 0
+    assert bench._traffic_record("no_such_kernel") is None
+    root = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench._traffic_record(key) == got
+    with open(root / "paper_1308_0692_gb300" / "csrc" / "step_march.cuh", "a") as f:
+        f.write("\n// edited\n")
+    assert bench._traffic_record(key) is None
+    os.remove(root / "profiles" / "traffic.json")
+    assert bench._traffic_record(key) is None
+
+
+def test_peak_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6791.0, "bf16_tflops": 1900.0}))
+    assert bench._peaks() == (6791.0, "measured")
+
+
+def test_gc_paused_restores_the_collector():
+    assert gc.isenabled()
+    with bench.gc_paused():
+        assert not gc.isenabled()
+    assert gc.isenabled()
+    with pytest.raises(RuntimeError):
+        with bench.gc_paused():
+            raise RuntimeError("inside a timed region")
+    assert gc.isenabled()
+    gc.disable()
+    try:
+        with bench.gc_paused():
+            pass
+        assert not gc.isenabled()          # a collector that was off stays off
+    finally:
+        gc.enable()
