@@ -62,28 +62,31 @@ def test_throttled_runs_are_rejected(clk, bad):
     assert bench.clocks_bad(clk) is bad
 
 
-def _copy_tree(tmp_path):
+def _tree_with_record(tmp_path, key, nbytes):
+    """A copy of the three hashed kernel sources and a traffic record stamped with their
+    hash (computed here independently: sha256 over the files in order, first 16 hex)."""
+    import hashlib
     root = tmp_path / "root"
-    src = os.path.join(bench.ROOT, "paper_1308_0692_gb300", "csrc")
-    os.makedirs(root / "paper_1308_0692_gb300" / "csrc")
-    for name in ("step_kernel.cuh", "step_tma.cuh", "step_march.cuh"):
-        shutil.copy(os.path.join(src, name), root / "paper_1308_0692_gb300" / "csrc" / name)
+    csrc = root / "paper_1308_0692_gb300" / "csrc"
+    os.makedirs(csrc)
     os.makedirs(root / "profiles")
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
+    h = hashlib.sha256()
+    for name in ("step_kernel.cuh", "step_tma.cuh", "step_march.cuh"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_1308_0692_gb300", "csrc", name), csrc / name)
+        h.update((csrc / name).read_bytes())
+    rec = {key: {"dram_bytes_per_launch": nbytes, "source_sha256_16": h.hexdigest()[:16]}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
     return root
 
 
 def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
-    """The committed record matches the current sources; editing a kernel source, or a record
-    taken from other sources, drops it (the bench then reports traffic null)."""
+    """A record stamped with the sources' hash is reported; editing a kernel source (even a
+    comment) or removing the record drops it, and the bench then reports traffic null."""
     key = "step_f32_m12_g6_pf4"
-    got = bench._traffic_record(key)
-    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))[key]
-    assert got == rec["dram_bytes_per_launch"] and got > 0
-    assert bench._traffic_record("no_such_kernel") is None
-    root = _copy_tree(tmp_path)
+    root = _tree_with_record(tmp_path, key, 4.9e9)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench._traffic_record(key) == got
+    assert bench._traffic_record(key) == 4.9e9
+    assert bench._traffic_record("no_such_kernel") is None
     with open(root / "paper_1308_0692_gb300" / "csrc" / "step_march.cuh", "a") as f:
         f.write("\n// edited\n")
     assert bench._traffic_record(key) is None
