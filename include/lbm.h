@@ -256,9 +256,12 @@ lbm_status lbm_norms(const void *a, const void *b, long count, int prec, void *s
  * The per-block partial sums live in a 512 KiB array inside the library that every GPU
  * loading the library holds until process exit; count is therefore limited to
  * 67,108,864 elements (one partial pair per 2048 elements): larger counts return
- * LBM_EINVAL.  The first call on each device (with that device current) looks up the
- * array's device address; make it before any stream capture that includes this call.
- * Calls share the array: each call writes every slot it reads, so nothing has to be
+ * LBM_EINVAL.  Each call whose stream is not being captured looks up the array's device
+ * address with the call's device current (so a cudaDeviceReset in between is harmless);
+ * a call made while its stream is being captured reuses the address found by the last
+ * uncaptured call on that device, so make one uncaptured call on each device before any
+ * stream capture that includes this call, and again after a cudaDeviceReset.  count = 0
+ * writes out = {0, 0}.  Calls share the array: each call writes every slot it reads, so nothing has to be
  * cleared, but calls that overlap on the GPU (other streams, concurrent graph launches)
  * race on it and must be serialised by the caller.  Never calls cudaMalloc or cudaFree.
  * Results equal lbm_norms up to summation order. */
@@ -275,7 +278,7 @@ lbm_status lbm_norms_noalloc(const void *a, const void *b, long count, int prec,
  * separates steps, and every residual_every steps instances whose residual is below tol
  * are frozen (their items are skipped from then on); with tol > 0 so is an instance whose
  * residual has not improved by 1 % over 20 checks (the FP32 rounding floor: its status
- * then reports converged with the residual it reached).  Supported: FP32 perturbation
+ * then reports it as stalled, not converged, with the residual it reached).  Supported: FP32 perturbation
  * storage with 4 or 8 nodes per axis (D2Q^h_16 / D2Q16, D2Q^h_64); wall densities are
  * summed in FP64, the ghosts evaluated in FP32.  A barrier that gives up makes the next
  * lbm_batch_poll return LBM_ETIMEOUT. */
@@ -318,9 +321,15 @@ lbm_status lbm_batch_reset(lbm_batch *b);
  * start.  Outputs may be NULL. */
 lbm_status lbm_batch_tune(lbm_batch *b, int steps_per_trial, int *best_warps_per_segment,
                           int *best_blocks_per_sm, int *best_order, double *best_ms_per_step);
-/* Instance i: steps taken (the step at which it converged, or all steps so far), last
- * residual, converged flag; its state as host FP64 [n][ny][nx]. */
+/* Instance i: steps taken (the step at which it was frozen, or all steps so far), last
+ * residual, and converged = 1 only if it was frozen because its residual fell below the
+ * tolerance (0 while it marches, and 0 if the stagnation rule froze it above the
+ * tolerance: see lbm_batch_stalled).  Synchronises the batch's stream. */
 lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, int *converged);
+/* stalled = 1 if instance i was frozen by the stagnation rule (no 1 % improvement of its
+ * residual over 20 checks, the FP32 rounding floor) with its residual still at or above the
+ * tolerance; lbm_batch_status gives that residual and the step.  Not in the paper. */
+lbm_status lbm_batch_stalled(lbm_batch *b, int i, int *stalled);
 lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h);
 /* Initial state of instance i before the first lbm_batch_advance: host FP64 [n][ny][nx],
  * or the warm start of a cavity instance from the network (see lbm_warm_start). */

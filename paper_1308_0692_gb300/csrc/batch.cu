@@ -1900,13 +1900,31 @@ lbm_status lbm_batch_status(lbm_batch *b, int i, long *steps, double *residual, 
     if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
     long f;
     double r;
+    int flat = 0;
     cudaError_t e = cudaMemcpyAsync(&f, b->d_frozen + i, sizeof(long), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, b->d_last_r + i, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flat, b->d_flat + i, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("reading instance status: ") + cudaGetErrorString(e));
     if (steps) *steps = f == LONG_MAX ? b->step : f;
     if (residual) *residual = r;
-    if (converged) *converged = f != LONG_MAX;
+    // frozen by the tolerance (the stagnation rule freezes at its 20th flat check and leaves
+    // that count in place; a freeze by the tolerance happens with fewer)
+    if (converged) *converged = f != LONG_MAX && flat < 20;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_stalled(lbm_batch *b, int i, int *stalled)
+{
+    if (!b || !stalled) return bfail(LBM_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
+    long f;
+    int flat = 0;
+    cudaError_t e = cudaMemcpyAsync(&f, b->d_frozen + i, sizeof(long), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flat, b->d_flat + i, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, std::string("reading instance status: ") + cudaGetErrorString(e));
+    *stalled = f != LONG_MAX && flat >= 20;
     return LBM_OK;
 }
 

@@ -6,13 +6,16 @@
 // instead of caller memory.
 //
 // The array (LBM_NORMS_STATIC_PARTIALS pairs of doubles, 512 KiB) exists on every GPU
-// that loads this library, from load until process exit.  Its device address is looked
-// up once per device with cudaGetSymbolAddress on the first call made with that device
-// current; make that first call before any stream capture that includes this entry
-// point.  All calls share the array: every slot that a call reads is written by the same
-// call first, so nothing needs clearing, but calls whose kernels overlap on the GPU
-// (different streams, or overlapping graph launches) race on it and must be serialised
-// by the caller.
+// that loads this library, from load until process exit.  In host code its name is only
+// a host-side handle, so the kernels get its device address from cudaGetSymbolAddress,
+// looked up with the call's device current.  A call whose stream is not being captured
+// looks the address up afresh (a few microseconds), so the address stays right after a
+// cudaDeviceReset; a call made while its stream is being captured reuses the address that
+// the last uncaptured call on that device found, so make one uncaptured call on each
+// device before capturing this entry point (and again after a cudaDeviceReset).  All calls
+// share the array: every slot that a call reads is written by the same call first, so
+// nothing needs clearing, but calls whose kernels overlap on the GPU (different streams,
+// or overlapping graph launches) race on it and must be serialised by the caller.
 #include <mutex>
 
 #include "../../include/lbm.h"
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(256) norms_chunk_kernel(const T *a, const T *b
 }
 
 std::mutex g_addr_mu;
-void *g_addr[256];        // device address of g_norms_scratch, per device ordinal
+void *g_addr[256];        // device address of g_norms_scratch found by the last uncaptured call
 bool g_addr_ok[256];
 
 }  // namespace
@@ -90,17 +93,25 @@ extern "C" lbm_status lbm_norms_noalloc(const void *a, const void *b, long count
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return lbm_norms_fail(LBM_ECUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= 256) return lbm_norms_fail(LBM_EINVAL, "lbm_norms_noalloc: device ordinal");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return lbm_norms_fail(LBM_ECUDA, cudaGetErrorString(e));
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_addr_mu);
-        if (!g_addr_ok[dev]) {
-            e = cudaGetSymbolAddress(&g_addr[dev], g_norms_scratch);
-            if (e != cudaSuccess) return lbm_norms_fail(LBM_ECUDA, cudaGetErrorString(e));
+        if (cap == cudaStreamCaptureStatusNone || !g_addr_ok[dev]) {
+            void *addr = nullptr;
+            e = cudaGetSymbolAddress(&addr, g_norms_scratch);
+            if (e != cudaSuccess) {
+                g_addr_ok[dev] = false;
+                return lbm_norms_fail(LBM_ECUDA, cudaGetErrorString(e));
+            }
+            g_addr[dev] = addr;
             g_addr_ok[dev] = true;
         }
         scratch = g_addr[dev];
     }
-    cudaStream_t s = (cudaStream_t)stream;
     double *partials = (double *)scratch;
     if (nblocks > 0) {
         if (prec == LBM_FP64)

@@ -98,6 +98,7 @@ def _load():
         "lbm_batch_set_timeout": (st, [_vp, ctypes.c_longlong]),
         "lbm_batch_poll": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]),
         "lbm_batch_status": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), _dp, ctypes.POINTER(ctypes.c_int)]),
+        "lbm_batch_stalled": (st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_get_state": (st, [_vp, ctypes.c_int, _dp]),
         "lbm_batch_reset": (st, [_vp]),
         "lbm_batch_moments": (st, [_vp, ctypes.c_int, _vp]),
@@ -501,9 +502,12 @@ def lbm_batch_poll(b: Batch):
 
 
 def lbm_batch_status(b: Batch, i: int):
-    st, r, cv = ctypes.c_long(), ctypes.c_double(), ctypes.c_int()
+    """Steps, last residual, converged (frozen below the tolerance) and stalled (frozen by the
+    stagnation rule above it) of instance i."""
+    st, r, cv, sl = ctypes.c_long(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
     _check(_load().lbm_batch_status(b.handle, int(i), ctypes.byref(st), ctypes.byref(r), ctypes.byref(cv)))
-    return {"steps": st.value, "residual": r.value, "converged": bool(cv.value)}
+    _check(_load().lbm_batch_stalled(b.handle, int(i), ctypes.byref(sl)))
+    return {"steps": st.value, "residual": r.value, "converged": bool(cv.value), "stalled": bool(sl.value)}
 
 
 def lbm_batch_get_state(b: Batch, i: int) -> np.ndarray:

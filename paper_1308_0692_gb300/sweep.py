@@ -104,8 +104,12 @@ def run(count=512, seed=BATCH_SEED, tol=1e-10, ref_max_cells=128 * 128, threads=
         if n_active == 0 or steps_done >= 2_000_000:
             break
     t_batch = time.perf_counter() - t0
-    steps = np.array([lbm.lbm_batch_status(b, i)["steps"] for i in range(count_local)])
-    log(f"sweep: batch march done, {int((steps < steps_done).sum())} of {count_local} instances converged")
+    status = [lbm.lbm_batch_status(b, i) for i in range(count_local)]
+    steps = np.array([st["steps"] for st in status])
+    n_conv = sum(st["converged"] for st in status)
+    n_stall = sum(st["stalled"] for st in status)
+    log(f"sweep: batch march done, {n_conv} of {count_local} instances converged below {tol32:g}, "
+        f"{n_stall} stalled at their FP32 floor above it (both go to the refinement)")
     cells = np.array([p.nx * p.ny for p in probs])
     log(f"sweep: FP32 batch march to {tol32:g} in {t_batch:.1f} s ({steps_done} steps launched, "
         f"{(steps * cells * 64).sum() / t_batch / 1e9:.1f} G updates/s on active instances)")

@@ -46,6 +46,7 @@ def generate(pairs, side=128, tol=1e-6, chunk=512, max_steps=400_000, steps_per_
     steps = np.zeros(len(pairs), dtype=np.int64)
     stream = torch.cuda.Stream()
     mom = torch.empty((6, ncells), dtype=torch.float64, device="cuda")
+    n_stall = 0
     for c0 in range(0, len(pairs), chunk):
         sub = pairs[c0:c0 + chunk]
         probs = [lbm.make_problem(lbm.LBM_CAVITY, side, side, kn, 0.0, uw, prec=lbm.LBM_FP32_PERTURB,
@@ -69,10 +70,12 @@ def generate(pairs, side=128, tol=1e-6, chunk=512, max_steps=400_000, steps_per_
                 out[c0 + i, :, 3] = ((m[3] - 1.0) / uw).float()
                 out[c0 + i, :, 4] = (m[4] / uw).float()
                 out[c0 + i, :, 5] = ((m[5] - 1.0) / uw).float()
-                steps[c0 + i] = lbm.lbm_batch_status(b, i)["steps"]
+                st = lbm.lbm_batch_status(b, i)
+                steps[c0 + i] = st["steps"]
+                n_stall += st["stalled"]
         stream.synchronize()
-        log(f"generate: instances {c0}..{c0 + len(sub) - 1} converged (tol {tol:g}) in "
-            f"{time.perf_counter() - t0:.1f} s, max steps {steps[c0:c0 + len(sub)].max()}")
+        log(f"generate: instances {c0}..{c0 + len(sub) - 1} marched (tol {tol:g}; {n_stall} stalled above "
+            f"it so far) in {time.perf_counter() - t0:.1f} s, max steps {steps[c0:c0 + len(sub)].max()}")
         b.close()
     return out, steps
 

@@ -122,6 +122,24 @@ def test_second_order_couette_converges_at_second_order():
     assert all(3.3 < r < 4.5 for r in ratios), (errs, ratios)
 
 
+def test_order_study_against_semidiscrete_references():
+    """The order study of the package, given the semi-discrete Couette shear as its reference
+    (D2Q^h_64, Kn = 0.1): the paper's scheme converges at first order (error ratios near 2,
+    observed order near 1), the second-order variant at second order (ratios near 4)."""
+    from oracle import quadrature as q
+    from oracle.couette_exact import couette_semidiscrete
+    from paper_1308_0692_gb300 import experiments
+    nodes, weights = q.halfrange_1d(4)
+    exact = couette_semidiscrete([float(v) for v in nodes], [float(v) for v in weights], 0.1, -0.01, 0.01)["pxy"]
+    out = experiments.order_study(kns=(0.1,), nys=(50, 100, 200), n_half=4, exact_pxy={0.1: exact})
+    runs = {(r["order"], r["ny"]): r for r in out["runs"]}
+    assert len(runs) == 6
+    for order, lo, hi in ((1, 1.7, 2.3), (2, 3.3, 4.5)):
+        for ny in (100, 200):
+            assert lo < runs[(order, ny)]["ratio"] < hi, (order, ny, runs[(order, ny)])
+        assert abs(runs[(order, 200)]["observed_order"] - order) < 0.3, runs[(order, 200)]
+
+
 def test_second_order_rejections():
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
     sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 64, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))

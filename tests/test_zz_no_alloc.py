@@ -59,3 +59,19 @@ def test_noalloc_rejects_counts_beyond_the_static_scratch():
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_norms_noalloc(a.data_ptr(), None, 2 ** 26 + 1, lbm.LBM_FP32_PERTURB, out.data_ptr())
     assert e.value.status == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("prec,dtype", [(lbm.LBM_FP64, torch.float64), (lbm.LBM_FP32_PERTURB, torch.float32)])
+def test_noalloc_empty_input_gives_zero_norms(prec, dtype):
+    """count = 0 launches no chunk blocks; the finalisation over zero partials writes {0, 0},
+    the same as lbm_norms, also right after a call that left partials in the static array."""
+    s = torch.cuda.current_stream()
+    a = torch.randn(5000, dtype=torch.float64).to(dtype).cuda()
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    lbm.lbm_norms_noalloc(a.data_ptr(), None, a.numel(), prec, out.data_ptr(), s)
+    for bb in (a, None):
+        out.fill_(-1.0)
+        lbm.lbm_norms_noalloc(a.data_ptr(), bb.data_ptr() if bb is not None else None, 0, prec, out.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert out.cpu().tolist() == [0.0, 0.0]
+        np.testing.assert_array_equal(_reference(a[:0], bb[:0] if bb is not None else None, prec), [0.0, 0.0])
