@@ -343,11 +343,9 @@ def run_own(args, dist: Dist):
     }
     if not args.no_e2e:
         out["e2e"] = run_e2e(sim, prob, n_vel, ncells, stream, dist, args)
-    if not args.no_extras:
+    if not args.no_extras and dist.world == 1:
         out["fp64"] = run_fp64_same_workload(vs, dist)
         out["time_to_residual"] = run_time_to_residual(dist)
-        if dist.rank == 0:
-            out["configs_time_to_residual"] = run_configs_time_to_residual()
     sim.close()
     del buf
     return out
@@ -438,104 +436,152 @@ def run_fp64_same_workload(vs, dist):
 REFINE_HEADLINE = "batched"
 
 
-def run_time_to_residual(dist, count=32):
+HELD_OUT_SEED = 20130805     # the warm-start network's 256 held-out (Kn, u_w) pairs
+HELD_OUT_COUNT = 256
+ABLATION_COUNT = 32         # the one-factor-at-a-time rows run on the first 32 of them
+
+
+def run_time_to_residual(dist):
     """Time to steady state of held-out lid-driven cavities (128 x 128, 64 half-range
     velocities, Kn log-uniform in [0.01, 10], u_w in [0.005, 0.02]; residual 1e-8 checked
-    every 100 steps), one factor at a time:
-      fp64        plain FP64 march, instances one after another (graph-captured intervals);
-      fp64_concurrent  the same solves, all instances at once on their own streams;
+    every 100 steps).
+
+    All 256 held-out pairs of the warm-start network (the headline):
+      fp64        plain FP64 march of every instance, 32 instances at a time on their own
+                  streams and host threads (graph-captured residual intervals);
+      batch_dc    one persistent batched FP32 sweep, then the batched FP64-defect refinement;
+      warm_dc     the same from the learned warm start.
+    The first 32 pairs, one factor at a time:
+      fp64        plain FP64 march, instances one after another;
+      fp64_concurrent  the same solves, all 32 at once on their own streams;
       fp32_dc     FP32 march + FP64-defect refinement, one after another;
-      batch_dc    all instances in one persistent batched FP32 sweep, then the batched
-                  refinement (all instances' FP64 defects and FP32 corrections in one
-                  persistent launch per chunk of steps); the same refinement run one
-                  simulation per instance is timed beside it;
-      warm_dc     the same with the learned warm start (if a trained network is present).
+      batch_dc, warm_dc as above (the refinement also run one simulation per instance).
     The refinement marches the correction until its per-step change is below tol (the
     criterion the FP64 march meets), i.e. equal accuracy by construction; the measured
-    accuracy of every variant, max |u - u_fp64| / u_w over the instances, is reported."""
+    accuracy of every variant, max |u - u_fp64| / u_w over every instance, is reported."""
     import numpy as np
     import torch
 
     from paper_1308_0692_gb300 import lbm, warmstart
-    pairs = warmstart.draw_pairs(count, seed=20130805)
+    pairs_all = warmstart.draw_pairs(HELD_OUT_COUNT, seed=HELD_OUT_SEED)
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
     tol = 1e-8
-    out = {"workload": f"{count} lid-driven cavities 128x128, D2Q^h_64, Kn log-uniform [0.01,10], "
-                       f"u_w U(0.005,0.02), residual {tol:g}", "pairs": pairs}
+    params = os.path.join(ROOT, "paper_1308_0692_gb300", "data", "warmstart_mlp.npy")
+    mlp = warmstart.load_mlp(params) if os.path.exists(params) else None
 
     def fields(sim):
         m = lbm.lbm_moments(sim, wall_shear=False)
         return m["ux"], m["uy"]
 
-    ref, t64, steps64 = [], 0.0, []
+    def fp64_concurrent(pairs, threads):
+        """Every instance's FP64 solve on its own stream, `threads` solves in flight."""
+        sims = []
+        for kn, uw in pairs:
+            prob = lbm.make_problem(lbm.LBM_CAVITY, 128, 128, kn, 0.0, uw, prec=lbm.LBM_FP64, residual_every=100)
+            sims.append(lbm.lbm_init(vs, prob, stream=lbm.PrivateStream()))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            infos = list(ex.map(lambda sm: lbm.lbm_solve(sm, tol, 2_000_000, 0), sims))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        refs = [fields(sm) for sm in sims]
+        for sm in sims:
+            sm.close()
+        return el, [i["steps"] for i in infos], refs
+
+    def batched(pairs, ref, net, per_instance):
+        def err(got, i):
+            return max(np.abs(got[0] - ref[i][0]).max(), np.abs(got[1] - ref[i][1]).max()) / pairs[i][1]
+        b, steps, tb = warmstart.batch_solve(vs, pairs, tol, mlp=net)
+        per = None
+        if per_instance:
+            # refinement one simulation per instance (own stream and host thread), from the
+            # same batch states, timed beside the batched refinement
+            sims, corr, tp = warmstart.refine_instances(vs, b, pairs, tol, refine_tol=tol)
+            per = {"refine_seconds": tp, "refine_steps": corr.tolist(),
+                   "max_err_vs_fp64": max(err(fields(sm), i) for i, sm in enumerate(sims))}
+            for sm in sims:
+                sm.close()
+        n_stall = sum(lbm.lbm_batch_status(b, i)["stalled"] for i in range(len(pairs)))
+        info, tr = warmstart.refine_batch(b, tol, refine_tol=tol)
+        errs = [err(warmstart.batch_fields(b, i), i) for i in range(len(pairs))]
+        b.close()
+        out = {"seconds": tb + tr, "batch_seconds": tb, "refine_seconds": tr, "refinement": "batched",
+               "steps": steps.tolist(), "refine_steps": [r["correction_steps"] for r in info],
+               "sweeps": [r["sweeps"] for r in info], "stalled_in_march": int(n_stall),
+               "max_err_vs_fp64": max(errs), "checked": len(errs)}
+        if per is not None:
+            out["per_instance_refinement"] = per
+        return out
+
+    # ---- all 256 held-out pairs
+    t64, steps64, ref_all = fp64_concurrent(pairs_all, 32)
+    upd_all = float(sum(steps64)) * 128 * 128 * 64
+    full = {"workload": f"{len(pairs_all)} held-out lid-driven cavities 128x128 (seed {HELD_OUT_SEED}), D2Q^h_64, "
+                        f"Kn log-uniform [0.01,10], u_w U(0.005,0.02), residual {tol:g}",
+            "fp64": {"seconds": t64, "steps": steps64, "updates_per_s": upd_all / t64,
+                     "schedule": "32 instances in flight, each on its own stream and host thread"}}
+    full["batch_dc"] = batched(pairs_all, ref_all, None, False)
+    full["warm_dc"] = batched(pairs_all, ref_all, mlp, False) if mlp is not None else None
+    for k in ("batch_dc", "warm_dc"):
+        if full[k]:
+            full[k]["speedup_vs_fp64"] = t64 / full[k]["seconds"]
+
+    # ---- the first 32 pairs, one factor at a time
+    pairs = pairs_all[:ABLATION_COUNT]
+    ref, t64s, steps64s = [], 0.0, []
     for kn, uw in pairs:
         sim, info, el = warmstart.solve_cavity(vs, kn, uw, prec=lbm.LBM_FP64, tol=tol, refine=0)
-        t64 += el
-        steps64.append(info["steps"])
+        t64s += el
+        steps64s.append(info["steps"])
         ref.append(fields(sim))
         sim.close()
-    updates = float(sum(steps64)) * 128 * 128 * 64
-    out["fp64"] = {"seconds": t64, "steps": steps64, "updates_per_s": updates / t64}
-
-    # the same FP64 solves, every instance on its own stream and host thread
-    sims64 = []
-    for kn, uw in pairs:
-        prob = lbm.make_problem(lbm.LBM_CAVITY, 128, 128, kn, 0.0, uw, prec=lbm.LBM_FP64, residual_every=100)
-        sims64.append(lbm.lbm_init(vs, prob, stream=lbm.PrivateStream()))
-    torch.cuda.synchronize()
-    tc0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=count) as ex:
-        list(ex.map(lambda sm: lbm.lbm_solve(sm, tol, 2_000_000, 0), sims64))
-    torch.cuda.synchronize()
-    t64c = time.perf_counter() - tc0
-    for sm in sims64:
-        sm.close()
-    out["fp64_concurrent"] = {"seconds": t64c, "updates_per_s": updates / t64c}
-
-    def err(got, i):
-        ux, uy = got
-        return max(np.abs(ux - ref[i][0]).max(), np.abs(uy - ref[i][1]).max()) / pairs[i][1]
-
+    upd = float(sum(steps64s)) * 128 * 128 * 64
+    sub = {"workload": f"the first {len(pairs)} of the held-out pairs", "pairs": pairs,
+           "fp64": {"seconds": t64s, "steps": steps64s, "updates_per_s": upd / t64s}}
+    t64c, _, _ = fp64_concurrent(pairs, len(pairs))
+    sub["fp64_concurrent"] = {"seconds": t64c, "updates_per_s": upd / t64c}
     t32, e32, st32 = 0.0, 0.0, []
     for i, (kn, uw) in enumerate(pairs):
         sim, info, el = warmstart.solve_cavity(vs, kn, uw, prec=lbm.LBM_FP32_PERTURB, tol=tol, refine=3,
                                                refine_tol=tol)
         t32 += el
         st32.append(info["steps"] + info["correction_steps"])
-        e32 = max(e32, err(fields(sim), i))
+        ux, uy = fields(sim)
+        e32 = max(e32, max(np.abs(ux - ref[i][0]).max(), np.abs(uy - ref[i][1]).max()) / uw)
         sim.close()
-    out["fp32_dc"] = {"seconds": t32, "steps": st32, "max_err_vs_fp64": e32, "speedup_vs_fp64": t64 / t32}
-
-    def batched(mlp):
-        b, steps, tb = warmstart.batch_solve(vs, pairs, tol, mlp=mlp)
-        # refinement one simulation per instance (own stream and host thread), then -- from
-        # the same batch states -- the batched refinement; the faster design is the headline
-        sims, corr, tp = warmstart.refine_instances(vs, b, pairs, tol, refine_tol=tol)
-        per = {"refine_seconds": tp, "refine_steps": corr.tolist(),
-               "max_err_vs_fp64": max(err(fields(s), i) for i, s in enumerate(sims))}
-        for s in sims:
-            s.close()
-        info, tr = warmstart.refine_batch(b, tol, refine_tol=tol)
-        bat = {"refine_seconds": tr, "refine_steps": [r["correction_steps"] for r in info],
-               "sweeps": [r["sweeps"] for r in info],
-               "max_err_vs_fp64": max(err(warmstart.batch_fields(b, i), i) for i in range(count))}
-        b.close()
-        head = per if REFINE_HEADLINE == "per_instance" else bat
-        t = tb + head["refine_seconds"]
-        return {"seconds": t, "batch_seconds": tb, "refine_seconds": head["refine_seconds"],
-                "refinement": REFINE_HEADLINE, "steps": steps.tolist(), "refine_steps": head["refine_steps"],
-                "max_err_vs_fp64": head["max_err_vs_fp64"], "speedup_vs_fp64": t64 / t,
-                "speedup_vs_fp64_concurrent": t64c / t, "per_instance_refinement": per,
-                "batched_refinement": bat}
-
-    out["batch_dc"] = batched(None)
-    params = os.path.join(ROOT, "paper_1308_0692_gb300", "data", "warmstart_mlp.npy")
-    if os.path.exists(params):
-        mlp = warmstart.load_mlp(params)
-        out["warm_dc"] = batched(mlp)
+    sub["fp32_dc"] = {"seconds": t32, "steps": st32, "max_err_vs_fp64": e32, "speedup_vs_fp64": t64s / t32}
+    sub["batch_dc"] = batched(pairs, ref, None, True)
+    sub["warm_dc"] = batched(pairs, ref, mlp, True) if mlp is not None else None
+    for k in ("batch_dc", "warm_dc"):
+        if sub[k]:
+            sub[k]["speedup_vs_fp64"] = t64s / sub[k]["seconds"]
+            sub[k]["speedup_vs_fp64_concurrent"] = t64c / sub[k]["seconds"]
+    if mlp is not None:
         mlp.close()
-    else:
-        out["warm_dc"] = None
+    return {"held_out_256": full, "ablation_32": sub}
+
+
+def ttr_summary(ttr: dict, oracle_rate: float | None) -> dict:
+    """A short digest of the time-to-residual runs (seconds, speed-ups, worst velocity error
+    against the FP64 march, instance counts), printed as the line's last key."""
+    def r3(x):
+        return None if x is None else float(f"{x:.4g}")
+    full, sub = ttr["held_out_256"], ttr["ablation_32"]
+    out = {"tol": 1e-8, "n": len(full["fp64"]["steps"]), "fp64_s": r3(full["fp64"]["seconds"]),
+           "batch_dc_s": r3(full["batch_dc"]["seconds"]),
+           "batch_dc_max_du": r3(full["batch_dc"]["max_err_vs_fp64"])}
+    if full.get("warm_dc"):
+        w = full["warm_dc"]
+        out.update({"warm_dc_s": r3(w["seconds"]), "warm_dc_max_du": r3(w["max_err_vs_fp64"]),
+                    "warm_vs_fp64": r3(w["speedup_vs_fp64"]), "checked": w["checked"]})
+    out["first32"] = {"fp64_seq_s": r3(sub["fp64"]["seconds"]), "fp64_conc_s": r3(sub["fp64_concurrent"]["seconds"]),
+                      "fp32_dc_s": r3(sub["fp32_dc"]["seconds"]), "batch_dc_s": r3(sub["batch_dc"]["seconds"]),
+                      "warm_dc_s": r3(sub["warm_dc"]["seconds"]) if sub.get("warm_dc") else None}
+    if oracle_rate:
+        upd = float(sum(full["fp64"]["steps"])) * 128 * 128 * 64
+        out["oracle_extrap_s"] = r3(upd / oracle_rate)
     return out
 
 
@@ -602,27 +648,48 @@ def _oracle_setup(rows: int):
     return p, h, cells
 
 
-def oracle_sample(seconds_target: float, threads: int):
-    """Time the oracle's step on bands of cells of the workload grid with `threads` host
-    threads (each calling the oracle on its own chunk).  Returns (updates/s, sample)."""
-    p, h, cells = _oracle_setup(rows=8)
-    chunks = [c for c in __import__("numpy").array_split(cells, threads) if len(c)]
+class OracleBand:
+    """The oracle's FP64 step on a band of `rows` middle rows of the workload grid, split into
+    one contiguous chunk of cells per host thread, with one thread pool kept for the whole
+    timing (the C step releases the GIL, so the threads run in parallel)."""
 
-    def one_pass():
-        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-            list(ex.map(lambda c: p.step_cells(h, c), chunks))
+    def __init__(self, rows: int, threads: int):
+        import numpy as np
+        self.p, self.h, cells = _oracle_setup(rows=rows)
+        self.rows = rows
+        self.threads = threads
+        self.ncells = int(len(cells))
+        self.chunks = [c for c in np.array_split(cells, threads) if len(c)]
+        self.ex = cf.ThreadPoolExecutor(max_workers=threads)
 
-    one_pass()
-    t = time.perf_counter()
-    passes = 0
-    while True:
-        one_pass()
-        passes += 1
-        el = time.perf_counter() - t
-        if el >= seconds_target:
-            break
-    ups = len(cells) * p.n * passes / el
-    return ups, {"cells_per_pass": int(len(cells)), "passes": passes, "seconds": el}
+    def step(self):
+        list(self.ex.map(lambda c: self.p.step_cells(self.h, c), self.chunks))
+
+    def updates_per_step(self) -> int:
+        return self.ncells * self.p.n
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def oracle_sample(seconds_target: float, threads: int, rows: int = 256):
+    """Time the oracle's step on a band of `rows` rows of the workload grid with `threads`
+    host threads for about `seconds_target` seconds.  Returns (updates/s, sample)."""
+    band = OracleBand(rows, threads)
+    try:
+        band.step()
+        t = time.perf_counter()
+        passes = 0
+        while True:
+            band.step()
+            passes += 1
+            el = time.perf_counter() - t
+            if el >= seconds_target:
+                break
+    finally:
+        band.close()
+    ups = band.updates_per_step() * passes / el
+    return ups, {"rows": rows, "cells_per_pass": band.ncells, "passes": passes, "seconds": el}
 
 
 def run_reference(args, dist: Dist):
@@ -631,29 +698,25 @@ def run_reference(args, dist: Dist):
     from oracle import march
     march.build()
     threads = os.cpu_count() or 1
-    ups_probe, _ = oracle_sample(1.0, threads)
+    ups_probe, _ = oracle_sample(1.0, threads, rows=64)
     # size each bench step so that warmup + steps end in about a minute
     budget = 60.0
     per_step_updates = max(144 * 2048, ups_probe * budget / max(1, args.steps + args.warmup))
     rows = max(1, min(int(per_step_updates / (2048 * 144)), WORKLOAD["ny"] - 2))
-    p, h, cells = _oracle_setup(rows=rows)
-    import numpy as np
-    chunks = [c for c in np.array_split(cells, threads) if len(c)]
-
-    def step():
-        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-            list(ex.map(lambda c: p.step_cells(h, c), chunks))
-
-    for _ in range(args.warmup):
-        step()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t
-    units = len(cells) * p.n * args.steps
+    band = OracleBand(rows, threads)
+    try:
+        for _ in range(args.warmup):
+            band.step()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            band.step()
+        el = time.perf_counter() - t
+    finally:
+        band.close()
+    units = band.updates_per_step() * args.steps
     value = units / el
-    sample = (f"{rows} grid rows ({len(cells)} cells x {p.n} velocities) of the 2048x2048 cavity per step, "
-              f"oracle step evaluated cell by cell on {threads} host threads")
+    sample = (f"{rows} grid rows ({band.ncells} cells x {band.p.n} velocities) of the 2048x2048 cavity per step, "
+              f"oracle step evaluated cell by cell, one contiguous chunk per host thread, {threads} threads")
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -694,23 +757,34 @@ def main(argv=None):
     if dist.rank == 0:
         if dist.world == 1 and not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
-            ups, sample = oracle_sample(12.0, threads)
-            ups1, sample1 = oracle_sample(4.0, 1)
+            ups, sample = oracle_sample(12.0, threads, rows=256)
+            ups1, sample1 = oracle_sample(4.0, 1, rows=16)
             out["cpu_baseline"] = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
                                    "sample": f"oracle FP64 step on {sample['cells_per_pass']} cells "
-                                             f"(8 middle rows) of the 2048x2048 x 144 workload, "
-                                             f"{sample['passes']} passes in {sample['seconds']:.1f} s",
+                                             f"({sample['rows']} middle rows) of the 2048x2048 x 144 workload, "
+                                             f"one contiguous chunk per thread, {sample['passes']} passes "
+                                             f"in {sample['seconds']:.1f} s",
                                    "single_thread_value": ups1}
-            ttr = out.get("time_to_residual")
-            if ttr and "fp64" in ttr:
-                # the oracle marching the same 32 cavities to the same residual: the FP64
-                # march's step counts (identical to the oracle's, which the configs cases
-                # check) times the updates per step at the oracle's measured rate
-                updates = float(sum(ttr["fp64"]["steps"])) * 128 * 128 * 64
-                ttr["oracle_extrapolated"] = {
-                    "seconds": updates / ups, "cores": threads,
-                    "basis": "extrapolated: FP64 march steps x 128^2 x 64 updates at the cpu_baseline rate",
-                    "vs_warm_dc": (updates / ups) / ttr["warm_dc"]["seconds"] if ttr.get("warm_dc") else None}
+            if not args.no_extras:
+                out["configs_time_to_residual"] = run_configs_time_to_residual()
+        ttr = out.get("time_to_residual")
+        if ttr:
+            # the oracle marching the same 256 cavities to the same residual, extrapolated: the
+            # FP64 march's step counts (equal to the oracle's, which the configurations'
+            # cases check) times the updates per step at the oracle's rate measured on the
+            # 128^2 cavity configurations (same grid and velocity set)
+            cases = [c for c in out.get("configs_time_to_residual", []) if c["case"].startswith("cavity 128x128 D2Q^h_64")]
+            rate = (sum(c["oracle"]["steps"] for c in cases) * 128 * 128 * 64 / sum(c["oracle"]["seconds"] for c in cases)
+                    if cases else None)
+            if rate:
+                full = ttr["held_out_256"]
+                upd = float(sum(full["fp64"]["steps"])) * 128 * 128 * 64
+                full["oracle_extrapolated"] = {
+                    "seconds": upd / rate, "updates_per_s": rate, "cores": os.cpu_count(),
+                    "basis": "extrapolated: FP64 march steps x 128^2 x 64 updates at the oracle's rate measured "
+                             "on the 128^2 D2Q^h_64 cavity configurations",
+                    "vs_warm_dc": (upd / rate) / full["warm_dc"]["seconds"] if full.get("warm_dc") else None}
+            out["ttr_summary"] = ttr_summary(ttr, rate)
         print(json.dumps(out), flush=True)
     dist.close()
     return 0

@@ -117,3 +117,41 @@ def test_gc_paused_restores_the_collector():
         assert not gc.isenabled()          # a collector that was off stays off
     finally:
         gc.enable()
+
+
+def _fake_ttr():
+    def run(sec, err, n):
+        return {"seconds": sec, "max_err_vs_fp64": err, "checked": n, "speedup_vs_fp64": 100.0 / sec}
+    full = {"fp64": {"seconds": 100.0, "steps": [1000] * 256},
+            "batch_dc": run(8.0, 2e-6, 256), "warm_dc": run(5.0, 3e-6, 256)}
+    sub = {"fp64": {"seconds": 22.0}, "fp64_concurrent": {"seconds": 12.0}, "fp32_dc": {"seconds": 7.0},
+           "batch_dc": run(1.0, 1e-6, 32), "warm_dc": run(0.7, 1e-6, 32)}
+    return {"held_out_256": full, "ablation_32": sub}
+
+
+def test_time_to_residual_digest_is_short_and_complete():
+    """The digest printed as the bench line's last key (the part of a long line that a
+    tail-truncated log keeps): counts, seconds, speed-up and worst error of each variant."""
+    d = bench.ttr_summary(_fake_ttr(), oracle_rate=1e9)
+    assert d["n"] == 256 and d["checked"] == 256
+    assert d["fp64_s"] == 100.0 and d["warm_dc_s"] == 5.0 and d["warm_vs_fp64"] == 20.0
+    assert d["warm_dc_max_du"] == 3e-6 and d["batch_dc_max_du"] == 2e-6
+    assert d["first32"]["fp32_dc_s"] == 7.0
+    assert d["oracle_extrap_s"] == pytest.approx(256 * 1000 * 128 * 128 * 64 / 1e9, rel=1e-3)
+    assert len(json.dumps(d)) < 700
+
+
+def test_oracle_band_one_contiguous_chunk_per_thread():
+    """The CPU baseline's sample: a band of middle rows of the 2048^2 workload, split into one
+    contiguous run of cells per thread, all chunks together covering the band once."""
+    import numpy as np
+    band = bench.OracleBand(rows=3, threads=4)
+    try:
+        cells = np.concatenate(band.chunks)
+        assert len(band.chunks) == 4 and band.ncells == 3 * 2048
+        np.testing.assert_array_equal(np.diff(cells), 1)
+        assert all(len(c) == 3 * 2048 // 4 for c in band.chunks)
+        assert band.updates_per_step() == 3 * 2048 * 144
+        band.step()
+    finally:
+        band.close()
