@@ -186,7 +186,14 @@ lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
  * deferred until after the next row's transport, its moments exchanged through mbarrier
  * phases instead of a block barrier (steps without the residual); FP32 cavities with nx a
  * multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12 warps (6 only for paths 6 and
- * 7), M = 8 with 2 or 4 warps (path 5)).
+ * 7), M = 8 with 2 or 4 warps (path 5)),
+ * 8 the column march of path 4 on a strip-tiled state (M = 12 with 6 warps, M = 8 with 4):
+ * choosing path 8 moves the current state into that layout (lbm_state_tiling), where one
+ * row of a 64-cell strip, all velocities, is one contiguous stretch of memory, so that a
+ * warp copies its lines of a row with one bulk copy; any other path moves it back to the
+ * planar layout.  Host transfers (lbm_get_state, lbm_set_state, lbm_set_moments,
+ * lbm_warm_start) and the diagnostics stay planar on the host side; lbm_solve's refinement
+ * sweeps run on the planar layout and return the state to the tiled one.
  * It changes speed, not results beyond rounding order.
  * lbm_init picks a default; lbm_set_variant returns LBM_EUNSUPPORTED for a combination
  * without a compiled kernel.  Used by the autotuner.  Call between steps only. */
@@ -226,14 +233,23 @@ lbm_status lbm_set_state(lbm_sim *sim, const double *h);
 lbm_status lbm_set_moments(lbm_sim *sim, const double *moments);
 
 /* Device pointer of the current state (FP64 or FP32 elements per the precision) and
- * the step counter.  The pointer changes after every step (double buffering).  The value
- * of velocity a at cell (x, y) is at element a * plane_pitch + y * row_pitch + x
- * (lbm_state_layout); the library currently keeps every state planar [a][y][x]
- * (plane_pitch = nx ny, row_pitch = nx), but callers that address the device state should
- * take the pitches from lbm_state_layout.  Host arrays of the ABI (lbm_init,
- * lbm_get_state, lbm_set_state) are planar. */
+ * the step counter.  The pointer changes after every step (double buffering).  In the
+ * planar layout [a][y][x] the value of velocity a at cell (x, y) is at element
+ * a * plane_pitch + y * row_pitch + x (lbm_state_layout: plane_pitch = nx ny, row_pitch =
+ * nx); lbm_state_layout returns LBM_EUNSUPPORTED while the state is strip-tiled (load path
+ * 8).  Host arrays of the ABI (lbm_init, lbm_get_state, lbm_set_state) are planar. */
 lbm_status lbm_state_device(lbm_sim *sim, void **ptr, long *step);
 lbm_status lbm_state_layout(const lbm_sim *sim, long *plane_pitch, long *row_pitch);
+/* The strip-tiled layout of load path 8 (all outputs 0 while the state is planar): tiles of
+ * tile_width = 64 cells in x, tile t holding x in [64 t - x_shift, 64 t - x_shift + 64)
+ * with x_shift = 32 (so that the column march's 64-cell strips are whole tiles), the value
+ * of velocity a at cell (x, y) at element
+ *   ((x + x_shift) / 64) * tile_pitch + y * row_pitch + a * 64 + (x + x_shift) % 64,
+ * row_pitch = 64 n, tile_pitch = ny row_pitch.  The buffer holds nx / 64 + 1 tiles; the
+ * positions outside the grid are padding.  Not in the paper: a memory layout for the
+ * march's access pattern. */
+lbm_status lbm_state_tiling(const lbm_sim *sim, int *tile_width, int *x_shift, long *tile_pitch,
+                            long *row_pitch);
 
 /* Squared norms of device vectors, FP64 accumulation (the residual reduction):
  *   out[0] = sum (a_i - b_i)^2, out[1] = sum a_i^2, i < count; b may be NULL (then

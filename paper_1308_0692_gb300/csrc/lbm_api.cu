@@ -4,6 +4,7 @@
 // discrete scheme (time step from the CFL number, upwind Courant numbers, relaxation
 // factor, wall-ghost coefficients of Eqs. 8-9), device memory layout, and the
 // stream-ordered launch sequence of the fused step kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -24,11 +25,11 @@ cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s
 cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s,
                                bool merged);
 cudaError_t prepare_step_f32_tma(int m, int g);
-cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool resid, const StepArgs &a, int grid,
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool tiled, bool resid, const StepArgs &a, int grid,
                                   cudaStream_t s);
-cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int *grid);
+cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, bool tiled, int *grid);
 cudaError_t launch_step_so(int prec, int m, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-bool march_supported(int m, int g, int slots, bool defer);
+bool march_supported(int m, int g, int slots, bool defer, bool tiled);
 int defect_lanes(int m);
 int correct_lanes(int m);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
@@ -54,7 +55,9 @@ struct lbm_sim {
     int splitting;        // LBM_SPLIT_LIE (stored state h) or LBM_SPLIT_STRANG[_EXACT] (stored g = R(dt/2) h)
     int order;            // transport order: 1 (first-order upwind, the paper's) or 2
     int grid;             // blocks of the bulk step kernel
-    int march_grid;       // persistent blocks of the column-march kernel (load paths 4 to 7)
+    int march_grid;       // persistent blocks of the column-march kernel (load paths 4 to 8)
+    bool tiled;           // the state buffers hold the strip-tiled layout (load path 8)
+    long tile_pitch;      // floats per tile of that layout
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
     int *wall_segs;       // device list of wall segments for the current lanes
     int wall_cap;
@@ -116,6 +119,12 @@ size_t elem_size(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(f
 
 bool kernel_m_supported(int m) { return m == 3 || m == 4 || m == 6 || m == 8 || m == 12; }
 
+// grids the column march can take (nx a multiple of 64, at least two strips' width, ten
+// rows); FP32 cavities of such grids get state buffers large enough for the strip-tiled
+// layout of load path 8 as well
+bool march_grid_ok(const lbm_problem *p) { return p->nx % 64 == 0 && p->nx >= 128 && p->ny >= 10; }
+bool tile_eligible(const lbm_problem *p) { return p->prec == LBM_FP32_PERTURB && p->geom == LBM_CAVITY && march_grid_ok(p); }
+
 struct Layout {
     size_t off_buf[4];
     size_t off_tab64, off_tab32, off_hdr, off_partials, off_result, off_moments, off_fy, off_fx, off_wsegs;
@@ -129,7 +138,8 @@ Layout make_layout(const lbm_vset *vs, const lbm_problem *p)
 {
     Layout L{};
     const long ncells = (long)p->nx * p->ny;
-    const size_t nvals = (size_t)vs->m * vs->m * ncells;
+    size_t nvals = (size_t)vs->m * vs->m * ncells;
+    if (tile_eligible(p)) nvals = std::max(nvals, tiled_values(vs->m * vs->m, p->nx, p->ny));
     const size_t es = elem_size(p->prec);
     L.nbuf = (p->prec == LBM_FP64) ? 2 : 4;
     size_t off = 0;
@@ -245,6 +255,8 @@ void fill_tables(lbm_sim *s, std::vector<double> &t64, std::vector<float> &t32, 
 
 bool planar(const lbm_sim *s) { return s->args.pa == s->ncells; }
 
+void drop_graphs_fwd(lbm_sim *s);
+
 // factor of the non-equilibrium part from h to the stored g = R(dt/2) h
 double half_relax_factor(const lbm_sim *s)
 {
@@ -277,6 +289,42 @@ lbm_status upload_state(lbm_sim *s, const double *h, void *dst)
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "uploading the state");
+}
+
+// Move the current state between the planar and the strip-tiled layout (through the other
+// state buffer, which the next step overwrites anyway).  Stream-ordered.
+cudaError_t set_tiled(lbm_sim *s, bool tiled)
+{
+    if (s->tiled == tiled) return cudaSuccess;
+    cudaError_t e = launch_tile_convert(tiled, (const float *)s->buf[s->cur], (float *)s->buf[s->cur ^ 1], s->nv,
+                                        s->prob.nx, s->prob.ny, s->tile_pitch, s->stream);
+    if (e != cudaSuccess) return e;
+    s->cur ^= 1;
+    s->tiled = tiled;
+    s->args.tile_pitch = tiled ? s->tile_pitch : 0;
+    drop_graphs_fwd(s);
+    return cudaSuccess;
+}
+
+// The current state in the planar layout: the state itself, or (strip-tiled state) a planar
+// copy in the other state buffer.  Stream-ordered; valid until the next step.
+const void *planar_state(lbm_sim *s, cudaError_t *e)
+{
+    *e = cudaSuccess;
+    if (!s->tiled) return s->buf[s->cur];
+    *e = launch_tile_convert(false, (const float *)s->buf[s->cur], (float *)s->buf[s->cur ^ 1], s->nv, s->prob.nx,
+                             s->prob.ny, s->tile_pitch, s->stream);
+    return s->buf[s->cur ^ 1];
+}
+
+// Where a writer puts a planar state, and the step that makes it current: a strip-tiled
+// simulation takes the planar state in the other buffer and tiles it into the current one.
+void *planar_target(lbm_sim *s) { return s->tiled ? s->buf[s->cur ^ 1] : s->buf[s->cur]; }
+cudaError_t commit_planar(lbm_sim *s)
+{
+    if (!s->tiled) return cudaSuccess;
+    return launch_tile_convert(true, (const float *)s->buf[s->cur ^ 1], (float *)s->buf[s->cur], s->nv, s->prob.nx,
+                               s->prob.ny, s->tile_pitch, s->stream);
 }
 
 StepArgs base_args(const lbm_sim *s) { return s->args; }
@@ -336,6 +384,8 @@ void drop_graphs(lbm_sim *s)
         s->graph_ok[p] = false;
     }
 }
+
+void drop_graphs_fwd(lbm_sim *s) { drop_graphs(s); }
 
 // Enqueue steps [first, first + count) starting from buffer `cur` on `st` (no bookkeeping).
 cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur, cudaStream_t st)
@@ -446,8 +496,9 @@ int default_lanes_per_cell(int prec, int m)
 
 // row slots of the column march's ring for load paths 4 (four), 5 (five), 6 (two slots,
 // two blocks per SM) and 7 (four, relaxation deferred by one row)
-static int march_slots(int pf) { return pf == 6 ? 2 : pf == 7 ? 4 : pf; }
+static int march_slots(int pf) { return pf == 6 ? 2 : (pf == 7 || pf == 8) ? 4 : pf; }
 static bool march_defer(int pf) { return pf == 7; }
+static bool march_tiled(int pf) { return pf == 8; }
 
 bool step_supported(int prec, int m, int g, int pf)
 {
@@ -459,7 +510,8 @@ bool step_supported(int prec, int m, int g, int pf)
         for (auto &v : tma) if (v[0] == m && v[1] == g) return true;
         return false;
     }
-    if (pf >= 4 && pf <= 7) return prec == LBM_FP32_PERTURB && march_supported(m, g, march_slots(pf), march_defer(pf));
+    if (pf >= 4 && pf <= 8)
+        return prec == LBM_FP32_PERTURB && march_supported(m, g, march_slots(pf), march_defer(pf), march_tiled(pf));
     if (prec == LBM_FP64) {
         for (auto &v : f64) if (v[0] == m && v[1] == g && v[2] == pf) return true;
     } else {
@@ -472,7 +524,8 @@ cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepAr
                         cudaStream_t s)
 {
     if (pf == 2 || pf == 3) return launch_step_f32_tma(m, g, resid, a, grid, s, pf == 3);
-    if (pf >= 4 && pf <= 7) return launch_step_f32_march(m, g, march_slots(pf), march_defer(pf), resid, a, grid, s);
+    if (pf >= 4 && pf <= 8)
+        return launch_step_f32_march(m, g, march_slots(pf), march_defer(pf), march_tiled(pf), resid, a, grid, s);
     if (prec == LBM_FP64)
         return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
                       : launch_step_f64_small(m, g, pf, resid, a, grid, s);
@@ -610,6 +663,8 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     s->splitting = LBM_SPLIT_LIE;
     s->order = 1;
     s->march_grid = 0;
+    s->tiled = false;
+    s->tile_pitch = (long)prob->ny * vs->m * vs->m * LBM_TILE_W;
     s->step = 0;
     s->resid_step = -1;
     s->cur = 0;
@@ -654,7 +709,7 @@ lbm_status lbm_init(const lbm_vset *vs, const lbm_problem *prob, const double *i
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->hdr, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, sizeof(double) * 16, s->stream);
-    const size_t state_bytes = (size_t)s->nv * s->ncells * elem_size(prob->prec);
+    const size_t state_bytes = (L.off_buf[1] - L.off_buf[0]);
     if (e == cudaSuccess && !init_h) e = cudaMemsetAsync(s->buf[0], 0, state_bytes, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -821,6 +876,12 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
     out.residual = r;
     out.defect = r;
     // --- FP32: mixed-precision refinement (defect in FP64, correction march in FP32) ---
+    // (on the planar state: a strip-tiled one is moved back to that layout afterwards)
+    const bool was_tiled = s->tiled;
+    if (refine_sweeps > 0 && was_tiled) {
+        cudaError_t e = set_tiled(s, false);
+        if (e != cudaSuccess) return cuda_fail(e, "moving the state to the planar layout");
+    }
     if (refine_sweeps > 0) {
         void *H = s->buf[s->cur];
         void *D = s->buf[2];
@@ -923,6 +984,11 @@ lbm_status lbm_solve(lbm_sim *s, double tol, long max_steps, int refine_sweeps, 
         }
         out.defect = r64;
     }
+    if (refine_sweeps > 0 && was_tiled) {
+        cudaError_t e = set_tiled(s, true);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "moving the state to the strip-tiled layout");
+    }
     if (info) *info = out;
     return LBM_OK;
 }
@@ -942,7 +1008,8 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "warm start");
     e = launch_warm_state(pred, s->prob.nx, s->prob.ny, s->args.pa, s->args.py, s->vs.m, s->hdr->xi1, s->hdr->w1,
-                          u_w / s->u_ref, s->buf[s->cur], s->prob.prec, s->stream);
+                          u_w / s->u_ref, planar_target(s), s->prob.prec, s->stream);
+    if (e == cudaSuccess) e = commit_planar(s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the warm-start state");
 }
@@ -950,7 +1017,7 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (prefetch < 0 || prefetch > 7) return fail(LBM_EINVAL, "load path must be 0 to 7");
+    if (prefetch < 0 || prefetch > 8) return fail(LBM_EINVAL, "load path must be 0 to 8");
     if (s->order == 2)
         return fail(LBM_EUNSUPPORTED, "the second-order transport has one kernel variant (lbm_set_transport)");
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
@@ -960,8 +1027,10 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
         return fail(LBM_EUNSUPPORTED, "TMA staging needs a cavity with nx and the cell count multiples of 4");
     if ((prefetch == 2 || prefetch == 3) && !planar(s))
         return fail(LBM_EUNSUPPORTED, "the TMA segment kernels need the planar state layout (nx < 64)");
-    if (prefetch >= 4 && (s->prob.nx % 64 != 0 || s->prob.nx < 128 || s->prob.ny < 10))
+    if (prefetch >= 4 && !march_grid_ok(&s->prob))
         return fail(LBM_EUNSUPPORTED, "the column march needs nx a multiple of 64, nx >= 128 and ny >= 10");
+    if (prefetch == 8 && !tile_eligible(&s->prob))
+        return fail(LBM_EUNSUPPORTED, "the strip-tiled march needs an FP32 cavity");
     if (prefetch == 2 || prefetch == 3) {
         cudaError_t e = prepare_step_f32_tma(s->vs.m, warps_per_segment);
         if (e != cudaSuccess) return cuda_fail(e, "enabling the TMA kernel's shared memory");
@@ -969,11 +1038,15 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
     if (prefetch >= 4) {
         int grid = 0;
         cudaError_t e = prepare_step_f32_march(s->vs.m, warps_per_segment, march_slots(prefetch), march_defer(prefetch),
-                                               &grid);
+                                               march_tiled(prefetch), &grid);
         if (e != cudaSuccess) return cuda_fail(e, "enabling the column-march kernel's shared memory");
         if (grid <= 0) return fail(LBM_EUNSUPPORTED, "the column-march kernel does not fit on an SM");
         s->march_grid = grid;
     }
+    // load path 8 marches the strip-tiled state, every other path the planar one
+    cudaError_t e = set_tiled(s, prefetch == 8);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "changing the state layout");
     s->prefetch = prefetch;
     return set_lanes(s, warps_per_segment);
 }
@@ -1007,6 +1080,9 @@ lbm_status lbm_set_transport(lbm_sim *s, int order)
     if (s->step != 0) return fail(LBM_EINVAL, "the transport order is chosen before the first step");
     s->order = order;
     s->prefetch = 0;
+    cudaError_t e = set_tiled(s, false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "changing the state layout");
     return set_lanes(s, default_lanes_per_cell(s->prob.prec, s->vs.m));
 }
 
@@ -1054,8 +1130,11 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     const int m = s->vs.m;
-    cudaError_t e = launch_moments(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m,
-                                   s->prob.nx, s->prob.ny, s->u_ref, s->moments, s->stream);
+    cudaError_t e;
+    const void *hs = planar_state(s, &e);
+    if (e == cudaSuccess)
+        e = launch_moments(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr, m, s->prob.nx, s->prob.ny,
+                           s->u_ref, s->moments, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the moments kernel");
     double *outs[6] = {rho, ux, uy, pxx, pxy, pyy};
     std::vector<double> tmp;
@@ -1088,9 +1167,9 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
         const int nx = s->prob.nx, ny = s->prob.ny;
         const bool cav = s->prob.geom == LBM_CAVITY;
         e = s->order == 2
-            ? launch_face_flux2(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
+            ? launch_face_flux2(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
                                 cav, s->u_ref, s->flux_y, s->flux_x, s->stream)
-            : launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
+            : launch_face_flux(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr, m, nx, ny,
                                cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
         std::vector<double> fy((size_t)(ny + 1) * nx), fx(cav ? (size_t)ny * (nx + 1) : 0);
@@ -1124,11 +1203,14 @@ lbm_status lbm_face_flux(lbm_sim *s, double *flux_y, double *flux_x)
     const int nx = s->prob.nx, ny = s->prob.ny;
     const bool cav = s->prob.geom == LBM_CAVITY;
     if (flux_x && !cav) return fail(LBM_EINVAL, "flux_x is defined for the cavity only");
-    cudaError_t e = s->order == 2
-        ? launch_face_flux2(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, s->vs.m, nx, ny,
-                            cav, s->u_ref, s->flux_y, s->flux_x, s->stream)
-        : launch_face_flux(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr,
-                           s->vs.m, nx, ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
+    cudaError_t e;
+    const void *hs = planar_state(s, &e);
+    if (e == cudaSuccess)
+        e = s->order == 2
+            ? launch_face_flux2(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr, s->vs.m, nx, ny,
+                                cav, s->u_ref, s->flux_y, s->flux_x, s->stream)
+            : launch_face_flux(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr,
+                               s->vs.m, nx, ny, cav, s->u_ref, s->flux_y, s->flux_x, nullptr, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launching the face-flux kernel");
     if (flux_y)
         e = cudaMemcpyAsync(flux_y, s->flux_y, sizeof(double) * (size_t)(ny + 1) * nx,
@@ -1151,8 +1233,10 @@ lbm_status lbm_get_state(lbm_sim *s, double *h)
         // the staging area of an FP64 simulation is its other state buffer, which the next
         // step overwrites anyway
         double *stage = staging(s, s->buf[s->cur]);
-        e = launch_relayout(s->prob.prec, false, stage, s->buf[s->cur], s->nv, s->prob.nx, s->prob.ny, s->args.pa,
-                            s->args.py, s->stream);
+        const void *hs = planar_state(s, &e);
+        if (e == cudaSuccess)
+            e = launch_relayout(s->prob.prec, false, stage, const_cast<void *>(hs), s->nv, s->prob.nx, s->prob.ny,
+                                s->args.pa, s->args.py, s->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h, stage, nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     }
@@ -1163,7 +1247,11 @@ lbm_status lbm_get_state(lbm_sim *s, double *h)
 lbm_status lbm_set_state(lbm_sim *s, const double *h)
 {
     if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
-    return upload_state(s, h, s->buf[s->cur]);
+    lbm_status st = upload_state(s, h, planar_target(s));
+    if (st != LBM_OK || !s->tiled) return st;
+    cudaError_t e = commit_planar(s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "tiling the state");
 }
 
 lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
@@ -1189,8 +1277,8 @@ lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
                                     s->stream);
     if (e == cudaSuccess)
         e = launch_moments_state(s->prob.prec, s->moments, s->prob.nx, s->prob.ny, s->args.pa, s->args.py, s->vs.m,
-                                 s->hdr, s->u_ref, s->buf[s->cur],
-                                 s->stream);
+                                 s->hdr, s->u_ref, planar_target(s), s->stream);
+    if (e == cudaSuccess) e = commit_planar(s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the state from moments");
 }
@@ -1206,8 +1294,20 @@ lbm_status lbm_state_device(lbm_sim *s, void **ptr, long *step)
 lbm_status lbm_state_layout(const lbm_sim *s, long *plane_pitch, long *row_pitch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (s->tiled)
+        return fail(LBM_EUNSUPPORTED, "the state is strip-tiled (load path 8): see lbm_state_tiling");
     if (plane_pitch) *plane_pitch = s->args.pa;
     if (row_pitch) *row_pitch = s->args.py;
+    return LBM_OK;
+}
+
+lbm_status lbm_state_tiling(const lbm_sim *s, int *tile_width, int *x_shift, long *tile_pitch, long *row_pitch)
+{
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (tile_width) *tile_width = s->tiled ? LBM_TILE_W : 0;
+    if (x_shift) *x_shift = s->tiled ? LBM_TILE_SHIFT : 0;
+    if (tile_pitch) *tile_pitch = s->tiled ? s->tile_pitch : 0;
+    if (row_pitch) *row_pitch = s->tiled ? (long)s->nv * LBM_TILE_W : 0;
     return LBM_OK;
 }
 

@@ -9,6 +9,18 @@
 #define LBM_MAX_M 12
 #define LBM_MAX_V (LBM_MAX_M * LBM_MAX_M)
 #define LBM_BLOCK 256
+#define LBM_TILE_W 64        // cells per tile row of the strip-tiled state
+#define LBM_TILE_SHIFT 32    // tile boundaries at x = 32 (mod 64): the march's strips are whole tiles
+
+// offset of cell (x, y), velocity 0, in the strip-tiled state of n velocities
+__host__ __device__ inline long tile_off(long x, long y, int n, long tile_pitch)
+{
+    const long xs = x + LBM_TILE_SHIFT;
+    return (xs / LBM_TILE_W) * tile_pitch + y * (long)n * LBM_TILE_W + (xs % LBM_TILE_W);
+}
+// tiles of a row of nx cells, and floats of a tiled state
+inline long tiles_for(int nx) { return (nx + LBM_TILE_SHIFT + LBM_TILE_W - 1) / LBM_TILE_W; }
+inline size_t tiled_values(int n, int nx, int ny) { return (size_t)tiles_for(nx) * ny * n * LBM_TILE_W; }
 
 // Per-velocity coefficient table of one simulation, structure of arrays, in device memory.
 // Rows (each LBM_MAX_V long), velocity a = iy*M + ix:
@@ -42,10 +54,15 @@ struct StepArgs {
     double *partials;     // per-block residual partial sums [2 * gridDim.x]
     int nx, ny;
     long ncells;
-    // state layout: value (velocity a, cell x, y) at a * pa + y * py + x.  Every state is
-    // planar [a][y][x] (pa = ncells, py = nx): the step kernels index it as a * ncells + c,
-    // the diagnostics and the host-transfer relayout take the pitches
+    // state layout: value (velocity a, cell x, y) at a * pa + y * py + x.  A planar state
+    // [a][y][x] (pa = ncells, py = nx): the step kernels index it as a * ncells + c, the
+    // diagnostics and the host-transfer relayout take the pitches
     long pa, py;
+    // strip-tiled FP32 state of the tiled column march (load path 8), 0 when planar: tiles of
+    // LBM_TILE_W cells in x, tile t holding x in [64 t - 32, 64 t + 32), laid out
+    // [t][y][a][x - 64 t + 32], so that one row of a 64-cell strip is one contiguous stretch
+    // of n * 256 bytes; value (a, x, y) at tile_off(x, y, n, tile_pitch) + a * LBM_TILE_W
+    long tile_pitch;      // floats per tile: ny * n * LBM_TILE_W
     int cavity;
     int homogeneous;      // drop the wall driving terms (correction sweeps)
     const int *wall_segs; // segments (32 consecutive cells) that contain a wall cell
@@ -107,6 +124,9 @@ cudaError_t launch_relayout(int prec, bool to_layout, double *planar, void *stat
                             long pa, long py, cudaStream_t s);
 
 cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream_t s);
+// FP32 state planar [a][y][x] <-> strip-tiled (to_tiled: planar -> tiled)
+cudaError_t launch_tile_convert(bool to_tiled, const float *src, float *dst, int n, int nx, int ny, long tile_pitch,
+                                cudaStream_t s);
 // state h from device FP64 moments [6][ncells] (rho, u_x, u_y, P_xx, P_xy, P_yy)
 cudaError_t launch_moments_state(int prec, const double *mom, int nx, int ny, long pa, long py, int m,
                                  const TableHeader *hdr, double u_ref, void *h, cudaStream_t s);

@@ -469,6 +469,35 @@ cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t
     return cudaGetLastError();
 }
 
+// Planar [a][y][x] <-> strip-tiled FP32 state: one block per row y of tile t, threads over
+// the tile row's n * 64 values (contiguous in both layouts for each velocity); the padding
+// positions of the tiled layout (x outside [0, nx)) are written as zero.
+__global__ void __launch_bounds__(256) tile_convert_kernel(int to_tiled, const float *__restrict__ src,
+                                                          float *__restrict__ dst, int n, int nx, int ny,
+                                                          long tile_pitch)
+{
+    const int t = blockIdx.x, y = blockIdx.y;
+    const long ncells = (long)nx * ny;
+    const long trow = (long)t * tile_pitch + (long)y * n * LBM_TILE_W;
+    const int x0 = t * LBM_TILE_W - LBM_TILE_SHIFT;
+    for (int i = threadIdx.x; i < n * LBM_TILE_W; i += blockDim.x) {
+        const int a = i / LBM_TILE_W, p = i - a * LBM_TILE_W;
+        const int x = x0 + p;
+        const bool in = x >= 0 && x < nx;
+        const long pl = (long)a * ncells + (long)y * nx + x;
+        if (to_tiled) dst[trow + i] = in ? src[pl] : 0.f;
+        else if (in) dst[pl] = src[trow + i];
+    }
+}
+
+cudaError_t launch_tile_convert(bool to_tiled, const float *src, float *dst, int n, int nx, int ny, long tile_pitch,
+                                cudaStream_t s)
+{
+    const dim3 grid((unsigned)tiles_for(nx), (unsigned)ny);
+    tile_convert_kernel<<<grid, 256, 0, s>>>(to_tiled ? 1 : 0, src, dst, n, nx, ny, tile_pitch);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_pairs(const double *partials, int nparts, double *out, int nres,
                                   cudaStream_t s)
 {

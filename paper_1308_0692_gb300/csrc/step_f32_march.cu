@@ -2,45 +2,49 @@
 // is in step_march.cuh).  Load path 4 keeps two rows of copies in flight per warp (ring of
 // four row slots), load path 5 three (ring of five), load path 6 none (ring of two, two
 // blocks per SM), load path 7 is path 4 with the relaxation of each row deferred until
-// after the next row's transport (steps without the residual).
+// after the next row's transport (steps without the residual), load path 8 is path 4 on the
+// strip-tiled state (one contiguous copy per warp and row).
 #include "step_march.cuh"
 
 using namespace lbmk;
 
-#define LBM_MARCH_LIST(X) \
-    X(12, 6, 4, false)    \
-    X(12, 6, 5, false)    \
-    X(12, 6, 2, false)    \
-    X(12, 6, 4, true)     \
-    X(12, 12, 4, false)   \
-    X(12, 12, 5, false)   \
-    X(8, 4, 5, false)     \
-    X(8, 2, 5, false)
+#define LBM_MARCH_LIST(X)     \
+    X(12, 6, 4, false, false) \
+    X(12, 6, 5, false, false) \
+    X(12, 6, 2, false, false) \
+    X(12, 6, 4, true, false)  \
+    X(12, 12, 4, false, false) \
+    X(12, 12, 5, false, false) \
+    X(8, 4, 5, false, false)  \
+    X(8, 2, 5, false, false)  \
+    X(12, 6, 4, false, true)  \
+    X(8, 4, 4, false, true)
 
-bool march_supported(int m, int g, int slots, bool defer)
+bool march_supported(int m, int g, int slots, bool defer, bool tiled)
 {
-#define LBM_MARCH_HAVE(M_, G_, S_, D_) \
-    if (m == M_ && g == G_ && slots == S_ && defer == D_) return true;
+#define LBM_MARCH_HAVE(M_, G_, S_, D_, T_) \
+    if (m == M_ && g == G_ && slots == S_ && defer == D_ && tiled == T_) return true;
     LBM_MARCH_LIST(LBM_MARCH_HAVE)
 #undef LBM_MARCH_HAVE
     return false;
 }
 
-cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool resid, const StepArgs &a, int grid,
-                                  cudaStream_t s)
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool tiled, bool resid, const StepArgs &a,
+                                  int grid, cudaStream_t s)
 {
-#define LBM_MARCH_LAUNCH(M_, G_, S_, D_)                                                          \
-    if (m == M_ && g == G_ && slots == S_ && defer == D_)                                         \
-        return resid ? launch_march<M_, G_, S_, D_, true>(a, grid, s) : launch_march<M_, G_, S_, D_, false>(a, grid, s);
+#define LBM_MARCH_LAUNCH(M_, G_, S_, D_, T_)                                                       \
+    if (m == M_ && g == G_ && slots == S_ && defer == D_ && tiled == T_)                          \
+        return resid ? launch_march<M_, G_, S_, D_, true, T_>(a, grid, s)                          \
+                     : launch_march<M_, G_, S_, D_, false, T_>(a, grid, s);
     LBM_MARCH_LIST(LBM_MARCH_LAUNCH)
 #undef LBM_MARCH_LAUNCH
     return cudaErrorInvalidValue;
 }
 
-cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int *grid)
+cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, bool tiled, int *grid)
 {
-#define LBM_MARCH_PREP(M_, G_, S_, D_) \
-    if (m == M_ && g == G_ && slots == S_ && defer == D_) return prepare_march<M_, G_, S_, D_>(grid);
+#define LBM_MARCH_PREP(M_, G_, S_, D_, T_) \
+    if (m == M_ && g == G_ && slots == S_ && defer == D_ && tiled == T_) return prepare_march<M_, G_, S_, D_, T_>(grid);
     LBM_MARCH_LIST(LBM_MARCH_PREP)
 #undef LBM_MARCH_PREP
     return cudaErrorInvalidValue;

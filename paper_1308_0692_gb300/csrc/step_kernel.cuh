@@ -41,7 +41,8 @@
 // mixed-precision refinement); DEFECT: write h^{n+1} - h^n instead of h^{n+1} (FP64
 // defect of an FP32 state); PART: wall kernel; PF: bulk variant that issues all own-cell
 // and y-neighbour loads of the warp's velocity rows before the arithmetic (more loads in
-// flight per warp, more registers).
+// flight per warp, more registers); TILED: the state is strip-tiled (lbm_internal.h,
+// tile_off) instead of planar -- used by the wall kernel beside the tiled column march.
 #pragma once
 
 #include "lbm_internal.h"
@@ -66,7 +67,7 @@ struct Shape {
 };
 
 template <typename TS, typename TC, int M, int G, bool RESID, bool SOURCE, bool DEFECT, bool PART,
-          bool PF = false>
+          bool PF = false, bool TILED = false>
 __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
 {
     constexpr int SPB = Shape<G>::SPB;
@@ -108,10 +109,26 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
 
     const bool wl = WALLS && cav && x == 0, wr = WALLS && cav && x == nx - 1;
     const bool wb = WALLS && y == 0, wt = WALLS && y == ny - 1;
-    const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);        // periodic in Couette
-    const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
-    const long c_below = (y > 0) ? c - nx : c;
-    const long c_above = (y < ny - 1) ? c + nx : c;
+    static_assert(!TILED || (!PF && !SOURCE && !DEFECT), "the tiled state is marched by plain steps only");
+    // offsets of the cell and its four neighbours in the state, and the stride between
+    // velocities: planar (cell index, stride ncells) or strip-tiled (cavity only)
+    long c_at, c_left, c_right, c_below, c_above, vstride;
+    if constexpr (TILED) {
+        const long tp = a.tile_pitch;
+        vstride = LBM_TILE_W;
+        c_at = tile_off(x, y, M * M, tp);
+        c_left = x > 0 ? tile_off(x - 1, y, M * M, tp) : c_at;
+        c_right = x < nx - 1 ? tile_off(x + 1, y, M * M, tp) : c_at;
+        c_below = y > 0 ? c_at - (long)M * M * LBM_TILE_W : c_at;
+        c_above = y < ny - 1 ? c_at + (long)M * M * LBM_TILE_W : c_at;
+    } else {
+        vstride = ncells;
+        c_at = c;
+        c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);        // periodic in Couette
+        c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
+        c_below = (y > 0) ? c - nx : c;
+        c_above = (y < ny - 1) ? c + nx : c;
+    }
     const TS *__restrict__ h = reinterpret_cast<const TS *>(a.h);
 
     // ---- wall densities rho'_w of the faces this cell touches (Eq. 9) ----
@@ -133,12 +150,12 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
                 while (m) {
                     const int L = __ffs(m) - 1;
                     m &= m - 1;
-                    const long cL = __shfl_sync(FULL, c, L);
+                    const long cL = __shfl_sync(FULL, c_at, L);
                     double part = 0.0;
                     for (int k = lane; k < NSIDE; k += 32) {
                         const int r = k / HALF, q = k - r * HALF;
                         const int iy = g * RPL + r, ix = side == 0 ? q : M - HALF + q;
-                        const TC v = (TC)ldg(h + (long)(iy * M + ix) * ncells + cL);
+                        const TC v = (TC)ldg(h + (long)(iy * M + ix) * vstride + cL);
                         const TC xv = pick<TC>(a.xi, a.xi_f, ix) * v;
                         part += side == 0 ? -(double)xv : (double)xv;
                     }
@@ -158,7 +175,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
                 TC rowsum = 0, left = 0, right = 0;
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
-                    const TC v = (TC)ldg(h + (long)(iy * M + ix) * ncells + c);
+                    const TC v = (TC)ldg(h + (long)(iy * M + ix) * vstride + c_at);
                     rowsum += v;
                     if (ix < HALF) left -= pick<TC>(a.xi, a.xi_f, ix) * v;       // towards the left wall
                     if (ix >= M - HALF) right += pick<TC>(a.xi, a.xi_f, ix) * v; // towards the right wall
@@ -200,11 +217,11 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
             const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
-            const long cy = xiy > TC(0) ? c_below : (xiy < TC(0) ? c_above : c);
+            const long cy = xiy > TC(0) ? c_below : (xiy < TC(0) ? c_above : c_at);
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * ncells;
-                hs[r * M + ix] = (TC)ldg(hp + c);
+                const TS *hp = h + (long)(iy * M + ix) * vstride;
+                hs[r * M + ix] = (TC)ldg(hp + c_at);
                 hyv[r * M + ix] = (TC)ldg(hp + cy);
             }
         }
@@ -216,7 +233,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * ncells;
+                const TS *hp = h + (long)(iy * M + ix) * vstride;
                 const TC hc = hs[r * M + ix];
                 TC v = hc;
                 if (ix >= M - HALF || ix < HALF) {
@@ -239,7 +256,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
             const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
             const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
-            const long cy = ypos ? c_below : (yneg ? c_above : c);
+            const long cy = ypos ? c_below : (yneg ? c_above : c_at);
             const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
             const TC rho_y = (TC)(ypos ? rb : rt);
             const TC u_y = (TC)(ypos ? a.u_bottom : a.u_top);
@@ -249,8 +266,8 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * ncells;
-                const TC hc = (TC)ldg(hp + c);
+                const TS *hp = h + (long)(iy * M + ix) * vstride;
+                const TC hc = (TC)ldg(hp + c_at);
                 const TC xix = pick<TC>(a.xi, a.xi_f, ix);
                 const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
                 TC v = hc;
@@ -306,7 +323,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a, const int bid)
             const TC jj = wom * jx;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const long off = (long)(iy * M + ix) * ncells + c;
+                const long off = (long)(iy * M + ix) * vstride + c_at;
                 const TC t = q + pick<TC>(a.xi, a.xi_f, ix) * jj;
                 TC v = b * hs[r * M + ix] + pick<TC>(a.w1, a.w1_f, ix) * t;
                 if (SOURCE) v += (TC)ldg(src + off);

@@ -32,6 +32,16 @@
 // Every wait on a copy is bounded: after the limit the warp sets the status word and a
 // block-wide abort flag, all warps leave the march at the next row barrier, wait (again
 // bounded) for the copies they still have in flight, and return.
+//
+// TILED (load path 8): the state is strip-tiled (lbm_internal.h): tile t holds x in
+// [64 t - 32, 64 t + 32) as [y][a][64], so the march's strip s is exactly tile s + 1 and one
+// row of it, all n velocities, is one contiguous stretch of n * 256 bytes.  Per row a warp
+// then copies its NV velocity lines with ONE bulk copy of NV * 256 contiguous bytes, plus,
+// per velocity, the 16 bytes of the neighbouring tile that hold its upwind x halo (positions
+// 60..63 of the left tile for xi_x > 0, 0..3 of the right tile for xi_x < 0; those tiles'
+// rows are being marched by the neighbouring blocks at about the same time, so these reads
+// are mostly L2 hits).  Every DRAM access of the march is then part of a long contiguous
+// stream instead of 144 separate 288-byte lines from planes 16.8 MB apart.
 #pragma once
 
 #include <cstdint>
@@ -41,12 +51,14 @@
 
 namespace lbmk {
 
-template <int M, int G, int S>
+template <int M, int G, int S, bool TILED = false>
 struct MarchShape {
     static constexpr int RPL = M / G;              // velocity rows per warp
     static constexpr int NV = RPL * M;             // velocities per warp
-    static constexpr int LINE = 72;                // floats per staged line (64 + 4 + 4)
-    static constexpr int SLOT = NV * LINE;         // floats of one warp's row slot
+    // planar: floats per staged line (64 + 4 + 4); tiled: dense 64-float lines, then a
+    // 4-float halo per velocity
+    static constexpr int LINE = TILED ? 64 : 72;
+    static constexpr int SLOT = TILED ? NV * (64 + 4) : NV * LINE;   // floats of one warp's row slot
     static constexpr int THREADS = 32 * G;
     static constexpr int SMEM = S * G * SLOT * 4 + S * G * 8;
     // a ring of two slots (the own row and its upwind row, nothing in flight ahead) is small
@@ -70,11 +82,12 @@ __device__ __forceinline__ int march_row0(int k, int rows, int nchunks)
     return 1 + (int)(((long)k * rows) / nchunks);
 }
 
-template <int M, int G, int S, bool RESID, bool DEFER>
-__global__ void __launch_bounds__(MarchShape<M, G, S>::THREADS, MarchShape<M, G, S>::MIN_BLOCKS)
+template <int M, int G, int S, bool RESID, bool DEFER, bool TILED = false>
+__global__ void __launch_bounds__(MarchShape<M, G, S, TILED>::THREADS, MarchShape<M, G, S, TILED>::MIN_BLOCKS)
 step_march_kernel(const StepArgs a)
 {
-    using Sh = MarchShape<M, G, S>;
+    using Sh = MarchShape<M, G, S, TILED>;
+    static_assert(!(TILED && DEFER), "the tiled march has no deferred-relaxation form");
     // deferred relaxation (steps without the residual): row t's moment partials are published
     // through an mbarrier phase and row t - 1 is relaxed after row t's transport, so a warp
     // meets the slowest warp's partials one transport later than at a block barrier
@@ -151,6 +164,19 @@ step_march_kernel(const StepArgs a)
     // plane offset of this lane's copy (lanes < NV issue one line each per row)
     const int kc = lane < NV ? lane : 0;
     const float *src_plane = h + (long)((g * RPL + kc / M) * M + (kc % M)) * ncells;
+    // tiled: rows of a tile are NVALL * 64 floats apart; this warp's lines start at velocity
+    // g * NV; lane kc's halo comes from the left tile (xi_x > 0) or the right tile (xi_x < 0),
+    // as an offset from the left tile's row
+    constexpr long TROW = (long)M * M * LBM_TILE_W;
+    const long tp = a.tile_pitch;
+    const long halo_off = (kc % M) >= M - HALF ? (long)(g * NV + kc) * LBM_TILE_W + (LBM_TILE_W - 4)
+                                               : 2 * tp + (long)(g * NV + kc) * LBM_TILE_W;
+    // x-upwind neighbour of a lane's cell pair, as base + k * step floats from the own row
+    // slot (velocity k of the warp): the neighbouring cell of the own line, or, for the
+    // strip's edge lane, the halo copied from the neighbouring tile
+    const int pl_base = lane > 0 ? 2 * lane - 1 : NV * LBM_TILE_W + 3, pl_step = lane > 0 ? LBM_TILE_W : 4;
+    const int pr_base = lane < 31 ? 2 * lane + 2 : NV * LBM_TILE_W, pr_step = lane < 31 ? LBM_TILE_W : 4;
+    (void)tp; (void)halo_off; (void)pl_base; (void)pl_step; (void)pr_base; (void)pr_step;
 
     // loader state (uniform within the warp)
     int l_pos = 0, l_item = s_items[0], l_i = 0;
@@ -168,12 +194,23 @@ step_march_kernel(const StepArgs a)
     auto issue = [&]() {
         const int slot = (int)(nl % S);
         const int row = l_row0 - (ypos ? 1 : 0) + l_i;
-        if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * LINE * 4));
-        __syncwarp();
-        fence_proxy_async_smem();   // this slot's earlier generic reads before the async writes
-        if (lane < NV)
-            bulk_copy(slots + slot * Sh::SLOT + lane * LINE,
-                      src_plane + (long)row * nx + 28 + 64L * l_strip, LINE * 4, &bars[slot]);
+        if constexpr (TILED) {
+            if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * (LBM_TILE_W + 4) * 4));
+            __syncwarp();
+            fence_proxy_async_smem();
+            float *dst = slots + slot * Sh::SLOT;
+            const float *left_row = h + (long)l_strip * tp + (long)row * TROW;
+            if (lane < NV) bulk_copy(dst + NV * LBM_TILE_W + 4 * lane, left_row + halo_off, 16, &bars[slot]);
+            if (lane == 0)
+                bulk_copy(dst, left_row + tp + (long)g * NV * LBM_TILE_W, NV * LBM_TILE_W * 4, &bars[slot]);
+        } else {
+            if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * LINE * 4));
+            __syncwarp();
+            fence_proxy_async_smem();   // this slot's earlier generic reads before the async writes
+            if (lane < NV)
+                bulk_copy(slots + slot * Sh::SLOT + lane * LINE,
+                          src_plane + (long)row * nx + 28 + 64L * l_strip, LINE * 4, &bars[slot]);
+        }
         ++nl;
         if (++l_i > l_len) {
             l_i = 0;
@@ -272,11 +309,19 @@ step_march_kernel(const StepArgs a)
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
                     const int k = r * M + ix;
-                    const float *lo = own + k * LINE;
-                    const float2 hc = *reinterpret_cast<const float2 *>(lo + 4 + 2 * lane);
-                    const float2 hx = (ix >= M - HALF) ? make_float2(lo[3 + 2 * lane], hc.x)     // xi_x > 0: x - 1
-                                                       : make_float2(hc.y, lo[6 + 2 * lane]);    // xi_x < 0: x + 1
-                    const float2 hy = *reinterpret_cast<const float2 *>(ynb + k * LINE + 4 + 2 * lane);
+                    float2 hc, hx, hy;
+                    if constexpr (TILED) {
+                        hc = *reinterpret_cast<const float2 *>(own + k * LINE + 2 * lane);
+                        hx = (ix >= M - HALF) ? make_float2(own[pl_base + k * pl_step], hc.x)   // xi_x > 0: x - 1
+                                              : make_float2(hc.y, own[pr_base + k * pr_step]);  // xi_x < 0: x + 1
+                        hy = *reinterpret_cast<const float2 *>(ynb + k * LINE + 2 * lane);
+                    } else {
+                        const float *lo = own + k * LINE;
+                        hc = *reinterpret_cast<const float2 *>(lo + 4 + 2 * lane);
+                        hx = (ix >= M - HALF) ? make_float2(lo[3 + 2 * lane], hc.x)     // xi_x > 0: x - 1
+                                              : make_float2(hc.y, lo[6 + 2 * lane]);    // xi_x < 0: x + 1
+                        hy = *reinterpret_cast<const float2 *>(ynb + k * LINE + 4 + 2 * lane);
+                    }
                     float2 v;
                     if constexpr (DEF) {
                         // h + nu_x (h_x - h) + nu_y (h_y - h): no per-velocity coefficient held
@@ -353,6 +398,8 @@ step_march_kernel(const StepArgs a)
         // ---- relaxation, store, residual ----
         const int y = c_row0 + c_u;
         const long cell = (long)y * nx + 32 + 64L * c_strip + 2 * lane;
+        // tiled: this lane's cell pair in velocity 0 of the strip's tile row
+        const long tcell = (long)(c_strip + 1) * tp + (long)y * TROW + 2 * lane;
         float2 psd2 = make_float2(0.f, 0.f), psn2 = psd2;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
@@ -361,19 +408,20 @@ step_march_kernel(const StepArgs a)
             const float xiy = a.xi_f[iy];
             const float2 q2 = __fmul2_rn(make_float2(wom, wom), __ffma2_rn(make_float2(xiy, xiy), jy2, rho2));
             const float2 jj2 = __fmul2_rn(make_float2(wom, wom), jx2);
-            float *rowp = hn + (long)(iy * M) * ncells + cell;
+            float *rowp = TILED ? hn + tcell + (long)(iy * M) * LBM_TILE_W : hn + (long)(iy * M) * ncells + cell;
+            const long vstride = TILED ? (long)LBM_TILE_W : ncells;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
                 const int k = r * M + ix;
                 const float2 t = __ffma2_rn(xi2[ix], jj2, q2);
                 const float2 v = __ffma2_rn(w2[ix], t, __fmul2_rn(b2, hs[k]));
                 if (RESID) {
-                    const float2 hc = *reinterpret_cast<const float2 *>(own + k * LINE + 4 + 2 * lane);
+                    const float2 hc = *reinterpret_cast<const float2 *>(own + k * LINE + (TILED ? 0 : 4) + 2 * lane);
                     const float2 d = __fadd2_rn(v, make_float2(-hc.x, -hc.y));
                     psd2 = __ffma2_rn(d, d, psd2);
                     psn2 = __ffma2_rn(v, v, psn2);
                 }
-                *reinterpret_cast<float2 *>(rowp + (long)ix * ncells) = v;
+                *reinterpret_cast<float2 *>(rowp + (long)ix * vstride) = v;
             }
         }
         if (RESID) {
@@ -435,23 +483,29 @@ step_march_kernel(const StepArgs a)
     }
 }
 
-template <int M, int G, int S, bool DEFER>
+template <int M, int G, int S, bool DEFER, bool TILED = false>
 cudaError_t prepare_march(int *grid)
 {
-    constexpr int SMEM = MarchShape<M, G, S>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true, DEFER>,
+    constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true, DEFER, TILED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false, DEFER>,
+        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false, DEFER, TILED>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    // the largest shared-memory carveout: otherwise the driver may pick the smallest one that
+    // holds one march block (164 KB for the tiled ring) and leave no room for the wall blocks
+    // that run beside it
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+        e = cudaFuncSetAttribute(r ? step_march_kernel<M, G, S, true, DEFER, TILED> : step_march_kernel<M, G, S, false, DEFER, TILED>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int per_sm = 0, dev = 0, sms = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false, DEFER>,
-                                                          MarchShape<M, G, S>::THREADS, SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false, DEFER, TILED>,
+                                                          MarchShape<M, G, S, TILED>::THREADS, SMEM);
     if (e == cudaSuccess && DEFER) {
         int per_sm_resid = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, step_march_kernel<M, G, S, true, DEFER>,
-                                                          MarchShape<M, G, S>::THREADS, SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, step_march_kernel<M, G, S, true, DEFER, TILED>,
+                                                          MarchShape<M, G, S, TILED>::THREADS, SMEM);
         if (per_sm_resid < per_sm) per_sm = per_sm_resid;
     }
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -465,20 +519,20 @@ cudaError_t prepare_march(int *grid)
 // write disjoint cells of the new one).  Block 0 waits for the march grid before it exits,
 // so that this grid completes only after the march has completed and its writes are
 // visible: work the stream orders after this launch sees the whole step.
-template <int M, int G, bool RESID>
+template <int M, int G, bool RESID, bool TILED = false>
 __global__ void __launch_bounds__(Shape<G>::THREADS) step_wall_beside_march_kernel(const StepArgs a)
 {
-    step_body<float, float, M, G, RESID, false, false, true, false>(a, blockIdx.x);
+    step_body<float, float, M, G, RESID, false, false, true, false, TILED>(a, blockIdx.x);
     if (blockIdx.x == 0) asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
 // March kernel over `grid` persistent blocks, and beside it the wall kernel over the wall
 // segments (programmatic dependent launch).
-template <int M, int G, int S, bool DEFER, bool RESID>
+template <int M, int G, int S, bool DEFER, bool RESID, bool TILED = false>
 cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
 {
-    constexpr int SMEM = MarchShape<M, G, S>::SMEM;
-    step_march_kernel<M, G, S, RESID, DEFER><<<grid, MarchShape<M, G, S>::THREADS, SMEM, s>>>(a);
+    constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;
+    step_march_kernel<M, G, S, RESID, DEFER, TILED><<<grid, MarchShape<M, G, S, TILED>::THREADS, SMEM, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_wall_segs == 0) return e;
     StepArgs b = a;
@@ -494,7 +548,7 @@ cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, step_wall_beside_march_kernel<M, G, RESID>, b);
+    return cudaLaunchKernelEx(&cfg, step_wall_beside_march_kernel<M, G, RESID, TILED>, b);
 }
 
 }  // namespace lbmk

@@ -84,6 +84,8 @@ def _load():
         "lbm_set_moments": (st, [_vp, _dp]),
         "lbm_state_device": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_long)]),
         "lbm_state_layout": (st, [_vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
+        "lbm_state_tiling": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
         "lbm_norms_scratch_bytes": (st, [ctypes.c_long, ctypes.POINTER(ctypes.c_size_t)]),
         "lbm_norms": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp]),
         "lbm_norms_noalloc": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, _vp]),
@@ -307,7 +309,8 @@ def lbm_solve(sim: Sim, tol: float, max_steps: int, refine_sweeps: int = 0, refi
 
 def lbm_set_variant(sim: Sim, warps_per_segment: int, prefetch: int = 0):
     """Step kernel: warps per 32-cell segment and load path (0 registers, 1 prefetch, 2/3 TMA
-    segments, 4 to 7 the column march; the C header lists which combinations exist)."""
+    segments, 4 to 7 the column march, 8 the column march on the strip-tiled state; the C
+    header lists which combinations exist)."""
     _check(_load().lbm_set_variant(sim.handle, int(warps_per_segment), int(prefetch)))
 
 
@@ -398,6 +401,15 @@ def lbm_state_layout(sim: Sim):
     pa, py = ctypes.c_long(), ctypes.c_long()
     _check(_load().lbm_state_layout(sim.handle, ctypes.byref(pa), ctypes.byref(py)))
     return pa.value, py.value
+
+
+def lbm_state_tiling(sim: Sim):
+    """(tile_width, x_shift, tile_pitch, row_pitch) of a strip-tiled device state (load path 8):
+    element (a, x, y) at ((x + x_shift) // tile_width) * tile_pitch + y * row_pitch
+    + a * tile_width + (x + x_shift) % tile_width; all zero for a planar state."""
+    w, sh, tp, rp = ctypes.c_int(), ctypes.c_int(), ctypes.c_long(), ctypes.c_long()
+    _check(_load().lbm_state_tiling(sim.handle, ctypes.byref(w), ctypes.byref(sh), ctypes.byref(tp), ctypes.byref(rp)))
+    return w.value, sh.value, tp.value, rp.value
 
 
 def lbm_norms_scratch_bytes(count: int) -> int:

@@ -200,7 +200,8 @@ def test_set_moments_matches_oracle_and_round_trips(prec, tol, nx, ny):
 @pytest.mark.parametrize("prec,tol,variant", [(lbm.LBM_FP64, FP64_TOL, None),
                                               (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, None),
                                               (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, (6, 4)),
-                                              (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, (6, 7))])
+                                              (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, (6, 7)),
+                                              (lbm.LBM_FP32_PERTURB, FP32_TOL_PER_STEP * 6, (6, 8))])
 def test_strang_splitting_matches_oracle(prec, tol, variant):
     """Symmetric splitting: the library's stored state g = R(dt/2) h after 6 steps equals the
     oracle's literal composition relaxation(dt/2), transport(dt), relaxation(dt/2), and the
@@ -355,13 +356,20 @@ def test_full_size_bench_variants(bench_case, variant):
         lbm.lbm_step(sim, 1)
         ptr, step = lbm.lbm_state_device(sim)
         assert step == 1
-        pa, py = lbm.lbm_state_layout(sim)
+        tw, shift, tp, rp = lbm.lbm_state_tiling(sim)
         off = ptr - buf.data_ptr()
-        nbytes = 4 * p.n * p.ncells
+        cy, cx = idx // 2048, idx % 2048
+        if tw:
+            # strip-tiled state (load path 8)
+            nbytes = 4 * (2048 // tw + 1) * tp
+            xs = cx + shift
+            elems = torch.arange(p.n, device="cuda")[:, None] * tw + ((xs // tw) * tp + cy * rp + xs % tw)[None, :]
+        else:
+            pa, py = lbm.lbm_state_layout(sim)
+            nbytes = 4 * p.n * p.ncells
+            elems = torch.arange(p.n, device="cuda")[:, None] * pa + (cy * py + cx)[None, :]
         torch.cuda.synchronize()
         state = buf[off:off + nbytes].view(torch.float32)
-        cy, cx = idx // 2048, idx % 2048
-        elems = torch.arange(p.n, device="cuda")[:, None] * pa + (cy * py + cx)[None, :]
         got = state[elems].double().cpu().numpy().T
         assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * np.abs(ref).max(), (variant, residual_every)
         if residual_every == 1:
@@ -411,15 +419,15 @@ def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
 
 @pytest.mark.parametrize("n_half,nx,ny,variants", [
     # 2 strips x 5 chunks: fewer items than blocks (most blocks find no work)
-    (6, 192, 45, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (12, 4), (12, 5)]),
+    (6, 192, 45, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (12, 4), (12, 5)]),
     # 5 strips x 65 chunks of 8 rows: more items than blocks, item-to-item pipelining
-    (6, 384, 522, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (12, 5)]),
-    (4, 256, 70, [(2, 0), (2, 5), (4, 0), (4, 5)]),
+    (6, 384, 522, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (12, 5)]),
+    (4, 256, 70, [(2, 0), (2, 5), (4, 0), (4, 5), (4, 8)]),
     # 15 strips x 41+ chunks: items beyond the fixed first three per block come from the counter
-    (6, 1024, 1000, [(6, 0), (6, 4), (6, 6), (6, 7), (12, 5)]),
+    (6, 1024, 1000, [(6, 0), (6, 4), (6, 6), (6, 7), (6, 8), (12, 5)]),
 ])
 def test_fp32_column_march_matches_oracle(n_half, nx, ny, variants):
-    """The column-march interior (load paths 4 to 7) gives the oracle's result to FP32 accuracy
+    """The column-march interior (load paths 4 to 8; 8 on the strip-tiled state) gives the oracle's result to FP32 accuracy
     over several steps, with and without the residual, and agrees with the segment kernels
     to within a few FP32 roundings."""
     p = oracle_problem("half", n_half, CAVITY, nx, ny, 0.07, 0.002, 0.01)
@@ -463,3 +471,57 @@ def test_tma_variant_rejected_where_lines_are_unaligned():
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_set_variant(sim, 2, 2)
     assert e.value.status == lbm.LBM_EUNSUPPORTED
+
+
+def test_strip_tiled_state_layout_changes_and_refinement():
+    """Load path 8 moves the state into the strip-tiled layout and any other path moves it
+    back, bit for bit; host transfers stay planar; the tiling is reported and the planar
+    pitches are refused while tiled; lbm_solve's refinement sweeps (run on the planar layout)
+    give the same state as on the planar column march and leave the state tiled."""
+    n_half, nx, ny = 6, 192, 45
+    p = oracle_problem("half", n_half, CAVITY, nx, ny, 0.07, 0.002, 0.01)
+    h0 = random_state(p.n, p.ncells, seed=43).astype(np.float32).astype(np.float64)
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    prob = lbm.make_problem(CAVITY, nx, ny, 0.07, 0.002, 0.01, prec=lbm.LBM_FP32_PERTURB, residual_every=3)
+    sim = lbm.lbm_init(vs, prob, h0, stream=torch.cuda.Stream())
+    assert lbm.lbm_state_tiling(sim) == (0, 0, 0, 0)
+    lbm.lbm_set_variant(sim, 6, 8)
+    assert lbm.lbm_state_tiling(sim) == (64, 32, ny * p.n * 64, p.n * 64)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_state_layout(sim)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    np.testing.assert_array_equal(lbm.lbm_get_state(sim), h0)
+    h1 = random_state(p.n, p.ncells, seed=44).astype(np.float32).astype(np.float64)
+    lbm.lbm_set_state(sim, h1)
+    np.testing.assert_array_equal(lbm.lbm_get_state(sim), h1)
+    lbm.lbm_set_variant(sim, 6, 4)
+    assert lbm.lbm_state_tiling(sim)[0] == 0
+    np.testing.assert_array_equal(lbm.lbm_get_state(sim), h1)
+    lbm.lbm_set_variant(sim, 6, 8)
+    ref = p.step(h1, 3)
+    lbm.lbm_step(sim, 3)
+    got = lbm.lbm_get_state(sim)
+    assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * 3 * np.abs(ref).max()
+    m = lbm.lbm_moments(sim)
+    mr = p.moments(got)
+    for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy"):
+        np.testing.assert_allclose(m[k], mr[k], rtol=0, atol=1e-12)
+    fy, fx = lbm.lbm_face_flux(sim)
+    np.testing.assert_allclose(fy, p.face_flux_y(got), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(fx, p.face_flux_x(got), rtol=0, atol=1e-12)
+    sim.close()
+    # the same solve on the planar and on the tiled column march
+    out = []
+    for pf in (4, 8):
+        sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.07, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB,
+                                                residual_every=100), stream=torch.cuda.Stream())
+        lbm.lbm_set_variant(sim, 6, pf)
+        info = lbm.lbm_solve(sim, 1e-8, 400_000, 3, 1e-8)
+        assert lbm.lbm_get_variant(sim) == (6, pf) and (lbm.lbm_state_tiling(sim)[0] == 64) == (pf == 8)
+        out.append((info, lbm.lbm_get_state(sim)))
+        sim.close()
+    (i4, s4), (i8, s8) = out
+    # same march steps, and the refinement ends at the same FP32 floor of the defect
+    assert i8["steps"] == i4["steps"] and i8["sweeps"] == i4["sweeps"], (i4, i8)
+    assert abs(i8["defect"] - i4["defect"]) <= 0.1 * i4["defect"] and i8["defect"] < 2e-8, (i4, i8)
+    assert np.abs(s8 - s4).max() <= 1e-5 * np.abs(s4).max()

@@ -157,3 +157,80 @@ def test_chunk_choice_fills_rounds():
     for nx, ny, g in [(2048, 2048, 152), (1024, 1024, 152), (384, 522, 152), (256, 70, 304)]:
         _, c = choose_chunks(nx, ny, g)
         assert (ny - 2) // c >= 8
+
+
+# ---- strip-tiled state (load path 8): tile t holds x in [64 t - 32, 64 t + 32) as [y][a][64]
+
+TILE_W, TILE_SHIFT = 64, 32
+
+
+def tiles_for(nx):
+    return (nx + TILE_SHIFT + TILE_W - 1) // TILE_W
+
+
+def tile_off(x, y, n, tile_pitch):
+    xs = x + TILE_SHIFT
+    return (xs // TILE_W) * tile_pitch + y * n * TILE_W + xs % TILE_W
+
+
+def tiled_cell(off, n, tile_pitch):
+    """(x, y, a) stored at float offset `off` of the tiled state, or None for padding."""
+    t, rem = divmod(off, tile_pitch)
+    y, rem = divmod(rem, n * TILE_W)
+    a, p = divmod(rem, TILE_W)
+    return t * TILE_W - TILE_SHIFT + p, y, a
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 10), (192, 11), (256, 13), (640, 12)])
+@pytest.mark.parametrize("n", [64, 144])
+def test_tiled_offsets_are_a_bijection_onto_the_buffer(nx, ny, n):
+    tp = ny * n * TILE_W
+    size = tiles_for(nx) * tp
+    seen = set()
+    for y in range(ny):
+        for x in range(nx):
+            for a in (0, n // 2, n - 1):
+                off = tile_off(x, y, n, tp) + a * TILE_W
+                assert 0 <= off < size and off not in seen
+                assert tiled_cell(off, n, tp) == (x, y, a)
+                seen.add(off)
+    # the buffer holds every (cell, velocity) once plus one tile column of padding
+    assert size == (nx + TILE_W) * ny * n
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 10), (192, 45), (384, 30), (2048, 12)])
+@pytest.mark.parametrize("m,g", [(12, 6), (8, 4)])
+def test_tiled_march_copies(nx, ny, m, g):
+    """Every row copy of the tiled march (one contiguous copy of the warp's lines, one 16-byte
+    halo copy per velocity) starts 16-byte aligned inside the buffer, the line copy covers
+    exactly the warp's velocities of the strip's cells in that row, and each halo copy holds
+    the upwind x neighbour of the strip's edge cell for that velocity at the position the
+    kernel reads (index 3 of the left halo, index 0 of the right halo)."""
+    n, half = m * m, m // 2
+    rpl = m // g
+    nvw = rpl * m
+    tp = ny * n * TILE_W
+    size = tiles_for(nx) * tp
+    strips = (nx - 64) // 64
+    for s in range(strips):
+        x0 = 32 + 64 * s
+        for row in range(ny):
+            left_row = s * tp + row * n * TILE_W
+            for w in range(g):
+                big = left_row + tp + w * nvw * TILE_W
+                assert big % 4 == 0 and 0 <= big and big + nvw * TILE_W <= size
+                for q in range(nvw * TILE_W):
+                    x, y, a = tiled_cell(big + q, n, tp)
+                    assert (y, a) == (row, w * nvw + q // TILE_W) and x == x0 + q % TILE_W
+                for k in range(nvw):
+                    ix = k % m
+                    a = w * nvw + k
+                    if ix >= m - half:
+                        halo = left_row + a * TILE_W + (TILE_W - 4)
+                        want, idx = x0 - 1, 3
+                    else:
+                        halo = left_row + 2 * tp + a * TILE_W
+                        want, idx = x0 + 64, 0
+                    assert halo % 4 == 0 and 0 <= halo and halo + 4 <= size
+                    x, y, aa = tiled_cell(halo + idx, n, tp)
+                    assert (x, y, aa) == (want, row, a) and 0 <= x < nx
