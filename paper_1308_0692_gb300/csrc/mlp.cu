@@ -1,9 +1,10 @@
 // Learned warm start: a coordinate MLP 4 -> 256 -> 256 -> 256 -> 6 (exact-erf GELU) that
 // maps (x, y, log Kn, u_w) to the six normalised moments of the steady state, trained
-// and evaluated with this file's kernels: a BF16 tensor-core GEMM with FP32 accumulation
-// (mma.sync m16n8k16, operands staged in shared memory by cp.async and read with
-// ldmatrix), elementwise GELU / GELU' / loss kernels, bias-gradient reductions and Adam
-// on FP32 master weights.  The warm-start kernel then builds the initial distribution
+// and evaluated with this file's kernels: BF16 GEMMs on the fifth-generation tensor cores
+// with FP32 accumulation in tensor memory (umma_gemm.cu: TMA tensor copies, tcgen05.mma,
+// tcgen05.ld; split-K with a fixed-order sum for the weight gradients, whose K is the
+// batch), elementwise GELU / GELU' / loss kernels, bias-gradient reductions and Adam on
+// FP32 master weights.  The warm-start kernel then builds the initial distribution
 // from the predicted moments by the second-order Hermite expansion
 //   h_a = w_a [rho' + xi_a . j' + 1/2 sum_ij (P'_ij - rho' delta_ij)(xi_i xi_j - delta_ij)].
 // The paper has no learned component; this follows the warm-start configuration of
@@ -22,143 +23,17 @@
 
 lbm_status lbm_norms_fail(lbm_status s, const char *msg);
 
+// tensor-core GEMM (umma_gemm.cu)
+cudaError_t umma_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc,
+                         const float *bias, int M, int N, int K, int splits, float *partials, int *status,
+                         cudaStream_t s);
+
 namespace {
 
 constexpr int NL = 4;                          // layers
 constexpr int WIDTH[NL + 1] = {4, 256, 256, 256, 6};
 constexpr int PADW[NL + 1] = {8, 256, 256, 256, 8};   // row lengths padded to 16 bytes
-
-// ------------------------------------------------------------------ GEMM (NT)
-// C[M][N] (fp32, ldc) = A[M][K] (bf16, lda) * B[N][K]^T (bf16, ldb) (+ bias[N]).
-// K must be a multiple of 8 and lda, ldb multiples of 8 (16-byte rows).
-constexpr int BM = 128, BN = 128, BK = 32, SROW = BK + 8;   // padded smem row (80 bytes)
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred)
-{
-    const int n = pred ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(n));
-}
-
-__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__global__ void __launch_bounds__(256) gemm_nt_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
-                                                     const __nv_bfloat16 *__restrict__ B, int ldb,
-                                                     float *__restrict__ C, int ldc, const float *__restrict__ bias,
-                                                     int M, int N, int K)
-{
-    __shared__ __align__(16) __nv_bfloat16 sA[2][BM][SROW];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][BN][SROW];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;     // warp tile: rows wm*64.., cols wn*32..
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-
-    auto load_stage = [&](int st, int k0) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int chunk = tid + i * 256;          // 512 chunks of 16 bytes per operand
-            const int r = chunk >> 2, cc = (chunk & 3) * 8;
-            const int gm = m0 + r, gk = k0 + cc;
-            const bool pa = gm < M && gk < K;
-            cp_async16(&sA[st][r][cc], pa ? (const void *)(A + (long)gm * lda + gk) : (const void *)A, pa);
-            const int gn = n0 + r;
-            const bool pb = gn < N && gk < K;
-            cp_async16(&sB[st][r][cc], pb ? (const void *)(B + (long)gn * ldb + gk) : (const void *)B, pb);
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-    };
-
-    const int ktiles = (K + BK - 1) / BK;
-    load_stage(0, 0);
-    for (int kt = 0; kt < ktiles; ++kt) {
-        const int st = kt & 1;
-        if (kt + 1 < ktiles) {
-            load_stage(st ^ 1, (kt + 1) * BK);
-            asm volatile("cp.async.wait_group 1;\n" ::);
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            unsigned af[4][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int row = wm * 64 + i * 16 + (lane & 15);
-                const int col = kk + (lane >> 4) * 8;
-                ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3], &sA[st][row][col]);
-            }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int nrow = wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3);
-                const int col = kk + ((lane >> 3) & 1) * 8;
-                unsigned r0, r1, r2, r3;
-                ldsm_x4(r0, r1, r2, r3, &sB[st][nrow][col]);
-                bfr[2 * j][0] = r0;
-                bfr[2 * j][1] = r1;
-                bfr[2 * j + 1][0] = r2;
-                bfr[2 * j + 1][1] = r3;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
-        }
-        __syncthreads();
-    }
-    // epilogue: thread holds (row lane/4, cols 2*(lane%4)+{0,1}) and row + 8 of each tile
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = n0 + wn * 32 + j * 8 + (lane & 3) * 2;
-#pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
-                const int row = m0 + wm * 64 + i * 16 + (lane >> 2) + hf * 8;
-                if (row >= M) continue;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    if (col + e >= N) continue;
-                    float v = acc[i][j][hf * 2 + e];
-                    if (bias) v += bias[col + e];
-                    C[(long)row * ldc + col + e] = v;
-                }
-            }
-        }
-    }
-}
-
-cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc,
-                    const float *bias, int M, int N, int K, cudaStream_t s)
-{
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_nt_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, bias, M, N, K);
-    return cudaGetLastError();
-}
+constexpr int SPLITK_MAX = 16;                        // K-splits of a weight-gradient GEMM
 
 // ------------------------------------------------------------------ elementwise kernels
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -341,6 +216,8 @@ struct lbm_mlp {
     __nv_bfloat16 *aT;        // transposed a [256][M]
     double *loss_part;
     double *host_loss;
+    float *splitk;            // split-K partial tiles of the weight-gradient GEMMs
+    int *status;              // set by a tensor-core GEMM whose bounded wait gave up
     long step;
 };
 
@@ -378,13 +255,27 @@ size_t mlp_layout(lbm_mlp *p, char *base, int M)
     __nv_bfloat16 *gT = (__nv_bfloat16 *)take(2 * (size_t)256 * (M + 8));
     __nv_bfloat16 *aT = (__nv_bfloat16 *)take(2 * (size_t)256 * (M + 8));
     double *lp = (double *)take(8 * 1216);
+    float *sk = (float *)take(4 * (size_t)SPLITK_MAX * 256 * 256);
+    int *stw = (int *)take(16);
     if (p) {
         p->x32 = x32; p->g32 = g32; p->g16 = g16; p->da = da; p->gT = gT; p->aT = aT; p->loss_part = lp;
+        p->splitk = sk; p->status = stw;
     }
     return off;
 }
 
 int blocks_for(long n) { long b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b)); }
+
+// C[M][N] = A[M][K] B[N][K]^T (+ bias) on the tensor cores; K-splits for long K (the batch)
+cudaError_t gemm(lbm_mlp *p, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc,
+                 const float *bias, int M, int N, int K)
+{
+    const int ktiles = (K + 63) / 64;
+    int splits = ktiles / 4;
+    if (splits > SPLITK_MAX) splits = SPLITK_MAX;
+    if (splits < 2 || (long)M * N > 256L * 256) splits = 1;
+    return umma_gemm_nt(A, lda, B, ldb, C, ldc, bias, M, N, K, splits, p->splitk, p->status, p->stream);
+}
 
 cudaError_t refresh_bf16(lbm_mlp *p, int l)
 {
@@ -407,7 +298,7 @@ cudaError_t forward(lbm_mlp *p, int M)
     to_bf16_kernel<<<blocks_for((long)M * PADW[0]), 256, 0, s>>>(p->x32, 4, p->a[0], PADW[0], M, 4);
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < NL && e == cudaSuccess; ++l) {
-        e = gemm_nt(p->a[l], PADW[l], p->Wq[l], PADW[l], p->z[l], WIDTH[l + 1], p->b[l], M, WIDTH[l + 1], PADW[l], s);
+        e = gemm(p, p->a[l], PADW[l], p->Wq[l], PADW[l], p->z[l], WIDTH[l + 1], p->b[l], M, WIDTH[l + 1], PADW[l]);
         if (e == cudaSuccess && l + 1 < NL) {
             gelu_fwd_kernel<<<blocks_for((long)M * PADW[l + 1]), 256, 0, s>>>(p->z[l], p->a[l + 1], PADW[l + 1], M,
                                                                             WIDTH[l + 1]);
@@ -435,14 +326,14 @@ cudaError_t backward(lbm_mlp *p, const float *t, int M, int *nparts)
         dim3 tg2((PADW[l] + 31) / 32, (M + 31) / 32);
         transpose_bf16_kernel<<<tg2, dim3(32, 8), 0, s>>>(p->a[l], PADW[l], p->aT, Mp, M, PADW[l], WIDTH[l]);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = gemm_nt(p->gT, Mp, p->aT, Mp, p->gW[l], WIDTH[l], nullptr, WIDTH[l + 1], WIDTH[l], Mp, s);
+        if (e == cudaSuccess) e = gemm(p, p->gT, Mp, p->aT, Mp, p->gW[l], WIDTH[l], nullptr, WIDTH[l + 1], WIDTH[l], Mp);
         if (e == cudaSuccess) {
             colsum_kernel<<<WIDTH[l + 1], 256, 0, s>>>(p->g32, M, ng, p->gb[l]);
             e = cudaGetLastError();
         }
         if (l == 0 || e != cudaSuccess) break;
         // da [M][K] = g W : A = g [M][N] (bf16 ld ldg), B = W^T [K][N] (WqT, ld PADW[l+1])
-        e = gemm_nt(p->g16, ldg, p->WqT[l], PADW[l + 1], p->da, WIDTH[l], nullptr, M, WIDTH[l], ldg, s);
+        e = gemm(p, p->g16, ldg, p->WqT[l], PADW[l + 1], p->da, WIDTH[l], nullptr, M, WIDTH[l], ldg);
         if (e == cudaSuccess) {
             const long n = (long)M * WIDTH[l];
             gelu_bwd_kernel<<<blocks_for(n), 256, 0, s>>>(p->da, p->z[l - 1], p->g16, p->g32, n);
@@ -581,9 +472,12 @@ static lbm_status grads_and_loss(lbm_mlp *p, const float *x_dev, const float *t_
     if (e == cudaSuccess) e = backward(p, t_dev, M, &np);
     if (e != cudaSuccess) return mfail(LBM_ECUDA, cudaGetErrorString(e));
     if (loss) {
+        int stw = 0;
         e = cudaMemcpyAsync(p->host_loss, p->loss_part, 8L * np, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&stw, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
         if (e != cudaSuccess) return mfail(LBM_ECUDA, cudaGetErrorString(e));
+        if (stw != 0) return mfail(LBM_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
         double s = 0.0;
         for (int i = 0; i < np; ++i) s += p->host_loss[i];
         *loss = s / ((double)M * WIDTH[NL]);

@@ -23,13 +23,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("rows", [1, 100, 1000])
+@pytest.mark.parametrize("rows", [1, 100, 1000, 4200])
 def test_forward_and_gradients_match_oracle(rows):
+    """Rows 1 to 4200: one partial 128-row tile up to 33 tiles with a ragged last one; the
+    weight gradients (K = rows) take 1, 4 and 16 K-splits (some splits past the end of K)."""
     rng = np.random.default_rng(rows)
     params = omlp.init_params(seed=7)
     x = rng.uniform(-1, 1, (rows, 4)).astype(np.float32)
     t = rng.standard_normal((rows, 6)).astype(np.float32)
-    m = lbm.lbm_mlp_create(4096, seed=1)
+    m = lbm.lbm_mlp_create(4200, seed=1)
     lbm.lbm_mlp_set_params(m, lbm.mlp_flatten(params))
     qparams = lbm.mlp_unflatten(lbm.lbm_mlp_get_params(m))       # the fp32 master weights
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
