@@ -33,7 +33,7 @@ namespace {
 constexpr int NL = 4;                          // layers
 constexpr int WIDTH[NL + 1] = {4, 256, 256, 256, 6};
 constexpr int PADW[NL + 1] = {8, 256, 256, 256, 8};   // row lengths padded to 16 bytes
-constexpr int SPLITK_MAX = 16;                        // K-splits of a weight-gradient GEMM
+constexpr int SPLITK_MAX = 32;                        // K-splits of a weight-gradient GEMM
 
 // ------------------------------------------------------------------ elementwise kernels
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -119,20 +119,35 @@ __global__ void transpose_bf16_kernel(const __nv_bfloat16 *src, int lds, __nv_bf
     }
 }
 
-// db[c] = sum_r g[r][c] (fp32, fixed order per column)
-__global__ void colsum_kernel(const float *g, int rows, int cols, float *db)
+// db[c] = sum_r g[r][c] (fp32, fixed order): block (x, y) sums rows [y*chunk, (y+1)*chunk)
+// of columns [32x, 32x+32), lane = column (coalesced reads), warps over rows; the second
+// kernel adds the row chunks in order.  At most CS_CHUNKS chunks (of at least 256 rows).
+constexpr int CS_CHUNKS = 2048;
+__global__ void __launch_bounds__(256) colsum_part_kernel(const float *g, int rows, int cols, int chunk, float *part)
 {
-    __shared__ float s[256];
-    const int c = blockIdx.x;
+    __shared__ float s[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
     float acc = 0.f;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) acc += g[(long)r * cols + c];
-    s[threadIdx.x] = acc;
+    if (c < cols)
+        for (int r = r0 + w; r < r1; r += 8) acc += g[(long)r * cols + c];
+    s[w][lane] = acc;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
+    if (w == 0 && c < cols) {
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += s[q][lane];
+        part[(long)blockIdx.y * cols + c] = t;
     }
-    if (threadIdx.x == 0) db[c] = s[0];
+}
+
+__global__ void colsum_final_kernel(const float *part, int chunks, int cols, float *db)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float t = 0.f;
+    for (int k = 0; k < chunks; ++k) t += part[(long)k * cols + c];
+    db[c] = t;
 }
 
 // Adam on FP32 master weights; refreshes the bf16 copy (ld = ldq, row length k)
@@ -255,7 +270,10 @@ size_t mlp_layout(lbm_mlp *p, char *base, int M)
     __nv_bfloat16 *gT = (__nv_bfloat16 *)take(2 * (size_t)256 * (M + 8));
     __nv_bfloat16 *aT = (__nv_bfloat16 *)take(2 * (size_t)256 * (M + 8));
     double *lp = (double *)take(8 * 1216);
+    // split-K partial tiles (<= SPLITK_MAX x 256 x 256), also the column sums' chunk partials
+    // (<= CS_CHUNKS x 256)
     float *sk = (float *)take(4 * (size_t)SPLITK_MAX * 256 * 256);
+    static_assert(CS_CHUNKS * 256 <= SPLITK_MAX * 256 * 256, "workspace too small for the column sums");
     int *stw = (int *)take(16);
     if (p) {
         p->x32 = x32; p->g32 = g32; p->g16 = g16; p->da = da; p->gT = gT; p->aT = aT; p->loss_part = lp;
@@ -328,7 +346,12 @@ cudaError_t backward(lbm_mlp *p, const float *t, int M, int *nparts)
         e = cudaGetLastError();
         if (e == cudaSuccess) e = gemm(p, p->gT, Mp, p->aT, Mp, p->gW[l], WIDTH[l], nullptr, WIDTH[l + 1], WIDTH[l], Mp);
         if (e == cudaSuccess) {
-            colsum_kernel<<<WIDTH[l + 1], 256, 0, s>>>(p->g32, M, ng, p->gb[l]);
+            // the split-K workspace is free again once the weight-gradient GEMM is done
+            int chunk = (M + CS_CHUNKS - 1) / CS_CHUNKS;
+            if (chunk < 256) chunk = 256;
+            const int chunks = (M + chunk - 1) / chunk;       // <= CS_CHUNKS: fits the workspace
+            colsum_part_kernel<<<dim3((ng + 31) / 32, chunks), 256, 0, s>>>(p->g32, M, ng, chunk, p->splitk);
+            colsum_final_kernel<<<(ng + 255) / 256, 256, 0, s>>>(p->splitk, chunks, ng, p->gb[l]);
             e = cudaGetLastError();
         }
         if (l == 0 || e != cudaSuccess) break;

@@ -2,8 +2,8 @@
 // (+ bias[N]), both operands K-major BF16 in global memory -- the products of the warm-start
 // network (forward z = a W^T, input gradient da = g W, weight gradient dW = g^T a).
 //
-// One CTA of four warps computes a 128 x BN tile of C (BN = 256, or 16 for the narrow
-// products with N <= 16):
+// One CTA of four warps computes a 128 x BN tile of C (BN = 256 or 128 -- 128 when 256-wide
+// tiles would leave most SMs idle -- or 16 for the narrow products with N <= 16):
 //   * warp 0, one lane: the producer.  Per 64-wide K step it has the Tensor Memory
 //     Accelerator copy the A tile [128][64] and the B tile [BN][64] into a ring of STAGES
 //     shared-memory stages (cp.async.bulk.tensor.2d, 128-byte swizzle, completion counted in
@@ -13,8 +13,10 @@
 //     (M = 128, N = BN, K = 16 each) accumulate into a 128 x BN FP32 accumulator in tensor
 //     memory (TMEM); tcgen05.commit then frees the stage ("empty" mbarrier) once those MMAs
 //     have read it, and after the last stage signals the accumulator;
-//   * all four warps: the epilogue.  Warp w reads TMEM lanes 32w..32w+31 (rows of the tile)
-//     with tcgen05.ld, adds the bias and stores the FP32 rows.
+//   * all four warps: the epilogue.  Warp w reads TMEM lanes 32w..32w+31 (rows of the tile),
+//     32 columns at a time, with tcgen05.ld, passes them through shared memory (the pipeline
+//     stages are free by then) so that each store instruction writes 32 consecutive columns
+//     of one row, and adds the bias.
 // Split-K (gridDim.z > 1): CTA z takes K steps [z*kper, (z+1)*kper) and writes its partial
 // tile to C + z * M * ldc; a second kernel sums the partials in a fixed order (deterministic).
 //
@@ -191,35 +193,41 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
         mma_commit(&accf);
     }
     __syncwarp();
+    __syncthreads();     // the producer's copies have all landed: the stages can take the staging
 
     // ---- epilogue: all four warps ----
     const bool ok = bar_wait(&accf, 0);
     if (!ok && lane == 0) atomicExch(status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
     const bool any = kt1 > kt0;
+    float *stg = reinterpret_cast<float *>(smem) + warp * 32 * 33;    // [32 rows][33], padded
     if (ok) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15])
+                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (row < M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col < N) {
-                        float v = any ? __uint_as_float(r[j]) : 0.f;
-                        if (bias) v += bias[col];
-                        Cz[(size_t)row * ldc + col] = v;
-                    }
+            for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = any ? __uint_as_float(r[j]) : 0.f;
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+            const float bv = (bias && col < N) ? bias[col] : 0.f;
+            if (col < N) {
+#pragma unroll 4
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = m0 + warp * 32 + rr;
+                    if (row < M) Cz[(size_t)row * ldc + col] = stg[rr * 33 + lane] + bv;
                 }
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -300,18 +308,22 @@ cudaError_t umma_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B
 {
     if (M < 1 || N < 1 || K < 1 || N > 256 || lda % 8 || ldb % 8 || K > lda || K > ldb) return cudaErrorInvalidValue;
     if ((((uintptr_t)A) & 15) || (((uintptr_t)B) & 15)) return cudaErrorInvalidValue;
-    const int bn = N <= 16 ? 16 : 256;
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, A, M, K, lda, UM) || !make_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
     const int ktiles = (K + UK - 1) / UK;
     if (splits < 1) splits = 1;
     if (splits > ktiles) splits = ktiles;
     const bool split = splits > 1 && partials;
+    // 256-wide tiles unless they would leave most SMs idle
+    int bn = N <= 16 ? 16 : 256;
+    if (bn == 256 && (long)((M + UM - 1) / UM) * ((N + 255) / 256) * (split ? splits : 1) < 152) bn = 128;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, M, K, lda, UM) || !make_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
     float *out = split ? partials : C;
     const int ldo = split ? N : ldc;
     const float *b = split ? nullptr : bias;
-    cudaError_t e = bn == 16 ? launch_bn<16>(ta, tb, out, ldo, b, M, N, ktiles, split ? splits : 1, status, s)
-                             : launch_bn<256>(ta, tb, out, ldo, b, M, N, ktiles, split ? splits : 1, status, s);
+    const int z = split ? splits : 1;
+    cudaError_t e = bn == 16    ? launch_bn<16>(ta, tb, out, ldo, b, M, N, ktiles, z, status, s)
+                    : bn == 128 ? launch_bn<128>(ta, tb, out, ldo, b, M, N, ktiles, z, status, s)
+                                : launch_bn<256>(ta, tb, out, ldo, b, M, N, ktiles, z, status, s);
     if (e != cudaSuccess || !split) return e;
     const long n = (long)M * N;
     const int nb = (int)std::min<long>(1216, (n + 255) / 256);
