@@ -427,9 +427,21 @@ def run_fp64_same_workload(vs, dist):
     sec = t0.elapsed_time(t1) / 1e3
     units = w["nx"] * w["ny"] * (2 * w["n_half"]) ** 2 * K
     sim.close()
+    # the FP64 pipe's measured rate (a throughput kernel of this library) and the FP64 pipe
+    # instructions the step executes per update (ncu, sm__inst_executed_pipe_fp64 x 32 lanes /
+    # updates, FP64 step kernel at 1024^2 x 144)
+    fma_rate = lbm.lbm_probe_fp64_rate(200_000, stream)
+    ops = FP64_PIPE_OPS_PER_UPDATE
     return {"value": units / sec, "unit": UNIT, "steps": K, "ms_per_step": sec / K * 1e3,
             "achieved_hbm_gbs": 16 * units / sec / 1e9,
+            "fp64_pipe": {"bound": "alu", "measured_fp64_ops_per_s": fma_rate, "ops_per_update": ops,
+                          "achieved_fp64_ops_per_s": units / sec * ops, "frac": units / sec * ops / fma_rate},
             "note": "FP64 storage+arithmetic; bounded by the FP64 pipe of GB300, not HBM"}
+
+
+# FP64 pipe instructions (lane operations) per node-velocity update of the FP64 step, from the
+# ncu count of sm__inst_executed_pipe_fp64 on the 1024^2 x 144 FP64 step (profiles/)
+FP64_PIPE_OPS_PER_UPDATE = 10.1
 
 
 # refinement design behind the time-to-residual headline: "per_instance" (one simulation per
@@ -741,6 +753,8 @@ def main(argv=None):
     ap.add_argument("--variant", default=None, help="force the step kernel variant 'warps,loadpath'")
     ap.add_argument("--nx", type=int, default=None,
                     help="side of the cavity (default 2048); smaller sides are for profiling only")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="time only the plain FP64 march of the workload (profiling of the FP64 step)")
     args = ap.parse_args(argv)
     if args.nx:
         WORKLOAD["nx"] = WORKLOAD["ny"] = args.nx
@@ -754,6 +768,15 @@ def main(argv=None):
         dist.close()
         return 0
     dist = Dist()
+    if args.fp64_only:
+        import torch
+
+        from paper_1308_0692_gb300 import lbm
+        torch.cuda.set_device(dist.local_rank)
+        vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, WORKLOAD["n_half"])
+        print(json.dumps({"fp64": run_fp64_same_workload(vs, dist), "nx": WORKLOAD["nx"]}), flush=True)
+        dist.close()
+        return 0
     out = run_own(args, dist)
     if dist.rank == 0:
         if dist.world == 1 and not args.no_cpu_baseline:

@@ -284,6 +284,12 @@ lbm_status lbm_norms(const void *a, const void *b, long count, int prec, void *s
 lbm_status lbm_norms_noalloc(const void *a, const void *b, long count, int prec, double *out,
                              void *stream);
 
+/* FP64 fused multiply-adds per second this GPU sustains (8 SMs' worth of blocks per SM, eight
+ * independent FMA chains of `iters` steps per thread, timed with CUDA events on `stream`;
+ * synchronises).  Not in the paper: the measured ceiling of the FP64 march, which is bound by
+ * the FP64 pipe rather than by memory on this GPU.  LBM_EINVAL for iters < 1. */
+lbm_status lbm_probe_fp64_rate(long iters, double *fma_per_s, void *stream);
+
 /* ---- Batched sweeps: many independent instances in one persistent launch ----
  * A batch holds independent problems (Couette channels and cavities of any size, Kn and
  * wall speeds; one shared velocity set, precision and residual_every) packed in one

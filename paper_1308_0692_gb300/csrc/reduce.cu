@@ -593,3 +593,56 @@ cudaError_t launch_face_flux(int prec, const void *h, long pa, long py, const do
             (const float *)h, pa, py, tab64, hdr, m, nx, ny, u_ref, flux_x);
     return cudaGetLastError();
 }
+
+lbm_status lbm_norms_fail(lbm_status s, const char *msg);   // error message (lbm_api.cu)
+
+// ---------------------------------------------------------------------------------------
+// FP64 throughput probe: eight independent FMA chains per thread on enough warps to keep
+// every SM's FP64 pipe busy; the result is stored only if it equals a value it never takes,
+// so the chains cannot be removed.  Measures the ceiling of the FP64 march on this GPU.
+__device__ double g_fp64_probe_sink;
+
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(long iters, double mul, double add)
+{
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1e-3 * threadIdx.x + k;
+    for (long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], mul, add);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -1.2345e300) g_fp64_probe_sink = s;
+}
+
+extern "C" lbm_status lbm_probe_fp64_rate(long iters, double *fma_per_s, void *stream)
+{
+    if (!fma_per_s || iters < 1) return lbm_norms_fail(LBM_EINVAL, "lbm_probe_fp64_rate: invalid argument");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int grid = 8 * sms, block = 256;
+    float ms = 0.f;
+    if (e == cudaSuccess) {
+        fp64_fma_probe_kernel<<<grid, block, 0, s>>>(iters / 8 + 1, 0.9999999999999, 1e-13);   // warm-up
+        e = cudaEventRecord(t0, s);
+    }
+    if (e == cudaSuccess) {
+        fp64_fma_probe_kernel<<<grid, block, 0, s>>>(iters, 0.9999999999999, 1e-13);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e != cudaSuccess) return lbm_norms_fail(LBM_ECUDA, cudaGetErrorString(e));
+    *fma_per_s = 8.0 * (double)iters * grid * block / (ms * 1e-3);
+    return LBM_OK;
+}

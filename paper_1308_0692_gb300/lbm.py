@@ -89,6 +89,7 @@ def _load():
         "lbm_norms_scratch_bytes": (st, [ctypes.c_long, ctypes.POINTER(ctypes.c_size_t)]),
         "lbm_norms": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp]),
         "lbm_norms_noalloc": (st, [_vp, _vp, ctypes.c_long, ctypes.c_int, _vp, _vp]),
+        "lbm_probe_fp64_rate": (st, [ctypes.c_long, _dp, _vp]),
         "lbm_batch_bytes": (st, [_vp, ctypes.POINTER(lbm_problem), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
         "lbm_batch_init": (st, [_vp, ctypes.POINTER(lbm_problem), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
                                 ctypes.POINTER(_vp)]),
@@ -422,6 +423,13 @@ def lbm_norms(a_ptr: int, b_ptr: int | None, count: int, prec: int, scratch_ptr:
               scratch_bytes: int, out_ptr: int, stream=None):
     _check(_load().lbm_norms(a_ptr, b_ptr, int(count), prec, scratch_ptr, scratch_bytes, out_ptr,
                              _stream_handle(stream)))
+
+
+def lbm_probe_fp64_rate(iters: int = 200_000, stream=None) -> float:
+    """FP64 fused multiply-adds per second of this GPU (a timed throughput kernel)."""
+    r = ctypes.c_double()
+    _check(_load().lbm_probe_fp64_rate(int(iters), ctypes.byref(r), _stream_handle(stream)))
+    return r.value
 
 
 def lbm_norms_noalloc(a_ptr: int, b_ptr: int | None, count: int, prec: int, out_ptr: int, stream=None):

@@ -260,3 +260,51 @@ def test_batch_freezes_instances_at_the_fp32_floor():
     # converged means below the tolerance; a stalled instance stopped at or above it
     assert all((s["residual"] < tol) == s["converged"] for s in stats), stats
     assert max(s["steps"] for s in stats) < done
+
+
+def test_compensated_fp32_wall_sums_at_the_worst_case():
+    """The batched column march forms the wall densities of Eq. 9 in compensated FP32 (TwoSum),
+    the FP64 march in FP64.  At the hardest case for those sums -- a 256^2 cavity at Kn = 0.01,
+    the longest walls and the slowest modes, next to a 512-cell Kn = 0.01 channel -- the batch
+    marched to 5e-8 and refined to a defect of 1e-10 agrees with the FP64 march (to 1e-11) on
+    the lid shear (every lid face and their mean, the drag), the density of the wall rows, the
+    side-wall shear and the velocity field, all to 1e-5 relative."""
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
+    insts = [(CAVITY, 256, 256, 0.01, 0.0, 0.01), (COUETTE, 1, 512, 0.01, 0.01, -0.01)]
+    probs = [lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP32_PERTURB, residual_every=100)
+             for g, nx, ny, kn, ub, ut in insts]
+    b = lbm.lbm_batch_init(vs, probs, stream=torch.cuda.Stream())
+    lbm.lbm_batch_set_march(b, True)
+    for _ in range(2000):
+        lbm.lbm_batch_advance(b, 1000, 5e-8)
+        if lbm.lbm_batch_poll(b)[0] == 0:
+            break
+    info = lbm.lbm_batch_refine(b, 1e-10, 3, 1e-10, 4_000_000)
+    for i, (g, nx, ny, kn, ub, ut) in enumerate(insts):
+        uw = max(abs(ub), abs(ut))
+        p = oracle_problem("half", 4, g, nx, ny, kn, ub, ut)
+        h32 = lbm.lbm_batch_get_state(b, i)
+        sim = lbm.lbm_init(vs, lbm.make_problem(g, nx, ny, kn, ub, ut, prec=lbm.LBM_FP64, residual_every=100),
+                           stream=torch.cuda.Stream())
+        ref = lbm.lbm_solve(sim, 1e-11, 4_000_000, 0)
+        assert ref["residual"] < 1e-11
+        h64 = lbm.lbm_get_state(sim)
+        sim.close()
+        m32, m64 = p.moments(h32), p.moments(h64)
+        du = max(np.abs(m32["ux"] - m64["ux"]).max(), np.abs(m32["uy"] - m64["uy"]).max()) / uw
+        assert du < 1e-5, (i, du, info[i])
+        # wall rows: density perturbation rho - 1 relative to its largest value there (or to u_w
+        # where it vanishes: the antisymmetric channel has rho = 1 exactly)
+        for row in (0, ny - 1):
+            scale = max(np.abs(m64["rho"][row] - 1.0).max(), uw)
+            assert np.abs(m32["rho"][row] - m64["rho"][row]).max() <= 1e-5 * scale, (i, row)
+        fy32, fy64 = p.face_flux_y(h32), p.face_flux_y(h64)
+        for j in (0, ny):                               # bottom wall and lid
+            scale = np.abs(fy64[j]).max()
+            assert np.abs(fy32[j] - fy64[j]).max() <= 1e-5 * scale, (i, j)
+            assert abs(fy32[j].mean() - fy64[j].mean()) <= 1e-5 * abs(fy64[j].mean()), (i, j)
+        if g == CAVITY:
+            fx32, fx64 = p.face_flux_x(h32), p.face_flux_x(h64)
+            for j in (0, nx):                           # side walls
+                assert np.abs(fx32[:, j] - fx64[:, j]).max() <= 1e-5 * np.abs(fx64[:, j]).max(), (i, j)
+    b.close()
