@@ -213,11 +213,12 @@ def _traffic_record(kernel_key: str):
     return rec.get("dram_bytes_per_launch")
 
 
-VARIANTS = [(4, 0), (6, 0), (6, 2), (6, 3), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (12, 4), (12, 5)]
+VARIANTS = [(4, 0), (6, 0), (6, 2), (6, 3), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (6, 9), (12, 4), (12, 5)]
 LOAD_PATHS = ["registers", "prefetch", "tma", "tma+walls merged", "column march (4 row slots)",
               "column march (5 row slots)", "column march (2 row slots, 2 blocks per SM)",
               "column march (4 row slots, relaxation deferred by one row)",
-              "column march on the strip-tiled state (4 row slots)"]
+              "column march on the strip-tiled state (4 row slots)",
+              "column march on the strip-tiled state (4 row slots, bulk asynchronous stores)"]
 
 
 def choose_variant(sim, stream, args):

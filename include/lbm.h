@@ -187,8 +187,9 @@ lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
  * phases instead of a block barrier (steps without the residual); FP32 cavities with nx a
  * multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12 warps (6 only for paths 6 and
  * 7), M = 8 with 2 or 4 warps (path 5)),
- * 8 the column march of path 4 on a strip-tiled state (M = 12 with 6 warps, M = 8 with 4):
- * choosing path 8 moves the current state into that layout (lbm_state_tiling), where one
+ * 8 the column march of path 4 on a strip-tiled state, 9 the same with the stores too as
+ * bulk asynchronous copies from shared memory (M = 12 with 6 warps, M = 8 with 4): choosing
+ * path 8 or 9 moves the current state into that layout (lbm_state_tiling), where one
  * row of a 64-cell strip, all velocities, is one contiguous stretch of memory, so that a
  * warp copies its lines of a row with one bulk copy; any other path moves it back to the
  * planar layout.  Host transfers (lbm_get_state, lbm_set_state, lbm_set_moments,
@@ -237,10 +238,10 @@ lbm_status lbm_set_moments(lbm_sim *sim, const double *moments);
  * planar layout [a][y][x] the value of velocity a at cell (x, y) is at element
  * a * plane_pitch + y * row_pitch + x (lbm_state_layout: plane_pitch = nx ny, row_pitch =
  * nx); lbm_state_layout returns LBM_EUNSUPPORTED while the state is strip-tiled (load path
- * 8).  Host arrays of the ABI (lbm_init, lbm_get_state, lbm_set_state) are planar. */
+ * 8 or 9).  Host arrays of the ABI (lbm_init, lbm_get_state, lbm_set_state) are planar. */
 lbm_status lbm_state_device(lbm_sim *sim, void **ptr, long *step);
 lbm_status lbm_state_layout(const lbm_sim *sim, long *plane_pitch, long *row_pitch);
-/* The strip-tiled layout of load path 8 (all outputs 0 while the state is planar): tiles of
+/* The strip-tiled layout of load paths 8 and 9 (all outputs 0 while the state is planar): tiles of
  * tile_width = 64 cells in x, tile t holding x in [64 t - x_shift, 64 t - x_shift + 64)
  * with x_shift = 32 (so that the column march's 64-cell strips are whole tiles), the value
  * of velocity a at cell (x, y) at element

@@ -25,11 +25,11 @@ cudaError_t launch_defect_f32(int m, const StepArgs &a, int grid, cudaStream_t s
 cudaError_t launch_step_f32_tma(int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s,
                                bool merged);
 cudaError_t prepare_step_f32_tma(int m, int g);
-cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, bool tiled, bool resid, const StepArgs &a, int grid,
+cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, int tiled, bool resid, const StepArgs &a, int grid,
                                   cudaStream_t s);
-cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, bool tiled, int *grid);
+cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int tiled, int *grid);
 cudaError_t launch_step_so(int prec, int m, bool resid, const StepArgs &a, int grid, cudaStream_t s);
-bool march_supported(int m, int g, int slots, bool defer, bool tiled);
+bool march_supported(int m, int g, int slots, bool defer, int tiled);
 int defect_lanes(int m);
 int correct_lanes(int m);
 cudaError_t launch_correct_f32(int m, int g, bool resid, const StepArgs &a, int grid,
@@ -56,7 +56,7 @@ struct lbm_sim {
     int order;            // transport order: 1 (first-order upwind, the paper's) or 2
     int grid;             // blocks of the bulk step kernel
     int march_grid;       // persistent blocks of the column-march kernel (load paths 4 to 8)
-    bool tiled;           // the state buffers hold the strip-tiled layout (load path 8)
+    bool tiled;           // the state buffers hold the strip-tiled layout (load paths 8, 9)
     long tile_pitch;      // floats per tile of that layout
     int nparts_step;      // residual partial slots of one step (bulk + wall kernels)
     int *wall_segs;       // device list of wall segments for the current lanes
@@ -121,7 +121,7 @@ bool kernel_m_supported(int m) { return m == 3 || m == 4 || m == 6 || m == 8 || 
 
 // grids the column march can take (nx a multiple of 64, at least two strips' width, ten
 // rows); FP32 cavities of such grids get state buffers large enough for the strip-tiled
-// layout of load path 8 as well
+// layout of load paths 8 and 9 as well
 bool march_grid_ok(const lbm_problem *p) { return p->nx % 64 == 0 && p->nx >= 128 && p->ny >= 10; }
 bool tile_eligible(const lbm_problem *p) { return p->prec == LBM_FP32_PERTURB && p->geom == LBM_CAVITY && march_grid_ok(p); }
 
@@ -496,9 +496,10 @@ int default_lanes_per_cell(int prec, int m)
 
 // row slots of the column march's ring for load paths 4 (four), 5 (five), 6 (two slots,
 // two blocks per SM) and 7 (four, relaxation deferred by one row)
-static int march_slots(int pf) { return pf == 6 ? 2 : (pf == 7 || pf == 8) ? 4 : pf; }
+// and on the strip-tiled state 8 (four slots) and 9 (four slots, bulk asynchronous stores)
+static int march_slots(int pf) { return pf == 6 ? 2 : (pf == 7 || pf == 8 || pf == 9) ? 4 : pf; }
 static bool march_defer(int pf) { return pf == 7; }
-static bool march_tiled(int pf) { return pf == 8; }
+static int march_tiled(int pf) { return pf == 8 ? 1 : pf == 9 ? 2 : 0; }
 
 bool step_supported(int prec, int m, int g, int pf)
 {
@@ -510,7 +511,7 @@ bool step_supported(int prec, int m, int g, int pf)
         for (auto &v : tma) if (v[0] == m && v[1] == g) return true;
         return false;
     }
-    if (pf >= 4 && pf <= 8)
+    if (pf >= 4 && pf <= 9)
         return prec == LBM_FP32_PERTURB && march_supported(m, g, march_slots(pf), march_defer(pf), march_tiled(pf));
     if (prec == LBM_FP64) {
         for (auto &v : f64) if (v[0] == m && v[1] == g && v[2] == pf) return true;
@@ -524,7 +525,7 @@ cudaError_t launch_step(int prec, int m, int g, int pf, bool resid, const StepAr
                         cudaStream_t s)
 {
     if (pf == 2 || pf == 3) return launch_step_f32_tma(m, g, resid, a, grid, s, pf == 3);
-    if (pf >= 4 && pf <= 8)
+    if (pf >= 4 && pf <= 9)
         return launch_step_f32_march(m, g, march_slots(pf), march_defer(pf), march_tiled(pf), resid, a, grid, s);
     if (prec == LBM_FP64)
         return m >= 8 ? launch_step_f64_large(m, g, pf, resid, a, grid, s)
@@ -1017,7 +1018,7 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
-    if (prefetch < 0 || prefetch > 8) return fail(LBM_EINVAL, "load path must be 0 to 8");
+    if (prefetch < 0 || prefetch > 9) return fail(LBM_EINVAL, "load path must be 0 to 9");
     if (s->order == 2)
         return fail(LBM_EUNSUPPORTED, "the second-order transport has one kernel variant (lbm_set_transport)");
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
@@ -1029,7 +1030,7 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
         return fail(LBM_EUNSUPPORTED, "the TMA segment kernels need the planar state layout (nx < 64)");
     if (prefetch >= 4 && !march_grid_ok(&s->prob))
         return fail(LBM_EUNSUPPORTED, "the column march needs nx a multiple of 64, nx >= 128 and ny >= 10");
-    if (prefetch == 8 && !tile_eligible(&s->prob))
+    if (march_tiled(prefetch) != 0 && !tile_eligible(&s->prob))
         return fail(LBM_EUNSUPPORTED, "the strip-tiled march needs an FP32 cavity");
     if (prefetch == 2 || prefetch == 3) {
         cudaError_t e = prepare_step_f32_tma(s->vs.m, warps_per_segment);
@@ -1043,8 +1044,8 @@ lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
         if (grid <= 0) return fail(LBM_EUNSUPPORTED, "the column-march kernel does not fit on an SM");
         s->march_grid = grid;
     }
-    // load path 8 marches the strip-tiled state, every other path the planar one
-    cudaError_t e = set_tiled(s, prefetch == 8);
+    // load paths 8 and 9 march the strip-tiled state, every other path the planar one
+    cudaError_t e = set_tiled(s, march_tiled(prefetch) != 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "changing the state layout");
     s->prefetch = prefetch;
@@ -1295,7 +1296,7 @@ lbm_status lbm_state_layout(const lbm_sim *s, long *plane_pitch, long *row_pitch
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (s->tiled)
-        return fail(LBM_EUNSUPPORTED, "the state is strip-tiled (load path 8): see lbm_state_tiling");
+        return fail(LBM_EUNSUPPORTED, "the state is strip-tiled (load path 8 or 9): see lbm_state_tiling");
     if (plane_pitch) *plane_pitch = s->args.pa;
     if (row_pitch) *row_pitch = s->args.py;
     return LBM_OK;

@@ -36,12 +36,21 @@
 // TILED (load path 8): the state is strip-tiled (lbm_internal.h): tile t holds x in
 // [64 t - 32, 64 t + 32) as [y][a][64], so the march's strip s is exactly tile s + 1 and one
 // row of it, all n velocities, is one contiguous stretch of n * 256 bytes.  Per row a warp
-// then copies its NV velocity lines with ONE bulk copy of NV * 256 contiguous bytes, plus,
-// per velocity, the 16 bytes of the neighbouring tile that hold its upwind x halo (positions
-// 60..63 of the left tile for xi_x > 0, 0..3 of the right tile for xi_x < 0; those tiles'
-// rows are being marched by the neighbouring blocks at about the same time, so these reads
-// are mostly L2 hits).  Every DRAM access of the march is then part of a long contiguous
-// stream instead of 144 separate 288-byte lines from planes 16.8 MB apart.
+// then copies its NV velocity lines with ONE bulk copy of NV * 256 contiguous bytes; the
+// upwind x halo of each velocity (the last cell of the left tile for xi_x > 0, the first
+// cell of the right tile for xi_x < 0; those tiles' rows are being marched by the
+// neighbouring blocks at about the same time, so these reads are mostly L2 hits) comes with
+// one 4-byte asynchronous copy per lane (cp.async, the load/store unit's path: as bulk
+// copies of 16 bytes, 24 per warp and row, they held the copy engine to 0.78 of the copy
+// rate), whose completion the same mbarrier tracks (cp.async.mbarrier.arrive.noinc; the
+// barrier expects 1 + NV arrivals).  Every DRAM access of the march is then part of a long
+// contiguous stream instead of 144 separate 288-byte lines from planes 16.8 MB apart.
+// With TILED = 2 (load path 9) the stores go the same way: each warp writes its relaxed row
+// (NV lines, contiguous in the tiled layout) into a staging buffer in shared memory and one
+// lane hands it to the copy engine as a single bulk asynchronous store
+// (cp.async.bulk.global.shared::cta), so the warps issue no global store instructions; the
+// staging buffer is reused only after the previous row's store has read it
+// (cp.async.bulk.wait_group.read), and every store has completed before the block exits.
 #pragma once
 
 #include <cstdint>
@@ -51,7 +60,7 @@
 
 namespace lbmk {
 
-template <int M, int G, int S, bool TILED = false>
+template <int M, int G, int S, int TILED = 0>
 struct MarchShape {
     static constexpr int RPL = M / G;              // velocity rows per warp
     static constexpr int NV = RPL * M;             // velocities per warp
@@ -60,7 +69,8 @@ struct MarchShape {
     static constexpr int LINE = TILED ? 64 : 72;
     static constexpr int SLOT = TILED ? NV * (64 + 4) : NV * LINE;   // floats of one warp's row slot
     static constexpr int THREADS = 32 * G;
-    static constexpr int SMEM = S * G * SLOT * 4 + S * G * 8;
+    static constexpr int OUT = TILED == 2 ? NV * 64 : 0;       // floats of one warp's store staging
+    static constexpr int SMEM = S * G * SLOT * 4 + S * G * 8 + G * OUT * 4;
     // a ring of two slots (the own row and its upwind row, nothing in flight ahead) is small
     // enough for two blocks per SM: the second block computes while the first waits
     static constexpr int MIN_BLOCKS = S == 2 ? 2 : 1;
@@ -82,7 +92,7 @@ __device__ __forceinline__ int march_row0(int k, int rows, int nchunks)
     return 1 + (int)(((long)k * rows) / nchunks);
 }
 
-template <int M, int G, int S, bool RESID, bool DEFER, bool TILED = false>
+template <int M, int G, int S, bool RESID, bool DEFER, int TILED = 0>
 __global__ void __launch_bounds__(MarchShape<M, G, S, TILED>::THREADS, MarchShape<M, G, S, TILED>::MIN_BLOCKS)
 step_march_kernel(const StepArgs a)
 {
@@ -119,6 +129,9 @@ step_march_kernel(const StepArgs a)
     const bool ypos = g * RPL >= HALF;   // xi_y > 0: upwind row y - 1; else y + 1
     float *slots = reinterpret_cast<float *>(smem_raw) + (long)g * S * Sh::SLOT;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (long)S * G * Sh::SLOT * 4) + g * S;
+    // staging of this warp's relaxed row for the bulk store (TILED = 2)
+    float *outst = reinterpret_cast<float *>(smem_raw + (long)S * G * Sh::SLOT * 4 + (long)S * G * 8) + g * Sh::OUT;
+    (void)outst;
     const float *__restrict__ h = reinterpret_cast<const float *>(a.h);
     float *__restrict__ hn = reinterpret_cast<float *>(a.hn);
 
@@ -138,7 +151,8 @@ step_march_kernel(const StepArgs a)
         }
     }
     if (lane == 0) {
-        for (int j = 0; j < S; ++j) mbar_init(&bars[j], 1);
+        // tiled: lane 0's expect-tx arrival and the NV lanes' halo copies complete a phase
+        for (int j = 0; j < S; ++j) mbar_init(&bars[j], TILED ? 1 + NV : 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -169,14 +183,16 @@ step_march_kernel(const StepArgs a)
     // as an offset from the left tile's row
     constexpr long TROW = (long)M * M * LBM_TILE_W;
     const long tp = a.tile_pitch;
-    const long halo_off = (kc % M) >= M - HALF ? (long)(g * NV + kc) * LBM_TILE_W + (LBM_TILE_W - 4)
-                                               : 2 * tp + (long)(g * NV + kc) * LBM_TILE_W;
+    const bool left_halo = (kc % M) >= M - HALF;
+    const long halo_off = left_halo ? (long)(g * NV + kc) * LBM_TILE_W + (LBM_TILE_W - 1)
+                                    : 2 * tp + (long)(g * NV + kc) * LBM_TILE_W;
+    const int halo_dst = NV * LBM_TILE_W + 4 * kc + (left_halo ? 3 : 0);   // where the kernel reads it
     // x-upwind neighbour of a lane's cell pair, as base + k * step floats from the own row
     // slot (velocity k of the warp): the neighbouring cell of the own line, or, for the
     // strip's edge lane, the halo copied from the neighbouring tile
     const int pl_base = lane > 0 ? 2 * lane - 1 : NV * LBM_TILE_W + 3, pl_step = lane > 0 ? LBM_TILE_W : 4;
     const int pr_base = lane < 31 ? 2 * lane + 2 : NV * LBM_TILE_W, pr_step = lane < 31 ? LBM_TILE_W : 4;
-    (void)tp; (void)halo_off; (void)pl_base; (void)pl_step; (void)pr_base; (void)pr_step;
+    (void)tp; (void)halo_off; (void)halo_dst; (void)pl_base; (void)pl_step; (void)pr_base; (void)pr_step;
 
     // loader state (uniform within the warp)
     int l_pos = 0, l_item = s_items[0], l_i = 0;
@@ -195,12 +211,18 @@ step_march_kernel(const StepArgs a)
         const int slot = (int)(nl % S);
         const int row = l_row0 - (ypos ? 1 : 0) + l_i;
         if constexpr (TILED) {
-            if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * (LBM_TILE_W + 4) * 4));
+            // transaction bytes of the bulk copy only: the halo copies count as arrivals
+            if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * LBM_TILE_W * 4));
             __syncwarp();
             fence_proxy_async_smem();
             float *dst = slots + slot * Sh::SLOT;
             const float *left_row = h + (long)l_strip * tp + (long)row * TROW;
-            if (lane < NV) bulk_copy(dst + NV * LBM_TILE_W + 4 * lane, left_row + halo_off, 16, &bars[slot]);
+            if (lane < NV) {
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n"
+                             "cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%2];\n" ::"r"(smem_addr(dst + halo_dst)),
+                             "l"(left_row + halo_off), "r"(smem_addr(&bars[slot]))
+                             : "memory");
+            }
             if (lane == 0)
                 bulk_copy(dst, left_row + tp + (long)g * NV * LBM_TILE_W, NV * LBM_TILE_W * 4, &bars[slot]);
         } else {
@@ -410,6 +432,13 @@ step_march_kernel(const StepArgs a)
             const float2 jj2 = __fmul2_rn(make_float2(wom, wom), jx2);
             float *rowp = TILED ? hn + tcell + (long)(iy * M) * LBM_TILE_W : hn + (long)(iy * M) * ncells + cell;
             const long vstride = TILED ? (long)LBM_TILE_W : ncells;
+            if constexpr (TILED == 2) {
+                if (r == 0) {
+                    // the previous row's bulk store must have read the staging buffer
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                    __syncwarp();
+                }
+            }
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
                 const int k = r * M + ix;
@@ -421,7 +450,22 @@ step_march_kernel(const StepArgs a)
                     psd2 = __ffma2_rn(d, d, psd2);
                     psn2 = __ffma2_rn(v, v, psn2);
                 }
-                *reinterpret_cast<float2 *>(rowp + (long)ix * vstride) = v;
+                if constexpr (TILED == 2)
+                    *reinterpret_cast<float2 *>(outst + k * LBM_TILE_W + 2 * lane) = v;
+                else
+                    *reinterpret_cast<float2 *>(rowp + (long)ix * vstride) = v;
+            }
+        }
+        if constexpr (TILED == 2) {
+            // this warp's NV lines of the strip's tile row, one contiguous stretch
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                float *dst = hn + (tcell - 2 * lane) + (long)g * NV * LBM_TILE_W;
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+                             "cp.async.bulk.commit_group;\n" ::"l"(dst), "r"(smem_addr(outst)),
+                             "r"((unsigned)(NV * LBM_TILE_W * 4))
+                             : "memory");
             }
         }
         if (RESID) {
@@ -450,6 +494,9 @@ step_march_kernel(const StepArgs a)
 
     // copies still in flight (abort path) must land before the block's shared memory goes
     for (; waited < nl; ++waited) mbar_wait_bounded(&bars[waited % S], (unsigned)((waited / S) & 1), 2000000000LL);
+    // and the bulk stores must have completed (their source and the new state)
+    if constexpr (TILED == 2)
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 
     if (RESID) {
 #pragma unroll
@@ -483,7 +530,7 @@ step_march_kernel(const StepArgs a)
     }
 }
 
-template <int M, int G, int S, bool DEFER, bool TILED = false>
+template <int M, int G, int S, bool DEFER, int TILED = 0>
 cudaError_t prepare_march(int *grid)
 {
     constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;
@@ -519,16 +566,16 @@ cudaError_t prepare_march(int *grid)
 // write disjoint cells of the new one).  Block 0 waits for the march grid before it exits,
 // so that this grid completes only after the march has completed and its writes are
 // visible: work the stream orders after this launch sees the whole step.
-template <int M, int G, bool RESID, bool TILED = false>
+template <int M, int G, bool RESID, int TILED = 0>
 __global__ void __launch_bounds__(Shape<G>::THREADS) step_wall_beside_march_kernel(const StepArgs a)
 {
-    step_body<float, float, M, G, RESID, false, false, true, false, TILED>(a, blockIdx.x);
+    step_body<float, float, M, G, RESID, false, false, true, false, TILED != 0>(a, blockIdx.x);
     if (blockIdx.x == 0) asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
 // March kernel over `grid` persistent blocks, and beside it the wall kernel over the wall
 // segments (programmatic dependent launch).
-template <int M, int G, int S, bool DEFER, bool RESID, bool TILED = false>
+template <int M, int G, int S, bool DEFER, bool RESID, int TILED = 0>
 cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
 {
     constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;

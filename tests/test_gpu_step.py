@@ -419,15 +419,16 @@ def test_fp32_kernel_variants_agree(n_half, nx, ny, variants):
 
 @pytest.mark.parametrize("n_half,nx,ny,variants", [
     # 2 strips x 5 chunks: fewer items than blocks (most blocks find no work)
-    (6, 192, 45, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (12, 4), (12, 5)]),
+    (6, 192, 45, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (6, 9), (12, 4), (12, 5)]),
     # 5 strips x 65 chunks of 8 rows: more items than blocks, item-to-item pipelining
-    (6, 384, 522, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (12, 5)]),
-    (4, 256, 70, [(2, 0), (2, 5), (4, 0), (4, 5), (4, 8)]),
+    (6, 384, 522, [(6, 0), (6, 4), (6, 5), (6, 6), (6, 7), (6, 8), (6, 9), (12, 5)]),
+    (4, 256, 70, [(2, 0), (2, 5), (4, 0), (4, 5), (4, 8), (4, 9)]),
     # 15 strips x 41+ chunks: items beyond the fixed first three per block come from the counter
-    (6, 1024, 1000, [(6, 0), (6, 4), (6, 6), (6, 7), (6, 8), (12, 5)]),
+    (6, 1024, 1000, [(6, 0), (6, 4), (6, 6), (6, 7), (6, 8), (6, 9), (12, 5)]),
 ])
 def test_fp32_column_march_matches_oracle(n_half, nx, ny, variants):
-    """The column-march interior (load paths 4 to 8; 8 on the strip-tiled state) gives the oracle's result to FP32 accuracy
+    """The column-march interior (load paths 4 to 9; 8 and 9 on the strip-tiled state, 9 with
+    bulk asynchronous stores) gives the oracle's result to FP32 accuracy
     over several steps, with and without the residual, and agrees with the segment kernels
     to within a few FP32 roundings."""
     p = oracle_problem("half", n_half, CAVITY, nx, ny, 0.07, 0.002, 0.01)

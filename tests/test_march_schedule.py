@@ -201,11 +201,12 @@ def test_tiled_offsets_are_a_bijection_onto_the_buffer(nx, ny, n):
 @pytest.mark.parametrize("nx,ny", [(128, 10), (192, 45), (384, 30), (2048, 12)])
 @pytest.mark.parametrize("m,g", [(12, 6), (8, 4)])
 def test_tiled_march_copies(nx, ny, m, g):
-    """Every row copy of the tiled march (one contiguous copy of the warp's lines, one 16-byte
-    halo copy per velocity) starts 16-byte aligned inside the buffer, the line copy covers
-    exactly the warp's velocities of the strip's cells in that row, and each halo copy holds
-    the upwind x neighbour of the strip's edge cell for that velocity at the position the
-    kernel reads (index 3 of the left halo, index 0 of the right halo)."""
+    """Every row copy of the tiled march (one contiguous bulk copy of the warp's lines, one
+    4-byte asynchronous copy of the x halo per velocity) lies inside the buffer, the bulk copy
+    starts 16-byte aligned and covers exactly the warp's velocities of the strip's cells in
+    that row, and each halo copy takes the upwind x neighbour of the strip's edge cell for that
+    velocity into the position the kernel reads (index 3 of the velocity's 4-float halo slot
+    for the left neighbour, index 0 for the right one)."""
     n, half = m * m, m // 2
     rpl = m // g
     nvw = rpl * m
@@ -222,15 +223,19 @@ def test_tiled_march_copies(nx, ny, m, g):
                 for q in range(nvw * TILE_W):
                     x, y, a = tiled_cell(big + q, n, tp)
                     assert (y, a) == (row, w * nvw + q // TILE_W) and x == x0 + q % TILE_W
+                dsts = set()
                 for k in range(nvw):
                     ix = k % m
                     a = w * nvw + k
                     if ix >= m - half:
-                        halo = left_row + a * TILE_W + (TILE_W - 4)
-                        want, idx = x0 - 1, 3
+                        halo = left_row + a * TILE_W + (TILE_W - 1)
+                        want, dst = x0 - 1, nvw * TILE_W + 4 * k + 3
                     else:
                         halo = left_row + 2 * tp + a * TILE_W
-                        want, idx = x0 + 64, 0
-                    assert halo % 4 == 0 and 0 <= halo and halo + 4 <= size
-                    x, y, aa = tiled_cell(halo + idx, n, tp)
+                        want, dst = x0 + 64, nvw * TILE_W + 4 * k
+                    assert 0 <= halo < size
+                    x, y, aa = tiled_cell(halo, n, tp)
                     assert (x, y, aa) == (want, row, a) and 0 <= x < nx
+                    # inside the warp's slot (dense lines, then 4 floats per velocity), one each
+                    assert nvw * TILE_W <= dst < nvw * (TILE_W + 4) and dst not in dsts
+                    dsts.add(dst)
