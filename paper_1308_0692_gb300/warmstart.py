@@ -235,7 +235,7 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--params", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
                                                      "warmstart_mlp.npy"))
-    ap.add_argument("--accuracy-count", type=int, default=16)
+    ap.add_argument("--accuracy-count", type=int, default=256)
     ap.add_argument("--out", default=None, help="write a JSON report here")
     args = ap.parse_args(argv)
     report = {}
