@@ -40,15 +40,39 @@ namespace {
 
 enum { BATCH_MARCH = 0, BATCH_CORRECT = 1, BATCH_DEFECT = 2 };
 
+// Instance state layouts.  Couette channels: planar [n][ny][nx].  Cavities: strip-tiled, tiles
+// of 32 columns (tile t holds x in [32 t, 32 t + 32)), each tile [y][pair][32 cells][2] with the
+// two velocities (2p, 2p + 1) of a pair side by side in every cell: value (a, x, y) at
+//   (x / 32) * tile_pitch + y * 32 n + (a / 2) * 64 + (x mod 32) * 2 + (a mod 2),
+// tile_pitch = 32 n ny.  A row of a 32-column strip is then one contiguous stretch of 128 n
+// bytes, and a warp's velocity pairs of that row one contiguous piece of it (the column march
+// copies it with one bulk copy); the last tile of a width that is not a multiple of 32 is
+// padded.
+__host__ __device__ inline long tile32_off(int x, int y, int n, int ny)
+{
+    return (long)(x >> 5) * (32L * n * ny) + (long)y * (32L * n) + (long)(x & 31) * 2;
+}
+__host__ __device__ inline long tile32_vel(int a) { return (long)(a >> 1) * 64 + (a & 1); }
+
 struct BatchInst {
-    long off;           // element offset of the instance's state [n][ncells] in each array
+    long off;           // element offset of the instance's state in each array
     long ncells;
     int nx, ny, cavity;
-    int pad;
+    int tiled;          // cavity: strip-tiled layout (tile32_off); else planar [n][ny][nx]
     double cx, cy;      // dt/dx (0 for a single periodic Couette column), dt/dy
     double omega, b;
     double u_bottom, u_top, inv_u_ref;
 };
+
+// values of an instance's state (with the padding of its last tile when tiled)
+__host__ __device__ inline long inst_vals(const BatchInst &I, int nv)
+{
+    return I.tiled ? (long)((I.nx + 31) / 32) * I.ny * nv * 32 : (long)nv * I.ncells;
+}
+__host__ __device__ inline long inst_index(const BatchInst &I, int n, int a, int x, int y)
+{
+    return I.tiled ? tile32_off(x, y, n, I.ny) + tile32_vel(a) : (long)a * I.ncells + (long)y * I.nx + x;
+}
 
 // One work item: a 32-cell segment of one instance, with the instance's addressing (first
 // 32 bytes: fetched one item group ahead, so that the state loads of a group do not wait
@@ -86,7 +110,10 @@ struct BatchArgs {
     long *frozen;          // [ninst] step count at convergence (LONG_MAX while active)
     unsigned *bar_count;
     unsigned *bar_gen;
-    unsigned *mcount;      // column march: next item of the step, per step parity [2]
+    unsigned *mcount;      // column march: next item of the launch (all steps, step-major)
+    unsigned *ifin;        // column march: [ninst] items of the instance finished in this launch
+    unsigned *idone;       // column march: [ninst] steps of the instance completed in this launch
+    const int *iitems;     // column march: [ninst] items of the instance per step
     int *err;
     long step0;
     int nsteps;
@@ -231,10 +258,19 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
     const int y = (int)(c / nx), x = (int)(c - (long)y * nx);
     const TS *hi = h + A.off;
     TS *hno = hn + A.off;
-    const long c_left = (x > 0) ? c - 1 : (cav ? c : c + nx - 1);
-    const long c_right = (x < nx - 1) ? c + 1 : (cav ? c : c - (nx - 1));
-    const long c_below = (y > 0) ? c - nx : c;
-    const long c_above = (y < ny - 1) ? c + nx : c;
+    // cell offsets (velocity 0) and the offset of velocity a, (a / 2) * ps + (a mod 2) * os:
+    // cavities are strip-tiled, channels planar
+    const bool tl = cav;
+    auto cell_off = [&](int xx, int yy) -> long {
+        return tl ? tile32_off(xx, yy, M * M, ny) : (long)yy * nx + xx;
+    };
+    const long ps = tl ? 64 : 2 * ncells, os = tl ? 1 : ncells;
+    auto vo = [&](int aa) -> long { return (long)(aa >> 1) * ps + (aa & 1) * os; };
+    const long c_at = cell_off(x, y);
+    const long c_left = (x > 0) ? cell_off(x - 1, y) : (cav ? c_at : cell_off(nx - 1, y));
+    const long c_right = (x < nx - 1) ? cell_off(x + 1, y) : (cav ? c_at : cell_off(0, y));
+    const long c_below = (y > 0) ? cell_off(x, y - 1) : c_at;
+    const long c_above = (y < ny - 1) ? cell_off(x, y + 1) : c_at;
     const bool wl = WALLS && cav && x == 0, wr = WALLS && cav && x == nx - 1;
     const bool wb = WALLS && y == 0, wt = WALLS && y == ny - 1;
 
@@ -255,12 +291,12 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
                 while (m) {
                     const int L = __ffs(m) - 1;
                     m &= m - 1;
-                    const long cL = __shfl_sync(FULL, c, L);
+                    const long cL = __shfl_sync(FULL, c_at, L);
                     double part = 0.0;
                     for (int k = lane; k < NSIDE; k += 32) {
                         const int r = k / HALF, q = k - r * HALF;
                         const int iy = g * RPL + r, ix = side == 0 ? q : M - HALF + q;
-                        const TC v = (TC)__ldg(hi + (long)(iy * M + ix) * ncells + cL);
+                        const TC v = (TC)__ldg(hi + vo(iy * M + ix) + cL);
                         const TC xv = pk<TC>(a.xi, a.xi_f, ix) * v;
                         part += side == 0 ? -(double)xv : (double)xv;
                     }
@@ -280,7 +316,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
                 TC rowsum = 0, left = 0, right = 0;
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
-                    const TC v = (TC)__ldg(hi + (long)(iy * M + ix) * ncells + c);
+                    const TC v = (TC)__ldg(hi + vo(iy * M + ix) + c_at);
                     rowsum += v;
                     if (ix < HALF) left -= pk<TC>(a.xi, a.xi_f, ix) * v;
                     if (ix >= M - HALF) right += pk<TC>(a.xi, a.xi_f, ix) * v;
@@ -320,7 +356,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
             const TC xiy = pk<TC>(a.xi, a.xi_f, iy);
             const TC nuy = (xiy < TC(0) ? -xiy : xiy) * cy;
             const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
-            const long cy_idx = ypos ? c_below : (yneg ? c_above : c);
+            const long cy_idx = ypos ? c_below : (yneg ? c_above : c_at);
             const bool ywall = WALLS && ((ypos && wb) || (yneg && wt));
             const TC rho_y = (TC)(ypos ? rb : rt);
             const TC u_y = ypos ? k_ub : k_ut;
@@ -330,8 +366,8 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = hi + (long)(iy * M + ix) * ncells;
-                const TC hc = (TC)__ldg(hp + c);
+                const TS *hp = hi + vo(iy * M + ix);
+                const TC hc = (TC)__ldg(hp + c_at);
                 const TC xix = pk<TC>(a.xi, a.xi_f, ix);
                 TC v = hc;
                 if (ix >= M - HALF || ix < HALF) {
@@ -381,7 +417,7 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, const BatchItem 
             const TC jj = wom * jx;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const long off = (long)(iy * M + ix) * ncells + c;
+                const long off = vo(iy * M + ix) + c_at;
                 const TC t = q + pk<TC>(a.xi, a.xi_f, ix) * jj;
                 TC v = b * hs[r * M + ix] + pk<TC>(a.w1, a.w1_f, ix) * t;
                 if (MODE == BATCH_CORRECT) v += (TC)__ldg(a.src + A.off + off);
@@ -484,21 +520,29 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float x)
     s = t;
 }
 
-// Column march over cavity instances.  A sub-block of M warps takes one item (a 32-column
-// strip of a chunk of rows); warp iy owns the M velocities of velocity row iy (one xi_y, so
-// its upwind y neighbour is the row below when xi_y > 0, the row above otherwise), lane l
-// owns column x0 + l.  The strip marches up its rows through a ring of four row slots per
-// warp in shared memory, filled by cp.async two rows ahead (the in-flight rows hold no
-// registers): every value is read from memory once per step, plus one extra row per chunk
-// and the two edge columns of each row (served by L2), and the x and y neighbours are read
-// from the ring.  Per row the warps exchange their moment partials through shared memory
-// (one named barrier per row, double-buffered), and with them the wall-density partials
-// of the next row (Eq. 9: side walls from the wall cells' outgoing velocities, the top
-// wall at the last row), so that the ghosts of the next row are known before its
+// Column march over cavity instances.  A sub-block of G warps takes one item (a 32-column
+// strip of a chunk of rows); warp g owns RPL velocity rows (one sign of xi_y, so its upwind y
+// neighbour is the row below when xi_y > 0, the row above otherwise), lane l owns column
+// x0 + l.  The strip marches up its rows through a ring of four row slots per warp in
+// shared memory, two rows ahead.  The instance is strip-tiled (tile32_off: a tile is one
+// 32-column strip), so a warp's velocity pairs of a row are one contiguous piece of
+// 8 * RPL * M bytes: one bulk asynchronous copy (cp.async.bulk) fills the slot, and the x
+// halo of each velocity pair (the left tile's last cell for pairs moving right, the right
+// tile's first cell for pairs moving left) comes with one 8-byte cp.async per pair on the
+// load/store unit; the slot's mbarrier counts the bulk copy's bytes and the halo copies'
+// arrivals (cp.async.mbarrier.arrive.noinc).  Every value is read from memory once per step,
+// plus one extra row per chunk and the halos (served by L2), and the x and y neighbours are
+// read from the ring.  Per row the warps exchange their moment partials through shared
+// memory (one named barrier per row, double-buffered), and with them the wall-density
+// partials of the next row (Eq. 9: side walls from the wall cells' outgoing velocities, the
+// top wall at the last row), so that the ghosts of the next row are known before its
 // transport; the bottom wall's are formed before the first row of a chunk that starts at
-// y = 0.  Arithmetic in FP32 with the same operations in the
-// same order as batch_group; the wall sums and the residual sums are compensated FP32
-// (comp_add), which keeps FP64-grade sums off the slow FP64 pipe.
+// y = 0.  Arithmetic in FP32 with the same operations in the same order as batch_group; the
+// wall sums and the residual sums are compensated FP32 (comp_add), which keeps FP64-grade
+// sums off the slow FP64 pipe.  Stores: each lane writes its cell's velocity pairs as 8-byte
+// stores, a warp instruction covering 256 contiguous bytes.  Every wait on a slot is bounded;
+// after the limit the batch's error word is set and the waits of the launch are skipped
+// (the grid barrier then ends the launch and the host reports LBM_ETIMEOUT).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void named_barrier(int id, int nthreads)
 {
@@ -510,12 +554,13 @@ struct MarchShared {
     static constexpr int RPL = M / G;    // velocity rows per warp
     static constexpr int SUB = 8 / G;    // items per block of 8 warps
     static constexpr int NS = 4;         // row slots per warp
-    static constexpr int RW = 34;        // a row line: left edge, 32 cells, right edge
     static constexpr int PW = RPL * M / 2;   // velocity pairs per warp
+    static constexpr int SLOT = PW * 32 + PW;   // float2: PW pair lines of 32 cells, then one halo per line
     float4 mom[SUB][2][G][32];           // [item][row parity][warp][lane]: (rho, jx, jy, -) partials
     float2 side[SUB][2][2][G];           // [item][parity][left, right][warp]: (sum, error)
     float2 tb[SUB][2][G][32];            // [item][parity][warp][lane]: bottom or top wall row
-    float2 ring[8][NS][PW][RW];          // [warp][slot][velocity pair][line]: velocities (2q, 2q + 1)
+    float2 ring[8][NS][SLOT];            // [warp][slot]: velocity pairs (2q, 2q + 1) of a row
+    uint64_t bar[8][NS];                 // [warp][slot]: fill of the slot complete
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p)
@@ -523,30 +568,36 @@ __device__ __forceinline__ unsigned smem_addr(const void *p)
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 // nodes and 1-D weights of the velocity pair (2j, 2j + 1)
 __device__ __forceinline__ float2 xi2(const BatchArgs &a, int j) { return make_float2(a.xi_f[2 * j], a.xi_f[2 * j + 1]); }
 __device__ __forceinline__ float2 w2(const BatchArgs &a, int j) { return make_float2(a.w1_f[2 * j], a.w1_f[2 * j + 1]); }
 
+__device__ __forceinline__ bool slot_try(uint64_t *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_addr(bar)), "r"(parity), "r"(1000000u)
+                 : "memory");
+    return done != 0;
+}
+
+// State of a warp's ring across items and steps: the parity each slot's next fill completes
+// with (bit s) and which slots have a fill not yet waited for.
+struct RingState {
+    unsigned ph = 0, pend = 0;
+};
+
 template <int M, int G, int MODE>
 __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *mi, long s, const float *h,
-                                           float *hn, bool resid, MarchShared<M, G> &sh)
+                                           float *hn, bool resid, MarchShared<M, G> &sh, RingState &rs)
 {
     using Sh = MarchShared<M, G>;
     constexpr int P = M / 2, PH = P / 2;                  // pairs per velocity row; j >= PH move right
-    constexpr int RPL = Sh::RPL, SUB = Sh::SUB, NS = Sh::NS, RW = Sh::RW, PW = Sh::PW;
-    static_assert(SUB * G == 8 && RPL * M <= 16 && (M / 2) % 2 == 0, "eight warps per block; edge lanes; pairs on one side");
+    constexpr int RPL = Sh::RPL, SUB = Sh::SUB, NS = Sh::NS, PW = Sh::PW;
+    static_assert(SUB * G == 8 && PW <= 32 && (M / 2) % 2 == 0, "eight warps per block; halo lanes; pairs on one side");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = warp / G, g = warp - sub * G;
@@ -559,7 +610,6 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     const long off = (long)(((unsigned long long)(unsigned)q0.y << 32) | (unsigned)q0.x);
     const int inst = q0.z, nx = q0.w, ny = q1.x, x0 = q1.y, y0 = q1.z, y1 = q1.w;
     if (a.frozen[inst] <= s) return;          // converged: its state stays put
-    const int nc = nx * ny;                   // cells of the instance (its state < 2^31 values)
     const float cx = k0.x, cy = k0.y, om = k0.z, bb = k0.w;
 
     // this warp's velocity rows iy0 .. iy0 + RPL - 1 share the sign of xi_y
@@ -583,31 +633,67 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     const bool wl = x == 0, wr = x == nx - 1;
     const bool side_l = x0 == 0, side_r = x0 + 32 >= nx, side = side_l || side_r;
     const int lr = nx - 1 - x0;               // lane of the right-wall cell when side_r
-    const float *hb = h + off + (long)(iy0 * M) * nc;
-    float *ho = hn + off + (long)(iy0 * M) * nc;
-    float2 (*ring)[PW][RW] = sh.ring[warp];
+    // strip-tiled addressing: the strip is tile x0 / 32; a row is 32 n floats; this warp's
+    // pairs start at pair iy0 * M / 2 of the row
+    constexpr int NVEL = M * M;
+    const long tp = 32L * NVEL * ny, trow = 32L * NVEL;
+    const int tile = x0 >> 5, ntiles = (nx + 31) >> 5;
+    const long wbase = off + (long)tile * tp + (long)(iy0 * M / 2) * 64;
+    float2(*ring)[Sh::SLOT] = sh.ring[warp];
+    uint64_t *bars = sh.bar[warp];
+    // halo source of pair lane (lanes < PW): left tile's cell 31 for pairs moving right, right
+    // tile's cell 0 for pairs moving left; a strip at a side wall takes its own tile there
+    // (the wall lane uses the ghost instead)
+    const int hq = lane < PW ? lane : 0, hj = hq % P;
+    const long halo_off = hj >= PH ? (tile > 0 ? -tp + 62 : 0) : (tile + 1 < ntiles ? tp : 0);
+    const float *hsrc = h + wbase + (long)hq * 64 + halo_off;
 
-    // copy row r of this warp's RPL * M velocities (local index k = rr * M + ix) into slot
-    // r mod NS: the 32 cells (clamped into the row), and in one more copy the edge columns
-    // x0 - 1 (lanes 0..RPL*M-1, one velocity each) and x0 + 32 (lanes 16..16+RPL*M-1); one
-    // commit group per call
-    const int xc = valid ? x : nx - 1;
-    const bool edge_l = lane < RPL * M, edge_r = lane >= 16 && lane < 16 + RPL * M;
-    const int e_k = edge_l ? lane : lane - 16;
-    const int e_x = edge_l ? (x0 > 0 ? x0 - 1 : 0) : min(x0 + 32, nx - 1);
-    auto copy_row = [&](int r, bool issue) {
-        if (issue) {
-            float2 (*slot)[RW] = ring[r & (NS - 1)];
-            const float *src = hb + (r * nx + xc);
-#pragma unroll
-            for (int k = 0; k < RPL * M; ++k)
-                cp_async4(reinterpret_cast<float *>(&slot[k >> 1][1 + lane]) + (k & 1), src + k * nc);
-            if (edge_l || edge_r)
-                cp_async4(reinterpret_cast<float *>(&slot[e_k >> 1][edge_l ? 0 : RW - 1]) + (e_k & 1),
-                          hb + (e_k * nc + r * nx + e_x));
+    auto wait_slot = [&](int sl) {
+        if (!((rs.pend >> sl) & 1)) return;
+        if (*(volatile int *)a.err == 0) {
+            const long long t0 = clock64();
+            bool ok = true;
+            while (!slot_try(&bars[sl], (rs.ph >> sl) & 1u)) {
+                if (clock64() - t0 > a.timeout_cycles) {
+                    ok = false;
+                    break;
+                }
+            }
+            ok = __all_sync(FULL, ok);
+            if (!ok && lane == 0) atomicExch(a.err, 1);
         }
-        cp_async_commit();
+        rs.ph ^= 1u << sl;
+        rs.pend &= ~(1u << sl);
     };
+    auto wait_row = [&](int r) { wait_slot(r & (NS - 1)); };
+    // fill the slot of row r with this warp's pairs of the row and their halos
+    auto copy_row = [&](int r, bool issue) {
+        if (!issue) return;
+        const int sl = r & (NS - 1);
+        wait_slot(sl);                          // (never pending here: its row was consumed)
+        float2 *slot = ring[sl];
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(&bars[sl])),
+                         "r"((unsigned)(PW * 256))
+                         : "memory");
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads of the slot first
+        if (lane == 0)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                         ::"r"(smem_addr(slot)), "l"(h + wbase + (long)r * trow), "r"((unsigned)(PW * 256)),
+                         "r"(smem_addr(&bars[sl]))
+                         : "memory");
+        if (lane < PW)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n"
+                         "cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%2];\n" ::"r"(smem_addr(slot + PW * 32 + lane)),
+                         "l"(hsrc + (long)r * trow), "r"(smem_addr(&bars[sl]))
+                         : "memory");
+        rs.pend |= 1u << sl;
+    };
+    // x-upwind neighbour of a lane's cell in pair line qq: the neighbouring cell of the line, or
+    // for the strip's edge lane the halo (index base + qq * step of the slot)
+    const int bl = lane > 0 ? lane - 1 : PW * 32, stl = lane > 0 ? 32 : 1;
+    const int br = lane < 31 ? lane + 1 : PW * 32, str = lane < 31 ? 32 : 1;
     // moving up: rows r - 1, r in hand and r + 1, r + 2 in flight at row r; moving down:
     // r, r + 1 in hand and r + 2, r + 3 in flight.  The last row a warp reads:
     const int lim = up ? y1 - 1 : min(y1, ny - 1);
@@ -620,21 +706,17 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         copy_row(y0 + 1, y0 + 1 <= lim);
         copy_row(y0 + 2, y0 + 2 <= lim);
     }
-    auto wait_in_hand = [&]() {               // all groups but the newest have landed
-        cp_async_wait<1>();
-        __syncwarp();
-    };
 
     // Eq. 9 sums: the outgoing velocities' normal fluxes at the wall cells of row r
     auto wall_partials = [&](int r, int p) {
-        const float2 (*row)[RW] = ring[r & (NS - 1)];
+        const float2 *row = ring[r & (NS - 1)];
         if (side_l && lane == 0) {
             float hi = 0.f, lo = 0.f;
 #pragma unroll
             for (int rr = 0; rr < RPL; ++rr)
 #pragma unroll
                 for (int j = 0; j < PH; ++j) {
-                    const float2 u = row[rr * P + j][1];
+                    const float2 u = row[(rr * P + j) * 32];
                     comp_add(hi, lo, -(a.xi_f[2 * j] * u.x));
                     comp_add(hi, lo, -(a.xi_f[2 * j + 1] * u.y));
                 }
@@ -646,7 +728,7 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
             for (int rr = 0; rr < RPL; ++rr)
 #pragma unroll
                 for (int j = PH; j < P; ++j) {
-                    const float2 u = row[rr * P + j][1 + lr];
+                    const float2 u = row[(rr * P + j) * 32 + lr];
                     comp_add(hi, lo, a.xi_f[2 * j] * u.x);
                     comp_add(hi, lo, a.xi_f[2 * j + 1] * u.y);
                 }
@@ -661,7 +743,7 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
                 float hi = 0.f, lo = 0.f;
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
-                    const float2 u = row[rr * P + j][1 + lane];
+                    const float2 u = row[(rr * P + j) * 32 + lane];
                     comp_add(hi, lo, u.x);
                     comp_add(hi, lo, u.y);
                 }
@@ -690,7 +772,7 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         if (side_r) rho_r = total(&sh.side[sub][p][1][0], 1, a.inv_dx_wall_f);
         if (r == 0 || r == ny - 1) rho_w = total(&sh.tb[sub][p][0][lane], 32, a.inv_dy_wall_f);
     };
-    wait_in_hand();
+    wait_row(y0);
     {
         const int p0 = (y0 + 1) & 1;
         wall_partials(y0, p0);
@@ -700,14 +782,14 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     // wall speed and driving term of the wall this warp's velocities come from (Eq. 8)
     const float uw = up ? k1.x : k1.y;
     const float dw = MODE == BATCH_CORRECT ? 0.f : (up ? k1.z : k1.w);
-    const float *sb = MODE == BATCH_CORRECT ? a.src + off + (long)(iy0 * M) * nc : nullptr;
+    const float *sb = MODE == BATCH_CORRECT ? a.src + wbase : nullptr;
 
     float2 v[PW];
     // transport (Eqs. 1, 8-9) of row r into v[] (FP32x2 over velocity pairs, per velocity the
     // same operations as batch_group); SIDE: a side-wall cell in the strip, WROW: the y ghost
     // of a wall row.  Returns the partial moments (rho, jx, jy) of the warp's velocities.
     // (called with literal flags: each call site is inlined and specialised)
-    auto transport = [&](bool SIDE, bool WROW, const float2 (*cur)[RW], const float2 (*yrow)[RW]) {
+    auto transport = [&](bool SIDE, bool WROW, const float2 *cur, const float2 *yrow) {
         float R = 0.f, X = 0.f, Y = 0.f;
 #pragma unroll
         for (int rr = 0; rr < RPL; ++rr) {
@@ -716,8 +798,8 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 const int qq = rr * P + j;
-                const float2 hc = cur[qq][1 + lane];
-                float2 xn = cur[qq][j >= PH ? lane : lane + 2];
+                const float2 hc = cur[qq * 32 + lane];
+                float2 xn = cur[j >= PH ? bl + qq * stl : br + qq * str];
                 if (SIDE) {
                     const float2 wa = __fmul2_rn(w2(a, j), wyy);
                     if (j >= PH && wl) xn = __fmul2_rn(wa, splat(rho_l));
@@ -729,7 +811,7 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
                     const float2 gg = __ffma2_rn(xi2(a, j), splat(uw), splat(1.f));
                     yn = __fmul2_rn(wa, __ffma2_rn(xi2(a, j), splat(dw), __fmul2_rn(splat(rho_w), gg)));
                 } else {
-                    yn = yrow[qq][1 + lane];
+                    yn = yrow[qq * 32 + lane];
                 }
                 float2 t = __ffma2_rn(nux2[j], __fadd2_rn(xn, neg2(hc)), hc);
                 t = __ffma2_rn(splat(nuyr[rr]), __fadd2_rn(yn, neg2(hc)), t);
@@ -747,8 +829,9 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     float psd = 0.f, psd_c = 0.f, psn = 0.f, psn_c = 0.f;
     // relaxation (Eqs. 5-7) towards w_a (rho + xi.j) and the store; RESID: residual sums
     float2 src[MODE == BATCH_CORRECT ? PW : 1];   // the correction's source of the current row
-    auto relax = [&](bool RESID, const float2 (*cur)[RW], float rho, float jx, float jy, int o) {
+    auto relax = [&](bool RESID, const float2 *cur, float rho, float jx, float jy, int r) {
         float2 sd = make_float2(0.f, 0.f), sn = make_float2(0.f, 0.f);
+        float2 *orow = reinterpret_cast<float2 *>(hn + wbase + (long)r * trow) + lane;
 #pragma unroll
         for (int rr = 0; rr < RPL; ++rr) {
             const float wom = om * wyr[rr];
@@ -761,14 +844,11 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
                 float2 nv = __ffma2_rn(w2(a, j), t, __fmul2_rn(splat(bb), v[qq]));
                 if (MODE == BATCH_CORRECT) nv = __fadd2_rn(nv, src[qq]);
                 if (RESID) {
-                    const float2 d = __fadd2_rn(nv, neg2(cur[qq][1 + lane]));
+                    const float2 d = __fadd2_rn(nv, neg2(cur[qq * 32 + lane]));
                     sd = __ffma2_rn(d, d, sd);
                     sn = __ffma2_rn(nv, nv, sn);
                 }
-                if (valid) {
-                    ho[(rr * M + 2 * j) * nc + o] = nv.x;
-                    ho[(rr * M + 2 * j + 1) * nc + o] = nv.y;
-                }
+                if (valid) orow[qq * 32] = nv;
             }
         }
         if (RESID && valid) {
@@ -779,18 +859,19 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
 
     for (int r = y0; r < y1; ++r) {
         const int p = r & 1;
-        if (r > y0) wait_in_hand();
+        // the rows of this step in hand: own row r and the upwind row (a wall row's ghost
+        // needs none)
+        wait_row(r);
+        if (up ? r > 0 : r < ny - 1) wait_row(up ? r - 1 : r + 1);
         // refill: the slot of row r - 2 (moving up) or r - 1 (moving down), read by now
         if (up) copy_row(r + 2, r + 2 <= lim);
         else copy_row(r + 3, r + 3 <= lim);
-        const float2 (*cur)[RW] = ring[r & (NS - 1)];
-        const float2 (*yrow)[RW] = ring[(up ? r - 1 : r + 1) & (NS - 1)];
+        const float2 *cur = ring[r & (NS - 1)];
+        const float2 *yrow = ring[(up ? r - 1 : r + 1) & (NS - 1)];
         if (MODE == BATCH_CORRECT) {          // issued now, used after the moment exchange
-            const int o = r * nx + (valid ? x : nx - 1);
+            const float2 *srow = reinterpret_cast<const float2 *>(sb + (long)r * trow) + lane;
 #pragma unroll
-            for (int k = 0; k < PW; ++k)
-                src[k] = valid ? make_float2(__ldg(sb + ((2 * k) * nc + o)), __ldg(sb + ((2 * k + 1) * nc + o)))
-                               : make_float2(0.f, 0.f);
+            for (int k = 0; k < PW; ++k) src[k] = valid ? __ldg(srow + k * 32) : make_float2(0.f, 0.f);
         }
         // the y ghost of a wall row: bottom for warps moving up, top for warps moving down
         const bool wrow = up ? r == 0 : r == ny - 1;
@@ -800,8 +881,7 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
         sh.mom[sub][p][g][lane] = make_float4(rx.x, rx.y, rx.z, 0.f);
         // the next row's wall sums travel with this row's moments
         if (r + 1 < y1 && (side || r + 1 == ny - 1)) {
-            cp_async_wait<1>();               // row r + 1 (moving up: the older group in flight)
-            __syncwarp();
+            wait_row(r + 1);
             wall_partials(r + 1, p);
         }
         named_barrier(bar_id, bar_n);
@@ -813,11 +893,12 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
             jx += u.y;
             jy += u.z;
         }
-        if (resid) relax(true, cur, rho, jx, jy, r * nx + x);
-        else relax(false, cur, rho, jx, jy, r * nx + x);
+        if (resid) relax(true, cur, rho, jx, jy, r);
+        else relax(false, cur, rho, jx, jy, r);
         if (r + 1 < y1) read_walls(r + 1, p);
     }
-    cp_async_wait<0>();
+    // every fill of the item has been waited for; none is left pending
+    for (int sl = 0; sl < NS; ++sl) wait_slot(sl);
     __syncwarp();
     if (resid) {
         double dd = (double)psd + (double)psd_c, dn = (double)psn + (double)psn_c;
@@ -833,6 +914,43 @@ __device__ __forceinline__ void march_item(const BatchArgs &a, const MarchItem *
     }
 }
 
+// The residual of instance i after step s (its sums complete): store it, check it is finite,
+// and freeze the instance once below tol -- or, with tol > 0 in the march, once it has not
+// improved by 1 % over 20 checks (the FP32 rounding floor); clear the sums for the next check.
+template <int MODE>
+__device__ void residual_decision(const BatchArgs &a, int i, long s)
+{
+    if (a.frozen[i] <= s) return;
+    const double sd = a.acc[2 * i];
+    // the correction's change is measured against the state it corrects
+    const double sn = MODE == BATCH_CORRECT ? a.ref_n2[i] : a.acc[2 * i + 1];
+    const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
+    a.last_r[i] = r;
+    if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
+    if (r < a.tol) {
+        a.frozen[i] = s + 1;
+    } else if (a.best_r && a.tol > 0) {
+        if (r < 0.99 * a.best_r[i]) {
+            a.best_r[i] = r;
+            a.flat[i] = 0;
+        } else if (++a.flat[i] >= 20) {
+            a.frozen[i] = s + 1;
+        }
+    }
+    a.acc[2 * i] = 0.0;
+    a.acc[2 * i + 1] = 0.0;
+}
+
+// Items of all the launch's steps form one sequence, step-major (item k of step si is number
+// si * nmitems + k), handed out one at a time to the warp groups by a counter.  An item of
+// step si > 0 first waits (bounded) until its instance has completed step si - 1 -- its reads
+// of the old state and its writes of the new one then cannot overlap another step of the same
+// instance -- so instances move through the steps independently and no grid-wide barrier is
+// needed: a group that finishes early starts on the next step of the instances that are done.
+// Every item waits only for items numbered before it, which groups resident in this
+// cooperative launch are running, so the launch always progresses.  The group that finishes
+// the last item of an instance's step evaluates its residual on residual steps (freezing it
+// when converged) and then publishes the completed step.
 template <int M, int G, int MODE>
 __global__ void __launch_bounds__(256, G == M ? 3 : 2) batch_march_kernel(const BatchArgs a)
 {
@@ -842,65 +960,75 @@ __global__ void __launch_bounds__(256, G == M ? 3 : 2) batch_march_kernel(const 
     Sh &sh = *reinterpret_cast<Sh *>(march_smem);
     __shared__ int s_item[SUB][2];            // fetched item of each warp group, double-buffered
     const int warp = (int)(threadIdx.x >> 5), sub = warp / G;
+    const int bar_id = 1 + sub, bar_n = 32 * G;
     const bool fetcher = warp == sub * G && (threadIdx.x & 31) == 0;
-    for (int si = 0; si < a.nsteps; ++si) {
+    // each warp's ring slots: a fill completes with the bulk copy's bytes (armed by lane 0)
+    // and one arrival per halo copy (Sh::PW lanes)
+    if ((threadIdx.x & 31) == 0) {
+        for (int sl = 0; sl < Sh::NS; ++sl)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(&sh.bar[warp][sl])),
+                         "r"((unsigned)(1 + Sh::PW)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    RingState rs;
+    const long total = (long)a.nsteps * a.nmitems;
+    for (int k = 0;; ++k) {
+        if (fetcher) s_item[sub][k & 1] = (int)atomicAdd(a.mcount, 1u);
+        named_barrier(bar_id, bar_n);
+        const long gi = (long)(unsigned)s_item[sub][k & 1];
+        if (gi >= total) break;
+        const int si = (int)(gi / a.nmitems), item = (int)(gi - (long)si * a.nmitems);
         const long s = a.step0 + si;
+        const MarchItem *mi = a.mitems + item;
+        const int inst = __ldg(&mi->inst);
+        if (si > 0) {
+            if (fetcher) {
+                const long long t0 = clock64();
+                while (*(volatile unsigned *)(a.idone + inst) < (unsigned)si) {
+                    if (*(volatile int *)a.err != 0) break;
+                    if (clock64() - t0 > a.timeout_cycles) {
+                        atomicExch(a.err, 1);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                __threadfence();
+            }
+            named_barrier(bar_id, bar_n);
+        }
+        // the state written by other SMs, read next by the copy engine
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
         const float *h = reinterpret_cast<const float *>(a.buf[s & 1]);
         float *hn = reinterpret_cast<float *>(a.buf[(s + 1) & 1]);
         const bool resid = ((s + 1) % a.resid_every) == 0;
-        // items are taken from a counter per step parity (the next step's is cleared here:
-        // its last use ended at the previous grid barrier); each warp group takes one item
-        // at a time, so that groups on less loaded SMs take more
-        unsigned *next = a.mcount + (s & 1);
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.mcount[(s + 1) & 1] = 0u;
-        for (int k = 0;; ++k) {
-            if (fetcher) s_item[sub][k & 1] = (int)atomicAdd(next, 1u);
-            named_barrier(1 + sub, 32 * G);
-            const int item = s_item[sub][k & 1];
-            if (item >= a.nmitems) break;
-            march_item<M, G, MODE>(a, a.mitems + item, s, h, hn, resid, sh);
-        }
-        if (!grid_barrier(a)) return;
-        if (resid) {
-            if (blockIdx.x == 0) {
-                for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
-                    if (a.frozen[i] <= s || a.kind[i] != a.kind_sel) continue;
-                    const double sd = a.acc[2 * i];
-                    const double sn = MODE == BATCH_CORRECT ? a.ref_n2[i] : a.acc[2 * i + 1];
-                    const double r = sn > 0.0 ? sqrt(sd / sn) : (sd == 0.0 ? 0.0 : INFINITY);
-                    a.last_r[i] = r;
-                    if (!(r == r) || isinf(r)) atomicExch(a.err, 2);
-                    if (r < a.tol) {
-                        a.frozen[i] = s + 1;
-                    } else if (a.best_r && a.tol > 0) {
-                        // the FP32 rounding floor: no 1 % improvement over 20 checks freezes too
-                        if (r < 0.99 * a.best_r[i]) {
-                            a.best_r[i] = r;
-                            a.flat[i] = 0;
-                        } else if (++a.flat[i] >= 20) {
-                            a.frozen[i] = s + 1;
-                        }
-                    }
-                    a.acc[2 * i] = 0.0;
-                    a.acc[2 * i + 1] = 0.0;
-                }
+        march_item<M, G, MODE>(a, mi, s, h, hn, resid, sh, rs);
+        named_barrier(bar_id, bar_n);          // the group's stores and sums are issued
+        if (fetcher) {
+            __threadfence();
+            const unsigned done = atomicAdd(a.ifin + inst, 1u) + 1u;
+            if (done == (unsigned)((si + 1) * __ldg(a.iitems + inst))) {
+                if (resid) residual_decision<MODE>(a, inst, s);
+                __threadfence();
+                atomicExch(a.idone + inst, (unsigned)(si + 1));
             }
-            if (!grid_barrier(a)) return;
         }
     }
 }
 
 // six linearised moments of one instance (rho, ux, uy, pxx, pxy, pyy per cell), FP64
 template <typename T>
-__global__ void inst_moments_kernel(const T *h, long ncells, int m, const BatchArgs a, double u_ref, double *out)
+__global__ void inst_moments_kernel(const T *h, const BatchInst I, int m, const BatchArgs a, double u_ref, double *out)
 {
+    const long ncells = I.ncells;
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
+        const int yc = (int)(c / I.nx), xc = (int)(c - (long)yc * I.nx);
         double s0 = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
         for (int iy = 0; iy < m; ++iy) {
             const double ey = a.xi[iy];
             for (int ix = 0; ix < m; ++ix) {
                 const double ex = a.xi[ix];
-                const double v = (double)h[(long)(iy * m + ix) * ncells + c];
+                const double v = (double)h[inst_index(I, m * m, iy * m + ix, xc, yc)];
                 s0 += v;
                 sx += ex * v;
                 sy += ey * v;
@@ -1011,6 +1139,7 @@ struct lbm_batch {
     unsigned char *d_kind;      // [count] 1: cavity instance marched by columns
     bool march;                 // cavity instances by the column-march kernel
     int nmitems, mgrid, mchunk; // march items, their co-resident grid, rows per chunk
+    std::vector<int> iitems;    // march items per instance (host copy of d_iitems)
     int mchunk_fixed;           // rows per chunk set by the caller (0: planned per rebuild)
     int mg;                     // warps per march item (0: the default shape)
     std::vector<std::pair<void *, int>> occ;   // resident blocks per SM of each kernel used
@@ -1019,6 +1148,9 @@ struct lbm_batch {
     double *d_acc, *d_last_r, *d_best;
     int *d_flat;
     long *d_frozen;
+    unsigned *d_ifin;     // [ninst] column march: items finished / steps completed in a launch
+    unsigned *d_idone;
+    int *d_iitems;        // [ninst] column-march items per step
     unsigned *d_bar;
     int *d_err;
     double *d_tab;          // 1-D nodes [LBM_MAX_M] then weights [LBM_MAX_M]
@@ -1075,6 +1207,7 @@ void inst_coeffs(const lbm_problem &p, const std::vector<double> &nodes, BatchIn
     I.nx = p.nx;
     I.ny = p.ny;
     I.cavity = p.geom == LBM_CAVITY;
+    I.tiled = I.cavity;
     I.ncells = (long)p.nx * p.ny;
 }
 
@@ -1144,10 +1277,13 @@ void build_items(const lbm_batch *b, int order, bool march, std::vector<BatchIte
     }
 }
 
-// Column-march items of the live cavity instances with chunks of about `chunk` rows:
-// chunk-major across instances (item k of every instance, then item k + 1, ...), so that
-// the static round-robin deal gives each block a mix of instances.
-void build_march_items(const lbm_batch *b, int chunk, std::vector<MarchItem> &out)
+// Column-march items of the live cavity instances with chunks of about `chunk` rows,
+// instance by instance (within an instance chunk by chunk, strips side by side, so that
+// neighbouring strips run at about the same time and their x halos are L2 hits): the items
+// of a step are taken in this order, so the first instances complete the step first, and the
+// warp groups that reach the next step find their instances ready (the kernel waits only for
+// an item's own instance).
+void build_march_items(const lbm_batch *b, double chunk, std::vector<MarchItem> &out)
 {
     out.clear();
     const int ni = (int)b->inst.size();
@@ -1156,7 +1292,7 @@ void build_march_items(const lbm_batch *b, int chunk, std::vector<MarchItem> &ou
     for (int i = 0; i < ni; ++i) {
         if (!b->live[i] || !b->inst[i].cavity) continue;
         const BatchInst &I = b->inst[i];
-        const int nch = std::max(1, (I.ny + chunk - 1) / chunk);
+        const int nch = std::max(1, (int)std::lround(I.ny / chunk));   // near-equal chunks of about `chunk` rows
         for (int k = 0; k < nch; ++k)
             for (int x0 = 0; x0 < I.nx; x0 += 32) {
                 MarchItem t;
@@ -1180,9 +1316,8 @@ void build_march_items(const lbm_batch *b, int chunk, std::vector<MarchItem> &ou
             }
         most = std::max(most, per[i].size());
     }
-    for (size_t k = 0; k < most; ++k)
-        for (int i = 0; i < ni; ++i)
-            if (k < per[i].size()) out.push_back(per[i][k]);
+    (void)most;
+    for (int i = 0; i < ni; ++i) out.insert(out.end(), per[i].begin(), per[i].end());
 }
 
 // Resident blocks per SM of a kernel of this batch (queried once per kernel) and the SM count.
@@ -1211,15 +1346,19 @@ cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks
 }
 
 // Rows per chunk of the column march: items are fetched dynamically, so the chunks only
-// have to be many enough to balance the SMs (about three per resident warp group) and long
-// enough to amortise an item's start (its first rows' copies and the wall prologue).
-int march_chunk_plan(const lbm_batch *b, long slots)
+// have to be many enough to keep the warp groups busy and long enough to amortise an item's
+// start (its first rows' copies and the wall prologue).
+double march_chunk_plan(const lbm_batch *b, long slots)
 {
     long strip_rows = 0;
     for (int i = 0; i < (int)b->inst.size(); ++i)
         if (b->live[i] && b->inst[i].cavity) strip_rows += (long)((b->inst[i].nx + 31) / 32) * b->inst[i].ny;
-    const long h = strip_rows / std::max(1L, 3 * slots);
-    return (int)std::max(4L, std::min(64L, h));
+    // about 1.7 items per warp group and step: with items taken instance by instance and each
+    // waiting only for its own instance, fewer, longer items beat a finer split (measured on
+    // 32 and 128 cavities of 128^2 and 8 of 256^2: 16, 64 and 16 rows, 0.71, 0.81, 0.68 of
+    // the copy rate); each chunk re-reads one row, so chunks stay at least 4 rows
+    const double h = (double)strip_rows / (1.7 * (double)std::max(1L, slots));
+    return std::max(4.0, std::min(128.0, h));
 }
 
 lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool march);
@@ -1251,15 +1390,22 @@ lbm_status apply_schedule_march(lbm_batch *b, int g, int bpsm, int order, bool m
             return bfail(LBM_EUNSUPPORTED, "column-march kernel does not fit on an SM");
         mb = std::min(mb, mbc);                // one grid serves the march and the correction
         const int sub = 8 / mf.g;
-        mchunk = b->mchunk_fixed > 0 ? b->mchunk_fixed : march_chunk_plan(b, (long)nsm * mb * sub);
-        build_march_items(b, mchunk, mitems);
+        const double rows = b->mchunk_fixed > 0 ? (double)b->mchunk_fixed : march_chunk_plan(b, (long)nsm * mb * sub);
+        mchunk = (int)std::lround(rows);
+        build_march_items(b, rows, mitems);
         mgrid = (int)std::min<long>((long)nsm * mb, std::max<long>(1, ((long)mitems.size() + sub - 1) / sub));
     }
     // stream-ordered uploads (pageable sources are staged before the calls return)
     e = cudaSuccess;
-    if (!mitems.empty())
+    if (!mitems.empty()) {
+        b->iitems.assign(b->inst.size(), 0);
+        for (const MarchItem &t : mitems) b->iitems[t.inst] += 1;
         e = cudaMemcpyAsync(b->d_mitems, mitems.data(), sizeof(MarchItem) * mitems.size(), cudaMemcpyHostToDevice,
                             b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_iitems, b->iitems.data(), sizeof(int) * b->iitems.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+    }
     if (e == cudaSuccess && !items.empty())
         e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                             b->stream);
@@ -1307,6 +1453,9 @@ BatchArgs make_args(const lbm_batch *b, int nsteps, double tol)
     a.bar_count = b->d_bar;
     a.bar_gen = b->d_bar + 1;
     a.mcount = b->d_bar + 8;
+    a.ifin = b->d_ifin;
+    a.idone = b->d_idone;
+    a.iitems = b->d_iitems;
     a.err = b->d_err;
     a.step0 = b->step;
     a.nsteps = nsteps;
@@ -1360,6 +1509,7 @@ cudaError_t launch_pair(lbm_batch *b, const BatchArgs &a0, void *mfn, void *sfn,
         BatchArgs a = a0;
         a.kind_sel = 1;
         e = cudaMemsetAsync(a.mcount, 0, 2 * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.ifin, 0, 2 * sizeof(unsigned) * b->inst.size(), st);
         if (e == cudaSuccess) e = launch_coop(mfn, b->mgrid, 256, a, st, march_fns(b->m, b->mg).smem);
     }
     if (e == cudaSuccess && (b->nitems > 0 || b->nwall > 0)) {
@@ -1393,7 +1543,7 @@ __global__ void batch_apply_kernel(float *h, const float *c0, const float *c1, c
                                    const long *frozen, const int *list, int nv)
 {
     const int i = list[blockIdx.y];
-    const long n = (long)nv * inst[i].ncells, off = inst[i].off;
+    const long n = inst_vals(inst[i], nv), off = inst[i].off;
     const float *c = (frozen[i] & 1) ? c1 : c0;
     for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
         h[off + k] += c[off + k];
@@ -1502,7 +1652,7 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
         if (insts[i].residual_every != insts[0].residual_every)
             return bfail(LBM_EINVAL, "all batch instances must share residual_every");
         const long nc = (long)insts[i].nx * insts[i].ny;
-        vals += (long)nv * nc;
+        vals += insts[i].geom == LBM_CAVITY ? (long)((insts[i].nx + 31) / 32) * insts[i].ny * nv * 32 : (long)nv * nc;
         segs += (nc + 31) / 32;
         if (insts[i].geom == LBM_CAVITY)     // column-march items: chunks of at least 4 rows
             mits += (long)((insts[i].nx + 31) / 32) * ((insts[i].ny + 3) / 4);
@@ -1522,6 +1672,7 @@ static lbm_status batch_layout(const lbm_vset *vs, const lbm_problem *insts, int
     off = align256(off + sizeof(double) * count);     // best residual
     off = align256(off + sizeof(int) * count);        // checks without improvement
     off = align256(off + sizeof(long) * count);
+    off = align256(off + sizeof(unsigned) * 3 * count);        // march completion counters, items per step
     off = align256(off + 64);
     off = align256(off + sizeof(double) * 2 * LBM_MAX_M);      // 1-D nodes and weights
     long maxc = 0;
@@ -1579,7 +1730,7 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     for (int i = 0; i < count; ++i) {
         inst_coeffs(insts[i], b->nodes, b->inst[i]);
         b->inst[i].off = off;
-        off += (long)nv * b->inst[i].ncells;
+        off += inst_vals(b->inst[i], nv);
     }
     b->stream = (cudaStream_t)stream;
     b->owns = device_buf == nullptr;
@@ -1630,6 +1781,10 @@ lbm_status lbm_batch_init(const lbm_vset *vs, const lbm_problem *insts, int coun
     o = align256(o + sizeof(int) * count);
     b->d_frozen = (long *)(p + o);
     o = align256(o + sizeof(long) * count);
+    b->d_ifin = (unsigned *)(p + o);
+    b->d_idone = b->d_ifin + count;
+    b->d_iitems = (int *)(b->d_ifin + 2 * count);
+    o = align256(o + sizeof(unsigned) * 3 * count);
     b->d_bar = (unsigned *)(p + o);
     b->d_err = (int *)(p + o + 16);
     o = align256(o + 64);
@@ -1939,7 +2094,7 @@ lbm_status lbm_batch_moments(lbm_batch *b, int i, double *out_dev)
     const BatchInst &I = b->inst[i];
     const int nb = (int)std::min<long>(1216, (I.ncells + 255) / 256);
     const float *h = (const float *)b->buf[steps & 1] + I.off;
-    inst_moments_kernel<float><<<nb, 256, 0, b->stream>>>(h, I.ncells, b->m, a, 1.0 / I.inv_u_ref, out_dev);
+    inst_moments_kernel<float><<<nb, 256, 0, b->stream>>>(h, I, b->m, a, 1.0 / I.inv_u_ref, out_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("instance moments: ") + cudaGetErrorString(e));
 }
@@ -1949,10 +2104,14 @@ lbm_status lbm_batch_set_state(lbm_batch *b, int i, const double *h)
     if (!b || !h) return bfail(LBM_EINVAL, "NULL argument");
     if (i < 0 || i >= (int)b->inst.size()) return bfail(LBM_EINVAL, "instance index out of range");
     if (b->step != 0) return bfail(LBM_EINVAL, "initial states can be set before the first advance only");
-    const long n = (long)b->nv * b->inst[i].ncells;
-    std::vector<float> tmp(n);
-    for (long k = 0; k < n; ++k) tmp[k] = (float)h[k];
-    cudaError_t e = cudaMemcpyAsync((float *)b->buf[0] + b->inst[i].off, tmp.data(), sizeof(float) * n,
+    const BatchInst &I = b->inst[i];
+    const long n = inst_vals(I, b->nv);
+    std::vector<float> tmp(n, 0.f);
+    for (int a = 0; a < b->nv; ++a)              // host order [n][ny][nx] into the instance's layout
+        for (int y = 0; y < I.ny; ++y)
+            for (int x = 0; x < I.nx; ++x)
+                tmp[inst_index(I, b->nv, a, x, y)] = (float)h[((long)a * I.ny + y) * I.nx + x];
+    cudaError_t e = cudaMemcpyAsync((float *)b->buf[0] + I.off, tmp.data(), sizeof(float) * n,
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("setting an instance state: ") + cudaGetErrorString(e));
@@ -1973,7 +2132,8 @@ lbm_status lbm_batch_warm_start(lbm_batch *b, int i, lbm_mlp *mlp, double kn, do
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = launch_warm_state(pred, I.nx, I.ny, I.ncells, I.nx, b->m, b->d_tab, b->d_tab + LBM_MAX_M,
-                              u_w * I.inv_u_ref, (float *)b->buf[0] + I.off, LBM_FP32_PERTURB, b->stream);
+                              u_w * I.inv_u_ref, (float *)b->buf[0] + I.off, LBM_FP32_PERTURB, b->stream,
+                              I.tiled != 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("warm start of an instance: ") + cudaGetErrorString(e));
 }
@@ -1985,21 +2145,19 @@ lbm_status lbm_batch_get_state(lbm_batch *b, int i, double *h)
     long steps;
     lbm_status st = lbm_batch_status(b, i, &steps, nullptr, nullptr);
     if (st != LBM_OK) return st;
-    const long n = (long)b->nv * b->inst[i].ncells;
+    const BatchInst &I = b->inst[i];
+    const long n = inst_vals(I, b->nv);
     const int par = (int)(steps & 1);
-    cudaError_t e;
-    if (b->prec == LBM_FP64) {
-        e = cudaMemcpyAsync(h, (double *)b->buf[par] + b->inst[i].off, sizeof(double) * n,
-                            cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    } else {
-        std::vector<float> tmp(n);
-        e = cudaMemcpyAsync(tmp.data(), (float *)b->buf[par] + b->inst[i].off, sizeof(float) * n,
-                            cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        if (e == cudaSuccess)
-            for (long k = 0; k < n; ++k) h[k] = tmp[k];
-    }
+    // batches are FP32 (lbm_batch_init refuses FP64)
+    std::vector<float> tmp(n);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), (float *)b->buf[par] + I.off, sizeof(float) * n,
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess)                         // the instance's layout into host order [n][ny][nx]
+        for (int a = 0; a < b->nv; ++a)
+            for (int y = 0; y < I.ny; ++y)
+                for (int x = 0; x < I.nx; ++x)
+                    h[((long)a * I.ny + y) * I.nx + x] = tmp[inst_index(I, b->nv, a, x, y)];
     return e == cudaSuccess ? LBM_OK : bfail(LBM_ECUDA, std::string("reading instance state: ") + cudaGetErrorString(e));
 }
 
@@ -2018,7 +2176,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         at[i] = fro[i] == LONG_MAX ? b->step : fro[i];
-        const size_t bytes = sizeof(float) * b->nv * b->inst[i].ncells;
+        const size_t bytes = sizeof(float) * inst_vals(b->inst[i], b->nv);
         e = cudaMemcpyAsync(b->r_h + b->inst[i].off, (const float *)b->buf[at[i] & 1] + b->inst[i].off, bytes,
                             cudaMemcpyDeviceToDevice, b->stream);
     }
@@ -2125,7 +2283,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
                 list.push_back(i);
                 csteps[i] += fro[i];
                 sweeps[i] += 1;
-                maxv = std::max(maxv, (long)b->nv * b->inst[i].ncells);
+                maxv = std::max(maxv, inst_vals(b->inst[i], b->nv));
             }
         e = cudaMemcpyAsync(b->r_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) {
@@ -2150,7 +2308,7 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         if (sweeps[i] > 0)
             e = cudaMemcpyAsync((float *)b->buf[at[i] & 1] + b->inst[i].off, b->r_h + b->inst[i].off,
-                                sizeof(float) * b->nv * b->inst[i].ncells, cudaMemcpyDeviceToDevice, b->stream);
+                                sizeof(float) * inst_vals(b->inst[i], b->nv), cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return restore(bfail(LBM_ECUDA, std::string("refinement: ") + cudaGetErrorString(e)));
     if (info)

@@ -135,7 +135,8 @@ cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t
 
 // warm start (mlp.cu): h from normalised predicted moments [ncells][6]
 cudaError_t launch_warm_state(const float *pred, int nx, int ny, long pa, long py, int m, const double *xi1,
-                              const double *w1, double uw_over_uref, void *h, int prec, cudaStream_t s);
+                              const double *w1, double uw_over_uref, void *h, int prec, cudaStream_t s,
+                              bool tiled32 = false);
 
 // Host quadrature (quadrature.cpp)
 bool lbm_rule_1d(int kind, int n, std::vector<double> &nodes, std::vector<double> &weights);

@@ -184,12 +184,17 @@ __global__ void features_kernel(int nx, int ny, float f2, float f3, float *x)
 
 // second-order Hermite reconstruction from normalised predicted moments
 // pred[c][0..5] = ((rho-1)/u_w, u_x/u_w, u_y/u_w, (P_xx-1)/u_w, P_xy/u_w, (P_yy-1)/u_w)
+// (tiled32: the strip-tiled layout of batch cavities, 32-column tiles with velocity pairs side
+// by side per cell; pa, py unused then)
 template <typename T>
 __global__ void warm_state_kernel(const float *pred, int nx, long ncells, long pa, long py, int m, const double *xi1,
-                                  const double *w1, double uw_over_uref, T *h)
+                                  const double *w1, double uw_over_uref, T *h, bool tiled32)
 {
+    const int ny = (int)(ncells / nx);
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
-        const long y = c / nx, co = y * py + (c - y * nx);
+        const long y = c / nx, co = tiled32 ? (long)((c - y * nx) >> 5) * (32L * m * m * ny) + y * (32L * m * m) +
+                                                  ((c - y * nx) & 31) * 2
+                                            : y * py + (c - y * nx);
         const double s = uw_over_uref;
         const double rp = s * pred[c * 6 + 0];
         const double jx = s * pred[c * 6 + 1];   // rho u / u_ref, linearised rho = 1
@@ -202,7 +207,8 @@ __global__ void warm_state_kernel(const float *pred, int nx, long ncells, long p
                 const double v = w1[ix] * w1[iy] *
                                  (rp + ex * jx + ey * jy +
                                   0.5 * ((pxx - rp) * (ex * ex - 1.0) + 2.0 * pxy * ex * ey + (pyy - rp) * (ey * ey - 1.0)));
-                h[(long)(iy * m + ix) * pa + co] = (T)v;
+                const int aa = iy * m + ix;
+                h[(tiled32 ? (long)(aa >> 1) * 64 + (aa & 1) : (long)aa * pa) + co] = (T)v;
             }
         }
     }
@@ -560,13 +566,15 @@ lbm_status lbm_mlp_features(lbm_mlp *p, int nx, int ny, double kn, double u_w, f
 }  // extern "C"
 
 cudaError_t launch_warm_state(const float *pred, int nx, int ny, long pa, long py, int m, const double *xi1,
-                              const double *w1, double uw_over_uref, void *h, int prec, cudaStream_t s)
+                              const double *w1, double uw_over_uref, void *h, int prec, cudaStream_t s, bool tiled32)
 {
     const long ncells = (long)nx * ny;
     const int nb = blocks_for(ncells);
     if (prec == LBM_FP64)
-        warm_state_kernel<double><<<nb, 256, 0, s>>>(pred, nx, ncells, pa, py, m, xi1, w1, uw_over_uref, (double *)h);
+        warm_state_kernel<double><<<nb, 256, 0, s>>>(pred, nx, ncells, pa, py, m, xi1, w1, uw_over_uref, (double *)h,
+                                                     tiled32);
     else
-        warm_state_kernel<float><<<nb, 256, 0, s>>>(pred, nx, ncells, pa, py, m, xi1, w1, uw_over_uref, (float *)h);
+        warm_state_kernel<float><<<nb, 256, 0, s>>>(pred, nx, ncells, pa, py, m, xi1, w1, uw_over_uref, (float *)h,
+                                                    tiled32);
     return cudaGetLastError();
 }

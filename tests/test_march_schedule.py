@@ -239,3 +239,68 @@ def test_tiled_march_copies(nx, ny, m, g):
                     # inside the warp's slot (dense lines, then 4 floats per velocity), one each
                     assert nvw * TILE_W <= dst < nvw * (TILE_W + 4) and dst not in dsts
                     dsts.add(dst)
+
+
+# ---- batched column march on strip-tiled cavity instances: 32-column tiles, velocity pairs
+# side by side per cell: value (a, x, y) at (x/32) tp + 32 n y + 64 (a/2) + 2 (x mod 32) + a mod 2
+
+def batch_tile_index(a, x, y, n, ny):
+    return (x >> 5) * (32 * n * ny) + y * 32 * n + (a >> 1) * 64 + (x & 31) * 2 + (a & 1)
+
+
+def batch_tiled_cell(off, n, ny):
+    """(a, x, y) stored at offset `off` of a tiled instance (x may lie in the last tile's padding)."""
+    t, rem = divmod(off, 32 * n * ny)
+    y, rem = divmod(rem, 32 * n)
+    pair, rem = divmod(rem, 64)
+    xc, odd = divmod(rem, 2)
+    return 2 * pair + odd, 32 * t + xc, y
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 2), (64, 5), (70, 9), (96, 4), (97, 6), (128, 3)])
+@pytest.mark.parametrize("m,g", [(8, 4), (8, 8), (4, 2), (4, 4)])
+def test_batch_tiled_march_copies(nx, ny, m, g):
+    """The batched column march's row copies on a strip-tiled cavity instance (the kernel's own
+    arithmetic): the bulk copy of a warp's velocity pairs of a row starts 16-byte aligned inside
+    the instance and covers exactly those pairs of the strip's 32 columns (padding past nx in a
+    ragged last tile); each 8-byte halo copy takes, for a pair moving right, the cell left of
+    the strip, for a pair moving left the cell right of it, both inside the instance; at a side
+    wall it takes a cell of the strip itself (the wall lane uses the ghost instead)."""
+    n = m * m
+    rpl, half_pairs, p_row = m // g, m // 4, m // 2
+    pw = rpl * m // 2
+    ntiles = (nx + 31) // 32
+    vals = ntiles * ny * n * 32
+    tp, trow = 32 * n * ny, 32 * n
+    # every (a, x, y) of the grid has its own place; the rest is padding
+    places = {batch_tile_index(a, x, y, n, ny) for a in range(n) for x in range(nx) for y in range(ny)}
+    assert len(places) == n * nx * ny and max(places) < vals
+    off = 16 * 37                                   # an instance offset as the batch lays them out
+    assert off % 16 == 0
+    for tile in range(ntiles):
+        x0 = 32 * tile
+        for w in range(g):
+            iy0 = w * rpl
+            wbase = off + tile * tp + (iy0 * m // 2) * 64
+            for r in range(ny):
+                src = wbase + r * trow
+                assert src % 4 == 0 and off <= src and src + pw * 64 <= off + vals
+                for k in range(pw * 64):
+                    a, x, y = batch_tiled_cell(src - off + k, n, ny)
+                    assert y == r and x0 <= x < x0 + 32 and a // 2 == iy0 * m // 2 + k // 64
+                for hq in range(pw):
+                    j = hq % p_row
+                    if j >= half_pairs:
+                        halo = -tp + 62 if tile > 0 else 0
+                        want = x0 - 1 if tile > 0 else None
+                    else:
+                        halo = tp if tile + 1 < ntiles else 0
+                        want = x0 + 32 if tile + 1 < ntiles else None
+                    h = wbase + hq * 64 + halo + r * trow
+                    assert h % 2 == 0 and off <= h and h + 2 <= off + vals
+                    a, x, y = batch_tiled_cell(h - off, n, ny)
+                    assert y == r and a == 2 * (iy0 * m // 2 + hq)
+                    if want is not None:
+                        assert x == want and 0 <= x < nx
+                    else:
+                        assert x0 <= x < x0 + 32
