@@ -317,24 +317,27 @@ lbm_status lbm_batch_set_schedule(lbm_batch *b, int warps_per_segment, int block
 lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, int *blocks_per_sm,
                                   int *order, int *grid);
 /* Column march of cavity instances (on by default where the velocity set has 4 or 8 nodes
- * per axis): cavity instances are advanced by a second persistent kernel in which a block
- * of eight warps marches a 32-column strip up a chunk of rows, one warp per velocity row,
- * keeping the upwind rows in registers (each value read once per step) and forming the
- * wall densities inline; Couette instances always take the segment kernel.  on = 0 puts
- * every instance on the segment kernel (same results up to FP32 summation order).
- * The warp groups take items from a per-step counter (dynamic balance across SMs).
- * rows_per_chunk: rows of one march item (>= 4), or 0 to let the library plan it at every
- * rebuild of the item lists (about three items per resident warp group, 4 to 64 rows).
- * warps_per_item: M (one velocity row per warp), M / 2 (two rows per warp, two items per
- * block; the default, 0) .  lbm_batch_get_march reports the switch, the rows per chunk
- * in use, the number of march items, the march kernel's grid and its warps per item
- * (outputs may be NULL). */
+ * per axis): cavity instances are advanced by a second persistent kernel in which a group
+ * of warps marches a 32-column strip up a chunk of rows, each warp owning one or two
+ * velocity rows, streaming the rows through a shared-memory ring (each value read once per
+ * step) and forming the wall densities inline; Couette instances always take the segment
+ * kernel.  on = 0 puts every instance on the segment kernel (same results up to FP32
+ * summation order).  Cavity states are stored strip-tiled (32-cell strips, velocity pairs
+ * interleaved; host transfers keep the planar order).  The warp groups take items of all
+ * the launch's steps from one counter, and an item waits only for its own instance's
+ * previous step (no grid-wide barrier between steps).  rows_per_chunk: rows of one march
+ * item (>= 4), or 0 to let the library plan it at every rebuild of the item lists (about
+ * 1.7 items per resident warp group and step, 4 to 128 rows).  warps_per_item: M (one
+ * velocity row per warp), M / 2 (two rows per warp, two items per block; the default, 0).
+ * lbm_batch_get_march reports the switch, the rows per chunk in use, the number of march
+ * items per step, the march kernel's grid and its warps per item (outputs may be NULL). */
 lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk, int warps_per_item);
 lbm_status lbm_batch_get_march(const lbm_batch *b, int *on, int *rows_per_chunk, int *items, int *grid,
                                int *warps_per_item);
 lbm_status lbm_batch_advance(lbm_batch *b, int nsteps, double tol);     /* asynchronous */
-/* Limit of every bounded wait in the grid barrier, in SM clock cycles (default 4e9, about
- * 2 s).  Exposed so that tests can make a wait give up and check the error path. */
+/* Limit of every bounded wait (the segment kernel's grid barrier, the column march's wait
+ * for an instance's previous step and for its row copies), in SM clock cycles (default 4e9,
+ * about 2 s).  Exposed so that tests can make a wait give up and check the error path. */
 lbm_status lbm_batch_set_timeout(lbm_batch *b, long long cycles);
 lbm_status lbm_batch_poll(lbm_batch *b, int *n_active, long *step);     /* synchronises */
 /* Back to the cold start (h = 0 everywhere, step 0, nothing converged). */

@@ -1288,7 +1288,6 @@ void build_march_items(const lbm_batch *b, double chunk, std::vector<MarchItem> 
     out.clear();
     const int ni = (int)b->inst.size();
     std::vector<std::vector<MarchItem>> per(ni);
-    size_t most = 0;
     for (int i = 0; i < ni; ++i) {
         if (!b->live[i] || !b->inst[i].cavity) continue;
         const BatchInst &I = b->inst[i];
@@ -1314,9 +1313,7 @@ void build_march_items(const lbm_batch *b, double chunk, std::vector<MarchItem> 
                 t.drive_top = (float)(I.u_top * I.inv_u_ref);
                 per[i].push_back(t);
             }
-        most = std::max(most, per[i].size());
     }
-    (void)most;
     for (int i = 0; i < ni; ++i) out.insert(out.end(), per[i].begin(), per[i].end());
 }
 
