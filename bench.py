@@ -196,7 +196,7 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic_record(kernel_key: str):
+def _traffic_record(kernel_key: str, order: int = 1):
     """ncu DRAM bytes per launch for the kernel, if captured for the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -205,7 +205,10 @@ def _traffic_record(kernel_key: str):
     if not rec:
         return None
     h = hashlib.sha256()
-    for name in ("step_kernel.cuh", "step_tma.cuh", "step_march.cuh"):
+    names = ("step_kernel.cuh", "step_tma.cuh", "step_march.cuh")
+    if order == 2:
+        names += ("step_so.cuh", "step_so_march.cu")
+    for name in names:
         h.update(open(os.path.join(ROOT, "paper_1308_0692_gb300", "csrc", name), "rb").read())
     digest = h.hexdigest()[:16]
     if rec.get("source_sha256_16") != digest:
@@ -219,21 +222,27 @@ LOAD_PATHS = ["registers", "prefetch", "tma", "tma+walls merged", "column march 
               "column march (4 row slots, relaxation deferred by one row)",
               "column march on the strip-tiled state (4 row slots)",
               "column march on the strip-tiled state (4 row slots, bulk asynchronous stores)"]
+# second-order transport (lbm_set_transport(sim, 2)): the segment kernel, and the second-order
+# column march on the strip-tiled state
+VARIANTS_SO = [(4, 0), (6, 8), (6, 9)]
+LOAD_PATHS_SO = {0: "second-order segment kernel (registers)",
+                 8: "second-order column march on the strip-tiled state (5 row slots)",
+                 9: "second-order column march on the strip-tiled state (4 row slots, bulk asynchronous stores)"}
 
 
-def choose_variant(sim, stream, args):
+def choose_variant(sim, stream, args, variants=None):
     """Autotune the step kernel on the workload itself: warps per segment x load path
-    (0 registers, 2 TMA-staged halo, 3 the same with the walls in one launch, 4 to 7 the
+    (0 registers, 2 TMA-staged halo, 3 the same with the walls in one launch, 4 to 9 the
     TMA column march), a few timed steps each; or the forced --variant."""
     import torch
 
     from paper_1308_0692_gb300 import lbm
-    if args.variant:
+    if args is not None and args.variant:
         g, pf = (int(v) for v in args.variant.split(","))
         lbm.lbm_set_variant(sim, g, pf)
         return (g, pf), None
     times = {}
-    for g, pf in VARIANTS:
+    for g, pf in (variants or VARIANTS):
         try:
             lbm.lbm_set_variant(sim, g, pf)
         except lbm.LBMError:
@@ -270,9 +279,14 @@ def run_own(args, dist: Dist):
     stream = torch.cuda.Stream()
     buf = torch.empty(lbm.lbm_sim_bytes(vs, prob), dtype=torch.uint8, device="cuda")
     sim = lbm.lbm_init(vs, prob, None, device_buf=buf, stream=stream)
+    order = args.transport
+    if order == 2:
+        lbm.lbm_set_transport(sim, 2)
+        lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG_EXACT)
     ncells = w["nx"] * w["ny"]
     units_per_step = ncells * n_vel
-    variant, tuning = choose_variant(sim, stream, args)
+    variant, tuning = choose_variant(sim, stream, args, VARIANTS_SO if order == 2 else VARIANTS)
+    load_path = LOAD_PATHS_SO[variant[1]] if order == 2 else LOAD_PATHS[variant[1]]
 
     def timed_block(K):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -324,20 +338,23 @@ def run_own(args, dist: Dist):
         "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"lid-driven cavity {w['nx']}x{w['ny']}, D2Q^h_144 (N=6 half-range Gauss-Hermite), "
-                               "Kn=0.05, lid u=0.01, FP32 perturbation storage, FP64 residual every 10 steps",
+                               "Kn=0.05, lid u=0.01, FP32 perturbation storage, FP64 residual every 10 steps"
+                               + ("; second-order transport (Beam-Warming face fluxes), symmetric splitting "
+                                  "with exact relaxation" if order == 2 else ""),
                    "nx": w["nx"], "ny": w["ny"], "velocities": n_vel, "unknowns": units_per_step,
                    "residual_every": w["residual_every"], "cold_start": True,
-                   "variant": {"warps_per_segment": variant[0], "load_path": LOAD_PATHS[variant[1]],
+                   "variant": {"warps_per_segment": variant[0], "load_path": load_path,
                                "autotune_ms_per_step": tuning},
                    "l2": f"inputs larger than L2 ({units_per_step * 4 / 1e9:.2f} GB per state copy), no flush",
                    "parallelism": f"replicas{dist.world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                      "kernel": f"fused step (interior + wall launches), {variant[0]} warps/segment, "
-                               f"{LOAD_PATHS[variant[1]]} loads",
+                               f"{load_path} loads",
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": avg * 1e3,
-                     "traffic": _traffic_record(f"step_f32_m12_g{variant[0]}_pf{variant[1]}")},
+                     "traffic": _traffic_record(f"step_f32_m12_g{variant[0]}_pf{variant[1]}"
+                                                + ("_so" if order == 2 else ""), order)},
         "residual_step_ms": (sum(resid) / len(resid) * 1e3) if resid else None,
         "last_residual": [r, rstep],
         "gpu_launches": launches,
@@ -345,9 +362,14 @@ def run_own(args, dist: Dist):
     }
     if not args.no_e2e:
         out["e2e"] = run_e2e(sim, prob, n_vel, ncells, stream, dist, args)
-    if not args.no_extras and dist.world == 1:
+    if not args.no_extras and dist.world == 1 and order == 1:
         out["fp64"] = run_fp64_same_workload(vs, dist)
+        sim.close()
+        del buf
+        torch.cuda.empty_cache()
+        out["second_order"] = run_second_order_same_workload(vs, dist)
         out["time_to_residual"] = run_time_to_residual(dist)
+        return out
     sim.close()
     del buf
     return out
@@ -438,6 +460,54 @@ def run_fp64_same_workload(vs, dist):
             "fp64_pipe": {"bound": "alu", "measured_fp64_ops_per_s": fma_rate, "ops_per_update": ops,
                           "achieved_fp64_ops_per_s": units / sec * ops, "frac": units / sec * ops / fma_rate},
             "note": "FP64 storage+arithmetic; bounded by the FP64 pipe of GB300, not HBM"}
+
+
+def run_second_order_same_workload(vs, dist, steps: int = 20):
+    """The second-order variant of the same workload (Beam-Warming face fluxes, symmetric
+    splitting with exact relaxation): the FP32 step through each of its kernel variants (the
+    fastest reported with its HBM roofline at 8 B per update) and the FP64 step."""
+    import torch
+
+    from paper_1308_0692_gb300 import lbm
+    w = WORKLOAD
+    units = w["nx"] * w["ny"] * (2 * w["n_half"]) ** 2
+    peak, peak_kind = _peaks()
+    res = {}
+    for prec in (lbm.LBM_FP32_PERTURB, lbm.LBM_FP64):
+        prob = lbm.make_problem(w["geom"], w["nx"], w["ny"], w["kn"], w["u_bottom"], w["u_top"], w["cfl"], prec,
+                                w["residual_every"])
+        stream = torch.cuda.Stream()
+        sim = lbm.lbm_init(vs, prob, None, stream=stream)
+        lbm.lbm_set_transport(sim, 2)
+        lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG_EXACT)
+        if prec == lbm.LBM_FP32_PERTURB:
+            variant, tuning = choose_variant(sim, stream, None, VARIANTS_SO)
+        else:
+            variant, tuning = lbm.lbm_get_variant(sim), None
+        lbm.lbm_step(sim, 3)
+        torch.cuda.synchronize()
+        K = steps if prec == lbm.LBM_FP32_PERTURB else 5
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        lbm.lbm_step(sim, K)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        sec = t0.elapsed_time(t1) / 1e3 / K
+        sim.close()
+        if prec == lbm.LBM_FP32_PERTURB:
+            achieved = 8 * units / sec / 1e9
+            res["fp32"] = {"value": units / sec, "unit": UNIT, "steps": K, "ms_per_step": sec * 1e3,
+                           "variant": {"warps_per_segment": variant[0], "load_path": LOAD_PATHS_SO[variant[1]],
+                                       "autotune_ms_per_step": tuning},
+                           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                        "frac": achieved / peak,
+                                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                                        "basis": "8 B per update (one FP32 read and write of every value), "
+                                                 "residual steps included"}}
+        else:
+            res["fp64"] = {"value": units / sec, "unit": UNIT, "steps": K, "ms_per_step": sec * 1e3,
+                           "note": "FP64 storage+arithmetic, second-order segment kernel; FP64-pipe bound"}
+    return res
 
 
 # FP64 pipe instructions (lane operations) per node-velocity update of the FP64 step, from the
@@ -754,6 +824,8 @@ def main(argv=None):
     ap.add_argument("--variant", default=None, help="force the step kernel variant 'warps,loadpath'")
     ap.add_argument("--nx", type=int, default=None,
                     help="side of the cavity (default 2048); smaller sides are for profiling only")
+    ap.add_argument("--transport", type=int, choices=[1, 2], default=1,
+                    help="2: time the second-order variant of the workload instead (profiling)")
     ap.add_argument("--fp64-only", action="store_true",
                     help="time only the plain FP64 march of the workload (profiling of the FP64 step)")
     args = ap.parse_args(argv)

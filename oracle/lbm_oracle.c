@@ -355,41 +355,75 @@ static double axis_get(const void *v, int k)
     return q->axis == 0 ? hat(q->p, q->h, q->a, pos, q->y) : hat(q->p, q->h, q->a, q->x, pos);
 }
 
-void orc_transport2(const orc_problem *p, const orc_coeffs *c, const double *h, double *out)
+/* Second-order transport of every velocity at one cell: out[a * ostride], a < n. */
+static void transport2_cell(const orc_problem *p, const orc_coeffs *c, const double *h, long cell, double *out,
+                            long ostride)
 {
     const int n = p->n, nx = p->nx, ny = p->ny;
     const long ncells = (long)nx * ny;
     const int cavity = p->geom == ORC_CAVITY;
     const int xmove = !(p->geom == ORC_COUETTE && nx == 1);
+    const int x = (int)(cell % nx), y = (int)(cell / nx);
+    double rho_b = 0, rho_t = 0, rho_l = 0, rho_r = 0;
+    if (y == 0) rho_b = wall_density2(p, c, h, x, y, FACE_BOTTOM);
+    if (y == ny - 1) rho_t = wall_density2(p, c, h, x, y, FACE_TOP);
+    if (cavity && x == 0) rho_l = wall_density2(p, c, h, x, y, FACE_LEFT);
+    if (cavity && x == nx - 1) rho_r = wall_density2(p, c, h, x, y, FACE_RIGHT);
+    for (int a = 0; a < n; ++a) {
+        double v = h[(long)a * ncells + cell];
+        axis_ctx q = {p, h, a, x, y, 0, 1};
+        if (xmove && p->xi_x[a] != 0) {
+            const double nu = fabs(p->xi_x[a]) * c->dt / c->dx;
+            q.axis = 0;
+            q.dir = p->xi_x[a] > 0 ? 1 : -1;
+            const int i = q.dir > 0 ? x : nx - 1 - x;
+            const double g = cavity ? (q.dir > 0 ? ghost(p, c, FACE_LEFT, a, rho_l) : ghost(p, c, FACE_RIGHT, a, rho_r))
+                                    : 0.0;
+            v -= flux_difference(nu, i, nx, !cavity, g, axis_get, &q);
+        }
+        if (p->xi_y[a] != 0) {
+            const double nu = fabs(p->xi_y[a]) * c->dt / c->dy;
+            q.axis = 1;
+            q.dir = p->xi_y[a] > 0 ? 1 : -1;
+            const int i = q.dir > 0 ? y : ny - 1 - y;
+            const double g = q.dir > 0 ? ghost(p, c, FACE_BOTTOM, a, rho_b) : ghost(p, c, FACE_TOP, a, rho_t);
+            v -= flux_difference(nu, i, ny, 0, g, axis_get, &q);
+        }
+        out[(long)a * ostride] = v;
+    }
+}
+
+void orc_transport2(const orc_problem *p, const orc_coeffs *c, const double *h, double *out)
+{
+    const long ncells = (long)p->nx * p->ny;
 #pragma omp parallel for schedule(static)
-    for (long cell = 0; cell < ncells; ++cell) {
-        const int x = (int)(cell % nx), y = (int)(cell / nx);
-        double rho_b = 0, rho_t = 0, rho_l = 0, rho_r = 0;
-        if (y == 0) rho_b = wall_density2(p, c, h, x, y, FACE_BOTTOM);
-        if (y == ny - 1) rho_t = wall_density2(p, c, h, x, y, FACE_TOP);
-        if (cavity && x == 0) rho_l = wall_density2(p, c, h, x, y, FACE_LEFT);
-        if (cavity && x == nx - 1) rho_r = wall_density2(p, c, h, x, y, FACE_RIGHT);
+    for (long cell = 0; cell < ncells; ++cell) transport2_cell(p, c, h, cell, out + cell, ncells);
+}
+
+/*
+ * One step of the second-order variant in its stored-state form at selected cells only:
+ * the second-order transport, then the exact relaxation over dt,
+ * out = E + exp(-omega) (h* - E), E_a = w_a (rho' + xi_a . j') of h* -- the step that the
+ * symmetric splitting with exact half relaxations takes on the half-relaxed state (as
+ * orc_transport2 followed by orc_relax_exp with frac = 1).  out[k * n + a] for cells[k].
+ */
+void orc_step2_cells(const orc_problem *p, const orc_coeffs *c, const double *h, const long *cells,
+                     long ncell_list, double *out)
+{
+    const int n = p->n;
+    const double decay = exp(-c->omega);
+    for (long k = 0; k < ncell_list; ++k) {
+        double *o = out + k * n;
+        transport2_cell(p, c, h, cells[k], o, 1);
+        double rho = 0, jx = 0, jy = 0;
         for (int a = 0; a < n; ++a) {
-            double v = h[(long)a * ncells + cell];
-            axis_ctx q = {p, h, a, x, y, 0, 1};
-            if (xmove && p->xi_x[a] != 0) {
-                const double nu = fabs(p->xi_x[a]) * c->dt / c->dx;
-                q.axis = 0;
-                q.dir = p->xi_x[a] > 0 ? 1 : -1;
-                const int i = q.dir > 0 ? x : nx - 1 - x;
-                const double g = cavity ? (q.dir > 0 ? ghost(p, c, FACE_LEFT, a, rho_l) : ghost(p, c, FACE_RIGHT, a, rho_r))
-                                        : 0.0;
-                v -= flux_difference(nu, i, nx, !cavity, g, axis_get, &q);
-            }
-            if (p->xi_y[a] != 0) {
-                const double nu = fabs(p->xi_y[a]) * c->dt / c->dy;
-                q.axis = 1;
-                q.dir = p->xi_y[a] > 0 ? 1 : -1;
-                const int i = q.dir > 0 ? y : ny - 1 - y;
-                const double g = q.dir > 0 ? ghost(p, c, FACE_BOTTOM, a, rho_b) : ghost(p, c, FACE_TOP, a, rho_t);
-                v -= flux_difference(nu, i, ny, 0, g, axis_get, &q);
-            }
-            out[(long)a * ncells + cell] = v;
+            rho += o[a];
+            jx += p->xi_x[a] * o[a];
+            jy += p->xi_y[a] * o[a];
+        }
+        for (int a = 0; a < n; ++a) {
+            const double heq = p->w[a] * (rho + p->xi_x[a] * jx + p->xi_y[a] * jy);
+            o[a] = heq + decay * (o[a] - heq);
         }
     }
 }

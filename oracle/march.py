@@ -74,6 +74,8 @@ def _load():
         lib.orc_face_flux2_x.restype = None
         lib.orc_step_cells.argtypes = [P, C, dp, lp, ctypes.c_long, dp]
         lib.orc_step_cells.restype = None
+        lib.orc_step2_cells.argtypes = [P, C, dp, lp, ctypes.c_long, dp]
+        lib.orc_step2_cells.restype = None
         lib.orc_residual.argtypes = [dp, dp, ctypes.c_long, dp, dp]
         lib.orc_residual.restype = ctypes.c_double
         lib.orc_march.argtypes = [P, C, dp, ctypes.c_long, ctypes.c_long, ctypes.c_double, dp]
@@ -210,6 +212,17 @@ class Problem:
         _load().orc_step_cells(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h),
                                cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
                                len(cells), _dp(out))
+        return out
+
+    def step2_cells(self, h: np.ndarray, cells) -> np.ndarray:
+        """One step of the second-order variant in stored-state form (second-order transport,
+        then the exact relaxation over dt) at the listed cells only: array (len(cells), n)."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.empty((len(cells), self.n), dtype=np.float64)
+        _load().orc_step2_cells(ctypes.byref(self._p), ctypes.byref(self._c), _dp(h),
+                                cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                len(cells), _dp(out))
         return out
 
     def march(self, h: np.ndarray, max_steps: int, every: int = 100, tol: float = 0.0):

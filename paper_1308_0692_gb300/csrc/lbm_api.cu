@@ -29,6 +29,14 @@ cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, int tiled
                                   cudaStream_t s);
 cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int tiled, int *grid);
 cudaError_t launch_step_so(int prec, int m, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_f32_so_march(int m, int g, int slots, int tiled, bool resid, const StepArgs &a, int grid,
+                                     cudaStream_t s);
+cudaError_t prepare_step_f32_so_march(int m, int g, int slots, int tiled, int *grid);
+bool so_march_supported(int m, int g, int slots, int tiled);
+// second-order transport on the strip-tiled state: load path 8 a ring of five row slots with
+// direct stores, 9 a ring of four with bulk asynchronous stores (step_so_march.cu)
+static int so_march_slots(int pf) { return pf == 8 ? 5 : 4; }
+static int so_march_tiled(int pf) { return pf == 8 ? 1 : 2; }
 bool march_supported(int m, int g, int slots, bool defer, int tiled);
 int defect_lanes(int m);
 int correct_lanes(int m);
@@ -359,6 +367,15 @@ void fill_args(lbm_sim *s, const TableHeader &hdr)
         a.nux_f[i] = (float)a.nux[i];
         a.nuy_f[i] = (float)a.nuy[i];
         a.w1_f[i] = (float)a.w1[i];
+        for (int ax = 0; ax < 2; ++ax) {
+            const double nu = ax == 0 ? a.nux[i] : a.nuy[i];
+            a.so_p[ax][i] = 0.5 * nu * (3.0 - nu);
+            a.so_b[ax][i] = nu * (2.0 - nu);
+            a.so_c[ax][i] = 0.5 * nu * (1.0 - nu);
+            a.so_p_f[ax][i] = (float)a.so_p[ax][i];
+            a.so_b_f[ax][i] = (float)a.so_b[ax][i];
+            a.so_c_f[ax][i] = (float)a.so_c[ax][i];
+        }
     }
     a.omega = s->omega;
     a.b = 1.0 - s->omega;
@@ -396,8 +413,13 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur, cudaStrea
         const bool resid = idx % s->prob.residual_every == 0;
         a.h = s->buf[cur];
         a.hn = s->buf[cur ^ 1];
-        cudaError_t e = s->order == 2 ? launch_step_so(s->prob.prec, s->vs.m, resid, a, s->grid, st)
-                                      : launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, st);
+        cudaError_t e;
+        if (s->order == 2)
+            e = s->prefetch >= 8 ? launch_step_f32_so_march(s->vs.m, s->lanes, so_march_slots(s->prefetch),
+                                                            so_march_tiled(s->prefetch), resid, a, s->grid, st)
+                                 : launch_step_so(s->prob.prec, s->vs.m, resid, a, s->grid, st);
+        else
+            e = launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, st);
         if (e != cudaSuccess) return e;
         if (resid) {
             e = launch_finalize_residual(s->partials, s->nparts_step, s->result, st);
@@ -454,12 +476,18 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     };
     // wall cells in ascending order: bottom row, the side cells of each inner row (cavity),
     // top row
-    for (int x = 0; x < nx; ++x) add(x);
-    for (int y = 1; y < ny - 1 && cav; ++y) {
+    // (the second-order march leaves rows 1 and ny - 2 to the wall kernel as well: their
+    // face fluxes reach a wall)
+    const bool rows2 = s->order == 2 && s->prefetch >= 8;
+    const int whole = rows2 ? 2 : 1;   // whole rows at each end
+    for (int y = 0; y < whole; ++y)
+        for (int x = 0; x < nx; ++x) add((long)y * nx + x);
+    for (int y = whole; y < ny - whole && cav; ++y) {
         add((long)y * nx);
         add((long)y * nx + nx - 1);
     }
-    for (int x = 0; x < nx; ++x) add((long)(ny - 1) * nx + x);
+    for (int y = ny - whole; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) add((long)y * nx + x);
     if ((int)segs.size() > s->wall_cap) return fail(LBM_EINVAL, "internal: wall segment list overflow");
     cudaError_t e = cudaMemcpyAsync(s->wall_segs, segs.data(), sizeof(int) * segs.size(),
                                     cudaMemcpyHostToDevice, s->stream);
@@ -475,7 +503,8 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     s->args.merged = (long)segs.size() * 10 > nseg_total ? 1 : 0;
     if (s->prefetch >= 4) {
         int strips = 0, chunks = 0;
-        lbm_march_plan(nx, ny, s->march_grid, &strips, &chunks);
+        // the plan cuts ny - 2 interior rows; the second-order march has ny - 4
+        lbm_march_plan(nx, rows2 ? ny - 2 : ny, s->march_grid, &strips, &chunks);
         s->grid = s->march_grid;
         s->args.march_strips = strips;
         s->args.march_chunks = chunks;
@@ -1015,12 +1044,44 @@ lbm_status lbm_warm_start(lbm_sim *s, lbm_mlp *mlp, double kn, double u_w)
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "building the warm-start state");
 }
 
+// Second-order transport: the segment kernel of step_so.cuh (load path 0, its fixed warps
+// per segment), or on FP32 cavities the second-order column march on the strip-tiled state
+// (load paths 8 and 9).
+static lbm_status set_variant_order2(lbm_sim *s, int warps_per_segment, int prefetch)
+{
+    const int m = s->vs.m;
+    if (prefetch == 0) {
+        if (warps_per_segment != default_lanes_per_cell(s->prob.prec, m))
+            return fail(LBM_EUNSUPPORTED, "the second-order segment kernel runs %d warps per segment for M = %d",
+                        default_lanes_per_cell(s->prob.prec, m), m);
+    } else if (prefetch == 8 || prefetch == 9) {
+        if (!so_march_supported(m, warps_per_segment, so_march_slots(prefetch), so_march_tiled(prefetch)))
+            return fail(LBM_EUNSUPPORTED, "no second-order column march with %d warps per segment (load path %d) for M = %d",
+                        warps_per_segment, prefetch, m);
+        if (!tile_eligible(&s->prob) || s->prob.ny < 12)
+            return fail(LBM_EUNSUPPORTED, "the second-order column march needs an FP32 cavity with nx a multiple of 64, "
+                                          "nx >= 128 and ny >= 12");
+        int grid = 0;
+        cudaError_t e = prepare_step_f32_so_march(m, warps_per_segment, so_march_slots(prefetch),
+                                                  so_march_tiled(prefetch), &grid);
+        if (e != cudaSuccess) return cuda_fail(e, "enabling the second-order column march's shared memory");
+        if (grid <= 0) return fail(LBM_EUNSUPPORTED, "the second-order column march does not fit on an SM");
+        s->march_grid = grid;
+    } else {
+        return fail(LBM_EUNSUPPORTED, "the second-order transport has load paths 0, 8 and 9");
+    }
+    cudaError_t e = set_tiled(s, prefetch != 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "changing the state layout");
+    s->prefetch = prefetch;
+    return set_lanes(s, warps_per_segment);
+}
+
 lbm_status lbm_set_variant(lbm_sim *s, int warps_per_segment, int prefetch)
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (prefetch < 0 || prefetch > 9) return fail(LBM_EINVAL, "load path must be 0 to 9");
-    if (s->order == 2)
-        return fail(LBM_EUNSUPPORTED, "the second-order transport has one kernel variant (lbm_set_transport)");
+    if (s->order == 2) return set_variant_order2(s, warps_per_segment, prefetch);
     if (!step_supported(s->prob.prec, s->vs.m, warps_per_segment, prefetch))
         return fail(LBM_EUNSUPPORTED, "no step kernel with %d warps per segment (prefetch %d) for M = %d",
                     warps_per_segment, prefetch, s->vs.m);

@@ -51,6 +51,14 @@
 // (cp.async.bulk.global.shared::cta), so the warps issue no global store instructions; the
 // staging buffer is reused only after the previous row's store has read it
 // (cp.async.bulk.wait_group.read), and every store has completed before the block exits.
+//
+// ORDER = 2 (the second-order transport of step_so.cuh on the strip-tiled state): the
+// march covers x in [32, nx - 32), y in [2, ny - 3], where no face flux reaches a wall, so
+// every cell takes the plain upwind-biased (Beam-Warming) flux difference.  A warp reads
+// its own row and its two upwind rows (an item copies its rows and the two upwind rows
+// below or above it; ring of S >= 4 slots, S - 3 rows in flight), and the halo copy of each
+// velocity is the pair of cells next to the strip on the upwind side (one 8-byte cp.async).
+// The wall kernel beside it then covers rows 0, 1, ny - 2, ny - 1 and the side segments.
 #pragma once
 
 #include <cstdint>
@@ -86,13 +94,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// first row of chunk k of the interior rows [1, ny - 2] cut into nchunks near-equal chunks
-__device__ __forceinline__ int march_row0(int k, int rows, int nchunks)
+// first row of chunk k of the interior rows [first, first + rows) cut into nchunks
+// near-equal chunks (first = 1 for the first-order transport, 2 for the second-order one)
+__device__ __forceinline__ int march_row0(int k, int rows, int nchunks, int first = 1)
 {
-    return 1 + (int)(((long)k * rows) / nchunks);
+    return first + (int)(((long)k * rows) / nchunks);
 }
 
-template <int M, int G, int S, bool RESID, bool DEFER, int TILED = 0>
+template <int M, int G, int S, bool RESID, bool DEFER, int TILED = 0, int ORDER = 1>
 __global__ void __launch_bounds__(MarchShape<M, G, S, TILED>::THREADS, MarchShape<M, G, S, TILED>::MIN_BLOCKS)
 step_march_kernel(const StepArgs a)
 {
@@ -111,6 +120,9 @@ step_march_kernel(const StepArgs a)
     // its upwind neighbour); a copy overwrites the slot of the row before those two, which the
     // warp finished reading in its previous row step
     static_assert(S >= 2, "own row and upwind row resident");
+    // second order: the two upwind rows and the two upwind cells in x (8-byte halos) are
+    // read; the tiled layout only, no deferred relaxation
+    static_assert(ORDER == 1 || (ORDER == 2 && TILED != 0 && !DEFER && S >= 4), "second-order march form");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ float2 s_mom[NMOM][3][G][32];
@@ -125,7 +137,7 @@ step_march_kernel(const StepArgs a)
     const int nx = a.nx;
     const int nstrips = a.march_strips, nchunks = a.march_chunks;
     const int nitems = nstrips * nchunks;
-    const int rows = a.ny - 2;
+    const int rows = a.ny - 2 * ORDER;   // interior rows [ORDER, ny - 1 - ORDER]
     const bool ypos = g * RPL >= HALF;   // xi_y > 0: upwind row y - 1; else y + 1
     float *slots = reinterpret_cast<float *>(smem_raw) + (long)g * S * Sh::SLOT;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (long)S * G * Sh::SLOT * 4) + g * S;
@@ -163,11 +175,36 @@ step_march_kernel(const StepArgs a)
     // coefficients as FP32x2 pairs (both halves equal: one coefficient, two cells), set
     // once: per velocity of the warp 1 - nu_x - nu_y (k = r*M + ix), per ix nu_x, xi, w
     float2 a0r[NV], nux2[M], xi2[M], w2[M];
+    // second order (Beam-Warming face fluxes, no wall within two cells): per direction with
+    // Courant number nu, P = nu (3 - nu) / 2 (own cell), B = nu (2 - nu) (first upwind
+    // cell), C = nu (1 - nu) / 2 (second upwind cell; the host's tables), so that
+    //     h* = (1 - P_x - P_y) h + B_x h_x1 - C_x h_x2 + B_y h_y1 - C_y h_y2;
+    // a0r then holds 1 - P_x - P_y (formed in FP64, rounded once), cx2 and cy2 hold -C
+    float2 bx2[ORDER == 2 ? M : 1], cx2[ORDER == 2 ? M : 1], by2[ORDER == 2 ? RPL : 1], cy2[ORDER == 2 ? RPL : 1];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const int r = k / M, ix = k - r * M;
-        const float v = 1.f - a.nux_f[ix] - a.nuy_f[g * RPL + r];
+        float v;
+        if constexpr (ORDER == 2) {
+            v = (float)(1.0 - a.so_p[0][ix] - a.so_p[1][g * RPL + r]);
+        } else {
+            v = 1.f - a.nux_f[ix] - a.nuy_f[g * RPL + r];
+        }
         a0r[k] = make_float2(v, v);
+    }
+    if constexpr (ORDER == 2) {
+#pragma unroll
+        for (int ix = 0; ix < M; ++ix) {
+            const float b = a.so_b_f[0][ix], c = -a.so_c_f[0][ix];
+            bx2[ix] = make_float2(b, b);
+            cx2[ix] = make_float2(c, c);
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const float b = a.so_b_f[1][g * RPL + r], c = -a.so_c_f[1][g * RPL + r];
+            by2[r] = make_float2(b, b);
+            cy2[r] = make_float2(c, c);
+        }
     }
 #pragma unroll
     for (int ix = 0; ix < M; ++ix) {
@@ -184,15 +221,22 @@ step_march_kernel(const StepArgs a)
     constexpr long TROW = (long)M * M * LBM_TILE_W;
     const long tp = a.tile_pitch;
     const bool left_halo = (kc % M) >= M - HALF;
-    const long halo_off = left_halo ? (long)(g * NV + kc) * LBM_TILE_W + (LBM_TILE_W - 1)
+    // (second order: the two cells next to the strip, 8 bytes, at halo slot floats 2-3 for
+    // the left pair x0 - 2, x0 - 1 and 0-1 for the right pair x0 + 64, x0 + 65)
+    const long halo_off = left_halo ? (long)(g * NV + kc) * LBM_TILE_W + (LBM_TILE_W - ORDER)
                                     : 2 * tp + (long)(g * NV + kc) * LBM_TILE_W;
-    const int halo_dst = NV * LBM_TILE_W + 4 * kc + (left_halo ? 3 : 0);   // where the kernel reads it
+    const int halo_dst = NV * LBM_TILE_W + 4 * kc + (left_halo ? 4 - ORDER : 0);   // where the kernel reads it
     // x-upwind neighbour of a lane's cell pair, as base + k * step floats from the own row
     // slot (velocity k of the warp): the neighbouring cell of the own line, or, for the
     // strip's edge lane, the halo copied from the neighbouring tile
     const int pl_base = lane > 0 ? 2 * lane - 1 : NV * LBM_TILE_W + 3, pl_step = lane > 0 ? LBM_TILE_W : 4;
     const int pr_base = lane < 31 ? 2 * lane + 2 : NV * LBM_TILE_W, pr_step = lane < 31 ? LBM_TILE_W : 4;
+    // second order: the neighbouring cell pair on the upwind side (x - 2, x - 1 or x + 2,
+    // x + 3 of the lane's first cell) as one 8-byte read at base + k * step
+    const int ql_base = lane > 0 ? 2 * lane - 2 : NV * LBM_TILE_W + 2, ql_step = lane > 0 ? LBM_TILE_W : 4;
+    const int qr_base = lane < 31 ? 2 * lane + 2 : NV * LBM_TILE_W, qr_step = lane < 31 ? LBM_TILE_W : 4;
     (void)tp; (void)halo_off; (void)halo_dst; (void)pl_base; (void)pl_step; (void)pr_base; (void)pr_step;
+    (void)ql_base; (void)ql_step; (void)qr_base; (void)qr_step;
 
     // loader state (uniform within the warp)
     int l_pos = 0, l_item = s_items[0], l_i = 0;
@@ -200,8 +244,8 @@ step_march_kernel(const StepArgs a)
     auto l_decode = [&]() {
         const int k = l_item / nstrips;
         l_strip = l_item - k * nstrips;
-        l_row0 = march_row0(k, rows, nchunks);
-        l_len = march_row0(k + 1, rows, nchunks) - l_row0;
+        l_row0 = march_row0(k, rows, nchunks, ORDER);
+        l_len = march_row0(k + 1, rows, nchunks, ORDER) - l_row0;
     };
     if (l_item < nitems) l_decode();
     long nl = 0;       // copies issued (row slots)
@@ -209,7 +253,7 @@ step_march_kernel(const StepArgs a)
 
     auto issue = [&]() {
         const int slot = (int)(nl % S);
-        const int row = l_row0 - (ypos ? 1 : 0) + l_i;
+        const int row = l_row0 - (ypos ? ORDER : 0) + l_i;   // an item's rows and ORDER upwind rows
         if constexpr (TILED) {
             // transaction bytes of the bulk copy only: the halo copies count as arrivals
             if (lane == 0) mbar_arrive_expect(&bars[slot], (unsigned)(NV * LBM_TILE_W * 4));
@@ -218,10 +262,16 @@ step_march_kernel(const StepArgs a)
             float *dst = slots + slot * Sh::SLOT;
             const float *left_row = h + (long)l_strip * tp + (long)row * TROW;
             if (lane < NV) {
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n"
-                             "cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%2];\n" ::"r"(smem_addr(dst + halo_dst)),
-                             "l"(left_row + halo_off), "r"(smem_addr(&bars[slot]))
-                             : "memory");
+                if constexpr (ORDER == 1)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n"
+                                 "cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%2];\n" ::"r"(smem_addr(dst + halo_dst)),
+                                 "l"(left_row + halo_off), "r"(smem_addr(&bars[slot]))
+                                 : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n"
+                                 "cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%2];\n" ::"r"(smem_addr(dst + halo_dst)),
+                                 "l"(left_row + halo_off), "r"(smem_addr(&bars[slot]))
+                                 : "memory");
             }
             if (lane == 0)
                 bulk_copy(dst, left_row + tp + (long)g * NV * LBM_TILE_W, NV * LBM_TILE_W * 4, &bars[slot]);
@@ -234,7 +284,7 @@ step_march_kernel(const StepArgs a)
                           src_plane + (long)row * nx + 28 + 64L * l_strip, LINE * 4, &bars[slot]);
         }
         ++nl;
-        if (++l_i > l_len) {
+        if (++l_i > l_len + ORDER - 1) {
             l_i = 0;
             ++l_pos;
             l_item = s_items[l_pos & 3];
@@ -257,8 +307,8 @@ step_march_kernel(const StepArgs a)
     auto c_decode = [&]() {
         const int k = c_item / nstrips;
         c_strip = c_item - k * nstrips;
-        c_row0 = march_row0(k, rows, nchunks);
-        c_len = march_row0(k + 1, rows, nchunks) - c_row0;
+        c_row0 = march_row0(k, rows, nchunks, ORDER);
+        c_len = march_row0(k + 1, rows, nchunks, ORDER) - c_row0;
     };
     if (c_item < nitems) c_decode();
     long gb = 0;       // row-slot index of load 0 of the item being computed
@@ -297,9 +347,9 @@ step_march_kernel(const StepArgs a)
     };
 
     while (c_item < nitems) {
-        // keep S - 2 rows of copies ahead of the rows being computed
+        // keep S - 1 - ORDER rows of copies ahead of the rows being computed
         while (l_item < nitems && nl <= gb + c_u + S - 1) issue();
-        if (ok) wait_through(gb + c_u + 1);
+        if (ok) wait_through(gb + c_u + ORDER);
         ok = __all_sync(FULL, ok);      // one verdict per warp
         if (!ok) {
             if (lane == 0) {
@@ -309,10 +359,13 @@ step_march_kernel(const StepArgs a)
             // deferred: leave now (the other warps' next moment wait runs out and they leave)
             if (DEF) break;
         }
-        const long jo = ypos ? gb + c_u + 1 : gb + c_u;      // own row y
-        const long jy = ypos ? gb + c_u : gb + c_u + 1;      // upwind row y -/+ 1
+        const long jo = ypos ? gb + c_u + ORDER : gb + c_u;              // own row y
+        const long jy = ypos ? gb + c_u + ORDER - 1 : gb + c_u + 1;      // upwind row y -/+ 1
+        const long jq = ypos ? gb + c_u : gb + c_u + 2;                  // second order: y -/+ 2
         const float *own = slots + (int)(jo % S) * Sh::SLOT;
         const float *ynb = slots + (int)(jy % S) * Sh::SLOT;
+        const float *ynb2 = slots + (int)(jq % S) * Sh::SLOT;
+        (void)ynb2;
 
         // ---- transport + moment sums (two cells per lane) ----
         float2 hs[NV];
@@ -332,6 +385,27 @@ step_march_kernel(const StepArgs a)
                 for (int ix = 0; ix < M; ++ix) {
                     const int k = r * M + ix;
                     float2 hc, hx, hy;
+                    if constexpr (ORDER == 2) {
+                        // the pair's upwind neighbours: in x the next pair on the upwind side
+                        // (x -/+ 2 of the first cell, one 8-byte read) and the cell between,
+                        // in y the same pair in the rows y -/+ 1 and y -/+ 2
+                        hc = *reinterpret_cast<const float2 *>(own + k * LINE + 2 * lane);
+                        const bool xpos = ix >= M - HALF;
+                        const float2 nb = xpos ? *reinterpret_cast<const float2 *>(own + ql_base + k * ql_step)
+                                               : *reinterpret_cast<const float2 *>(own + qr_base + k * qr_step);
+                        const float2 h1x = xpos ? make_float2(nb.y, hc.x) : make_float2(hc.y, nb.x);
+                        const float2 h1y = *reinterpret_cast<const float2 *>(ynb + k * LINE + 2 * lane);
+                        const float2 h2y = *reinterpret_cast<const float2 *>(ynb2 + k * LINE + 2 * lane);
+                        float2 v = __fmul2_rn(a0r[k], hc);
+                        v = __ffma2_rn(bx2[ix], h1x, v);
+                        v = __ffma2_rn(cx2[ix], nb, v);
+                        v = __ffma2_rn(by2[r], h1y, v);
+                        v = __ffma2_rn(cy2[r], h2y, v);
+                        hs[k] = v;
+                        R2[ix % NACC] = __fadd2_rn(R2[ix % NACC], v);
+                        X2[ix % NACC] = __ffma2_rn(xi2[ix], v, X2[ix % NACC]);
+                        continue;
+                    }
                     if constexpr (TILED) {
                         hc = *reinterpret_cast<const float2 *>(own + k * LINE + 2 * lane);
                         hx = (ix >= M - HALF) ? make_float2(own[pl_base + k * pl_step], hc.x)   // xi_x > 0: x - 1
@@ -394,7 +468,7 @@ step_march_kernel(const StepArgs a)
             for (int k = 0; k < NV; ++k) hp[k] = hs[k];
             ++t;
             if (++c_u == c_len) {
-                gb += c_len + 1;
+                gb += c_len + ORDER;
                 c_u = 0;
                 ++c_pos;
                 c_item = s_items[c_pos & 3];
@@ -475,7 +549,7 @@ step_march_kernel(const StepArgs a)
 
         // ---- next row / item ----
         if (++c_u == c_len) {
-            gb += c_len + 1;
+            gb += c_len + ORDER;
             c_u = 0;
             ++c_pos;
             c_item = s_items[c_pos & 3];
@@ -530,28 +604,29 @@ step_march_kernel(const StepArgs a)
     }
 }
 
-template <int M, int G, int S, bool DEFER, int TILED = 0>
+template <int M, int G, int S, bool DEFER, int TILED = 0, int ORDER = 1>
 cudaError_t prepare_march(int *grid)
 {
     constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true, DEFER, TILED>,
+    cudaError_t e = cudaFuncSetAttribute(step_march_kernel<M, G, S, true, DEFER, TILED, ORDER>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false, DEFER, TILED>,
+        e = cudaFuncSetAttribute(step_march_kernel<M, G, S, false, DEFER, TILED, ORDER>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     // the largest shared-memory carveout: otherwise the driver may pick the smallest one that
     // holds one march block (164 KB for the tiled ring) and leave no room for the wall blocks
     // that run beside it
     for (int r = 0; r < 2 && e == cudaSuccess; ++r)
-        e = cudaFuncSetAttribute(r ? step_march_kernel<M, G, S, true, DEFER, TILED> : step_march_kernel<M, G, S, false, DEFER, TILED>,
+        e = cudaFuncSetAttribute(r ? step_march_kernel<M, G, S, true, DEFER, TILED, ORDER>
+                                   : step_march_kernel<M, G, S, false, DEFER, TILED, ORDER>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int per_sm = 0, dev = 0, sms = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false, DEFER, TILED>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_march_kernel<M, G, S, false, DEFER, TILED, ORDER>,
                                                           MarchShape<M, G, S, TILED>::THREADS, SMEM);
     if (e == cudaSuccess && DEFER) {
         int per_sm_resid = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, step_march_kernel<M, G, S, true, DEFER, TILED>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, step_march_kernel<M, G, S, true, DEFER, TILED, ORDER>,
                                                           MarchShape<M, G, S, TILED>::THREADS, SMEM);
         if (per_sm_resid < per_sm) per_sm = per_sm_resid;
     }
@@ -575,13 +650,11 @@ __global__ void __launch_bounds__(Shape<G>::THREADS) step_wall_beside_march_kern
 
 // March kernel over `grid` persistent blocks, and beside it the wall kernel over the wall
 // segments (programmatic dependent launch).
-template <int M, int G, int S, bool DEFER, bool RESID, int TILED = 0>
-cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
+// The wall kernel `wall` over the wall segments as a programmatic dependent launch of the
+// march grid just enqueued on `s` (its residual partials after the march's `grid` slots).
+template <int G>
+cudaError_t launch_wall_beside(void (*wall)(const StepArgs), const StepArgs &a, int grid, cudaStream_t s)
 {
-    constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;
-    step_march_kernel<M, G, S, RESID, DEFER, TILED><<<grid, MarchShape<M, G, S, TILED>::THREADS, SMEM, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.n_wall_segs == 0) return e;
     StepArgs b = a;
     b.partials_offset = grid;
     cudaLaunchConfig_t cfg;
@@ -595,7 +668,17 @@ cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, step_wall_beside_march_kernel<M, G, RESID, TILED>, b);
+    return cudaLaunchKernelEx(&cfg, wall, b);
+}
+
+template <int M, int G, int S, bool DEFER, bool RESID, int TILED = 0>
+cudaError_t launch_march(const StepArgs &a, int grid, cudaStream_t s)
+{
+    constexpr int SMEM = MarchShape<M, G, S, TILED>::SMEM;
+    step_march_kernel<M, G, S, RESID, DEFER, TILED><<<grid, MarchShape<M, G, S, TILED>::THREADS, SMEM, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.n_wall_segs == 0) return e;
+    return launch_wall_beside<G>(step_wall_beside_march_kernel<M, G, RESID, TILED>, a, grid, s);
 }
 
 }  // namespace lbmk

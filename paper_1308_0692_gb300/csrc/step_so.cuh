@@ -11,14 +11,20 @@
 //
 // Same decomposition as step_kernel.cuh (32-cell segments, G warps per segment owning M/G
 // velocity rows, moments through shared memory, wall segments in a second kernel), with
-// register loads of the two upwind neighbours per direction.
+// register loads of the two upwind neighbours per direction.  TILED: the state is the
+// strip-tiled FP32 layout of the column march (lbm_internal.h); the kernel then serves as
+// the wall kernel beside the second-order march (step_so_march.cu).
 #pragma once
 
 #include "step_kernel.cuh"
 
 namespace lbmk {
 
-template <typename TS, typename TC, int M, int G, bool RESID, bool PART>
+// a * b + c rounded once, in the arithmetic type
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename TS, typename TC, int M, int G, bool RESID, bool PART, bool TILED = false>
 __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
 {
     constexpr int SPB = Shape<G>::SPB;
@@ -57,19 +63,27 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
     const bool valid = work && in_grid;
     const TS *__restrict__ h = reinterpret_cast<const TS *>(a.h);
 
+    // offset of velocity 0 of cell (xx, yy) and the stride between velocities: planar, or
+    // strip-tiled (cavity only)
+    auto at = [&](int xx, int yy) -> long {
+        if constexpr (TILED) return tile_off(xx, yy, M * M, a.tile_pitch);
+        else return (long)yy * nx + xx;
+    };
+    const long vstride = TILED ? (long)LBM_TILE_W : ncells;
     // neighbour cells along x (periodic in Couette, clamped in the cavity) and y (clamped);
     // a clamped index is only ever read where its value is not used
     auto xcell = [&](int k) -> long {
         int xx = x + k;
         if (!cav) xx = ((xx % nx) + nx) % nx;
         else xx = xx < 0 ? 0 : (xx > nx - 1 ? nx - 1 : xx);
-        return (long)y * nx + xx;
+        return at(xx, y);
     };
     auto ycell = [&](int k) -> long {
         int yy = y + k;
         yy = yy < 0 ? 0 : (yy > ny - 1 ? ny - 1 : yy);
-        return (long)yy * nx + x;
+        return at(x, yy);
     };
+    const long cat = at(x, y);
     const long cxm1 = xcell(-1), cxm2 = xcell(-2), cxp1 = xcell(1), cxp2 = xcell(2);
     const long cym1 = ycell(-1), cym2 = ycell(-2), cyp1 = ycell(1), cyp2 = ycell(2);
 
@@ -86,8 +100,8 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
                 TC sy = 0, left = 0, right = 0;
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
-                    const TS *hp = h + (long)(iy * M + ix) * ncells;
-                    const TC v = (TC)ldg(hp + c);
+                    const TS *hp = h + (long)(iy * M + ix) * vstride;
+                    const TC v = (TC)ldg(hp + cat);
                     // towards the bottom wall (xi_y < 0): inner cell y + 1; top: y - 1
                     if (xiy != TC(0)) {
                         const TC inner = (TC)ldg(hp + (xiy < TC(0) ? cyp1 : cym1));
@@ -128,8 +142,16 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
     }
 
     // ---- second-order transport + moment row sums ----
-    // position along the transport direction, counted from the upwind end: 0 is the
-    // wall-adjacent cell (inflow across the wall face), 1 the next (first-order inflow)
+    // h* = h - D_x - D_y, per direction the face-flux difference with Courant number nu,
+    // P = nu (3 - nu) / 2, B = nu (2 - nu), C = nu (1 - nu) / 2 (host tables) and h_1, h_2
+    // the first and second upwind cells:
+    //     D = P h - B h_1 + C h_2     two or more cells from the upwind wall (or periodic)
+    //     D = P h - P h_1             the second cell (first-order inflow face)
+    //     D = nu h - nu g             the wall-adjacent cell (g: the wall-emitted population)
+    // Every neighbour is loaded (clamped index, unused where its coefficient is 0) and the
+    // case only selects coefficients, so that the loads of all velocities can be in flight
+    // together.  Position along a direction counted from its upwind end: 0 is the
+    // wall-adjacent cell.
     const int ixp = x, ixn = nx - 1 - x, iyp = y, iyn = ny - 1 - y;
     TC hs[RPL * M];
     TC rho = 0, jx = 0, jy = 0;
@@ -138,58 +160,52 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
             const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
+            // sign of xi_y from the node index (nodes ascend; odd full-range sets have a 0)
+            const int ys = iy >= M - HALF ? 1 : (iy < HALF ? -1 : 0);
+            const int jpos = ys > 0 ? iyp : iyn;
             const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
-            const bool ypos = xiy > TC(0), yneg = xiy < TC(0);
-            const int jpos = ypos ? iyp : iyn;
-            const TC rho_y = (TC)(ypos ? rb : rt);
-            const TC u_y = (TC)(ypos ? a.u_bottom : a.u_top);
-            const TC drive_y = a.homogeneous ? TC(0) : (TC)((ypos ? a.u_bottom : a.u_top) * a.inv_u_ref);
+            const TC Py = pick<TC>(a.so_p[1], a.so_p_f[1], iy), By = pick<TC>(a.so_b[1], a.so_b_f[1], iy),
+                     Cy = pick<TC>(a.so_c[1], a.so_c_f[1], iy);
+            const bool y0 = jpos == 0, y1 = jpos == 1;
+            const TC ay = ys == 0 ? TC(0) : (y0 ? nuy : Py);
+            const TC by = (ys == 0 || y0) ? TC(0) : (y1 ? Py : By);
+            const TC cy = (ys == 0 || y0 || y1) ? TC(0) : -Cy;
+            const long c1y = ys > 0 ? cym1 : cyp1, c2y = ys > 0 ? cym2 : cyp2;
+            // wall-emitted population across a bottom or top wall face (Eq. 8), PART only
+            const TC gy = (PART && ys != 0 && y0) ? nuy : TC(0);
+            const TC rho_y = (TC)(ys > 0 ? rb : rt);
+            const TC u_y = (TC)(ys > 0 ? a.u_bottom : a.u_top);
+            const TC drive_y = a.homogeneous ? TC(0) : (TC)((ys > 0 ? a.u_bottom : a.u_top) * a.inv_u_ref);
             const TC wy = pick<TC>(a.w1, a.w1_f, iy);
             TC R = 0, X = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const TS *hp = h + (long)(iy * M + ix) * ncells;
-                const TC hc = (TC)ldg(hp + c);
+                const TS *hp = h + (long)(iy * M + ix) * vstride;
+                const TC hc = (TC)ldg(hp + cat);
+                const TC h1y = (TC)ldg(hp + c1y), h2y = (TC)ldg(hp + c2y);
                 const TC xix = pick<TC>(a.xi, a.xi_f, ix);
-                const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
-                TC v = hc;
-                if (xmove && (ix >= M - HALF || ix < HALF)) {
-                    const bool xpos = ix >= M - HALF;
+                TC v = fma_(-ay, hc, hc);
+                v = fma_(by, h1y, v);
+                v = fma_(cy, h2y, v);
+                const int xs = ix >= M - HALF ? 1 : (ix < HALF ? -1 : 0);
+                if (xmove && xs != 0) {
                     const TC nu = pick<TC>(a.nux, a.nux_f, ix);
-                    const TC h1 = (TC)ldg(hp + (xpos ? cxm1 : cxp1));
-                    const int i = xpos ? ixp : ixn;
-                    TC fin, fout;
-                    if (cav && i == 0) {
-                        // ghost of the side wall (at rest): w_a rho'_w
-                        fin = nu * (wxy * (TC)(xpos ? rl : rr));
-                        fout = nu * hc;
-                    } else {
-                        if (cav && i == 1) {
-                            fin = nu * h1;
-                        } else {
-                            const TC h2 = (TC)ldg(hp + (xpos ? cxm2 : cxp2));
-                            fin = nu * (h1 + TC(0.5) * (TC(1) - nu) * (h1 - h2));
-                        }
-                        fout = nu * (hc + TC(0.5) * (TC(1) - nu) * (hc - h1));
-                    }
-                    v -= fout - fin;
+                    const TC Px = pick<TC>(a.so_p[0], a.so_p_f[0], ix), Bx = pick<TC>(a.so_b[0], a.so_b_f[0], ix),
+                             Cx = pick<TC>(a.so_c[0], a.so_c_f[0], ix);
+                    const TC h1x = (TC)ldg(hp + (xs > 0 ? cxm1 : cxp1)), h2x = (TC)ldg(hp + (xs > 0 ? cxm2 : cxp2));
+                    const int i = xs > 0 ? ixp : ixn;
+                    const bool x0 = cav && i == 0, x1 = cav && i == 1;
+                    const TC ax = x0 ? nu : Px;
+                    const TC bx = x0 ? TC(0) : (x1 ? Px : Bx);
+                    const TC cx = (x0 || x1) ? TC(0) : -Cx;
+                    v = fma_(-ax, hc, v);
+                    v = fma_(bx, h1x, v);
+                    v = fma_(cx, h2x, v);
+                    if (PART && x0) v += nu * (pick<TC>(a.w1, a.w1_f, ix) * wy * (TC)(xs > 0 ? rl : rr));
                 }
-                if (ypos || yneg) {
-                    const TC h1 = (TC)ldg(hp + (ypos ? cym1 : cyp1));
-                    TC fin, fout;
-                    if (jpos == 0) {
-                        fin = nuy * (wxy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y));
-                        fout = nuy * hc;
-                    } else {
-                        if (jpos == 1) {
-                            fin = nuy * h1;
-                        } else {
-                            const TC h2 = (TC)ldg(hp + (ypos ? cym2 : cyp2));
-                            fin = nuy * (h1 + TC(0.5) * (TC(1) - nuy) * (h1 - h2));
-                        }
-                        fout = nuy * (hc + TC(0.5) * (TC(1) - nuy) * (hc - h1));
-                    }
-                    v -= fout - fin;
+                if (PART && gy != TC(0)) {
+                    const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
+                    v += gy * (wxy * (rho_y * (TC(1) + xix * u_y) + xix * drive_y));
                 }
                 hs[r * M + ix] = v;
                 R += v;
@@ -228,7 +244,7 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
             const TC jj = wom * jx;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const long off = (long)(iy * M + ix) * ncells + c;
+                const long off = (long)(iy * M + ix) * vstride + cat;
                 const TC t = q + pick<TC>(a.xi, a.xi_f, ix) * jj;
                 const TC v = b * hs[r * M + ix] + pick<TC>(a.w1, a.w1_f, ix) * t;
                 if (RESID) {

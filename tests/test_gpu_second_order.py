@@ -7,7 +7,7 @@ import pytest
 
 from oracle.march import CAVITY, COUETTE, make_problem as oracle_problem
 from paper_1308_0692_gb300 import lbm
-from paper_1308_0692_gb300.inputs import random_state
+from paper_1308_0692_gb300.inputs import random_cells, random_state
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -85,6 +85,115 @@ def test_second_order_step_parity_fp32(case):
     assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * steps * np.abs(ref).max()
 
 
+def _stored_form_steps(p, g0, steps):
+    """The oracle's stored-state form of the variant: second-order transport, then the
+    exact relaxation over dt; every state along the way."""
+    out = [g0]
+    for _ in range(steps):
+        out.append(p.relax_exp(p.transport2(out[-1]), 1.0))
+    return out
+
+
+MARCH2 = [
+    # n per half-axis, nx, ny, kn, u_bottom, u_top, warps per segment
+    (6, 192, 45, 0.05, 0.003, 0.01, 6),    # D2Q^h_144, moving bottom, ragged chunks
+    (4, 256, 70, 0.1, 0.0, 0.01, 4),       # D2Q^h_64
+    (6, 128, 12, 0.05, 0.0, 0.01, 6),      # the smallest grid the march takes
+]
+
+
+@pytest.mark.parametrize("path", [8, 9])
+@pytest.mark.parametrize("case", MARCH2, ids=["cav192x45-144", "cav256x70-64", "cav128x12-144"])
+def test_second_order_column_march_matches_oracle(case, path):
+    """The second-order column march on the strip-tiled state (its interior rows 2 .. ny-3,
+    the wall kernel beside it on the rest) against the oracle's stored-state steps, the
+    residual of a residual step included; the segment kernel (load path 0) agrees with it
+    to a few FP32 roundings."""
+    n, nx, ny, kn, ub, ut, g = case
+    p = oracle_problem("half", n, CAVITY, nx, ny, kn, ub, ut)
+    g0 = p.relax_exp(random_state(p.n, p.ncells, seed=81), 0.5).astype(np.float32).astype(np.float64)
+    steps = 6
+    refs = _stored_form_steps(p, g0, steps)
+    sim = _sim(("half", n, CAVITY, nx, ny, kn, ub, ut), lbm.LBM_FP32_PERTURB, g0, lbm.LBM_SPLIT_STRANG_EXACT)
+    lbm.lbm_set_variant(sim, g, path)
+    assert lbm.lbm_get_variant(sim) == (g, path)
+    assert lbm.lbm_state_tiling(sim)[0] == 64
+    lbm.lbm_step(sim, steps)
+    got = lbm.lbm_get_state(sim)
+    ref = refs[-1]
+    assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * steps * np.abs(ref).max()
+    # residual_every = 4: the residual of step 4
+    r, st = lbm.lbm_residual(sim)
+    d, m = refs[4] - refs[3], refs[4]
+    r_ref = math.sqrt(float(np.sum(d * d)) / float(np.sum(m * m)))
+    assert st == 4 and abs(r - r_ref) <= 1e-3 * r_ref
+    seg = _sim(("half", n, CAVITY, nx, ny, kn, ub, ut), lbm.LBM_FP32_PERTURB, g0, lbm.LBM_SPLIT_STRANG_EXACT)
+    lbm.lbm_step(seg, steps)
+    assert np.abs(lbm.lbm_get_state(seg) - got).max() <= 4e-7 * steps * np.abs(ref).max()
+    # outputs read through the tiles
+    fy, fx = lbm.lbm_face_flux(sim)
+    ry = p.face_flux2_y(got)
+    assert np.abs(fy - ry).max() <= 1e-11 * max(np.abs(ry).max(), 1e-300)
+    sim.close()
+    seg.close()
+
+
+@pytest.fixture(scope="module")
+def so_bench_case():
+    """The benchmark's workload (cavity 2048 x 2048, D2Q^h_144, Kn 0.05, lid 0.01, FP32) with
+    the second-order variant: one FP32-representable state and the oracle's stored-state
+    step at 400 sampled cells, among them the rows and columns next to the walls and to the
+    march's strip and interior edges."""
+    nx = ny = 2048
+    p = oracle_problem("half", 6, CAVITY, nx, ny, 0.05, 0.0, 0.01)
+    h0 = random_state(p.n, p.ncells, seed=83).astype(np.float32).astype(np.float64)
+    edges = [(x, y) for y in (0, 1, 2, 3, ny // 2, ny - 4, ny - 3, ny - 2, ny - 1)
+             for x in (0, 1, 2, 31, 32, 33, 95, 96, 1023, 1024, nx - 34, nx - 33, nx - 32, nx - 31, nx - 2, nx - 1)]
+    cells = random_cells(p.ncells, 400, seed=84, include=[y * nx + x for x, y in edges])
+    return p, h0, cells, p.step2_cells(h0, cells)
+
+
+@pytest.mark.parametrize("variant", [(6, 8), (6, 9), (4, 0)], ids=["march-path8", "march-path9", "segments"])
+def test_second_order_full_size_sampled_step(so_bench_case, variant):
+    """One second-order step at the benchmark's size through each kernel variant, on
+    sampled cells, with and without the residual."""
+    p, h0, cells, ref = so_bench_case
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
+    idx = torch.as_tensor(np.asarray(cells, dtype=np.int64), device="cuda")
+    cy, cx = idx // 2048, idx % 2048
+    for residual_every in (1, 2):
+        prob = lbm.make_problem(CAVITY, 2048, 2048, 0.05, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB,
+                                residual_every=residual_every)
+        buf = torch.empty(lbm.lbm_sim_bytes(vs, prob), dtype=torch.uint8, device="cuda")
+        sim = lbm.lbm_init(vs, prob, h0, device_buf=buf, stream=torch.cuda.Stream())
+        lbm.lbm_set_transport(sim, 2)
+        lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG_EXACT)
+        lbm.lbm_set_variant(sim, *variant)
+        lbm.lbm_step(sim, 1)
+        ptr, step = lbm.lbm_state_device(sim)
+        assert step == 1
+        tw, shift, tp, rp = lbm.lbm_state_tiling(sim)
+        off = ptr - buf.data_ptr()
+        if tw:
+            nbytes = 4 * (2048 // tw + 1) * tp
+            xs = cx + shift
+            elems = torch.arange(p.n, device="cuda")[:, None] * tw + ((xs // tw) * tp + cy * rp + xs % tw)[None, :]
+        else:
+            pa, py = lbm.lbm_state_layout(sim)
+            nbytes = 4 * p.n * p.ncells
+            elems = torch.arange(p.n, device="cuda")[:, None] * pa + (cy * py + cx)[None, :]
+        torch.cuda.synchronize()
+        state = buf[off:off + nbytes].view(torch.float32)
+        got = state[elems].double().cpu().numpy().T
+        assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * np.abs(ref).max(), (variant, residual_every)
+        if residual_every == 1:
+            r, st = lbm.lbm_residual(sim)
+            assert st == 1 and np.isfinite(r) and r > 0
+        sim.close()
+        del buf, state
+    torch.cuda.empty_cache()
+
+
 def test_second_order_transport_with_lie_splitting():
     case = CASES[2]
     kind, n, geom, nx, ny, kn, ub, ut = case
@@ -144,9 +253,13 @@ def test_second_order_rejections():
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 4)
     sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, 64, 64, 0.1, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB))
     lbm.lbm_set_transport(sim, 2)
-    with pytest.raises(lbm.LBMError) as e:
-        lbm.lbm_set_variant(sim, 4, 0)
-    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    # the segment kernel has one warps-per-segment choice (2 for D2Q^h_64 in FP32); the
+    # column march exists for load paths 8 and 9 and needs nx a multiple of 64, >= 128
+    for variant in ((4, 0), (4, 4), (4, 8), (3, 9)):
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_set_variant(sim, *variant)
+        assert e.value.status == lbm.LBM_EUNSUPPORTED, variant
+    lbm.lbm_set_variant(sim, 2, 0)
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_solve(sim, 1e-8, 1000, 2)
     assert e.value.status == lbm.LBM_EUNSUPPORTED

@@ -14,8 +14,8 @@ and the interior x in [32, nx-32), y in [1, ny-2] is written exactly once.
 import pytest
 
 
-def march_row0(k, rows, nchunks):
-    return 1 + (k * rows) // nchunks
+def march_row0(k, rows, nchunks, first=1):
+    return first + (k * rows) // nchunks
 
 
 def choose_chunks(nx, ny, grid):
@@ -33,16 +33,18 @@ def choose_chunks(nx, ny, grid):
     return strips, chunks
 
 
-def simulate(nx, ny, S, grid, defer=False):
-    strips, nchunks = choose_chunks(nx, ny, grid)
-    rows, nitems, ncells = ny - 2, strips * nchunks, nx * ny
+def simulate(nx, ny, S, grid, defer=False, order=1):
+    """order 2: the second-order march (rows [2, ny - 3], an item's rows plus two upwind
+    rows copied, own row and both upwind rows read; the host plans ny - 4 rows)."""
+    strips, nchunks = choose_chunks(nx, ny - 2 * (order - 1), grid)
+    rows, nitems, ncells = ny - 2 * order, strips * nchunks, nx * ny
     written = {}
     counter = [3 * grid]
 
     def decode(it):
         k = it // strips
-        r0 = march_row0(k, rows, nchunks)
-        return it - k * strips, r0, march_row0(k + 1, rows, nchunks) - r0
+        r0 = march_row0(k, rows, nchunks, order)
+        return it - k * strips, r0, march_row0(k + 1, rows, nchunks, order) - r0
 
     for b in range(grid):
         fetched = []                       # dynamic ids of this block, in fetch order
@@ -65,25 +67,31 @@ def simulate(nx, ny, S, grid, defer=False):
                 while l_item < nitems and nl <= gb + c_u + S - 1:
                     if nl - S >= 0:
                         assert nl - S < gb + c_u            # slot's previous row no longer needed
-                    row = l_row0 - (1 if ypos else 0) + l_i
-                    start = row * nx + 28 + 64 * l_strip
-                    assert start % 4 == 0 and start >= 0 and start + 72 <= ncells
-                    assert start // nx == row and (start + 71) // nx == row
+                    row = l_row0 - (order if ypos else 0) + l_i
+                    assert 0 <= row < ny
+                    if order == 1:    # the planar copy of a row line (load paths 4-7)
+                        start = row * nx + 28 + 64 * l_strip
+                        assert start % 4 == 0 and start >= 0 and start + 72 <= ncells
+                        assert start // nx == row and (start + 71) // nx == row
                     loads.append((row, l_strip))
                     nl += 1
                     l_i += 1
-                    if l_i > l_len:
+                    if l_i > l_len + order - 1:
                         l_i, l_pos = 0, l_pos + 1
                         assert l_pos in visible
                         l_item = items[l_pos]
                         if l_item < nitems:
                             l_strip, l_row0, l_len = decode(l_item)
-                assert gb + c_u + 1 < nl
-                jo = gb + c_u + (1 if ypos else 0)
-                jy = gb + c_u + (0 if ypos else 1)
+                assert gb + c_u + order < nl
+                jo = gb + c_u + (order if ypos else 0)
+                jy = gb + c_u + (order - 1 if ypos else 1)
                 y = c_row0 + c_u
                 assert loads[jo] == (y, c_strip)
                 assert loads[jy] == (y - 1 if ypos else y + 1, c_strip)
+                if order == 2:
+                    jq = gb + c_u + (0 if ypos else 2)
+                    assert loads[jq] == (y - 2 if ypos else y + 2, c_strip)
+                    assert nl - 1 < min(jo, jy, jq) + S         # all three still in the ring
                 assert nl - 1 < min(jo, jy) + S                 # both still in the ring
                 if defer:
                     # deferred relaxation: an id written after row t's moments were published
@@ -100,7 +108,7 @@ def simulate(nx, ny, S, grid, defer=False):
                         written[c] = written.get(c, 0) + 1
                 c_u += 1
                 if c_u == c_len:
-                    gb, c_u, c_pos = gb + c_len + 1, 0, c_pos + 1
+                    gb, c_u, c_pos = gb + c_len + order, 0, c_pos + 1
                     assert c_pos in visible
                     c_item = items[c_pos]
                     if c_item < nitems:
@@ -112,7 +120,7 @@ def simulate(nx, ny, S, grid, defer=False):
                         counter[0] += 1
                         fetched.append(items[c_pos + 2])
                     pending.append(c_pos + 2)
-    interior = {y * nx + x for y in range(1, ny - 1) for x in range(32, nx - 32)}
+    interior = {y * nx + x for y in range(order, ny - order) for x in range(32, nx - 32)}
     assert set(written) == interior and all(v == 1 for v in written.values())
     return strips, nchunks
 
@@ -125,6 +133,15 @@ def test_march_schedule_covers_interior_once(nx, ny, slots, defer, grid):
     """Load paths 4, 5 (rings of 4 and 5 slots), 6 (a ring of 2: nothing read ahead) and 7
     (ring of 4, relaxation deferred by one row)."""
     simulate(nx, ny, slots, grid, defer)
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 12), (192, 45), (256, 70), (640, 33), (1024, 300), (2048, 130)])
+@pytest.mark.parametrize("slots", [4, 5])
+@pytest.mark.parametrize("grid", [7, 152, 304])
+def test_second_order_march_schedule_covers_interior_once(nx, ny, slots, grid):
+    """Second-order march (load paths 8 and 9 after lbm_set_transport(sim, 2)): rings of five
+    and four slots, rows [2, ny - 3]."""
+    simulate(nx, ny, slots, grid, order=2)
 
 
 def _library():
@@ -200,7 +217,8 @@ def test_tiled_offsets_are_a_bijection_onto_the_buffer(nx, ny, n):
 
 @pytest.mark.parametrize("nx,ny", [(128, 10), (192, 45), (384, 30), (2048, 12)])
 @pytest.mark.parametrize("m,g", [(12, 6), (8, 4)])
-def test_tiled_march_copies(nx, ny, m, g):
+@pytest.mark.parametrize("order", [1, 2])
+def test_tiled_march_copies(nx, ny, m, g, order):
     """Every row copy of the tiled march (one contiguous bulk copy of the warp's lines, one
     4-byte asynchronous copy of the x halo per velocity) lies inside the buffer, the bulk copy
     starts 16-byte aligned and covers exactly the warp's velocities of the strip's cells in
@@ -227,18 +245,23 @@ def test_tiled_march_copies(nx, ny, m, g):
                 for k in range(nvw):
                     ix = k % m
                     a = w * nvw + k
+                    # order 1: the upwind cell next to the strip (4 bytes); order 2: the two
+                    # upwind cells (8 bytes, 8-byte aligned on both sides)
                     if ix >= m - half:
-                        halo = left_row + a * TILE_W + (TILE_W - 1)
-                        want, dst = x0 - 1, nvw * TILE_W + 4 * k + 3
+                        halo = left_row + a * TILE_W + (TILE_W - order)
+                        want, dst = x0 - order, nvw * TILE_W + 4 * k + 4 - order
                     else:
                         halo = left_row + 2 * tp + a * TILE_W
                         want, dst = x0 + 64, nvw * TILE_W + 4 * k
-                    assert 0 <= halo < size
-                    x, y, aa = tiled_cell(halo, n, tp)
-                    assert (x, y, aa) == (want, row, a) and 0 <= x < nx
-                    # inside the warp's slot (dense lines, then 4 floats per velocity), one each
-                    assert nvw * TILE_W <= dst < nvw * (TILE_W + 4) and dst not in dsts
-                    dsts.add(dst)
+                    for j in range(order):
+                        assert 0 <= halo + j < size
+                        x, y, aa = tiled_cell(halo + j, n, tp)
+                        assert (x, y, aa) == (want + j, row, a) and 0 <= x < nx
+                        # inside the warp's slot (dense lines, then 4 floats per velocity), one each
+                        assert nvw * TILE_W <= dst + j < nvw * (TILE_W + 4) and dst + j not in dsts
+                        dsts.add(dst + j)
+                    if order == 2:
+                        assert halo % 2 == 0 and dst % 2 == 0
 
 
 # ---- batched column march on strip-tiled cavity instances: 32-column tiles, velocity pairs

@@ -45,6 +45,19 @@ def test_step_cells_matches_full_step():
     np.testing.assert_array_equal(part, full[:, cells].T)
 
 
+@pytest.mark.parametrize("geom,nx,ny,n", [(CAVITY, 7, 6, 4), (CAVITY, 9, 8, 6), (COUETTE, 1, 12, 4),
+                                         (COUETTE, 5, 7, 2)])
+def test_step2_cells_matches_transport2_then_exact_relaxation(geom, nx, ny, n):
+    """The per-cell second-order step is the whole-grid second-order transport followed by
+    the exact relaxation over dt, at every cell (walls, corners, the second cell from a
+    wall, periodic columns), bit for bit."""
+    p = make_problem("half", n, geom, nx, ny, 0.1, 0.0 if geom == CAVITY else 0.01, 0.01 if geom == CAVITY else -0.01)
+    h = random_state(p.n, p.ncells, seed=5)
+    full = p.relax_exp(p.transport2(h), 1.0)
+    cells = list(range(p.ncells))[::-1]
+    np.testing.assert_array_equal(p.step2_cells(h, cells), full[:, cells].T)
+
+
 @pytest.mark.parametrize("geom,nx,ny", [(CAVITY, 13, 11), (COUETTE, 1, 30), (COUETTE, 4, 9)])
 def test_total_mass_conserved(geom, nx, ny):
     """Transport with impermeable walls (Eq. 9) and relaxation (Eqs. 5-7) conserve total mass."""
