@@ -224,13 +224,13 @@ LOAD_PATHS = ["registers", "prefetch", "tma", "tma+walls merged", "column march 
               "column march on the strip-tiled state (4 row slots, bulk asynchronous stores)"]
 # second-order transport (lbm_set_transport(sim, 2)): the segment kernel, and the second-order
 # column march on the strip-tiled state
-VARIANTS_SO = [(4, 0), (6, 8), (6, 9)]
+VARIANTS_SO = [(6, 0), (6, 8), (6, 9)]
 LOAD_PATHS_SO = {0: "second-order segment kernel (registers)",
                  8: "second-order column march on the strip-tiled state (5 row slots)",
                  9: "second-order column march on the strip-tiled state (4 row slots, bulk asynchronous stores)"}
 
 
-def choose_variant(sim, stream, args, variants=None):
+def choose_variant(sim, stream, args, variants=None, steps_per_trial=8):
     """Autotune the step kernel on the workload itself: warps per segment x load path
     (0 registers, 2 TMA-staged halo, 3 the same with the walls in one launch, 4 to 9 the
     TMA column march), a few timed steps each; or the forced --variant."""
@@ -249,13 +249,13 @@ def choose_variant(sim, stream, args, variants=None):
             continue
         lbm.lbm_step(sim, 2)
         trials = []
-        for _ in range(3):                      # best of three runs of 8 steps
+        for _ in range(3):                      # best of three runs of steps_per_trial steps
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lbm.lbm_step(sim, 8)
+            lbm.lbm_step(sim, steps_per_trial)
             e1.record(stream)
             torch.cuda.synchronize()
-            trials.append(e0.elapsed_time(e1) / 8)
+            trials.append(e0.elapsed_time(e1) / steps_per_trial)
         times[f"{g},{pf}"] = min(trials)
     best = min(times, key=times.get)
     g, pf = (int(v) for v in best.split(","))
@@ -429,8 +429,9 @@ def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
                           "cyclic garbage collector paused during the timed calls (as timeit does)"}
 
 
-def run_fp64_same_workload(vs, dist):
-    """The plain FP64 march of the same workload (FP64 storage and arithmetic), few steps."""
+def run_fp64_same_workload(vs, dist, order: int = 1):
+    """The plain FP64 march of the same workload (FP64 storage and arithmetic), few steps;
+    order 2: its second-order variant (profiling)."""
     import torch
 
     from paper_1308_0692_gb300 import lbm
@@ -439,6 +440,9 @@ def run_fp64_same_workload(vs, dist):
                             lbm.LBM_FP64, w["residual_every"])
     stream = torch.cuda.Stream()
     sim = lbm.lbm_init(vs, prob, None, stream=stream)
+    if order == 2:
+        lbm.lbm_set_transport(sim, 2)
+        lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG_EXACT)
     lbm.lbm_step(sim, 3)
     K = 20
     torch.cuda.synchronize()
@@ -481,7 +485,8 @@ def run_second_order_same_workload(vs, dist, steps: int = 20):
         lbm.lbm_set_transport(sim, 2)
         lbm.lbm_set_splitting(sim, lbm.LBM_SPLIT_STRANG_EXACT)
         if prec == lbm.LBM_FP32_PERTURB:
-            variant, tuning = choose_variant(sim, stream, None, VARIANTS_SO)
+            # trials of one residual interval each: every trial holds one residual step
+            variant, tuning = choose_variant(sim, stream, None, VARIANTS_SO, w["residual_every"])
         else:
             variant, tuning = lbm.lbm_get_variant(sim), None
         lbm.lbm_step(sim, 3)
@@ -505,9 +510,27 @@ def run_second_order_same_workload(vs, dist, steps: int = 20):
                                         "basis": "8 B per update (one FP32 read and write of every value), "
                                                  "residual steps included"}}
         else:
+            # FP64 pipe operations of the step: the per-update counts of its two kernels (ncu,
+            # 1024^2 x 144) weighted by the cells each takes here (the wall kernel: the bottom
+            # and top rows and the 32-cell segments at both ends of every other row)
+            nx, ny = w["nx"], w["ny"]
+            wall_cells = 2 * nx + (ny - 2) * 64
+            ops = (FP64_SO_OPS_BULK * (nx * ny - wall_cells) + FP64_SO_OPS_WALL * wall_cells) / (nx * ny)
+            rate = lbm.lbm_probe_fp64_rate(200_000, stream)
             res["fp64"] = {"value": units / sec, "unit": UNIT, "steps": K, "ms_per_step": sec * 1e3,
+                           "variant": {"warps_per_segment": variant[0], "load_path": LOAD_PATHS_SO[variant[1]]},
+                           "fp64_pipe": {"bound": "alu", "measured_fp64_ops_per_s": rate, "ops_per_update": ops,
+                                         "achieved_fp64_ops_per_s": units / sec * ops,
+                                         "frac": units / sec * ops / rate},
                            "note": "FP64 storage+arithmetic, second-order segment kernel; FP64-pipe bound"}
     return res
+
+
+# FP64 pipe instructions (lane operations) per update of the second-order FP64 step's bulk
+# and wall kernels (ncu sm__inst_executed_pipe_fp64 x 32 / updates, 1024^2 x 144, six warps
+# per segment; profiles/)
+FP64_SO_OPS_BULK = 12.38
+FP64_SO_OPS_WALL = 24.0
 
 
 # FP64 pipe instructions (lane operations) per node-velocity update of the FP64 step, from the
@@ -847,7 +870,8 @@ def main(argv=None):
         from paper_1308_0692_gb300 import lbm
         torch.cuda.set_device(dist.local_rank)
         vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, WORKLOAD["n_half"])
-        print(json.dumps({"fp64": run_fp64_same_workload(vs, dist), "nx": WORKLOAD["nx"]}), flush=True)
+        print(json.dumps({"fp64": run_fp64_same_workload(vs, dist, args.transport), "nx": WORKLOAD["nx"],
+                          "transport": args.transport}), flush=True)
         dist.close()
         return 0
     out = run_own(args, dist)

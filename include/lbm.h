@@ -167,10 +167,18 @@ lbm_status lbm_get_splitting(const lbm_sim *sim, int *scheme);
  * nu [h_u + (1 - nu)/2 (h_u - h_uu)] (h_u, h_uu the two upwind cells; first order where h_uu
  * lies beyond a wall; nu times the wall-emitted population across a wall face), wall
  * densities (Eq. 9) balancing that outflow.  With LBM_SPLIT_STRANG_EXACT the steady state
- * converges at second order in the grid spacing.  Order 2 runs one register-path kernel per
- * velocity-set size (lbm_set_variant returns LBM_EUNSUPPORTED), has no FP32 refinement
- * (lbm_solve with refine_sweeps > 0 returns LBM_EUNSUPPORTED), and lbm_face_flux and the
- * wall shear of lbm_moments use its face values.  Call before the first step. */
+ * converges at second order in the grid spacing.  Order 2 has its own kernels: the segment
+ * kernel (load path 0; warps per segment 1 for M <= 4 and FP32 M = 6, 2 for FP64 M = 6 and
+ * FP32 M = 8, 4 for FP64 M = 8, 4 or 6 for M = 12 and 12 for FP64 M = 12; 6 by default for
+ * M = 12) and, on FP32 cavities with nx a multiple of 64, nx >= 128 and ny >= 12, the
+ * second-order column march on the strip-tiled state (load path 8: ring of five row slots,
+ * 9: four slots with bulk asynchronous stores; M = 12 with 6 warps, M = 8 with 4), which
+ * marches the cells two or more cells from every wall while the segment kernel takes rows
+ * 0, 1, ny-2, ny-1 and the 32-cell side segments; any other load path returns
+ * LBM_EUNSUPPORTED.  Order 2 has no FP32 refinement (lbm_solve with refine_sweeps > 0
+ * returns LBM_EUNSUPPORTED), and lbm_face_flux and the wall shear of lbm_moments use its
+ * face values.  Setting the order returns the sim to load path 0 and the planar layout.
+ * Call before the first step. */
 lbm_status lbm_set_transport(lbm_sim *sim, int order);
 lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
 

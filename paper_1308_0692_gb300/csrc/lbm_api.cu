@@ -28,7 +28,8 @@ cudaError_t prepare_step_f32_tma(int m, int g);
 cudaError_t launch_step_f32_march(int m, int g, int slots, bool defer, int tiled, bool resid, const StepArgs &a, int grid,
                                   cudaStream_t s);
 cudaError_t prepare_step_f32_march(int m, int g, int slots, bool defer, int tiled, int *grid);
-cudaError_t launch_step_so(int prec, int m, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step_so(int prec, int m, int g, bool resid, const StepArgs &a, int grid, cudaStream_t s);
+bool so_supported(int prec, int m, int g);
 cudaError_t launch_step_f32_so_march(int m, int g, int slots, int tiled, bool resid, const StepArgs &a, int grid,
                                      cudaStream_t s);
 cudaError_t prepare_step_f32_so_march(int m, int g, int slots, int tiled, int *grid);
@@ -371,7 +372,7 @@ void fill_args(lbm_sim *s, const TableHeader &hdr)
             const double nu = ax == 0 ? a.nux[i] : a.nuy[i];
             a.so_p[ax][i] = 0.5 * nu * (3.0 - nu);
             a.so_b[ax][i] = nu * (2.0 - nu);
-            a.so_c[ax][i] = 0.5 * nu * (1.0 - nu);
+            a.so_c[ax][i] = -0.5 * nu * (1.0 - nu);
             a.so_p_f[ax][i] = (float)a.so_p[ax][i];
             a.so_b_f[ax][i] = (float)a.so_b[ax][i];
             a.so_c_f[ax][i] = (float)a.so_c[ax][i];
@@ -417,7 +418,7 @@ cudaError_t enqueue_steps(lbm_sim *s, long first, long count, int cur, cudaStrea
         if (s->order == 2)
             e = s->prefetch >= 8 ? launch_step_f32_so_march(s->vs.m, s->lanes, so_march_slots(s->prefetch),
                                                             so_march_tiled(s->prefetch), resid, a, s->grid, st)
-                                 : launch_step_so(s->prob.prec, s->vs.m, resid, a, s->grid, st);
+                                 : launch_step_so(s->prob.prec, s->vs.m, s->lanes, resid, a, s->grid, st);
         else
             e = launch_step(s->prob.prec, s->vs.m, s->lanes, s->prefetch, resid, a, s->grid, st);
         if (e != cudaSuccess) return e;
@@ -1051,9 +1052,9 @@ static lbm_status set_variant_order2(lbm_sim *s, int warps_per_segment, int pref
 {
     const int m = s->vs.m;
     if (prefetch == 0) {
-        if (warps_per_segment != default_lanes_per_cell(s->prob.prec, m))
-            return fail(LBM_EUNSUPPORTED, "the second-order segment kernel runs %d warps per segment for M = %d",
-                        default_lanes_per_cell(s->prob.prec, m), m);
+        if (!so_supported(s->prob.prec, m, warps_per_segment))
+            return fail(LBM_EUNSUPPORTED, "no second-order segment kernel with %d warps per segment for M = %d",
+                        warps_per_segment, m);
     } else if (prefetch == 8 || prefetch == 9) {
         if (!so_march_supported(m, warps_per_segment, so_march_slots(prefetch), so_march_tiled(prefetch)))
             return fail(LBM_EUNSUPPORTED, "no second-order column march with %d warps per segment (load path %d) for M = %d",
@@ -1145,7 +1146,10 @@ lbm_status lbm_set_transport(lbm_sim *s, int order)
     cudaError_t e = set_tiled(s, false);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "changing the state layout");
-    return set_lanes(s, default_lanes_per_cell(s->prob.prec, s->vs.m));
+    // warps per segment of the second-order segment kernel: six for D2Q^h_144 (two velocity
+    // rows a warp; four left one block of eight warps per SM at 176 registers in FP64)
+    const int lanes = order == 2 && s->vs.m == 12 ? 6 : default_lanes_per_cell(s->prob.prec, s->vs.m);
+    return set_lanes(s, lanes);
 }
 
 lbm_status lbm_get_transport(const lbm_sim *s, int *order)

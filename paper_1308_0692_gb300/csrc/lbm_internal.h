@@ -82,7 +82,8 @@ struct StepArgs {
     double w1[LBM_MAX_M];   // 1-D weights (w_a = w1[ix] w1[iy])
     float xi_f[LBM_MAX_M], nux_f[LBM_MAX_M], nuy_f[LBM_MAX_M], w1_f[LBM_MAX_M];
     // second-order transport, per axis (0: x, 1: y) and node with Courant number nu:
-    // P = nu (3 - nu) / 2, B = nu (2 - nu), C = nu (1 - nu) / 2 (step_so.cuh)
+    // P = nu (3 - nu) / 2, B = nu (2 - nu), and the second upwind cell's coefficient
+    // -C = -nu (1 - nu) / 2 held negated (step_so.cuh, step_march.cuh)
     double so_p[2][LBM_MAX_M], so_b[2][LBM_MAX_M], so_c[2][LBM_MAX_M];
     float so_p_f[2][LBM_MAX_M], so_b_f[2][LBM_MAX_M], so_c_f[2][LBM_MAX_M];
     double omega, b;        // dt / Kn, 1 - omega

@@ -177,7 +177,7 @@ step_march_kernel(const StepArgs a)
     float2 a0r[NV], nux2[M], xi2[M], w2[M];
     // second order (Beam-Warming face fluxes, no wall within two cells): per direction with
     // Courant number nu, P = nu (3 - nu) / 2 (own cell), B = nu (2 - nu) (first upwind
-    // cell), C = nu (1 - nu) / 2 (second upwind cell; the host's tables), so that
+    // cell), C = nu (1 - nu) / 2 (second upwind cell; the host's tables hold -C), so that
     //     h* = (1 - P_x - P_y) h + B_x h_x1 - C_x h_x2 + B_y h_y1 - C_y h_y2;
     // a0r then holds 1 - P_x - P_y (formed in FP64, rounded once), cx2 and cy2 hold -C
     float2 bx2[ORDER == 2 ? M : 1], cx2[ORDER == 2 ? M : 1], by2[ORDER == 2 ? RPL : 1], cy2[ORDER == 2 ? RPL : 1];
@@ -195,13 +195,13 @@ step_march_kernel(const StepArgs a)
     if constexpr (ORDER == 2) {
 #pragma unroll
         for (int ix = 0; ix < M; ++ix) {
-            const float b = a.so_b_f[0][ix], c = -a.so_c_f[0][ix];
+            const float b = a.so_b_f[0][ix], c = a.so_c_f[0][ix];
             bx2[ix] = make_float2(b, b);
             cx2[ix] = make_float2(c, c);
         }
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
-            const float b = a.so_b_f[1][g * RPL + r], c = -a.so_c_f[1][g * RPL + r];
+            const float b = a.so_b_f[1][g * RPL + r], c = a.so_c_f[1][g * RPL + r];
             by2[r] = make_float2(b, b);
             cy2[r] = make_float2(c, c);
         }

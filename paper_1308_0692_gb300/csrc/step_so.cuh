@@ -88,38 +88,64 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
     const long cym1 = ycell(-1), cym2 = ycell(-2), cyp1 = ycell(1), cyp2 = ycell(2);
 
     // ---- wall densities (Eq. 9) balancing the second-order outflow through each wall face ----
+    // Segments in the bottom or top row form the y-wall sums on every lane (partial sums of
+    // a velocity row in the arithmetic type, across rows and warps in FP64).  A side wall
+    // touches one or two cells of a segment: their sums are formed cooperatively, the
+    // velocities towards that wall dealt to the lanes (products in the arithmetic type, the
+    // sum in FP64), instead of by every lane of the segment.
     double rb = 0.0, rt = 0.0, rl = 0.0, rr = 0.0;
     if (PART) {
         double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
-        if (work) {
+        const bool rows_wall = __any_sync(FULL, in_grid && (y == 0 || y == ny - 1));
+        if (work && rows_wall) {
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
                 const int iy = g * RPL + r;
-                const TC xiy = pick<TC>(a.xi, a.xi_f, iy);
+                const int ys = iy >= M - HALF ? 1 : (iy < HALF ? -1 : 0);
+                if (ys == 0) continue;
                 const TC nuy = pick<TC>(a.nuy, a.nuy_f, iy);
-                TC sy = 0, left = 0, right = 0;
+                const TC kap = TC(0.5) * (TC(1) - nuy);
+                // towards the bottom wall (xi_y < 0): inner cell y + 1; top: y - 1
+                const long cin = ys < 0 ? cyp1 : cym1;
+                TC sy = 0;
 #pragma unroll
                 for (int ix = 0; ix < M; ++ix) {
                     const TS *hp = h + (long)(iy * M + ix) * vstride;
                     const TC v = (TC)ldg(hp + cat);
-                    // towards the bottom wall (xi_y < 0): inner cell y + 1; top: y - 1
-                    if (xiy != TC(0)) {
-                        const TC inner = (TC)ldg(hp + (xiy < TC(0) ? cyp1 : cym1));
-                        sy += v + TC(0.5) * (TC(1) - nuy) * (v - inner);
-                    }
-                    if (ix < HALF || ix >= M - HALF) {
+                    sy += v + kap * (v - (TC)ldg(hp + cin));
+                }
+                const double xiy = a.xi[iy];
+                if (ys < 0) sb -= xiy * (double)sy;
+                else st += xiy * (double)sy;
+            }
+        }
+        if (work && cav) {
+            constexpr int NSIDE = RPL * HALF;   // velocities of this warp towards one side wall
+            for (int side = 0; side < 2; ++side) {
+                unsigned mask = __ballot_sync(FULL, in_grid && (side == 0 ? x == 0 : x == nx - 1));
+                while (mask) {
+                    const int L = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const long cL = __shfl_sync(FULL, cat, L);
+                    const long cI = __shfl_sync(FULL, side == 0 ? cxp1 : cxm1, L);   // inner neighbour
+                    double part = 0.0;
+                    for (int k = lane; k < NSIDE; k += 32) {
+                        const int r = k / HALF, q = k - r * HALF;
+                        const int iy = g * RPL + r, ix = side == 0 ? q : M - HALF + q;
+                        const TS *hp = h + (long)(iy * M + ix) * vstride;
+                        const TC v = (TC)ldg(hp + cL);
                         const TC nux = pick<TC>(a.nux, a.nux_f, ix);
-                        const TC xix = pick<TC>(a.xi, a.xi_f, ix);
-                        const TC inner = (TC)ldg(hp + (ix < HALF ? cxp1 : cxm1));
-                        const TC fv = v + TC(0.5) * (TC(1) - nux) * (v - inner);
-                        if (ix < HALF) left -= xix * fv;       // towards the left wall
-                        else right += xix * fv;                // towards the right wall
+                        const TC fv = v + TC(0.5) * (TC(1) - nux) * (v - (TC)ldg(hp + cI));
+                        const TC xf = pick<TC>(a.xi, a.xi_f, ix) * fv;
+                        part += side == 0 ? -(double)xf : (double)xf;
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(FULL, part, off);
+                    if (lane == L) {
+                        if (side == 0) sls = part;
+                        else srs = part;
                     }
                 }
-                if (xiy < TC(0)) sb -= (double)xiy * (double)sy;
-                if (xiy > TC(0)) st += (double)xiy * (double)sy;
-                sls += (double)left;
-                srs += (double)right;
             }
         }
         s_wall[0][g][sl][lane] = sb;
@@ -169,7 +195,7 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
             const bool y0 = jpos == 0, y1 = jpos == 1;
             const TC ay = ys == 0 ? TC(0) : (y0 ? nuy : Py);
             const TC by = (ys == 0 || y0) ? TC(0) : (y1 ? Py : By);
-            const TC cy = (ys == 0 || y0 || y1) ? TC(0) : -Cy;
+            const TC cy = (ys == 0 || y0 || y1) ? TC(0) : Cy;     // the table holds -C
             const long c1y = ys > 0 ? cym1 : cyp1, c2y = ys > 0 ? cym2 : cyp2;
             // wall-emitted population across a bottom or top wall face (Eq. 8), PART only
             const TC gy = (PART && ys != 0 && y0) ? nuy : TC(0);
@@ -197,7 +223,7 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
                     const bool x0 = cav && i == 0, x1 = cav && i == 1;
                     const TC ax = x0 ? nu : Px;
                     const TC bx = x0 ? TC(0) : (x1 ? Px : Bx);
-                    const TC cx = (x0 || x1) ? TC(0) : -Cx;
+                    const TC cx = (x0 || x1) ? TC(0) : Cx;      // the table holds -C
                     v = fma_(-ax, hc, v);
                     v = fma_(bx, h1x, v);
                     v = fma_(cx, h2x, v);

@@ -14,8 +14,11 @@ using namespace lbmk;
 
 namespace {
 
+// At most 64 registers a thread: two of its blocks then fit on an SM beside a march block
+// (up to 200 registers x 192 threads), as the first-order wall kernel's do; with one the
+// wall segments were still running when the march had finished.
 template <int M, int G, bool RESID>
-__global__ void __launch_bounds__(Shape<G>::THREADS) step_so_wall_beside_march_kernel(const StepArgs a)
+__global__ void __maxnreg__(64) step_so_wall_beside_march_kernel(const StepArgs a)
 {
     step_so_body<float, float, M, G, RESID, true, true>(a, blockIdx.x);
     // see step_wall_beside_march_kernel: the grid completes after the march grid
