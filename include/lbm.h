@@ -196,7 +196,7 @@ lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
  * multiple of 64, nx >= 128, ny >= 10; M = 12 with 6 or 12 warps (6 only for paths 6 and
  * 7), M = 8 with 2 or 4 warps (path 5)),
  * 8 the column march of path 4 on a strip-tiled state, 9 the same with the stores too as
- * bulk asynchronous copies from shared memory (M = 12 with 6 warps, M = 8 with 4): choosing
+ * bulk asynchronous copies from shared memory (M = 12 with 6 warps, M = 8 with 4, M = 4 with 2): choosing
  * path 8 or 9 moves the current state into that layout (lbm_state_tiling), where one
  * row of a 64-cell strip, all velocities, is one contiguous stretch of memory, so that a
  * warp copies its lines of a row with one bulk copy; any other path moves it back to the

@@ -504,15 +504,21 @@ lbm_status set_lanes(lbm_sim *s, int lanes)
     s->args.merged = (long)segs.size() * 10 > nseg_total ? 1 : 0;
     if (s->prefetch >= 4) {
         int strips = 0, chunks = 0;
+        // every march block writes one residual partial: the march grid and the wall kernel's
+        // blocks stay within the partials region (small grids of small velocity sets have
+        // more resident blocks than 32-cell segments)
+        const int grid = std::min(s->march_grid, s->npartials - wall_grid(lanes, (int)segs.size()));
+        if (grid < 1) return fail(LBM_EINVAL, "internal: no room for the column march's residual partials");
         // the plan cuts ny - 2 interior rows; the second-order march has ny - 4
-        lbm_march_plan(nx, rows2 ? ny - 2 : ny, s->march_grid, &strips, &chunks);
-        s->grid = s->march_grid;
+        lbm_march_plan(nx, rows2 ? ny - 2 : ny, grid, &strips, &chunks);
+        s->grid = grid;
         s->args.march_strips = strips;
         s->args.march_chunks = chunks;
         s->args.counters = (int *)(s->result + 12);
         s->args.merged = 0;
     }
     s->nparts_step = s->grid + wall_grid(lanes, (int)segs.size());
+    if (s->nparts_step > s->npartials) return fail(LBM_EINVAL, "internal: residual partials overflow");
     return LBM_OK;
 }
 

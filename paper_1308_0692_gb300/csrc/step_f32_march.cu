@@ -4,7 +4,8 @@
 // blocks per SM), load path 7 is path 4 with the relaxation of each row deferred until
 // after the next row's transport (steps without the residual), load path 8 is path 4 on the
 // strip-tiled state (one contiguous copy per warp and row), load path 9 path 8 with the stores
-// as bulk asynchronous copies from shared memory too.
+// as bulk asynchronous copies from shared memory too.  M = 4 (the 16-velocity sets D2Q^h_16
+// and D2Q_16) has the tiled forms only.
 #include "step_march.cuh"
 
 using namespace lbmk;
@@ -21,7 +22,9 @@ using namespace lbmk;
     X(12, 6, 4, false, 1)     \
     X(12, 6, 4, false, 2)     \
     X(8, 4, 4, false, 1)      \
-    X(8, 4, 4, false, 2)
+    X(8, 4, 4, false, 2)      \
+    X(4, 2, 4, false, 1)      \
+    X(4, 2, 4, false, 2)
 
 bool march_supported(int m, int g, int slots, bool defer, int tiled)
 {

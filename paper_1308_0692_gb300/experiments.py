@@ -3,7 +3,11 @@ library's FP64 march: the Couette Kn sweep (Figs. 1-2), the Couette profile and 
 stress at Kn = 1 (Fig. 3 and the statement on the number of full-range nodes), and the
 driven cavity's centre-line profile, lid drag D and vortex flow rate G (Fig. 4, Table 2).
 
-    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2,order,hybrid,cavity_hybrid} --out r.json
+    python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2,order,hybrid,cavity_hybrid,rates} --out r.json
+
+`rates` times the step of a large cavity (default 2048 x 2048) for every velocity set of
+these comparisons, both precisions and every compiled kernel variant, and reports the
+fastest with its algorithmic HBM rate (8 B per update in FP32, 16 B in FP64).
 
 Couette flow between plates at -u_w and +u_w: for each Knudsen number and velocity set the
 steady state is marched on the GPU to a residual tolerance, and the shear stress (the
@@ -22,6 +26,7 @@ import numpy as np
 from . import lbm
 
 SETS = {
+    "D2Q9": (lbm.LBM_FULL_RANGE_GH, 3),
     "D2Q^h_16": (lbm.LBM_HALF_RANGE_GH, 2),
     "D2Q_16": (lbm.LBM_FULL_RANGE_GH, 4),
     "D2Q^h_64": (lbm.LBM_HALF_RANGE_GH, 4),
@@ -296,14 +301,58 @@ def cavity_hybrid_study(kns=(0.1, 1.0), side=128, n_half=4, layers=(0, 4, 8, 16,
     return out
 
 
+# kernel variants offered to `rates`: (warps per segment, load path); lbm_set_variant rejects
+# the ones without a compiled kernel for a set and precision
+RATE_VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (6, 0), (12, 0), (2, 1), (4, 1), (6, 1), (4, 2), (6, 2),
+                 (6, 4), (6, 5), (4, 5), (2, 8), (4, 8), (6, 8), (2, 9), (4, 9), (6, 9)]
+
+
+def step_rates(side: int = 2048, sets=("D2Q9", "D2Q^h_16", "D2Q_16", "D2Q^h_64", "D2Q^h_144"), steps: int = 30):
+    """Step time of a side x side lid-driven cavity (Kn 0.05, lid 0.01, residual every 10
+    steps) per velocity set, precision and kernel variant, timed with CUDA events on the
+    simulation's stream after a residual interval of warm-up."""
+    import torch
+    out = {"side": side, "steps": steps, "runs": []}
+    for name in sets:
+        kind, n = SETS[name]
+        vs = lbm.lbm_make_velocity_set(kind, n)
+        nvel = len(lbm.lbm_vset_query(vs)[2])
+        for prec in (lbm.LBM_FP32_PERTURB, lbm.LBM_FP64):
+            stream = torch.cuda.Stream()
+            sim = lbm.lbm_init(vs, lbm.make_problem(lbm.LBM_CAVITY, side, side, 0.05, 0.0, 0.01, prec=prec,
+                                                    residual_every=10), stream=stream)
+            times = {}
+            for g, pf in RATE_VARIANTS:
+                try:
+                    lbm.lbm_set_variant(sim, g, pf)
+                except lbm.LBMError:
+                    continue
+                lbm.lbm_step(sim, 10)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lbm.lbm_step(sim, steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times[f"{g},{pf}"] = e0.elapsed_time(e1) / steps
+            sim.close()
+            best = min(times, key=times.get)
+            upd = side * side * nvel
+            bpu = 8 if prec == lbm.LBM_FP32_PERTURB else 16
+            out["runs"].append({"set": name, "velocities": nvel, "precision": "fp32" if prec else "fp64",
+                                "ms_per_step": times, "best": best, "updates_per_s": upd / times[best] * 1e3,
+                                "algorithmic_gbs": upd * bpu / times[best] / 1e6})
+    out["summary"] = {f"{r['set']} {r['precision']}": [r["best"], round(r["algorithmic_gbs"])] for r in out["runs"]}
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order", "hybrid",
-                                           "cavity_hybrid"])
+                                           "cavity_hybrid", "rates"])
     ap.add_argument("--out", required=True)
-    ap.add_argument("--side", type=int, default=128)
+    ap.add_argument("--side", type=int, default=None, help="cavity side (128; rates: 2048)")
     args = ap.parse_args(argv)
     if args.study == "kn_sweep":
         r = kn_sweep()
@@ -314,9 +363,11 @@ def main(argv=None):
     elif args.study == "hybrid":
         r = hybrid_study()
     elif args.study == "cavity_hybrid":
-        r = cavity_hybrid_study(side=args.side)
+        r = cavity_hybrid_study(side=args.side or 128)
+    elif args.study == "rates":
+        r = step_rates(side=args.side or 2048)
     else:
-        r = cavity_table2_study(side=args.side)
+        r = cavity_table2_study(side=args.side or 128)
     with open(args.out, "w") as f:
         json.dump(r, f, indent=1)
     if args.study == "order":

@@ -454,6 +454,36 @@ def test_fp32_column_march_matches_oracle(n_half, nx, ny, variants):
             assert np.abs(got - base).max() <= 1e-6 * np.abs(ref).max(), (g, pf)
 
 
+@pytest.mark.parametrize("kind,n_half,nx,ny", [("half", 2, 128, 40), ("full", 4, 256, 70), ("half", 2, 192, 23)],
+                         ids=["Dh16-128x40", "D16-256x70", "Dh16-192x23"])
+def test_fp32_column_march_16_velocity_sets(kind, n_half, nx, ny):
+    """The tiled column march (load paths 8 and 9) on the 16-velocity sets of the paper's
+    half- versus full-range comparison (two warps, two velocity rows each) against the
+    oracle over several steps with the residual, and against the register kernel."""
+    p = oracle_problem(kind, n_half, CAVITY, nx, ny, 0.2, 0.0, 0.01)
+    h0 = random_state(p.n, p.ncells, seed=43).astype(np.float32).astype(np.float64)
+    steps = 4
+    ref = p.step(h0, steps)
+    ref_r = oracle_residual(ref, p.step(h0, steps - 1))
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH if kind == "half" else lbm.LBM_FULL_RANGE_GH, n_half)
+    base = None
+    for g, pf in [(1, 0), (2, 8), (2, 9)]:
+        sim = lbm.lbm_init(vs, lbm.make_problem(CAVITY, nx, ny, 0.2, 0.0, 0.01, prec=lbm.LBM_FP32_PERTURB,
+                                                residual_every=steps), h0, stream=torch.cuda.Stream())
+        lbm.lbm_set_variant(sim, g, pf)
+        assert lbm.lbm_get_variant(sim) == (g, pf)
+        lbm.lbm_step(sim, steps)
+        got = lbm.lbm_get_state(sim)
+        r, st = lbm.lbm_residual(sim)
+        assert st == steps and abs(r - ref_r) <= 1e-4 * ref_r, (g, pf, r, ref_r)
+        assert np.abs(got - ref).max() <= FP32_TOL_PER_STEP * steps * np.abs(ref).max(), (g, pf)
+        if base is None:
+            base = got
+        else:
+            assert np.abs(got - base).max() <= 1e-6 * np.abs(ref).max(), (g, pf)
+        sim.close()
+
+
 def test_column_march_rejected_where_strips_do_not_fit():
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, 6)
     for nx, ny in [(160, 64), (64, 64), (128, 9)]:
