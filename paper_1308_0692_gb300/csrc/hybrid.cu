@@ -15,16 +15,20 @@
 //     rule);
 //   * relaxation towards w (rho + xi . j) in the cell's own set (Eqs. 1, 5-7).
 // Cells with an interface face: one warp per cell (projections in shared memory); all other
-// cells: a lane group per cell, several cells per warp, the upwind values read directly.  The
-// state is packed cell after cell, each cell's values in its own set's velocity order
-// (a = iy * M + ix).  dt = cfl dy / max |xi_y| over the sets present,
-// dt <= Kn.
+// cells: the plain-cell kernel, one lane per cell with the 1-D node tables of its set in the
+// kernel parameters.  State layout: tiles of up to 32 consecutive cells (in the cell order
+// c = y nx + x) of one set; velocity a of the cell in position p of a tile lies at
+// tile base + p + 32 a, so that a warp reads one velocity of a tile's cells as one
+// contiguous stretch (toff[c] = tile base + p).  Host transfers keep the packed order,
+// cell after cell, each cell's values in its own set's velocity order (a = iy * M + ix).
+// dt = cfl dy / max |xi_y| over the sets present, dt <= Kn.
 #include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -61,9 +65,11 @@ struct HybTables {
     double pt[2][HMAXV * HMAXF];
 };
 
+constexpr int HST = 32;        // stride between the velocities of a cell in the tiled state
+
 struct HybArgs {
     const HybTables *tab;
-    const int *off;            // [ny + 1] first value of each cell in the packed state
+    const int *toff;           // [ncells] velocity 0 of each cell in the tiled state
     const unsigned char *half; // [ncells] 1: half-range cell
     const double *h;
     double *hn;
@@ -115,19 +121,25 @@ __device__ void project_warp(const HybTables &tb, int ti, const double *h, doubl
     __syncwarp();
 }
 
+// The n values of cell k into buf[0..n) (a warp; velocity b at toff[k] + HST b).
+__device__ void gather_cell(const double *h, const int *toff, int k, int n, double *buf)
+{
+    const double *hk = h + toff[k];
+    for (int b = threadIdx.x & 31; b < n; b += 32) buf[b] = hk[(long)HST * b];
+    __syncwarp();
+}
+
 // Values of neighbour cell k as seen by a cell of set sj, into buf[0..S.n): its own values
-// for the same set, else their projection.
-__device__ void neighbour_values(const HybArgs &a, int k, int sj, double *buf)
+// for the same set, else their projection (tmp: the neighbour's values, gathered first).
+__device__ void neighbour_values(const HybArgs &a, int k, int sj, double *buf, double *tmp)
 {
     const HybTables &tb = *a.tab;
-    const HybSet &S = tb.set[sj];
     const int sk = a.half[k] ? 0 : 1;
-    const double *hk = a.h + a.off[k];
     if (sk == sj) {
-        for (int b = threadIdx.x & 31; b < S.n; b += 32) buf[b] = hk[b];
-        __syncwarp();
+        gather_cell(a.h, a.toff, k, tb.set[sj].n, buf);
     } else {
-        project_warp(tb, sk, hk, buf);
+        gather_cell(a.h, a.toff, k, tb.set[sk].n, tmp);
+        project_warp(tb, sk, tmp, buf);
     }
 }
 
@@ -176,6 +188,7 @@ __device__ void face_moments(const HybSet &S, const double *v, int axis, bool po
 struct HybShared {
     double nbv[HWARPS][4][HMAXV];   // left, right, below, above: upwind values in the cell's set
     double ph[HWARPS][HMAXV], nb[HWARPS][HMAXV];
+    double own[HWARPS][HMAXV], tmp[HWARPS][HMAXV];   // the cell's values; a neighbour's before projection
 };
 
 // A cell with an interface face (a neighbour in the other set): one warp, warp `wi` of the
@@ -189,21 +202,23 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     const int sj = a.half[c] ? 0 : 1;
     const HybSet &S = tb.set[sj];
     const HybSet &H = tb.set[0];
-    const double *hc = a.h + a.off[c];
+    double *hc = sh.own[wi];
+    gather_cell(a.h, a.toff, c, S.n, hc);
+    double *tmp = sh.tmp[wi];
     const int x = c % nx, y = c / nx;
     double(*nbv)[HMAXV] = sh.nbv[wi];
     // upwind values: x (cavity only) and y neighbours in this cell's set, or the walls' ghosts;
     // the four faces as (axis, side, neighbour or -1)
     int nbc[4] = {-1, -1, -1, -1};
     if (a.cavity) {
-        if (x > 0) neighbour_values(a, nbc[0] = c - 1, sj, nbv[0]);
+        if (x > 0) neighbour_values(a, nbc[0] = c - 1, sj, nbv[0], tmp);
         else wall_ghost(a, S, hc, 2, nbv[0]);
-        if (x < nx - 1) neighbour_values(a, nbc[1] = c + 1, sj, nbv[1]);
+        if (x < nx - 1) neighbour_values(a, nbc[1] = c + 1, sj, nbv[1], tmp);
         else wall_ghost(a, S, hc, 3, nbv[1]);
     }
-    if (y > 0) neighbour_values(a, nbc[2] = c - nx, sj, nbv[2]);
+    if (y > 0) neighbour_values(a, nbc[2] = c - nx, sj, nbv[2], tmp);
     else wall_ghost(a, S, hc, 0, nbv[2]);
-    if (y < ny - 1) neighbour_values(a, nbc[3] = c + nx, sj, nbv[3]);
+    if (y < ny - 1) neighbour_values(a, nbc[3] = c + nx, sj, nbv[3], tmp);
     else wall_ghost(a, S, hc, 1, nbv[3]);
     // interface faces of a full-range cell: mass and momentum exchange made equal to the
     // half-range evaluation of the face
@@ -218,7 +233,7 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
             if (nbc[f] < 0 || !a.half[nbc[f]]) continue;
             const int axis = f >> 1;
             const bool lower = (f & 1) == 0;                  // the neighbour is on the lower side
-            neighbour_values(a, nbc[f], 0, nb);               // its own half-range values
+            neighbour_values(a, nbc[f], 0, nb, tmp);          // its own half-range values
             double up[3], dn[3], got[3], sent[3];
             face_moments(H, lower ? nb : ph, axis, true, up);
             face_moments(H, lower ? ph : nb, axis, false, dn);
@@ -260,7 +275,7 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     rho = warp_sum(rho);
     jx = warp_sum(jx);
     jy = warp_sum(jy);
-    double *out = a.hn + a.off[c];
+    double *out = a.hn + a.toff[c];
     double pd = 0.0, pn = 0.0;
 #pragma unroll
     for (int i = 0; i < (HMAXV + 31) / 32; ++i) {
@@ -268,7 +283,7 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
         if (b < S.n) {
             const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
             const double o = hs[i] - a.omega * (hs[i] - heq);
-            out[b] = o;
+            out[(long)HST * b] = o;
             if (resid) {
                 const double d = o - hc[b];
                 pd += d * d;
@@ -286,135 +301,254 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     }
 }
 
-// sum over the `width` lanes of an aligned lane group (width a power of two <= 32)
-__device__ __forceinline__ double group_sum(double v, int width)
+// Cells with an interface face, one warp each (their projections are long latency chains;
+// launched first, so that the plain-cell kernel's blocks fill in beside them).
+__global__ void __launch_bounds__(32 * HWARPS, 4) hybrid_interface_kernel(const HybArgs a, const int *cells, int ncells,
+                                                                         double dt, double dx, double dy, int resid)
 {
-    for (int o = width >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    __shared__ HybShared sh;
+    const int wi = threadIdx.x >> 5;
+    const int ci = (int)blockIdx.x * HWARPS + wi;
+    if (ci < ncells) interface_cell(a, sh, wi, cells[ci], dt, dx, dy, resid);     // whole warps
 }
 
-constexpr int HMAXPL = (HMAXV + 31) / 32;     // velocities per lane in the plain-cell kernel
+// Plain cells of one set: all their existing neighbours carry the same set.  Per tile (up to
+// 32 consecutive cells of the set) G warps, lane p the tile's cell p, warp g the velocity rows
+// iy in [g M / G, (g + 1) M / G); the set's 1-D nodes, weights and Courant numbers are kernel
+// parameters (velocity a = iy M + ix: xi = (xi[ix], xi[iy]), w = w1[ix] w1[iy]).  The same
+// update as interface_cell without projections: first-order upwind transport with the wall
+// ghosts of Eqs. 8-9 (the wall density a flux balance over the cell's set), relaxation
+// towards w (rho + xi . j) (Eqs. 1, 5-7).  Interface cells of a tile are left to their own
+// kernel; idle lanes mirror the tile's first cell and store nothing.
+struct PlainArgs {
+    const int *toff;
+    const unsigned char *iface;   // [ncells] 1: a neighbour carries the other set
+    const double *h;
+    double *hn, *part;
+    int nx, ny, cavity;
+    double omega, b, u_bottom, u_top, inv_u_ref;   // b = 1 - omega
+    double inv_dx_wall, inv_dy_wall;   // 1 / sum_{xi > 0} xi w over the set, per axis
+    double xi[12], w1[12], nux[12], nuy[12];
+    double a0[144];                    // 1 - nu_x - nu_y per velocity a = iy M + ix
+};
 
-// Cells whose existing neighbours all carry the cell's own set (no interface face): the
-// same update as hybrid_step_kernel without projections.  A warp takes a task, a run of
-// consecutive cells of one set (contiguous in the packed state); a group of S.lanes lanes
-// takes a cell, lane g its velocities g, g + lanes, ...; the upwind values are read straight
-// from the neighbour cells, the wall densities and moments are sums over the group.
-__device__ void plain_task(const HybArgs &a, const int2 tk, int resid)
+template <int M, int G>
+struct PlainShape {
+    static constexpr int TPB = G >= 4 ? 1 : 4 / G;     // tiles per block
+    static constexpr int THREADS = 32 * G * TPB;
+};
+
+template <int M, int G>
+__global__ void __launch_bounds__(PlainShape<M, G>::THREADS) hybrid_plain_kernel(const PlainArgs p, const int2 *tiles,
+                                                                                int ntiles, int resid)
 {
-    const int lane = threadIdx.x & 31;
-    const HybTables &tb = *a.tab;
-    const HybSet &S = tb.set[a.half[tk.x] ? 0 : 1];
-    const int n = S.n, L = S.lanes;
-    const int sub = lane / L, g = lane - sub * L;
-    const bool on = sub < tk.y;
-    const int c = tk.x + (on ? sub : 0);         // idle groups repeat the first cell and store nothing
-    const int nx = a.nx, ny = a.ny, x = c % nx, y = c / nx;
-    const double *hc = a.h + a.off[c];
-    const bool cav = a.cavity != 0;
+    constexpr int TPB = PlainShape<M, G>::TPB, RPL = M / G, HALF = M / 2;
+    static_assert(M % G == 0 && M <= 12, "warps split the velocity rows evenly");
+    __shared__ double s_x[TPB][G][4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tl = warp / G, g = warp - tl * G;
+    const int t = (int)blockIdx.x * TPB + tl;
+    int c0 = 0, k = 0;
+    if (t < ntiles) {
+        const int2 T = tiles[t];
+        c0 = T.x;
+        k = T.y;
+    }
+    const int cl = lane < k ? c0 + lane : c0;
+    const bool on = lane < k && !p.iface[cl];
+    const int nx = p.nx, ny = p.ny, x = cl % nx, y = cl / nx;
+    const bool cav = p.cavity != 0;
     const bool wl = cav && x == 0, wr = cav && x == nx - 1, wb = y == 0, wt = y == ny - 1;
-    const double *hl = (cav && !wl) ? a.h + a.off[c - 1] : hc;
-    const double *hr = (cav && !wr) ? a.h + a.off[c + 1] : hc;
-    const double *hd = !wb ? a.h + a.off[c - nx] : hc;
-    const double *hu = !wt ? a.h + a.off[c + nx] : hc;
-    double hv[HMAXPL];
-    double pw[4] = {0.0, 0.0, 0.0, 0.0};         // outflow through the bottom, top, left, right walls
-    const bool walls = __any_sync(0xffffffffu, wl || wr || wb || wt);
-#pragma unroll
-    for (int i = 0; i < HMAXPL; ++i) {
-        const int b = g + L * i;
-        hv[i] = 0.0;
-        if (b < n) {
-            const double v = hc[b];
-            hv[i] = v;
-            if (walls) {
-                const double ex = S.xi_x[b], ey = S.xi_y[b];
-                const int sgx = S.sx[b], sgy = S.sy[b];
-                if (sgy < 0) pw[0] -= ey * v;
-                if (sgy > 0) pw[1] += ey * v;
-                if (sgx < 0) pw[2] -= ex * v;
-                if (sgx > 0) pw[3] += ex * v;
-            }
-        }
-    }
-    // wall densities (Eq. 9 as a flux balance over the cell's set)
+    const double *h = p.h;
+    const long oc = p.toff[cl];
+    // same-set neighbours of a plain cell; an idle or interface lane reads only its own cell
+    const long ol = (on && cav && !wl) ? p.toff[cl - 1] : oc;
+    const long orr = (on && cav && !wr) ? p.toff[cl + 1] : oc;
+    const long od = (on && !wb) ? p.toff[cl - nx] : oc;
+    const long ou = (on && !wt) ? p.toff[cl + nx] : oc;
+
+    // ---- wall densities, where a lane of the block touches a wall ----
     double rw[4] = {0.0, 0.0, 0.0, 0.0};
-    if (walls) {
+    if (__syncthreads_or((int)(on && (wl || wr || wb || wt)))) {
+        double pw[4] = {0.0, 0.0, 0.0, 0.0};     // outflow through the bottom, top, left, right walls
 #pragma unroll
-        for (int f = 0; f < 4; ++f) rw[f] = group_sum(pw[f], L) / (f < 2 ? S.d_y : S.d_x);
-    }
-    const double ub = a.u_bottom, ut = a.u_top;
-    double hs[HMAXPL];
-    double rho = 0.0, jx = 0.0, jy = 0.0;
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
 #pragma unroll
-    for (int i = 0; i < HMAXPL; ++i) {
-        const int b = g + L * i;
-        double v = 0.0;
-        if (b < n) {
-            const double ex = S.xi_x[b], ey = S.xi_y[b], wb_ = S.w[b];
-            const double h0 = hv[i];
-            const int sgx = S.sx[b], sgy = S.sy[b];
-            double hx = h0, nux = 0.0;
-            if (cav) {
-                if (sgx > 0) hx = wl ? wb_ * rw[2] : hl[b];          // side walls at rest
-                else if (sgx < 0) hx = wr ? wb_ * rw[3] : hr[b];
-                nux = S.nux[b];
+            for (int ix = 0; ix < M; ++ix) {
+                const double v = h[oc + (long)HST * (iy * M + ix)];
+                if (iy < HALF) pw[0] -= p.xi[iy] * v;
+                if (iy >= M - HALF) pw[1] += p.xi[iy] * v;
+                if (ix < HALF) pw[2] -= p.xi[ix] * v;
+                if (ix >= M - HALF) pw[3] += p.xi[ix] * v;
             }
-            double hy = h0;
-            if (sgy > 0) hy = wb ? wb_ * (rw[0] * (1.0 + ex * ub) + ex * ub / a.u_ref) : hd[b];
-            else if (sgy < 0) hy = wt ? wb_ * (rw[1] * (1.0 + ex * ut) + ex * ut / a.u_ref) : hu[b];
-            const double nuy = S.nuy[b];
-            v = h0 - nux * (h0 - hx) - nuy * (h0 - hy);
-            rho += v;
-            jx += ex * v;
-            jy += ey * v;
         }
-        hs[i] = v;
+        if (G > 1) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s_x[tl][g][f][lane] = pw[f];
+            __syncthreads();
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                pw[f] = 0.0;
+#pragma unroll
+                for (int q = 0; q < G; ++q) pw[f] += s_x[tl][q][f][lane];
+            }
+            __syncthreads();
+        }
+        rw[0] = pw[0] * p.inv_dy_wall;
+        rw[1] = pw[1] * p.inv_dy_wall;
+        rw[2] = pw[2] * p.inv_dx_wall;
+        rw[3] = pw[3] * p.inv_dx_wall;
     }
-    rho = group_sum(rho, L);
-    jx = group_sum(jx, L);
-    jy = group_sum(jy, L);
-    double *out = a.hn + a.off[c];
+
+    // ---- transport and moment sums ----
+    // h* = (1 - nu_x - nu_y) h + nu_x h_x + nu_y h_y; rho, j_x per velocity, j_y per row.
+    // The wall ghosts are formed only in tiles that touch a wall (WALLS): as a select in every
+    // tile they doubled the FP64 operations of the step.
+    const double ub = p.u_bottom, ut = p.u_top;
+    double hs[RPL * M];
+    double R = 0.0, X = 0.0, Y = 0.0;
+    auto transport = [&](auto walls_tag) {
+        constexpr bool WALLS = decltype(walls_tag)::value;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int iy = g * RPL + r;
+            const double nuy = p.nuy[iy], wy = p.w1[iy];
+            double Rr = 0.0, Xr = 0.0;
+#pragma unroll
+            for (int ix = 0; ix < M; ++ix) {
+                const long a = (long)HST * (iy * M + ix);
+                const double h0 = h[oc + a];
+                double v = p.a0[iy * M + ix] * h0;
+                if (cav) {
+                    double hx = h0;
+                    if (ix >= M - HALF) {
+                        hx = h[ol + a];
+                        if (WALLS && wl) hx = p.w1[ix] * wy * rw[2];          // side walls at rest
+                    } else if (ix < HALF) {
+                        hx = h[orr + a];
+                        if (WALLS && wr) hx = p.w1[ix] * wy * rw[3];
+                    }
+                    v = fma(p.nux[ix], hx, v);
+                }
+                double hy = h0;
+                if (iy >= M - HALF) {
+                    hy = h[od + a];
+                    if (WALLS && wb) hy = p.w1[ix] * wy * (rw[0] * (1.0 + p.xi[ix] * ub) + p.xi[ix] * ub * p.inv_u_ref);
+                } else if (iy < HALF) {
+                    hy = h[ou + a];
+                    if (WALLS && wt) hy = p.w1[ix] * wy * (rw[1] * (1.0 + p.xi[ix] * ut) + p.xi[ix] * ut * p.inv_u_ref);
+                }
+                v = fma(nuy, hy, v);
+                hs[r * M + ix] = v;
+                Rr += v;
+                Xr = fma(p.xi[ix], v, Xr);
+            }
+            R += Rr;
+            X += Xr;
+            Y = fma(p.xi[iy], Rr, Y);
+        }
+    };
+    if (__any_sync(0xffffffffu, wl || wr || wb || wt)) transport(std::true_type{});
+    else transport(std::false_type{});
+    if (G > 1) {
+        s_x[tl][g][0][lane] = R;
+        s_x[tl][g][1][lane] = X;
+        s_x[tl][g][2][lane] = Y;
+        __syncthreads();
+        R = X = Y = 0.0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            R += s_x[tl][q][0][lane];
+            X += s_x[tl][q][1][lane];
+            Y += s_x[tl][q][2][lane];
+        }
+        __syncthreads();
+    }
+
+    // ---- relaxation h' = (1 - omega) h* + omega w (rho + xi . j), store, residual sums ----
     double pd = 0.0, pn = 0.0;
 #pragma unroll
-    for (int i = 0; i < HMAXPL; ++i) {
-        const int b = g + L * i;
-        if (b < n) {
-            const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
-            const double o = hs[i] - a.omega * (hs[i] - heq);
-            if (on) out[b] = o;
+    for (int r = 0; r < RPL; ++r) {
+        const int iy = g * RPL + r;
+        const double ow = p.omega * p.w1[iy];
+        const double A = ow * fma(p.xi[iy], Y, R), B = ow * X;
+#pragma unroll
+        for (int ix = 0; ix < M; ++ix) {
+            const long a = (long)HST * (iy * M + ix);
+            const double o = fma(p.b, hs[r * M + ix], p.w1[ix] * fma(p.xi[ix], B, A));
+            if (on) p.hn[oc + a] = o;
             if (resid) {
-                const double d = o - hv[i];
+                const double d = o - h[oc + a];
                 pd += d * d;
                 pn += o * o;
             }
         }
     }
     if (resid) {
-        pd = group_sum(pd, L);
-        pn = group_sum(pn, L);
+        if (G > 1) {
+            s_x[tl][g][0][lane] = pd;
+            s_x[tl][g][1][lane] = pn;
+            __syncthreads();
+            pd = pn = 0.0;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                pd += s_x[tl][q][0][lane];
+                pn += s_x[tl][q][1][lane];
+            }
+        }
         if (on && g == 0) {
-            a.part[2 * c] = pd;
-            a.part[2 * c + 1] = pn;
+            p.part[2 * cl] = pd;
+            p.part[2 * cl + 1] = pn;
         }
     }
 }
 
-// One step: the blocks for the interface cells first (their projections are the long
-// latency chains), then the plain-cell tasks, so that both run side by side in one launch.
-__global__ void __launch_bounds__(32 * HWARPS, 5) hybrid_step_kernel(const HybArgs a, const int *cells, int ncells,
-                                                                   const int2 *tasks, int ntasks, double dt, double dx,
-                                                                   double dy, int resid)
+// Warps per tile of the plain-cell kernel for a set of M nodes per axis (the velocity rows of
+// a cell split over them: at most 36 velocities a lane)
+constexpr int plain_warps(int m) { return m <= 6 ? 1 : (m == 8 ? 4 : (m == 10 ? 5 : 6)); }
+
+template <int M>
+cudaError_t launch_plain_m(const PlainArgs &pa, const int2 *tiles, int ntiles, int resid, cudaStream_t st)
 {
-    __shared__ HybShared sh;
-    const int wi = threadIdx.x >> 5;
-    const int if_blocks = (ncells + HWARPS - 1) / HWARPS;
-    if ((int)blockIdx.x < if_blocks) {
-        const int ci = (int)blockIdx.x * HWARPS + wi;
-        if (ci < ncells) interface_cell(a, sh, wi, cells[ci], dt, dx, dy, resid);     // whole warps
-    } else {
-        const int t = ((int)blockIdx.x - if_blocks) * HWARPS + wi;
-        if (t < ntasks) plain_task(a, tasks[t], resid);
+    constexpr int G = plain_warps(M);
+    using Sh = PlainShape<M, G>;
+    hybrid_plain_kernel<M, G><<<(ntiles + Sh::TPB - 1) / Sh::TPB, Sh::THREADS, 0, st>>>(pa, tiles, ntiles, resid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(int m, const PlainArgs &pa, const int2 *tiles, int ntiles, int resid, cudaStream_t st)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    switch (m) {
+    case 2: return launch_plain_m<2>(pa, tiles, ntiles, resid, st);
+    case 3: return launch_plain_m<3>(pa, tiles, ntiles, resid, st);
+    case 4: return launch_plain_m<4>(pa, tiles, ntiles, resid, st);
+    case 5: return launch_plain_m<5>(pa, tiles, ntiles, resid, st);
+    case 6: return launch_plain_m<6>(pa, tiles, ntiles, resid, st);
+    case 8: return launch_plain_m<8>(pa, tiles, ntiles, resid, st);
+    case 10: return launch_plain_m<10>(pa, tiles, ntiles, resid, st);
+    case 12: return launch_plain_m<12>(pa, tiles, ntiles, resid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// packed (cell after cell) <-> tiled state: one thread per value
+__global__ void hybrid_relayout_kernel(const double *src, double *dst, const int *poff, const int *toff, int ncells,
+                                       int to_tiled)
+{
+    const long total = poff[ncells];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        // the cell of packed value i: poff is ascending
+        int lo = 0, hi = ncells - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (poff[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const long b = i - poff[lo], ti = toff[lo] + (long)HST * b;
+        if (to_tiled) dst[ti] = src[i];
+        else dst[i] = src[ti];
     }
 }
 
@@ -458,8 +592,8 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const Hyb
     double up = 0.0, dn = 0.0;
     if (k > 0 && k < a.ny && a.half[k - 1] != a.half[k]) {
         const HybSet &H = tb.set[0];
-        neighbour_values(a, k - 1, 0, lo);
-        neighbour_values(a, k, 0, hi);
+        neighbour_values(a, k - 1, 0, lo, sh.tmp[wi]);
+        neighbour_values(a, k, 0, hi, sh.tmp[wi]);
         double mu[3], md[3];
         face_moments(H, lo, 1, true, mu);
         face_moments(H, hi, 1, false, md);
@@ -468,7 +602,9 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const Hyb
     } else {
         const int cb = k == 0 ? 0 : k - 1, ca = k == a.ny ? a.ny - 1 : k;
         const HybSet &Sb = tb.set[a.half[cb] ? 0 : 1], &Sa = tb.set[a.half[ca] ? 0 : 1];
-        const double *vb = a.h + a.off[cb], *va = a.h + a.off[ca];
+        double *vb = sh.own[wi], *va = sh.tmp[wi];
+        gather_cell(a.h, a.toff, cb, Sb.n, vb);
+        gather_cell(a.h, a.toff, ca, Sa.n, va);
         if (k == 0) {
             wall_ghost(a, Sb, vb, 0, lo);
             vb = lo;
@@ -496,12 +632,13 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_velocity_kernel(const HybA
     const int c = blockIdx.x * HWARPS + (threadIdx.x >> 5);
     if (c >= a.nx * a.ny) return;
     const HybSet &S = a.tab->set[a.half[c] ? 0 : 1];
-    const double *hc = a.h + a.off[c];
+    const double *hc = a.h + a.toff[c];
     double s0 = 0.0, sx = 0.0, sy = 0.0;
     for (int b = lane; b < S.n; b += 32) {
-        s0 += hc[b];
-        sx += S.xi_x[b] * hc[b];
-        sy += S.xi_y[b] * hc[b];
+        const double v = hc[(long)HST * b];
+        s0 += v;
+        sx += S.xi_x[b] * v;
+        sy += S.xi_y[b] * v;
     }
     s0 = warp_sum(s0);
     sx = warp_sum(sx);
@@ -518,20 +655,24 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_velocity_kernel(const HybA
 struct lbm_hybrid {
     int geom, n_half, nx, ny, layer, order;
     double kn, u_bottom, u_top, cfl, dt, dx, dy, omega, u_ref;
-    std::vector<int> off;
+    std::vector<int> off;    // [ncells + 1] packed (host-transfer) offsets, cell after cell
     std::vector<unsigned char> half;
-    long unknowns;
+    long unknowns;           // values of the packed state
+    long tiled;              // doubles of the tiled device state (tiles padded to 32 cells)
     cudaStream_t stream;
     HybTables *d_tab;
-    int *d_off;
-    unsigned char *d_half;
+    int *d_poff, *d_toff;    // packed offsets; tiled offsets of velocity 0 of each cell
+    unsigned char *d_half, *d_iface;
     double *d_h[2], *d_part, *d_res;
     double *h_res;           // pinned
     int cur;
     bool have_resid;
-    int n_if, n_tasks;       // interface cells, plain-cell tasks
-    int *d_if;               // [n_if] cells with an interface face
-    int2 *d_tasks;           // [n_tasks] runs of plain cells (first cell, count)
+    int n_if;                // cells with an interface face
+    int *d_if;               // [n_if]
+    int n_tiles[2];          // tiles of the half-range (0) and full-range (1) set holding a plain cell
+    int2 *d_tiles[2];        // (first cell, count)
+    int m1[2];               // nodes per axis of each set
+    double x1[2][12], w1[2][12], inv_dx_wall[2], inv_dy_wall[2];
 };
 
 namespace {
@@ -577,7 +718,7 @@ HybArgs hargs(const lbm_hybrid *hb)
     HybArgs a;
     std::memset(&a, 0, sizeof a);
     a.tab = hb->d_tab;
-    a.off = hb->d_off;
+    a.toff = hb->d_toff;
     a.half = hb->d_half;
     a.h = hb->d_h[hb->cur];
     a.hn = hb->d_h[hb->cur ^ 1];
@@ -591,6 +732,37 @@ HybArgs hargs(const lbm_hybrid *hb)
     a.u_top = hb->u_top;
     a.u_ref = hb->u_ref;
     return a;
+}
+
+PlainArgs plain_args(const lbm_hybrid *hb, int set)
+{
+    PlainArgs p;
+    std::memset(&p, 0, sizeof p);
+    p.toff = hb->d_toff;
+    p.iface = hb->d_iface;
+    p.h = hb->d_h[hb->cur];
+    p.hn = hb->d_h[hb->cur ^ 1];
+    p.part = hb->d_part;
+    p.nx = hb->nx;
+    p.ny = hb->ny;
+    p.cavity = hb->geom == LBM_CAVITY;
+    p.omega = hb->omega;
+    p.b = 1.0 - hb->omega;
+    p.u_bottom = hb->u_bottom;
+    p.u_top = hb->u_top;
+    p.inv_u_ref = 1.0 / hb->u_ref;
+    p.inv_dx_wall = hb->inv_dx_wall[set];
+    p.inv_dy_wall = hb->inv_dy_wall[set];
+    for (int i = 0; i < hb->m1[set]; ++i) {
+        p.xi[i] = hb->x1[set][i];
+        p.w1[i] = hb->w1[set][i];
+        p.nux[i] = p.cavity ? std::fabs(p.xi[i]) * hb->dt / hb->dx : 0.0;
+        p.nuy[i] = std::fabs(p.xi[i]) * hb->dt / hb->dy;
+    }
+    const int m = hb->m1[set];
+    for (int iy = 0; iy < m; ++iy)
+        for (int ix = 0; ix < m; ++ix) p.a0[iy * m + ix] = 1.0 - p.nux[ix] - p.nuy[iy];
+    return p;
 }
 
 }  // namespace
@@ -625,14 +797,14 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     hb->cur = 0;
     hb->have_resid = false;
     hb->d_tab = nullptr;
-    hb->d_off = nullptr;
-    hb->d_half = nullptr;
+    hb->d_poff = hb->d_toff = nullptr;
+    hb->d_half = hb->d_iface = nullptr;
     hb->d_h[0] = hb->d_h[1] = nullptr;
     hb->d_part = hb->d_res = nullptr;
     hb->h_res = nullptr;
     hb->d_if = nullptr;
-    hb->d_tasks = nullptr;
-    hb->n_if = hb->n_tasks = 0;
+    hb->d_tiles[0] = hb->d_tiles[1] = nullptr;
+    hb->n_if = hb->n_tiles[0] = hb->n_tiles[1] = 0;
     std::vector<HybTables> tabv(1);     // ~130 KB: on the heap, zero-initialised
     HybTables &tab = tabv[0];
     double my_h = 0, my_f = 0;
@@ -640,6 +812,17 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
         !fill_set(tab.set[1], LBM_FULL_RANGE_GH, n_half, hb->order, my_f)) {
         delete hb;
         return hfail(LBM_EINVAL, "quadrature construction failed");
+    }
+    for (int t = 0; t < 2; ++t) {       // the sets' 1-D rules for the plain-cell kernel
+        std::vector<double> x, w;
+        lbm_rule_1d(t == 0 ? LBM_HALF_RANGE_GH : LBM_FULL_RANGE_GH, n_half, x, w);
+        hb->m1[t] = (int)x.size();
+        for (int i = 0; i < hb->m1[t]; ++i) {
+            hb->x1[t][i] = x[i];
+            hb->w1[t][i] = w[i];
+        }
+        hb->inv_dx_wall[t] = 1.0 / tab.set[t].d_x;
+        hb->inv_dy_wall[t] = 1.0 / tab.set[t].d_y;
     }
     double f = 1.0;
     for (int k = 0; k <= HMAXQ; ++k) {
@@ -683,31 +866,43 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     }
     hb->off[nc] = (int)o;
     hb->unknowns = o;
-    // cells with a neighbour in the other set go to the projecting kernel; runs of the others
-    // (consecutive cells of one set, as many as fill a warp) to the plain-cell kernel
+    // cells with a neighbour in the other set go to the projecting kernel, the others to the
+    // plain-cell kernel; the tiled layout: runs of consecutive cells of one set cut into tiles
+    // of up to 32 cells, each tile n_set x 32 doubles
     std::vector<int> if_cells;
-    std::vector<int2> tasks;
+    std::vector<unsigned char> iface(nc, 0);
     for (long c = 0; c < nc; ++c) {
         const int x = (int)(c % nx), y = (int)(c / nx);
         const unsigned char hc_ = hb->half[c];
-        bool iface = (y > 0 && hb->half[c - nx] != hc_) || (y < ny - 1 && hb->half[c + nx] != hc_);
-        if (geom == LBM_CAVITY) iface = iface || (x > 0 && hb->half[c - 1] != hc_) || (x < nx - 1 && hb->half[c + 1] != hc_);
-        if (iface) {
-            if_cells.push_back((int)c);
-            continue;
-        }
-        const int cap = 32 / tab.set[hc_ ? 0 : 1].lanes;
-        if (!tasks.empty()) {
-            int2 &tk = tasks.back();
-            if (tk.x + tk.y == c && hb->half[tk.x] == hc_ && tk.y < cap) {
-                ++tk.y;
-                continue;
-            }
-        }
-        tasks.push_back(make_int2((int)c, 1));
+        bool ifc = (y > 0 && hb->half[c - nx] != hc_) || (y < ny - 1 && hb->half[c + nx] != hc_);
+        if (geom == LBM_CAVITY) ifc = ifc || (x > 0 && hb->half[c - 1] != hc_) || (x < nx - 1 && hb->half[c + 1] != hc_);
+        iface[c] = ifc ? 1 : 0;
+        if (ifc) if_cells.push_back((int)c);
     }
+    std::vector<int> toff(nc);
+    std::vector<int2> tiles[2];
+    long tb = 0;
+    for (long c = 0; c < nc;) {
+        const int set = hb->half[c] ? 0 : 1;
+        long e = c + 1;
+        while (e < nc && e - c < 32 && hb->half[e] == hb->half[c]) ++e;
+        bool plain = false;
+        for (long q = c; q < e; ++q) {
+            toff[q] = (int)std::min(tb + (q - c), (long)INT_MAX);     // checked below
+            plain |= !iface[q];
+        }
+        if (plain) tiles[set].push_back(make_int2((int)c, (int)(e - c)));
+        tb += 32L * tab.set[set].n;
+        c = e;
+    }
+    if (tb > (long)INT_MAX) {
+        delete hb;
+        return hfail(LBM_EINVAL, "too many unknowns for the hybrid's 32-bit cell offsets");
+    }
+    hb->tiled = tb;
     hb->n_if = (int)if_cells.size();
-    hb->n_tasks = (int)tasks.size();
+    hb->n_tiles[0] = (int)tiles[0].size();
+    hb->n_tiles[1] = (int)tiles[1].size();
     // dt = cfl / (max|xi_x|/dx + max|xi_y|/dy) over the sets present (the x term dropped for
     // the Couette column), dt <= Kn; the sets are symmetric, so max |xi_x| = max |xi_y|
     hb->dy = 1.0 / ny;
@@ -726,25 +921,33 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     const double ur = std::max(std::fabs(u_bottom), std::fabs(u_top));
     hb->u_ref = ur > 0 ? ur : 1.0;
     cudaError_t e = cudaMalloc(&hb->d_tab, sizeof(HybTables));
-    if (e == cudaSuccess) e = cudaMalloc(&hb->d_off, sizeof(int) * (nc + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_poff, sizeof(int) * (nc + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_toff, sizeof(int) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_half, nc);
-    if (e == cudaSuccess) e = cudaMalloc(&hb->d_h[0], sizeof(double) * o);
-    if (e == cudaSuccess) e = cudaMalloc(&hb->d_h[1], sizeof(double) * o);
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_iface, nc);
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_h[0], sizeof(double) * tb);
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_h[1], sizeof(double) * tb);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_part, sizeof(double) * 2 * nc);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_res, sizeof(double) * 2);
     if (e == cudaSuccess) e = cudaMallocHost(&hb->h_res, sizeof(double) * 2);
     if (e == cudaSuccess && hb->n_if > 0) e = cudaMalloc(&hb->d_if, sizeof(int) * hb->n_if);
-    if (e == cudaSuccess && hb->n_tasks > 0) e = cudaMalloc(&hb->d_tasks, sizeof(int2) * hb->n_tasks);
+    for (int t = 0; t < 2 && e == cudaSuccess; ++t)
+        if (hb->n_tiles[t] > 0) e = cudaMalloc(&hb->d_tiles[t], sizeof(int2) * hb->n_tiles[t]);
     if (e == cudaSuccess && hb->n_if > 0)
         e = cudaMemcpyAsync(hb->d_if, if_cells.data(), sizeof(int) * hb->n_if, cudaMemcpyHostToDevice, hb->stream);
-    if (e == cudaSuccess && hb->n_tasks > 0)
-        e = cudaMemcpyAsync(hb->d_tasks, tasks.data(), sizeof(int2) * hb->n_tasks, cudaMemcpyHostToDevice,
-                            hb->stream);
+    for (int t = 0; t < 2 && e == cudaSuccess; ++t)
+        if (hb->n_tiles[t] > 0)
+            e = cudaMemcpyAsync(hb->d_tiles[t], tiles[t].data(), sizeof(int2) * hb->n_tiles[t], cudaMemcpyHostToDevice,
+                                hb->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb->d_tab, &tab, sizeof tab, cudaMemcpyHostToDevice, hb->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hb->d_off, hb->off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, hb->stream);
+        e = cudaMemcpyAsync(hb->d_poff, hb->off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, hb->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb->d_toff, toff.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, hb->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb->d_half, hb->half.data(), nc, cudaMemcpyHostToDevice, hb->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hb->d_h[0], 0, sizeof(double) * o, hb->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb->d_iface, iface.data(), nc, cudaMemcpyHostToDevice, hb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hb->d_h[0], 0, sizeof(double) * tb, hb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hb->d_h[1], 0, sizeof(double) * tb, hb->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
     if (e != cudaSuccess) {
         lbm_hybrid_destroy(hb);
@@ -760,14 +963,17 @@ void lbm_hybrid_destroy(lbm_hybrid *hb)
     if (hb->stream) cudaStreamSynchronize(hb->stream);
     else cudaDeviceSynchronize();
     cudaFree(hb->d_tab);
-    cudaFree(hb->d_off);
+    cudaFree(hb->d_poff);
+    cudaFree(hb->d_toff);
     cudaFree(hb->d_half);
+    cudaFree(hb->d_iface);
     cudaFree(hb->d_h[0]);
     cudaFree(hb->d_h[1]);
     cudaFree(hb->d_part);
     cudaFree(hb->d_res);
     cudaFree(hb->d_if);
-    cudaFree(hb->d_tasks);
+    cudaFree(hb->d_tiles[0]);
+    cudaFree(hb->d_tiles[1]);
     if (hb->h_res) cudaFreeHost(hb->h_res);
     delete hb;
 }
@@ -785,11 +991,21 @@ lbm_status lbm_hybrid_query(const lbm_hybrid *hb, long *unknowns, int *half_rang
     return LBM_OK;
 }
 
+// packed <-> tiled through the other state buffer (it is rewritten by the next step)
+static cudaError_t hybrid_relayout(lbm_hybrid *hb, const double *src, double *dst, bool to_tiled)
+{
+    const int nc = hb->nx * hb->ny;
+    const int blocks = (int)std::min<long>((hb->unknowns + 255) / 256, 152L * 16);
+    hybrid_relayout_kernel<<<blocks, 256, 0, hb->stream>>>(src, dst, hb->d_poff, hb->d_toff, nc, to_tiled ? 1 : 0);
+    return cudaGetLastError();
+}
+
 lbm_status lbm_hybrid_set_state(lbm_hybrid *hb, const double *h)
 {
     if (!hb || !h) return hfail(LBM_EINVAL, "NULL argument");
-    cudaError_t e = cudaMemcpyAsync(hb->d_h[hb->cur], h, sizeof(double) * hb->unknowns, cudaMemcpyHostToDevice,
-                                    hb->stream);
+    double *scratch = hb->d_h[hb->cur ^ 1];
+    cudaError_t e = cudaMemcpyAsync(scratch, h, sizeof(double) * hb->unknowns, cudaMemcpyHostToDevice, hb->stream);
+    if (e == cudaSuccess) e = hybrid_relayout(hb, scratch, hb->d_h[hb->cur], true);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
     hb->have_resid = false;
     return e == cudaSuccess ? LBM_OK : hfail(LBM_ECUDA, std::string("setting the state: ") + cudaGetErrorString(e));
@@ -798,8 +1014,10 @@ lbm_status lbm_hybrid_set_state(lbm_hybrid *hb, const double *h)
 lbm_status lbm_hybrid_get_state(lbm_hybrid *hb, double *h)
 {
     if (!hb || !h) return hfail(LBM_EINVAL, "NULL argument");
-    cudaError_t e = cudaMemcpyAsync(h, hb->d_h[hb->cur], sizeof(double) * hb->unknowns, cudaMemcpyDeviceToHost,
-                                    hb->stream);
+    double *scratch = hb->d_h[hb->cur ^ 1];
+    cudaError_t e = hybrid_relayout(hb, hb->d_h[hb->cur], scratch, false);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, scratch, sizeof(double) * hb->unknowns, cudaMemcpyDeviceToHost, hb->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
     return e == cudaSuccess ? LBM_OK : hfail(LBM_ECUDA, std::string("reading the state: ") + cudaGetErrorString(e));
 }
@@ -810,10 +1028,14 @@ lbm_status lbm_hybrid_step(lbm_hybrid *hb, long nsteps)
     const int nc = hb->nx * hb->ny;
     for (long s = 0; s < nsteps; ++s) {
         const bool last = s == nsteps - 1;
-        const int blocks = (hb->n_if + HWARPS - 1) / HWARPS + (hb->n_tasks + HWARPS - 1) / HWARPS;
-        hybrid_step_kernel<<<blocks, 32 * HWARPS, 0, hb->stream>>>(hargs(hb), hb->d_if, hb->n_if, hb->d_tasks,
-                                                                   hb->n_tasks, hb->dt, hb->dx, hb->dy, last ? 1 : 0);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = cudaSuccess;
+        if (hb->n_if > 0) {
+            hybrid_interface_kernel<<<(hb->n_if + HWARPS - 1) / HWARPS, 32 * HWARPS, 0, hb->stream>>>(
+                hargs(hb), hb->d_if, hb->n_if, hb->dt, hb->dx, hb->dy, last ? 1 : 0);
+            e = cudaGetLastError();
+        }
+        for (int t = 0; t < 2 && e == cudaSuccess; ++t)
+            e = launch_plain(hb->m1[t], plain_args(hb, t), hb->d_tiles[t], hb->n_tiles[t], last ? 1 : 0, hb->stream);
         if (e == cudaSuccess && last) {
             hybrid_finalize_kernel<<<1, HFIN, 0, hb->stream>>>(hb->d_part, nc, hb->d_res);
             e = cudaGetLastError();

@@ -5,7 +5,8 @@ driven cavity's centre-line profile, lid drag D and vortex flow rate G (Fig. 4, 
 
     python -m paper_1308_0692_gb300.experiments {kn_sweep,couette_kn1,cavity_table2,order,hybrid,cavity_hybrid,rates} --out r.json
 
-`rates` times the step of a large cavity (default 2048 x 2048) for every velocity set of
+`hybrid_rates` times the hybrid cavity per layer width against the plain FP64 half-range
+march.  `rates` times the step of a large cavity (default 2048 x 2048) for every velocity set of
 these comparisons, both precisions and every compiled kernel variant, and reports the
 fastest with its algorithmic HBM rate (8 B per update in FP32, 16 B in FP64).
 
@@ -345,14 +346,55 @@ def step_rates(side: int = 2048, sets=("D2Q9", "D2Q^h_16", "D2Q_16", "D2Q^h_64",
     return out
 
 
+def hybrid_rates(side: int = 1024, layers=(0, 4, 16, 64), n_half: int = 4, steps: int = 50):
+    """Step time of the hybrid half-range / full-range cavity (Kn 0.1, lid 0.01) per layer
+    width, and of the plain FP64 half-range march of the same cavity, timed with CUDA events
+    on the objects' streams after ten warm-up steps."""
+    import torch
+    out = {"side": side, "n_half": n_half, "steps": steps, "runs": []}
+    for layer in layers:
+        stream = torch.cuda.Stream()
+        hb = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n_half, side, side, 0.1, 0.0, 0.01, layer, stream=stream)
+        q = lbm.lbm_hybrid_query(hb)
+        lbm.lbm_hybrid_step(hb, 10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lbm.lbm_hybrid_step(hb, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        hb.close()
+        out["runs"].append({"layer": layer, "unknowns": q["unknowns"], "half_range_cells": q["half_range_cells"],
+                            "ms_per_step": ms, "unknowns_per_s": q["unknowns"] / ms * 1e3})
+    vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
+    stream = torch.cuda.Stream()
+    sim = lbm.lbm_init(vs, lbm.make_problem(lbm.LBM_CAVITY, side, side, 0.1, 0.0, 0.01, prec=lbm.LBM_FP64,
+                                            residual_every=100), stream=stream)
+    lbm.lbm_step(sim, 10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lbm.lbm_step(sim, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sim.close()
+    nvel = (2 * n_half) ** 2
+    out["plain_half_range_fp64"] = {"unknowns": side * side * nvel, "ms_per_step": ms,
+                                    "unknowns_per_s": side * side * nvel / ms * 1e3}
+    out["summary"] = {f"layer {r['layer']}": round(r["ms_per_step"], 4) for r in out["runs"]}
+    out["summary"]["plain half-range"] = round(ms, 4)
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["kn_sweep", "couette_kn1", "cavity_table2", "order", "hybrid",
-                                           "cavity_hybrid", "rates"])
+                                           "cavity_hybrid", "rates", "hybrid_rates"])
     ap.add_argument("--out", required=True)
-    ap.add_argument("--side", type=int, default=None, help="cavity side (128; rates: 2048)")
+    ap.add_argument("--side", type=int, default=None, help="cavity side (128; rates: 2048; hybrid_rates: 1024)")
+    ap.add_argument("--layers", default=None, help="hybrid_rates: comma-separated layer widths (0,4,16,64)")
     args = ap.parse_args(argv)
     if args.study == "kn_sweep":
         r = kn_sweep()
@@ -366,6 +408,9 @@ def main(argv=None):
         r = cavity_hybrid_study(side=args.side or 128)
     elif args.study == "rates":
         r = step_rates(side=args.side or 2048)
+    elif args.study == "hybrid_rates":
+        layers = tuple(int(v) for v in args.layers.split(",")) if args.layers else (0, 4, 16, 64)
+        r = hybrid_rates(side=args.side or 1024, layers=layers)
     else:
         r = cavity_table2_study(side=args.side or 128)
     with open(args.out, "w") as f:

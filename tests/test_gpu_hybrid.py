@@ -102,6 +102,8 @@ CAVITY_CASES = [
     (3, 7, 6, 0.2, 0.0, 0.01, 0),      # all full-range
     (3, 7, 6, 0.2, 0.0, 0.01, 4),      # all half-range
     (6, 6, 5, 0.5, 0.0, 0.01, 1),      # 144 half-range velocities next to 36 full-range
+    (4, 96, 80, 0.1, 0.002, 0.01, 5),  # tiles of 32 cells, runs across row ends, tiles mixing interface cells
+    (5, 70, 37, 0.3, 0.0, 0.01, 3),    # odd full-range set, ragged tiles
 ]
 
 
