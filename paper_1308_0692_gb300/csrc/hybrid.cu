@@ -301,16 +301,6 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     }
 }
 
-// Cells with an interface face, one warp each (their projections are long latency chains;
-// launched first, so that the plain-cell kernel's blocks fill in beside them).
-__global__ void __launch_bounds__(32 * HWARPS, 4) hybrid_interface_kernel(const HybArgs a, const int *cells, int ncells,
-                                                                         double dt, double dx, double dy, int resid)
-{
-    __shared__ HybShared sh;
-    const int wi = threadIdx.x >> 5;
-    const int ci = (int)blockIdx.x * HWARPS + wi;
-    if (ci < ncells) interface_cell(a, sh, wi, cells[ci], dt, dx, dy, resid);     // whole warps
-}
 
 // Plain cells of one set: all their existing neighbours carry the same set.  Per tile (up to
 // 32 consecutive cells of the set) G warps, lane p the tile's cell p, warp g the velocity rows
@@ -332,22 +322,21 @@ struct PlainArgs {
     double a0[144];                    // 1 - nu_x - nu_y per velocity a = iy M + ix
 };
 
+// blocks of four warps: G warps per tile, 4 / G tiles per block
 template <int M, int G>
 struct PlainShape {
-    static constexpr int TPB = G >= 4 ? 1 : 4 / G;     // tiles per block
-    static constexpr int THREADS = 32 * G * TPB;
+    static constexpr int TPB = HWARPS / G;             // tiles per block
+    static_assert(M % G == 0 && HWARPS % G == 0 && M <= 12, "warps split the velocity rows evenly");
 };
 
 template <int M, int G>
-__global__ void __launch_bounds__(PlainShape<M, G>::THREADS) hybrid_plain_kernel(const PlainArgs p, const int2 *tiles,
-                                                                                int ntiles, int resid)
+__device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tiles, int ntiles, int bid, int resid,
+                                            double (*s_x)[G][4][32])
 {
     constexpr int TPB = PlainShape<M, G>::TPB, RPL = M / G, HALF = M / 2;
-    static_assert(M % G == 0 && M <= 12, "warps split the velocity rows evenly");
-    __shared__ double s_x[TPB][G][4][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tl = warp / G, g = warp - tl * G;
-    const int t = (int)blockIdx.x * TPB + tl;
+    const int t = bid * TPB + tl;
     int c0 = 0, k = 0;
     if (t < ntiles) {
         const int2 T = tiles[t];
@@ -504,31 +493,65 @@ __global__ void __launch_bounds__(PlainShape<M, G>::THREADS) hybrid_plain_kernel
     }
 }
 
-// Warps per tile of the plain-cell kernel for a set of M nodes per axis (the velocity rows of
-// a cell split over them: at most 36 velocities a lane)
-constexpr int plain_warps(int m) { return m <= 6 ? 1 : (m == 8 ? 4 : (m == 10 ? 5 : 6)); }
+// Warps per half-range tile (2N nodes per axis): four where they split the velocity rows
+// evenly, else two; a full-range tile (N nodes) takes one warp
+__host__ __device__ constexpr int half_warps(int n) { return (2 * n) % 4 == 0 ? 4 : 2; }
 
-template <int M>
-cudaError_t launch_plain_m(const PlainArgs &pa, const int2 *tiles, int ntiles, int resid, cudaStream_t st)
+// One step, one launch: the blocks for the interface cells first (one warp per cell: their
+// projections are long latency chains), then those for the half-range and the full-range
+// tiles, so that all three run side by side.
+struct StepLists {
+    const int *cells;          // interface cells
+    int ncells;
+    const int2 *tiles[2];      // half-range, full-range tiles with a plain cell
+    int ntiles[2];
+};
+
+template <int N>
+__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, const PlainArgs ph, const PlainArgs pf,
+                                                                   const StepLists L, double dt, double dx, double dy,
+                                                                   int resid)
 {
-    constexpr int G = plain_warps(M);
-    using Sh = PlainShape<M, G>;
-    hybrid_plain_kernel<M, G><<<(ntiles + Sh::TPB - 1) / Sh::TPB, Sh::THREADS, 0, st>>>(pa, tiles, ntiles, resid);
+    constexpr int GH = half_warps(N);
+    __shared__ union {
+        HybShared sh;
+        double hx[HWARPS / GH][GH][4][32];
+        double fx[HWARPS][1][4][32];
+    } u;
+    const int bid = (int)blockIdx.x;
+    const int ifb = (L.ncells + HWARPS - 1) / HWARPS;
+    const int hbk = (L.ntiles[0] + HWARPS / GH - 1) / (HWARPS / GH);
+    if (bid < ifb) {
+        const int wi = threadIdx.x >> 5, ci = bid * HWARPS + wi;
+        if (ci < L.ncells) interface_cell(a, u.sh, wi, L.cells[ci], dt, dx, dy, resid);    // whole warps
+    } else if (bid < ifb + hbk) {
+        plain_tiles<2 * N, GH>(ph, L.tiles[0], L.ntiles[0], bid - ifb, resid, u.hx);
+    } else {
+        plain_tiles<N, 1>(pf, L.tiles[1], L.ntiles[1], bid - ifb - hbk, resid, u.fx);
+    }
+}
+
+template <int N>
+cudaError_t launch_step_n(const HybArgs &a, const PlainArgs &ph, const PlainArgs &pf, const StepLists &L, double dt,
+                          double dx, double dy, int resid, cudaStream_t st)
+{
+    constexpr int GH = half_warps(N);
+    const int blocks = (L.ncells + HWARPS - 1) / HWARPS + (L.ntiles[0] + HWARPS / GH - 1) / (HWARPS / GH) +
+                       (L.ntiles[1] + HWARPS - 1) / HWARPS;
+    if (blocks == 0) return cudaSuccess;
+    hybrid_step_kernel<N><<<blocks, 32 * HWARPS, 0, st>>>(a, ph, pf, L, dt, dx, dy, resid);
     return cudaGetLastError();
 }
 
-cudaError_t launch_plain(int m, const PlainArgs &pa, const int2 *tiles, int ntiles, int resid, cudaStream_t st)
+cudaError_t launch_hybrid_step(int n, const HybArgs &a, const PlainArgs &ph, const PlainArgs &pf, const StepLists &L,
+                               double dt, double dx, double dy, int resid, cudaStream_t st)
 {
-    if (ntiles <= 0) return cudaSuccess;
-    switch (m) {
-    case 2: return launch_plain_m<2>(pa, tiles, ntiles, resid, st);
-    case 3: return launch_plain_m<3>(pa, tiles, ntiles, resid, st);
-    case 4: return launch_plain_m<4>(pa, tiles, ntiles, resid, st);
-    case 5: return launch_plain_m<5>(pa, tiles, ntiles, resid, st);
-    case 6: return launch_plain_m<6>(pa, tiles, ntiles, resid, st);
-    case 8: return launch_plain_m<8>(pa, tiles, ntiles, resid, st);
-    case 10: return launch_plain_m<10>(pa, tiles, ntiles, resid, st);
-    case 12: return launch_plain_m<12>(pa, tiles, ntiles, resid, st);
+    switch (n) {
+    case 2: return launch_step_n<2>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 3: return launch_step_n<3>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 4: return launch_step_n<4>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 5: return launch_step_n<5>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 6: return launch_step_n<6>(a, ph, pf, L, dt, dx, dy, resid, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -555,11 +578,15 @@ __global__ void hybrid_relayout_kernel(const double *src, double *dst, const int
 // residual sums over the cells: one block, each thread a fixed stride of cells, then a fixed
 // tree (the same order every call)
 constexpr int HFIN = 1024;
+// stage 1: block b sums the pairs of cells [b HCHUNK, (b + 1) HCHUNK) into out[2 b..2 b + 1];
+// stage 2 (one block) sums those partials: the same fixed order at every call
+constexpr int HCHUNK = 8192;
 __global__ void __launch_bounds__(HFIN) hybrid_finalize_kernel(const double *part, int ncells, double *out)
 {
     __shared__ double sd[HFIN], sn[HFIN];
     double d = 0.0, n = 0.0;
-    for (int j = threadIdx.x; j < ncells; j += HFIN) {
+    const int first = (int)blockIdx.x * HCHUNK, last = min(ncells, first + HCHUNK);
+    for (int j = first + (int)threadIdx.x; j < last; j += HFIN) {
         d += part[2 * j];
         n += part[2 * j + 1];
     }
@@ -574,8 +601,8 @@ __global__ void __launch_bounds__(HFIN) hybrid_finalize_kernel(const double *par
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out[0] = sd[0];
-        out[1] = sn[0];
+        out[2 * blockIdx.x] = sd[0];
+        out[2 * blockIdx.x + 1] = sn[0];
     }
 }
 
@@ -928,7 +955,8 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_h[0], sizeof(double) * tb);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_h[1], sizeof(double) * tb);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_part, sizeof(double) * 2 * nc);
-    if (e == cudaSuccess) e = cudaMalloc(&hb->d_res, sizeof(double) * 2);
+    // the residual sums and the first-stage partials of their reduction
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_res, sizeof(double) * 2 * (1 + (nc + HCHUNK - 1) / HCHUNK));
     if (e == cudaSuccess) e = cudaMallocHost(&hb->h_res, sizeof(double) * 2);
     if (e == cudaSuccess && hb->n_if > 0) e = cudaMalloc(&hb->d_if, sizeof(int) * hb->n_if);
     for (int t = 0; t < 2 && e == cudaSuccess; ++t)
@@ -1028,17 +1056,23 @@ lbm_status lbm_hybrid_step(lbm_hybrid *hb, long nsteps)
     const int nc = hb->nx * hb->ny;
     for (long s = 0; s < nsteps; ++s) {
         const bool last = s == nsteps - 1;
-        cudaError_t e = cudaSuccess;
-        if (hb->n_if > 0) {
-            hybrid_interface_kernel<<<(hb->n_if + HWARPS - 1) / HWARPS, 32 * HWARPS, 0, hb->stream>>>(
-                hargs(hb), hb->d_if, hb->n_if, hb->dt, hb->dx, hb->dy, last ? 1 : 0);
-            e = cudaGetLastError();
+        StepLists L;
+        L.cells = hb->d_if;
+        L.ncells = hb->n_if;
+        for (int t = 0; t < 2; ++t) {
+            L.tiles[t] = hb->d_tiles[t];
+            L.ntiles[t] = hb->n_tiles[t];
         }
-        for (int t = 0; t < 2 && e == cudaSuccess; ++t)
-            e = launch_plain(hb->m1[t], plain_args(hb, t), hb->d_tiles[t], hb->n_tiles[t], last ? 1 : 0, hb->stream);
+        cudaError_t e = launch_hybrid_step(hb->n_half, hargs(hb), plain_args(hb, 0), plain_args(hb, 1), L, hb->dt, hb->dx,
+                                           hb->dy, last ? 1 : 0, hb->stream);
         if (e == cudaSuccess && last) {
-            hybrid_finalize_kernel<<<1, HFIN, 0, hb->stream>>>(hb->d_part, nc, hb->d_res);
+            const int nb1 = (nc + HCHUNK - 1) / HCHUNK;
+            hybrid_finalize_kernel<<<nb1, HFIN, 0, hb->stream>>>(hb->d_part, nc, hb->d_res + 2);
             e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                hybrid_finalize_kernel<<<1, HFIN, 0, hb->stream>>>(hb->d_res + 2, nb1, hb->d_res);
+                e = cudaGetLastError();
+            }
         }
         if (e != cudaSuccess) return hfail(LBM_ECUDA, std::string("launching the hybrid step: ") + cudaGetErrorString(e));
         hb->cur ^= 1;
