@@ -410,12 +410,16 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
  * equals it: mass and momentum are conserved exactly, a state at rest stays at rest.
  * layer = 0 is the full-range march, a layer beyond the half width the half-range march.
  * dt = cfl / (max|xi_x|/dx + max|xi_y|/dy) over the sets present (the x term dropped for the
- * column), dt <= Kn.  FP64 throughout.  State layout (host FP64, packed): cell after cell
+ * column), dt <= Kn.  FP64 by default; lbm_hybrid_set_precision(hb, LBM_FP32_PERTURB) switches
+ * the march to FP32 storage and arithmetic (interface cells computed in FP64 from the FP32
+ * values) with the mixed-precision refinement of lbm_hybrid_refine (below).  State layout
+ * (host FP64, packed): cell after cell
  * (c = y * nx + x), each cell's values in its own set's order a = iy * M + ix (M = 2N
  * half-range, N full-range); lbm_hybrid_query reports the total.  2 <= N <= 6.
  * lbm_hybrid_step is stream-ordered; lbm_hybrid_residual returns ||h^{n+1} - h^n|| /
  * ||h^{n+1}|| of the last step taken (synchronises); lbm_hybrid_solve marches in blocks of
- * `every` steps until that residual is below tol or max_steps; lbm_hybrid_velocity writes
+ * `every` steps until that residual is below tol or max_steps (in FP32 also once it has not
+ * improved by 1 % over 20 checks: the FP32 rounding floor); lbm_hybrid_velocity writes
  * (u_x, u_y) per cell (host [ny][nx]); lbm_hybrid_face_flux (column only) the x-momentum
  * flux through the ny + 1 faces (host [ny + 1], interface faces in the half-range
  * evaluation; LBM_EUNSUPPORTED for the cavity). */
@@ -431,6 +435,19 @@ lbm_status lbm_hybrid_residual(lbm_hybrid *hb, double *r);
 lbm_status lbm_hybrid_solve(lbm_hybrid *hb, double tol, long max_steps, int every, long *steps, double *r);
 lbm_status lbm_hybrid_velocity(lbm_hybrid *hb, double *ux, double *uy);
 lbm_status lbm_hybrid_face_flux(lbm_hybrid *hb, double *pxy);
+/* Precision of the hybrid march: LBM_FP64 (default) or LBM_FP32_PERTURB; the current state is
+ * converted.  Allocates the FP32 buffers on first use.  Not in the paper. */
+lbm_status lbm_hybrid_set_precision(lbm_hybrid *hb, int prec);
+/* Mixed-precision refinement of the FP32 hybrid state (the hybrid form of lbm_solve's
+ * sweeps; not in the paper): D = M64(h) - h by one FP64 hybrid step of the stored state,
+ * the correction march delta <- L(delta) + D of the homogeneous problem (walls without
+ * driving) in FP32 from delta = 0, residual checks every `every` steps, until its per-step
+ * change is below refine_tol ||M64(h)|| (refine_tol <= 0: 0.1 tol) or has not improved by
+ * 1 % over 20 checks or max_steps, then h += delta; at most max_sweeps sweeps, stopping once
+ * the FP64 defect ||D|| / ||M64(h)|| is below tol or stops halving.  Outputs the correction
+ * steps taken and that defect (may be NULL).  LBM_EINVAL for an FP64 hybrid. */
+lbm_status lbm_hybrid_refine(lbm_hybrid *hb, double tol, int max_sweeps, double refine_tol, long max_steps, int every,
+                             long *correction_steps, double *defect);
 
 /* ---- Learned warm start (not in the paper) ----
  * A coordinate MLP 4 -> 256 -> 256 -> 256 -> 6 with exact-erf GELU maps the features

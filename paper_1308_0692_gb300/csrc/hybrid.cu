@@ -71,14 +71,20 @@ struct HybArgs {
     const HybTables *tab;
     const int *toff;           // [ncells] velocity 0 of each cell in the tiled state
     const unsigned char *half; // [ncells] 1: half-range cell
-    const double *h;
-    double *hn;
+    const void *h;             // state (FP64, or FP32 in the mixed-precision march), tiled
+    void *hn;
+    const float *src;          // correction march: the FP64 defect added after relaxation (else NULL)
     double *part;              // [2 ncells] residual sums per cell (||h^{n+1} - h^n||^2, ||h^{n+1}||^2)
     int nx, ny, order;
     int cavity;                // 0: Couette column (no x transport), 1: cavity (walls on all faces)
+    int homogeneous;           // correction march: the walls' driving terms dropped
     double omega;
     double u_bottom, u_top, u_ref;
 };
+
+// a * b + c rounded once, in the arithmetic type
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -121,24 +127,27 @@ __device__ void project_warp(const HybTables &tb, int ti, const double *h, doubl
     __syncwarp();
 }
 
-// The n values of cell k into buf[0..n) (a warp; velocity b at toff[k] + HST b).
-__device__ void gather_cell(const double *h, const int *toff, int k, int n, double *buf)
+// The n values of cell k into buf[0..n) in FP64 (a warp; velocity b at toff[k] + HST b).
+template <typename TS>
+__device__ void gather_cell(const TS *h, const int *toff, int k, int n, double *buf)
 {
-    const double *hk = h + toff[k];
-    for (int b = threadIdx.x & 31; b < n; b += 32) buf[b] = hk[(long)HST * b];
+    const TS *hk = h + toff[k];
+    for (int b = threadIdx.x & 31; b < n; b += 32) buf[b] = (double)hk[(long)HST * b];
     __syncwarp();
 }
 
 // Values of neighbour cell k as seen by a cell of set sj, into buf[0..S.n): its own values
 // for the same set, else their projection (tmp: the neighbour's values, gathered first).
+template <typename TS>
 __device__ void neighbour_values(const HybArgs &a, int k, int sj, double *buf, double *tmp)
 {
     const HybTables &tb = *a.tab;
     const int sk = a.half[k] ? 0 : 1;
+    const TS *h = static_cast<const TS *>(a.h);
     if (sk == sj) {
-        gather_cell(a.h, a.toff, k, tb.set[sj].n, buf);
+        gather_cell(h, a.toff, k, tb.set[sj].n, buf);
     } else {
-        gather_cell(a.h, a.toff, k, tb.set[sk].n, tmp);
+        gather_cell(h, a.toff, k, tb.set[sk].n, tmp);
         project_warp(tb, sk, tmp, buf);
     }
 }
@@ -160,7 +169,7 @@ __device__ void wall_ghost(const HybArgs &a, const HybSet &S, const double *hc, 
     const double u = face == 0 ? a.u_bottom : face == 1 ? a.u_top : 0.0;
     for (int b = lane; b < S.n; b += 32) {
         const double xt = face < 2 ? S.xi_x[b] : S.xi_y[b];
-        buf[b] = S.w[b] * (rho_w * (1.0 + xt * u) + xt * u / a.u_ref);
+        buf[b] = S.w[b] * (rho_w * (1.0 + xt * u) + (a.homogeneous ? 0.0 : xt * u / a.u_ref));
     }
     __syncwarp();
 }
@@ -193,6 +202,7 @@ struct HybShared {
 
 // A cell with an interface face (a neighbour in the other set): one warp, warp `wi` of the
 // block's shared buffers.
+template <typename TS>
 __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, double dt, double dx, double dy,
                                int resid)
 {
@@ -203,7 +213,7 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     const HybSet &S = tb.set[sj];
     const HybSet &H = tb.set[0];
     double *hc = sh.own[wi];
-    gather_cell(a.h, a.toff, c, S.n, hc);
+    gather_cell(static_cast<const TS *>(a.h), a.toff, c, S.n, hc);
     double *tmp = sh.tmp[wi];
     const int x = c % nx, y = c / nx;
     double(*nbv)[HMAXV] = sh.nbv[wi];
@@ -211,14 +221,14 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     // the four faces as (axis, side, neighbour or -1)
     int nbc[4] = {-1, -1, -1, -1};
     if (a.cavity) {
-        if (x > 0) neighbour_values(a, nbc[0] = c - 1, sj, nbv[0], tmp);
+        if (x > 0) neighbour_values<TS>(a, nbc[0] = c - 1, sj, nbv[0], tmp);
         else wall_ghost(a, S, hc, 2, nbv[0]);
-        if (x < nx - 1) neighbour_values(a, nbc[1] = c + 1, sj, nbv[1], tmp);
+        if (x < nx - 1) neighbour_values<TS>(a, nbc[1] = c + 1, sj, nbv[1], tmp);
         else wall_ghost(a, S, hc, 3, nbv[1]);
     }
-    if (y > 0) neighbour_values(a, nbc[2] = c - nx, sj, nbv[2], tmp);
+    if (y > 0) neighbour_values<TS>(a, nbc[2] = c - nx, sj, nbv[2], tmp);
     else wall_ghost(a, S, hc, 0, nbv[2]);
-    if (y < ny - 1) neighbour_values(a, nbc[3] = c + nx, sj, nbv[3], tmp);
+    if (y < ny - 1) neighbour_values<TS>(a, nbc[3] = c + nx, sj, nbv[3], tmp);
     else wall_ghost(a, S, hc, 1, nbv[3]);
     // interface faces of a full-range cell: mass and momentum exchange made equal to the
     // half-range evaluation of the face
@@ -233,7 +243,7 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
             if (nbc[f] < 0 || !a.half[nbc[f]]) continue;
             const int axis = f >> 1;
             const bool lower = (f & 1) == 0;                  // the neighbour is on the lower side
-            neighbour_values(a, nbc[f], 0, nb, tmp);          // its own half-range values
+            neighbour_values<TS>(a, nbc[f], 0, nb, tmp);      // its own half-range values
             double up[3], dn[3], got[3], sent[3];
             face_moments(H, lower ? nb : ph, axis, true, up);
             face_moments(H, lower ? ph : nb, axis, false, dn);
@@ -275,19 +285,22 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     rho = warp_sum(rho);
     jx = warp_sum(jx);
     jy = warp_sum(jy);
-    double *out = a.hn + a.toff[c];
+    TS *out = static_cast<TS *>(a.hn) + a.toff[c];
+    constexpr bool MIXED = std::is_same<TS, float>::value;      // the FP32 march's correction sweeps
+    const float *src = (MIXED && a.src) ? a.src + a.toff[c] : nullptr;
     double pd = 0.0, pn = 0.0;
 #pragma unroll
     for (int i = 0; i < (HMAXV + 31) / 32; ++i) {
         const int b = lane + 32 * i;
         if (b < S.n) {
             const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
-            const double o = hs[i] - a.omega * (hs[i] - heq);
-            out[(long)HST * b] = o;
+            double o = hs[i] - a.omega * (hs[i] - heq);
+            if (MIXED && src) o += (double)src[(long)HST * b];
+            out[(long)HST * b] = (TS)o;
             if (resid) {
-                const double d = o - hc[b];
+                const double os = (double)(TS)o, d = os - hc[b];
                 pd += d * d;
-                pn += o * o;
+                pn += os * os;
             }
         }
     }
@@ -310,16 +323,20 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
 // ghosts of Eqs. 8-9 (the wall density a flux balance over the cell's set), relaxation
 // towards w (rho + xi . j) (Eqs. 1, 5-7).  Interface cells of a tile are left to their own
 // kernel; idle lanes mirror the tile's first cell and store nothing.
+// TC: the arithmetic and storage type (double for the FP64 march, float for the FP32 one)
+template <typename TC>
 struct PlainArgs {
     const int *toff;
     const unsigned char *iface;   // [ncells] 1: a neighbour carries the other set
-    const double *h;
-    double *hn, *part;
-    int nx, ny, cavity;
-    double omega, b, u_bottom, u_top, inv_u_ref;   // b = 1 - omega
+    const TC *h;
+    TC *hn;
+    double *part;
+    const float *src;             // correction march: the defect added after relaxation (else NULL)
+    int nx, ny, cavity, homogeneous;
+    TC omega, b, u_bottom, u_top, inv_u_ref;   // b = 1 - omega
     double inv_dx_wall, inv_dy_wall;   // 1 / sum_{xi > 0} xi w over the set, per axis
-    double xi[12], w1[12], nux[12], nuy[12];
-    double a0[144];                    // 1 - nu_x - nu_y per velocity a = iy M + ix
+    TC xi[12], w1[12], nux[12], nuy[12];
+    TC a0[144];                        // 1 - nu_x - nu_y per velocity a = iy M + ix
 };
 
 // blocks of four warps: G warps per tile, 4 / G tiles per block
@@ -329,8 +346,8 @@ struct PlainShape {
     static_assert(M % G == 0 && HWARPS % G == 0 && M <= 12, "warps split the velocity rows evenly");
 };
 
-template <int M, int G>
-__device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tiles, int ntiles, int bid, int resid,
+template <int M, int G, typename TC>
+__device__ __forceinline__ void plain_tiles(const PlainArgs<TC> &p, const int2 *tiles, int ntiles, int bid, int resid,
                                             double (*s_x)[G][4][32])
 {
     constexpr int TPB = PlainShape<M, G>::TPB, RPL = M / G, HALF = M / 2;
@@ -348,7 +365,7 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
     const int nx = p.nx, ny = p.ny, x = cl % nx, y = cl / nx;
     const bool cav = p.cavity != 0;
     const bool wl = cav && x == 0, wr = cav && x == nx - 1, wb = y == 0, wt = y == ny - 1;
-    const double *h = p.h;
+    const TC *h = p.h;
     const long oc = p.toff[cl];
     // same-set neighbours of a plain cell; an idle or interface lane reads only its own cell
     const long ol = (on && cav && !wl) ? p.toff[cl - 1] : oc;
@@ -357,7 +374,7 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
     const long ou = (on && !wt) ? p.toff[cl + nx] : oc;
 
     // ---- wall densities, where a lane of the block touches a wall ----
-    double rw[4] = {0.0, 0.0, 0.0, 0.0};
+    TC rw[4] = {0, 0, 0, 0};
     if (__syncthreads_or((int)(on && (wl || wr || wb || wt)))) {
         double pw[4] = {0.0, 0.0, 0.0, 0.0};     // outflow through the bottom, top, left, right walls
 #pragma unroll
@@ -365,11 +382,12 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
             const int iy = g * RPL + r;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                const double v = h[oc + (long)HST * (iy * M + ix)];
-                if (iy < HALF) pw[0] -= p.xi[iy] * v;
-                if (iy >= M - HALF) pw[1] += p.xi[iy] * v;
-                if (ix < HALF) pw[2] -= p.xi[ix] * v;
-                if (ix >= M - HALF) pw[3] += p.xi[ix] * v;
+                // products in the arithmetic type, sums in FP64
+                const TC v = h[oc + (long)HST * (iy * M + ix)];
+                if (iy < HALF) pw[0] -= (double)(p.xi[iy] * v);
+                if (iy >= M - HALF) pw[1] += (double)(p.xi[iy] * v);
+                if (ix < HALF) pw[2] -= (double)(p.xi[ix] * v);
+                if (ix >= M - HALF) pw[3] += (double)(p.xi[ix] * v);
             }
         }
         if (G > 1) {
@@ -384,33 +402,37 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
             }
             __syncthreads();
         }
-        rw[0] = pw[0] * p.inv_dy_wall;
-        rw[1] = pw[1] * p.inv_dy_wall;
-        rw[2] = pw[2] * p.inv_dx_wall;
-        rw[3] = pw[3] * p.inv_dx_wall;
+        rw[0] = (TC)(pw[0] * p.inv_dy_wall);
+        rw[1] = (TC)(pw[1] * p.inv_dy_wall);
+        rw[2] = (TC)(pw[2] * p.inv_dx_wall);
+        rw[3] = (TC)(pw[3] * p.inv_dx_wall);
     }
 
     // ---- transport and moment sums ----
     // h* = (1 - nu_x - nu_y) h + nu_x h_x + nu_y h_y; rho, j_x per velocity, j_y per row.
     // The wall ghosts are formed only in tiles that touch a wall (WALLS): as a select in every
     // tile they doubled the FP64 operations of the step.
-    const double ub = p.u_bottom, ut = p.u_top;
-    double hs[RPL * M];
-    double R = 0.0, X = 0.0, Y = 0.0;
+    // the FP32 march's correction sweeps drop the walls' driving terms and add the defect; the
+    // FP64 march never does (its kernels carry no code for it)
+    constexpr bool MIXED = std::is_same<TC, float>::value;
+    const TC ub = p.u_bottom, ut = p.u_top;
+    const TC drive = (MIXED && p.homogeneous) ? TC(0) : p.inv_u_ref;     // the walls' driving term
+    TC hs[RPL * M];
+    TC R = 0, X = 0, Y = 0;
     auto transport = [&](auto walls_tag) {
         constexpr bool WALLS = decltype(walls_tag)::value;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
-            const double nuy = p.nuy[iy], wy = p.w1[iy];
-            double Rr = 0.0, Xr = 0.0;
+            const TC nuy = p.nuy[iy], wy = p.w1[iy];
+            TC Rr = 0, Xr = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
                 const long a = (long)HST * (iy * M + ix);
-                const double h0 = h[oc + a];
-                double v = p.a0[iy * M + ix] * h0;
+                const TC h0 = h[oc + a];
+                TC v = p.a0[iy * M + ix] * h0;
                 if (cav) {
-                    double hx = h0;
+                    TC hx = h0;
                     if (ix >= M - HALF) {
                         hx = h[ol + a];
                         if (WALLS && wl) hx = p.w1[ix] * wy * rw[2];          // side walls at rest
@@ -418,24 +440,24 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
                         hx = h[orr + a];
                         if (WALLS && wr) hx = p.w1[ix] * wy * rw[3];
                     }
-                    v = fma(p.nux[ix], hx, v);
+                    v = fma_(p.nux[ix], hx, v);
                 }
-                double hy = h0;
+                TC hy = h0;
                 if (iy >= M - HALF) {
                     hy = h[od + a];
-                    if (WALLS && wb) hy = p.w1[ix] * wy * (rw[0] * (1.0 + p.xi[ix] * ub) + p.xi[ix] * ub * p.inv_u_ref);
+                    if (WALLS && wb) hy = p.w1[ix] * wy * (rw[0] * (TC(1) + p.xi[ix] * ub) + p.xi[ix] * ub * drive);
                 } else if (iy < HALF) {
                     hy = h[ou + a];
-                    if (WALLS && wt) hy = p.w1[ix] * wy * (rw[1] * (1.0 + p.xi[ix] * ut) + p.xi[ix] * ut * p.inv_u_ref);
+                    if (WALLS && wt) hy = p.w1[ix] * wy * (rw[1] * (TC(1) + p.xi[ix] * ut) + p.xi[ix] * ut * drive);
                 }
-                v = fma(nuy, hy, v);
+                v = fma_(nuy, hy, v);
                 hs[r * M + ix] = v;
                 Rr += v;
-                Xr = fma(p.xi[ix], v, Xr);
+                Xr = fma_(p.xi[ix], v, Xr);
             }
             R += Rr;
             X += Xr;
-            Y = fma(p.xi[iy], Rr, Y);
+            Y = fma_(p.xi[iy], Rr, Y);
         }
     };
     if (__any_sync(0xffffffffu, wl || wr || wb || wt)) transport(std::true_type{});
@@ -445,30 +467,32 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
         s_x[tl][g][1][lane] = X;
         s_x[tl][g][2][lane] = Y;
         __syncthreads();
-        R = X = Y = 0.0;
+        R = X = Y = 0;
 #pragma unroll
         for (int q = 0; q < G; ++q) {
-            R += s_x[tl][q][0][lane];
-            X += s_x[tl][q][1][lane];
-            Y += s_x[tl][q][2][lane];
+            R += (TC)s_x[tl][q][0][lane];
+            X += (TC)s_x[tl][q][1][lane];
+            Y += (TC)s_x[tl][q][2][lane];
         }
         __syncthreads();
     }
 
     // ---- relaxation h' = (1 - omega) h* + omega w (rho + xi . j), store, residual sums ----
-    double pd = 0.0, pn = 0.0;
+    TC pd = 0, pn = 0;
+    const float *src = (MIXED && p.src) ? p.src + oc : nullptr;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         const int iy = g * RPL + r;
-        const double ow = p.omega * p.w1[iy];
-        const double A = ow * fma(p.xi[iy], Y, R), B = ow * X;
+        const TC ow = p.omega * p.w1[iy];
+        const TC A = ow * fma_(p.xi[iy], Y, R), B = ow * X;
 #pragma unroll
         for (int ix = 0; ix < M; ++ix) {
             const long a = (long)HST * (iy * M + ix);
-            const double o = fma(p.b, hs[r * M + ix], p.w1[ix] * fma(p.xi[ix], B, A));
+            TC o = fma_(p.b, hs[r * M + ix], p.w1[ix] * fma_(p.xi[ix], B, A));
+            if (MIXED && src) o += (TC)src[a];
             if (on) p.hn[oc + a] = o;
             if (resid) {
-                const double d = o - h[oc + a];
+                const TC d = o - h[oc + a];
                 pd += d * d;
                 pn += o * o;
             }
@@ -476,19 +500,21 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs &p, const int2 *tile
     }
     if (resid) {
         if (G > 1) {
-            s_x[tl][g][0][lane] = pd;
-            s_x[tl][g][1][lane] = pn;
+            s_x[tl][g][0][lane] = (double)pd;
+            s_x[tl][g][1][lane] = (double)pn;
             __syncthreads();
-            pd = pn = 0.0;
+            double sd = 0.0, sn = 0.0;
 #pragma unroll
             for (int q = 0; q < G; ++q) {
-                pd += s_x[tl][q][0][lane];
-                pn += s_x[tl][q][1][lane];
+                sd += s_x[tl][q][0][lane];
+                sn += s_x[tl][q][1][lane];
             }
+            pd = (TC)sd;
+            pn = (TC)sn;
         }
         if (on && g == 0) {
-            p.part[2 * cl] = pd;
-            p.part[2 * cl + 1] = pn;
+            p.part[2 * cl] = (double)pd;
+            p.part[2 * cl + 1] = (double)pn;
         }
     }
 }
@@ -507,10 +533,10 @@ struct StepLists {
     int ntiles[2];
 };
 
-template <int N>
-__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, const PlainArgs ph, const PlainArgs pf,
-                                                                   const StepLists L, double dt, double dx, double dy,
-                                                                   int resid)
+template <int N, typename TS>
+__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, const PlainArgs<TS> ph,
+                                                                   const PlainArgs<TS> pf, const StepLists L, double dt,
+                                                                   double dx, double dy, int resid)
 {
     constexpr int GH = half_warps(N);
     __shared__ union {
@@ -523,7 +549,7 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs 
     const int hbk = (L.ntiles[0] + HWARPS / GH - 1) / (HWARPS / GH);
     if (bid < ifb) {
         const int wi = threadIdx.x >> 5, ci = bid * HWARPS + wi;
-        if (ci < L.ncells) interface_cell(a, u.sh, wi, L.cells[ci], dt, dx, dy, resid);    // whole warps
+        if (ci < L.ncells) interface_cell<TS>(a, u.sh, wi, L.cells[ci], dt, dx, dy, resid);    // whole warps
     } else if (bid < ifb + hbk) {
         plain_tiles<2 * N, GH>(ph, L.tiles[0], L.ntiles[0], bid - ifb, resid, u.hx);
     } else {
@@ -531,33 +557,88 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs 
     }
 }
 
-template <int N>
-cudaError_t launch_step_n(const HybArgs &a, const PlainArgs &ph, const PlainArgs &pf, const StepLists &L, double dt,
-                          double dx, double dy, int resid, cudaStream_t st)
+template <int N, typename TS>
+cudaError_t launch_step_n(const HybArgs &a, const PlainArgs<TS> &ph, const PlainArgs<TS> &pf, const StepLists &L,
+                          double dt, double dx, double dy, int resid, cudaStream_t st)
 {
     constexpr int GH = half_warps(N);
     const int blocks = (L.ncells + HWARPS - 1) / HWARPS + (L.ntiles[0] + HWARPS / GH - 1) / (HWARPS / GH) +
                        (L.ntiles[1] + HWARPS - 1) / HWARPS;
     if (blocks == 0) return cudaSuccess;
-    hybrid_step_kernel<N><<<blocks, 32 * HWARPS, 0, st>>>(a, ph, pf, L, dt, dx, dy, resid);
+    hybrid_step_kernel<N, TS><<<blocks, 32 * HWARPS, 0, st>>>(a, ph, pf, L, dt, dx, dy, resid);
     return cudaGetLastError();
 }
 
-cudaError_t launch_hybrid_step(int n, const HybArgs &a, const PlainArgs &ph, const PlainArgs &pf, const StepLists &L,
-                               double dt, double dx, double dy, int resid, cudaStream_t st)
+template <typename TS>
+cudaError_t launch_hybrid_step(int n, const HybArgs &a, const PlainArgs<TS> &ph, const PlainArgs<TS> &pf,
+                               const StepLists &L, double dt, double dx, double dy, int resid, cudaStream_t st)
 {
     switch (n) {
-    case 2: return launch_step_n<2>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 3: return launch_step_n<3>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 4: return launch_step_n<4>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 5: return launch_step_n<5>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 6: return launch_step_n<6>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 2: return launch_step_n<2, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 3: return launch_step_n<3, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 4: return launch_step_n<4, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 5: return launch_step_n<5, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 6: return launch_step_n<6, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-// packed (cell after cell) <-> tiled state: one thread per value
-__global__ void hybrid_relayout_kernel(const double *src, double *dst, const int *poff, const int *toff, int ncells,
+// elementwise over the tiled state (padding included): float <-> double, y += x, and the FP64
+// defect d = m - h as float with its sums over the cells' values (packed index i -> cell by
+// binary search over poff, as the relayout)
+__global__ void hybrid_f32_to_f64_kernel(const float *x, double *y, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] = x[i];
+}
+
+__global__ void hybrid_f64_to_f32_kernel(const double *x, float *y, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] = (float)x[i];
+}
+
+__global__ void hybrid_add_f32_kernel(float *y, const float *x, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] += x[i];
+}
+
+__global__ void __launch_bounds__(256) hybrid_defect_kernel(const double *m, const float *h, float *d, const int *poff,
+                                                            const int *toff, int ncells, double *sums)
+{
+    __shared__ double sd[256], sn[256];
+    const long total = poff[ncells];
+    double a = 0.0, b = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = ncells - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (poff[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const long ti = toff[lo] + (long)HST * (i - poff[lo]);
+        const double mv = m[ti], dv = mv - (double)h[ti];
+        d[ti] = (float)dv;
+        a += dv * dv;
+        b += mv * mv;
+    }
+    sd[threadIdx.x] = a;
+    sn[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sd[threadIdx.x] += sd[threadIdx.x + w];
+            sn[threadIdx.x] += sn[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sums[2 * blockIdx.x] = sd[0];
+        sums[2 * blockIdx.x + 1] = sn[0];
+    }
+}
+
+// packed FP64 (cell after cell) <-> tiled state of type TS: one thread per value
+template <typename TS>
+__global__ void hybrid_relayout_kernel(const void *src, void *dst, const int *poff, const int *toff, int ncells,
                                        int to_tiled)
 {
     const long total = poff[ncells];
@@ -570,8 +651,8 @@ __global__ void hybrid_relayout_kernel(const double *src, double *dst, const int
             else hi = mid - 1;
         }
         const long b = i - poff[lo], ti = toff[lo] + (long)HST * b;
-        if (to_tiled) dst[ti] = src[i];
-        else dst[i] = src[ti];
+        if (to_tiled) static_cast<TS *>(dst)[ti] = (TS)static_cast<const double *>(src)[i];
+        else static_cast<double *>(dst)[i] = (double)static_cast<const TS *>(src)[ti];
     }
 }
 
@@ -619,8 +700,8 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const Hyb
     double up = 0.0, dn = 0.0;
     if (k > 0 && k < a.ny && a.half[k - 1] != a.half[k]) {
         const HybSet &H = tb.set[0];
-        neighbour_values(a, k - 1, 0, lo, sh.tmp[wi]);
-        neighbour_values(a, k, 0, hi, sh.tmp[wi]);
+        neighbour_values<double>(a, k - 1, 0, lo, sh.tmp[wi]);
+        neighbour_values<double>(a, k, 0, hi, sh.tmp[wi]);
         double mu[3], md[3];
         face_moments(H, lo, 1, true, mu);
         face_moments(H, hi, 1, false, md);
@@ -630,8 +711,8 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const Hyb
         const int cb = k == 0 ? 0 : k - 1, ca = k == a.ny ? a.ny - 1 : k;
         const HybSet &Sb = tb.set[a.half[cb] ? 0 : 1], &Sa = tb.set[a.half[ca] ? 0 : 1];
         double *vb = sh.own[wi], *va = sh.tmp[wi];
-        gather_cell(a.h, a.toff, cb, Sb.n, vb);
-        gather_cell(a.h, a.toff, ca, Sa.n, va);
+        gather_cell(static_cast<const double *>(a.h), a.toff, cb, Sb.n, vb);
+        gather_cell(static_cast<const double *>(a.h), a.toff, ca, Sa.n, va);
         if (k == 0) {
             wall_ghost(a, Sb, vb, 0, lo);
             vb = lo;
@@ -659,7 +740,7 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_velocity_kernel(const HybA
     const int c = blockIdx.x * HWARPS + (threadIdx.x >> 5);
     if (c >= a.nx * a.ny) return;
     const HybSet &S = a.tab->set[a.half[c] ? 0 : 1];
-    const double *hc = a.h + a.toff[c];
+    const double *hc = static_cast<const double *>(a.h) + a.toff[c];
     double s0 = 0.0, sx = 0.0, sy = 0.0;
     for (int b = lane; b < S.n; b += 32) {
         const double v = hc[(long)HST * b];
@@ -700,6 +781,12 @@ struct lbm_hybrid {
     int2 *d_tiles[2];        // (first cell, count)
     int m1[2];               // nodes per axis of each set
     double x1[2][12], w1[2][12], inv_dx_wall[2], inv_dy_wall[2];
+    // FP32 march (lbm_hybrid_set_precision): tiled float buffers, the state ping-pong (0, 1),
+    // the FP64 defect (2) and the correction ping-pong (3, 4); the FP64 buffers d_h then serve
+    // as scratch (the defect's FP64 step, host transfers)
+    int prec;
+    float *d_f[5];
+    double *d_sums;          // [2 * HDEF] partial sums of the defect pass
 };
 
 namespace {
@@ -740,15 +827,23 @@ bool fill_set(HybSet &S, int kind, int n, int order, double &max_y)
     return true;
 }
 
-HybArgs hargs(const lbm_hybrid *hb)
+constexpr int HDEF = 152 * 4;   // blocks of the defect pass
+
+// Step arguments from state h to hn (the current ones by default), with an optional source
+// (correction march, homogeneous walls)
+HybArgs hargs(const lbm_hybrid *hb, const void *h = nullptr, void *hn = nullptr, const float *src = nullptr,
+              int homogeneous = 0)
 {
     HybArgs a;
     std::memset(&a, 0, sizeof a);
     a.tab = hb->d_tab;
     a.toff = hb->d_toff;
     a.half = hb->d_half;
-    a.h = hb->d_h[hb->cur];
-    a.hn = hb->d_h[hb->cur ^ 1];
+    const bool f32 = hb->prec == LBM_FP32_PERTURB;
+    a.h = h ? h : (f32 ? (const void *)hb->d_f[hb->cur] : (const void *)hb->d_h[hb->cur]);
+    a.hn = hn ? hn : (f32 ? (void *)hb->d_f[hb->cur ^ 1] : (void *)hb->d_h[hb->cur ^ 1]);
+    a.src = src;
+    a.homogeneous = homogeneous;
     a.part = hb->d_part;
     a.nx = hb->nx;
     a.ny = hb->ny;
@@ -761,36 +856,74 @@ HybArgs hargs(const lbm_hybrid *hb)
     return a;
 }
 
-PlainArgs plain_args(const lbm_hybrid *hb, int set)
+// the plain-cell kernel's arguments for set `set` in arithmetic type TC (coefficients formed
+// in FP64 and rounded once)
+template <typename TC>
+PlainArgs<TC> plain_args(const lbm_hybrid *hb, int set, const HybArgs &a)
 {
-    PlainArgs p;
+    PlainArgs<TC> p;
     std::memset(&p, 0, sizeof p);
     p.toff = hb->d_toff;
     p.iface = hb->d_iface;
-    p.h = hb->d_h[hb->cur];
-    p.hn = hb->d_h[hb->cur ^ 1];
+    p.h = static_cast<const TC *>(a.h);
+    p.hn = static_cast<TC *>(a.hn);
     p.part = hb->d_part;
+    p.src = a.src;
     p.nx = hb->nx;
     p.ny = hb->ny;
     p.cavity = hb->geom == LBM_CAVITY;
-    p.omega = hb->omega;
-    p.b = 1.0 - hb->omega;
-    p.u_bottom = hb->u_bottom;
-    p.u_top = hb->u_top;
-    p.inv_u_ref = 1.0 / hb->u_ref;
+    p.homogeneous = a.homogeneous;
+    p.omega = (TC)hb->omega;
+    p.b = (TC)(1.0 - hb->omega);
+    p.u_bottom = (TC)hb->u_bottom;
+    p.u_top = (TC)hb->u_top;
+    p.inv_u_ref = (TC)(1.0 / hb->u_ref);
     p.inv_dx_wall = hb->inv_dx_wall[set];
     p.inv_dy_wall = hb->inv_dy_wall[set];
-    for (int i = 0; i < hb->m1[set]; ++i) {
-        p.xi[i] = hb->x1[set][i];
-        p.w1[i] = hb->w1[set][i];
-        p.nux[i] = p.cavity ? std::fabs(p.xi[i]) * hb->dt / hb->dx : 0.0;
-        p.nuy[i] = std::fabs(p.xi[i]) * hb->dt / hb->dy;
-    }
     const int m = hb->m1[set];
+    double nux[12], nuy[12];
+    for (int i = 0; i < m; ++i) {
+        nux[i] = p.cavity ? std::fabs(hb->x1[set][i]) * hb->dt / hb->dx : 0.0;
+        nuy[i] = std::fabs(hb->x1[set][i]) * hb->dt / hb->dy;
+        p.xi[i] = (TC)hb->x1[set][i];
+        p.w1[i] = (TC)hb->w1[set][i];
+        p.nux[i] = (TC)nux[i];
+        p.nuy[i] = (TC)nuy[i];
+    }
     for (int iy = 0; iy < m; ++iy)
-        for (int ix = 0; ix < m; ++ix) p.a0[iy * m + ix] = 1.0 - p.nux[ix] - p.nuy[iy];
+        for (int ix = 0; ix < m; ++ix) p.a0[iy * m + ix] = (TC)(1.0 - nux[ix] - nuy[iy]);
     return p;
 }
+
+// One step from a.h into a.hn in precision TS (the residual partials when resid)
+template <typename TS>
+cudaError_t hybrid_launch(const lbm_hybrid *hb, const HybArgs &a, int resid)
+{
+    StepLists L;
+    L.cells = hb->d_if;
+    L.ncells = hb->n_if;
+    for (int t = 0; t < 2; ++t) {
+        L.tiles[t] = hb->d_tiles[t];
+        L.ntiles[t] = hb->n_tiles[t];
+    }
+    return launch_hybrid_step<TS>(hb->n_half, a, plain_args<TS>(hb, 0, a), plain_args<TS>(hb, 1, a), L, hb->dt, hb->dx,
+                                  hb->dy, resid, hb->stream);
+}
+
+// the two-stage reduction of the residual partials into d_res[0..1]
+cudaError_t hybrid_finalize(const lbm_hybrid *hb)
+{
+    const int nc = hb->nx * hb->ny, nb1 = (nc + HCHUNK - 1) / HCHUNK;
+    hybrid_finalize_kernel<<<nb1, HFIN, 0, hb->stream>>>(hb->d_part, nc, hb->d_res + 2);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        hybrid_finalize_kernel<<<1, HFIN, 0, hb->stream>>>(hb->d_res + 2, nb1, hb->d_res);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+int elem_blocks(long n) { return (int)std::max(1L, std::min<long>((n + 255) / 256, 152L * 16)); }
 
 }  // namespace
 
@@ -832,6 +965,9 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     hb->d_if = nullptr;
     hb->d_tiles[0] = hb->d_tiles[1] = nullptr;
     hb->n_if = hb->n_tiles[0] = hb->n_tiles[1] = 0;
+    hb->prec = LBM_FP64;
+    for (auto &f : hb->d_f) f = nullptr;
+    hb->d_sums = nullptr;
     std::vector<HybTables> tabv(1);     // ~130 KB: on the heap, zero-initialised
     HybTables &tab = tabv[0];
     double my_h = 0, my_f = 0;
@@ -1002,6 +1138,8 @@ void lbm_hybrid_destroy(lbm_hybrid *hb)
     cudaFree(hb->d_if);
     cudaFree(hb->d_tiles[0]);
     cudaFree(hb->d_tiles[1]);
+    for (auto f : hb->d_f) cudaFree(f);
+    cudaFree(hb->d_sums);
     if (hb->h_res) cudaFreeHost(hb->h_res);
     delete hb;
 }
@@ -1020,20 +1158,41 @@ lbm_status lbm_hybrid_query(const lbm_hybrid *hb, long *unknowns, int *half_rang
 }
 
 // packed <-> tiled through the other state buffer (it is rewritten by the next step)
-static cudaError_t hybrid_relayout(lbm_hybrid *hb, const double *src, double *dst, bool to_tiled)
+static cudaError_t hybrid_relayout(lbm_hybrid *hb, const void *src, void *dst, bool to_tiled)
 {
-    const int nc = hb->nx * hb->ny;
-    const int blocks = (int)std::min<long>((hb->unknowns + 255) / 256, 152L * 16);
-    hybrid_relayout_kernel<<<blocks, 256, 0, hb->stream>>>(src, dst, hb->d_poff, hb->d_toff, nc, to_tiled ? 1 : 0);
+    const int nc = hb->nx * hb->ny, blocks = elem_blocks(hb->unknowns);
+    if (hb->prec == LBM_FP32_PERTURB)
+        hybrid_relayout_kernel<float><<<blocks, 256, 0, hb->stream>>>(src, dst, hb->d_poff, hb->d_toff, nc, to_tiled ? 1 : 0);
+    else
+        hybrid_relayout_kernel<double><<<blocks, 256, 0, hb->stream>>>(src, dst, hb->d_poff, hb->d_toff, nc, to_tiled ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// the current state's buffer (FP64 or FP32, tiled)
+static void *hybrid_state(lbm_hybrid *hb)
+{
+    return hb->prec == LBM_FP32_PERTURB ? (void *)hb->d_f[hb->cur] : (void *)hb->d_h[hb->cur];
+}
+
+// the current state as FP64 in a tiled buffer (itself, or its FP64 copy in scratch d_h[0])
+static cudaError_t hybrid_state_f64(lbm_hybrid *hb, const double **out)
+{
+    if (hb->prec != LBM_FP32_PERTURB) {
+        *out = hb->d_h[hb->cur];
+        return cudaSuccess;
+    }
+    hybrid_f32_to_f64_kernel<<<elem_blocks(hb->tiled), 256, 0, hb->stream>>>(hb->d_f[hb->cur], hb->d_h[0], hb->tiled);
+    *out = hb->d_h[0];
     return cudaGetLastError();
 }
 
 lbm_status lbm_hybrid_set_state(lbm_hybrid *hb, const double *h)
 {
     if (!hb || !h) return hfail(LBM_EINVAL, "NULL argument");
-    double *scratch = hb->d_h[hb->cur ^ 1];
+    // scratch: the FP64 buffer the state is not in
+    double *scratch = hb->prec == LBM_FP32_PERTURB ? hb->d_h[0] : hb->d_h[hb->cur ^ 1];
     cudaError_t e = cudaMemcpyAsync(scratch, h, sizeof(double) * hb->unknowns, cudaMemcpyHostToDevice, hb->stream);
-    if (e == cudaSuccess) e = hybrid_relayout(hb, scratch, hb->d_h[hb->cur], true);
+    if (e == cudaSuccess) e = hybrid_relayout(hb, scratch, hybrid_state(hb), true);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
     hb->have_resid = false;
     return e == cudaSuccess ? LBM_OK : hfail(LBM_ECUDA, std::string("setting the state: ") + cudaGetErrorString(e));
@@ -1042,8 +1201,8 @@ lbm_status lbm_hybrid_set_state(lbm_hybrid *hb, const double *h)
 lbm_status lbm_hybrid_get_state(lbm_hybrid *hb, double *h)
 {
     if (!hb || !h) return hfail(LBM_EINVAL, "NULL argument");
-    double *scratch = hb->d_h[hb->cur ^ 1];
-    cudaError_t e = hybrid_relayout(hb, hb->d_h[hb->cur], scratch, false);
+    double *scratch = hb->prec == LBM_FP32_PERTURB ? hb->d_h[0] : hb->d_h[hb->cur ^ 1];
+    cudaError_t e = hybrid_relayout(hb, hybrid_state(hb), scratch, false);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h, scratch, sizeof(double) * hb->unknowns, cudaMemcpyDeviceToHost, hb->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
@@ -1054,26 +1213,13 @@ lbm_status lbm_hybrid_step(lbm_hybrid *hb, long nsteps)
 {
     if (!hb || nsteps < 0) return hfail(LBM_EINVAL, "invalid step arguments");
     const int nc = hb->nx * hb->ny;
+    (void)nc;
     for (long s = 0; s < nsteps; ++s) {
         const bool last = s == nsteps - 1;
-        StepLists L;
-        L.cells = hb->d_if;
-        L.ncells = hb->n_if;
-        for (int t = 0; t < 2; ++t) {
-            L.tiles[t] = hb->d_tiles[t];
-            L.ntiles[t] = hb->n_tiles[t];
-        }
-        cudaError_t e = launch_hybrid_step(hb->n_half, hargs(hb), plain_args(hb, 0), plain_args(hb, 1), L, hb->dt, hb->dx,
-                                           hb->dy, last ? 1 : 0, hb->stream);
-        if (e == cudaSuccess && last) {
-            const int nb1 = (nc + HCHUNK - 1) / HCHUNK;
-            hybrid_finalize_kernel<<<nb1, HFIN, 0, hb->stream>>>(hb->d_part, nc, hb->d_res + 2);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) {
-                hybrid_finalize_kernel<<<1, HFIN, 0, hb->stream>>>(hb->d_res + 2, nb1, hb->d_res);
-                e = cudaGetLastError();
-            }
-        }
+        const HybArgs a = hargs(hb);
+        cudaError_t e = hb->prec == LBM_FP32_PERTURB ? hybrid_launch<float>(hb, a, last ? 1 : 0)
+                                                     : hybrid_launch<double>(hb, a, last ? 1 : 0);
+        if (e == cudaSuccess && last) e = hybrid_finalize(hb);
         if (e != cudaSuccess) return hfail(LBM_ECUDA, std::string("launching the hybrid step: ") + cudaGetErrorString(e));
         hb->cur ^= 1;
     }
@@ -1098,7 +1244,8 @@ lbm_status lbm_hybrid_solve(lbm_hybrid *hb, double tol, long max_steps, int ever
 {
     if (!hb || every < 1 || max_steps < 0 || !(tol >= 0)) return hfail(LBM_EINVAL, "invalid solve arguments");
     long taken = 0;
-    double res = INFINITY;
+    double res = INFINITY, best = INFINITY;
+    int flat = 0;
     while (taken < max_steps) {
         lbm_status st = lbm_hybrid_step(hb, every);
         if (st != LBM_OK) return st;
@@ -1106,9 +1253,138 @@ lbm_status lbm_hybrid_solve(lbm_hybrid *hb, double tol, long max_steps, int ever
         st = lbm_hybrid_residual(hb, &res);
         if (st != LBM_OK) return st;
         if (res < tol) break;
+        // the FP32 march stops at its rounding floor: no 1 % improvement over 20 checks
+        if (hb->prec == LBM_FP32_PERTURB) {
+            if (res < 0.99 * best) {
+                best = res;
+                flat = 0;
+            } else if (++flat >= 20) {
+                break;
+            }
+        }
     }
     if (steps) *steps = taken;
     if (r) *r = res;
+    return LBM_OK;
+}
+
+lbm_status lbm_hybrid_set_precision(lbm_hybrid *hb, int prec)
+{
+    if (!hb) return hfail(LBM_EINVAL, "hybrid is NULL");
+    if (prec != LBM_FP64 && prec != LBM_FP32_PERTURB) return hfail(LBM_EINVAL, "unknown precision");
+    if (prec == hb->prec) return LBM_OK;
+    cudaError_t e = cudaSuccess;
+    if (prec == LBM_FP32_PERTURB) {
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+            if (!hb->d_f[i]) {
+                e = cudaMalloc(&hb->d_f[i], sizeof(float) * hb->tiled);
+                if (e == cudaSuccess) e = cudaMemsetAsync(hb->d_f[i], 0, sizeof(float) * hb->tiled, hb->stream);
+            }
+        if (e == cudaSuccess && !hb->d_sums) e = cudaMalloc(&hb->d_sums, sizeof(double) * 2 * HDEF);
+        if (e == cudaSuccess) {
+            hybrid_f64_to_f32_kernel<<<elem_blocks(hb->tiled), 256, 0, hb->stream>>>(hb->d_h[hb->cur], hb->d_f[hb->cur],
+                                                                                   hb->tiled);
+            e = cudaGetLastError();
+        }
+    } else {
+        hybrid_f32_to_f64_kernel<<<elem_blocks(hb->tiled), 256, 0, hb->stream>>>(hb->d_f[hb->cur], hb->d_h[hb->cur],
+                                                                               hb->tiled);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
+    if (e != cudaSuccess) return hfail(LBM_ECUDA, std::string("changing the hybrid's precision: ") + cudaGetErrorString(e));
+    hb->prec = prec;
+    hb->have_resid = false;
+    return LBM_OK;
+}
+
+// FP64 defect of the FP32 state: D = M64(H) - H into d_f[2]; *dsum = ||D||^2, *nsum = ||M64(H)||^2
+static lbm_status hybrid_defect(lbm_hybrid *hb, double *dsum, double *nsum)
+{
+    const float *H = hb->d_f[hb->cur];
+    hybrid_f32_to_f64_kernel<<<elem_blocks(hb->tiled), 256, 0, hb->stream>>>(H, hb->d_h[0], hb->tiled);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = hybrid_launch<double>(hb, hargs(hb, hb->d_h[0], hb->d_h[1]), 0);
+    if (e == cudaSuccess) {
+        hybrid_defect_kernel<<<HDEF, 256, 0, hb->stream>>>(hb->d_h[1], H, hb->d_f[2], hb->d_poff, hb->d_toff,
+                                                          hb->nx * hb->ny, hb->d_sums);
+        e = cudaGetLastError();
+    }
+    std::vector<double> sums(2 * HDEF);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sums.data(), hb->d_sums, sizeof(double) * 2 * HDEF, cudaMemcpyDeviceToHost, hb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
+    if (e != cudaSuccess) return hfail(LBM_ECUDA, std::string("hybrid defect pass: ") + cudaGetErrorString(e));
+    double d = 0.0, n = 0.0;
+    for (int b = 0; b < HDEF; ++b) {
+        d += sums[2 * b];
+        n += sums[2 * b + 1];
+    }
+    if (!std::isfinite(d) || !std::isfinite(n)) return hfail(LBM_ENONFINITE, "non-finite hybrid defect");
+    *dsum = d;
+    *nsum = n;
+    return LBM_OK;
+}
+
+lbm_status lbm_hybrid_refine(lbm_hybrid *hb, double tol, int max_sweeps, double refine_tol, long max_steps, int every,
+                             long *correction_steps, double *defect)
+{
+    if (!hb) return hfail(LBM_EINVAL, "hybrid is NULL");
+    if (hb->prec != LBM_FP32_PERTURB) return hfail(LBM_EINVAL, "refinement applies to the FP32 march");
+    if (!(tol > 0) || max_sweeps < 0 || refine_tol < 0 || max_steps < 1 || every < 1)
+        return hfail(LBM_EINVAL, "invalid refinement arguments");
+    double dsum, nsum;
+    lbm_status st = hybrid_defect(hb, &dsum, &nsum);
+    if (st != LBM_OK) return st;
+    double r64 = nsum > 0 ? std::sqrt(dsum / nsum) : 0.0;
+    const double hnorm = std::sqrt(nsum), ctol = refine_tol > 0 ? refine_tol : 0.1 * tol;
+    long ksum = 0;
+    for (int sw = 0; sw < max_sweeps && r64 >= tol && hnorm > 0; ++sw) {
+        // correction march delta <- L(delta) + D from delta = 0 (walls without driving)
+        float *C[2] = {hb->d_f[3], hb->d_f[4]};
+        int cc = 0;
+        cudaError_t e = cudaMemsetAsync(C[0], 0, sizeof(float) * hb->tiled, hb->stream);
+        long k = 0;
+        double cbest = INFINITY;
+        int cflat = 0;
+        while (e == cudaSuccess && k < max_steps) {
+            for (int j = 1; j <= every && e == cudaSuccess; ++j) {
+                e = hybrid_launch<float>(hb, hargs(hb, C[cc], C[cc ^ 1], hb->d_f[2], 1), j == every ? 1 : 0);
+                cc ^= 1;
+            }
+            if (e == cudaSuccess) e = hybrid_finalize(hb);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hb->h_res, hb->d_res, sizeof(double) * 2, cudaMemcpyDeviceToHost, hb->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(hb->stream);
+            if (e != cudaSuccess) break;
+            k += every;
+            // change per step relative to ||M64(H)||, below ctol: the correction's own error is
+            // its per-step change times the conditioning of the slow modes
+            const double change = std::sqrt(hb->h_res[0]) / hnorm;
+            if (!std::isfinite(change)) return hfail(LBM_ENONFINITE, "non-finite hybrid correction");
+            if (change < ctol) break;
+            if (change < 0.99 * cbest) {
+                cbest = change;
+                cflat = 0;
+            } else if (++cflat >= 20) {
+                break;
+            }
+        }
+        if (e == cudaSuccess) {
+            hybrid_add_f32_kernel<<<elem_blocks(hb->tiled), 256, 0, hb->stream>>>(hb->d_f[hb->cur], C[cc], hb->tiled);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return hfail(LBM_ECUDA, std::string("hybrid correction march: ") + cudaGetErrorString(e));
+        ksum += k;
+        const double prev = r64;
+        st = hybrid_defect(hb, &dsum, &nsum);
+        if (st != LBM_OK) return st;
+        r64 = nsum > 0 ? std::sqrt(dsum / nsum) : 0.0;
+        if (r64 > 0.5 * prev) break;          // at the FP32 rounding floor
+    }
+    hb->have_resid = false;
+    if (correction_steps) *correction_steps = ksum;
+    if (defect) *defect = r64;
     return LBM_OK;
 }
 
@@ -1117,9 +1393,11 @@ lbm_status lbm_hybrid_velocity(lbm_hybrid *hb, double *ux, double *uy)
     if (!hb || !ux || !uy) return hfail(LBM_EINVAL, "NULL argument");
     const int nc = hb->nx * hb->ny;
     double *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, sizeof(double) * 2 * nc);
+    const double *h64 = nullptr;
+    cudaError_t e = hybrid_state_f64(hb, &h64);
+    if (e == cudaSuccess) e = cudaMalloc(&d, sizeof(double) * 2 * nc);
     if (e == cudaSuccess) {
-        hybrid_velocity_kernel<<<(nc + HWARPS - 1) / HWARPS, 32 * HWARPS, 0, hb->stream>>>(hargs(hb), hb->u_ref, d,
+        hybrid_velocity_kernel<<<(nc + HWARPS - 1) / HWARPS, 32 * HWARPS, 0, hb->stream>>>(hargs(hb, h64), hb->u_ref, d,
                                                                                             d + nc);
         e = cudaGetLastError();
     }
@@ -1135,9 +1413,11 @@ lbm_status lbm_hybrid_face_flux(lbm_hybrid *hb, double *pxy)
     if (!hb || !pxy) return hfail(LBM_EINVAL, "NULL argument");
     if (hb->geom != LBM_COUETTE) return hfail(LBM_EUNSUPPORTED, "face fluxes are reported for the Couette column");
     double *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, sizeof(double) * (hb->ny + 1));
+    const double *h64 = nullptr;
+    cudaError_t e = hybrid_state_f64(hb, &h64);
+    if (e == cudaSuccess) e = cudaMalloc(&d, sizeof(double) * (hb->ny + 1));
     if (e == cudaSuccess) {
-        hybrid_face_flux_kernel<<<(hb->ny + 1 + HWARPS - 1) / HWARPS, 32 * HWARPS, 0, hb->stream>>>(hargs(hb),
+        hybrid_face_flux_kernel<<<(hb->ny + 1 + HWARPS - 1) / HWARPS, 32 * HWARPS, 0, hb->stream>>>(hargs(hb, h64),
                                                                                                     hb->u_ref, d);
         e = cudaGetLastError();
     }

@@ -121,6 +121,9 @@ def _load():
                                   ctypes.POINTER(ctypes.c_double)]),
         "lbm_hybrid_velocity": (st, [_vp, _vp, _vp]),
         "lbm_hybrid_face_flux": (st, [_vp, _vp]),
+        "lbm_hybrid_set_precision": (st, [_vp, ctypes.c_int]),
+        "lbm_hybrid_refine": (st, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double)]),
         "lbm_batch_get_march": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int)]),
@@ -723,6 +726,18 @@ def lbm_hybrid_solve(hb: Hybrid, tol: float, max_steps: int, every: int = 100) -
     _check(_load().lbm_hybrid_solve(hb.handle, float(tol), int(max_steps), int(every), ctypes.byref(s),
                                     ctypes.byref(r)))
     return {"steps": s.value, "residual": r.value}
+
+
+def lbm_hybrid_set_precision(hb: Hybrid, prec: int):
+    _check(_load().lbm_hybrid_set_precision(hb.handle, int(prec)))
+
+
+def lbm_hybrid_refine(hb: Hybrid, tol: float, max_sweeps: int = 3, refine_tol: float = 0.0,
+                      max_steps: int = 2_000_000, every: int = 100) -> dict:
+    k, d = ctypes.c_long(), ctypes.c_double()
+    _check(_load().lbm_hybrid_refine(hb.handle, float(tol), int(max_sweeps), float(refine_tol), int(max_steps),
+                                     int(every), ctypes.byref(k), ctypes.byref(d)))
+    return {"correction_steps": k.value, "defect": d.value}
 
 
 def lbm_hybrid_velocity(hb: Hybrid):

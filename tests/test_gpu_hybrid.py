@@ -156,3 +156,66 @@ def test_hybrid_rejects_invalid_arguments():
     with pytest.raises(ValueError):
         lbm.lbm_hybrid_set_state(hb, np.zeros(3))
     hb.close()
+
+
+# ---- FP32 hybrid march with FP64 defect correction (lbm_hybrid_set_precision, lbm_hybrid_refine)
+
+FP32_CASES = [
+    # n_half, nx, ny, kn, u_bottom, u_top, layer
+    (4, 48, 40, 0.1, 0.0, 0.01, 4),
+    (2, 33, 30, 1.0, 0.0, 0.02, 3),
+    (6, 20, 18, 0.5, 0.003, 0.01, 2),
+    (3, 7, 6, 0.2, 0.0, 0.01, 0),      # all full-range
+]
+
+
+@pytest.mark.parametrize("case", FP32_CASES)
+def test_hybrid_fp32_steps_match_oracle(case):
+    """The FP32 march (plain cells in FP32, interface cells in FP64 from the FP32 values)
+    against the FP64 oracle from an FP32-representable state, to FP32 accuracy per step."""
+    n, nx, ny, kn, ub, ut, layer = case
+    p = hy.HybridCavity(n, nx, ny, kn, ub, ut, layer)
+    rng = np.random.default_rng(nx * 7 + layer)
+    h0 = [(rng.standard_normal(p.vset(c).n) * 1e-2).astype(np.float32).astype(np.float64) for c in range(p.ncells)]
+    hb = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n, nx, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    lbm.lbm_hybrid_set_state(hb, _pack(h0))
+    lbm.lbm_hybrid_set_precision(hb, lbm.LBM_FP32_PERTURB)
+    assert np.array_equal(lbm.lbm_hybrid_get_state(hb), _pack(h0))        # FP32-representable: exact
+    steps = 6
+    lbm.lbm_hybrid_step(hb, steps)
+    got = lbm.lbm_hybrid_get_state(hb)
+    want = _pack(p.step(h0, steps))
+    assert np.abs(got - want).max() <= 2e-6 * steps * np.abs(want).max()
+    assert np.isfinite(lbm.lbm_hybrid_residual(hb))
+    ux, uy = lbm.lbm_hybrid_velocity(hb)
+    assert np.isfinite(ux).all() and np.isfinite(uy).all()
+    # back to FP64: the state carries over
+    lbm.lbm_hybrid_set_precision(hb, lbm.LBM_FP64)
+    assert np.array_equal(lbm.lbm_hybrid_get_state(hb), got)
+    hb.close()
+
+
+@pytest.mark.parametrize("case", [(4, 40, 40, 0.1, 0.0, 0.01, 4), (4, 32, 24, 1.0, 0.0, 0.01, 3)])
+def test_hybrid_fp32_refined_reaches_the_fp64_steady_state(case):
+    """FP32 march to its floor, then the FP64-defect refinement: the steady velocity field
+    agrees with the FP64 hybrid march to 1e-12 within 1e-5 of the lid speed.  The defect of
+    the refined state stops at the FP32 storage floor (the rounding of the stored state itself,
+    about 1e-8 of the field), as in the plain march's refinement."""
+    n, nx, ny, kn, ub, ut, layer = case
+    ref = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n, nx, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    info = lbm.lbm_hybrid_solve(ref, 1e-12, 400000, 100)
+    assert info["residual"] < 1e-12
+    wx, wy = lbm.lbm_hybrid_velocity(ref)
+    ref.close()
+    hb = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n, nx, ny, kn, ub, ut, layer, stream=torch.cuda.Stream())
+    lbm.lbm_hybrid_set_precision(hb, lbm.LBM_FP32_PERTURB)
+    m = lbm.lbm_hybrid_solve(hb, 5e-8, 400000, 100)
+    assert m["steps"] < 400000
+    r = lbm.lbm_hybrid_refine(hb, 1e-10, 3, 0.0, 400000, 100)
+    assert r["defect"] < 3e-8 and r["correction_steps"] > 0
+    ux, uy = lbm.lbm_hybrid_velocity(hb)
+    err = max(np.abs(ux - wx).max(), np.abs(uy - wy).max()) / ut
+    assert err < 1e-5, err
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_hybrid_refine(lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n, 8, 8, kn, ub, ut, 1), 1e-10)   # FP64: refused
+    hb.close()
