@@ -65,10 +65,27 @@ struct HybTables {
     double pt[2][HMAXV * HMAXF];
 };
 
+// Device copy of the tables in the arithmetic type T of the interface cells (double for the
+// FP64 march, float for the FP32 one: GB300 retires FP64 at 2 lanes per cycle per SM)
+template <typename T>
+struct HybSetT {
+    int n, lanes;
+    T xi_x[HMAXV], xi_y[HMAXV], w[HMAXV];
+    T d_x, d_y;
+    T nux[HMAXV], nuy[HMAXV];
+    signed char sx[HMAXV], sy[HMAXV];
+};
+
+template <typename T>
+struct HybTabT {
+    HybSetT<T> set[2];
+    T pt[2][HMAXV * HMAXF];
+};
+
 constexpr int HST = 32;        // stride between the velocities of a cell in the tiled state
 
 struct HybArgs {
-    const HybTables *tab;
+    const void *tab;           // HybTabT<double> or HybTabT<float>, the type the interface cells compute in
     const int *toff;           // [ncells] velocity 0 of each cell in the tiled state
     const unsigned char *half; // [ncells] 1: half-range cell
     const void *h;             // state (FP64, or FP32 in the mixed-precision march), tiled
@@ -86,7 +103,8 @@ struct HybArgs {
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -99,15 +117,16 @@ __device__ __forceinline__ double warp_sum(double v)
 // Target sets of more than 16 velocities: each lane whole sums for outputs lane, lane + 32,
 // ...; smaller ones: the source velocities split over 32 / lanes lane groups, the partial sums
 // combined by shuffles (every lane of the warp calls this).
-__device__ void project_warp(const HybTables &tb, int ti, const double *h, double *out)
+template <typename T>
+__device__ void project_warp(const HybTabT<T> &tb, int ti, const T *h, T *out)
 {
     const int lane = threadIdx.x & 31;
-    const HybSet &T = tb.set[ti], &S = tb.set[ti ^ 1];
-    const double *pt = tb.pt[ti];
-    const int nt = T.n, ns = S.n;
+    const HybSetT<T> &Tg = tb.set[ti], &S = tb.set[ti ^ 1];
+    const T *pt = tb.pt[ti];
+    const int nt = Tg.n, ns = S.n;
     if (ns > 16) {
         for (int b = lane; b < ns; b += 32) {
-            double s4[4] = {0.0, 0.0, 0.0, 0.0};
+            T s4[4] = {0, 0, 0, 0};
             int a = 0;
             for (; a + 4 <= nt; a += 4) {
 #pragma unroll
@@ -118,7 +137,7 @@ __device__ void project_warp(const HybTables &tb, int ti, const double *h, doubl
         }
     } else {
         const int ls = S.lanes, parts = 32 / ls, part = lane / ls, b = lane - part * ls;
-        double acc = 0.0;
+        T acc = 0;
         if (b < ns)
             for (int a = part; a < nt; a += parts) acc += pt[a * ns + b] * h[a];
         for (int o = ls; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -127,21 +146,21 @@ __device__ void project_warp(const HybTables &tb, int ti, const double *h, doubl
     __syncwarp();
 }
 
-// The n values of cell k into buf[0..n) in FP64 (a warp; velocity b at toff[k] + HST b).
-template <typename TS>
-__device__ void gather_cell(const TS *h, const int *toff, int k, int n, double *buf)
+// The n values of cell k into buf[0..n) (a warp; velocity b at toff[k] + HST b).
+template <typename TS, typename T>
+__device__ void gather_cell(const TS *h, const int *toff, int k, int n, T *buf)
 {
     const TS *hk = h + toff[k];
-    for (int b = threadIdx.x & 31; b < n; b += 32) buf[b] = (double)hk[(long)HST * b];
+    for (int b = threadIdx.x & 31; b < n; b += 32) buf[b] = (T)hk[(long)HST * b];
     __syncwarp();
 }
 
 // Values of neighbour cell k as seen by a cell of set sj, into buf[0..S.n): its own values
 // for the same set, else their projection (tmp: the neighbour's values, gathered first).
-template <typename TS>
-__device__ void neighbour_values(const HybArgs &a, int k, int sj, double *buf, double *tmp)
+template <typename TS, typename T>
+__device__ void neighbour_values(const HybArgs &a, int k, int sj, T *buf, T *tmp)
 {
-    const HybTables &tb = *a.tab;
+    const HybTabT<T> &tb = *static_cast<const HybTabT<T> *>(a.tab);
     const int sk = a.half[k] ? 0 : 1;
     const TS *h = static_cast<const TS *>(a.h);
     if (sk == sj) {
@@ -154,36 +173,38 @@ __device__ void neighbour_values(const HybArgs &a, int k, int sj, double *buf, d
 
 // Ghost of Eq. 8 (perturbation form) for the velocities leaving wall `face` (0 bottom, 1 top,
 // 2 left, 3 right; the side walls at rest), into buf; rho_w by Eq. 9 over the cell's own set.
-__device__ void wall_ghost(const HybArgs &a, const HybSet &S, const double *hc, int face, double *buf)
+template <typename T>
+__device__ void wall_ghost(const HybArgs &a, const HybSetT<T> &S, const T *hc, int face, T *buf)
 {
     const int lane = threadIdx.x & 31;
-    double part = 0.0;
+    T part = 0;
     for (int b = lane; b < S.n; b += 32) {
         const int sn = face == 0 ? S.sy[b] : face == 1 ? -S.sy[b] : face == 2 ? S.sx[b] : -S.sx[b];
         if (sn < 0) {
-            const double xn = face == 0 ? S.xi_y[b] : face == 1 ? -S.xi_y[b] : face == 2 ? S.xi_x[b] : -S.xi_x[b];
+            const T xn = face == 0 ? S.xi_y[b] : face == 1 ? -S.xi_y[b] : face == 2 ? S.xi_x[b] : -S.xi_x[b];
             part += -xn * hc[b];
         }
     }
-    const double rho_w = warp_sum(part) / (face < 2 ? S.d_y : S.d_x);
-    const double u = face == 0 ? a.u_bottom : face == 1 ? a.u_top : 0.0;
+    const T rho_w = warp_sum(part) / (face < 2 ? S.d_y : S.d_x);
+    const T u = (T)(face == 0 ? a.u_bottom : face == 1 ? a.u_top : 0.0);
     for (int b = lane; b < S.n; b += 32) {
-        const double xt = face < 2 ? S.xi_x[b] : S.xi_y[b];
-        buf[b] = S.w[b] * (rho_w * (1.0 + xt * u) + (a.homogeneous ? 0.0 : xt * u / a.u_ref));
+        const T xt = face < 2 ? S.xi_x[b] : S.xi_y[b];
+        buf[b] = S.w[b] * (rho_w * (T(1) + xt * u) + (a.homogeneous ? T(0) : xt * u / (T)a.u_ref));
     }
     __syncwarp();
 }
 
 // (mass, x-momentum, y-momentum) flux sum |xi_d| (1, xi_x, xi_y) v over the velocities of S
 // moving along +axis (positive) or -axis; axis 0 = x, 1 = y.
-__device__ void face_moments(const HybSet &S, const double *v, int axis, bool positive, double (&m)[3])
+template <typename T>
+__device__ void face_moments(const HybSetT<T> &S, const T *v, int axis, bool positive, T (&m)[3])
 {
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    T p0 = 0, p1 = 0, p2 = 0;
     for (int b = threadIdx.x & 31; b < S.n; b += 32) {
         const int sd = axis == 0 ? S.sx[b] : S.sy[b];
         if (positive ? sd > 0 : sd < 0) {
-            const double xd = axis == 0 ? S.xi_x[b] : S.xi_y[b];
-            const double t = fabs(xd) * v[b];
+            const T xd = axis == 0 ? S.xi_x[b] : S.xi_y[b];
+            const T t = (xd < 0 ? -xd : xd) * v[b];
             p0 += t;
             p1 += t * S.xi_x[b];
             p2 += t * S.xi_y[b];
@@ -194,29 +215,31 @@ __device__ void face_moments(const HybSet &S, const double *v, int axis, bool po
     m[2] = warp_sum(p2);
 }
 
+template <typename T>
 struct HybShared {
-    double nbv[HWARPS][4][HMAXV];   // left, right, below, above: upwind values in the cell's set
-    double ph[HWARPS][HMAXV], nb[HWARPS][HMAXV];
-    double own[HWARPS][HMAXV], tmp[HWARPS][HMAXV];   // the cell's values; a neighbour's before projection
+    T nbv[HWARPS][4][HMAXV];   // left, right, below, above: upwind values in the cell's set
+    T ph[HWARPS][HMAXV], nb[HWARPS][HMAXV];
+    T own[HWARPS][HMAXV], tmp[HWARPS][HMAXV];   // the cell's values; a neighbour's before projection
 };
 
 // A cell with an interface face (a neighbour in the other set): one warp, warp `wi` of the
-// block's shared buffers.
+// block's shared buffers; arithmetic in the storage type TS.
 template <typename TS>
-__device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, double dt, double dx, double dy,
+__device__ void interface_cell(const HybArgs &a, HybShared<TS> &sh, int wi, int c, double dt, double dx, double dy,
                                int resid)
 {
+    using T = TS;
     const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny;
-    const HybTables &tb = *a.tab;
+    const HybTabT<T> &tb = *static_cast<const HybTabT<T> *>(a.tab);
     const int sj = a.half[c] ? 0 : 1;
-    const HybSet &S = tb.set[sj];
-    const HybSet &H = tb.set[0];
-    double *hc = sh.own[wi];
+    const HybSetT<T> &S = tb.set[sj];
+    const HybSetT<T> &H = tb.set[0];
+    T *hc = sh.own[wi];
     gather_cell(static_cast<const TS *>(a.h), a.toff, c, S.n, hc);
-    double *tmp = sh.tmp[wi];
+    T *tmp = sh.tmp[wi];
     const int x = c % nx, y = c / nx;
-    double(*nbv)[HMAXV] = sh.nbv[wi];
+    T(*nbv)[HMAXV] = sh.nbv[wi];
     // upwind values: x (cavity only) and y neighbours in this cell's set, or the walls' ghosts;
     // the four faces as (axis, side, neighbour or -1)
     int nbc[4] = {-1, -1, -1, -1};
@@ -232,48 +255,48 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     else wall_ghost(a, S, hc, 1, nbv[3]);
     // interface faces of a full-range cell: mass and momentum exchange made equal to the
     // half-range evaluation of the face
-    double cr[3] = {0.0, 0.0, 0.0};
+    T cr[3] = {0, 0, 0};
     bool any_if = false;
     if (sj == 1)
         for (int f = 0; f < 4; ++f) any_if |= nbc[f] >= 0 && a.half[nbc[f]];
     if (any_if) {
-        double *ph = sh.ph[wi], *nb = sh.nb[wi];
+        T *ph = sh.ph[wi], *nb = sh.nb[wi];
         project_warp(tb, 1, hc, ph);                            // this cell seen in H
         for (int f = 0; f < 4; ++f) {
             if (nbc[f] < 0 || !a.half[nbc[f]]) continue;
             const int axis = f >> 1;
             const bool lower = (f & 1) == 0;                  // the neighbour is on the lower side
             neighbour_values<TS>(a, nbc[f], 0, nb, tmp);      // its own half-range values
-            double up[3], dn[3], got[3], sent[3];
+            T up[3], dn[3], got[3], sent[3];
             face_moments(H, lower ? nb : ph, axis, true, up);
             face_moments(H, lower ? ph : nb, axis, false, dn);
             face_moments(S, nbv[f], axis, lower, got);
             face_moments(S, hc, axis, !lower, sent);
-            const double fac = dt / (axis == 0 ? dx : dy);
+            const T fac = (T)(dt / (axis == 0 ? dx : dy));
             for (int q = 0; q < 3; ++q) {
-                const double want = lower ? up[q] - dn[q] : dn[q] - up[q];
+                const T want = lower ? up[q] - dn[q] : dn[q] - up[q];
                 cr[q] += fac * (want - (got[q] - sent[q]));
             }
         }
     }
     // transport, moments, relaxation
-    double hs[(HMAXV + 31) / 32];
-    double rho = 0.0, jx = 0.0, jy = 0.0;
+    T hs[(HMAXV + 31) / 32];
+    T rho = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int i = 0; i < (HMAXV + 31) / 32; ++i) {
         const int b = lane + 32 * i;
-        double v = 0.0;
+        T v = 0;
         if (b < S.n) {
-            const double ex = S.xi_x[b], ey = S.xi_y[b];
-            const double h0 = hc[b];
-            double hx = h0, nux = 0.0;
+            const T ex = S.xi_x[b], ey = S.xi_y[b];
+            const T h0 = hc[b];
+            T hx = h0, nux = 0;
             const int sgx = S.sx[b], sgy = S.sy[b];
             if (a.cavity) {
                 hx = sgx > 0 ? nbv[0][b] : (sgx < 0 ? nbv[1][b] : h0);
                 nux = S.nux[b];
             }
-            const double hy = sgy > 0 ? nbv[2][b] : (sgy < 0 ? nbv[3][b] : h0);
-            const double nuy = S.nuy[b];
+            const T hy = sgy > 0 ? nbv[2][b] : (sgy < 0 ? nbv[3][b] : h0);
+            const T nuy = S.nuy[b];
             v = h0 - nux * (h0 - hx) - nuy * (h0 - hy);
             if (any_if) v += (cr[0] + cr[1] * ex + cr[2] * ey) * S.w[b];
             rho += v;
@@ -288,19 +311,20 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
     TS *out = static_cast<TS *>(a.hn) + a.toff[c];
     constexpr bool MIXED = std::is_same<TS, float>::value;      // the FP32 march's correction sweeps
     const float *src = (MIXED && a.src) ? a.src + a.toff[c] : nullptr;
-    double pd = 0.0, pn = 0.0;
+    const T om = (T)a.omega;
+    T pd = 0, pn = 0;
 #pragma unroll
     for (int i = 0; i < (HMAXV + 31) / 32; ++i) {
         const int b = lane + 32 * i;
         if (b < S.n) {
-            const double heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
-            double o = hs[i] - a.omega * (hs[i] - heq);
-            if (MIXED && src) o += (double)src[(long)HST * b];
-            out[(long)HST * b] = (TS)o;
+            const T heq = S.w[b] * (rho + S.xi_x[b] * jx + S.xi_y[b] * jy);
+            T o = hs[i] - om * (hs[i] - heq);
+            if (MIXED && src) o += (T)src[(long)HST * b];
+            out[(long)HST * b] = o;
             if (resid) {
-                const double os = (double)(TS)o, d = os - hc[b];
+                const T d = o - hc[b];
                 pd += d * d;
-                pn += os * os;
+                pn += o * o;
             }
         }
     }
@@ -308,12 +332,11 @@ __device__ void interface_cell(const HybArgs &a, HybShared &sh, int wi, int c, d
         pd = warp_sum(pd);
         pn = warp_sum(pn);
         if (lane == 0) {
-            a.part[2 * c] = pd;
-            a.part[2 * c + 1] = pn;
+            a.part[2 * c] = (double)pd;
+            a.part[2 * c + 1] = (double)pn;
         }
     }
 }
-
 
 // Plain cells of one set: all their existing neighbours carry the same set.  Per tile (up to
 // 32 consecutive cells of the set) G warps, lane p the tile's cell p, warp g the velocity rows
@@ -533,14 +556,19 @@ struct StepLists {
     int ntiles[2];
 };
 
+// blocks a SM the FP32 build asks for: eight (64 registers a thread) where that does not
+// spill, six for the 100-velocity half-range set; FP64 as the compiler chooses
 template <int N, typename TS>
-__global__ void __launch_bounds__(32 * HWARPS) hybrid_step_kernel(const HybArgs a, const PlainArgs<TS> ph,
+constexpr int hybrid_min_blocks() { return sizeof(TS) == 8 ? 1 : (N == 5 ? 6 : 8); }
+
+template <int N, typename TS>
+__global__ void __launch_bounds__(32 * HWARPS, hybrid_min_blocks<N, TS>()) hybrid_step_kernel(const HybArgs a, const PlainArgs<TS> ph,
                                                                    const PlainArgs<TS> pf, const StepLists L, double dt,
                                                                    double dx, double dy, int resid)
 {
     constexpr int GH = half_warps(N);
     __shared__ union {
-        HybShared sh;
+        HybShared<TS> sh;
         double hx[HWARPS / GH][GH][4][32];
         double fx[HWARPS][1][4][32];
     } u;
@@ -691,15 +719,15 @@ __global__ void __launch_bounds__(HFIN) hybrid_finalize_kernel(const double *par
 // the half-range set); one warp per face k
 __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const HybArgs a, double u_ref, double *pxy)
 {
-    __shared__ HybShared sh;
+    __shared__ HybShared<double> sh;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int k = blockIdx.x * HWARPS + wi;
     if (k > a.ny) return;
-    const HybTables &tb = *a.tab;
+    const HybTabT<double> &tb = *static_cast<const HybTabT<double> *>(a.tab);
     double *lo = sh.nbv[wi][0], *hi = sh.nbv[wi][1];
     double up = 0.0, dn = 0.0;
     if (k > 0 && k < a.ny && a.half[k - 1] != a.half[k]) {
-        const HybSet &H = tb.set[0];
+        const HybSetT<double> &H = tb.set[0];
         neighbour_values<double>(a, k - 1, 0, lo, sh.tmp[wi]);
         neighbour_values<double>(a, k, 0, hi, sh.tmp[wi]);
         double mu[3], md[3];
@@ -709,7 +737,7 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_face_flux_kernel(const Hyb
         dn = -md[1];                                            // sum over xi_y < 0 of xi_y xi_x h
     } else {
         const int cb = k == 0 ? 0 : k - 1, ca = k == a.ny ? a.ny - 1 : k;
-        const HybSet &Sb = tb.set[a.half[cb] ? 0 : 1], &Sa = tb.set[a.half[ca] ? 0 : 1];
+        const HybSetT<double> &Sb = tb.set[a.half[cb] ? 0 : 1], &Sa = tb.set[a.half[ca] ? 0 : 1];
         double *vb = sh.own[wi], *va = sh.tmp[wi];
         gather_cell(static_cast<const double *>(a.h), a.toff, cb, Sb.n, vb);
         gather_cell(static_cast<const double *>(a.h), a.toff, ca, Sa.n, va);
@@ -739,7 +767,7 @@ __global__ void __launch_bounds__(32 * HWARPS) hybrid_velocity_kernel(const HybA
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * HWARPS + (threadIdx.x >> 5);
     if (c >= a.nx * a.ny) return;
-    const HybSet &S = a.tab->set[a.half[c] ? 0 : 1];
+    const HybSetT<double> &S = static_cast<const HybTabT<double> *>(a.tab)->set[a.half[c] ? 0 : 1];
     const double *hc = static_cast<const double *>(a.h) + a.toff[c];
     double s0 = 0.0, sx = 0.0, sy = 0.0;
     for (int b = lane; b < S.n; b += 32) {
@@ -768,7 +796,8 @@ struct lbm_hybrid {
     long unknowns;           // values of the packed state
     long tiled;              // doubles of the tiled device state (tiles padded to 32 cells)
     cudaStream_t stream;
-    HybTables *d_tab;
+    HybTabT<double> *d_tab;  // the tables for the FP64 kernels
+    HybTabT<float> *d_tab32; // and for the FP32 march
     int *d_poff, *d_toff;    // packed offsets; tiled offsets of velocity 0 of each cell
     unsigned char *d_half, *d_iface;
     double *d_h[2], *d_part, *d_res;
@@ -897,8 +926,10 @@ PlainArgs<TC> plain_args(const lbm_hybrid *hb, int set, const HybArgs &a)
 
 // One step from a.h into a.hn in precision TS (the residual partials when resid)
 template <typename TS>
-cudaError_t hybrid_launch(const lbm_hybrid *hb, const HybArgs &a, int resid)
+cudaError_t hybrid_launch(const lbm_hybrid *hb, const HybArgs &a0, int resid)
 {
+    HybArgs a = a0;
+    a.tab = std::is_same<TS, float>::value ? (const void *)hb->d_tab32 : (const void *)hb->d_tab;
     StepLists L;
     L.cells = hb->d_if;
     L.ncells = hb->n_if;
@@ -957,6 +988,7 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     hb->cur = 0;
     hb->have_resid = false;
     hb->d_tab = nullptr;
+    hb->d_tab32 = nullptr;
     hb->d_poff = hb->d_toff = nullptr;
     hb->d_half = hb->d_iface = nullptr;
     hb->d_h[0] = hb->d_h[1] = nullptr;
@@ -1083,7 +1115,40 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
     }
     const double ur = std::max(std::fabs(u_bottom), std::fabs(u_top));
     hb->u_ref = ur > 0 ? ur : 1.0;
-    cudaError_t e = cudaMalloc(&hb->d_tab, sizeof(HybTables));
+    // device tables in both arithmetic types
+    std::vector<HybTabT<double>> t64(1);
+    std::vector<HybTabT<float>> t32(1);
+    for (int t = 0; t < 2; ++t) {
+        const HybSet &S = tab.set[t];
+        HybSetT<double> &D = t64[0].set[t];
+        HybSetT<float> &F = t32[0].set[t];
+        D.n = F.n = S.n;
+        D.lanes = F.lanes = S.lanes;
+        D.d_x = S.d_x;
+        D.d_y = S.d_y;
+        F.d_x = (float)S.d_x;
+        F.d_y = (float)S.d_y;
+        for (int b = 0; b < S.n; ++b) {
+            D.xi_x[b] = S.xi_x[b];
+            D.xi_y[b] = S.xi_y[b];
+            D.w[b] = S.w[b];
+            D.nux[b] = S.nux[b];
+            D.nuy[b] = S.nuy[b];
+            F.xi_x[b] = (float)S.xi_x[b];
+            F.xi_y[b] = (float)S.xi_y[b];
+            F.w[b] = (float)S.w[b];
+            F.nux[b] = (float)S.nux[b];
+            F.nuy[b] = (float)S.nuy[b];
+            D.sx[b] = F.sx[b] = S.sx[b];
+            D.sy[b] = F.sy[b] = S.sy[b];
+        }
+        for (int i = 0; i < HMAXV * HMAXF; ++i) {
+            t64[0].pt[t][i] = tab.pt[t][i];
+            t32[0].pt[t][i] = (float)tab.pt[t][i];
+        }
+    }
+    cudaError_t e = cudaMalloc(&hb->d_tab, sizeof(HybTabT<double>));
+    if (e == cudaSuccess) e = cudaMalloc(&hb->d_tab32, sizeof(HybTabT<float>));
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_poff, sizeof(int) * (nc + 1));
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_toff, sizeof(int) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&hb->d_half, nc);
@@ -1103,7 +1168,10 @@ lbm_status lbm_hybrid_init(int geom, int n_half, int nx, int ny, double kn, doub
         if (hb->n_tiles[t] > 0)
             e = cudaMemcpyAsync(hb->d_tiles[t], tiles[t].data(), sizeof(int2) * hb->n_tiles[t], cudaMemcpyHostToDevice,
                                 hb->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb->d_tab, &tab, sizeof tab, cudaMemcpyHostToDevice, hb->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb->d_tab, t64.data(), sizeof(HybTabT<double>), cudaMemcpyHostToDevice, hb->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb->d_tab32, t32.data(), sizeof(HybTabT<float>), cudaMemcpyHostToDevice, hb->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hb->d_poff, hb->off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, hb->stream);
     if (e == cudaSuccess)
@@ -1127,6 +1195,7 @@ void lbm_hybrid_destroy(lbm_hybrid *hb)
     if (hb->stream) cudaStreamSynchronize(hb->stream);
     else cudaDeviceSynchronize();
     cudaFree(hb->d_tab);
+    cudaFree(hb->d_tab32);
     cudaFree(hb->d_poff);
     cudaFree(hb->d_toff);
     cudaFree(hb->d_half);

@@ -346,15 +346,19 @@ def step_rates(side: int = 2048, sets=("D2Q9", "D2Q^h_16", "D2Q_16", "D2Q^h_64",
     return out
 
 
-def hybrid_rates(side: int = 1024, layers=(0, 4, 16, 64), n_half: int = 4, steps: int = 50):
+def hybrid_rates(side: int = 1024, layers=(0, 4, 16, 64), n_half: int = 4, steps: int = 50, precision: str = "fp64"):
     """Step time of the hybrid half-range / full-range cavity (Kn 0.1, lid 0.01) per layer
-    width, and of the plain FP64 half-range march of the same cavity, timed with CUDA events
-    on the objects' streams after ten warm-up steps."""
+    width, and of the plain half-range march of the same cavity (precision "fp64", or "fp32":
+    the FP32 hybrid against the plain FP32 march's fastest kernel), timed with CUDA events on
+    the objects' streams after ten warm-up steps."""
     import torch
-    out = {"side": side, "n_half": n_half, "steps": steps, "runs": []}
+    f32 = precision == "fp32"
+    out = {"side": side, "n_half": n_half, "steps": steps, "precision": precision, "runs": []}
     for layer in layers:
         stream = torch.cuda.Stream()
         hb = lbm.lbm_hybrid_init(lbm.LBM_CAVITY, n_half, side, side, 0.1, 0.0, 0.01, layer, stream=stream)
+        if f32:
+            lbm.lbm_hybrid_set_precision(hb, lbm.LBM_FP32_PERTURB)
         q = lbm.lbm_hybrid_query(hb)
         lbm.lbm_hybrid_step(hb, 10)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -368,8 +372,16 @@ def hybrid_rates(side: int = 1024, layers=(0, 4, 16, 64), n_half: int = 4, steps
                             "ms_per_step": ms, "unknowns_per_s": q["unknowns"] / ms * 1e3})
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
     stream = torch.cuda.Stream()
-    sim = lbm.lbm_init(vs, lbm.make_problem(lbm.LBM_CAVITY, side, side, 0.1, 0.0, 0.01, prec=lbm.LBM_FP64,
+    sim = lbm.lbm_init(vs, lbm.make_problem(lbm.LBM_CAVITY, side, side, 0.1, 0.0, 0.01,
+                                            prec=lbm.LBM_FP32_PERTURB if f32 else lbm.LBM_FP64,
                                             residual_every=100), stream=stream)
+    if f32:
+        for v in ((n_half, 9), (n_half, 8)):     # the tiled march (M / 2 warps), where the grid takes it
+            try:
+                lbm.lbm_set_variant(sim, *v)
+                break
+            except lbm.LBMError:
+                continue
     lbm.lbm_step(sim, 10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -377,10 +389,11 @@ def hybrid_rates(side: int = 1024, layers=(0, 4, 16, 64), n_half: int = 4, steps
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    variant = lbm.lbm_get_variant(sim)
     sim.close()
     nvel = (2 * n_half) ** 2
-    out["plain_half_range_fp64"] = {"unknowns": side * side * nvel, "ms_per_step": ms,
-                                    "unknowns_per_s": side * side * nvel / ms * 1e3}
+    out["plain_half_range_" + precision] = {"unknowns": side * side * nvel, "ms_per_step": ms, "variant": variant,
+                                            "unknowns_per_s": side * side * nvel / ms * 1e3}
     out["summary"] = {f"layer {r['layer']}": round(r["ms_per_step"], 4) for r in out["runs"]}
     out["summary"]["plain half-range"] = round(ms, 4)
     return out
@@ -395,6 +408,7 @@ def main(argv=None):
     ap.add_argument("--out", required=True)
     ap.add_argument("--side", type=int, default=None, help="cavity side (128; rates: 2048; hybrid_rates: 1024)")
     ap.add_argument("--layers", default=None, help="hybrid_rates: comma-separated layer widths (0,4,16,64)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"], help="hybrid_rates: the march's precision")
     args = ap.parse_args(argv)
     if args.study == "kn_sweep":
         r = kn_sweep()
@@ -410,7 +424,7 @@ def main(argv=None):
         r = step_rates(side=args.side or 2048)
     elif args.study == "hybrid_rates":
         layers = tuple(int(v) for v in args.layers.split(",")) if args.layers else (0, 4, 16, 64)
-        r = hybrid_rates(side=args.side or 1024, layers=layers)
+        r = hybrid_rates(side=args.side or 1024, layers=layers, precision=args.precision)
     else:
         r = cavity_table2_study(side=args.side or 128)
     with open(args.out, "w") as f:
