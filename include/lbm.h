@@ -411,8 +411,8 @@ lbm_status lbm_batch_refine(lbm_batch *b, double tol, int max_sweeps, double ref
  * layer = 0 is the full-range march, a layer beyond the half width the half-range march.
  * dt = cfl / (max|xi_x|/dx + max|xi_y|/dy) over the sets present (the x term dropped for the
  * column), dt <= Kn.  FP64 by default; lbm_hybrid_set_precision(hb, LBM_FP32_PERTURB) switches
- * the march to FP32 storage and arithmetic (interface cells computed in FP64 from the FP32
- * values) with the mixed-precision refinement of lbm_hybrid_refine (below).  State layout
+ * the march to FP32 storage and arithmetic (the interface projections and face moments
+ * too, with FP32 tables) with the mixed-precision refinement of lbm_hybrid_refine (below).  State layout
  * (host FP64, packed): cell after cell
  * (c = y * nx + x), each cell's values in its own set's order a = iy * M + ix (M = 2N
  * half-range, N full-range); lbm_hybrid_query reports the total.  2 <= N <= 6.

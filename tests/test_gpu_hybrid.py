@@ -171,7 +171,7 @@ FP32_CASES = [
 
 @pytest.mark.parametrize("case", FP32_CASES)
 def test_hybrid_fp32_steps_match_oracle(case):
-    """The FP32 march (plain cells in FP32, interface cells in FP64 from the FP32 values)
+    """The FP32 march (every cell in FP32, the interface projections with FP32 tables)
     against the FP64 oracle from an FP32-representable state, to FP32 accuracy per step."""
     n, nx, ny, kn, ub, ut, layer = case
     p = hy.HybridCavity(n, nx, ny, kn, ub, ut, layer)
