@@ -1348,13 +1348,24 @@ cudaError_t occupancy(lbm_batch *b, void *fn, int threads, int *nsm, int *blocks
 double march_chunk_plan(const lbm_batch *b, long slots)
 {
     long strip_rows = 0;
+    int cavities = 0;
     for (int i = 0; i < (int)b->inst.size(); ++i)
-        if (b->live[i] && b->inst[i].cavity) strip_rows += (long)((b->inst[i].nx + 31) / 32) * b->inst[i].ny;
-    // about 1.7 items per warp group and step: with items taken instance by instance and each
-    // waiting only for its own instance, fewer, longer items beat a finer split (measured on
-    // 32 and 128 cavities of 128^2 and 8 of 256^2: 16, 64 and 16 rows, 0.71, 0.81, 0.68 of
-    // the copy rate); each chunk re-reads one row, so chunks stay at least 4 rows
-    const double h = (double)strip_rows / (1.7 * (double)std::max(1L, slots));
+        if (b->live[i] && b->inst[i].cavity) {
+            strip_rows += (long)((b->inst[i].nx + 31) / 32) * b->inst[i].ny;
+            ++cavities;
+        }
+    // Items per warp group and step: about 1.3 with eight or more cavities, 1.7 with fewer.
+    // Items are taken step after step, each waiting only for its own instance's previous
+    // step, so a group that finishes early starts the next step's items: fewer, longer
+    // items amortise each item's start (its first rows' copies, the wall prologue) as long
+    // as every group still has one.  Measured over chunk lengths (ms per step, best against
+    // the 1.7 rule): 16 x 128^2 0.0307 / 0.0321, 32 x 128^2 0.0534 / 0.0557, 64 x 128^2
+    // 0.1015 / 0.1043, 8 x 256^2 0.0570 / 0.0582.  With few instances the end of each
+    // instance's step, where its groups run out of items, costs more than the starts: two
+    // 512^2 cavities run best at 1.7 (0.0570 ms; 0.0582 at 1.4).  Each chunk re-reads one
+    // row, so chunks stay at least 4 rows.
+    const double per_group = cavities >= 8 ? 1.3 : 1.7;
+    const double h = (double)strip_rows / (per_group * (double)std::max(1L, slots));
     return std::max(4.0, std::min(128.0, h));
 }
 
