@@ -362,6 +362,10 @@ def run_own(args, dist: Dist):
     }
     if not args.no_e2e:
         out["e2e"] = run_e2e(sim, prob, n_vel, ncells, stream, dist, args)
+        # the same calls with the FP64 host upload (lbm_set_state), twice the uploaded bytes
+        e64 = run_e2e(sim, prob, n_vel, ncells, stream, dist, args, host_fp64=True)
+        out["e2e"]["fp64_host_upload"] = {"value": e64["value"], "ms_per_call": round(e64["ms_per_call"], 2),
+                                          "h2d_bytes_per_step": e64["h2d_bytes_per_step"]}
     if not args.no_extras and dist.world == 1 and order == 1:
         out["fp64"] = run_fp64_same_workload(vs, dist)
         sim.close()
@@ -375,9 +379,10 @@ def run_own(args, dist: Dist):
     return out
 
 
-def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
-    """Same metric through the public C-ABI with host buffers: upload a host FP64 state
-    (pinned), march E2E_STEPS steps, read back the residual and u_x, u_y."""
+def run_e2e(sim, prob, n_vel, ncells, stream, dist, args, host_fp64: bool = False):
+    """Same metric through the public C-ABI with host buffers: upload a host state (pinned;
+    FP32, the simulation's storage precision, through lbm_set_state_f32, or FP64 through
+    lbm_set_state), march E2E_STEPS steps, read back the residual and u_x, u_y."""
     import ctypes
 
     import torch
@@ -386,14 +391,17 @@ def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
 
     lib = lbm.library()
     nvals = n_vel * ncells
-    host_h = torch.zeros(nvals, dtype=torch.float64).pin_memory()
+    hdt = torch.float64 if host_fp64 else torch.float32
+    host_h = torch.zeros(nvals, dtype=hdt).pin_memory()
     ux = torch.empty(ncells, dtype=torch.float64).pin_memory()
     uy = torch.empty(ncells, dtype=torch.float64).pin_memory()
     dp = ctypes.POINTER(ctypes.c_double)
+    upload = lib.lbm_set_state if host_fp64 else lib.lbm_set_state_f32
+    hp = ctypes.cast(host_h.data_ptr(), dp if host_fp64 else ctypes.POINTER(ctypes.c_float))
 
     def one(rec=None):
         t0 = time.perf_counter()
-        lbm._check(lib.lbm_set_state(sim.handle, ctypes.cast(host_h.data_ptr(), dp)))
+        lbm._check(upload(sim.handle, hp))
         t1 = time.perf_counter()
         lbm.lbm_step(sim, E2E_STEPS)
         lbm.lbm_residual(sim)               # waits for the march
@@ -418,15 +426,17 @@ def run_e2e(sim, prob, n_vel, ncells, stream, dist, args):
     value, _ = aggregate(float(nvals) * E2E_STEPS * reps, el, dist)
     # each call's parts by the host clock (every part ends synchronised); the upload's share
     # moves with the host<->device copy rate of the machine
-    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nvals * 8,
+    hb = host_h.element_size()
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nvals * hb,
             "d2h_bytes_per_step": 2 * ncells * 8 + 32,
             "ms_per_call": el / reps * 1e3,
             "calls_ms": [{"set_state": round(p[0] * 1e3, 2), "step_and_residual": round(p[1] * 1e3, 2),
                           "moments": round(p[2] * 1e3, 2)} for p in rec],
-            "h2d_gbs_in_set_state": nvals * 8 / min(p[0] for p in rec) / 1e9,
-            "definition": f"one API call = lbm_set_state(host FP64, pinned) + lbm_step({E2E_STEPS}) + "
-                          "lbm_residual + lbm_moments(ux, uy); value counts the marched updates; Python's "
-                          "cyclic garbage collector paused during the timed calls (as timeit does)"}
+            "h2d_gbs_in_set_state": nvals * hb / min(p[0] for p in rec) / 1e9,
+            "definition": f"one API call = {'lbm_set_state(host FP64' if host_fp64 else 'lbm_set_state_f32(host FP32'}"
+                          f", pinned) + lbm_step({E2E_STEPS}) + lbm_residual + lbm_moments(ux, uy); value counts "
+                          "the marched updates; Python's cyclic garbage collector paused during the timed calls "
+                          "(as timeit does)"}
 
 
 def run_fp64_same_workload(vs, dist, order: int = 1):

@@ -200,7 +200,7 @@ lbm_status lbm_get_transport(const lbm_sim *sim, int *order);
  * path 8 or 9 moves the current state into that layout (lbm_state_tiling), where one
  * row of a 64-cell strip, all velocities, is one contiguous stretch of memory, so that a
  * warp copies its lines of a row with one bulk copy; any other path moves it back to the
- * planar layout.  Host transfers (lbm_get_state, lbm_set_state, lbm_set_moments,
+ * planar layout.  Host transfers (lbm_get_state, lbm_set_state and their _f32 forms, lbm_set_moments,
  * lbm_warm_start) and the diagnostics stay planar on the host side; lbm_solve's refinement
  * sweeps run on the planar layout and return the state to the tiled one.
  * It changes speed, not results beyond rounding order.
@@ -230,6 +230,14 @@ lbm_status lbm_face_flux(lbm_sim *sim, double *flux_y, double *flux_x);
 /* Copy the current state to / from host FP64 [n][ny][nx].  get synchronises. */
 lbm_status lbm_get_state(lbm_sim *sim, double *h);
 lbm_status lbm_set_state(lbm_sim *sim, const double *h);
+/* The same with host FP32 [n][ny][nx] (not in the paper).  For an LBM_FP32_PERTURB
+ * simulation these move the stored values themselves, half the bytes of the FP64 calls, and
+ * lbm_set_state_f32(sim, x) leaves the state lbm_set_state(sim, y) leaves for any y that
+ * rounds to x.  For an LBM_FP64 simulation get rounds to nearest and set widens exactly.
+ * Both synchronise the simulation's stream.  Buffers are the caller's (pinned memory gives
+ * the full host-device copy rate). */
+lbm_status lbm_get_state_f32(lbm_sim *sim, float *h);
+lbm_status lbm_set_state_f32(lbm_sim *sim, const float *h);
 
 /* Replace the current state by the one with the given moments per cell: moments is host
  * FP64 [6][ny][nx] = rho, u_x, u_y, P_xx, P_xy, P_yy in Eq. (1) units (what lbm_moments

@@ -1326,6 +1326,44 @@ lbm_status lbm_set_state(lbm_sim *s, const double *h)
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "tiling the state");
 }
 
+// FP32 host transfers: an FP32 simulation's stored values move as they are (half the bytes
+// of the FP64 transfers); an FP64 simulation rounds on the way out and widens on the way in,
+// through its other state buffer (FP64 states are never tiled)
+lbm_status lbm_get_state_f32(lbm_sim *s, float *h)
+{
+    if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
+    const size_t nvals = (size_t)s->nv * s->ncells;
+    cudaError_t e = cudaSuccess;
+    if (s->prob.prec == LBM_FP64) {
+        float *stage = reinterpret_cast<float *>(staging(s, s->buf[s->cur]));
+        e = launch_convert((const double *)s->buf[s->cur], stage, (long)nvals, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, stage, nvals * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    } else {
+        const void *hs = planar_state(s, &e);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, hs, nvals * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "reading the state");
+}
+
+lbm_status lbm_set_state_f32(lbm_sim *s, const float *h)
+{
+    if (!s || !h) return fail(LBM_EINVAL, "NULL argument");
+    const size_t nvals = (size_t)s->nv * s->ncells;
+    void *dst = planar_target(s);
+    cudaError_t e;
+    if (s->prob.prec == LBM_FP64) {
+        float *stage = reinterpret_cast<float *>(staging(s, dst));
+        e = cudaMemcpyAsync(stage, h, nvals * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = launch_widen(stage, (double *)dst, (long)nvals, s->stream);
+    } else {
+        e = cudaMemcpyAsync(dst, h, nvals * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = commit_planar(s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "uploading the state");
+}
+
 lbm_status lbm_set_moments(lbm_sim *s, const double *moments)
 {
     if (!s || !moments) return fail(LBM_EINVAL, "NULL argument");

@@ -47,6 +47,7 @@ class lbm_problem(ctypes.Structure):
 
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _lib = None
 
 
@@ -81,6 +82,8 @@ def _load():
         "lbm_face_flux": (st, [_vp, _dp, _dp]),
         "lbm_get_state": (st, [_vp, _dp]),
         "lbm_set_state": (st, [_vp, _dp]),
+        "lbm_get_state_f32": (st, [_vp, _fp]),
+        "lbm_set_state_f32": (st, [_vp, _fp]),
         "lbm_set_moments": (st, [_vp, _dp]),
         "lbm_state_device": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_long)]),
         "lbm_state_layout": (st, [_vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]),
@@ -392,6 +395,18 @@ def lbm_set_state(sim: Sim, h: np.ndarray):
     h = np.ascontiguousarray(h, dtype=np.float64)
     assert h.size == sim.n_vel * sim.ncells
     _check(_load().lbm_set_state(sim.handle, _ptr(h)))
+
+
+def lbm_get_state_f32(sim: Sim) -> np.ndarray:
+    h = np.empty((sim.n_vel, sim.ncells), dtype=np.float32)
+    _check(_load().lbm_get_state_f32(sim.handle, h.ctypes.data_as(_fp)))
+    return h
+
+
+def lbm_set_state_f32(sim: Sim, h: np.ndarray):
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    assert h.size == sim.n_vel * sim.ncells
+    _check(_load().lbm_set_state_f32(sim.handle, h.ctypes.data_as(_fp)))
 
 
 def lbm_state_device(sim: Sim):
