@@ -1202,11 +1202,19 @@ lbm_status lbm_moments(lbm_sim *s, double *rho, double *ux, double *uy, double *
 {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     const int m = s->vs.m;
-    cudaError_t e;
-    const void *hs = planar_state(s, &e);
-    if (e == cudaSuccess)
-        e = launch_moments(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr, m, s->prob.nx, s->prob.ny,
-                           s->u_ref, s->moments, s->stream);
+    cudaError_t e = cudaSuccess;
+    const bool want_p = pxx || pxy || pyy;
+    // the moments read a strip-tiled state in place; the wall fluxes take the planar copy
+    const void *hs = nullptr;
+    if (wall_shear || !s->tiled) hs = planar_state(s, &e);
+    if (e == cudaSuccess) {
+        if (s->tiled)
+            e = launch_moments(s->prob.prec, s->buf[s->cur], s->args.pa, s->args.py, s->tab64, s->hdr, m, s->prob.nx,
+                               s->prob.ny, s->u_ref, s->moments, s->stream, s->tile_pitch, want_p);
+        else
+            e = launch_moments(s->prob.prec, hs, s->args.pa, s->args.py, s->tab64, s->hdr, m, s->prob.nx, s->prob.ny,
+                               s->u_ref, s->moments, s->stream, 0, want_p);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "launching the moments kernel");
     double *outs[6] = {rho, ux, uy, pxx, pxy, pyy};
     std::vector<double> tmp;
@@ -1326,6 +1334,41 @@ lbm_status lbm_set_state(lbm_sim *s, const double *h)
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "tiling the state");
 }
 
+// Host FP32 planar state -> the strip-tiled current state, through the planar copy in the
+// other buffer, in chunks of velocity planes: the copies run on the sim's private stream and
+// each chunk is tiled on the sim's stream as soon as it has landed, so that the tiling
+// overlaps the next chunk's copy (the host link, not the tiling, then sets the time).
+// Stream-ordered after the work already on the sim's stream.
+cudaError_t upload_tiled_f32(lbm_sim *s, const float *h, float *planar)
+{
+    constexpr int NCHUNK = 8;
+    cudaError_t e = make_capture_stream(s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev[NCHUNK + 1];
+    int made = 0;
+    for (; made <= NCHUNK && e == cudaSuccess; ++made) e = cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming);
+    if (e != cudaSuccess) --made;
+    if (e == cudaSuccess) e = cudaEventRecord(ev[NCHUNK], s->stream);         // earlier work on the sim's stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cap_stream, ev[NCHUNK], 0);
+    const int n = s->nv;
+    for (int k = 0; k < NCHUNK && e == cudaSuccess; ++k) {
+        const int a0 = (int)((long)n * k / NCHUNK), a1 = (int)((long)n * (k + 1) / NCHUNK);
+        if (a1 == a0) continue;
+        const size_t off = (size_t)a0 * s->ncells, cnt = (size_t)(a1 - a0) * s->ncells;
+        e = cudaMemcpyAsync(planar + off, h + off, cnt * sizeof(float), cudaMemcpyHostToDevice, s->cap_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k], s->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, ev[k], 0);
+        if (e == cudaSuccess)
+            e = launch_tile_convert_range(true, planar, (float *)s->buf[s->cur], n, a0, a1 - a0, s->prob.nx,
+                                          s->prob.ny, s->tile_pitch, s->stream);
+    }
+    // a copy still in flight after an error must not outlive the call (the host buffer is
+    // the caller's); events may be destroyed with work pending on them (release is deferred)
+    if (e != cudaSuccess) cudaStreamSynchronize(s->cap_stream);
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    return e;
+}
+
 // FP32 host transfers: an FP32 simulation's stored values move as they are (half the bytes
 // of the FP64 transfers); an FP64 simulation rounds on the way out and widens on the way in,
 // through its other state buffer (FP64 states are never tiled)
@@ -1356,9 +1399,10 @@ lbm_status lbm_set_state_f32(lbm_sim *s, const float *h)
         float *stage = reinterpret_cast<float *>(staging(s, dst));
         e = cudaMemcpyAsync(stage, h, nvals * sizeof(float), cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess) e = launch_widen(stage, (double *)dst, (long)nvals, s->stream);
-    } else {
+    } else if (!s->tiled) {
         e = cudaMemcpyAsync(dst, h, nvals * sizeof(float), cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = commit_planar(s);
+    } else {
+        e = upload_tiled_f32(s, h, (float *)dst);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "uploading the state");

@@ -114,8 +114,11 @@ cudaError_t launch_finalize_pairs(const double *partials, int nparts, double *ou
 cudaError_t launch_norms(const void *a, const void *b, long count, int prec, double *partials,
                          int nparts, double *out, cudaStream_t s);
 int norms_blocks(long count);
+// moments of a planar state (tile_pitch 0) or of the strip-tiled FP32 state (its tile pitch);
+// need_p false: rho, u_x, u_y only (outputs 3-5 are not written)
 cudaError_t launch_moments(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
-                           int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s);
+                           int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s, long tile_pitch = 0,
+                           bool need_p = true);
 cudaError_t launch_face_flux(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
                              int m, int nx, int ny, int cavity, double u_ref, double *flux_y,
                              double *flux_x, double *wall_sums, cudaStream_t s);
@@ -132,6 +135,9 @@ cudaError_t launch_convert(const double *src, float *dst, long count, cudaStream
 // FP32 state planar [a][y][x] <-> strip-tiled (to_tiled: planar -> tiled)
 cudaError_t launch_tile_convert(bool to_tiled, const float *src, float *dst, int n, int nx, int ny, long tile_pitch,
                                 cudaStream_t s);
+// the same for velocities a0 .. a0 + na - 1 of the n
+cudaError_t launch_tile_convert_range(bool to_tiled, const float *src, float *dst, int n, int a0, int na, int nx,
+                                      int ny, long tile_pitch, cudaStream_t s);
 // state h from device FP64 moments [6][ncells] (rho, u_x, u_y, P_xx, P_xy, P_yy)
 cudaError_t launch_moments_state(int prec, const double *mom, int nx, int ny, long pa, long py, int m,
                                  const TableHeader *hdr, double u_ref, void *h, cudaStream_t s);

@@ -139,8 +139,11 @@ __device__ __forceinline__ void df_add_prod(DFAcc &a, float xh, float xl, float 
     a.lo += e;
 }
 
+// The state is planar (tile_pitch 0: velocity planes pa apart) or strip-tiled (velocity
+// lines LBM_TILE_W apart from the cell's tile row).  P: also the P_ij sums (outputs 3-5).
+template <bool P>
 __global__ void moments_f32_kernel(const float *h, long pa, long py, int nx, const TableHeader *hdr, int m, long ncells,
-                                   double u_ref, double *out)
+                                   double u_ref, double *out, long tile_pitch)
 {
     __shared__ float s_x[LBM_MAX_M][4];   // xi hi, lo; xi^2 hi, lo
     if (threadIdx.x < m) {
@@ -154,33 +157,38 @@ __global__ void moments_f32_kernel(const float *h, long pa, long py, int nx, con
     __syncthreads();
     const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
-    const long y = c / nx, co = y * py + (c - y * nx);
+    const long y = c / nx, x = c - y * nx;
+    const long base = tile_pitch > 0 ? tile_off(x, y, m * m, tile_pitch) : y * py + x;
+    const long vstride = tile_pitch > 0 ? (long)LBM_TILE_W : pa;
     double s0 = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
     for (int iy = 0; iy < m; ++iy) {
         DFAcc r0 = {0.f, 0.f}, r1 = {0.f, 0.f}, r2 = {0.f, 0.f};
         for (int ix = 0; ix < m; ++ix) {
-            const float v = h[(long)(iy * m + ix) * pa + co];
+            const float v = h[base + (long)(iy * m + ix) * vstride];
             df_add(r0, v);
             df_add_prod(r1, s_x[ix][0], s_x[ix][1], v);
-            df_add_prod(r2, s_x[ix][2], s_x[ix][3], v);
+            if (P) df_add_prod(r2, s_x[ix][2], s_x[ix][3], v);
         }
         const double ey = hdr->xi1[iy];
-        const double a0 = (double)r0.hi + (double)r0.lo, a1 = (double)r1.hi + (double)r1.lo,
-                     a2 = (double)r2.hi + (double)r2.lo;
+        const double a0 = (double)r0.hi + (double)r0.lo, a1 = (double)r1.hi + (double)r1.lo;
         s0 += a0;
         sx += a1;
         sy += ey * a0;
-        sxx += a2;
-        sxy += ey * a1;
-        syy += ey * ey * a0;
+        if (P) {
+            sxx += (double)r2.hi + (double)r2.lo;
+            sxy += ey * a1;
+            syy += ey * ey * a0;
+        }
     }
     const double rho = 1.0 + u_ref * s0;
     out[c] = rho;
     out[ncells + c] = u_ref * sx / rho;
     out[2 * ncells + c] = u_ref * sy / rho;
-    out[3 * ncells + c] = 1.0 + u_ref * sxx;
-    out[4 * ncells + c] = u_ref * sxy;
-    out[5 * ncells + c] = 1.0 + u_ref * syy;
+    if (P) {
+        out[3 * ncells + c] = 1.0 + u_ref * sxx;
+        out[4 * ncells + c] = u_ref * sxy;
+        out[5 * ncells + c] = 1.0 + u_ref * syy;
+    }
 }
 
 // rho'_w of a wall face of the cell at plane offset co; dir: 0 bottom, 1 top, 2 left, 3 right
@@ -472,15 +480,16 @@ cudaError_t launch_widen(const float *src, double *dst, long count, cudaStream_t
 // Planar [a][y][x] <-> strip-tiled FP32 state: one block per row y of tile t, threads over
 // the tile row's n * 64 values (contiguous in both layouts for each velocity); the padding
 // positions of the tiled layout (x outside [0, nx)) are written as zero.
+// Velocities a0 .. a0 + na - 1 only (the whole state: 0, n).
 __global__ void __launch_bounds__(256) tile_convert_kernel(int to_tiled, const float *__restrict__ src,
                                                           float *__restrict__ dst, int n, int nx, int ny,
-                                                          long tile_pitch)
+                                                          long tile_pitch, int a0, int na)
 {
     const int t = blockIdx.x, y = blockIdx.y;
     const long ncells = (long)nx * ny;
     const long trow = (long)t * tile_pitch + (long)y * n * LBM_TILE_W;
     const int x0 = t * LBM_TILE_W - LBM_TILE_SHIFT;
-    for (int i = threadIdx.x; i < n * LBM_TILE_W; i += blockDim.x) {
+    for (int i = a0 * LBM_TILE_W + threadIdx.x; i < (a0 + na) * LBM_TILE_W; i += blockDim.x) {
         const int a = i / LBM_TILE_W, p = i - a * LBM_TILE_W;
         const int x = x0 + p;
         const bool in = x >= 0 && x < nx;
@@ -494,7 +503,17 @@ cudaError_t launch_tile_convert(bool to_tiled, const float *src, float *dst, int
                                 cudaStream_t s)
 {
     const dim3 grid((unsigned)tiles_for(nx), (unsigned)ny);
-    tile_convert_kernel<<<grid, 256, 0, s>>>(to_tiled ? 1 : 0, src, dst, n, nx, ny, tile_pitch);
+    tile_convert_kernel<<<grid, 256, 0, s>>>(to_tiled ? 1 : 0, src, dst, n, nx, ny, tile_pitch, 0, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_convert_range(bool to_tiled, const float *src, float *dst, int n, int a0, int na, int nx,
+                                      int ny, long tile_pitch, cudaStream_t s)
+{
+    if (a0 < 0 || na < 0 || a0 + na > n) return cudaErrorInvalidValue;
+    if (na == 0) return cudaSuccess;
+    const dim3 grid((unsigned)tiles_for(nx), (unsigned)ny);
+    tile_convert_kernel<<<grid, 256, 0, s>>>(to_tiled ? 1 : 0, src, dst, n, nx, ny, tile_pitch, a0, na);
     return cudaGetLastError();
 }
 
@@ -536,15 +555,22 @@ cudaError_t launch_norms(const void *a, const void *b, long count, int prec, dou
 }
 
 cudaError_t launch_moments(int prec, const void *h, long pa, long py, const double *tab64, const TableHeader *hdr,
-                           int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s)
+                           int m, int nx, int ny, double u_ref, double *out6, cudaStream_t s, long tile_pitch,
+                           bool need_p)
 {
     (void)tab64;
     const long ncells = (long)nx * ny;
     const int grid = (int)((ncells + 255) / 256);
-    if (prec == 0)
+    if (prec == 0) {
+        if (tile_pitch > 0) return cudaErrorInvalidValue;    // FP64 states are never tiled
         moments_kernel<double><<<grid, 256, 0, s>>>((const double *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
-    else
-        moments_f32_kernel<<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6);
+    } else if (need_p) {
+        moments_f32_kernel<true><<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6,
+                                                      tile_pitch);
+    } else {
+        moments_f32_kernel<false><<<grid, 256, 0, s>>>((const float *)h, pa, py, nx, hdr, m, ncells, u_ref, out6,
+                                                       tile_pitch);
+    }
     return cudaGetLastError();
 }
 

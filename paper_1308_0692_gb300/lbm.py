@@ -356,12 +356,15 @@ def lbm_residual(sim: Sim):
     return r.value, s.value
 
 
-def lbm_moments(sim: Sim, wall_shear: bool = True):
+MOMENT_NAMES = ("rho", "ux", "uy", "pxx", "pxy", "pyy")
+
+
+def lbm_moments(sim: Sim, wall_shear: bool = True, which=MOMENT_NAMES):
+    """The moments named in `which` (the others are not requested: NULL outputs)."""
     n = sim.ncells
-    outs = {k: np.empty(n) for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy")}
+    outs = {k: np.empty(n) for k in MOMENT_NAMES if k in which}
     ws = np.empty(4) if wall_shear else None
-    _check(_load().lbm_moments(sim.handle, *[_ptr(outs[k]) for k in ("rho", "ux", "uy", "pxx", "pxy", "pyy")],
-                               _ptr(ws)))
+    _check(_load().lbm_moments(sim.handle, *[_ptr(outs.get(k)) for k in MOMENT_NAMES], _ptr(ws)))
     res = {k: v.reshape(sim.prob.ny, sim.prob.nx) for k, v in outs.items()}
     if ws is not None:
         res["wall_shear"] = ws
