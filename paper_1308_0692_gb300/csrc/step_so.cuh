@@ -93,10 +93,14 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
     // touches one or two cells of a segment: their sums are formed cooperatively, the
     // velocities towards that wall dealt to the lanes (products in the arithmetic type, the
     // sum in FP64), instead of by every lane of the segment.
-    double rb = 0.0, rt = 0.0, rl = 0.0, rr = 0.0;
+    // the densities and the wall terms of Eq. (8) in the arithmetic type, formed once per
+    // lane and only in warps with a lane at that wall (FP64 work runs on this GPU's slowest
+    // pipe: forming all four on every lane of a wall segment kept it two thirds busy)
+    TC rb = 0, rt = 0, rl = 0, rr = 0;
+    TC ub = 0, ut = 0, db = 0, dt = 0;
+    const bool rows_wall = PART && __any_sync(FULL, in_grid && (y == 0 || y == ny - 1));
     if (PART) {
         double sb = 0.0, st = 0.0, sls = 0.0, srs = 0.0;
-        const bool rows_wall = __any_sync(FULL, in_grid && (y == 0 || y == ny - 1));
         if (work && rows_wall) {
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
@@ -153,18 +157,23 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
         s_wall[PART ? 2 : 0][g][sl][lane] = sls;
         s_wall[PART ? 3 : 0][g][sl][lane] = srs;
         __syncthreads();
-        sb = st = sls = srs = 0.0;
+        // totals over the warps of the segment
+        auto total = [&](int k) {
+            double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < G; ++q) {
-            sb += s_wall[0][q][sl][lane];
-            st += s_wall[PART ? 1 : 0][q][sl][lane];
-            sls += s_wall[PART ? 2 : 0][q][sl][lane];
-            srs += s_wall[PART ? 3 : 0][q][sl][lane];
+            for (int q = 0; q < G; ++q) t += s_wall[k][q][sl][lane];
+            return t;
+        };
+        if (__any_sync(FULL, in_grid && y == 0)) rb = (TC)(total(0) * a.inv_dy_wall);
+        if (__any_sync(FULL, in_grid && y == ny - 1)) rt = (TC)(total(1) * a.inv_dy_wall);
+        if (cav && __any_sync(FULL, in_grid && x == 0)) rl = (TC)(total(2) * a.inv_dx_wall);
+        if (cav && __any_sync(FULL, in_grid && x == nx - 1)) rr = (TC)(total(3) * a.inv_dx_wall);
+        if (rows_wall) {
+            ub = (TC)a.u_bottom;
+            ut = (TC)a.u_top;
+            db = a.homogeneous ? TC(0) : (TC)(a.u_bottom * a.inv_u_ref);
+            dt = a.homogeneous ? TC(0) : (TC)(a.u_top * a.inv_u_ref);
         }
-        rb = sb * a.inv_dy_wall;
-        rt = st * a.inv_dy_wall;
-        rl = sls * a.inv_dx_wall;
-        rr = srs * a.inv_dx_wall;
     }
 
     // ---- second-order transport + moment row sums ----
@@ -199,9 +208,9 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
             const long c1y = ys > 0 ? cym1 : cyp1, c2y = ys > 0 ? cym2 : cyp2;
             // wall-emitted population across a bottom or top wall face (Eq. 8), PART only
             const TC gy = (PART && ys != 0 && y0) ? nuy : TC(0);
-            const TC rho_y = (TC)(ys > 0 ? rb : rt);
-            const TC u_y = (TC)(ys > 0 ? a.u_bottom : a.u_top);
-            const TC drive_y = a.homogeneous ? TC(0) : (TC)((ys > 0 ? a.u_bottom : a.u_top) * a.inv_u_ref);
+            const TC rho_y = ys > 0 ? rb : rt;
+            const TC u_y = ys > 0 ? ub : ut;
+            const TC drive_y = ys > 0 ? db : dt;
             const TC wy = pick<TC>(a.w1, a.w1_f, iy);
             TC R = 0, X = 0;
 #pragma unroll
@@ -227,7 +236,7 @@ __device__ __forceinline__ void step_so_body(const StepArgs &a, const int bid)
                     v = fma_(-ax, hc, v);
                     v = fma_(bx, h1x, v);
                     v = fma_(cx, h2x, v);
-                    if (PART && x0) v += nu * (pick<TC>(a.w1, a.w1_f, ix) * wy * (TC)(xs > 0 ? rl : rr));
+                    if (PART && x0) v += nu * (pick<TC>(a.w1, a.w1_f, ix) * wy * (xs > 0 ? rl : rr));
                 }
                 if (PART && gy != TC(0)) {
                     const TC wxy = pick<TC>(a.w1, a.w1_f, ix) * wy;
