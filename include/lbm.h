@@ -343,8 +343,10 @@ lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *warps_per_segment, in
  * the launch's steps from one counter, and an item waits only for its own instance's
  * previous step (no grid-wide barrier between steps).  rows_per_chunk: rows of one march
  * item (>= 4), or 0 to let the library plan it at every rebuild of the item lists (about
- * 1.7 items per resident warp group and step, 4 to 128 rows).  warps_per_item: M (one
- * velocity row per warp), M / 2 (two rows per warp, two items per block; the default, 0).
+ * 1.3 items per resident warp group and step with eight or more live cavities, 1.7 with
+ * fewer, 4 to 128 rows).  warps_per_item: M (one velocity row per warp), M / 2 (two rows
+ * per warp, two items per block of eight warps), for M = 8 also 2 (four rows per warp, four
+ * items per block); 0 the default: four rows per warp for M = 8, two for M = 4.
  * lbm_batch_get_march reports the switch, the rows per chunk in use, the number of march
  * items per step, the march kernel's grid and its warps per item (outputs may be NULL). */
 lbm_status lbm_batch_set_march(lbm_batch *b, int on, int rows_per_chunk, int warps_per_item);

@@ -952,7 +952,7 @@ __device__ void residual_decision(const BatchArgs &a, int i, long s)
 // the last item of an instance's step evaluates its residual on residual steps (freezing it
 // when converged) and then publishes the completed step.
 template <int M, int G, int MODE>
-__global__ void __launch_bounds__(256, G == M ? 3 : 2) batch_march_kernel(const BatchArgs a)
+__global__ void __launch_bounds__(256, G == M ? 3 : (2 * G == M ? 2 : 1)) batch_march_kernel(const BatchArgs a)
 {
     using Sh = MarchShared<M, G>;
     constexpr int SUB = Sh::SUB;
@@ -1073,7 +1073,8 @@ const std::vector<Variant> &variants()
 }
 
 // column-march kernels (cavity instances): M = 4 or 8 nodes per axis, G warps per item
-// (one velocity row per warp with G = M, two with G = M / 2); dynamic shared memory
+// (one velocity row per warp with G = M, two with G = M / 2, four with G = M / 4); dynamic
+// shared memory
 struct MarchFns {
     void *march, *correct;
     int g;
@@ -1087,17 +1088,21 @@ MarchFns march_fns_of()
             sizeof(MarchShared<M, G>)};
 }
 
-// g <= 0: the default shape, two velocity rows per warp (G = M / 2: 21 % faster than one
-// row per warp on 32 cavities of 128^2 -- the per-row fixed costs and the moment exchange
-// are shared by twice the updates)
+// g <= 0: the default shape, four velocity rows per warp for M = 8 (G = 2: 5-6 % faster
+// than two rows on 32 cavities of 128^2 and 8 of 256^2, equal on 128 of 128^2; two rows had
+// been 21 % faster than one -- the per-row fixed costs and the moment exchange are shared by
+// more updates), two rows for M = 4
 MarchFns march_fns(int m, int g = 0)
 {
-    if (m == 8) return g == 8 ? march_fns_of<8, 8>() : march_fns_of<8, 4>();
+    if (m == 8) return g == 8 ? march_fns_of<8, 8>() : (g == 4 ? march_fns_of<8, 4>() : march_fns_of<8, 2>());
     if (m == 4) return g == 4 ? march_fns_of<4, 4>() : march_fns_of<4, 2>();
     return {nullptr, nullptr, 0, 0};
 }
 
-bool march_shape_ok(int m, int g) { return g <= 0 || (m == 8 && (g == 8 || g == 4)) || (m == 4 && (g == 4 || g == 2)); }
+bool march_shape_ok(int m, int g)
+{
+    return g <= 0 || (m == 8 && (g == 8 || g == 4 || g == 2)) || (m == 4 && (g == 4 || g == 2));
+}
 
 struct DefectShape {
     void *fn;

@@ -67,9 +67,8 @@ def test_batch_matches_oracle_per_instance(schedule, march):
         assert err <= FP32_TOL_PER_STEP * steps, (i, err)
 
 
-@pytest.mark.parametrize("n_half", [2, 4])
-@pytest.mark.parametrize("two_rows", [False, True])
-def test_batch_column_march_odd_shapes(n_half, two_rows):
+@pytest.mark.parametrize("n_half,rows_per_warp", [(2, 1), (2, 2), (4, 1), (4, 2), (4, 4)])
+def test_batch_column_march_odd_shapes(n_half, rows_per_warp):
     """The column march on ragged strips, short chunks and tiny cavities agrees with the FP64
     oracle step by step (and the Couette instance beside them with the segment kernel)."""
     vs = lbm.lbm_make_velocity_set(lbm.LBM_HALF_RANGE_GH, n_half)
@@ -77,9 +76,9 @@ def test_batch_column_march_odd_shapes(n_half, two_rows):
              for g, nx, ny, kn, ub, ut in ODD]
     b = lbm.lbm_batch_init(vs, probs, stream=torch.cuda.Stream())
     m = 2 * n_half
-    lbm.lbm_batch_set_march(b, True, 0, m // 2 if two_rows else m)     # warps per item
+    lbm.lbm_batch_set_march(b, True, 0, m // rows_per_warp)     # warps per item
     info = lbm.lbm_batch_get_march(b)
-    assert info["on"] and info["items"] > 0 and info["warps_per_item"] == (m // 2 if two_rows else m)
+    assert info["on"] and info["items"] > 0 and info["warps_per_item"] == m // rows_per_warp
     steps = 25
     lbm.lbm_batch_advance(b, steps, 0.0)
     assert lbm.lbm_batch_poll(b) == (len(ODD), steps)
@@ -232,7 +231,7 @@ def test_batch_chunk_height_does_not_change_results():
                 lbm.lbm_batch_set_march(b, True, 3)
             assert e.value.status == lbm.LBM_EINVAL
             with pytest.raises(lbm.LBMError) as e:
-                lbm.lbm_batch_set_march(b, True, 0, 3)        # warps per item: 8 or 4 here
+                lbm.lbm_batch_set_march(b, True, 0, 3)        # warps per item: 8, 4 or 2 here
             assert e.value.status == lbm.LBM_EINVAL
         b.close()
     for other in states[1:]:
