@@ -215,7 +215,9 @@ lbm_status lbm_residual(lbm_sim *sim, double *r, long *step);
 
 /* Macroscopic fields of the current state, Eq. (1) units, linearised about rho = 1:
  *   rho = 1 + u_ref sum h, u = u_ref sum xi h / rho, P_ij = delta_ij + u_ref sum xi_i xi_j h.
- * Each output is host FP64 [ny][nx] or NULL.  wall_shear (NULL or double[4]) receives
+ * Each output is host FP64 [ny][nx] or NULL (with pxx, pxy and pyy all NULL their sums are
+ * not formed; a strip-tiled FP32 state is read through its tiles in place, the wall shear
+ * from a planar copy in the other state buffer).  wall_shear (NULL or double[4]) receives
  * the mean tangential momentum flux through the bottom, top, left and right walls
  * (the drag the gas exerts; left/right are 0 for Couette).  Synchronises. */
 lbm_status lbm_moments(lbm_sim *sim, double *rho, double *ux, double *uy, double *pxx,
