@@ -225,7 +225,7 @@ struct HybShared {
 // A cell with an interface face (a neighbour in the other set): one warp, warp `wi` of the
 // block's shared buffers; arithmetic in the storage type TS.
 template <typename TS>
-__device__ void interface_cell(const HybArgs &a, HybShared<TS> &sh, int wi, int c, double dt, double dx, double dy,
+__device__ void interface_cell(const HybArgs &a, HybShared<TS> &sh, int wi, int c, double dt_dx, double dt_dy,
                                int resid)
 {
     using T = TS;
@@ -272,7 +272,7 @@ __device__ void interface_cell(const HybArgs &a, HybShared<TS> &sh, int wi, int 
             face_moments(H, lower ? ph : nb, axis, false, dn);
             face_moments(S, nbv[f], axis, lower, got);
             face_moments(S, hc, axis, !lower, sent);
-            const T fac = (T)(dt / (axis == 0 ? dx : dy));
+            const T fac = (T)(axis == 0 ? dt_dx : dt_dy);
             for (int q = 0; q < 3; ++q) {
                 const T want = lower ? up[q] - dn[q] : dn[q] - up[q];
                 cr[q] += fac * (want - (got[q] - sent[q]));
@@ -400,18 +400,24 @@ __device__ __forceinline__ void plain_tiles(const PlainArgs<TC> &p, const int2 *
     TC rw[4] = {0, 0, 0, 0};
     if (__syncthreads_or((int)(on && (wl || wr || wb || wt)))) {
         double pw[4] = {0.0, 0.0, 0.0, 0.0};     // outflow through the bottom, top, left, right walls
+        // products and the sums over one velocity row in the arithmetic type, the sums over
+        // rows and warps in FP64 (as the single-domain kernels do; per-velocity FP64 sums kept
+        // the FP64 pipe of the FP32 hybrid step 38 % busy)
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int iy = g * RPL + r;
+            TC ys = 0, ls = 0, rs = 0;
 #pragma unroll
             for (int ix = 0; ix < M; ++ix) {
-                // products in the arithmetic type, sums in FP64
                 const TC v = h[oc + (long)HST * (iy * M + ix)];
-                if (iy < HALF) pw[0] -= (double)(p.xi[iy] * v);
-                if (iy >= M - HALF) pw[1] += (double)(p.xi[iy] * v);
-                if (ix < HALF) pw[2] -= (double)(p.xi[ix] * v);
-                if (ix >= M - HALF) pw[3] += (double)(p.xi[ix] * v);
+                ys += v;
+                if (ix < HALF) ls -= p.xi[ix] * v;
+                if (ix >= M - HALF) rs += p.xi[ix] * v;
             }
+            if (iy < HALF) pw[0] -= (double)(p.xi[iy] * ys);
+            if (iy >= M - HALF) pw[1] += (double)(p.xi[iy] * ys);
+            pw[2] += (double)ls;
+            pw[3] += (double)rs;
         }
         if (G > 1) {
 #pragma unroll
@@ -563,8 +569,8 @@ constexpr int hybrid_min_blocks() { return sizeof(TS) == 8 ? 1 : (N == 5 ? 6 : 8
 
 template <int N, typename TS>
 __global__ void __launch_bounds__(32 * HWARPS, hybrid_min_blocks<N, TS>()) hybrid_step_kernel(const HybArgs a, const PlainArgs<TS> ph,
-                                                                   const PlainArgs<TS> pf, const StepLists L, double dt,
-                                                                   double dx, double dy, int resid)
+                                                                   const PlainArgs<TS> pf, const StepLists L,
+                                                                   double dt_dx, double dt_dy, int resid)
 {
     constexpr int GH = half_warps(N);
     __shared__ union {
@@ -577,7 +583,7 @@ __global__ void __launch_bounds__(32 * HWARPS, hybrid_min_blocks<N, TS>()) hybri
     const int hbk = (L.ntiles[0] + HWARPS / GH - 1) / (HWARPS / GH);
     if (bid < ifb) {
         const int wi = threadIdx.x >> 5, ci = bid * HWARPS + wi;
-        if (ci < L.ncells) interface_cell<TS>(a, u.sh, wi, L.cells[ci], dt, dx, dy, resid);    // whole warps
+        if (ci < L.ncells) interface_cell<TS>(a, u.sh, wi, L.cells[ci], dt_dx, dt_dy, resid);    // whole warps
     } else if (bid < ifb + hbk) {
         plain_tiles<2 * N, GH>(ph, L.tiles[0], L.ntiles[0], bid - ifb, resid, u.hx);
     } else {
@@ -587,26 +593,26 @@ __global__ void __launch_bounds__(32 * HWARPS, hybrid_min_blocks<N, TS>()) hybri
 
 template <int N, typename TS>
 cudaError_t launch_step_n(const HybArgs &a, const PlainArgs<TS> &ph, const PlainArgs<TS> &pf, const StepLists &L,
-                          double dt, double dx, double dy, int resid, cudaStream_t st)
+                          double dt_dx, double dt_dy, int resid, cudaStream_t st)
 {
     constexpr int GH = half_warps(N);
     const int blocks = (L.ncells + HWARPS - 1) / HWARPS + (L.ntiles[0] + HWARPS / GH - 1) / (HWARPS / GH) +
                        (L.ntiles[1] + HWARPS - 1) / HWARPS;
     if (blocks == 0) return cudaSuccess;
-    hybrid_step_kernel<N, TS><<<blocks, 32 * HWARPS, 0, st>>>(a, ph, pf, L, dt, dx, dy, resid);
+    hybrid_step_kernel<N, TS><<<blocks, 32 * HWARPS, 0, st>>>(a, ph, pf, L, dt_dx, dt_dy, resid);
     return cudaGetLastError();
 }
 
 template <typename TS>
 cudaError_t launch_hybrid_step(int n, const HybArgs &a, const PlainArgs<TS> &ph, const PlainArgs<TS> &pf,
-                               const StepLists &L, double dt, double dx, double dy, int resid, cudaStream_t st)
+                               const StepLists &L, double dt_dx, double dt_dy, int resid, cudaStream_t st)
 {
     switch (n) {
-    case 2: return launch_step_n<2, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 3: return launch_step_n<3, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 4: return launch_step_n<4, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 5: return launch_step_n<5, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
-    case 6: return launch_step_n<6, TS>(a, ph, pf, L, dt, dx, dy, resid, st);
+    case 2: return launch_step_n<2, TS>(a, ph, pf, L, dt_dx, dt_dy, resid, st);
+    case 3: return launch_step_n<3, TS>(a, ph, pf, L, dt_dx, dt_dy, resid, st);
+    case 4: return launch_step_n<4, TS>(a, ph, pf, L, dt_dx, dt_dy, resid, st);
+    case 5: return launch_step_n<5, TS>(a, ph, pf, L, dt_dx, dt_dy, resid, st);
+    case 6: return launch_step_n<6, TS>(a, ph, pf, L, dt_dx, dt_dy, resid, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -937,8 +943,10 @@ cudaError_t hybrid_launch(const lbm_hybrid *hb, const HybArgs &a0, int resid)
         L.tiles[t] = hb->d_tiles[t];
         L.ntiles[t] = hb->n_tiles[t];
     }
-    return launch_hybrid_step<TS>(hb->n_half, a, plain_args<TS>(hb, 0, a), plain_args<TS>(hb, 1, a), L, hb->dt, hb->dx,
-                                  hb->dy, resid, hb->stream);
+    // the interface faces' dt / dx and dt / dy, divided once here (the device's FP64 divide
+    // would run on every lane of every interface warp)
+    return launch_hybrid_step<TS>(hb->n_half, a, plain_args<TS>(hb, 0, a), plain_args<TS>(hb, 1, a), L,
+                                  hb->dt / hb->dx, hb->dt / hb->dy, resid, hb->stream);
 }
 
 // the two-stage reduction of the residual partials into d_res[0..1]
